@@ -1,0 +1,258 @@
+/*
+ * mdls.h -- C ABI of the B300 (sm_103a) library for the MDFIS local-search hot path of
+ * Lei & Hao, "A GPU-Accelerated Hybrid Method for a Class of Multi-Depot Vehicle Routing
+ * Problems" (MDFIHA-ETGA).
+ *
+ * The library evaluates whole neighbourhoods of Relocate, Swap, 2-opt*, Depot-Insert and
+ * Depot-Replace (Section 3.2.2) for many solutions at once, scores every move under the
+ * multi-penalty evaluation function F (Eq. 2, detailed in Eq. A1) from per-route prefix and
+ * suffix segment summaries, selects a leader and non-conflicting followers (Section 3.2.5),
+ * applies them and rebuilds only the touched routes (Alg. 2, "update tensor T_s").
+ *
+ * Conventions shared by every call:
+ *   - Every call returns md_status.  On failure md_last_error() returns a message describing
+ *     the first error of the calling thread (thread-local; valid until the next failing call).
+ *   - Handles are opaque.  The library copies every host input it needs and owns all the
+ *     device memory behind a handle until the matching *_destroy call.
+ *   - Device work is stream ordered on `stream`, a cudaStream_t passed as void* (NULL = the
+ *     legacy default stream).  Calls that return host data synchronise that stream.
+ *   - Node ids: depots are 0..n_depots-1, customers n_depots..n_depots+n_customers-1; at most
+ *     16384 nodes (move ids pack two node ids in 14 bits each).
+ *   - Fixed point: every distance and time is an integer equal to round(scale * value), with
+ *     distances rounded half away from zero from the FP64 Euclidean distance; travel time
+ *     equals distance (t_ij = c_ij).  Demands and capacities are plain integers.
+ *   - Move ids: op << 32 | u << 18 | v << 4 | variant (see MD_OP_*); they are independent of
+ *     how routes are laid out in memory and break every tie.
+ */
+#ifndef MDLS_H
+#define MDLS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum md_status {
+    MD_OK = 0,
+    MD_ERR_ARG = 1,      /* invalid argument or input data */
+    MD_ERR_CUDA = 2,     /* a CUDA runtime call failed */
+    MD_ERR_CAPACITY = 3, /* a route or buffer capacity was exceeded */
+    MD_ERR_TIMEOUT = 4,  /* a bounded device-side wait gave up */
+    MD_ERR_STATE = 5     /* calls made in an order the object does not allow */
+} md_status;
+
+/* Instance variant flags (Section 1: MDVRP, MDVRPTW, MDOVRP). */
+#define MD_VARIANT_TW 1u        /* time windows: time-warp penalty V1 */
+#define MD_VARIANT_OPEN 2u      /* open routes: no return arc, no closure term */
+#define MD_VARIANT_SYMMETRIC 4u /* 2-node sequences may be reversed (Section 3.2.2) */
+
+/* Operators (Section 3.2.2).  Variants per operator:
+ *   RELOCATE  0: seq(u) of 1 node after v        1: 1 node before v (v first on its route)
+ *             2: seq(u) of 2 nodes after v       3: 2 nodes before v (v first)
+ *             4: 2 nodes reversed after v        5: 2 nodes reversed before v (v first)
+ *             (4 and 5 only on symmetric instances)
+ *   SWAP      (|seq(u)|, |seq(v)|) = 0:(1,1) 1:(2,1) 2:(1,2) 3:(2,2); on symmetric instances
+ *             also 4:(2r,1) 5:(1,2r) 6:(2r,2) 7:(2,2r) 8:(2r,2r), r = reversed where placed
+ *   TWO_OPT_STAR  0: head(..u) + tail(v..) and head(..pred v) + tail(succ u..)
+ *   DEPOT_INSERT  u = c_k, v = depot d: [ds..c_k, d] and [d, c_k+1..de], 1 <= k < L
+ *   DEPOT_REPLACE u = first customer of the route, v = depot d, variant = case 0: departure,
+ *                 1: arrival, 2: both; one move per (route, d): the best case by (dF, case)
+ */
+#define MD_OP_RELOCATE 0
+#define MD_OP_SWAP 1
+#define MD_OP_TWO_OPT_STAR 2
+#define MD_OP_DEPOT_INSERT 3
+#define MD_OP_DEPOT_REPLACE 4
+#define MD_N_OPS 5
+
+/* md_eval_neighborhood flags */
+#define MD_EVAL_DUMP 1u      /* also write every scored move to the moves object's dump list */
+#define MD_EVAL_FOLLOWERS 2u /* record the best follower of every route pair (multi-move) */
+
+/* md_apply_and_rebuild flags */
+#define MD_APPLY_UPDATE_LAMBDA 1u /* adapt lambda after an accepted step (Section 3.2.1) */
+
+typedef struct md_instance md_instance;
+typedef struct md_solutions md_solutions;
+typedef struct md_moves md_moves;
+
+/* Problem data of Section 1 (Eq. 1).  All arrays have n_depots + n_customers entries, depots
+ * first; the library copies them.  Times (service, tw_early, tw_late, D) are fixed point
+ * (already multiplied by `scale`); coordinates are plain doubles and are scaled when the
+ * distances are built.  Depot entries of demand and service are ignored (taken as 0).
+ * tw_early / tw_late may be NULL when MD_VARIANT_TW is not set. */
+typedef struct md_instance_desc {
+    int32_t n_depots;
+    int32_t n_customers;
+    const double *x;
+    const double *y;
+    const int32_t *demand;
+    const int32_t *service;
+    const int32_t *tw_early;
+    const int32_t *tw_late;
+    int32_t Q;       /* vehicle capacity */
+    int32_t N_V;     /* vehicles per depot */
+    int32_t D;       /* maximum route duration, fixed point; 0 = no limit */
+    uint32_t variant;/* MD_VARIANT_* */
+    double scale;    /* fixed-point factor, e.g. 100 */
+    int32_t theta;   /* granular neighbours per customer (Section 3.2.3); 0 = all customers */
+} md_instance_desc;
+
+/* One scored move, as written by MD_EVAL_DUMP.  Deltas are new minus old for: total distance D,
+ * time warp (V1 before Gamma), load excess (V2 before Theta/Q), duration excess (V3 before
+ * Theta/D), depot violations (V4 before Theta: closures plus vehicle excess).  dF combines
+ * them in FP64 as (((dD + w1 dTW) + w2 dLoad) + w3 dDur) + w4 dV4 with w1 = lambda1 Gamma,
+ * w2 = lambda2 Theta / Q, w3 = lambda3 Theta / D (0 without D), w4 = lambda4 Theta (Eq. A1). */
+typedef struct md_move {
+    uint64_t id;
+    int64_t dD, dTW, dLoad, dDur, dV4;
+    double dF;
+    int32_t sol;   /* solution index */
+    int32_t pad;
+} md_move;
+
+/* Settings of the MDFIS descent (Alg. 2). */
+typedef struct md_config {
+    int32_t n_ops;          /* operators per pass, 1..8 */
+    int32_t max_pass;       /* search depth delta: passes of the while loop of Alg. 2 */
+    const uint8_t *op_perm; /* host [n_sol * max_pass * n_ops]: the operator order of every pass
+                               (Alg. 2 draws a random permutation; the caller supplies the draws) */
+    const float *lambda0;   /* host [n_sol * 4] initial lambda, or NULL for (1, 1, 1, 1) */
+    int32_t multi_move;     /* 1: leader + followers (Section 3.2.5); 0: leader only */
+    int32_t lambda_update;  /* 1: adapt lambda after every accepted step (kappa = 0.5) */
+    int32_t use_graph;      /* 1: replay one captured CUDA graph per pass */
+    int32_t poll_every;     /* passes between host checks of the per-solution done flags */
+} md_config;
+
+/* Totals over all solutions of one md_descend call. */
+typedef struct md_stats {
+    int64_t moves_scored;   /* scored move tuples (op, u, v, variant) */
+    int64_t steps;          /* operator evaluations (solution x operator) */
+    int64_t accepted_steps; /* steps that applied a leader */
+    int64_t applied_moves;  /* leaders + followers applied */
+    int64_t passes_max;     /* largest number of passes any solution ran */
+    int64_t launches;       /* kernels launched by the call */
+} md_stats;
+
+/* Message for the calling thread's last failing call ("" if none). */
+const char *md_last_error(void);
+
+/* Builds the instance on the device (Section 1; Eq. A1 for Theta = 2 max c - min c and
+ * Gamma = sum c / sum t; Section 3.2.3 for the neighbour lists: edge (u,v) is pruned when
+ * e_u + s_u + t_uv > l_v (time windows only), then the theta candidates with the smallest
+ * eta_uv of Eq. 3 (alpha = 1, beta = 10; ties by node id) are kept).
+ * MD_ERR_ARG: null pointers, sizes out of range (n_depots < 1, n_customers < 1, more than
+ * 16384 nodes, Q < 1, N_V < 1, theta < 0), windows with tw_early > tw_late or above 2^30. */
+md_status md_instance_create(const md_instance_desc *desc, md_instance **out);
+md_status md_instance_destroy(md_instance *inst);
+
+/* Theta (int64) and Gamma (FP64) of Eq. A1. */
+md_status md_instance_params(const md_instance *inst, int64_t *theta_big, double *gamma);
+
+/* Copies the distance matrix (int32, [n_nodes * n_nodes], row-major) to host memory. */
+md_status md_instance_read_dist(const md_instance *inst, int32_t *host_out);
+
+/* Copies the neighbour lists: host_nbr [n_customers * theta] node ids (row = customer index),
+ * host_cnt [n_customers] list lengths.  MD_ERR_STATE when theta = 0. */
+md_status md_instance_read_neighbors(const md_instance *inst, int32_t *host_nbr, int32_t *host_cnt);
+
+/* Allocates n_sol solutions of the instance, each with r_slots route slots of up to k_max
+ * customers.  A route slot holds one route [ds, c_1..c_L, de] (Eq. 1 notation) with its
+ * per-customer prefix/suffix segment summaries (Section 3.2.2, sequence concatenation).
+ * MD_ERR_ARG when k_max is so large that int32 summaries could overflow. */
+md_status md_solutions_create(const md_instance *inst, int32_t n_sol, int32_t r_slots,
+                              int32_t k_max, md_solutions **out);
+md_status md_solutions_destroy(md_solutions *sols);
+
+/* Loads routes from host memory: route i of the flattened list is
+ * route_nodes[route_offsets[i] .. route_offsets[i+1]) = [ds, c_1..c_L, de] (de is kept but has
+ * no meaning for open routes); solution s owns the next routes_per_sol[s] routes.  Validates
+ * that every customer appears exactly once per solution and that every route is non-empty with
+ * depots at both ends (MD_ERR_ARG), and that it fits the slots (MD_ERR_CAPACITY).  Resets the
+ * per-solution lambda to (1, 1, 1, 1) and rebuilds every summary on the device. */
+md_status md_solutions_load(md_solutions *sols, const int32_t *route_nodes,
+                            const int64_t *route_offsets, const int32_t *routes_per_sol,
+                            void *stream);
+
+/* Device-to-device copy of the routes of src into dst (same instance and shape), followed by a
+ * rebuild of every summary; lambda reset to (1, 1, 1, 1). */
+md_status md_solutions_copy(md_solutions *dst, const md_solutions *src, void *stream);
+
+/* Exports the routes in the md_solutions_load layout (slot order).  MD_ERR_CAPACITY when
+ * node_cap or route_cap is too small. */
+md_status md_solutions_read(md_solutions *sols, int32_t *route_nodes, int64_t *route_offsets,
+                            int32_t *routes_per_sol, int64_t node_cap, int64_t route_cap,
+                            void *stream);
+
+/* Per solution: comps [n_sol * 8] = D, TW, LoadEx, DurEx, closures, vehicle excess, V4, routes
+ * (int64, Eq. A1 before the weights) and F [n_sol] under the solution's current lambda. */
+md_status md_solution_cost(md_solutions *sols, int64_t *comps, double *F, void *stream);
+
+/* Current lambda [n_sol * 4] (FP32). */
+md_status md_solutions_lambda(md_solutions *sols, float *lambda, void *stream);
+
+/* Per-customer summaries, for tests: pre/suf [n_sol * n_customers * 8] int32 with
+ * pre = {dist, load, dur, tw, E, L, route slot, position} of [ds..c] and
+ * suf = {dist, load, dur, tw, E, L, pred node, succ node} of [c..de] (open routes: [c..c_L]). */
+md_status md_solutions_read_summaries(md_solutions *sols, int32_t *pre, int32_t *suf, void *stream);
+
+/* Scratch for one evaluation: per-block leader candidates, the follower table (one entry per
+ * route pair), the selection and an optional dump list of dump_capacity moves. */
+md_status md_moves_create(const md_solutions *sols, int64_t dump_capacity, md_moves **out);
+md_status md_moves_destroy(md_moves *moves);
+
+/* Evaluates the whole neighbourhood of operator ops[s] for every solution s (ops[s] < 0 skips
+ * it): every valid move (u, v, variant) of Section 3.2.2 over u's neighbour list (or all
+ * customers when theta = 0), plus every route x depot of the depot operators, each scored from
+ * the segment summaries (Eq. A1) with dF as in md_move.  Records per solution the leader (the
+ * smallest dF < 0, ties by id) and, with MD_EVAL_FOLLOWERS, the best follower (dD < 0 and no
+ * change in any penalty term, Section 3.2.5) of every route pair.  lambda: host [n_sol * 4] to
+ * set before evaluating, or NULL to keep the current values.
+ * MD_ERR_CAPACITY when MD_EVAL_DUMP overflows the dump list (the list then holds a prefix). */
+md_status md_eval_neighborhood(md_solutions *sols, const int32_t *ops, const float *lambda,
+                               uint32_t flags, md_moves *moves, void *stream);
+
+/* Results of the last evaluation: leader id (0 when none) and dF per solution, and the number
+ * of scored move tuples per solution. */
+md_status md_moves_read_leaders(md_moves *moves, uint64_t *ids, double *dF, int64_t *n_scored,
+                                void *stream);
+
+/* The dump list of the last MD_EVAL_DUMP evaluation, in no particular order. */
+md_status md_moves_read_dump(md_moves *moves, md_move *host_out, int64_t cap, int64_t *n_out,
+                             void *stream);
+
+/* Leader-follower selection (Section 3.2.5): per solution the leader, then the followers in
+ * ascending (dD, id) order, each taken when none of its routes is already claimed.  Computed
+ * on the device by rounds of per-route minimum claims, which yields the same set as that
+ * sequential greedy.  multi_move = 0 keeps the leader only. */
+md_status md_select_multimove(md_solutions *sols, md_moves *moves, int32_t multi_move,
+                              void *stream);
+
+/* The selection: ids [n_sol * cap] (leader first), counts [n_sol]. */
+md_status md_selection_read(md_moves *moves, uint64_t *ids, int32_t *counts, int32_t cap,
+                            void *stream);
+
+/* Applies the selected moves (route-disjoint) and rebuilds the summaries of the touched routes
+ * only; an emptied route is deleted and Depot-Insert takes a free slot.  With
+ * MD_APPLY_UPDATE_LAMBDA, lambda_i is divided by kappa = 0.5 where term i is violated after
+ * the step and multiplied by it otherwise, kept in [2^-16, 2^16] (Section 3.2.1); lambda_out
+ * (host [n_sol * 4], may be NULL) receives the values.  MD_ERR_CAPACITY when a new route does
+ * not fit k_max or no free slot is left (that move is skipped). */
+md_status md_apply_and_rebuild(md_solutions *sols, md_moves *moves, uint32_t flags,
+                               float *lambda_out, void *stream);
+
+/* MDFIS descent (Alg. 2) of every solution: per pass, the operators in the order of op_perm;
+ * each step evaluates, selects and applies on the device; a solution stops after a pass that
+ * applied nothing or after max_pass passes.  The host only polls the done flags. */
+md_status md_descend(md_solutions *sols, const md_config *cfg, md_stats *out, void *stream);
+
+/* Per-solution counters of the last md_descend: [n_sol * 5] = moves scored, steps, accepted
+ * steps, applied moves, passes. */
+md_status md_solutions_stats(md_solutions *sols, int64_t *per_sol, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MDLS_H */

@@ -1,0 +1,354 @@
+// api.cu -- C ABI entry points for evaluation, selection, apply and the MDFIS descent (Alg. 2).
+#include <stdlib.h>
+#include <string.h>
+
+#include <vector>
+
+#include "mdls_internal.cuh"
+
+namespace {
+
+// Leader per solution from the per-block candidates (one block per solution).
+__global__ void k_leaders(DevSols D, DevMoves M, unsigned long long *ids, double *fs) {
+    __shared__ double lf[32];
+    __shared__ uint32_t lid[32];
+    __shared__ int lv[32];
+    const int s = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    double f = 0.0;
+    uint32_t id = 0xffffffffu;
+    int valid = 0;
+    for (int k = tid; k < M.nblk; k += blockDim.x) {
+        LeadRec r = M.lpart[(size_t)s * M.nblk + k];
+        if (r.valid && (!valid || r.f < f || (r.f == f && r.id < id))) { f = r.f; id = r.id; valid = 1; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const double of = __shfl_xor_sync(0xffffffffu, f, o);
+        const uint32_t oi = __shfl_xor_sync(0xffffffffu, id, o);
+        const int ov = __shfl_xor_sync(0xffffffffu, valid, o);
+        if (ov && (!valid || of < f || (of == f && oi < id))) { f = of; id = oi; valid = 1; }
+    }
+    if (lane == 0) { lf[warp] = f; lid[warp] = id; lv[warp] = valid; }
+    __syncthreads();
+    if (tid == 0) {
+        f = 0.0; id = 0xffffffffu; valid = 0;
+        for (int k = 0; k < (int)(blockDim.x + 31) / 32; k++)
+            if (lv[k] && (!valid || lf[k] < f || (lf[k] == f && lid[k] < id))) { f = lf[k]; id = lid[k]; valid = 1; }
+        ids[s] = valid ? (((unsigned long long)D.ops[s] << 32) | id) : 0ull;
+        fs[s] = valid ? f : 0.0;
+    }
+}
+
+// Descent start: counters cleared, first operator of pass 0 for every solution.
+__global__ void k_descend_init(DevSols D, int n_ops, int max_pass, int multi, int lup) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= D.S) return;
+    int *st = D.state + (size_t)s * 8;
+    st[0] = 0; st[1] = 0; st[2] = 0; st[3] = 0;
+    st[4] = n_ops; st[5] = max_pass; st[6] = multi; st[7] = lup;
+    for (int k = 0; k < 8; k++) D.stats[(size_t)s * 8 + k] = 0;
+    D.ops[s] = (int)D.perm[(size_t)s * max_pass * n_ops];
+}
+
+__global__ void k_set_ops(DevSols D, const int32_t *ops) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < D.S) D.ops[s] = ops[s];
+}
+
+}  // namespace
+
+static size_t moves_ncap(const md_solutions *s) {
+    const long long R = s->R, nc = s->inst->d.nc, th = s->inst->d.theta;
+    long long full = R * (R + 1) / 2;
+    if (th > 0) {
+        long long g = nc * th > R ? nc * th : R;
+        return (size_t)(g < full ? g : full);
+    }
+    return (size_t)full;
+}
+
+static void free_moves(md_moves *m) {
+    if (!m) return;
+    DevMoves &d = m->d;
+    cudaFree(d.lpart); cudaFree(d.nscored); cudaFree(d.foltab); cudaFree(d.cand_key);
+    cudaFree(d.cand_rt); cudaFree(d.sel); cudaFree(d.nsel); cudaFree(d.dump); cudaFree(d.dump_n);
+    free(m);
+}
+
+extern "C" md_status md_moves_create(const md_solutions *sols, int64_t dump_capacity, md_moves **out) {
+    if (!sols || !out || dump_capacity < 0) { md_set_error("md_moves_create: invalid argument"); return MD_ERR_ARG; }
+    *out = nullptr;
+    if (sols->R > 8192) { md_set_error("md_moves_create: the selector supports at most 8192 route slots"); return MD_ERR_ARG; }
+    md_moves *m = (md_moves *)calloc(1, sizeof(md_moves));
+    m->sols = sols;
+    DevMoves &d = m->d;
+    const size_t S = sols->n_sol, R = sols->R;
+    d.nblk = md_eval_blocks(sols);
+    d.ncap = (int)moves_ncap(sols);
+    d.dump_cap = dump_capacity;
+    cudaError_t e = cudaSuccess;
+#define MDM(call) do { if (e == cudaSuccess) e = (call); } while (0)
+    MDM(cudaMalloc(&d.lpart, sizeof(LeadRec) * S * d.nblk));
+    MDM(cudaMalloc(&d.nscored, sizeof(unsigned long long) * S));
+    MDM(cudaMalloc(&d.foltab, sizeof(unsigned long long) * S * R * R));
+    MDM(cudaMalloc(&d.cand_key, sizeof(unsigned long long) * S * d.ncap));
+    MDM(cudaMalloc(&d.cand_rt, sizeof(uint32_t) * S * d.ncap));
+    MDM(cudaMalloc(&d.sel, sizeof(uint32_t) * S * R));
+    MDM(cudaMalloc(&d.nsel, sizeof(int32_t) * S));
+    MDM(cudaMalloc(&d.dump_n, sizeof(unsigned long long)));
+    if (dump_capacity > 0) MDM(cudaMalloc(&d.dump, sizeof(md_move) * dump_capacity));
+    MDM(cudaMemset(d.nscored, 0, sizeof(unsigned long long) * S));
+    MDM(cudaMemset(d.foltab, 0xff, sizeof(unsigned long long) * S * R * R));
+    MDM(cudaMemset(d.nsel, 0, sizeof(int32_t) * S));
+    MDM(cudaMemset(d.lpart, 0, sizeof(LeadRec) * S * d.nblk));
+    MDM(cudaMemset(d.dump_n, 0, sizeof(unsigned long long)));
+    MDM(cudaDeviceSynchronize());
+#undef MDM
+    if (e != cudaSuccess) {
+        md_status st = md_cuda_check(e, "md_moves_create");
+        free_moves(m);
+        return st;
+    }
+    *out = m;
+    return MD_OK;
+}
+
+extern "C" md_status md_moves_destroy(md_moves *m) {
+    free_moves(m);
+    return MD_OK;
+}
+
+static md_status upload_lambda(md_solutions *s, const float *lambda, cudaStream_t st) {
+    if (lambda) MD_CUDA(cudaMemcpyAsync(s->d.lam, lambda, sizeof(float) * 4 * s->n_sol, cudaMemcpyHostToDevice, st));
+    return md_launch_totals(s, st);  // totals and the FP64 weights of the current lambda
+}
+
+extern "C" md_status md_eval_neighborhood(md_solutions *s, const int32_t *ops, const float *lambda,
+                                          uint32_t flags, md_moves *m, void *stream) {
+    if (!s || !ops || !m || m->sols != s) { md_set_error("md_eval_neighborhood: invalid argument"); return MD_ERR_ARG; }
+    for (int i = 0; i < s->n_sol; i++)
+        if (ops[i] >= MD_N_OPS) { md_set_error("md_eval_neighborhood: unknown operator %d", ops[i]); return MD_ERR_ARG; }
+    if ((flags & MD_EVAL_DUMP) && m->d.dump_cap == 0) { md_set_error("md_eval_neighborhood: no dump capacity"); return MD_ERR_STATE; }
+    cudaStream_t st = (cudaStream_t)stream;
+    int32_t *dops = nullptr;
+    MD_CUDA(cudaMallocAsync(&dops, sizeof(int32_t) * s->n_sol, st));
+    MD_CUDA(cudaMemcpyAsync(dops, ops, sizeof(int32_t) * s->n_sol, cudaMemcpyHostToDevice, st));
+    k_set_ops<<<(s->n_sol + 127) / 128, 128, 0, st>>>(s->d, dops);
+    MD_CUDA(cudaGetLastError());
+    MD_CUDA(cudaFreeAsync(dops, st));
+    md_status r = upload_lambda(s, lambda, st);
+    if (r != MD_OK) return r;
+    MD_CUDA(cudaMemsetAsync(m->d.nscored, 0, sizeof(unsigned long long) * s->n_sol, st));
+    MD_CUDA(cudaMemsetAsync(m->d.dump_n, 0, sizeof(unsigned long long), st));
+    r = md_launch_eval(s, m, flags, st);
+    if (r != MD_OK) return r;
+    m->last_flags = (int)flags;
+    m->evaluated = 1;
+    m->selected = 0;
+    if (flags & MD_EVAL_DUMP) {
+        unsigned long long n = 0;
+        MD_CUDA(cudaMemcpyAsync(&n, m->d.dump_n, sizeof(n), cudaMemcpyDeviceToHost, st));
+        MD_CUDA(cudaStreamSynchronize(st));
+        if ((long long)n > m->d.dump_cap) {
+            md_set_error("md_eval_neighborhood: %llu moves exceed the dump capacity %lld", n, (long long)m->d.dump_cap);
+            return MD_ERR_CAPACITY;
+        }
+    }
+    return MD_OK;
+}
+
+extern "C" md_status md_moves_read_leaders(md_moves *m, uint64_t *ids, double *dF, int64_t *n_scored, void *stream) {
+    if (!m) { md_set_error("md_moves_read_leaders: null argument"); return MD_ERR_ARG; }
+    if (!m->evaluated) { md_set_error("md_moves_read_leaders: nothing evaluated"); return MD_ERR_STATE; }
+    cudaStream_t st = (cudaStream_t)stream;
+    const md_solutions *s = m->sols;
+    const int S = s->n_sol;
+    unsigned long long *did = nullptr;
+    double *df = nullptr;
+    MD_CUDA(cudaMallocAsync(&did, sizeof(unsigned long long) * S, st));
+    MD_CUDA(cudaMallocAsync(&df, sizeof(double) * S, st));
+    k_leaders<<<S, 256, 0, st>>>(s->d, m->d, did, df);
+    MD_CUDA(cudaGetLastError());
+    if (ids) MD_CUDA(cudaMemcpyAsync(ids, did, sizeof(uint64_t) * S, cudaMemcpyDeviceToHost, st));
+    if (dF) MD_CUDA(cudaMemcpyAsync(dF, df, sizeof(double) * S, cudaMemcpyDeviceToHost, st));
+    if (n_scored) MD_CUDA(cudaMemcpyAsync(n_scored, m->d.nscored, sizeof(int64_t) * S, cudaMemcpyDeviceToHost, st));
+    MD_CUDA(cudaFreeAsync(did, st));
+    MD_CUDA(cudaFreeAsync(df, st));
+    MD_CUDA(cudaStreamSynchronize(st));
+    return MD_OK;
+}
+
+extern "C" md_status md_moves_read_dump(md_moves *m, md_move *out, int64_t cap, int64_t *n_out, void *stream) {
+    if (!m || !n_out) { md_set_error("md_moves_read_dump: null argument"); return MD_ERR_ARG; }
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned long long n = 0;
+    MD_CUDA(cudaMemcpyAsync(&n, m->d.dump_n, sizeof(n), cudaMemcpyDeviceToHost, st));
+    MD_CUDA(cudaStreamSynchronize(st));
+    long long k = (long long)n < m->d.dump_cap ? (long long)n : m->d.dump_cap;
+    *n_out = (int64_t)n;
+    if (out && k > 0) {
+        long long c = k < cap ? k : cap;
+        MD_CUDA(cudaMemcpyAsync(out, m->d.dump, sizeof(md_move) * c, cudaMemcpyDeviceToHost, st));
+        MD_CUDA(cudaStreamSynchronize(st));
+    }
+    if ((long long)n > m->d.dump_cap || (long long)n > cap) {
+        md_set_error("md_moves_read_dump: %llu moves, buffer holds fewer", n);
+        return MD_ERR_CAPACITY;
+    }
+    return MD_OK;
+}
+
+extern "C" md_status md_select_multimove(md_solutions *s, md_moves *m, int32_t multi_move, void *stream) {
+    if (!s || !m || m->sols != s) { md_set_error("md_select_multimove: invalid argument"); return MD_ERR_ARG; }
+    if (!m->evaluated) { md_set_error("md_select_multimove: evaluate first"); return MD_ERR_STATE; }
+    if (multi_move && !(m->last_flags & MD_EVAL_FOLLOWERS)) {
+        md_set_error("md_select_multimove: followers need MD_EVAL_FOLLOWERS at evaluation");
+        return MD_ERR_STATE;
+    }
+    md_status r = md_launch_select(s, m, multi_move ? 1 : 0, (cudaStream_t)stream);
+    if (r != MD_OK) return r;
+    m->selected = 1;
+    return MD_OK;
+}
+
+extern "C" md_status md_selection_read(md_moves *m, uint64_t *ids, int32_t *counts, int32_t cap, void *stream) {
+    if (!m || !ids || !counts) { md_set_error("md_selection_read: null argument"); return MD_ERR_ARG; }
+    if (!m->selected) { md_set_error("md_selection_read: select first"); return MD_ERR_STATE; }
+    cudaStream_t st = (cudaStream_t)stream;
+    const md_solutions *s = m->sols;
+    const int S = s->n_sol, R = s->R;
+    std::vector<uint32_t> sel((size_t)S * R);
+    std::vector<int32_t> ops(S);
+    MD_CUDA(cudaMemcpyAsync(sel.data(), m->d.sel, sizeof(uint32_t) * S * R, cudaMemcpyDeviceToHost, st));
+    MD_CUDA(cudaMemcpyAsync(counts, m->d.nsel, sizeof(int32_t) * S, cudaMemcpyDeviceToHost, st));
+    MD_CUDA(cudaMemcpyAsync(ops.data(), s->d.ops, sizeof(int32_t) * S, cudaMemcpyDeviceToHost, st));
+    MD_CUDA(cudaStreamSynchronize(st));
+    md_status r = MD_OK;
+    for (int i = 0; i < S; i++) {
+        if (counts[i] > cap) { r = MD_ERR_CAPACITY; md_set_error("md_selection_read: cap %d < %d selected", cap, counts[i]); }
+        for (int k = 0; k < counts[i] && k < cap; k++)
+            ids[(size_t)i * cap + k] = ((uint64_t)(uint32_t)ops[i] << 32) | sel[(size_t)i * R + k];
+    }
+    return r;
+}
+
+static md_status check_err(md_solutions *s, cudaStream_t st) {
+    int32_t err = 0;
+    MD_CUDA(cudaMemcpyAsync(&err, s->d.err, sizeof(err), cudaMemcpyDeviceToHost, st));
+    MD_CUDA(cudaStreamSynchronize(st));
+    if (err) {
+        MD_CUDA(cudaMemsetAsync(s->d.err, 0, sizeof(int32_t), st));
+        md_set_error("device reported error %d (capacity: a route exceeded k_max or no free slot)", err);
+        return (md_status)err;
+    }
+    return MD_OK;
+}
+
+extern "C" md_status md_apply_and_rebuild(md_solutions *s, md_moves *m, uint32_t flags, float *lambda_out, void *stream) {
+    if (!s || !m || m->sols != s) { md_set_error("md_apply_and_rebuild: invalid argument"); return MD_ERR_ARG; }
+    if (!m->selected) { md_set_error("md_apply_and_rebuild: select first"); return MD_ERR_STATE; }
+    cudaStream_t st = (cudaStream_t)stream;
+    md_status r = md_launch_apply(s, m, (flags & MD_APPLY_UPDATE_LAMBDA) ? 1 : 0, st);
+    if (r != MD_OK) return r;
+    m->selected = 0;
+    m->evaluated = 0;
+    if (lambda_out) MD_CUDA(cudaMemcpyAsync(lambda_out, s->d.lam, sizeof(float) * 4 * s->n_sol, cudaMemcpyDeviceToHost, st));
+    return check_err(s, st);
+}
+
+extern "C" md_status md_descend(md_solutions *s, const md_config *cfg, md_stats *out, void *stream) {
+    if (!s || !cfg || !cfg->op_perm) { md_set_error("md_descend: null argument"); return MD_ERR_ARG; }
+    if (cfg->n_ops < 1 || cfg->n_ops > MD_MAX_OPS || cfg->max_pass < 1) {
+        md_set_error("md_descend: need 1 <= n_ops <= %d and max_pass >= 1", MD_MAX_OPS);
+        return MD_ERR_ARG;
+    }
+    const size_t nperm = (size_t)s->n_sol * cfg->max_pass * cfg->n_ops;
+    for (size_t i = 0; i < nperm; i++)
+        if (cfg->op_perm[i] >= MD_N_OPS) { md_set_error("md_descend: unknown operator in op_perm"); return MD_ERR_ARG; }
+    cudaStream_t st = (cudaStream_t)stream;
+    // the evaluation scratch of the descent is created once and kept with the solutions
+    if (!s->scratch) {
+        md_status r = md_moves_create(s, 0, &s->scratch);
+        if (r != MD_OK) return r;
+    }
+    md_moves *m = s->scratch;
+    if (s->perm_bytes < nperm) {
+        cudaFree(s->perm_dev);
+        s->perm_dev = nullptr;
+        s->perm_bytes = 0;
+        MD_CUDA(cudaMalloc(&s->perm_dev, nperm));
+        s->perm_bytes = nperm;
+    }
+    MD_CUDA(cudaMemcpyAsync(s->perm_dev, cfg->op_perm, nperm, cudaMemcpyHostToDevice, st));
+    s->d.perm = s->perm_dev;
+    long long launches = 0;
+    if (cfg->lambda0) MD_CUDA(cudaMemcpyAsync(s->d.lam, cfg->lambda0, sizeof(float) * 4 * s->n_sol, cudaMemcpyHostToDevice, st));
+    md_status r = md_launch_totals(s, st);
+    if (r != MD_OK) return r;
+    launches++;
+    MD_CUDA(cudaMemsetAsync(m->d.foltab, 0xff, sizeof(unsigned long long) * s->n_sol * s->R * s->R, st));
+    MD_CUDA(cudaMemsetAsync(m->d.nscored, 0, sizeof(unsigned long long) * s->n_sol, st));
+    k_descend_init<<<(s->n_sol + 127) / 128, 128, 0, st>>>(s->d, cfg->n_ops, cfg->max_pass, cfg->multi_move ? 1 : 0,
+                                                         cfg->lambda_update ? 1 : 0);
+    MD_CUDA(cudaGetLastError());
+    launches++;
+    const uint32_t eflags = cfg->multi_move ? MD_EVAL_FOLLOWERS : 0u;
+    const int poll = cfg->poll_every > 0 ? cfg->poll_every : 1;
+    const int steps_per_poll = cfg->n_ops * poll;
+    std::vector<int32_t> state((size_t)s->n_sol * 8);
+    cudaGraphExec_t exec = nullptr;
+    cudaGraph_t graph = nullptr;
+    const bool use_graph = cfg->use_graph && st != nullptr;
+    if (use_graph) {
+        MD_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        md_status cr = MD_OK;
+        for (int k = 0; k < steps_per_poll && cr == MD_OK; k++) {
+            cr = md_launch_eval(s, m, eflags, st);
+            if (cr == MD_OK) cr = md_launch_step(s, m, st);
+        }
+        cudaError_t ce = cudaStreamEndCapture(st, &graph);
+        if (cr != MD_OK) { if (graph) cudaGraphDestroy(graph); return cr; }
+        MD_CUDA(ce);
+        MD_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+    }
+    int passes_done = 0;
+    bool all_done = false;
+    while (!all_done && passes_done <= cfg->max_pass) {
+        if (use_graph) {
+            MD_CUDA(cudaGraphLaunch(exec, st));
+        } else {
+            for (int k = 0; k < steps_per_poll; k++) {
+                r = md_launch_eval(s, m, eflags, st);
+                if (r != MD_OK) return r;
+                r = md_launch_step(s, m, st);
+                if (r != MD_OK) return r;
+            }
+        }
+        launches += 2LL * steps_per_poll;
+        passes_done += poll;
+        MD_CUDA(cudaMemcpyAsync(state.data(), s->d.state, sizeof(int32_t) * 8 * s->n_sol, cudaMemcpyDeviceToHost, st));
+        MD_CUDA(cudaStreamSynchronize(st));
+        all_done = true;
+        for (int i = 0; i < s->n_sol; i++) all_done &= state[(size_t)i * 8 + 3] != 0;
+    }
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    r = check_err(s, st);
+    if (r != MD_OK) return r;
+    if (!all_done) { md_set_error("md_descend: solutions still running after max_pass passes"); return MD_ERR_STATE; }
+    if (out) {
+        std::vector<long long> h((size_t)s->n_sol * 8);
+        MD_CUDA(cudaMemcpyAsync(h.data(), s->d.stats, sizeof(long long) * 8 * s->n_sol, cudaMemcpyDeviceToHost, st));
+        MD_CUDA(cudaStreamSynchronize(st));
+        memset(out, 0, sizeof(*out));
+        for (int i = 0; i < s->n_sol; i++) {
+            const long long *x = &h[(size_t)i * 8];
+            out->moves_scored += x[0];
+            out->steps += x[1];
+            out->accepted_steps += x[2];
+            out->applied_moves += x[3];
+            if (x[4] > out->passes_max) out->passes_max = x[4];
+        }
+        out->launches = launches;
+    }
+    return MD_OK;
+}

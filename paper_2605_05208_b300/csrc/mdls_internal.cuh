@@ -1,0 +1,225 @@
+// mdls_internal.cuh -- device data layout and segment arithmetic of the B300 library.
+//
+// Layout in HBM (one instance, S solutions, R route slots per solution, K customers per slot):
+//   dist    int32 [nn * nn]         c_ij = t_ij, fixed point, row-major (symmetric)
+//   node    int4  [nn]              {q, s, e, l}; without time windows e = 0, l = 2^30
+//   nbr     int32 [nc * theta]      granular neighbour lists (node ids), nnbr int32 [nc]
+//   rnodes  int32 [S * R * K]       customers of each route slot, positions 1..L at 0..L-1
+//   rhdr    int4  [S * R]           {L, ds, de, last customer}; L = 0 marks a free slot
+//   rterm   Seg8  [S * R]           summary of the whole route [ds..de] ([ds..c_L] if open)
+//   rcore   Seg8  [S * R]           summary of [c_1..c_L]
+//   cpre    Seg8  [S * nc]          summary of [ds..c] plus {route slot, position} of c
+//   csuf    Seg8  [S * nc]          summary of [c..de] ([c..c_L] if open) plus {pred, succ}
+//   dcount  int32 [S * nd]          non-empty routes departing from each depot
+//   tot     int64 [S * 8]           D, TW, LoadEx, DurEx, closures, vehicle excess, V4, routes
+//   lam     float [S * 4], w double [S * 4]  penalty coefficients and FP64 weights
+// Summaries are 32-byte records so a gather of one summary is one 32-byte sector.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/mdls.h"
+
+#define MD_MAX_NODES 16384
+#define MD_NO_LATE (1 << 30)
+#define MD_NONE (-1)
+#define MD_MAX_OPS 8
+#define MD_EMPTY_KEY 0xFFFFFFFFFFFFFFFFull
+
+struct __align__(16) Seg8 {
+    int dist, load, dur, tw, E, L, a, b;
+};
+
+// Summary of a sequence (Section 3.2.2 sequence concatenation; time warp of Appendix A1).
+struct Seg {
+    int dist, load, dur, tw, E, L;
+};
+
+struct DevInst {
+    int nd, nc, nn;
+    int Q, NV, D;
+    uint32_t variant;
+    int theta;
+    int64_t Theta;
+    double Gamma;
+    const int32_t *dist;
+    const int4 *node;
+    const int32_t *nbr;
+    const int32_t *nnbr;
+};
+
+struct DevSols {
+    int S, R, K;
+    int32_t *rnodes;
+    int4 *rhdr;
+    Seg8 *rterm;
+    Seg8 *rcore;
+    Seg8 *cpre;
+    Seg8 *csuf;
+    int32_t *dcount;
+    long long *tot;
+    float *lam;
+    double *w;
+    int32_t *ops;      // [S] operator of the current step (-1 = none)
+    int32_t *state;    // [S * 8] pass, slot, improved, done, n_ops, max_pass, multi, lambda_update
+    long long *stats;  // [S * 8] moves scored, steps, accepted, applied, passes
+    int32_t *err;      // [1] first error code raised on the device
+    const uint8_t *perm; // [S * max_pass * n_ops] operator order (descent only)
+};
+
+// Leader candidate of one block: smallest (dF, id) with dF < 0.
+struct __align__(16) LeadRec {
+    double f;
+    uint32_t id;
+    uint32_t valid;
+};
+
+struct DevMoves {
+    int nblk;              // leader partials per solution
+    LeadRec *lpart;        // [S * nblk]
+    unsigned long long *nscored;   // [S]
+    unsigned long long *foltab;    // [S * R * R] best follower key per route pair (i <= j used)
+    unsigned long long *cand_key;  // [S * ncap] follower candidates for the selection
+    uint32_t *cand_rt;             // [S * ncap] packed route pair (i | j << 16)
+    int ncap;
+    uint32_t *sel;         // [S * R] selected move ids (32-bit part), leader first
+    int32_t *nsel;         // [S]
+    md_move *dump;         // [dump_cap]
+    unsigned long long *dump_n;
+    long long dump_cap;
+};
+
+// ------------------------------------------------------------------------------------------
+// Segment arithmetic
+// ------------------------------------------------------------------------------------------
+
+__device__ __forceinline__ Seg seg_of(const Seg8 &g) {
+    Seg s;
+    s.dist = g.dist; s.load = g.load; s.dur = g.dur; s.tw = g.tw; s.E = g.E; s.L = g.L;
+    return s;
+}
+
+__device__ __forceinline__ Seg node_seg(const int4 nd) {
+    Seg s;
+    s.dist = 0; s.load = nd.x; s.dur = nd.y; s.tw = 0; s.E = nd.z; s.L = nd.w;
+    return s;
+}
+
+// a followed by b, joined by an arc of travel time t (time-warp concatenation, Vidal et al.
+// 2013, the method the paper cites for V1 and V3).  Without time windows no node ever waits or
+// warps, so TW = false keeps only distance, load and duration.
+template <bool TW>
+__device__ __forceinline__ Seg seg_cat(const Seg &a, const Seg &b, int t) {
+    Seg r;
+    r.dist = a.dist + b.dist + t;
+    r.load = a.load + b.load;
+    if (TW) {
+        int delta = a.dur - a.tw + t;
+        int wait = max(b.E - delta - a.L, 0);
+        int warp = max(a.E + delta - b.L, 0);
+        r.dur = a.dur + b.dur + t + wait;
+        r.tw = a.tw + b.tw + warp;
+        r.E = max(b.E - delta, a.E) - wait;
+        r.L = min(b.L - delta, a.L) + warp;
+    } else {
+        r.dur = a.dur + b.dur + t;
+        r.tw = 0;
+        r.E = 0;
+        r.L = MD_NO_LATE;
+    }
+    return r;
+}
+
+__device__ __forceinline__ int load_ex(int load, int Q) { return max(load - Q, 0); }
+__device__ __forceinline__ int dur_ex(int dur, int D) { return D > 0 ? max(dur - D, 0) : 0; }
+
+__device__ __forceinline__ Seg8 ldg_seg8(const Seg8 *p) {
+    const int4 *q = reinterpret_cast<const int4 *>(p);
+    int4 x = __ldg(q), y = __ldg(q + 1);
+    Seg8 g;
+    g.dist = x.x; g.load = x.y; g.dur = x.z; g.tw = x.w; g.E = y.x; g.L = y.y; g.a = y.z; g.b = y.w;
+    return g;
+}
+
+__device__ __forceinline__ Seg8 ld_seg8(const Seg8 *p) {
+    const int4 *q = reinterpret_cast<const int4 *>(p);
+    int4 x = q[0], y = q[1];
+    Seg8 g;
+    g.dist = x.x; g.load = x.y; g.dur = x.z; g.tw = x.w; g.E = y.x; g.L = y.y; g.a = y.z; g.b = y.w;
+    return g;
+}
+
+__device__ __forceinline__ void st_seg8(Seg8 *p, const Seg &s, int a, int b) {
+    int4 *q = reinterpret_cast<int4 *>(p);
+    q[0] = make_int4(s.dist, s.load, s.dur, s.tw);
+    q[1] = make_int4(s.E, s.L, a, b);
+}
+
+// FP64 combination of the integer deltas (Eq. A1 weights), left to right, no contraction.
+__device__ __forceinline__ double combine_df(const double *w, int dD, int dTW, int dL, int dU, int dV) {
+    double f = (double)dD;
+    if ((dTW | dL | dU | dV) == 0) return f;  // every product is +0: the sum is f exactly
+    f = __dadd_rn(f, __dmul_rn(w[0], (double)dTW));
+    f = __dadd_rn(f, __dmul_rn(w[1], (double)dL));
+    f = __dadd_rn(f, __dmul_rn(w[2], (double)dU));
+    f = __dadd_rn(f, __dmul_rn(w[3], (double)dV));
+    return f;
+}
+
+__device__ __forceinline__ uint32_t make_id32(int u, int v, int var) {
+    return ((uint32_t)u << 18) | ((uint32_t)v << 4) | (uint32_t)var;
+}
+
+// Vehicle-excess change when depot d gains (+1) or loses (-1) one route.
+__device__ __forceinline__ int veh_delta(int cnt, int NV, int change) {
+    return max(cnt + change - NV, 0) - max(cnt - NV, 0);
+}
+
+// ------------------------------------------------------------------------------------------
+// Host-side helpers shared by the translation units
+// ------------------------------------------------------------------------------------------
+
+struct md_instance {
+    DevInst d;
+    int32_t *dist;
+    int4 *node;
+    int32_t *nbr;
+    int32_t *nnbr;
+    int max_c, max_s, max_l;
+};
+
+struct md_solutions {
+    const md_instance *inst;
+    DevSols d;
+    int n_sol, R, K;
+    uint8_t *perm_dev;   // operator order of the last md_descend call
+    size_t perm_bytes;
+    md_moves *scratch;   // evaluation scratch of md_descend, created on first use
+};
+
+struct md_moves {
+    const md_solutions *sols;
+    DevMoves d;
+    int last_flags;
+    int evaluated;
+    int selected;
+};
+
+void md_set_error(const char *fmt, ...);
+md_status md_cuda_check(cudaError_t e, const char *what);
+
+#define MD_CUDA(call)                                                     \
+    do {                                                                  \
+        cudaError_t _e = (call);                                          \
+        if (_e != cudaSuccess) return md_cuda_check(_e, #call);           \
+    } while (0)
+
+// Launchers implemented in the .cu files.
+md_status md_launch_rebuild_all(md_solutions *s, cudaStream_t st);
+md_status md_launch_totals(md_solutions *s, cudaStream_t st);
+md_status md_launch_eval(md_solutions *s, md_moves *m, uint32_t flags, cudaStream_t st);
+md_status md_launch_select(md_solutions *s, md_moves *m, int multi, cudaStream_t st);
+md_status md_launch_apply(md_solutions *s, md_moves *m, int update_lambda, cudaStream_t st);
+md_status md_launch_step(md_solutions *s, md_moves *m, cudaStream_t st);
+int md_eval_blocks(const md_solutions *s);

@@ -1,0 +1,123 @@
+// route_build.cuh -- per-route summaries by warp scans of the sequence concatenation.
+//
+// For route [ds, c_1..c_L, de] one warp writes, for every customer c_k,
+//   cpre[c_k] = [ds, c_1..c_k]                 and {route slot, k}
+//   csuf[c_k] = [c_k..c_L, de] ([c_k..c_L] open) and {pred node, succ node (MD_NONE: none)}
+// plus rterm = the whole route and rcore = [c_1..c_L].  The concatenation is associative and
+// exact in integers, so the scan tree gives the same summaries as a left-to-right fold.
+#pragma once
+
+#include "mdls_internal.cuh"
+
+struct SegN {  // summary with its end nodes, the scan element
+    Seg s;
+    int first, last;
+};
+
+__device__ __forceinline__ SegN shfl_up_segn(const SegN &x, int off) {
+    SegN y;
+    y.s.dist = __shfl_up_sync(0xffffffffu, x.s.dist, off);
+    y.s.load = __shfl_up_sync(0xffffffffu, x.s.load, off);
+    y.s.dur = __shfl_up_sync(0xffffffffu, x.s.dur, off);
+    y.s.tw = __shfl_up_sync(0xffffffffu, x.s.tw, off);
+    y.s.E = __shfl_up_sync(0xffffffffu, x.s.E, off);
+    y.s.L = __shfl_up_sync(0xffffffffu, x.s.L, off);
+    y.first = __shfl_up_sync(0xffffffffu, x.first, off);
+    y.last = __shfl_up_sync(0xffffffffu, x.last, off);
+    return y;
+}
+
+__device__ __forceinline__ SegN shfl_segn(const SegN &x, int src) {
+    SegN y;
+    y.s.dist = __shfl_sync(0xffffffffu, x.s.dist, src);
+    y.s.load = __shfl_sync(0xffffffffu, x.s.load, src);
+    y.s.dur = __shfl_sync(0xffffffffu, x.s.dur, src);
+    y.s.tw = __shfl_sync(0xffffffffu, x.s.tw, src);
+    y.s.E = __shfl_sync(0xffffffffu, x.s.E, src);
+    y.s.L = __shfl_sync(0xffffffffu, x.s.L, src);
+    y.first = __shfl_sync(0xffffffffu, x.first, src);
+    y.last = __shfl_sync(0xffffffffu, x.last, src);
+    return y;
+}
+
+template <bool TW>
+__device__ __forceinline__ SegN segn_cat(const DevInst &I, const SegN &a, const SegN &b) {
+    SegN r;
+    r.s = seg_cat<TW>(a.s, b.s, I.dist[(size_t)a.last * I.nn + b.first]);
+    r.first = a.first;
+    r.last = b.last;
+    return r;
+}
+
+__device__ __forceinline__ SegN segn_node(const DevInst &I, int n) {
+    SegN r;
+    r.s = node_seg(I.node[n]);
+    r.first = n;
+    r.last = n;
+    return r;
+}
+
+// Rebuilds every summary of route slot r of solution s; called by all 32 lanes of one warp.
+template <bool TW>
+__device__ void rebuild_route(const DevInst &I, const DevSols &D, int s, int r) {
+    const int lane = threadIdx.x & 31;
+    const size_t sr = (size_t)s * D.R + r;
+    const int4 h = D.rhdr[sr];
+    const int L = h.x, ds = h.y, de = h.z;
+    if (L <= 0) return;
+    const bool open = (I.variant & MD_VARIANT_OPEN) != 0;
+    const int32_t *nodes = D.rnodes + sr * D.K;
+    Seg8 *cpre = D.cpre + (size_t)s * I.nc;
+    Seg8 *csuf = D.csuf + (size_t)s * I.nc;
+
+    // prefixes, chunks of 32 customers from the front
+    SegN carry = segn_node(I, ds);
+    SegN core;
+    bool have_core = false;
+    for (int base = 0; base < L; base += 32) {
+        const int k = base + lane;
+        const bool act = k < L;
+        const int n = act ? nodes[k] : nodes[L - 1];
+        SegN x = segn_node(I, n);
+        for (int off = 1; off < 32; off <<= 1) {
+            SegN y = shfl_up_segn(x, off);
+            if (lane >= off) x = segn_cat<TW>(I, y, x);
+        }
+        const int tail = min(31, L - 1 - base);
+        SegN chunk = shfl_segn(x, tail);
+        SegN p = segn_cat<TW>(I, carry, x);
+        if (act) st_seg8(&cpre[n - I.nd], p.s, r, k + 1);
+        carry = shfl_segn(p, tail);
+        core = have_core ? segn_cat<TW>(I, core, chunk) : chunk;
+        have_core = true;
+    }
+    // suffixes, chunks of 32 customers from the back; lane i holds position end-1-i
+    SegN rc;
+    bool have_rc = !open;
+    if (!open) rc = segn_node(I, de);
+    for (int end = L; end > 0; end -= 32) {
+        const int k = end - 1 - lane;
+        const bool act = k >= 0;
+        const int n = act ? nodes[k] : nodes[0];
+        SegN x = segn_node(I, n);
+        for (int off = 1; off < 32; off <<= 1) {
+            SegN y = shfl_up_segn(x, off);
+            if (lane >= off) x = segn_cat<TW>(I, x, y);
+        }
+        SegN sfx = have_rc ? segn_cat<TW>(I, x, rc) : x;
+        if (act) {
+            const int pred = k == 0 ? ds : nodes[k - 1];
+            const int succ = k == L - 1 ? (open ? MD_NONE : de) : nodes[k + 1];
+            st_seg8(&csuf[n - I.nd], sfx.s, pred, succ);
+        }
+        const int tail = min(31, end - 1);
+        rc = shfl_segn(sfx, tail);
+        have_rc = true;
+    }
+    if (lane == 0) {
+        SegN whole = open ? carry : segn_cat<TW>(I, carry, segn_node(I, de));
+        st_seg8(&D.rterm[sr], whole.s, ds, whole.last);
+        st_seg8(&D.rcore[sr], core.s, core.first, core.last);
+        D.rhdr[sr] = make_int4(L, ds, de, nodes[L - 1]);
+    }
+}

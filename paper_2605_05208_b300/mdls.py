@@ -1,0 +1,347 @@
+"""Python binding of the C ABI in include/mdls.h (libmdls.so, built in-tree for sm_103a).
+
+Argument marshalling only: every step of the hot path runs in the library's CUDA kernels.  The
+binding raises if the shared library is missing -- there is no CPU fallback.
+
+Streams are passed as integers (a cudaStream_t, e.g. torch.cuda.current_stream().cuda_stream)
+or None for the legacy default stream.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmdls.so")
+
+MD_OK, MD_ERR_ARG, MD_ERR_CUDA, MD_ERR_CAPACITY, MD_ERR_TIMEOUT, MD_ERR_STATE = range(6)
+VARIANT_TW, VARIANT_OPEN, VARIANT_SYMMETRIC = 1, 2, 4
+OP_RELOCATE, OP_SWAP, OP_TWO_OPT_STAR, OP_DEPOT_INSERT, OP_DEPOT_REPLACE = range(5)
+N_OPS = 5
+EVAL_DUMP, EVAL_FOLLOWERS = 1, 2
+APPLY_UPDATE_LAMBDA = 1
+
+EXPORTED = (
+    "md_last_error", "md_instance_create", "md_instance_destroy", "md_instance_params",
+    "md_instance_read_dist", "md_instance_read_neighbors", "md_solutions_create",
+    "md_solutions_destroy", "md_solutions_load", "md_solutions_copy", "md_solutions_read",
+    "md_solution_cost", "md_solutions_lambda", "md_solutions_read_summaries", "md_moves_create",
+    "md_moves_destroy", "md_eval_neighborhood", "md_moves_read_leaders", "md_moves_read_dump",
+    "md_select_multimove", "md_selection_read", "md_apply_and_rebuild", "md_descend",
+    "md_solutions_stats",
+)
+
+
+class MdError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"md status {status}: {msg}")
+        self.status = status
+
+
+class InstanceDesc(C.Structure):
+    _fields_ = [("n_depots", C.c_int32), ("n_customers", C.c_int32),
+                ("x", C.POINTER(C.c_double)), ("y", C.POINTER(C.c_double)),
+                ("demand", C.POINTER(C.c_int32)), ("service", C.POINTER(C.c_int32)),
+                ("tw_early", C.POINTER(C.c_int32)), ("tw_late", C.POINTER(C.c_int32)),
+                ("Q", C.c_int32), ("N_V", C.c_int32), ("D", C.c_int32), ("variant", C.c_uint32),
+                ("scale", C.c_double), ("theta", C.c_int32)]
+
+
+class MoveRec(C.Structure):
+    _fields_ = [("id", C.c_uint64), ("dD", C.c_int64), ("dTW", C.c_int64), ("dLoad", C.c_int64),
+                ("dDur", C.c_int64), ("dV4", C.c_int64), ("dF", C.c_double), ("sol", C.c_int32),
+                ("pad", C.c_int32)]
+
+
+MOVE_DTYPE = np.dtype([("id", np.uint64), ("dD", np.int64), ("dTW", np.int64), ("dLoad", np.int64),
+                       ("dDur", np.int64), ("dV4", np.int64), ("dF", np.float64), ("sol", np.int32),
+                       ("pad", np.int32)])
+
+
+class Config(C.Structure):
+    _fields_ = [("n_ops", C.c_int32), ("max_pass", C.c_int32), ("op_perm", C.POINTER(C.c_uint8)),
+                ("lambda0", C.POINTER(C.c_float)), ("multi_move", C.c_int32),
+                ("lambda_update", C.c_int32), ("use_graph", C.c_int32), ("poll_every", C.c_int32)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("moves_scored", C.c_int64), ("steps", C.c_int64), ("accepted_steps", C.c_int64),
+                ("applied_moves", C.c_int64), ("passes_max", C.c_int64), ("launches", C.c_int64)]
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """The loaded libmdls.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with python -m paper_2605_05208_b300.build")
+        L = C.CDLL(LIB_PATH)
+        L.md_last_error.restype = C.c_char_p
+        P = C.c_void_p
+        PP = C.POINTER(C.c_void_p)
+        sigs = {
+            "md_instance_create": [C.POINTER(InstanceDesc), PP],
+            "md_instance_destroy": [P],
+            "md_instance_params": [P, C.POINTER(C.c_int64), C.POINTER(C.c_double)],
+            "md_instance_read_dist": [P, P],
+            "md_instance_read_neighbors": [P, P, P],
+            "md_solutions_create": [P, C.c_int32, C.c_int32, C.c_int32, PP],
+            "md_solutions_destroy": [P],
+            "md_solutions_load": [P, P, P, P, P],
+            "md_solutions_copy": [P, P, P],
+            "md_solutions_read": [P, P, P, P, C.c_int64, C.c_int64, P],
+            "md_solution_cost": [P, P, P, P],
+            "md_solutions_lambda": [P, P, P],
+            "md_solutions_read_summaries": [P, P, P, P],
+            "md_moves_create": [P, C.c_int64, PP],
+            "md_moves_destroy": [P],
+            "md_eval_neighborhood": [P, P, P, C.c_uint32, P, P],
+            "md_moves_read_leaders": [P, P, P, P, P],
+            "md_moves_read_dump": [P, P, C.c_int64, C.POINTER(C.c_int64), P],
+            "md_select_multimove": [P, P, C.c_int32, P],
+            "md_selection_read": [P, P, P, C.c_int32, P],
+            "md_apply_and_rebuild": [P, P, C.c_uint32, P, P],
+            "md_descend": [P, C.POINTER(Config), C.POINTER(Stats), P],
+            "md_solutions_stats": [P, P, P],
+        }
+        for name, args in sigs.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status != MD_OK:
+        raise MdError(status, lib().md_last_error().decode())
+
+
+def _ptr(a: np.ndarray | None):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _stream(stream):
+    return None if stream is None else C.c_void_p(int(stream))
+
+
+class Instance:
+    """Device instance (md_instance_create) from a workloads.InstanceSpec."""
+
+    def __init__(self, spec):
+        self.spec = spec
+        self._keep = [np.ascontiguousarray(spec.x, np.float64), np.ascontiguousarray(spec.y, np.float64),
+                      np.ascontiguousarray(spec.demand, np.int32), np.ascontiguousarray(spec.service, np.int32),
+                      np.ascontiguousarray(spec.tw_early, np.int32), np.ascontiguousarray(spec.tw_late, np.int32)]
+        x, y, q, s, e, l = self._keep
+        tw = bool(spec.variant & VARIANT_TW)
+        d = InstanceDesc(spec.n_depots, spec.n_customers,
+                         x.ctypes.data_as(C.POINTER(C.c_double)), y.ctypes.data_as(C.POINTER(C.c_double)),
+                         q.ctypes.data_as(C.POINTER(C.c_int32)), s.ctypes.data_as(C.POINTER(C.c_int32)),
+                         e.ctypes.data_as(C.POINTER(C.c_int32)) if tw else None,
+                         l.ctypes.data_as(C.POINTER(C.c_int32)) if tw else None,
+                         spec.Q, spec.N_V, spec.D, spec.variant, float(spec.scale), spec.theta)
+        h = C.c_void_p()
+        _check(lib().md_instance_create(C.byref(d), C.byref(h)))
+        self.h = h
+        self.nd, self.nc = spec.n_depots, spec.n_customers
+        self.nn = self.nd + self.nc
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().md_instance_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self):
+        t = C.c_int64()
+        g = C.c_double()
+        _check(lib().md_instance_params(self.h, C.byref(t), C.byref(g)))
+        return int(t.value), float(g.value)
+
+    def dist(self) -> np.ndarray:
+        out = np.zeros(self.nn * self.nn, dtype=np.int32)
+        _check(lib().md_instance_read_dist(self.h, _ptr(out)))
+        return out.reshape(self.nn, self.nn)
+
+    def neighbors(self):
+        th = self.spec.theta
+        nb = np.zeros(self.nc * th, dtype=np.int32)
+        cnt = np.zeros(self.nc, dtype=np.int32)
+        _check(lib().md_instance_read_neighbors(self.h, _ptr(nb), _ptr(cnt)))
+        return nb.reshape(self.nc, th), cnt
+
+
+def flatten(sols):
+    nodes, offs, per = [], [0], []
+    for sol in sols:
+        per.append(len(sol))
+        for r in sol:
+            nodes.extend(r)
+            offs.append(len(nodes))
+    return (np.asarray(nodes, dtype=np.int32), np.asarray(offs, dtype=np.int64),
+            np.asarray(per, dtype=np.int32))
+
+
+@dataclass
+class DescendStats:
+    moves_scored: int
+    steps: int
+    accepted_steps: int
+    applied_moves: int
+    passes_max: int
+    launches: int
+
+
+class Solutions:
+    """A batch of solutions on the device (md_solutions_create / load)."""
+
+    def __init__(self, inst: Instance, n_sol: int, r_slots: int, k_max: int):
+        self.inst = inst
+        self.n_sol, self.R, self.K = n_sol, r_slots, k_max
+        h = C.c_void_p()
+        _check(lib().md_solutions_create(inst.h, n_sol, r_slots, k_max, C.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().md_solutions_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def load(self, sols, stream=None):
+        nodes, offs, per = flatten(sols)
+        self.load_flat(nodes, offs, per, stream)
+
+    def load_flat(self, nodes, offs, per, stream=None):
+        _check(lib().md_solutions_load(self.h, _ptr(nodes), _ptr(offs), _ptr(per), _stream(stream)))
+
+    def copy_from(self, other: "Solutions", stream=None):
+        _check(lib().md_solutions_copy(self.h, other.h, _stream(stream)))
+
+    def read(self, stream=None):
+        cap_r = self.n_sol * self.R
+        cap_n = self.n_sol * (self.inst.nc + 2 * self.R)
+        nodes = np.zeros(cap_n, dtype=np.int32)
+        offs = np.zeros(cap_r + 1, dtype=np.int64)
+        per = np.zeros(self.n_sol, dtype=np.int32)
+        _check(lib().md_solutions_read(self.h, _ptr(nodes), _ptr(offs), _ptr(per), cap_n, cap_r, _stream(stream)))
+        out, k = [], 0
+        for n in per:
+            sol = []
+            for _ in range(int(n)):
+                sol.append([int(v) for v in nodes[offs[k]:offs[k + 1]]])
+                k += 1
+            out.append(sol)
+        return out
+
+    def cost(self, stream=None):
+        comps = np.zeros((self.n_sol, 8), dtype=np.int64)
+        F = np.zeros(self.n_sol, dtype=np.float64)
+        _check(lib().md_solution_cost(self.h, _ptr(comps), _ptr(F), _stream(stream)))
+        return comps, F
+
+    def lam(self, stream=None):
+        out = np.zeros((self.n_sol, 4), dtype=np.float32)
+        _check(lib().md_solutions_lambda(self.h, _ptr(out), _stream(stream)))
+        return out
+
+    def summaries(self, stream=None):
+        n = self.n_sol * self.inst.nc
+        pre = np.zeros(n * 8, dtype=np.int32)
+        suf = np.zeros(n * 8, dtype=np.int32)
+        _check(lib().md_solutions_read_summaries(self.h, _ptr(pre), _ptr(suf), _stream(stream)))
+        return pre.reshape(self.n_sol, self.inst.nc, 8), suf.reshape(self.n_sol, self.inst.nc, 8)
+
+    def stats(self, stream=None):
+        out = np.zeros((self.n_sol, 5), dtype=np.int64)
+        _check(lib().md_solutions_stats(self.h, _ptr(out), _stream(stream)))
+        return out
+
+    def descend(self, perm: np.ndarray, max_pass: int, multi: bool = True, lambda_update: bool = False,
+                lambda0=None, use_graph: bool = False, poll_every: int = 1, stream=None) -> DescendStats:
+        perm = np.ascontiguousarray(perm, dtype=np.uint8)
+        assert perm.shape[0] == self.n_sol and perm.shape[1] >= max_pass
+        perm = np.ascontiguousarray(perm[:, :max_pass])
+        n_ops = perm.shape[2]
+        lam = None if lambda0 is None else np.ascontiguousarray(lambda0, dtype=np.float32)
+        cfg = Config(n_ops, max_pass, perm.ctypes.data_as(C.POINTER(C.c_uint8)),
+                     lam.ctypes.data_as(C.POINTER(C.c_float)) if lam is not None else None,
+                     int(multi), int(lambda_update), int(use_graph), int(poll_every))
+        st = Stats()
+        _check(lib().md_descend(self.h, C.byref(cfg), C.byref(st), _stream(stream)))
+        return DescendStats(st.moves_scored, st.steps, st.accepted_steps, st.applied_moves,
+                            st.passes_max, st.launches)
+
+
+class Moves:
+    """Evaluation scratch (md_moves_create) with an optional dump list."""
+
+    def __init__(self, sols: Solutions, dump_capacity: int = 0):
+        self.sols = sols
+        h = C.c_void_p()
+        _check(lib().md_moves_create(sols.h, dump_capacity, C.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().md_moves_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def evaluate(self, ops, lam=None, flags: int = 0, stream=None):
+        ops = np.ascontiguousarray(ops, dtype=np.int32)
+        lam = None if lam is None else np.ascontiguousarray(lam, dtype=np.float32)
+        _check(lib().md_eval_neighborhood(self.sols.h, _ptr(ops), _ptr(lam), flags, self.h, _stream(stream)))
+
+    def leaders(self, stream=None):
+        S = self.sols.n_sol
+        ids = np.zeros(S, dtype=np.uint64)
+        f = np.zeros(S, dtype=np.float64)
+        n = np.zeros(S, dtype=np.int64)
+        _check(lib().md_moves_read_leaders(self.h, _ptr(ids), _ptr(f), _ptr(n), _stream(stream)))
+        return ids, f, n
+
+    def dump(self, cap: int, stream=None) -> np.ndarray:
+        out = np.zeros(max(cap, 1), dtype=MOVE_DTYPE)
+        n = C.c_int64()
+        _check(lib().md_moves_read_dump(self.h, _ptr(out), cap, C.byref(n), _stream(stream)))
+        return out[: n.value]
+
+    def select(self, multi: bool = True, stream=None):
+        _check(lib().md_select_multimove(self.sols.h, self.h, int(multi), _stream(stream)))
+
+    def selection(self, stream=None):
+        S, R = self.sols.n_sol, self.sols.R
+        ids = np.zeros(S * R, dtype=np.uint64)
+        cnt = np.zeros(S, dtype=np.int32)
+        _check(lib().md_selection_read(self.h, _ptr(ids), _ptr(cnt), R, _stream(stream)))
+        ids = ids.reshape(S, R)
+        return [[int(x) for x in ids[s, :cnt[s]]] for s in range(S)]
+
+    def apply(self, update_lambda: bool = False, stream=None):
+        lam = np.zeros((self.sols.n_sol, 4), dtype=np.float32)
+        _check(lib().md_apply_and_rebuild(self.sols.h, self.h, APPLY_UPDATE_LAMBDA if update_lambda else 0,
+                                          _ptr(lam), _stream(stream)))
+        return lam

@@ -1,0 +1,283 @@
+"""GPU path (through the C ABI) against the CPU oracle, element by element on the same seeded inputs.
+
+Integer components (dD, dTW, dLoad, dDur, dV4, counts, ids, routes) must match bit-exactly; the FP64
+dF within 1e-12 relative (both sides combine the same integers in the same order, so it is exact in
+practice).  Sizes span several evaluation tiles (8 customers per block) with ragged tails.
+"""
+import numpy as np
+import pytest
+
+from paper_2605_05208_b300 import workloads as W
+
+from _util import random_solution, tiny_spec
+
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def md():
+    from paper_2605_05208_b300 import build, mdls
+    build.build()
+    return mdls
+
+
+def close(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return np.all(np.abs(a - b) <= RTOL * np.maximum(np.abs(a), np.abs(b)))
+
+
+def setup(md, spec, sols, R=None, K=None):
+    inst = md.Instance(spec)
+    R = R or spec.n_customers + 1
+    K = K or spec.n_customers
+    S = md.Solutions(inst, len(sols), R, K)
+    S.load(sols)
+    return inst, S
+
+
+def canon(spec, sol):
+    return W.canonical(sol, bool(spec.variant & W.VAR_OPEN))
+
+
+# ------------------------------------------------------------------------------------------
+# Instance tensors (Section 1, Eq. A1, Section 3.2.3 / Eq. 3)
+# ------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("which", ["mdvrp", "mdvrptw", "mdovrp"])
+def test_instance_tensors(md, oracle_lib, which):
+    spec = {"mdvrp": W.gen_mdvrp(3, theta=7), "mdvrptw": W.mdvrptw_6x288(2),
+            "mdovrp": W.gen_mdovrp(4, n_depots=5, n_customers=700, theta=9)}[which]
+    inst = md.Instance(spec)
+    o = oracle_lib.Instance(spec)
+    assert np.array_equal(inst.dist().astype(np.int64), o.dist())
+    theta_big, gamma = inst.params()
+    assert theta_big == o.Theta and gamma == o.Gamma
+    nb, cnt = inst.neighbors()
+    onb, ocnt = o.neighbors()
+    assert np.array_equal(cnt, ocnt)
+    for cu in range(spec.n_customers):
+        assert list(nb[cu, :cnt[cu]]) == list(onb[cu, :ocnt[cu]])
+
+
+# ------------------------------------------------------------------------------------------
+# Segment summaries (Section 3.2.2 concatenation) against left-to-right folds of the oracle
+# ------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("which", ["mdvrptw", "mdovrp", "tiny-tw"])
+def test_summaries_match_route_folds(md, oracle_lib, which):
+    if which == "mdvrptw":
+        spec = W.mdvrptw_6x288(3)
+        sols = W.initial_solutions(spec, 3, 3)
+    elif which == "mdovrp":
+        spec = W.gen_mdovrp(5, n_depots=4, n_customers=300)
+        a = W.initial_solution(spec, 6, 0)
+        # merge the first six routes into one long route: the scans then span several chunks of 32
+        merged = [a[0][0]] + [c for r in a[:6] for c in r[1:-1]] + [a[0][-1]]
+        sols = [[merged] + a[6:], W.initial_solution(spec, 7, 1)]
+    else:
+        spec = tiny_spec(8, nd=3, nc=70, tw=True, Q=40, NV=2, D=300, horizon=2000, wmin=100, wmax=600)
+        sols = [random_solution(spec, 8, max_len=40), random_solution(spec, 9, max_len=3)]
+    inst, S = setup(md, spec, sols)
+    pre, suf = S.summaries()
+    closed = W._assemble(spec.name, spec.n_depots, spec.n_customers, spec.x, spec.y, spec.demand,
+                         spec.service, spec.tw_early, spec.tw_late, spec.Q, spec.N_V, spec.D,
+                         spec.variant & ~W.VAR_OPEN, 0, 1)
+    o = oracle_lib.Instance(closed)
+    open_ = bool(spec.variant & W.VAR_OPEN)
+    nd = spec.n_depots
+    for s, sol in enumerate(sols):
+        for r in sol:
+            body = r[1:-1]
+            for k, c in enumerate(body):
+                tp = o.route_terms(r[:k + 2])
+                ts = o.route_terms(body[k:] if open_ else r[k + 1:])
+                gp, gs = pre[s, c - nd], suf[s, c - nd]
+                assert (gp[0], gp[1], gp[2], gp[3]) == (tp["dist"], tp["load"], tp["dur"], tp["tw"])
+                assert (gs[0], gs[1], gs[2], gs[3]) == (ts["dist"], ts["load"], ts["dur"], ts["tw"])
+                assert gp[7] == k + 1
+                assert gs[6] == (r[k] if k > 0 else r[0])
+                assert gs[7] == (body[k + 1] if k + 1 < len(body) else (-1 if open_ else r[-1]))
+        comps, F = S.cost()
+        T, Fo = oracle_lib.Instance(spec).solution_terms(sol)
+        assert list(comps[s]) == [T[k] for k in ("D", "TW", "LoadEx", "DurEx", "closure", "vehEx", "V4", "nroutes")]
+        assert close(F[s], Fo)
+
+
+# ------------------------------------------------------------------------------------------
+# Neighbourhood evaluation: every move, every component
+# ------------------------------------------------------------------------------------------
+
+def _eval_cases():
+    return {
+        "mdvrp-4x50": (W.mdvrp_4x50(11), None, (1.0, 1.0, 1.0, 1.0)),
+        "mdvrptw-6x288-theta50": (W.mdvrptw_6x288(12), 3, (1.0, 1.0, 1.0, 1.0)),
+        "mdvrptw-6x120-full": (W.gen_mdvrptw(13, n_customers=120, theta=0), 2, (2.0, 0.5, 4.0, 0.25)),
+        "mdovrp-5x400": (W.gen_mdovrp(14, n_depots=5, n_customers=400), 2, (1.0, 1.0, 1.0, 1.0)),
+        "tiny-mixed-depots-tw": (tiny_spec(15, nd=4, nc=41, tw=True, Q=30, NV=2, D=250, horizon=1500,
+                                           wmin=60, wmax=500), "random", (1.0, 3.0, 0.5, 2.0)),
+        "tiny-mixed-depots-open": (tiny_spec(16, nd=3, nc=37, open_=True, sym=True, Q=25, NV=1),
+                                   "random", (1.0, 1.0, 1.0, 1.0)),
+        "tiny-sym-theta": (tiny_spec(17, nd=3, nc=45, sym=True, Q=30, NV=2, theta=6), "random",
+                           (1.0, 1.0, 1.0, 8.0)),
+    }
+
+
+@pytest.mark.parametrize("case", list(_eval_cases()))
+def test_eval_every_move_matches_oracle(md, oracle_lib, case):
+    spec, nsol, lam = _eval_cases()[case]
+    if nsol == "random":
+        sols = [random_solution(spec, 100 + i, max_len=5) for i in range(3)]
+    else:
+        sols = W.initial_solutions(spec, 21, nsol)
+    o = oracle_lib.Instance(spec)
+    inst, S = setup(md, spec, sols)
+    lamv = np.tile(np.asarray(lam, np.float32), (len(sols), 1))
+    for op in range(W.N_OPS):
+        want = [o.eval_op(sol, op, lam) for sol in sols]
+        cap = sum(len(w[0]) for w in want) + 16
+        M = md.Moves(S, dump_capacity=cap)
+        M.evaluate(np.full(len(sols), op, np.int32), lamv, flags=md.EVAL_DUMP)
+        got = M.dump(cap)
+        ids, f, n = M.leaders()
+        for s, (mv, scored) in enumerate(want):
+            g = np.sort(got[got["sol"] == s], order="id")
+            w = np.sort(mv, order="id")
+            assert len(g) == len(w), (op, s)
+            assert np.array_equal(g["id"], w["id"]), (op, s)
+            for k in ("dD", "dTW", "dLoad", "dDur", "dV4"):
+                assert np.array_equal(g[k], w[k]), (op, s, k)
+            assert close(g["dF"], w["dF"]), (op, s)
+            assert n[s] == scored, (op, s)
+            neg = w[w["dF"] < 0]
+            if len(neg):
+                best = neg[np.lexsort((neg["id"] & 0xFFFFFFFF, neg["dF"]))[0]]
+                assert ids[s] == best["id"] and f[s] == best["dF"], (op, s)
+            else:
+                assert ids[s] == 0
+        M.close()
+
+
+# ------------------------------------------------------------------------------------------
+# Selection (Section 3.2.5) and apply + rebuild
+# ------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("case", ["mdvrp-4x50", "mdvrptw-6x288-theta50", "tiny-mixed-depots-tw",
+                                  "tiny-mixed-depots-open", "tiny-sym-theta"])
+@pytest.mark.parametrize("multi", [True, False])
+def test_select_and_apply_match_oracle(md, oracle_lib, case, multi):
+    spec, nsol, lam = _eval_cases()[case]
+    if nsol == "random":
+        sols = [random_solution(spec, 200 + i, max_len=5) for i in range(3)]
+    else:
+        sols = W.initial_solutions(spec, 31, nsol or 4)
+    o = oracle_lib.Instance(spec)
+    lamv = np.tile(np.asarray(lam, np.float32), (len(sols), 1))
+    for op in range(W.N_OPS):
+        inst, S = setup(md, spec, sols)
+        M = md.Moves(S)
+        M.evaluate(np.full(len(sols), op, np.int32), lamv, flags=md.EVAL_FOLLOWERS if multi else 0)
+        M.select(multi=multi)
+        sel = M.selection()
+        lam_gpu = M.apply(update_lambda=True)
+        after = S.read()
+        comps, F = S.cost()
+        for s, sol in enumerate(sols):
+            mv, _ = o.eval_op(sol, op, lam)
+            want = o.select(mv, len(sol), multi=multi)
+            assert sorted(sel[s]) == sorted(want), (op, s)
+            if want:
+                assert sel[s][0] == want[0]  # the leader comes first
+            new = o.apply(sol, want)
+            assert canon(spec, after[s]) == canon(spec, new), (op, s)
+            T, _ = o.solution_terms(new)
+            assert comps[s][6] == T["V4"] and comps[s][0] == T["D"]
+            wl = o.update_lambda(new, lam) if want else np.asarray(lam, np.float32)
+            assert np.array_equal(lam_gpu[s], wl), (op, s)
+
+
+# ------------------------------------------------------------------------------------------
+# Descent (Alg. 2): final solutions and every counter
+# ------------------------------------------------------------------------------------------
+
+def _descent_cases():
+    return {
+        "mdvrp-4x50": (W.mdvrp_4x50(41), 8),
+        "mdvrptw-6x288-theta50": (W.mdvrptw_6x288(42), 2),
+        "mdovrp-4x150": (W.gen_mdovrp(43, n_depots=4, n_customers=150), 3),
+        "tiny-mixed-tw": (tiny_spec(44, nd=3, nc=40, tw=True, Q=30, NV=2, D=250, horizon=1500,
+                                    wmin=60, wmax=500), 3),
+    }
+
+
+@pytest.mark.parametrize("case", list(_descent_cases()))
+@pytest.mark.parametrize("mode", ["multi", "single", "multi-lambda"])
+def test_descent_matches_oracle(md, oracle_lib, case, mode):
+    spec, nsol = _descent_cases()[case]
+    if case.startswith("tiny"):
+        sols = [random_solution(spec, 300 + i, max_len=6) for i in range(nsol)]
+    else:
+        sols = W.initial_solutions(spec, 51, nsol)
+    multi = mode != "single"
+    lup = mode == "multi-lambda"
+    max_pass = 60
+    perm = W.op_permutations(7, nsol, max_pass)
+    inst, S = setup(md, spec, sols)
+    st = S.descend(perm, max_pass, multi=multi, lambda_update=lup, use_graph=(mode == "multi"))
+    got = S.read()
+    per = S.stats()
+    lam = S.lam()
+    o = oracle_lib.Instance(spec)
+    tot = np.zeros(5, np.int64)
+    for s, sol in enumerate(sols):
+        d = o.descend(sol, perm[s], max_pass, multi=multi, lambda_update=lup)
+        assert canon(spec, got[s]) == canon(spec, d.solution), s
+        assert list(per[s]) == [d.moves_scored, d.steps, d.accepted_steps, d.applied_moves, d.passes], s
+        assert np.array_equal(lam[s], d.lam)
+        tot += per[s]
+    assert st.moves_scored == tot[0] and st.steps == tot[1] and st.applied_moves == tot[3]
+
+
+# ------------------------------------------------------------------------------------------
+# Edge cases
+# ------------------------------------------------------------------------------------------
+
+def test_single_customer_and_single_route(md, oracle_lib):
+    spec = tiny_spec(60, nd=3, nc=1, Q=5, NV=1)
+    sols = [[[0, 3, 1]], [[2, 3, 2]]]
+    o = oracle_lib.Instance(spec)
+    inst, S = setup(md, spec, sols, R=4, K=2)
+    for op in range(W.N_OPS):
+        M = md.Moves(S, dump_capacity=64)
+        M.evaluate(np.full(2, op, np.int32), flags=md.EVAL_DUMP)
+        got = M.dump(64)
+        for s, sol in enumerate(sols):
+            want, _ = o.eval_op(sol, op)
+            assert sorted(got[got["sol"] == s]["id"].tolist()) == sorted(want["id"].tolist())
+
+
+def test_every_customer_in_one_route_and_theta_above_n(md, oracle_lib):
+    spec = tiny_spec(61, nd=2, nc=50, tw=True, Q=200, NV=1, D=400, horizon=3000, wmin=200, wmax=900, theta=80)
+    sol = [[0] + list(range(2, 52)) + [1]]
+    o = oracle_lib.Instance(spec)
+    inst, S = setup(md, spec, [sol])
+    perm = W.op_permutations(3, 1, 40)
+    S.descend(perm, 40)
+    d = o.descend(sol, perm[0], 40)
+    assert canon(spec, S.read()[0]) == canon(spec, d.solution)
+
+
+def test_capacity_error_is_reported(md):
+    spec = tiny_spec(62, nd=2, nc=12, Q=100, NV=3)
+    sols = [[[0, 2, 3, 4, 0], [1, 5, 6, 7, 8, 9, 10, 11, 12, 13, 1]]]
+    inst = md.Instance(spec)
+    with pytest.raises(md.MdError) as e:
+        S = md.Solutions(inst, 1, 2, 5)  # route of 9 customers does not fit k_max = 5
+        S.load(sols)
+    assert e.value.status == md.MD_ERR_CAPACITY
+    S = md.Solutions(inst, 1, 4, 12)
+    with pytest.raises(md.MdError) as e:
+        S.load([[[0, 2, 3, 0], [1, 4, 4, 1]]])  # repeated customer
+    assert e.value.status == md.MD_ERR_ARG
