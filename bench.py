@@ -1,0 +1,332 @@
+#!/usr/bin/env python3
+"""Benchmark of the MDFIS local-search hot path on B300: moves evaluated/s and LS descents/s.
+
+One step = one complete MDFIS descent (Alg. 2: relocate, swap, 2-opt*, Depot-Insert and
+Depot-Replace in a seeded random order per pass, leader-follower multi-move update, until a pass
+applies nothing or delta = 500 passes) of 32 seeded solutions of a synthetic MDVRPTW instance with
+6 depots and 288 customers (theta = 50 granular neighbours, the paper's setting).  The instance and
+the initial solutions are resident in HBM before the timed region; every step restores the initial
+routes on the device, rebuilds all summaries and descends.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun every rank descends its own 32 solutions (weak scaling); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2605_05208_b300 import workloads as W  # noqa: E402
+
+METRIC = "moves evaluated/s"
+UNIT = "moves/s"
+MAX_PASS = 500          # search depth delta (Table 1)
+SEED = 1
+N_SOL = 32
+THETA = 50
+# Algorithmic bytes per scored move of each operator: the solution-dependent gathers the method
+# must make (distance-matrix entries of the arcs a move creates, plus the route summaries of the
+# second route for 2-opt* and the depot operators); u-independent summaries are amortised.
+ALG_BYTES = {W.OP_RELOCATE: 8, W.OP_SWAP: 16, W.OP_TWO_OPT_STAR: 56, W.OP_DEPOT_INSERT: 32,
+             W.OP_DEPOT_REPLACE: 32}
+CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+def workload_spec(rank: int = 0):
+    spec = W.mdvrptw_6x288(SEED + rank, theta=THETA)
+    sols = W.initial_solutions(spec, SEED + rank, N_SOL)
+    perm = W.op_permutations(SEED + rank, N_SOL, MAX_PASS)
+    return spec, sols, perm
+
+
+def workload_name() -> str:
+    return (f"mdvrptw-6x288 (6 depots, 288 customers, horizon 1000, Q=200, N_V=6, D=1000), "
+            f"theta={THETA}, {N_SOL} solutions, full descent to local optimum (delta={MAX_PASS}), "
+            f"multi-move, lambda=(1,1,1,1)")
+
+
+# ------------------------------------------------------------------------------------------
+# CPU oracle baseline (test infrastructure: the plain oracle, untuned, on the host cores)
+# ------------------------------------------------------------------------------------------
+
+_ORACLE_CACHE = {}
+
+
+def _oracle_descend(args):
+    rank, idx = args
+    from oracle import oracle as O
+    if rank not in _ORACLE_CACHE:
+        spec, sols, perm = workload_spec(rank)
+        _ORACLE_CACHE[rank] = (O.Instance(spec), sols, perm)
+    inst, sols, perm = _ORACLE_CACHE[rank]
+    t0 = time.perf_counter()
+    d = inst.descend(sols[idx], perm[idx], MAX_PASS, multi=True)
+    return d.moves_scored, time.perf_counter() - t0
+
+
+def oracle_sample(pool, n: int, rank: int = 0):
+    t0 = time.perf_counter()
+    res = pool.map(_oracle_descend, [(rank, i % N_SOL) for i in range(n)])
+    wall = time.perf_counter() - t0
+    moves = sum(r[0] for r in res)
+    cpu = sum(r[1] for r in res)
+    return moves, wall, cpu
+
+
+def make_pool(n: int):
+    from oracle import oracle as O
+    O.build()
+    return mp.get_context("spawn").Pool(n)
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cores = min(os.cpu_count() or 1, 16)
+    sample = cores
+    pool = make_pool(cores)
+    for _ in range(args.warmup):
+        oracle_sample(pool, sample)
+    tot_moves, tot_wall, tot_cpu = 0, 0.0, 0.0
+    for _ in range(args.steps):
+        m, w, c = oracle_sample(pool, sample)
+        tot_moves += m
+        tot_wall += w
+        tot_cpu += c
+    pool.close()
+    value = tot_moves / tot_wall
+    desc = (f"plain C oracle, {sample} of the {N_SOL} descents per step ({cores} processes), "
+            f"{tot_cpu / args.steps:.1f} s CPU per step")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_wall / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64/f64",
+        "data": "synthetic", "config": {"workload": workload_name(), "sample": desc},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+# ------------------------------------------------------------------------------------------
+# GPU arm
+# ------------------------------------------------------------------------------------------
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={CLOCK_FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names[1:], f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2605_05208_b300 import build, mdls
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    build.build()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(dev)  # a real stream: the legacy default stream cannot be captured
+    torch.cuda.set_stream(stream)
+    sptr = stream.cuda_stream
+
+    # CPU baseline pool before the first GPU call (spawn), rank 0 only
+    pool = None
+    if rank == 0 and not args.no_cpu_baseline:
+        ncores = min(os.cpu_count() or 1, 16)
+        pool = make_pool(ncores)
+
+    spec, sols, perm = workload_spec(rank)
+    inst = mdls.Instance(spec)
+    max_routes = max(len(s) for s in sols)
+    R = min(spec.n_customers, max(64, 2 * max_routes, spec.n_depots * spec.N_V + 8))
+    K = min(spec.n_customers, 64)
+    init = mdls.Solutions(inst, N_SOL, R, K)
+    work = mdls.Solutions(inst, N_SOL, R, K)
+    init.load(sols)
+    perm_dev = torch.from_numpy(np.ascontiguousarray(perm)).to(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)  # > 126 MB L2
+
+    def step(time_eval=False):
+        work.copy_from(init, stream=sptr)
+        return work.descend(perm_dev.data_ptr(), MAX_PASS, multi=True, use_graph=True, poll_every=1,
+                            stream=sptr, n_ops=W.N_OPS, time_eval=time_eval)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    stats = []
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.fill_(k)  # evict the working set from L2 between timed steps
+            ev0[k].record(stream)
+            stats.append(step(time_eval=True))
+            ev1[k].record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
+    total_ms = float(sum(ms))
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms_max = float(t.item())
+    moves = sum(s.moves_scored for s in stats)
+    mv = torch.tensor([float(moves)], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(mv, op=dist.ReduceOp.SUM)
+    moves_all = float(mv.item())
+    value = moves_all / (total_ms_max / 1e3)
+    descents = N_SOL * world * args.steps / (total_ms_max / 1e3)
+
+    # dominant kernel: the neighbourhood evaluation, timed live with events around each launch
+    eval_ms = sum(s.eval_ms for s in stats)
+    eval_launches = sum(s.eval_launches for s in stats)
+    by_op = np.sum([s.moves_by_op for s in stats], axis=0)
+    alg_bytes = float(sum(int(by_op[o]) * ALG_BYTES[o] for o in range(W.N_OPS)))
+    achieved = alg_bytes / (eval_ms / 1e3) / 1e9
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    peak = float(peaks.get("hbm_gbs", 6400.0))
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+
+    # end to end through the C ABI with host buffers: H2D of the routes and the operator order,
+    # the descent, D2H of the per-solution costs
+    nodes, offs, per = mdls.flatten(sols)
+    pin = lambda a: torch.from_numpy(a).pin_memory()
+    h_nodes, h_offs, h_per = pin(nodes), pin(offs), pin(per)
+    h_perm = np.ascontiguousarray(perm)
+    e2e_ms = []
+    for k in range(args.steps):
+        flush.fill_(k)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        work.load_flat(h_nodes.numpy(), h_offs.numpy(), h_per.numpy(), stream=sptr)
+        work.descend(h_perm, MAX_PASS, multi=True, use_graph=True, poll_every=1, stream=sptr)
+        comps, F = work.cost(stream=sptr)
+        e2e_ms.append(1e3 * (time.perf_counter() - t0))
+    n_routes = int(per.sum())
+    h2d = nodes.nbytes + 16 * n_routes + h_perm.nbytes
+    d2h = comps.nbytes + F.nbytes
+    e2e_value = (moves / args.steps) * world / (statistics.mean(e2e_ms) / 1e3)
+
+    cpu = None
+    if rank == 0 and pool is not None:
+        m, wall, cpu_s = oracle_sample(pool, pool._processes)
+        desc = (f"{pool._processes} of the {N_SOL} descents of this workload, one per process; "
+                f"{cpu_s:.1f} s CPU, {wall:.1f} s wall")
+        cpu = {"value": m / wall, "unit": UNIT, "cores": pool._processes, "kind": "oracle", "sample": desc}
+        pool.close()
+
+    if rank == 0:
+        last = stats[-1]
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32/f64", "data": "synthetic",
+            "config": {"workload": workload_name(), "l2": "flushed between timed steps (256 MB write)",
+                       "route_slots": R, "k_max": K, "parallelism": f"{world} independent replicas"},
+            "descents_per_s": descents,
+            "moves_per_step": moves / args.steps,
+            "passes_max": last.passes_max, "steps_per_descent": last.steps / N_SOL,
+            "roofline": {"kernel": "k_eval (neighbourhood evaluation)", "bound": "hbm",
+                         "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "peak_source": peak_src, "traffic": None,
+                         "eval_ms_per_launch": eval_ms / max(eval_launches, 1),
+                         "alg_bytes_per_launch": alg_bytes / max(eval_launches, 1),
+                         "eval_share_of_step": eval_ms / total_ms},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "ms_per_step": statistics.mean(e2e_ms)},
+            "gpu_launches": int(sum(s.launches for s in stats) + 3 * args.steps),
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -123,6 +123,8 @@ typedef struct md_config {
     int32_t lambda_update;  /* 1: adapt lambda after every accepted step (kappa = 0.5) */
     int32_t use_graph;      /* 1: replay one captured CUDA graph per pass */
     int32_t poll_every;     /* passes between host checks of the per-solution done flags */
+    int32_t op_perm_device; /* 1: op_perm points to device memory (no host copy per call) */
+    int32_t time_eval;      /* 1: time every evaluation launch with CUDA events (md_stats.eval_ms) */
 } md_config;
 
 /* Totals over all solutions of one md_descend call. */
@@ -133,6 +135,9 @@ typedef struct md_stats {
     int64_t applied_moves;  /* leaders + followers applied */
     int64_t passes_max;     /* largest number of passes any solution ran */
     int64_t launches;       /* kernels launched by the call */
+    int64_t eval_launches;  /* evaluation kernel launches */
+    double eval_ms;         /* summed device time of the evaluation launches (time_eval = 1) */
+    int64_t moves_by_op[MD_N_OPS]; /* scored move tuples per operator */
 } md_stats;
 
 /* Message for the calling thread's last failing call ("" if none). */

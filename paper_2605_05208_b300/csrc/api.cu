@@ -45,7 +45,7 @@ __global__ void k_descend_init(DevSols D, int n_ops, int max_pass, int multi, in
     int *st = D.state + (size_t)s * 8;
     st[0] = 0; st[1] = 0; st[2] = 0; st[3] = 0;
     st[4] = n_ops; st[5] = max_pass; st[6] = multi; st[7] = lup;
-    for (int k = 0; k < 8; k++) D.stats[(size_t)s * 8 + k] = 0;
+    for (int k = 0; k < 16; k++) D.stats[(size_t)s * 16 + k] = 0;
     D.ops[s] = (int)D.perm[(size_t)s * max_pass * n_ops];
 }
 
@@ -262,8 +262,9 @@ extern "C" md_status md_descend(md_solutions *s, const md_config *cfg, md_stats 
         return MD_ERR_ARG;
     }
     const size_t nperm = (size_t)s->n_sol * cfg->max_pass * cfg->n_ops;
-    for (size_t i = 0; i < nperm; i++)
-        if (cfg->op_perm[i] >= MD_N_OPS) { md_set_error("md_descend: unknown operator in op_perm"); return MD_ERR_ARG; }
+    if (!cfg->op_perm_device)
+        for (size_t i = 0; i < nperm; i++)
+            if (cfg->op_perm[i] >= MD_N_OPS) { md_set_error("md_descend: unknown operator in op_perm"); return MD_ERR_ARG; }
     cudaStream_t st = (cudaStream_t)stream;
     // the evaluation scratch of the descent is created once and kept with the solutions
     if (!s->scratch) {
@@ -271,16 +272,20 @@ extern "C" md_status md_descend(md_solutions *s, const md_config *cfg, md_stats 
         if (r != MD_OK) return r;
     }
     md_moves *m = s->scratch;
-    if (s->perm_bytes < nperm) {
-        cudaFree(s->perm_dev);
-        s->perm_dev = nullptr;
-        s->perm_bytes = 0;
-        MD_CUDA(cudaMalloc(&s->perm_dev, nperm));
-        s->perm_bytes = nperm;
+    if (cfg->op_perm_device) {
+        s->d.perm = cfg->op_perm;
+    } else {
+        if (s->perm_bytes < nperm) {
+            cudaFree(s->perm_dev);
+            s->perm_dev = nullptr;
+            s->perm_bytes = 0;
+            MD_CUDA(cudaMalloc(&s->perm_dev, nperm));
+            s->perm_bytes = nperm;
+        }
+        MD_CUDA(cudaMemcpyAsync(s->perm_dev, cfg->op_perm, nperm, cudaMemcpyHostToDevice, st));
+        s->d.perm = s->perm_dev;
     }
-    MD_CUDA(cudaMemcpyAsync(s->perm_dev, cfg->op_perm, nperm, cudaMemcpyHostToDevice, st));
-    s->d.perm = s->perm_dev;
-    long long launches = 0;
+    long long launches = 0, eval_launches = 0;
     if (cfg->lambda0) MD_CUDA(cudaMemcpyAsync(s->d.lam, cfg->lambda0, sizeof(float) * 4 * s->n_sol, cudaMemcpyHostToDevice, st));
     md_status r = md_launch_totals(s, st);
     if (r != MD_OK) return r;
@@ -294,61 +299,92 @@ extern "C" md_status md_descend(md_solutions *s, const md_config *cfg, md_stats 
     const uint32_t eflags = cfg->multi_move ? MD_EVAL_FOLLOWERS : 0u;
     const int poll = cfg->poll_every > 0 ? cfg->poll_every : 1;
     const int steps_per_poll = cfg->n_ops * poll;
+    std::vector<cudaEvent_t> ev;
+    if (cfg->time_eval) {
+        ev.resize(2 * (size_t)steps_per_poll);
+        for (auto &e : ev) MD_CUDA(cudaEventCreate(&e));
+    }
+    auto release = [&]() { for (auto &e : ev) cudaEventDestroy(e); ev.clear(); };
+    // one pass chunk: (evaluate, select + apply + advance) per step, optionally bracketed by
+    // events; inside a stream capture an event only becomes a record node (and so gets a
+    // timestamp at every replay) when it is recorded as external
+    auto enqueue = [&](bool capturing) -> md_status {
+        const unsigned int rf = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
+        for (int k = 0; k < steps_per_poll; k++) {
+            if (!ev.empty()) MD_CUDA(cudaEventRecordWithFlags(ev[2 * k], st, rf));
+            md_status q = md_launch_eval(s, m, eflags, st);
+            if (q != MD_OK) return q;
+            if (!ev.empty()) MD_CUDA(cudaEventRecordWithFlags(ev[2 * k + 1], st, rf));
+            q = md_launch_step(s, m, st);
+            if (q != MD_OK) return q;
+        }
+        return MD_OK;
+    };
     std::vector<int32_t> state((size_t)s->n_sol * 8);
     cudaGraphExec_t exec = nullptr;
     cudaGraph_t graph = nullptr;
     const bool use_graph = cfg->use_graph && st != nullptr;
     if (use_graph) {
         MD_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-        md_status cr = MD_OK;
-        for (int k = 0; k < steps_per_poll && cr == MD_OK; k++) {
-            cr = md_launch_eval(s, m, eflags, st);
-            if (cr == MD_OK) cr = md_launch_step(s, m, st);
-        }
+        md_status cr = enqueue(true);
         cudaError_t ce = cudaStreamEndCapture(st, &graph);
-        if (cr != MD_OK) { if (graph) cudaGraphDestroy(graph); return cr; }
-        MD_CUDA(ce);
-        MD_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+        if (cr != MD_OK) { if (graph) cudaGraphDestroy(graph); release(); return cr; }
+        if (ce != cudaSuccess) { release(); return md_cuda_check(ce, "cudaStreamEndCapture"); }
+        ce = cudaGraphInstantiate(&exec, graph, 0);
+        if (ce != cudaSuccess) { cudaGraphDestroy(graph); release(); return md_cuda_check(ce, "cudaGraphInstantiate"); }
     }
+    double eval_ms = 0.0;
     int passes_done = 0;
     bool all_done = false;
+    md_status rr = MD_OK;
     while (!all_done && passes_done <= cfg->max_pass) {
         if (use_graph) {
-            MD_CUDA(cudaGraphLaunch(exec, st));
+            cudaError_t ce = cudaGraphLaunch(exec, st);
+            if (ce != cudaSuccess) { rr = md_cuda_check(ce, "cudaGraphLaunch"); break; }
         } else {
-            for (int k = 0; k < steps_per_poll; k++) {
-                r = md_launch_eval(s, m, eflags, st);
-                if (r != MD_OK) return r;
-                r = md_launch_step(s, m, st);
-                if (r != MD_OK) return r;
-            }
+            rr = enqueue(false);
+            if (rr != MD_OK) break;
         }
         launches += 2LL * steps_per_poll;
+        eval_launches += steps_per_poll;
         passes_done += poll;
-        MD_CUDA(cudaMemcpyAsync(state.data(), s->d.state, sizeof(int32_t) * 8 * s->n_sol, cudaMemcpyDeviceToHost, st));
-        MD_CUDA(cudaStreamSynchronize(st));
+        cudaError_t ce = cudaMemcpyAsync(state.data(), s->d.state, sizeof(int32_t) * 8 * s->n_sol, cudaMemcpyDeviceToHost, st);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+        if (ce != cudaSuccess) { rr = md_cuda_check(ce, "md_descend poll"); break; }
+        for (int k = 0; k < steps_per_poll && !ev.empty(); k++) {
+            float ms = 0.0f;
+            ce = cudaEventElapsedTime(&ms, ev[2 * k], ev[2 * k + 1]);
+            if (ce != cudaSuccess) break;
+            eval_ms += ms;
+        }
+        if (ce != cudaSuccess) { rr = md_cuda_check(ce, "cudaEventElapsedTime"); break; }
         all_done = true;
         for (int i = 0; i < s->n_sol; i++) all_done &= state[(size_t)i * 8 + 3] != 0;
     }
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
+    release();
+    if (rr != MD_OK) return rr;
     r = check_err(s, st);
     if (r != MD_OK) return r;
     if (!all_done) { md_set_error("md_descend: solutions still running after max_pass passes"); return MD_ERR_STATE; }
     if (out) {
-        std::vector<long long> h((size_t)s->n_sol * 8);
-        MD_CUDA(cudaMemcpyAsync(h.data(), s->d.stats, sizeof(long long) * 8 * s->n_sol, cudaMemcpyDeviceToHost, st));
+        std::vector<long long> h((size_t)s->n_sol * 16);
+        MD_CUDA(cudaMemcpyAsync(h.data(), s->d.stats, sizeof(long long) * 16 * s->n_sol, cudaMemcpyDeviceToHost, st));
         MD_CUDA(cudaStreamSynchronize(st));
         memset(out, 0, sizeof(*out));
         for (int i = 0; i < s->n_sol; i++) {
-            const long long *x = &h[(size_t)i * 8];
+            const long long *x = &h[(size_t)i * 16];
             out->moves_scored += x[0];
             out->steps += x[1];
             out->accepted_steps += x[2];
             out->applied_moves += x[3];
             if (x[4] > out->passes_max) out->passes_max = x[4];
+            for (int o = 0; o < MD_N_OPS; o++) out->moves_by_op[o] += x[8 + o];
         }
         out->launches = launches;
+        out->eval_launches = eval_launches;
+        out->eval_ms = eval_ms;
     }
     return MD_OK;
 }

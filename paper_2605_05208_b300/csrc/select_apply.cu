@@ -392,8 +392,9 @@ __global__ void k_step(DevInst I, DevSols D, DevMoves M) {
         if (lup) update_lambda(I, D, s);
     }
     if (threadIdx.x == 0) {
-        long long *stt = D.stats + (size_t)s * 8;
+        long long *stt = D.stats + (size_t)s * 16;
         stt[0] += (long long)M.nscored[s];
+        stt[8 + D.ops[s]] += (long long)M.nscored[s];
         M.nscored[s] = 0;
         stt[1] += 1;
         if (nsel > 0) { stt[2] += 1; stt[3] += nsel; st[2] = 1; }

@@ -115,12 +115,12 @@ extern "C" md_status md_solutions_create(const md_instance *inst, int32_t n_sol,
     MDA(cudaMalloc(&d.w, sizeof(double) * (size_t)n_sol * 4));
     MDA(cudaMalloc(&d.ops, sizeof(int32_t) * n_sol));
     MDA(cudaMalloc(&d.state, sizeof(int32_t) * (size_t)n_sol * 8));
-    MDA(cudaMalloc(&d.stats, sizeof(long long) * (size_t)n_sol * 8));
+    MDA(cudaMalloc(&d.stats, sizeof(long long) * (size_t)n_sol * 16));
     MDA(cudaMalloc(&d.err, sizeof(int32_t)));
     MDA(cudaMemset(d.rhdr, 0, sizeof(int4) * SR));
     MDA(cudaMemset(d.ops, 0xff, sizeof(int32_t) * n_sol));
     MDA(cudaMemset(d.state, 0, sizeof(int32_t) * (size_t)n_sol * 8));
-    MDA(cudaMemset(d.stats, 0, sizeof(long long) * (size_t)n_sol * 8));
+    MDA(cudaMemset(d.stats, 0, sizeof(long long) * (size_t)n_sol * 16));
     MDA(cudaMemset(d.err, 0, sizeof(int32_t)));
     MDA(cudaMemset(d.tot, 0, sizeof(long long) * (size_t)n_sol * 8));
 #undef MDA
@@ -289,10 +289,10 @@ extern "C" md_status md_solutions_read_summaries(md_solutions *S, int32_t *pre, 
 extern "C" md_status md_solutions_stats(md_solutions *S, int64_t *per_sol, void *stream) {
     if (!S || !per_sol) { md_set_error("md_solutions_stats: null argument"); return MD_ERR_ARG; }
     cudaStream_t st = (cudaStream_t)stream;
-    std::vector<long long> h((size_t)S->n_sol * 8);
-    MD_CUDA(cudaMemcpyAsync(h.data(), S->d.stats, sizeof(long long) * 8 * S->n_sol, cudaMemcpyDeviceToHost, st));
+    std::vector<long long> h((size_t)S->n_sol * 16);
+    MD_CUDA(cudaMemcpyAsync(h.data(), S->d.stats, sizeof(long long) * 16 * S->n_sol, cudaMemcpyDeviceToHost, st));
     MD_CUDA(cudaStreamSynchronize(st));
     for (int s = 0; s < S->n_sol; s++)
-        for (int k = 0; k < 5; k++) per_sol[(size_t)s * 5 + k] = h[(size_t)s * 8 + k];
+        for (int k = 0; k < 5; k++) per_sol[(size_t)s * 5 + k] = h[(size_t)s * 16 + k];
     return MD_OK;
 }

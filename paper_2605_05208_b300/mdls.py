@@ -64,12 +64,14 @@ MOVE_DTYPE = np.dtype([("id", np.uint64), ("dD", np.int64), ("dTW", np.int64), (
 class Config(C.Structure):
     _fields_ = [("n_ops", C.c_int32), ("max_pass", C.c_int32), ("op_perm", C.POINTER(C.c_uint8)),
                 ("lambda0", C.POINTER(C.c_float)), ("multi_move", C.c_int32),
-                ("lambda_update", C.c_int32), ("use_graph", C.c_int32), ("poll_every", C.c_int32)]
+                ("lambda_update", C.c_int32), ("use_graph", C.c_int32), ("poll_every", C.c_int32),
+                ("op_perm_device", C.c_int32), ("time_eval", C.c_int32)]
 
 
 class Stats(C.Structure):
     _fields_ = [("moves_scored", C.c_int64), ("steps", C.c_int64), ("accepted_steps", C.c_int64),
-                ("applied_moves", C.c_int64), ("passes_max", C.c_int64), ("launches", C.c_int64)]
+                ("applied_moves", C.c_int64), ("passes_max", C.c_int64), ("launches", C.c_int64),
+                ("eval_launches", C.c_int64), ("eval_ms", C.c_double), ("moves_by_op", C.c_int64 * 5)]
 
 
 _lib = None
@@ -202,6 +204,9 @@ class DescendStats:
     applied_moves: int
     passes_max: int
     launches: int
+    eval_launches: int
+    eval_ms: float
+    moves_by_op: tuple
 
 
 class Solutions:
@@ -274,20 +279,30 @@ class Solutions:
         _check(lib().md_solutions_stats(self.h, _ptr(out), _stream(stream)))
         return out
 
-    def descend(self, perm: np.ndarray, max_pass: int, multi: bool = True, lambda_update: bool = False,
-                lambda0=None, use_graph: bool = False, poll_every: int = 1, stream=None) -> DescendStats:
-        perm = np.ascontiguousarray(perm, dtype=np.uint8)
-        assert perm.shape[0] == self.n_sol and perm.shape[1] >= max_pass
-        perm = np.ascontiguousarray(perm[:, :max_pass])
-        n_ops = perm.shape[2]
+    def descend(self, perm, max_pass: int, multi: bool = True, lambda_update: bool = False,
+                lambda0=None, use_graph: bool = False, poll_every: int = 1, stream=None,
+                n_ops: int | None = None, time_eval: bool = False) -> DescendStats:
+        """MDFIS descent.  perm: uint8 host array [n_sol, >= max_pass, n_ops], or an int device
+        pointer to a [n_sol, max_pass, n_ops] uint8 buffer (then n_ops must be given)."""
+        if isinstance(perm, int):
+            assert n_ops is not None
+            pptr, on_dev = C.cast(C.c_void_p(perm), C.POINTER(C.c_uint8)), 1
+        else:
+            perm = np.ascontiguousarray(perm, dtype=np.uint8)
+            assert perm.shape[0] == self.n_sol and perm.shape[1] >= max_pass
+            perm = np.ascontiguousarray(perm[:, :max_pass])
+            n_ops = perm.shape[2]
+            pptr, on_dev = perm.ctypes.data_as(C.POINTER(C.c_uint8)), 0
         lam = None if lambda0 is None else np.ascontiguousarray(lambda0, dtype=np.float32)
-        cfg = Config(n_ops, max_pass, perm.ctypes.data_as(C.POINTER(C.c_uint8)),
+        cfg = Config(n_ops, max_pass, pptr,
                      lam.ctypes.data_as(C.POINTER(C.c_float)) if lam is not None else None,
-                     int(multi), int(lambda_update), int(use_graph), int(poll_every))
+                     int(multi), int(lambda_update), int(use_graph), int(poll_every), on_dev,
+                     int(time_eval))
         st = Stats()
         _check(lib().md_descend(self.h, C.byref(cfg), C.byref(st), _stream(stream)))
         return DescendStats(st.moves_scored, st.steps, st.accepted_steps, st.applied_moves,
-                            st.passes_max, st.launches)
+                            st.passes_max, st.launches, st.eval_launches, st.eval_ms,
+                            tuple(st.moves_by_op))
 
 
 class Moves:

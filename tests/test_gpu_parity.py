@@ -23,6 +23,13 @@ def md():
     return mdls
 
 
+@pytest.fixture(scope="module")
+def stream():
+    """A non-default CUDA stream (graph capture needs one)."""
+    import torch
+    return torch.cuda.Stream().cuda_stream
+
+
 def close(a, b):
     a = np.asarray(a, np.float64)
     b = np.asarray(b, np.float64)
@@ -214,7 +221,7 @@ def _descent_cases():
 
 @pytest.mark.parametrize("case", list(_descent_cases()))
 @pytest.mark.parametrize("mode", ["multi", "single", "multi-lambda"])
-def test_descent_matches_oracle(md, oracle_lib, case, mode):
+def test_descent_matches_oracle(md, oracle_lib, stream, case, mode):
     spec, nsol = _descent_cases()[case]
     if case.startswith("tiny"):
         sols = [random_solution(spec, 300 + i, max_len=6) for i in range(nsol)]
@@ -225,7 +232,8 @@ def test_descent_matches_oracle(md, oracle_lib, case, mode):
     max_pass = 60
     perm = W.op_permutations(7, nsol, max_pass)
     inst, S = setup(md, spec, sols)
-    st = S.descend(perm, max_pass, multi=multi, lambda_update=lup, use_graph=(mode == "multi"))
+    st = S.descend(perm, max_pass, multi=multi, lambda_update=lup, use_graph=(mode == "multi"),
+                   stream=stream if mode == "multi" else None)
     got = S.read()
     per = S.stats()
     lam = S.lam()
@@ -238,6 +246,24 @@ def test_descent_matches_oracle(md, oracle_lib, case, mode):
         assert np.array_equal(lam[s], d.lam)
         tot += per[s]
     assert st.moves_scored == tot[0] and st.steps == tot[1] and st.applied_moves == tot[3]
+
+
+def test_timed_graph_descent_matches_untimed(md, stream):
+    # Event timing of every evaluation launch inside the captured graph changes nothing else.
+    spec = W.mdvrptw_6x288(45)
+    sols = W.initial_solutions(spec, 45, 8)
+    perm = W.op_permutations(8, 8, 100)
+    inst = md.Instance(spec)
+    runs = []
+    for graph, timed in ((False, False), (True, True), (False, True)):
+        S = md.Solutions(inst, 8, 64, 64)
+        S.load(sols)
+        st = S.descend(perm, 100, use_graph=graph, time_eval=timed, poll_every=2, stream=stream)
+        runs.append((st, canon(spec, S.read()[0]), S.stats()))
+    for st, sol0, per in runs[1:]:
+        assert sol0 == runs[0][1] and np.array_equal(per, runs[0][2])
+        assert st.eval_ms > 0 and st.eval_launches >= st.steps // 8
+        assert sum(st.moves_by_op) == st.moves_scored
 
 
 # ------------------------------------------------------------------------------------------
