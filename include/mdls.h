@@ -256,6 +256,21 @@ md_status md_descend(md_solutions *sols, const md_config *cfg, md_stats *out, vo
  * steps, applied moves, passes. */
 md_status md_solutions_stats(md_solutions *sols, int64_t *per_sol, void *stream);
 
+/* Allocation-free variant of md_eval_neighborhood + md_moves_read_leaders.  The paper has no
+ * counterpart: it exists for callers that cannot call cudaMalloc (device memory budgeted up front,
+ * latency-critical loops that must not enter the allocator, code handed only raw device buffers).
+ * Evaluates operator ops_dev[s] (device int32 [n_sol]; < 0 skips the solution) for every solution
+ * with its current lambda and writes, to device buffers the caller owns, the leader id (0 when
+ * none) ids_dev [n_sol], its dF dF_dev [n_sol] and the scored-move count n_scored_dev [n_sol].
+ * No follower table and no dump.  Scratch: a static device array of 1 MiB that every GPU loading
+ * the library holds until exit; it must hold n_sol * (16 * ceil(min(n_customers / 8, 1024)) + 8)
+ * bytes, else MD_ERR_CAPACITY.  The first call on each device looks up the array's device
+ * address, so make that first call before any stream capture.  All calls share the array: calls
+ * that overlap on the GPU (other streams, other threads) race and must be serialised by the
+ * caller.  Calls no cudaMalloc or cudaFree. */
+md_status md_eval_leaders_noalloc(md_solutions *sols, const int32_t *ops_dev, uint64_t *ids_dev,
+                                  double *dF_dev, int64_t *n_scored_dev, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

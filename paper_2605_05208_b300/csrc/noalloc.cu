@@ -1,0 +1,117 @@
+// noalloc.cu -- md_eval_leaders_noalloc: neighbourhood evaluation that allocates nothing.
+//
+// Some callers cannot call cudaMalloc: a host whose device memory is budgeted up front (a later
+// allocation could fail or block behind another user of the GPU), a latency-critical loop that
+// must not enter the allocator, or code that is only handed raw device buffers by its caller.
+// For them this entry point evaluates the whole neighbourhood of one operator per solution and
+// writes each solution's leader into device buffers the caller owns.  Its scratch -- the
+// per-block leader candidates and the per-solution scored-move counters -- lives in the
+// file-scope device array below, which every GPU that loads the library holds until the process
+// exits.
+#include <mutex>
+
+#include "mdls_internal.cuh"
+
+// Upper bound of the scratch: n_sol * (evaluation blocks * 16 + 8) bytes must fit (1 MiB).
+#define MD_NOALLOC_SCRATCH_BYTES (1u << 20)
+#define MD_NOALLOC_MAX_DEVICES 64
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[MD_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+// Device address of g_noalloc_scratch, per device.  In host code the array's name is only a
+// host-side stand-in, so the address is asked for once per device and kept here.
+std::mutex g_setup_mutex;
+void *g_scratch_ptr[MD_NOALLOC_MAX_DEVICES] = {nullptr};
+
+__global__ void k_noalloc_set_ops(DevSols D, const int32_t *ops) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < D.S) D.ops[s] = ops[s];
+}
+
+// Leader per solution (one block per solution) from the per-block candidates in the scratch.
+__global__ void k_noalloc_leaders(DevSols D, const LeadRec *lpart, int nblk, const unsigned long long *nscored,
+                                  uint64_t *ids, double *fs, int64_t *n_scored) {
+    __shared__ double lf[32];
+    __shared__ uint32_t lid[32];
+    __shared__ int lv[32];
+    const int s = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    double f = 0.0;
+    uint32_t id = 0xffffffffu;
+    int valid = 0;
+    for (int k = tid; k < nblk; k += blockDim.x) {
+        const LeadRec r = lpart[(size_t)s * nblk + k];
+        if (r.valid && (!valid || r.f < f || (r.f == f && r.id < id))) { f = r.f; id = r.id; valid = 1; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const double of = __shfl_xor_sync(0xffffffffu, f, o);
+        const uint32_t oi = __shfl_xor_sync(0xffffffffu, id, o);
+        const int ov = __shfl_xor_sync(0xffffffffu, valid, o);
+        if (ov && (!valid || of < f || (of == f && oi < id))) { f = of; id = oi; valid = 1; }
+    }
+    if (lane == 0) { lf[warp] = f; lid[warp] = id; lv[warp] = valid; }
+    __syncthreads();
+    if (tid == 0) {
+        f = 0.0; id = 0xffffffffu; valid = 0;
+        for (int k = 0; k < (int)(blockDim.x + 31) / 32; k++)
+            if (lv[k] && (!valid || lf[k] < f || (lf[k] == f && lid[k] < id))) { f = lf[k]; id = lid[k]; valid = 1; }
+        ids[s] = valid ? (((uint64_t)D.ops[s] << 32) | id) : 0ull;
+        fs[s] = valid ? f : 0.0;
+        n_scored[s] = (int64_t)nscored[s];
+    }
+}
+
+}  // namespace
+
+extern "C" md_status md_eval_leaders_noalloc(md_solutions *sols, const int32_t *ops_dev, uint64_t *ids_dev,
+                                             double *dF_dev, int64_t *n_scored_dev, void *stream) {
+    if (!sols || !ops_dev || !ids_dev || !dF_dev || !n_scored_dev) {
+        md_set_error("md_eval_leaders_noalloc: null argument");
+        return MD_ERR_ARG;
+    }
+    const int nblk = md_eval_blocks(sols);
+    const size_t lbytes = (size_t)sols->n_sol * nblk * sizeof(LeadRec);
+    const size_t need = lbytes + (size_t)sols->n_sol * sizeof(unsigned long long);
+    if (need > MD_NOALLOC_SCRATCH_BYTES) {
+        md_set_error("md_eval_leaders_noalloc: %d solutions need %zu bytes of scratch; the static limit is %u bytes",
+                     sols->n_sol, need, (unsigned)MD_NOALLOC_SCRATCH_BYTES);
+        return MD_ERR_CAPACITY;
+    }
+    int dev = 0;
+    MD_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= MD_NOALLOC_MAX_DEVICES) {
+        md_set_error("md_eval_leaders_noalloc: device %d beyond the %d supported", dev, MD_NOALLOC_MAX_DEVICES);
+        return MD_ERR_ARG;
+    }
+    void *base = nullptr;
+    {
+        // the first call on a device looks up the array's device address with that device current
+        std::lock_guard<std::mutex> lock(g_setup_mutex);
+        if (!g_scratch_ptr[dev]) {
+            void *p = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess) return md_cuda_check(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+            g_scratch_ptr[dev] = p;
+        }
+        base = g_scratch_ptr[dev];
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    LeadRec *lpart = reinterpret_cast<LeadRec *>(base);
+    unsigned long long *nscored = reinterpret_cast<unsigned long long *>(static_cast<unsigned char *>(base) + lbytes);
+    // the array keeps the previous call's contents: the counters must start at zero; every leader
+    // candidate is overwritten by the evaluation itself
+    MD_CUDA(cudaMemsetAsync(nscored, 0, sizeof(unsigned long long) * sols->n_sol, st));
+    k_noalloc_set_ops<<<(sols->n_sol + 127) / 128, 128, 0, st>>>(sols->d, ops_dev);
+    MD_CUDA(cudaGetLastError());
+    md_moves view = {};
+    view.sols = sols;
+    view.d.nblk = nblk;
+    view.d.lpart = lpart;
+    view.d.nscored = nscored;
+    md_status r = md_launch_eval(sols, &view, 0u, st);
+    if (r != MD_OK) return r;
+    k_noalloc_leaders<<<sols->n_sol, 256, 0, st>>>(sols->d, lpart, nblk, nscored, ids_dev, dF_dev, n_scored_dev);
+    MD_CUDA(cudaGetLastError());
+    return MD_OK;
+}

@@ -31,7 +31,7 @@ EXPORTED = (
     "md_solution_cost", "md_solutions_lambda", "md_solutions_read_summaries", "md_moves_create",
     "md_moves_destroy", "md_eval_neighborhood", "md_moves_read_leaders", "md_moves_read_dump",
     "md_select_multimove", "md_selection_read", "md_apply_and_rebuild", "md_descend",
-    "md_solutions_stats",
+    "md_solutions_stats", "md_eval_leaders_noalloc",
 )
 
 
@@ -111,6 +111,7 @@ def lib() -> C.CDLL:
             "md_apply_and_rebuild": [P, P, C.c_uint32, P, P],
             "md_descend": [P, C.POINTER(Config), C.POINTER(Stats), P],
             "md_solutions_stats": [P, P, P],
+            "md_eval_leaders_noalloc": [P, P, P, P, P, P],
         }
         for name, args in sigs.items():
             f = getattr(L, name)
