@@ -263,7 +263,7 @@ md_status md_solutions_stats(md_solutions *sols, int64_t *per_sol, void *stream)
  * with its current lambda and writes, to device buffers the caller owns, the leader id (0 when
  * none) ids_dev [n_sol], its dF dF_dev [n_sol] and the scored-move count n_scored_dev [n_sol].
  * No follower table and no dump.  Scratch: a static device array of 1 MiB that every GPU loading
- * the library holds until exit; it must hold n_sol * (16 * ceil(min(n_customers / 8, 1024)) + 8)
+ * the library holds until exit; it must hold n_sol * (128 * min(ceil(n_customers / 8), 1024) + 8)
  * bytes, else MD_ERR_CAPACITY.  The first call on each device looks up the array's device
  * address, so make that first call before any stream capture.  All calls share the array: calls
  * that overlap on the GPU (other streams, other threads) race and must be serialised by the

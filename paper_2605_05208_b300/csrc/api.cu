@@ -82,7 +82,7 @@ extern "C" md_status md_moves_create(const md_solutions *sols, int64_t dump_capa
     m->sols = sols;
     DevMoves &d = m->d;
     const size_t S = sols->n_sol, R = sols->R;
-    d.nblk = md_eval_blocks(sols);
+    d.nblk = md_eval_partials(sols);
     d.ncap = (int)moves_ncap(sols);
     d.dump_cap = dump_capacity;
     cudaError_t e = cudaSuccess;

@@ -6,8 +6,15 @@
 // (everything that depends on u only -- its route, the route left after removing seq(u), the
 // 1- and 2-node sequences -- is computed once per warp) and its 32 lanes walk u's candidate
 // list v.  An inter-route move costs O(1): two or four concatenations of prefix/suffix
-// summaries gathered by customer id.  An intra-route move (u and v on one route) is folded
-// over the new node order, O(route length).
+// summaries gathered by customer id.  An intra-route move (u and v on one route) takes the
+// prefix before and the suffix after the rearranged part from the same summaries and folds only
+// the customers strictly between u's and v's sequences.
+//
+// The FP64 penalised delta dF is needed only for the leader (Section 3.2.5): a move whose
+// integer deltas make dF >= 0 certain, or whose FP32 estimate (with a margin ten times its
+// rounding bound) is above the lane's best dF so far, cannot be the leader and skips FP64.  B300
+// runs FP64 at a small fraction of its integer rate.  Every warp writes its own leader
+// candidate, so no warp waits for the others of its block.
 #include "mdls_internal.cuh"
 
 namespace {
@@ -30,6 +37,7 @@ struct Ctx {
     uint32_t flags;
     int s;
     double w[4];
+    float wf[4];
     bool open, sym;
 };
 
@@ -85,15 +93,35 @@ __device__ __forceinline__ Seg join_opt(const Ctx &C, const Seg &a, int a_last, 
     return join<TW>(C, a, a_last, suffix_from(C, tail_first), tail_first);
 }
 
-__device__ __forceinline__ void sink(const Ctx &C, uint32_t id, int dD, int dTW, int dL, int dU, int dV,
-                                     int rA, int rB, Best &b, bool count = true) {
+// Records one scored move: follower table, leader candidate of the lane, dump.  f_in is the FP64
+// dF when the caller already has it (have_f), otherwise it is computed here only if needed.
+__device__ __forceinline__ void offer(const Ctx &C, uint32_t id, int dD, int dTW, int dL, int dU, int dV,
+                                      int rA, int rB, Best &b, bool count, bool have_f, double f_in) {
     if (count) b.n++;
-    if ((C.flags & MD_EVAL_FOLLOWERS) && dD < 0 && (dTW | dL | dU | dV) == 0) {
+    const bool pen = (dTW | dL | dU | dV) != 0;
+    if ((C.flags & MD_EVAL_FOLLOWERS) && dD < 0 && !pen) {
         const int lo = min(rA, rB), hi = max(rA, rB);
         const unsigned long long key = ((unsigned long long)((uint32_t)dD ^ 0x80000000u) << 32) | id;
         atomicMin(&C.M.foltab[((size_t)C.s * C.D.R + lo) * C.D.R + hi], key);
     }
-    const double f = combine_df(C.w, dD, dTW, dL, dU, dV);
+    double f;
+    if (have_f) {
+        f = f_in;
+    } else if (C.flags & MD_EVAL_DUMP) {
+        f = combine_df(C.w, dD, dTW, dL, dU, dV);
+    } else if (!pen) {
+        if (dD >= 0) return;
+        f = (double)dD;
+    } else {
+        if (dD >= 0 && dTW >= 0 && dL >= 0 && dU >= 0 && dV >= 0) return;  // dF >= 0: never a leader
+        const float est = __fmaf_rn(C.wf[3], (float)dV, __fmaf_rn(C.wf[2], (float)dU,
+                          __fmaf_rn(C.wf[1], (float)dL, __fmaf_rn(C.wf[0], (float)dTW, (float)dD))));
+        const float mag = fabsf((float)dD) + C.wf[0] * fabsf((float)dTW) + C.wf[1] * fabsf((float)dL) +
+                          C.wf[2] * fabsf((float)dU) + C.wf[3] * fabsf((float)dV);
+        const float bound = b.valid ? __double2float_ru(b.f) : 0.0f;
+        if (est - 4e-6f * mag > bound) return;  // dF > bound for certain
+        f = combine_df(C.w, dD, dTW, dL, dU, dV);
+    }
     if (f < 0.0 && (!b.valid || f < b.f || (f == b.f && id < b.id))) {
         b.f = f;
         b.id = id;
@@ -113,31 +141,54 @@ __device__ __forceinline__ void sink(const Ctx &C, uint32_t id, int dD, int dTW,
     }
 }
 
-// Route terms of the node order given by up to five position ranges of route slot r
-// (position 0 = ds, 1..L = customers, L+1 = de); a range with rev set is walked backwards.
-template <bool TW>
-__device__ RT fold_pieces(const Ctx &C, int r, int L, int ds, int de, const int *lo, const int *hi,
-                          const bool *rev, int np) {
-    const int32_t *rn = C.D.rnodes + ((size_t)C.s * C.D.R + r) * C.D.K;
-    Seg acc;
-    int last = -1;
-    bool started = false;
-    for (int q = 0; q < np; q++) {
-        for (int t = 0; t <= hi[q] - lo[q]; t++) {
-            const int k = rev[q] ? hi[q] - t : lo[q] + t;
-            const int n = k == 0 ? ds : (k == L + 1 ? de : rn[k - 1]);
-            const Seg ns = nseg(C, n);
-            if (!started) { acc = ns; started = true; }
-            else acc = seg_cat<TW>(acc, ns, cost(C.I, last, n));
-            last = n;
-        }
-    }
-    return rt_of(acc, C.I);
+__device__ __forceinline__ void sink(const Ctx &C, uint32_t id, int dD, int dTW, int dL, int dU, int dV,
+                                     int rA, int rB, Best &b) {
+    offer(C, id, dD, dTW, dL, dU, dV, rA, rB, b, true, false, 0.0);
 }
 
-__device__ __forceinline__ void put(int *lo, int *hi, bool *rev, int &np, int a, int b, bool rv) {
-    if (a > b) return;
-    lo[np] = a; hi[np] = b; rev[np] = rv; np++;
+// A summary with its end nodes; e marks the empty sequence.
+struct SN {
+    Seg s;
+    int f, l;
+    bool e;
+};
+
+__device__ __forceinline__ SN sn(const Seg &g, int f, int l) {
+    SN r;
+    r.s = g; r.f = f; r.l = l; r.e = false;
+    return r;
+}
+
+__device__ __forceinline__ SN sn_none() {
+    SN r;
+    r.s = Seg{0, 0, 0, 0, 0, MD_NO_LATE};
+    r.f = -1; r.l = -1; r.e = true;
+    return r;
+}
+
+template <bool TW>
+__device__ __forceinline__ SN sn_cat(const Ctx &C, const SN &a, const SN &b) {
+    if (a.e) return b;
+    if (b.e) return a;
+    return sn(seg_cat<TW>(a.s, b.s, cost(C.I, a.l, b.f)), a.f, b.l);
+}
+
+// Summary of the route from node n to its end as an SN (empty after an open route's last customer).
+__device__ __forceinline__ SN sn_suffix(const Ctx &C, int n) {
+    return n == MD_NONE ? sn_none() : sn(suffix_from(C, n), n, n);
+}
+
+// Customers at positions lo..hi (1-based, lo <= hi) of route row rn, folded left to right.
+template <bool TW>
+__device__ SN fold_mid(const Ctx &C, const int32_t *rn, int lo, int hi) {
+    int n = rn[lo - 1];
+    SN r = sn(nseg(C, n), n, n);
+    for (int k = lo + 1; k <= hi; k++) {
+        const int m = rn[k - 1];
+        r.s = seg_cat<TW>(r.s, nseg(C, m), cost(C.I, r.l, m));
+        r.l = m;
+    }
+    return r;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -158,10 +209,10 @@ __device__ void eval_relocate(const Ctx &C, int cu, int lane, Best &b) {
     const RT A1 = LA == 1 ? rt_zero() : rt_of(join_opt<TW>(C, PP, pu, su), I);
     const bool has2 = su >= I.nd;
     const int x = has2 ? su : -1;
+    const int sx = has2 ? suf8(C, x).b : MD_NONE;
     RT A2 = rt_zero();
     Seg q2, q2r;
     if (has2) {
-        const int sx = suf8(C, x).b;
         if (LA > 2) A2 = rt_of(join_opt<TW>(C, PP, pu, sx), I);
         q2 = join<TW>(C, nseg(C, u), u, nseg(C, x), x);
         q2r = join<TW>(C, nseg(C, x), x, nseg(C, u), u);
@@ -176,8 +227,8 @@ __device__ void eval_relocate(const Ctx &C, int cu, int lane, Best &b) {
         const Seg8 Pv = pre8(C, v), Sv = suf8(C, v);
         const int B = Pv.a, j = Pv.b, sv = Sv.b;
         if (B == A) {
-            // intra-route: fold the new node order
-            const int end = C.open ? LA : LA + 1;
+            // intra-route: prefix before and suffix after the rearranged part, middle folded
+            const int32_t *rn = C.D.rnodes + sA * C.D.K;
             for (int var = 0; var < 6; var++) {
                 const int k = var >= 2 ? 2 : 1;
                 const bool rev = var >= 4, before = var & 1;
@@ -186,21 +237,18 @@ __device__ void eval_relocate(const Ctx &C, int cu, int lane, Best &b) {
                 if (k == 2 && v == x) continue;
                 if (before && j != 1) continue;
                 if (!before && !rev && j == p - 1) continue;  // already right after v
-                int lo[5], hi[5], np = 0;
-                bool rv[5];
-                const int at = before ? 0 : j;  // insert after this position
+                const int at = before ? 0 : j;  // seq(u) goes right after this position
+                const SN q = k == 1 ? sn(q1, u, u) : (rev ? sn(q2r, x, u) : sn(q2, u, x));
+                SN g;
                 if (at < p) {
-                    put(lo, hi, rv, np, 0, at, false);
-                    put(lo, hi, rv, np, p, p + k - 1, rev);
-                    put(lo, hi, rv, np, at + 1, p - 1, false);
-                    put(lo, hi, rv, np, p + k, end, false);
+                    const SN head = at == 0 ? sn(nseg(C, dsA), dsA, dsA) : sn(seg_of(Pv), dsA, v);
+                    const SN mid = at + 1 <= p - 1 ? fold_mid<TW>(C, rn, at + 1, p - 1) : sn_none();
+                    g = sn_cat<TW>(C, sn_cat<TW>(C, sn_cat<TW>(C, head, q), mid), sn_suffix(C, k == 1 ? su : sx));
                 } else {
-                    put(lo, hi, rv, np, 0, p - 1, false);
-                    put(lo, hi, rv, np, p + k, at, false);
-                    put(lo, hi, rv, np, p, p + k - 1, rev);
-                    put(lo, hi, rv, np, at + 1, end, false);
+                    const SN mid = fold_mid<TW>(C, rn, p + k, at);
+                    g = sn_cat<TW>(C, sn_cat<TW>(C, sn_cat<TW>(C, sn(PP, dsA, pu), mid), q), sn_suffix(C, sv));
                 }
-                const RT nA = fold_pieces<TW>(C, A, LA, dsA, deA, lo, hi, rv, np);
+                const RT nA = rt_of(g.s, I);
                 sink(C, make_id32(u, v, var), nA.dist - oldA.dist, nA.tw - oldA.tw, nA.lex - oldA.lex,
                      nA.dex - oldA.dex, 0, A, A, b);
             }
@@ -254,7 +302,7 @@ __device__ void eval_swap(const Ctx &C, int cu, int lane, Best &b) {
     const int A = Pu.a, p = Pu.b, pu = Su.a, su = Su.b;
     const size_t sA = (size_t)C.s * C.D.R + A;
     const int4 hA = C.D.rhdr[sA];
-    const int LA = hA.x, dsA = hA.y, deA = hA.z;
+    const int dsA = hA.y;
     const RT oldA = rt_of(seg_of(ldg_seg8(&C.D.rterm[sA])), I);
     const Seg PU = prefix_through(C, pu);
     const bool hasx = su >= I.nd;
@@ -274,29 +322,33 @@ __device__ void eval_swap(const Ctx &C, int cu, int lane, Best &b) {
         const int B = Pv.a, j = Pv.b, pv = Sv.a, sv = Sv.b;
         const bool hasy = sv >= I.nd;
         const int y = hasy ? sv : -1;
+        const int sy = hasy ? suf8(C, y).b : MD_NONE;
+        Seg v1 = nseg(C, v), v2, v2r;
+        if (hasy) {
+            v2 = join<TW>(C, nseg(C, v), v, nseg(C, y), y);
+            v2r = join<TW>(C, nseg(C, y), y, nseg(C, v), v);
+        }
         if (B == A) {
-            const int end = C.open ? LA : LA + 1;
+            // intra-route: prefix, one sequence, the customers between them, the other sequence, suffix
+            const int32_t *rn = C.D.rnodes + sA * C.D.K;
             for (int var = 0; var < nvar; var++) {
                 const int ku = SW_KU[var], kv = SW_KV[var];
                 const bool ru = SW_RU[var], rvv = SW_RV[var];
                 if ((ku == 2 && !hasx) || (kv == 2 && !hasy)) continue;
                 if (!(p + ku - 1 < j || j + kv - 1 < p)) continue;  // overlapping sequences
-                int lo[5], hi[5], np = 0;
-                bool rv[5];
+                const SN qv = kv == 1 ? sn(v1, v, v) : (rvv ? sn(v2r, y, v) : sn(v2, v, y));
+                const SN qu = ku == 1 ? sn(u1, u, u) : (ru ? sn(u2r, x, u) : sn(u2, u, x));
+                SN g;
                 if (p < j) {
-                    put(lo, hi, rv, np, 0, p - 1, false);
-                    put(lo, hi, rv, np, j, j + kv - 1, rvv);
-                    put(lo, hi, rv, np, p + ku, j - 1, false);
-                    put(lo, hi, rv, np, p, p + ku - 1, ru);
-                    put(lo, hi, rv, np, j + kv, end, false);
+                    const SN mid = p + ku <= j - 1 ? fold_mid<TW>(C, rn, p + ku, j - 1) : sn_none();
+                    g = sn_cat<TW>(C, sn(PU, dsA, pu), qv);
+                    g = sn_cat<TW>(C, sn_cat<TW>(C, sn_cat<TW>(C, g, mid), qu), sn_suffix(C, kv == 1 ? sv : sy));
                 } else {
-                    put(lo, hi, rv, np, 0, j - 1, false);
-                    put(lo, hi, rv, np, p, p + ku - 1, ru);
-                    put(lo, hi, rv, np, j + kv, p - 1, false);
-                    put(lo, hi, rv, np, j, j + kv - 1, rvv);
-                    put(lo, hi, rv, np, p + ku, end, false);
+                    const SN mid = j + kv <= p - 1 ? fold_mid<TW>(C, rn, j + kv, p - 1) : sn_none();
+                    g = sn_cat<TW>(C, sn(prefix_through(C, pv), dsA, pv), qu);
+                    g = sn_cat<TW>(C, sn_cat<TW>(C, sn_cat<TW>(C, g, mid), qv), sn_suffix(C, ku == 1 ? su : sx));
                 }
-                const RT nA = fold_pieces<TW>(C, A, LA, dsA, deA, lo, hi, rv, np);
+                const RT nA = rt_of(g.s, I);
                 sink(C, make_id32(u, v, var), nA.dist - oldA.dist, nA.tw - oldA.tw, nA.lex - oldA.lex,
                      nA.dex - oldA.dex, 0, A, A, b);
             }
@@ -305,12 +357,6 @@ __device__ void eval_swap(const Ctx &C, int cu, int lane, Best &b) {
         const size_t sB = (size_t)C.s * C.D.R + B;
         const RT oldB = rt_of(seg_of(ldg_seg8(&C.D.rterm[sB])), I);
         const Seg PV = prefix_through(C, pv);
-        const int sy = hasy ? suf8(C, y).b : MD_NONE;
-        Seg v1 = nseg(C, v), v2, v2r;
-        if (hasy) {
-            v2 = join<TW>(C, nseg(C, v), v, nseg(C, y), y);
-            v2r = join<TW>(C, nseg(C, y), y, nseg(C, v), v);
-        }
         for (int var = 0; var < nvar; var++) {
             const int ku = SW_KU[var], kv = SW_KV[var];
             const bool ru = SW_RU[var], rvv = SW_RV[var];
@@ -452,22 +498,21 @@ __device__ void eval_depot_replace(const Ctx &C, int cu, int lane, Best &b) {
                 bf = f; bcase = cs; bD = dD; bT = dT; bL = dL; bU = dU; bV = dV;
             }
         }
-        if (bcase >= 0) sink(C, make_id32(u, d, bcase), bD, bT, bL, bU, bV, A, A, b, false);
+        if (bcase >= 0) offer(C, make_id32(u, d, bcase), bD, bT, bL, bU, bV, A, A, b, false, true, bf);
     }
 }
 
 template <bool TW>
-__global__ void __launch_bounds__(256) k_eval(DevInst I, DevSols D, DevMoves M, uint32_t flags) {
-    __shared__ double red_f[8];
-    __shared__ uint32_t red_id[8];
-    __shared__ int red_v[8];
-    __shared__ unsigned long long red_n[8];
+__global__ void __launch_bounds__(256, 2) k_eval(DevInst I, DevSols D, DevMoves M, uint32_t flags) {
     Ctx C;
     C.I = I; C.D = D; C.M = M; C.flags = flags;
     C.s = blockIdx.y;
     C.open = (I.variant & MD_VARIANT_OPEN) != 0;
     C.sym = (I.variant & MD_VARIANT_SYMMETRIC) != 0;
-    for (int k = 0; k < 4; k++) C.w[k] = D.w[4 * C.s + k];
+    for (int k = 0; k < 4; k++) {
+        C.w[k] = D.w[4 * C.s + k];
+        C.wf[k] = (float)C.w[k];
+    }
     const int op = D.ops[C.s];
     Best b;
     b.f = 0.0; b.id = 0xffffffffu; b.valid = 0; b.n = 0;
@@ -484,7 +529,7 @@ __global__ void __launch_bounds__(256) k_eval(DevInst I, DevSols D, DevMoves M, 
             }
         }
     }
-    // block reduction of the leader candidate and of the scored count
+    // warp reduction of the leader candidate and of the scored count; one record per warp
     for (int o = 16; o > 0; o >>= 1) {
         const double of = __shfl_xor_sync(0xffffffffu, b.f, o);
         const uint32_t oi = __shfl_xor_sync(0xffffffffu, b.id, o);
@@ -492,20 +537,11 @@ __global__ void __launch_bounds__(256) k_eval(DevInst I, DevSols D, DevMoves M, 
         b.n += __shfl_xor_sync(0xffffffffu, b.n, o);
         if (ov && (!b.valid || of < b.f || (of == b.f && oi < b.id))) { b.f = of; b.id = oi; b.valid = 1; }
     }
-    if (lane == 0) { red_f[warp] = b.f; red_id[warp] = b.id; red_v[warp] = b.valid; red_n[warp] = b.n; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
+    if (lane == 0) {
         LeadRec r;
-        r.f = 0.0; r.id = 0xffffffffu; r.valid = 0;
-        unsigned long long n = 0;
-        for (int k = 0; k < wpb; k++) {
-            n += red_n[k];
-            if (red_v[k] && (!r.valid || red_f[k] < r.f || (red_f[k] == r.f && red_id[k] < r.id))) {
-                r.f = red_f[k]; r.id = red_id[k]; r.valid = 1;
-            }
-        }
-        M.lpart[(size_t)C.s * M.nblk + blockIdx.x] = r;
-        if (n) atomicAdd(&M.nscored[C.s], n);
+        r.f = b.f; r.id = b.id; r.valid = b.valid;
+        M.lpart[(size_t)C.s * M.nblk + (size_t)blockIdx.x * wpb + warp] = r;
+        if (b.n) atomicAdd(&M.nscored[C.s], b.n);
     }
 }
 
@@ -513,15 +549,17 @@ __global__ void __launch_bounds__(256) k_eval(DevInst I, DevSols D, DevMoves M, 
 
 int md_eval_blocks(const md_solutions *s) {
     int nc = s->inst->d.nc;
-    int b = (nc + 7) / 8;
+    int b = (nc + MD_EVAL_WARPS - 1) / MD_EVAL_WARPS;
     return b < 1024 ? b : 1024;
 }
 
+int md_eval_partials(const md_solutions *s) { return md_eval_blocks(s) * MD_EVAL_WARPS; }
+
 md_status md_launch_eval(md_solutions *s, md_moves *m, uint32_t flags, cudaStream_t st) {
     const DevInst &I = s->inst->d;
-    dim3 grid(m->d.nblk, s->n_sol);
-    if (I.variant & MD_VARIANT_TW) k_eval<true><<<grid, 256, 0, st>>>(I, s->d, m->d, flags);
-    else k_eval<false><<<grid, 256, 0, st>>>(I, s->d, m->d, flags);
+    dim3 grid(m->d.nblk / MD_EVAL_WARPS, s->n_sol);
+    if (I.variant & MD_VARIANT_TW) k_eval<true><<<grid, 32 * MD_EVAL_WARPS, 0, st>>>(I, s->d, m->d, flags);
+    else k_eval<false><<<grid, 32 * MD_EVAL_WARPS, 0, st>>>(I, s->d, m->d, flags);
     MD_CUDA(cudaGetLastError());
     return MD_OK;
 }

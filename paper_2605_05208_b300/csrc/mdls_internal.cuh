@@ -26,6 +26,7 @@
 #define MD_NONE (-1)
 #define MD_MAX_OPS 8
 #define MD_EMPTY_KEY 0xFFFFFFFFFFFFFFFFull
+#define MD_EVAL_WARPS 8  // warps per evaluation block; one leader record per warp
 
 struct __align__(16) Seg8 {
     int dist, load, dur, tw, E, L, a, b;
@@ -76,7 +77,7 @@ struct __align__(16) LeadRec {
 };
 
 struct DevMoves {
-    int nblk;              // leader partials per solution
+    int nblk;              // leader records per solution (evaluation blocks x MD_EVAL_WARPS)
     LeadRec *lpart;        // [S * nblk]
     unsigned long long *nscored;   // [S]
     unsigned long long *foltab;    // [S * R * R] best follower key per route pair (i <= j used)
@@ -223,3 +224,4 @@ md_status md_launch_select(md_solutions *s, md_moves *m, int multi, cudaStream_t
 md_status md_launch_apply(md_solutions *s, md_moves *m, int update_lambda, cudaStream_t st);
 md_status md_launch_step(md_solutions *s, md_moves *m, cudaStream_t st);
 int md_eval_blocks(const md_solutions *s);
+int md_eval_partials(const md_solutions *s);

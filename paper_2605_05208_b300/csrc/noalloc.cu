@@ -5,14 +5,15 @@
 // must not enter the allocator, or code that is only handed raw device buffers by its caller.
 // For them this entry point evaluates the whole neighbourhood of one operator per solution and
 // writes each solution's leader into device buffers the caller owns.  Its scratch -- the
-// per-block leader candidates and the per-solution scored-move counters -- lives in the
+// per-warp leader candidates and the per-solution scored-move counters -- lives in the
 // file-scope device array below, which every GPU that loads the library holds until the process
 // exits.
 #include <mutex>
 
 #include "mdls_internal.cuh"
 
-// Upper bound of the scratch: n_sol * (evaluation blocks * 16 + 8) bytes must fit (1 MiB).
+// Upper bound of the scratch: n_sol * (leader records * 16 + 8) bytes must fit (1 MiB), with one
+// leader record per evaluation warp.
 #define MD_NOALLOC_SCRATCH_BYTES (1u << 20)
 #define MD_NOALLOC_MAX_DEVICES 64
 
@@ -70,7 +71,7 @@ extern "C" md_status md_eval_leaders_noalloc(md_solutions *sols, const int32_t *
         md_set_error("md_eval_leaders_noalloc: null argument");
         return MD_ERR_ARG;
     }
-    const int nblk = md_eval_blocks(sols);
+    const int nblk = md_eval_partials(sols);
     const size_t lbytes = (size_t)sols->n_sol * nblk * sizeof(LeadRec);
     const size_t need = lbytes + (size_t)sols->n_sol * sizeof(unsigned long long);
     if (need > MD_NOALLOC_SCRATCH_BYTES) {
