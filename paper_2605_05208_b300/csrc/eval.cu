@@ -28,6 +28,7 @@ struct Best {
     uint32_t id;
     int valid;
     unsigned long long n;
+    float fb;  // f rounded towards +inf (0 while there is no candidate): the pruning bound
 };
 
 struct Ctx {
@@ -111,6 +112,7 @@ __device__ __forceinline__ void offer(const Ctx &C, uint32_t id, int dD, int dTW
         f = combine_df(C.w, dD, dTW, dL, dU, dV);
     } else if (!pen) {
         if (dD >= 0) return;
+        if (__int2float_rd(dD) > b.fb) return;  // dF = dD > best for certain
         f = (double)dD;
     } else {
         if (dD >= 0 && dTW >= 0 && dL >= 0 && dU >= 0 && dV >= 0) return;  // dF >= 0: never a leader
@@ -118,14 +120,14 @@ __device__ __forceinline__ void offer(const Ctx &C, uint32_t id, int dD, int dTW
                           __fmaf_rn(C.wf[1], (float)dL, __fmaf_rn(C.wf[0], (float)dTW, (float)dD))));
         const float mag = fabsf((float)dD) + C.wf[0] * fabsf((float)dTW) + C.wf[1] * fabsf((float)dL) +
                           C.wf[2] * fabsf((float)dU) + C.wf[3] * fabsf((float)dV);
-        const float bound = b.valid ? __double2float_ru(b.f) : 0.0f;
-        if (est - 4e-6f * mag > bound) return;  // dF > bound for certain
+        if (est - 4e-6f * mag > b.fb) return;  // dF > best for certain
         f = combine_df(C.w, dD, dTW, dL, dU, dV);
     }
     if (f < 0.0 && (!b.valid || f < b.f || (f == b.f && id < b.id))) {
         b.f = f;
         b.id = id;
         b.valid = 1;
+        b.fb = __double2float_ru(f);
     }
     if (C.flags & MD_EVAL_DUMP) {
         const unsigned long long k = atomicAdd(C.M.dump_n, 1ull);
@@ -515,7 +517,7 @@ __global__ void __launch_bounds__(256, 2) k_eval(DevInst I, DevSols D, DevMoves 
     }
     const int op = D.ops[C.s];
     Best b;
-    b.f = 0.0; b.id = 0xffffffffu; b.valid = 0; b.n = 0;
+    b.f = 0.0; b.id = 0xffffffffu; b.valid = 0; b.n = 0; b.fb = 0.0f;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
     if (op >= 0) {
         for (int cu = blockIdx.x * wpb + warp; cu < I.nc; cu += gridDim.x * wpb) {
