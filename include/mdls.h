@@ -125,6 +125,8 @@ typedef struct md_config {
     int32_t poll_every;     /* passes between host checks of the per-solution done flags */
     int32_t op_perm_device; /* 1: op_perm points to device memory (no host copy per call) */
     int32_t time_eval;      /* 1: time every evaluation launch with CUDA events (md_stats.eval_ms) */
+    int32_t n_groups;       /* > 1: solutions advance in this many groups on concurrent streams
+                               (needs a non-NULL stream); results do not depend on it */
 } md_config;
 
 /* Totals over all solutions of one md_descend call. */

@@ -71,6 +71,7 @@ static void free_moves(md_moves *m) {
     DevMoves &d = m->d;
     cudaFree(d.lpart); cudaFree(d.nscored); cudaFree(d.foltab); cudaFree(d.cand_key);
     cudaFree(d.cand_rt); cudaFree(d.sel); cudaFree(d.nsel); cudaFree(d.dump); cudaFree(d.dump_n);
+    cudaFree(d.flist); cudaFree(d.fcount);
     free(m);
 }
 
@@ -92,6 +93,9 @@ extern "C" md_status md_moves_create(const md_solutions *sols, int64_t dump_capa
     MDM(cudaMalloc(&d.foltab, sizeof(unsigned long long) * S * R * R));
     MDM(cudaMalloc(&d.cand_key, sizeof(unsigned long long) * S * d.ncap));
     MDM(cudaMalloc(&d.cand_rt, sizeof(uint32_t) * S * d.ncap));
+    MDM(cudaMalloc(&d.flist, sizeof(uint32_t) * S * d.ncap));
+    MDM(cudaMalloc(&d.fcount, sizeof(uint32_t) * S));
+    MDM(cudaMemset(d.fcount, 0, sizeof(uint32_t) * S));
     MDM(cudaMalloc(&d.sel, sizeof(uint32_t) * S * R));
     MDM(cudaMalloc(&d.nsel, sizeof(int32_t) * S));
     MDM(cudaMalloc(&d.dump_n, sizeof(unsigned long long)));
@@ -139,8 +143,14 @@ extern "C" md_status md_eval_neighborhood(md_solutions *s, const int32_t *ops, c
     if (r != MD_OK) return r;
     MD_CUDA(cudaMemsetAsync(m->d.nscored, 0, sizeof(unsigned long long) * s->n_sol, st));
     MD_CUDA(cudaMemsetAsync(m->d.dump_n, 0, sizeof(unsigned long long), st));
+    if (m->pending) {  // a follower table no selection consumed: start from an empty one
+        MD_CUDA(cudaMemsetAsync(m->d.foltab, 0xff, sizeof(unsigned long long) * s->n_sol * s->R * s->R, st));
+        MD_CUDA(cudaMemsetAsync(m->d.fcount, 0, sizeof(uint32_t) * s->n_sol, st));
+        m->pending = 0;
+    }
     r = md_launch_eval(s, m, flags, st);
     if (r != MD_OK) return r;
+    m->pending = (flags & MD_EVAL_FOLLOWERS) ? 1 : 0;
     m->last_flags = (int)flags;
     m->evaluated = 1;
     m->selected = 0;
@@ -207,6 +217,7 @@ extern "C" md_status md_select_multimove(md_solutions *s, md_moves *m, int32_t m
     md_status r = md_launch_select(s, m, multi_move ? 1 : 0, (cudaStream_t)stream);
     if (r != MD_OK) return r;
     m->selected = 1;
+    m->pending = 0;  // the selection clears every listed table entry
     return MD_OK;
 }
 
@@ -291,6 +302,7 @@ extern "C" md_status md_descend(md_solutions *s, const md_config *cfg, md_stats 
     if (r != MD_OK) return r;
     launches++;
     MD_CUDA(cudaMemsetAsync(m->d.foltab, 0xff, sizeof(unsigned long long) * s->n_sol * s->R * s->R, st));
+    MD_CUDA(cudaMemsetAsync(m->d.fcount, 0, sizeof(uint32_t) * s->n_sol, st));
     MD_CUDA(cudaMemsetAsync(m->d.nscored, 0, sizeof(unsigned long long) * s->n_sol, st));
     k_descend_init<<<(s->n_sol + 127) / 128, 128, 0, st>>>(s->d, cfg->n_ops, cfg->max_pass, cfg->multi_move ? 1 : 0,
                                                          cfg->lambda_update ? 1 : 0);
@@ -299,24 +311,69 @@ extern "C" md_status md_descend(md_solutions *s, const md_config *cfg, md_stats 
     const uint32_t eflags = cfg->multi_move ? MD_EVAL_FOLLOWERS : 0u;
     const int poll = cfg->poll_every > 0 ? cfg->poll_every : 1;
     const int steps_per_poll = cfg->n_ops * poll;
+    // Solutions are independent: with n_groups > 1 they advance in groups on concurrent streams
+    // (forked from and joined back to `stream`), so one group's selection/apply kernel overlaps
+    // the evaluation of another.
+    int G = cfg->n_groups > 1 ? cfg->n_groups : 1;
+    if (G > s->n_sol) G = s->n_sol;
+    if (st == nullptr) G = 1;
+    std::vector<cudaStream_t> side(G, st);
+    std::vector<cudaEvent_t> joins;
+    cudaEvent_t fork = nullptr;
     std::vector<cudaEvent_t> ev;
-    if (cfg->time_eval) {
-        ev.resize(2 * (size_t)steps_per_poll);
-        for (auto &e : ev) MD_CUDA(cudaEventCreate(&e));
+    auto release = [&]() {
+        for (auto &e : ev) if (e) cudaEventDestroy(e);
+        ev.clear();
+        for (auto &e : joins) if (e) cudaEventDestroy(e);
+        joins.clear();
+        if (fork) cudaEventDestroy(fork);
+        fork = nullptr;
+        for (int g = 1; g < (int)side.size(); g++) if (side[g] != st) cudaStreamDestroy(side[g]);
+        side.assign(1, st);
+    };
+    if (G > 1) {
+        MD_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+        joins.resize(G, nullptr);
+        for (int g = 1; g < G; g++) {
+            cudaError_t ce = cudaStreamCreateWithFlags(&side[g], cudaStreamNonBlocking);
+            if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&joins[g], cudaEventDisableTiming);
+            if (ce != cudaSuccess) { release(); return md_cuda_check(ce, "md_descend streams"); }
+        }
     }
-    auto release = [&]() { for (auto &e : ev) cudaEventDestroy(e); ev.clear(); };
-    // one pass chunk: (evaluate, select + apply + advance) per step, optionally bracketed by
-    // events; inside a stream capture an event only becomes a record node (and so gets a
-    // timestamp at every replay) when it is recorded as external
+    if (cfg->time_eval) {
+        ev.assign(2 * (size_t)steps_per_poll * G, nullptr);
+        for (auto &e : ev) {
+            cudaError_t ce = cudaEventCreate(&e);
+            if (ce != cudaSuccess) { release(); return md_cuda_check(ce, "md_descend events"); }
+        }
+    }
+    // one pass chunk per group: (evaluate, select + apply + advance) per step, optionally
+    // bracketed by events; inside a stream capture an event only becomes a record node (and so
+    // gets a timestamp at every replay) when it is recorded as external
     auto enqueue = [&](bool capturing) -> md_status {
         const unsigned int rf = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
+        if (G > 1) {
+            MD_CUDA(cudaEventRecord(fork, st));
+            for (int g = 1; g < G; g++) MD_CUDA(cudaStreamWaitEvent(side[g], fork, 0));
+        }
         for (int k = 0; k < steps_per_poll; k++) {
-            if (!ev.empty()) MD_CUDA(cudaEventRecordWithFlags(ev[2 * k], st, rf));
-            md_status q = md_launch_eval(s, m, eflags, st);
-            if (q != MD_OK) return q;
-            if (!ev.empty()) MD_CUDA(cudaEventRecordWithFlags(ev[2 * k + 1], st, rf));
-            q = md_launch_step(s, m, st);
-            if (q != MD_OK) return q;
+            for (int g = 0; g < G; g++) {
+                const int a = (int)((long long)s->n_sol * g / G), b = (int)((long long)s->n_sol * (g + 1) / G);
+                cudaStream_t sg = side[g];
+                cudaEvent_t *e = ev.empty() ? nullptr : &ev[2 * ((size_t)k * G + g)];
+                if (e) MD_CUDA(cudaEventRecordWithFlags(e[0], sg, rf));
+                md_status q = md_launch_eval(s, m, eflags, sg, a, b - a);
+                if (q != MD_OK) return q;
+                if (e) MD_CUDA(cudaEventRecordWithFlags(e[1], sg, rf));
+                q = md_launch_step(s, m, sg, a, b - a);
+                if (q != MD_OK) return q;
+            }
+        }
+        if (G > 1) {
+            for (int g = 1; g < G; g++) {
+                MD_CUDA(cudaEventRecord(joins[g], side[g]));
+                MD_CUDA(cudaStreamWaitEvent(st, joins[g], 0));
+            }
         }
         return MD_OK;
     };
@@ -345,13 +402,13 @@ extern "C" md_status md_descend(md_solutions *s, const md_config *cfg, md_stats 
             rr = enqueue(false);
             if (rr != MD_OK) break;
         }
-        launches += 2LL * steps_per_poll;
-        eval_launches += steps_per_poll;
+        launches += 2LL * steps_per_poll * G;
+        eval_launches += (long long)steps_per_poll * G;
         passes_done += poll;
         cudaError_t ce = cudaMemcpyAsync(state.data(), s->d.state, sizeof(int32_t) * 8 * s->n_sol, cudaMemcpyDeviceToHost, st);
         if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
         if (ce != cudaSuccess) { rr = md_cuda_check(ce, "md_descend poll"); break; }
-        for (int k = 0; k < steps_per_poll && !ev.empty(); k++) {
+        for (size_t k = 0; k < ev.size() / 2; k++) {
             float ms = 0.0f;
             ce = cudaEventElapsedTime(&ms, ev[2 * k], ev[2 * k + 1]);
             if (ce != cudaSuccess) break;

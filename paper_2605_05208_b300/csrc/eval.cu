@@ -103,7 +103,13 @@ __device__ __forceinline__ void offer(const Ctx &C, uint32_t id, int dD, int dTW
     if ((C.flags & MD_EVAL_FOLLOWERS) && dD < 0 && !pen) {
         const int lo = min(rA, rB), hi = max(rA, rB);
         const unsigned long long key = ((unsigned long long)((uint32_t)dD ^ 0x80000000u) << 32) | id;
-        atomicMin(&C.M.foltab[((size_t)C.s * C.D.R + lo) * C.D.R + hi], key);
+        const uint32_t pair = (uint32_t)lo * (uint32_t)C.D.R + (uint32_t)hi;
+        const unsigned long long old = atomicMin(&C.M.foltab[(size_t)C.s * C.D.R * C.D.R + pair], key);
+        if (old == MD_EMPTY_KEY) {  // first follower of this route pair: list the pair once
+            const uint32_t k = atomicAdd(&C.M.fcount[C.s], 1u);
+            if (k < (uint32_t)C.M.ncap) C.M.flist[(size_t)C.s * C.M.ncap + k] = pair;
+            else atomicCAS(C.D.err, 0, (int)MD_ERR_CAPACITY);
+        }
     }
     double f;
     if (have_f) {
@@ -505,10 +511,10 @@ __device__ void eval_depot_replace(const Ctx &C, int cu, int lane, Best &b) {
 }
 
 template <bool TW>
-__global__ void __launch_bounds__(256, 2) k_eval(DevInst I, DevSols D, DevMoves M, uint32_t flags) {
+__global__ void __launch_bounds__(256, 2) k_eval(DevInst I, DevSols D, DevMoves M, uint32_t flags, int s0) {
     Ctx C;
     C.I = I; C.D = D; C.M = M; C.flags = flags;
-    C.s = blockIdx.y;
+    C.s = s0 + blockIdx.y;
     C.open = (I.variant & MD_VARIANT_OPEN) != 0;
     C.sym = (I.variant & MD_VARIANT_SYMMETRIC) != 0;
     for (int k = 0; k < 4; k++) {
@@ -557,11 +563,13 @@ int md_eval_blocks(const md_solutions *s) {
 
 int md_eval_partials(const md_solutions *s) { return md_eval_blocks(s) * MD_EVAL_WARPS; }
 
-md_status md_launch_eval(md_solutions *s, md_moves *m, uint32_t flags, cudaStream_t st) {
+md_status md_launch_eval(md_solutions *s, md_moves *m, uint32_t flags, cudaStream_t st, int s0, int count) {
     const DevInst &I = s->inst->d;
-    dim3 grid(m->d.nblk / MD_EVAL_WARPS, s->n_sol);
-    if (I.variant & MD_VARIANT_TW) k_eval<true><<<grid, 32 * MD_EVAL_WARPS, 0, st>>>(I, s->d, m->d, flags);
-    else k_eval<false><<<grid, 32 * MD_EVAL_WARPS, 0, st>>>(I, s->d, m->d, flags);
+    if (count < 0) count = s->n_sol - s0;
+    if (count <= 0) return MD_OK;
+    dim3 grid(m->d.nblk / MD_EVAL_WARPS, count);
+    if (I.variant & MD_VARIANT_TW) k_eval<true><<<grid, 32 * MD_EVAL_WARPS, 0, st>>>(I, s->d, m->d, flags, s0);
+    else k_eval<false><<<grid, 32 * MD_EVAL_WARPS, 0, st>>>(I, s->d, m->d, flags, s0);
     MD_CUDA(cudaGetLastError());
     return MD_OK;
 }

@@ -84,6 +84,8 @@ struct DevMoves {
     unsigned long long *cand_key;  // [S * ncap] follower candidates for the selection
     uint32_t *cand_rt;             // [S * ncap] packed route pair (i | j << 16)
     int ncap;
+    uint32_t *flist;               // [S * ncap] route pairs (i * R + j) whose table entry is set
+    uint32_t *fcount;              // [S] entries of flist
     uint32_t *sel;         // [S * R] selected move ids (32-bit part), leader first
     int32_t *nsel;         // [S]
     md_move *dump;         // [dump_cap]
@@ -205,6 +207,7 @@ struct md_moves {
     int last_flags;
     int evaluated;
     int selected;
+    int pending;  // the follower table holds entries no selection has consumed
 };
 
 void md_set_error(const char *fmt, ...);
@@ -219,9 +222,10 @@ md_status md_cuda_check(cudaError_t e, const char *what);
 // Launchers implemented in the .cu files.
 md_status md_launch_rebuild_all(md_solutions *s, cudaStream_t st);
 md_status md_launch_totals(md_solutions *s, cudaStream_t st);
-md_status md_launch_eval(md_solutions *s, md_moves *m, uint32_t flags, cudaStream_t st);
+// s0 / count restrict a launch to solutions s0 .. s0 + count - 1 (count < 0: all from s0).
+md_status md_launch_eval(md_solutions *s, md_moves *m, uint32_t flags, cudaStream_t st, int s0 = 0, int count = -1);
 md_status md_launch_select(md_solutions *s, md_moves *m, int multi, cudaStream_t st);
 md_status md_launch_apply(md_solutions *s, md_moves *m, int update_lambda, cudaStream_t st);
-md_status md_launch_step(md_solutions *s, md_moves *m, cudaStream_t st);
+md_status md_launch_step(md_solutions *s, md_moves *m, cudaStream_t st, int s0 = 0, int count = -1);
 int md_eval_blocks(const md_solutions *s);
 int md_eval_partials(const md_solutions *s);

@@ -84,22 +84,25 @@ __device__ int select_moves(const DevInst &I, const DevSols &D, const DevMoves &
     }
     __syncthreads();
     const int have_leader = s_n;
-    // followers: collect every non-empty route-pair entry (and clear the table for the next step)
+    // followers: the route pairs the evaluation listed (each entry is cleared for the next step)
     const size_t tab = (size_t)s * R * R;
     unsigned long long *ck = M.cand_key + (size_t)s * M.ncap;
     uint32_t *cr = M.cand_rt + (size_t)s * M.ncap;
     const bool use = have_leader && multi;
-    for (size_t e = tid; e < (size_t)R * R; e += nt) {
-        const unsigned long long key = M.foltab[tab + e];
-        if (key == MD_EMPTY_KEY) continue;
-        M.foltab[tab + e] = MD_EMPTY_KEY;
+    const int nf = min((int)M.fcount[s], M.ncap);
+    const uint32_t *fl = M.flist + (size_t)s * M.ncap;
+    for (int e = tid; e < nf; e += nt) {
+        const uint32_t pair = fl[e];
+        const unsigned long long key = M.foltab[tab + pair];
+        M.foltab[tab + pair] = MD_EMPTY_KEY;
         if (!use) continue;
-        const int i = (int)(e / R), j = (int)(e % R);
+        const int i = (int)(pair / (uint32_t)R), j = (int)(pair % (uint32_t)R);
         if (i == s_rA || i == s_rB || j == s_rA || j == s_rB) continue;  // blocked by the leader
         const int k = atomicAdd(&s_ncand, 1);
         if (k < M.ncap) { ck[k] = key; cr[k] = (uint32_t)i | ((uint32_t)j << 16); }
     }
     __syncthreads();
+    if (tid == 0) M.fcount[s] = 0;
     if (!use) {
         if (tid == 0) M.nsel[s] = have_leader;
         __syncthreads();
@@ -379,10 +382,10 @@ __global__ void k_apply(DevInst I, DevSols D, DevMoves M, int update_lambda_flag
 // One step of the descent for every solution still running: select, apply, rebuild, update
 // counters and lambda, then advance (pass, slot) and set the next operator.
 template <bool TW>
-__global__ void k_step(DevInst I, DevSols D, DevMoves M) {
+__global__ void k_step(DevInst I, DevSols D, DevMoves M, int s0) {
     extern __shared__ __align__(16) unsigned char smem[];
     const StepSmem sm = carve(smem, D.R, I.nd, D.K, blockDim.x >> 5);
-    const int s = blockIdx.x;
+    const int s = s0 + blockIdx.x;
     int *st = D.state + (size_t)s * 8;
     if (st[3]) return;
     const int n_ops = st[4], max_pass = st[5], multi = st[6], lup = st[7];
@@ -442,14 +445,16 @@ md_status md_launch_apply(md_solutions *s, md_moves *m, int update_lambda, cudaS
     return MD_OK;
 }
 
-md_status md_launch_step(md_solutions *s, md_moves *m, cudaStream_t st) {
+md_status md_launch_step(md_solutions *s, md_moves *m, cudaStream_t st, int s0, int count) {
     const size_t sm = step_smem(s, STEP_THREADS);
+    if (count < 0) count = s->n_sol - s0;
+    if (count <= 0) return MD_OK;
     if (s->inst->d.variant & MD_VARIANT_TW) {
         MD_CUDA(cudaFuncSetAttribute(k_step<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        k_step<true><<<s->n_sol, STEP_THREADS, sm, st>>>(s->inst->d, s->d, m->d);
+        k_step<true><<<count, STEP_THREADS, sm, st>>>(s->inst->d, s->d, m->d, s0);
     } else {
         MD_CUDA(cudaFuncSetAttribute(k_step<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        k_step<false><<<s->n_sol, STEP_THREADS, sm, st>>>(s->inst->d, s->d, m->d);
+        k_step<false><<<count, STEP_THREADS, sm, st>>>(s->inst->d, s->d, m->d, s0);
     }
     MD_CUDA(cudaGetLastError());
     return MD_OK;

@@ -65,7 +65,7 @@ class Config(C.Structure):
     _fields_ = [("n_ops", C.c_int32), ("max_pass", C.c_int32), ("op_perm", C.POINTER(C.c_uint8)),
                 ("lambda0", C.POINTER(C.c_float)), ("multi_move", C.c_int32),
                 ("lambda_update", C.c_int32), ("use_graph", C.c_int32), ("poll_every", C.c_int32),
-                ("op_perm_device", C.c_int32), ("time_eval", C.c_int32)]
+                ("op_perm_device", C.c_int32), ("time_eval", C.c_int32), ("n_groups", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -282,7 +282,7 @@ class Solutions:
 
     def descend(self, perm, max_pass: int, multi: bool = True, lambda_update: bool = False,
                 lambda0=None, use_graph: bool = False, poll_every: int = 1, stream=None,
-                n_ops: int | None = None, time_eval: bool = False) -> DescendStats:
+                n_ops: int | None = None, time_eval: bool = False, n_groups: int = 1) -> DescendStats:
         """MDFIS descent.  perm: uint8 host array [n_sol, >= max_pass, n_ops], or an int device
         pointer to a [n_sol, max_pass, n_ops] uint8 buffer (then n_ops must be given)."""
         if isinstance(perm, int):
@@ -298,7 +298,7 @@ class Solutions:
         cfg = Config(n_ops, max_pass, pptr,
                      lam.ctypes.data_as(C.POINTER(C.c_float)) if lam is not None else None,
                      int(multi), int(lambda_update), int(use_graph), int(poll_every), on_dev,
-                     int(time_eval))
+                     int(time_eval), int(n_groups))
         st = Stats()
         _check(lib().md_descend(self.h, C.byref(cfg), C.byref(st), _stream(stream)))
         return DescendStats(st.moves_scored, st.steps, st.accepted_steps, st.applied_moves,

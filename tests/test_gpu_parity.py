@@ -249,20 +249,23 @@ def test_descent_matches_oracle(md, oracle_lib, stream, case, mode):
 
 
 def test_timed_graph_descent_matches_untimed(md, stream):
-    # Event timing of every evaluation launch inside the captured graph changes nothing else.
+    # Event timing inside the captured graph, and grouped solutions on concurrent streams, change
+    # nothing but the timing.
     spec = W.mdvrptw_6x288(45)
     sols = W.initial_solutions(spec, 45, 8)
     perm = W.op_permutations(8, 8, 100)
     inst = md.Instance(spec)
     runs = []
-    for graph, timed in ((False, False), (True, True), (False, True)):
+    for graph, timed, groups in ((False, False, 1), (True, True, 1), (False, True, 1), (True, True, 3),
+                                 (False, False, 2)):
         S = md.Solutions(inst, 8, 64, 64)
         S.load(sols)
-        st = S.descend(perm, 100, use_graph=graph, time_eval=timed, poll_every=2, stream=stream)
-        runs.append((st, canon(spec, S.read()[0]), S.stats()))
-    for st, sol0, per in runs[1:]:
+        st = S.descend(perm, 100, use_graph=graph, time_eval=timed, poll_every=2, stream=stream,
+                       n_groups=groups)
+        runs.append((st, canon(spec, S.read()[0]), S.stats(), timed))
+    for st, sol0, per, timed in runs[1:]:
         assert sol0 == runs[0][1] and np.array_equal(per, runs[0][2])
-        assert st.eval_ms > 0 and st.eval_launches >= st.steps // 8
+        assert (st.eval_ms > 0) == timed and st.eval_launches >= st.steps // 8
         assert sum(st.moves_by_op) == st.moves_scored
 
 
