@@ -258,6 +258,31 @@ md_status md_descend(md_solutions *sols, const md_config *cfg, md_stats *out, vo
  * steps, applied moves, passes. */
 md_status md_solutions_stats(md_solutions *sols, int64_t *per_sol, void *stream);
 
+/* Batches of instances of uneven size.  A batch groups solution sets of different instances
+ * (each from md_solutions_create/load on the same device, each still owned by the caller) so
+ * that every solution of every instance advances with ONE evaluation launch and ONE select/apply
+ * launch per descent step (Alg. 2), replayed from a CUDA graph per pass: the evaluation launch is
+ * persistent, its blocks walking a work list of (instance, solution, tile) with the largest
+ * instances first.  MD_ERR_ARG on null or empty input. */
+typedef struct md_batch md_batch;
+md_status md_batch_create(md_solutions *const *sols, int32_t n, md_batch **out);
+md_status md_batch_destroy(md_batch *batch);
+
+/* Autotuner of the batch's tile shapes: per instance, the customers per warp of an evaluation
+ * tile (1, 2 or 4), timed with CUDA events on that instance alone; then the persistent grid
+ * (1, 2, 4 or 8 blocks per SM), timed on the whole batch.  Uses the loaded solutions and sets
+ * every solution's operator to a fixed mix for the timings.  Results only change speed. */
+md_status md_batch_tune(md_batch *batch, void *stream);
+
+/* The chosen shapes: upw [n] customers per warp per instance (caller order), grid blocks. */
+md_status md_batch_tuning(const md_batch *batch, int32_t *upw, int32_t *grid);
+
+/* MDFIS descent (Alg. 2) of every solution of every instance, as md_descend per instance would
+ * do it (identical results).  cfg->op_perm covers the solutions of all instances in the order
+ * they were given to md_batch_create ([sum n_sol * max_pass * n_ops]); cfg->lambda0 likewise
+ * ([sum n_sol * 4]) or NULL.  cfg->n_groups is ignored. */
+md_status md_batch_descend(md_batch *batch, const md_config *cfg, md_stats *out, void *stream);
+
 /* Allocation-free variant of md_eval_neighborhood + md_moves_read_leaders.  The paper has no
  * counterpart: it exists for callers that cannot call cudaMalloc (device memory budgeted up front,
  * latency-critical loops that must not enter the allocator, code handed only raw device buffers).

@@ -266,24 +266,21 @@ extern "C" md_status md_apply_and_rebuild(md_solutions *s, md_moves *m, uint32_t
     return check_err(s, st);
 }
 
-extern "C" md_status md_descend(md_solutions *s, const md_config *cfg, md_stats *out, void *stream) {
-    if (!s || !cfg || !cfg->op_perm) { md_set_error("md_descend: null argument"); return MD_ERR_ARG; }
-    if (cfg->n_ops < 1 || cfg->n_ops > MD_MAX_OPS || cfg->max_pass < 1) {
-        md_set_error("md_descend: need 1 <= n_ops <= %d and max_pass >= 1", MD_MAX_OPS);
-        return MD_ERR_ARG;
-    }
+// Everything a descent does before its first step: scratch, operator order, lambda, totals,
+// cleared follower tables and counters, per-solution state.  perm_dev (may be NULL) overrides
+// cfg->op_perm with a device buffer already laid out for these solutions.
+md_status md_descend_prepare(md_solutions *s, const md_config *cfg, const uint8_t *perm_dev, cudaStream_t st,
+                             long long *launches) {
     const size_t nperm = (size_t)s->n_sol * cfg->max_pass * cfg->n_ops;
-    if (!cfg->op_perm_device)
-        for (size_t i = 0; i < nperm; i++)
-            if (cfg->op_perm[i] >= MD_N_OPS) { md_set_error("md_descend: unknown operator in op_perm"); return MD_ERR_ARG; }
-    cudaStream_t st = (cudaStream_t)stream;
     // the evaluation scratch of the descent is created once and kept with the solutions
     if (!s->scratch) {
         md_status r = md_moves_create(s, 0, &s->scratch);
         if (r != MD_OK) return r;
     }
     md_moves *m = s->scratch;
-    if (cfg->op_perm_device) {
+    if (perm_dev) {
+        s->d.perm = perm_dev;
+    } else if (cfg->op_perm_device) {
         s->d.perm = cfg->op_perm;
     } else {
         if (s->perm_bytes < nperm) {
@@ -296,18 +293,35 @@ extern "C" md_status md_descend(md_solutions *s, const md_config *cfg, md_stats 
         MD_CUDA(cudaMemcpyAsync(s->perm_dev, cfg->op_perm, nperm, cudaMemcpyHostToDevice, st));
         s->d.perm = s->perm_dev;
     }
-    long long launches = 0, eval_launches = 0;
     if (cfg->lambda0) MD_CUDA(cudaMemcpyAsync(s->d.lam, cfg->lambda0, sizeof(float) * 4 * s->n_sol, cudaMemcpyHostToDevice, st));
     md_status r = md_launch_totals(s, st);
     if (r != MD_OK) return r;
-    launches++;
+    ++*launches;
     MD_CUDA(cudaMemsetAsync(m->d.foltab, 0xff, sizeof(unsigned long long) * s->n_sol * s->R * s->R, st));
     MD_CUDA(cudaMemsetAsync(m->d.fcount, 0, sizeof(uint32_t) * s->n_sol, st));
     MD_CUDA(cudaMemsetAsync(m->d.nscored, 0, sizeof(unsigned long long) * s->n_sol, st));
     k_descend_init<<<(s->n_sol + 127) / 128, 128, 0, st>>>(s->d, cfg->n_ops, cfg->max_pass, cfg->multi_move ? 1 : 0,
                                                          cfg->lambda_update ? 1 : 0);
     MD_CUDA(cudaGetLastError());
-    launches++;
+    ++*launches;
+    return MD_OK;
+}
+
+extern "C" md_status md_descend(md_solutions *s, const md_config *cfg, md_stats *out, void *stream) {
+    if (!s || !cfg || !cfg->op_perm) { md_set_error("md_descend: null argument"); return MD_ERR_ARG; }
+    if (cfg->n_ops < 1 || cfg->n_ops > MD_MAX_OPS || cfg->max_pass < 1) {
+        md_set_error("md_descend: need 1 <= n_ops <= %d and max_pass >= 1", MD_MAX_OPS);
+        return MD_ERR_ARG;
+    }
+    const size_t nperm = (size_t)s->n_sol * cfg->max_pass * cfg->n_ops;
+    if (!cfg->op_perm_device)
+        for (size_t i = 0; i < nperm; i++)
+            if (cfg->op_perm[i] >= MD_N_OPS) { md_set_error("md_descend: unknown operator in op_perm"); return MD_ERR_ARG; }
+    cudaStream_t st = (cudaStream_t)stream;
+    long long launches = 0, eval_launches = 0;
+    md_status r = md_descend_prepare(s, cfg, nullptr, st, &launches);
+    if (r != MD_OK) return r;
+    md_moves *m = s->scratch;
     const uint32_t eflags = cfg->multi_move ? MD_EVAL_FOLLOWERS : 0u;
     const int poll = cfg->poll_every > 0 ? cfg->poll_every : 1;
     const int steps_per_poll = cfg->n_ops * poll;

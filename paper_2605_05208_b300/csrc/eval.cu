@@ -510,6 +510,39 @@ __device__ void eval_depot_replace(const Ctx &C, int cu, int lane, Best &b) {
     }
 }
 
+__device__ __forceinline__ void best_init(Best &b) {
+    b.f = 0.0; b.id = 0xffffffffu; b.valid = 0; b.n = 0; b.fb = 0.0f;
+}
+
+template <bool TW>
+__device__ __forceinline__ void eval_customer(const Ctx &C, int op, int cu, int lane, Best &b) {
+    switch (op) {
+    case MD_OP_RELOCATE: eval_relocate<TW>(C, cu, lane, b); break;
+    case MD_OP_SWAP: eval_swap<TW>(C, cu, lane, b); break;
+    case MD_OP_TWO_OPT_STAR: eval_2optstar<TW>(C, cu, lane, b); break;
+    case MD_OP_DEPOT_INSERT: eval_depot_insert<TW>(C, cu, lane, b); break;
+    case MD_OP_DEPOT_REPLACE: eval_depot_replace<TW>(C, cu, lane, b); break;
+    default: break;
+    }
+}
+
+// Warp reduction of the lanes' leader candidates and scored counts; one record per warp slot.
+__device__ __forceinline__ void warp_commit(const Ctx &C, Best &b, size_t slot, int lane) {
+    for (int o = 16; o > 0; o >>= 1) {
+        const double of = __shfl_xor_sync(0xffffffffu, b.f, o);
+        const uint32_t oi = __shfl_xor_sync(0xffffffffu, b.id, o);
+        const int ov = __shfl_xor_sync(0xffffffffu, b.valid, o);
+        b.n += __shfl_xor_sync(0xffffffffu, b.n, o);
+        if (ov && (!b.valid || of < b.f || (of == b.f && oi < b.id))) { b.f = of; b.id = oi; b.valid = 1; }
+    }
+    if (lane == 0) {
+        LeadRec r;
+        r.f = b.f; r.id = b.id; r.valid = b.valid;
+        C.M.lpart[(size_t)C.s * C.M.nblk + slot] = r;
+        if (b.n) atomicAdd(&C.M.nscored[C.s], b.n);
+    }
+}
+
 template <bool TW>
 __global__ void __launch_bounds__(256, 2) k_eval(DevInst I, DevSols D, DevMoves M, uint32_t flags, int s0) {
     Ctx C;
@@ -523,33 +556,44 @@ __global__ void __launch_bounds__(256, 2) k_eval(DevInst I, DevSols D, DevMoves 
     }
     const int op = D.ops[C.s];
     Best b;
-    b.f = 0.0; b.id = 0xffffffffu; b.valid = 0; b.n = 0; b.fb = 0.0f;
+    best_init(b);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
-    if (op >= 0) {
-        for (int cu = blockIdx.x * wpb + warp; cu < I.nc; cu += gridDim.x * wpb) {
-            switch (op) {
-            case MD_OP_RELOCATE: eval_relocate<TW>(C, cu, lane, b); break;
-            case MD_OP_SWAP: eval_swap<TW>(C, cu, lane, b); break;
-            case MD_OP_TWO_OPT_STAR: eval_2optstar<TW>(C, cu, lane, b); break;
-            case MD_OP_DEPOT_INSERT: eval_depot_insert<TW>(C, cu, lane, b); break;
-            case MD_OP_DEPOT_REPLACE: eval_depot_replace<TW>(C, cu, lane, b); break;
-            default: break;
-            }
+    if (op >= 0)
+        for (int cu = blockIdx.x * wpb + warp; cu < I.nc; cu += gridDim.x * wpb) eval_customer<TW>(C, op, cu, lane, b);
+    warp_commit(C, b, (size_t)blockIdx.x * wpb + warp, lane);
+}
+
+// Batched form: one persistent launch covers every (instance, solution, tile) of a batch of
+// instances of uneven size.  Tiles are taken in grid-stride order over the global work list.
+template <bool TW>
+__global__ void __launch_bounds__(256, 2) k_eval_batch(const BatchItem *items, int n_items, int total_tiles,
+                                                      uint32_t flags) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
+        int it = 0;
+        while (it + 1 < n_items && items[it + 1].tile_base <= tile) it++;
+        const BatchItem &B = items[it];
+        const int local = tile - B.tile_base;
+        Ctx C;
+        C.I = B.I; C.D = B.D; C.M = B.M; C.flags = flags;
+        C.s = local / B.tiles_per_sol;
+        const int t = local - C.s * B.tiles_per_sol;
+        C.open = (C.I.variant & MD_VARIANT_OPEN) != 0;
+        C.sym = (C.I.variant & MD_VARIANT_SYMMETRIC) != 0;
+        for (int k = 0; k < 4; k++) {
+            C.w[k] = C.D.w[4 * C.s + k];
+            C.wf[k] = (float)C.w[k];
         }
-    }
-    // warp reduction of the leader candidate and of the scored count; one record per warp
-    for (int o = 16; o > 0; o >>= 1) {
-        const double of = __shfl_xor_sync(0xffffffffu, b.f, o);
-        const uint32_t oi = __shfl_xor_sync(0xffffffffu, b.id, o);
-        const int ov = __shfl_xor_sync(0xffffffffu, b.valid, o);
-        b.n += __shfl_xor_sync(0xffffffffu, b.n, o);
-        if (ov && (!b.valid || of < b.f || (of == b.f && oi < b.id))) { b.f = of; b.id = oi; b.valid = 1; }
-    }
-    if (lane == 0) {
-        LeadRec r;
-        r.f = b.f; r.id = b.id; r.valid = b.valid;
-        M.lpart[(size_t)C.s * M.nblk + (size_t)blockIdx.x * wpb + warp] = r;
-        if (b.n) atomicAdd(&M.nscored[C.s], b.n);
+        const int op = C.D.ops[C.s];
+        Best b;
+        best_init(b);
+        const int ws = t * MD_EVAL_WARPS + warp;  // warp slot within the solution
+        if (op >= 0)
+            for (int q = 0; q < B.upw; q++) {
+                const int cu = ws * B.upw + q;
+                if (cu < C.I.nc) eval_customer<TW>(C, op, cu, lane, b);
+            }
+        warp_commit(C, b, ws, lane);
     }
 }
 
@@ -570,6 +614,16 @@ md_status md_launch_eval(md_solutions *s, md_moves *m, uint32_t flags, cudaStrea
     dim3 grid(m->d.nblk / MD_EVAL_WARPS, count);
     if (I.variant & MD_VARIANT_TW) k_eval<true><<<grid, 32 * MD_EVAL_WARPS, 0, st>>>(I, s->d, m->d, flags, s0);
     else k_eval<false><<<grid, 32 * MD_EVAL_WARPS, 0, st>>>(I, s->d, m->d, flags, s0);
+    MD_CUDA(cudaGetLastError());
+    return MD_OK;
+}
+
+md_status md_launch_eval_batch(const BatchItem *items, int n_items, int total_tiles, int grid, bool tw,
+                               uint32_t flags, cudaStream_t st) {
+    if (total_tiles <= 0) return MD_OK;
+    if (grid < 1) grid = 1;
+    if (tw) k_eval_batch<true><<<grid, 32 * MD_EVAL_WARPS, 0, st>>>(items, n_items, total_tiles, flags);
+    else k_eval_batch<false><<<grid, 32 * MD_EVAL_WARPS, 0, st>>>(items, n_items, total_tiles, flags);
     MD_CUDA(cudaGetLastError());
     return MD_OK;
 }

@@ -210,6 +210,20 @@ struct md_moves {
     int pending;  // the follower table holds entries no selection has consumed
 };
 
+// One instance of a batch (md_batch_*): its tensors, solutions and scratch, and its place in the
+// batch's work lists.  A tile is 8 warps x upw customers of one solution.
+struct BatchItem {
+    DevInst I;
+    DevSols D;
+    DevMoves M;
+    int tile_base;      // first global tile of this item
+    int tiles_per_sol;  // ceil(nc / (8 * upw))
+    int upw;            // customers per warp in a tile
+    int nrec;           // leader records per solution in use (tiles_per_sol * 8)
+    int sol_base;       // first global solution index of this item
+    int pad[3];
+};
+
 void md_set_error(const char *fmt, ...);
 md_status md_cuda_check(cudaError_t e, const char *what);
 
@@ -227,5 +241,12 @@ md_status md_launch_eval(md_solutions *s, md_moves *m, uint32_t flags, cudaStrea
 md_status md_launch_select(md_solutions *s, md_moves *m, int multi, cudaStream_t st);
 md_status md_launch_apply(md_solutions *s, md_moves *m, int update_lambda, cudaStream_t st);
 md_status md_launch_step(md_solutions *s, md_moves *m, cudaStream_t st, int s0 = 0, int count = -1);
+md_status md_launch_eval_batch(const BatchItem *items, int n_items, int total_tiles, int grid, bool tw,
+                               uint32_t flags, cudaStream_t st);
+md_status md_launch_step_batch(const BatchItem *items, int n_items, int total_sols, size_t smem, bool tw,
+                               cudaStream_t st);
+size_t md_step_smem(const md_solutions *s);
+md_status md_descend_prepare(md_solutions *s, const md_config *cfg, const uint8_t *perm_dev, cudaStream_t st,
+                             long long *launches);
 int md_eval_blocks(const md_solutions *s);
 int md_eval_partials(const md_solutions *s);

@@ -45,7 +45,7 @@ __device__ __forceinline__ void move_routes(const DevInst &I, const DevSols &D, 
 
 // Leader + followers of solution s into M.sel / M.nsel.  Returns the number selected.
 __device__ int select_moves(const DevInst &I, const DevSols &D, const DevMoves &M, int s, int multi,
-                            const StepSmem &sm) {
+                            const StepSmem &sm, int nrec) {
     __shared__ double lf[32];
     __shared__ uint32_t lid[32];
     __shared__ int lv[32];
@@ -56,7 +56,7 @@ __device__ int select_moves(const DevInst &I, const DevSols &D, const DevMoves &
     double f = 0.0;
     uint32_t id = 0xffffffffu;
     int valid = 0;
-    for (int k = tid; k < M.nblk; k += nt) {
+    for (int k = tid; k < nrec; k += nt) {
         LeadRec r = M.lpart[(size_t)s * M.nblk + k];
         if (r.valid && (!valid || r.f < f || (r.f == f && r.id < id))) { f = r.f; id = r.id; valid = 1; }
     }
@@ -365,7 +365,7 @@ __device__ void update_lambda(const DevInst &I, const DevSols &D, int s) {
 __global__ void k_select(DevInst I, DevSols D, DevMoves M, int multi) {
     extern __shared__ __align__(16) unsigned char smem[];
     const StepSmem sm = carve(smem, D.R, I.nd, D.K, blockDim.x >> 5);
-    select_moves(I, D, M, blockIdx.x, multi, sm);
+    select_moves(I, D, M, blockIdx.x, multi, sm, M.nblk);
 }
 
 template <bool TW>
@@ -382,14 +382,13 @@ __global__ void k_apply(DevInst I, DevSols D, DevMoves M, int update_lambda_flag
 // One step of the descent for every solution still running: select, apply, rebuild, update
 // counters and lambda, then advance (pass, slot) and set the next operator.
 template <bool TW>
-__global__ void k_step(DevInst I, DevSols D, DevMoves M, int s0) {
+__device__ void step_body(const DevInst &I, const DevSols &D, const DevMoves &M, int s, int nrec) {
     extern __shared__ __align__(16) unsigned char smem[];
     const StepSmem sm = carve(smem, D.R, I.nd, D.K, blockDim.x >> 5);
-    const int s = s0 + blockIdx.x;
     int *st = D.state + (size_t)s * 8;
     if (st[3]) return;
     const int n_ops = st[4], max_pass = st[5], multi = st[6], lup = st[7];
-    const int nsel = select_moves(I, D, M, s, multi, sm);
+    const int nsel = select_moves(I, D, M, s, multi, sm, nrec);
     if (nsel > 0) {
         apply_selection<TW>(I, D, M, s, nsel, sm);
         if (lup) update_lambda(I, D, s);
@@ -415,6 +414,23 @@ __global__ void k_step(DevInst I, DevSols D, DevMoves M, int s0) {
     }
 }
 
+template <bool TW>
+__global__ void k_step(DevInst I, DevSols D, DevMoves M, int s0) {
+    step_body<TW>(I, D, M, s0 + blockIdx.x, M.nblk);
+}
+
+// Batched form: one block per (instance, solution) of a batch.
+template <bool TW>
+__global__ void k_step_batch(const BatchItem *items, int n_items) {
+    int it = 0;
+    while (it + 1 < n_items && items[it + 1].sol_base <= (int)blockIdx.x) it++;
+    const BatchItem &B = items[it];
+    const DevInst I = B.I;
+    const DevSols D = B.D;
+    const DevMoves M = B.M;
+    step_body<TW>(I, D, M, (int)blockIdx.x - B.sol_base, B.nrec);
+}
+
 }  // namespace
 
 static size_t step_smem(const md_solutions *s, int threads) {
@@ -423,6 +439,22 @@ static size_t step_smem(const md_solutions *s, int threads) {
 }
 
 static const int STEP_THREADS = 256;
+
+size_t md_step_smem(const md_solutions *s) { return step_smem(s, STEP_THREADS); }
+
+md_status md_launch_step_batch(const BatchItem *items, int n_items, int total_sols, size_t smem, bool tw,
+                               cudaStream_t st) {
+    if (total_sols <= 0) return MD_OK;
+    if (tw) {
+        MD_CUDA(cudaFuncSetAttribute(k_step_batch<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_step_batch<true><<<total_sols, STEP_THREADS, smem, st>>>(items, n_items);
+    } else {
+        MD_CUDA(cudaFuncSetAttribute(k_step_batch<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_step_batch<false><<<total_sols, STEP_THREADS, smem, st>>>(items, n_items);
+    }
+    MD_CUDA(cudaGetLastError());
+    return MD_OK;
+}
 
 md_status md_launch_select(md_solutions *s, md_moves *m, int multi, cudaStream_t st) {
     const size_t sm = step_smem(s, STEP_THREADS);

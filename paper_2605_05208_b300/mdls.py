@@ -31,7 +31,8 @@ EXPORTED = (
     "md_solution_cost", "md_solutions_lambda", "md_solutions_read_summaries", "md_moves_create",
     "md_moves_destroy", "md_eval_neighborhood", "md_moves_read_leaders", "md_moves_read_dump",
     "md_select_multimove", "md_selection_read", "md_apply_and_rebuild", "md_descend",
-    "md_solutions_stats", "md_eval_leaders_noalloc",
+    "md_solutions_stats", "md_eval_leaders_noalloc", "md_batch_create", "md_batch_destroy",
+    "md_batch_tune", "md_batch_tuning", "md_batch_descend",
 )
 
 
@@ -112,6 +113,11 @@ def lib() -> C.CDLL:
             "md_descend": [P, C.POINTER(Config), C.POINTER(Stats), P],
             "md_solutions_stats": [P, P, P],
             "md_eval_leaders_noalloc": [P, P, P, P, P, P],
+            "md_batch_create": [P, C.c_int32, PP],
+            "md_batch_destroy": [P],
+            "md_batch_tune": [P, P],
+            "md_batch_tuning": [P, P, P],
+            "md_batch_descend": [P, C.POINTER(Config), C.POINTER(Stats), P],
         }
         for name, args in sigs.items():
             f = getattr(L, name)
@@ -361,3 +367,56 @@ class Moves:
         _check(lib().md_apply_and_rebuild(self.sols.h, self.h, APPLY_UPDATE_LAMBDA if update_lambda else 0,
                                           _ptr(lam), _stream(stream)))
         return lam
+
+
+class Batch:
+    """Solution sets of several instances descended together (md_batch_*)."""
+
+    def __init__(self, sols_list):
+        self.sols_list = list(sols_list)  # keeps the solution sets alive
+        arr = (C.c_void_p * len(self.sols_list))(*[s.h.value for s in self.sols_list])
+        h = C.c_void_p()
+        _check(lib().md_batch_create(arr, len(self.sols_list), C.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().md_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def tune(self, stream=None):
+        _check(lib().md_batch_tune(self.h, _stream(stream)))
+        return self.tuning()
+
+    def tuning(self):
+        upw = np.zeros(len(self.sols_list), dtype=np.int32)
+        g = np.zeros(1, dtype=np.int32)
+        _check(lib().md_batch_tuning(self.h, _ptr(upw), _ptr(g)))
+        return upw, int(g[0])
+
+    def descend(self, perm, max_pass: int, multi: bool = True, lambda_update: bool = False,
+                use_graph: bool = True, poll_every: int = 1, stream=None, n_ops: int | None = None,
+                time_eval: bool = False) -> DescendStats:
+        """perm: uint8 host array [sum n_sol, >= max_pass, n_ops] in the order the solution sets
+        were given, or an int device pointer (then n_ops must be given)."""
+        if isinstance(perm, int):
+            assert n_ops is not None
+            pptr, on_dev = C.cast(C.c_void_p(perm), C.POINTER(C.c_uint8)), 1
+        else:
+            perm = np.ascontiguousarray(np.ascontiguousarray(perm, dtype=np.uint8)[:, :max_pass])
+            n_ops = perm.shape[2]
+            pptr, on_dev = perm.ctypes.data_as(C.POINTER(C.c_uint8)), 0
+        cfg = Config(n_ops, max_pass, pptr, None, int(multi), int(lambda_update), int(use_graph),
+                     int(poll_every), on_dev, int(time_eval), 1)
+        st = Stats()
+        _check(lib().md_batch_descend(self.h, C.byref(cfg), C.byref(st), _stream(stream)))
+        return DescendStats(st.moves_scored, st.steps, st.accepted_steps, st.applied_moves,
+                            st.passes_max, st.launches, st.eval_launches, st.eval_ms,
+                            tuple(st.moves_by_op))
+

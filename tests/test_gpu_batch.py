@@ -1,0 +1,83 @@
+"""Batches of uneven instances (one persistent evaluation launch and one select/apply launch per
+descent step for every instance) against per-instance descents and the CPU oracle."""
+import numpy as np
+import pytest
+
+from paper_2605_05208_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+MAX_PASS = 80
+
+
+def _specs():
+    return [W.gen_mdvrp(81, n_depots=3, n_customers=70, n_solutions=3),
+            W.gen_mdvrptw(82, n_depots=2, n_customers=130, theta=20, n_solutions=3),
+            W.gen_mdovrp(83, n_depots=4, n_customers=95, n_solutions=3),
+            W.gen_mdvrptw(84, n_depots=3, n_customers=60, theta=0, n_solutions=2)]
+
+
+def _load(md, spec, sols):
+    inst = md.Instance(spec)
+    S = md.Solutions(inst, len(sols), spec.n_customers + 1, spec.n_customers)
+    S.load(sols)
+    return inst, S
+
+
+@pytest.fixture(scope="module")
+def case():
+    from paper_2605_05208_b300 import build, mdls
+    build.build()
+    specs = _specs()
+    sols = [W.initial_solutions(sp, 90 + i, sp.n_solutions) for i, sp in enumerate(specs)]
+    perms = [W.op_permutations(95 + i, sp.n_solutions, MAX_PASS) for i, sp in enumerate(specs)]
+    return mdls, specs, sols, perms
+
+
+def _reference(md, specs, sols, perms):
+    out = []
+    for sp, so, pe in zip(specs, sols, perms):
+        inst, S = _load(md, sp, so)
+        S.descend(pe, MAX_PASS)
+        out.append(([W.canonical(r, bool(sp.variant & W.VAR_OPEN)) for r in S.read()], S.stats()))
+    return out
+
+
+@pytest.mark.parametrize("tuned,graph", [(False, True), (True, True), (True, False)])
+def test_batch_descent_matches_per_instance(case, tuned, graph):
+    import torch
+    md, specs, sols, perms = case
+    ref = _reference(md, specs, sols, perms)
+    loaded = [_load(md, sp, so) for sp, so in zip(specs, sols)]
+    B = md.Batch([S for _, S in loaded])
+    stream = torch.cuda.Stream().cuda_stream
+    if tuned:
+        upw, grid = B.tune(stream=stream)
+        assert set(upw.tolist()) <= {1, 2, 4} and grid > 0
+        for (_, S), so in zip(loaded, sols):
+            S.load(so)  # tuning leaves the solutions untouched; reload anyway to start clean
+    st = B.descend(np.concatenate(perms), MAX_PASS, use_graph=graph, stream=stream)
+    total = 0
+    for (_, S), sp, (want_routes, want_stats) in zip(loaded, specs, ref):
+        got = [W.canonical(r, bool(sp.variant & W.VAR_OPEN)) for r in S.read()]
+        assert got == want_routes
+        assert np.array_equal(S.stats(), want_stats)
+        total += int(want_stats[:, 0].sum())
+    assert st.moves_scored == total and sum(st.moves_by_op) == total
+
+
+def test_batch_matches_oracle(case, oracle_lib):
+    md, specs, sols, perms = case
+    loaded = [_load(md, sp, so) for sp, so in zip(specs, sols)]
+    B = md.Batch([S for _, S in loaded])
+    B.descend(np.concatenate(perms), MAX_PASS)
+    for i in (0, 2):  # MDVRP and MDOVRP items
+        sp = specs[i]
+        o = oracle_lib.Instance(sp)
+        got = loaded[i][1].read()
+        per = loaded[i][1].stats()
+        for s, sol in enumerate(sols[i]):
+            d = o.descend(sol, perms[i][s], MAX_PASS)
+            op = bool(sp.variant & W.VAR_OPEN)
+            assert W.canonical(got[s], op) == W.canonical(d.solution, op)
+            assert list(per[s]) == [d.moves_scored, d.steps, d.accepted_steps, d.applied_moves, d.passes]
