@@ -17,6 +17,10 @@
 // candidate, so no warp waits for the others of its block.
 #include "mdls_internal.cuh"
 
+#ifndef MD_EVAL_MIN_BLOCKS
+#define MD_EVAL_MIN_BLOCKS 2  // evaluation blocks resident per SM (register budget 65536 / (256 x this))
+#endif
+
 namespace {
 
 struct RT {  // the four integer terms of one route (Eq. A1)
@@ -544,7 +548,7 @@ __device__ __forceinline__ void warp_commit(const Ctx &C, Best &b, size_t slot, 
 }
 
 template <bool TW>
-__global__ void __launch_bounds__(256, 2) k_eval(DevInst I, DevSols D, DevMoves M, uint32_t flags, int s0) {
+__global__ void __launch_bounds__(256, MD_EVAL_MIN_BLOCKS) k_eval(DevInst I, DevSols D, DevMoves M, uint32_t flags, int s0) {
     Ctx C;
     C.I = I; C.D = D; C.M = M; C.flags = flags;
     C.s = s0 + blockIdx.y;
@@ -565,35 +569,49 @@ __global__ void __launch_bounds__(256, 2) k_eval(DevInst I, DevSols D, DevMoves 
 
 // Batched form: one persistent launch covers every (instance, solution, tile) of a batch of
 // instances of uneven size.  Tiles are taken in grid-stride order over the global work list.
-template <bool TW>
-__global__ void __launch_bounds__(256, 2) k_eval_batch(const BatchItem *items, int n_items, int total_tiles,
+// TW_ANY: at least one item has time windows; items without them take the TW = false path.
+template <bool TW_ANY>
+__global__ void __launch_bounds__(256, MD_EVAL_MIN_BLOCKS) k_eval_batch(const BatchItem *__restrict__ items, int n_items, int total_tiles,
                                                       uint32_t flags) {
+    // Each warp keeps the context of its current tile in its own shared-memory slot: the
+    // instance, solution and scratch descriptors are read from there when needed instead of
+    // being held in registers.
+    __shared__ Ctx cs[MD_EVAL_WARPS];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    Ctx &C = cs[warp];
     for (int tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
         int it = 0;
         while (it + 1 < n_items && items[it + 1].tile_base <= tile) it++;
         const BatchItem &B = items[it];
         const int local = tile - B.tile_base;
-        Ctx C;
-        C.I = B.I; C.D = B.D; C.M = B.M; C.flags = flags;
-        C.s = local / B.tiles_per_sol;
-        const int t = local - C.s * B.tiles_per_sol;
-        C.open = (C.I.variant & MD_VARIANT_OPEN) != 0;
-        C.sym = (C.I.variant & MD_VARIANT_SYMMETRIC) != 0;
-        for (int k = 0; k < 4; k++) {
-            C.w[k] = C.D.w[4 * C.s + k];
-            C.wf[k] = (float)C.w[k];
+        const int s = local / B.tiles_per_sol;
+        const int t = local - s * B.tiles_per_sol;
+        const int upw = B.upw;
+        if (lane == 0) {
+            C.I = B.I; C.D = B.D; C.M = B.M; C.flags = flags;
+            C.s = s;
+            C.open = (B.I.variant & MD_VARIANT_OPEN) != 0;
+            C.sym = (B.I.variant & MD_VARIANT_SYMMETRIC) != 0;
+            for (int k = 0; k < 4; k++) {
+                C.w[k] = B.D.w[4 * s + k];
+                C.wf[k] = (float)C.w[k];
+            }
         }
-        const int op = C.D.ops[C.s];
+        __syncwarp();
+        const int op = C.D.ops[s];
         Best b;
         best_init(b);
         const int ws = t * MD_EVAL_WARPS + warp;  // warp slot within the solution
+        const bool tw = TW_ANY && (C.I.variant & MD_VARIANT_TW) != 0;
         if (op >= 0)
-            for (int q = 0; q < B.upw; q++) {
-                const int cu = ws * B.upw + q;
-                if (cu < C.I.nc) eval_customer<TW>(C, op, cu, lane, b);
+            for (int q = 0; q < upw; q++) {
+                const int cu = ws * upw + q;
+                if (cu >= C.I.nc) break;
+                if (tw) eval_customer<true>(C, op, cu, lane, b);
+                else eval_customer<false>(C, op, cu, lane, b);
             }
         warp_commit(C, b, ws, lane);
+        __syncwarp();  // every lane is done with this tile's context
     }
 }
 

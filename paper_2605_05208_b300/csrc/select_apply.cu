@@ -419,8 +419,8 @@ __global__ void k_step(DevInst I, DevSols D, DevMoves M, int s0) {
     step_body<TW>(I, D, M, s0 + blockIdx.x, M.nblk);
 }
 
-// Batched form: one block per (instance, solution) of a batch.
-template <bool TW>
+// Batched form: one block per (instance, solution) of a batch; TW_ANY as for k_eval_batch.
+template <bool TW_ANY>
 __global__ void k_step_batch(const BatchItem *items, int n_items) {
     int it = 0;
     while (it + 1 < n_items && items[it + 1].sol_base <= (int)blockIdx.x) it++;
@@ -428,7 +428,8 @@ __global__ void k_step_batch(const BatchItem *items, int n_items) {
     const DevInst I = B.I;
     const DevSols D = B.D;
     const DevMoves M = B.M;
-    step_body<TW>(I, D, M, (int)blockIdx.x - B.sol_base, B.nrec);
+    if (TW_ANY && (I.variant & MD_VARIANT_TW)) step_body<true>(I, D, M, (int)blockIdx.x - B.sol_base, B.nrec);
+    else step_body<false>(I, D, M, (int)blockIdx.x - B.sol_base, B.nrec);
 }
 
 }  // namespace

@@ -282,6 +282,30 @@ def _sweep_order(dxs: np.ndarray, dys: np.ndarray, ids: np.ndarray) -> list[int]
     return sorted(range(len(ids)), key=functools.cmp_to_key(cmp))
 
 
+def _depot_sweeps(inst: InstanceSpec) -> list[list[int]]:
+    """Per depot, its nearest customers in sweep order (computed once per instance)."""
+    cached = inst.meta.get("_sweeps")
+    if cached is not None:
+        return cached
+    nd, nc = inst.n_depots, inst.n_customers
+    xi = np.rint(inst.x).astype(np.int64)
+    yi = np.rint(inst.y).astype(np.int64)
+    assign: dict[int, list[int]] = {d: [] for d in range(nd)}
+    for c in range(nd, nd + nc):
+        d2 = (xi[:nd] - xi[c]) ** 2 + (yi[:nd] - yi[c]) ** 2
+        assign[int(np.argmin(d2))].append(c)
+    out = []
+    for d in range(nd):
+        cs = np.asarray(assign[d], dtype=np.int64)
+        if len(cs) == 0:
+            out.append([])
+            continue
+        order = _sweep_order(xi[cs] - xi[d], yi[cs] - yi[d], cs)
+        out.append([int(cs[i]) for i in order])
+    inst.meta["_sweeps"] = out
+    return out
+
+
 def initial_solution(inst: InstanceSpec, seed: int, sol_index: int, n_random: int = 10,
                      shuffle_start: bool = True) -> list[list[int]]:
     """One seeded initial solution as a list of routes [ds, c1..cL, de] (node ids).
@@ -290,20 +314,13 @@ def initial_solution(inst: InstanceSpec, seed: int, sol_index: int, n_random: in
     sweep (start angle rotated per solution when shuffle_start) split greedily at Q; then
     n_random uniformly random relocations (customer, target route, position)."""
     nd, nc = inst.n_depots, inst.n_customers
-    xi = np.rint(inst.x).astype(np.int64)
-    yi = np.rint(inst.y).astype(np.int64)
     st = Stream(seed, 10, sol_index)
     routes: list[list[int]] = []
-    assign: dict[int, list[int]] = {d: [] for d in range(nd)}
-    for c in range(nd, nd + nc):
-        d2 = (xi[:nd] - xi[c]) ** 2 + (yi[:nd] - yi[c]) ** 2
-        assign[int(np.argmin(d2))].append(c)
+    sweeps = _depot_sweeps(inst)
     for d in range(nd):
-        cs = np.asarray(assign[d], dtype=np.int64)
-        if len(cs) == 0:
+        seq = list(sweeps[d])
+        if not seq:
             continue
-        order = _sweep_order(xi[cs] - xi[d], yi[cs] - yi[d], cs)
-        seq = [int(cs[i]) for i in order]
         if shuffle_start and len(seq) > 1:
             k = int(st.randint(0, len(seq) - 1, 1)[0])
             seq = seq[k:] + seq[:k]
