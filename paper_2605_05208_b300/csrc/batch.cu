@@ -33,6 +33,7 @@ struct md_batch {
     size_t smem;
     BatchItem *items_d;
     int *running_d;
+    int *next_tile_d;  // tile counter of the persistent evaluation launch
     uint8_t *perm_d;
     size_t perm_bytes;
     int total_sols;
@@ -109,6 +110,7 @@ extern "C" md_status md_batch_create(md_solutions *const *sols, int32_t n, md_ba
                      [&](int a, int c) { return sols[a]->inst->d.nc > sols[c]->inst->d.nc; });
     cudaError_t e = cudaMalloc(&b->items_d, sizeof(BatchItem) * n);
     if (e == cudaSuccess) e = cudaMalloc(&b->running_d, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&b->next_tile_d, sizeof(int));
     if (e != cudaSuccess) { cudaFree(b->items_d); delete b; return md_cuda_check(e, "md_batch_create"); }
     *out = b;
     return MD_OK;
@@ -118,6 +120,7 @@ extern "C" md_status md_batch_destroy(md_batch *b) {
     if (!b) return MD_OK;
     cudaFree(b->items_d);
     cudaFree(b->running_d);
+    cudaFree(b->next_tile_d);
     cudaFree(b->perm_d);
     delete b;
     return MD_OK;
@@ -149,7 +152,7 @@ md_status time_eval(md_batch *b, const std::vector<int> &order, int grid, int re
     MD_CUDA(cudaEventCreate(&e1));
     for (int k = 0; k < reps + 1; k++) {
         cudaEventRecord(e0, st);
-        r = md_launch_eval_batch(b->items_d, (int)v.size(), tiles, grid, b->tw, 0u, st);
+        r = md_launch_eval_batch(b->items_d, (int)v.size(), tiles, grid, b->tw, 0u, b->next_tile_d, st);
         cudaEventRecord(e1, st);
         if (r != MD_OK) break;
         cudaError_t ce = cudaEventSynchronize(e1);
@@ -248,7 +251,7 @@ extern "C" md_status md_batch_descend(md_batch *b, const md_config *cfg, md_stat
     const int steps = cfg->n_ops * poll;
     auto enqueue = [&]() -> md_status {
         for (int k = 0; k < steps; k++) {
-            md_status q = md_launch_eval_batch(b->items_d, b->n, tiles, b->grid, b->tw, eflags, st);
+            md_status q = md_launch_eval_batch(b->items_d, b->n, tiles, b->grid, b->tw, eflags, b->next_tile_d, st);
             if (q != MD_OK) return q;
             q = md_launch_step_batch(b->items_d, b->n, sols, b->smem, b->tw, st);
             if (q != MD_OK) return q;

@@ -572,14 +572,23 @@ __global__ void __launch_bounds__(256, MD_EVAL_MIN_BLOCKS) k_eval(DevInst I, Dev
 // TW_ANY: at least one item has time windows; items without them take the TW = false path.
 template <bool TW_ANY>
 __global__ void __launch_bounds__(256, MD_EVAL_MIN_BLOCKS) k_eval_batch(const BatchItem *__restrict__ items, int n_items, int total_tiles,
-                                                      uint32_t flags) {
+                                                      uint32_t flags, int *next_tile) {
     // Each warp keeps the context of its current tile in its own shared-memory slot: the
     // instance, solution and scratch descriptors are read from there when needed instead of
     // being held in registers.
+    // Tiles are claimed dynamically from a counter (zeroed before the launch), in work-list order:
+    // largest instances first, so the long tiles start early and the short ones fill the gaps.
     __shared__ Ctx cs[MD_EVAL_WARPS];
+    __shared__ int s_tile;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     Ctx &C = cs[warp];
-    for (int tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
+    int have_it = -1, have_s = -1;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_tile = atomicAdd(next_tile, 1);
+        __syncthreads();
+        const int tile = s_tile;
+        if (tile >= total_tiles) break;
         int it = 0;
         while (it + 1 < n_items && items[it + 1].tile_base <= tile) it++;
         const BatchItem &B = items[it];
@@ -587,7 +596,7 @@ __global__ void __launch_bounds__(256, MD_EVAL_MIN_BLOCKS) k_eval_batch(const Ba
         const int s = local / B.tiles_per_sol;
         const int t = local - s * B.tiles_per_sol;
         const int upw = B.upw;
-        if (lane == 0) {
+        if (lane == 0 && (it != have_it || s != have_s)) {
             C.I = B.I; C.D = B.D; C.M = B.M; C.flags = flags;
             C.s = s;
             C.open = (B.I.variant & MD_VARIANT_OPEN) != 0;
@@ -597,6 +606,8 @@ __global__ void __launch_bounds__(256, MD_EVAL_MIN_BLOCKS) k_eval_batch(const Ba
                 C.wf[k] = (float)C.w[k];
             }
         }
+        have_it = it;
+        have_s = s;
         __syncwarp();
         const int op = C.D.ops[s];
         Best b;
@@ -637,11 +648,12 @@ md_status md_launch_eval(md_solutions *s, md_moves *m, uint32_t flags, cudaStrea
 }
 
 md_status md_launch_eval_batch(const BatchItem *items, int n_items, int total_tiles, int grid, bool tw,
-                               uint32_t flags, cudaStream_t st) {
+                               uint32_t flags, int *next_tile, cudaStream_t st) {
     if (total_tiles <= 0) return MD_OK;
     if (grid < 1) grid = 1;
-    if (tw) k_eval_batch<true><<<grid, 32 * MD_EVAL_WARPS, 0, st>>>(items, n_items, total_tiles, flags);
-    else k_eval_batch<false><<<grid, 32 * MD_EVAL_WARPS, 0, st>>>(items, n_items, total_tiles, flags);
+    MD_CUDA(cudaMemsetAsync(next_tile, 0, sizeof(int), st));
+    if (tw) k_eval_batch<true><<<grid, 32 * MD_EVAL_WARPS, 0, st>>>(items, n_items, total_tiles, flags, next_tile);
+    else k_eval_batch<false><<<grid, 32 * MD_EVAL_WARPS, 0, st>>>(items, n_items, total_tiles, flags, next_tile);
     MD_CUDA(cudaGetLastError());
     return MD_OK;
 }

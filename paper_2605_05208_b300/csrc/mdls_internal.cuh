@@ -242,7 +242,7 @@ md_status md_launch_select(md_solutions *s, md_moves *m, int multi, cudaStream_t
 md_status md_launch_apply(md_solutions *s, md_moves *m, int update_lambda, cudaStream_t st);
 md_status md_launch_step(md_solutions *s, md_moves *m, cudaStream_t st, int s0 = 0, int count = -1);
 md_status md_launch_eval_batch(const BatchItem *items, int n_items, int total_tiles, int grid, bool tw,
-                               uint32_t flags, cudaStream_t st);
+                               uint32_t flags, int *next_tile, cudaStream_t st);
 md_status md_launch_step_batch(const BatchItem *items, int n_items, int total_sols, size_t smem, bool tw,
                                cudaStream_t st);
 size_t md_step_smem(const md_solutions *s);
