@@ -127,6 +127,9 @@ typedef struct md_config {
     int32_t time_eval;      /* 1: time every evaluation launch with CUDA events (md_stats.eval_ms) */
     int32_t n_groups;       /* > 1: solutions advance in this many groups on concurrent streams
                                (needs a non-NULL stream); results do not depend on it */
+    int32_t sweep_every;    /* > 0: every sweep_every-th step of a solution evaluates the full
+                               neighbourhood (all customers) instead of the neighbour lists; the
+                               fallback of pruned lists.  0: never */
 } md_config;
 
 /* Totals over all solutions of one md_descend call. */
@@ -163,6 +166,16 @@ md_status md_instance_read_dist(const md_instance *inst, int32_t *host_out);
 /* Copies the neighbour lists: host_nbr [n_customers * theta] node ids (row = customer index),
  * host_cnt [n_customers] list lengths.  MD_ERR_STATE when theta = 0. */
 md_status md_instance_read_neighbors(const md_instance *inst, int32_t *host_nbr, int32_t *host_cnt);
+
+/* Recomputes the granular neighbour lists with a new width theta (ranking of
+ * md_instance_create, Section 3.2.3 / Eq. 3); theta = 0 switches to the full neighbourhood.  Takes
+ * effect for evaluations launched afterwards. */
+md_status md_instance_build_neighbors(md_instance *inst, int32_t theta);
+
+/* Installs caller-chosen neighbour lists: nbr [n_customers * theta] node ids (row = customer
+ * index), cnt [n_customers] list lengths (<= theta).  Every entry must be a customer other than
+ * the row's own (MD_ERR_ARG otherwise).  Used for learned candidate lists. */
+md_status md_instance_set_neighbors(md_instance *inst, const int32_t *nbr, const int32_t *cnt, int32_t theta);
 
 /* Allocates n_sol solutions of the instance, each with r_slots route slots of up to k_max
  * customers.  A route slot holds one route [ds, c_1..c_L, de] (Eq. 1 notation) with its

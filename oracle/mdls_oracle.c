@@ -150,6 +150,20 @@ OInst *or_inst_new(int nd, int nc, const double *x, const double *y, const int32
     return I;
 }
 
+/* Replaces the neighbour lists by caller-chosen ones (learned candidate lists); theta = 0 means
+   every other customer. */
+void or_inst_set_nbrs(OInst *I, const int32_t *nbr, const int32_t *cnt, int theta) {
+    free(I->nbr);
+    free(I->nnbr);
+    I->theta = theta;
+    I->nnbr = (int32_t *)calloc(I->nc > 0 ? I->nc : 1, sizeof(int32_t));
+    I->nbr = (int32_t *)calloc((size_t)(I->nc > 0 ? I->nc : 1) * (theta > 0 ? theta : 1), sizeof(int32_t));
+    if (theta > 0) {
+        memcpy(I->nbr, nbr, sizeof(int32_t) * (size_t)I->nc * theta);
+        memcpy(I->nnbr, cnt, sizeof(int32_t) * I->nc);
+    }
+}
+
 void or_inst_free(OInst *I) {
     if (!I) return;
     free(I->c); free(I->q); free(I->s); free(I->e); free(I->l); free(I->nbr); free(I->nnbr);
@@ -616,7 +630,8 @@ static int n_variants(int op) {
 /* Enumerates the operator's neighbourhood.  Every valid move is written when out != NULL and
    there is room; returns the number of valid moves.  *n_scored counts the scored tuples (each
    valid Depot-Replace case counts once). */
-static int64_t enumerate(OCtx *C, int op, const double *w, OMove *out, int64_t cap, int64_t *n_scored) {
+static int64_t enumerate(OCtx *C, int op, const double *w, OMove *out, int64_t cap, int64_t *n_scored,
+                         int full) {
     const OInst *I = C->I;
     const OSol *S = C->S;
     int64_t n = 0, scored = 0;
@@ -626,9 +641,10 @@ static int64_t enumerate(OCtx *C, int op, const double *w, OMove *out, int64_t c
         int nv = n_variants(op);
         for (int cu = 0; cu < I->nc; cu++) {
             int u = I->nd + cu;
-            int cnt = I->theta > 0 ? I->nnbr[cu] : I->nc;
+            const int lists = I->theta > 0 && !full;  /* full: every other customer */
+            int cnt = lists ? I->nnbr[cu] : I->nc;
             for (int t = 0; t < cnt; t++) {
-                int v = I->theta > 0 ? I->nbr[(size_t)cu * I->theta + t] : I->nd + t;
+                int v = lists ? I->nbr[(size_t)cu * I->theta + t] : I->nd + t;
                 if (v == u) continue;
                 for (int var = 0; var < nv; var++) {
                     if (!build_move(C, op, u, v, var, &B)) continue;
@@ -678,7 +694,7 @@ int64_t or_eval_op(const OInst *I, const int32_t *nodes, const int64_t *off, int
     ctx_init(&C, I, S);
     double w[4];
     weights(I, lam, w);
-    int64_t n = enumerate(&C, op, w, out, cap, n_scored);
+    int64_t n = enumerate(&C, op, w, out, cap, n_scored, 0);
     ctx_free(&C);
     sol_free(S);
     return n;
@@ -831,11 +847,12 @@ typedef struct {
 } OStats;
 
 /* MDFIS (Alg. 2): repeat passes over the operators in the given order per pass until a pass
-   applies nothing or max_pass passes ran.  perm is [max_pass * n_ops] operator indices. */
+   applies nothing or max_pass passes ran.  perm is [max_pass * n_ops] operator indices.
+   sweep_every > 0: every sweep_every-th step evaluates all customers instead of the lists. */
 int or_descend(const OInst *I, const int32_t *nodes, const int64_t *off, int nr,
                const uint8_t *perm, int n_ops, int max_pass, int multi, int lambda_update,
                float *lam, int32_t *out_nodes, int64_t *out_off, int64_t node_cap, int route_cap,
-               OStats *st, double *trace_F, int trace_cap) {
+               OStats *st, double *trace_F, int trace_cap, int sweep_every) {
     OSol *S = sol_from_flat(nodes, off, nr);
     memset(st, 0, sizeof(*st));
     int64_t cap = 1 << 16;
@@ -851,12 +868,13 @@ int or_descend(const OInst *I, const int32_t *nodes, const int64_t *off, int nr,
             double w[4];
             weights(I, lam, w);
             int64_t scored = 0;
-            int64_t n = enumerate(&C, op, w, mv, cap, &scored);
+            const int full = sweep_every > 0 && (st->steps + 1) % sweep_every == 0;
+            int64_t n = enumerate(&C, op, w, mv, cap, &scored, full);
             if (n > cap) {
                 free(mv);
                 cap = n;
                 mv = (OMove *)malloc(sizeof(OMove) * cap);
-                n = enumerate(&C, op, w, mv, cap, &scored);
+                n = enumerate(&C, op, w, mv, cap, &scored, full);
             }
             ctx_free(&C);
             st->moves_scored += scored;

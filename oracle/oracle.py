@@ -87,7 +87,9 @@ def lib():
         L.or_update_lambda.argtypes = [P, i32p, i64p, C.c_int, f32p]
         L.or_descend.restype = C.c_int
         L.or_descend.argtypes = [P, i32p, i64p, C.c_int, u8p, C.c_int, C.c_int, C.c_int, C.c_int,
-                                 f32p, i32p, i64p, C.c_int64, C.c_int, C.POINTER(OStats), P, C.c_int]
+                                 f32p, i32p, i64p, C.c_int64, C.c_int, C.POINTER(OStats), P, C.c_int,
+                                 C.c_int]
+        L.or_inst_set_nbrs.argtypes = [P, i32p, i32p, C.c_int]
         _lib = L
     return _lib
 
@@ -159,7 +161,7 @@ class Instance:
         return float(lib().or_inst_Gamma(self.h))
 
     def neighbors(self):
-        th = max(self.spec.theta, 0)
+        th = max(getattr(self, "theta", self.spec.theta), 0)
         out = np.zeros(max(self.nc * th, 1), dtype=np.int32)
         cnt = np.zeros(self.nc, dtype=np.int32)
         lib().or_inst_nbrs(self.h, out, cnt)
@@ -217,8 +219,17 @@ class Instance:
         lib().or_update_lambda(self.h, nodes, off, len(sol), lamv)
         return lamv
 
+    def set_neighbors(self, nbr, cnt):
+        """Installs caller-chosen neighbour lists (nbr [nc, theta] node ids, cnt [nc])."""
+        nbr = np.ascontiguousarray(nbr, dtype=np.int32)
+        cnt = np.ascontiguousarray(cnt, dtype=np.int32)
+        theta = nbr.shape[1] if nbr.ndim == 2 else 0
+        lib().or_inst_set_nbrs(self.h, nbr.reshape(-1) if theta else np.zeros(1, np.int32),
+                               cnt if theta else np.zeros(max(self.nc, 1), np.int32), theta)
+        self.theta = theta
+
     def descend(self, sol, perm, max_pass, multi=True, lambda_update=False, lam=(1, 1, 1, 1),
-                trace=False) -> Descent:
+                trace=False, sweep_every=0) -> Descent:
         """MDFIS descent (Alg. 2) of one solution; perm is uint8 [max_pass, n_ops]."""
         nodes, off = _flat(sol)
         perm = np.ascontiguousarray(perm, dtype=np.uint8)
@@ -233,7 +244,8 @@ class Instance:
         tr = np.zeros(max(tcap, 1), dtype=np.float64)
         nr = lib().or_descend(self.h, nodes, off, len(sol), perm.reshape(-1), n_ops, max_pass,
                               int(multi), int(lambda_update), lamv, on, oo, cap_n, cap_r,
-                              C.byref(st), tr.ctypes.data_as(C.c_void_p) if trace else None, tcap)
+                              C.byref(st), tr.ctypes.data_as(C.c_void_p) if trace else None, tcap,
+                              int(sweep_every))
         assert nr >= 0
         ntr = min(int(st.steps), tcap)
         return Descent(_unflat(on, oo, nr), int(st.moves_scored), int(st.steps),

@@ -33,20 +33,21 @@ __global__ void k_leaders(DevSols D, DevMoves M, unsigned long long *ids, double
         f = 0.0; id = 0xffffffffu; valid = 0;
         for (int k = 0; k < (int)(blockDim.x + 31) / 32; k++)
             if (lv[k] && (!valid || lf[k] < f || (lf[k] == f && lid[k] < id))) { f = lf[k]; id = lid[k]; valid = 1; }
-        ids[s] = valid ? (((unsigned long long)D.ops[s] << 32) | id) : 0ull;
+        ids[s] = valid ? (((unsigned long long)(D.ops[s] & MD_OP_MASK) << 32) | id) : 0ull;
         fs[s] = valid ? f : 0.0;
     }
 }
 
 // Descent start: counters cleared, first operator of pass 0 for every solution.
-__global__ void k_descend_init(DevSols D, int n_ops, int max_pass, int multi, int lup) {
+__global__ void k_descend_init(DevSols D, int n_ops, int max_pass, int multi, int lup, int sweep) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= D.S) return;
-    int *st = D.state + (size_t)s * 8;
+    int *st = D.state + (size_t)s * MD_STATE;
     st[0] = 0; st[1] = 0; st[2] = 0; st[3] = 0;
     st[4] = n_ops; st[5] = max_pass; st[6] = multi; st[7] = lup;
+    st[8] = sweep; st[9] = 0;
     for (int k = 0; k < 16; k++) D.stats[(size_t)s * 16 + k] = 0;
-    D.ops[s] = (int)D.perm[(size_t)s * max_pass * n_ops];
+    D.ops[s] = (int)D.perm[(size_t)s * max_pass * n_ops] | (sweep == 1 ? MD_OP_SWEEP : 0);
 }
 
 __global__ void k_set_ops(DevSols D, const int32_t *ops) {
@@ -237,7 +238,7 @@ extern "C" md_status md_selection_read(md_moves *m, uint64_t *ids, int32_t *coun
     for (int i = 0; i < S; i++) {
         if (counts[i] > cap) { r = MD_ERR_CAPACITY; md_set_error("md_selection_read: cap %d < %d selected", cap, counts[i]); }
         for (int k = 0; k < counts[i] && k < cap; k++)
-            ids[(size_t)i * cap + k] = ((uint64_t)(uint32_t)ops[i] << 32) | sel[(size_t)i * R + k];
+            ids[(size_t)i * cap + k] = ((uint64_t)(uint32_t)(ops[i] & MD_OP_MASK) << 32) | sel[(size_t)i * R + k];
     }
     return r;
 }
@@ -301,7 +302,7 @@ md_status md_descend_prepare(md_solutions *s, const md_config *cfg, const uint8_
     MD_CUDA(cudaMemsetAsync(m->d.fcount, 0, sizeof(uint32_t) * s->n_sol, st));
     MD_CUDA(cudaMemsetAsync(m->d.nscored, 0, sizeof(unsigned long long) * s->n_sol, st));
     k_descend_init<<<(s->n_sol + 127) / 128, 128, 0, st>>>(s->d, cfg->n_ops, cfg->max_pass, cfg->multi_move ? 1 : 0,
-                                                         cfg->lambda_update ? 1 : 0);
+                                                         cfg->lambda_update ? 1 : 0, cfg->sweep_every > 0 ? cfg->sweep_every : 0);
     MD_CUDA(cudaGetLastError());
     ++*launches;
     return MD_OK;
@@ -391,7 +392,7 @@ extern "C" md_status md_descend(md_solutions *s, const md_config *cfg, md_stats 
         }
         return MD_OK;
     };
-    std::vector<int32_t> state((size_t)s->n_sol * 8);
+    std::vector<int32_t> state((size_t)s->n_sol * MD_STATE);
     cudaGraphExec_t exec = nullptr;
     cudaGraph_t graph = nullptr;
     const bool use_graph = cfg->use_graph && st != nullptr;
@@ -419,7 +420,7 @@ extern "C" md_status md_descend(md_solutions *s, const md_config *cfg, md_stats 
         launches += 2LL * steps_per_poll * G;
         eval_launches += (long long)steps_per_poll * G;
         passes_done += poll;
-        cudaError_t ce = cudaMemcpyAsync(state.data(), s->d.state, sizeof(int32_t) * 8 * s->n_sol, cudaMemcpyDeviceToHost, st);
+        cudaError_t ce = cudaMemcpyAsync(state.data(), s->d.state, sizeof(int32_t) * MD_STATE * s->n_sol, cudaMemcpyDeviceToHost, st);
         if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
         if (ce != cudaSuccess) { rr = md_cuda_check(ce, "md_descend poll"); break; }
         for (size_t k = 0; k < ev.size() / 2; k++) {
@@ -430,7 +431,7 @@ extern "C" md_status md_descend(md_solutions *s, const md_config *cfg, md_stats 
         }
         if (ce != cudaSuccess) { rr = md_cuda_check(ce, "cudaEventElapsedTime"); break; }
         all_done = true;
-        for (int i = 0; i < s->n_sol; i++) all_done &= state[(size_t)i * 8 + 3] != 0;
+        for (int i = 0; i < s->n_sol; i++) all_done &= state[(size_t)i * MD_STATE + 3] != 0;
     }
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);

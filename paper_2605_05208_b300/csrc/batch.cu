@@ -18,7 +18,7 @@ __global__ void k_batch_running(const BatchItem *items, int n_items, int total_s
     int it = 0;
     while (it + 1 < n_items && items[it + 1].sol_base <= g) it++;
     const int s = g - items[it].sol_base;
-    if (!items[it].D.state[(size_t)s * 8 + 3]) atomicAdd(running, 1);
+    if (!items[it].D.state[(size_t)s * MD_STATE + 3]) atomicAdd(running, 1);
 }
 
 }  // namespace

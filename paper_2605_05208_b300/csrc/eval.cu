@@ -44,6 +44,7 @@ struct Ctx {
     double w[4];
     float wf[4];
     bool open, sym;
+    bool lists;  // candidates from the neighbour lists (theta > 0 and not a full-sweep step)
 };
 
 __device__ __forceinline__ int cost(const DevInst &I, int a, int b) {
@@ -143,7 +144,7 @@ __device__ __forceinline__ void offer(const Ctx &C, uint32_t id, int dD, int dTW
         const unsigned long long k = atomicAdd(C.M.dump_n, 1ull);
         if ((long long)k < C.M.dump_cap) {
             md_move m;
-            m.id = ((uint64_t)C.D.ops[C.s] << 32) | id;
+            m.id = ((uint64_t)(C.D.ops[C.s] & MD_OP_MASK) << 32) | id;
             m.dD = dD; m.dTW = dTW; m.dLoad = dL; m.dDur = dU; m.dV4 = dV;
             m.dF = f;
             m.sol = C.s;
@@ -232,9 +233,9 @@ __device__ void eval_relocate(const Ctx &C, int cu, int lane, Best &b) {
     const Seg q1 = nseg(C, u);
     const int dV_empty = ((!C.open && dsA != deA) ? -1 : 0) +
                          veh_delta(C.D.dcount[(size_t)C.s * I.nd + dsA], I.NV, -1);
-    const int ncand = I.theta > 0 ? I.nnbr[cu] : I.nc;
+    const int ncand = C.lists ? I.nnbr[cu] : I.nc;
     for (int i = lane; i < ncand; i += 32) {
-        const int v = I.theta > 0 ? __ldg(&I.nbr[(size_t)cu * I.theta + i]) : I.nd + i;
+        const int v = C.lists ? __ldg(&I.nbr[(size_t)cu * I.theta + i]) : I.nd + i;
         if (v == u) continue;
         const Seg8 Pv = pre8(C, v), Sv = suf8(C, v);
         const int B = Pv.a, j = Pv.b, sv = Sv.b;
@@ -326,9 +327,9 @@ __device__ void eval_swap(const Ctx &C, int cu, int lane, Best &b) {
         u2r = join<TW>(C, nseg(C, x), x, nseg(C, u), u);
     }
     const int nvar = C.sym ? 9 : 4;
-    const int ncand = I.theta > 0 ? I.nnbr[cu] : I.nc;
+    const int ncand = C.lists ? I.nnbr[cu] : I.nc;
     for (int i = lane; i < ncand; i += 32) {
-        const int v = I.theta > 0 ? __ldg(&I.nbr[(size_t)cu * I.theta + i]) : I.nd + i;
+        const int v = C.lists ? __ldg(&I.nbr[(size_t)cu * I.theta + i]) : I.nd + i;
         if (v == u) continue;
         const Seg8 Pv = pre8(C, v), Sv = suf8(C, v);
         const int B = Pv.a, j = Pv.b, pv = Sv.a, sv = Sv.b;
@@ -406,9 +407,9 @@ __device__ void eval_2optstar(const Ctx &C, int cu, int lane, Best &b) {
     const RT oldA = rt_of(seg_of(ldg_seg8(&C.D.rterm[sA])), I);
     const Seg PU = seg_of(Pu);
     const bool u_last = su < I.nd;  // depot or MD_NONE after u
-    const int ncand = I.theta > 0 ? I.nnbr[cu] : I.nc;
+    const int ncand = C.lists ? I.nnbr[cu] : I.nc;
     for (int i = lane; i < ncand; i += 32) {
-        const int v = I.theta > 0 ? __ldg(&I.nbr[(size_t)cu * I.theta + i]) : I.nd + i;
+        const int v = C.lists ? __ldg(&I.nbr[(size_t)cu * I.theta + i]) : I.nd + i;
         if (v == u) continue;
         const Seg8 Pv = pre8(C, v), Sv = suf8(C, v);
         const int B = Pv.a, pv = Sv.a;
@@ -558,7 +559,9 @@ __global__ void __launch_bounds__(256, MD_EVAL_MIN_BLOCKS) k_eval(DevInst I, Dev
         C.w[k] = D.w[4 * C.s + k];
         C.wf[k] = (float)C.w[k];
     }
-    const int op = D.ops[C.s];
+    const int op_raw = D.ops[C.s];
+    const int op = op_raw < 0 ? -1 : (op_raw & MD_OP_MASK);
+    C.lists = I.theta > 0 && !(op_raw >= 0 && (op_raw & MD_OP_SWEEP));
     Best b;
     best_init(b);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
@@ -609,7 +612,10 @@ __global__ void __launch_bounds__(256, MD_EVAL_MIN_BLOCKS) k_eval_batch(const Ba
         have_it = it;
         have_s = s;
         __syncwarp();
-        const int op = C.D.ops[s];
+        const int op_raw = C.D.ops[s];
+        const int op = op_raw < 0 ? -1 : (op_raw & MD_OP_MASK);
+        if (lane == 0) C.lists = C.I.theta > 0 && !(op_raw >= 0 && (op_raw & MD_OP_SWEEP));
+        __syncwarp();
         Best b;
         best_init(b);
         const int ws = t * MD_EVAL_WARPS + warp;  // warp slot within the solution

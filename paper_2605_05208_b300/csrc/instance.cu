@@ -260,3 +260,63 @@ extern "C" md_status md_instance_read_neighbors(const md_instance *I, int32_t *h
     MD_CUDA(cudaMemcpy(host_cnt, I->nnbr, sizeof(int32_t) * I->d.nc, cudaMemcpyDeviceToHost));
     return MD_OK;
 }
+
+// Neighbour lists of width theta in (re)allocated device buffers.
+static md_status ensure_lists(md_instance *I, int theta) {
+    if (theta == I->d.theta && I->nbr) return MD_OK;
+    cudaFree(I->nbr);
+    cudaFree(I->nnbr);
+    I->nbr = nullptr;
+    I->nnbr = nullptr;
+    I->d.nbr = nullptr;
+    I->d.nnbr = nullptr;
+    I->d.theta = 0;
+    if (theta == 0) return MD_OK;
+    MD_CUDA(cudaMalloc(&I->nbr, sizeof(int32_t) * (size_t)I->d.nc * theta));
+    MD_CUDA(cudaMalloc(&I->nnbr, sizeof(int32_t) * I->d.nc));
+    I->d.nbr = I->nbr;
+    I->d.nnbr = I->nnbr;
+    I->d.theta = theta;
+    return MD_OK;
+}
+
+extern "C" md_status md_instance_build_neighbors(md_instance *I, int32_t theta) {
+    if (!I || theta < 0) { md_set_error("md_instance_build_neighbors: invalid argument"); return MD_ERR_ARG; }
+    md_status r = ensure_lists(I, theta);
+    if (r != MD_OK) return r;
+    if (theta == 0) return MD_OK;
+    const int nc = I->d.nc;
+    int P = 1;
+    while (P < nc) P <<= 1;
+    size_t sm = (size_t)P * (sizeof(unsigned long long) + sizeof(int));
+    MD_CUDA(cudaFuncSetAttribute(k_nbrs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_nbrs<<<nc, 1024, sm>>>(I->d, P, I->nbr, I->nnbr);
+    MD_CUDA(cudaGetLastError());
+    MD_CUDA(cudaDeviceSynchronize());
+    return MD_OK;
+}
+
+extern "C" md_status md_instance_set_neighbors(md_instance *I, const int32_t *nbr, const int32_t *cnt, int32_t theta) {
+    if (!I || theta < 0 || (theta > 0 && (!nbr || !cnt))) {
+        md_set_error("md_instance_set_neighbors: invalid argument");
+        return MD_ERR_ARG;
+    }
+    const int nd = I->d.nd, nc = I->d.nc;
+    for (int cu = 0; cu < nc && theta > 0; cu++) {
+        if (cnt[cu] < 0 || cnt[cu] > theta) { md_set_error("md_instance_set_neighbors: bad count for customer %d", cu); return MD_ERR_ARG; }
+        for (int i = 0; i < cnt[cu]; i++) {
+            const int v = nbr[(size_t)cu * theta + i];
+            if (v < nd || v >= nd + nc || v == nd + cu) {
+                md_set_error("md_instance_set_neighbors: customer %d lists invalid neighbour %d", cu, v);
+                return MD_ERR_ARG;
+            }
+        }
+    }
+    md_status r = ensure_lists(I, theta);
+    if (r != MD_OK) return r;
+    if (theta == 0) return MD_OK;
+    MD_CUDA(cudaMemcpy(I->nbr, nbr, sizeof(int32_t) * (size_t)nc * theta, cudaMemcpyHostToDevice));
+    MD_CUDA(cudaMemcpy(I->nnbr, cnt, sizeof(int32_t) * nc, cudaMemcpyHostToDevice));
+    return MD_OK;
+}
+

@@ -27,6 +27,9 @@
 #define MD_MAX_OPS 8
 #define MD_EMPTY_KEY 0xFFFFFFFFFFFFFFFFull
 #define MD_EVAL_WARPS 8  // warps per evaluation block; one leader record per warp
+#define MD_STATE 16      // ints of per-solution descent state
+#define MD_OP_SWEEP 0x100  // set in ops[s]: this step evaluates the full neighbourhood
+#define MD_OP_MASK 0xff
 
 struct __align__(16) Seg8 {
     int dist, load, dur, tw, E, L, a, b;
@@ -63,7 +66,8 @@ struct DevSols {
     float *lam;
     double *w;
     int32_t *ops;      // [S] operator of the current step (-1 = none)
-    int32_t *state;    // [S * 8] pass, slot, improved, done, n_ops, max_pass, multi, lambda_update
+    int32_t *state;    // [S * 16] pass, slot, improved, done, n_ops, max_pass, multi, lambda_update,
+                       // sweep period (0: never), step index
     long long *stats;  // [S * 16] moves scored, steps, accepted, applied, passes; [8+op] moves per op
     int32_t *err;      // [1] first error code raised on the device
     const uint8_t *perm; // [S * max_pass * n_ops] operator order (descent only)

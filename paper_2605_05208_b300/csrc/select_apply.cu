@@ -76,7 +76,7 @@ __device__ int select_moves(const DevInst &I, const DevSols &D, const DevMoves &
         s_ncand = 0;
         if (valid) {
             int rA, rB;
-            move_routes(I, D, s, D.ops[s], id, rA, rB);
+            move_routes(I, D, s, D.ops[s] & MD_OP_MASK, id, rA, rB);
             s_rA = rA; s_rB = rB;
             M.sel[(size_t)s * R] = id;
             s_n = 1;
@@ -314,7 +314,7 @@ __device__ void apply_selection(const DevInst &I, const DevSols &D, const DevMov
                                 const StepSmem &sm) {
     __shared__ int s_nfree, s_ntouch;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
-    const int R = D.R, op = D.ops[s];
+    const int R = D.R, op = D.ops[s] & MD_OP_MASK;
     const uint32_t *sel = M.sel + (size_t)s * R;
     if (tid == 0) { s_nfree = 0; s_ntouch = 0; }
     __syncthreads();
@@ -385,7 +385,7 @@ template <bool TW>
 __device__ void step_body(const DevInst &I, const DevSols &D, const DevMoves &M, int s, int nrec) {
     extern __shared__ __align__(16) unsigned char smem[];
     const StepSmem sm = carve(smem, D.R, I.nd, D.K, blockDim.x >> 5);
-    int *st = D.state + (size_t)s * 8;
+    int *st = D.state + (size_t)s * MD_STATE;
     if (st[3]) return;
     const int n_ops = st[4], max_pass = st[5], multi = st[6], lup = st[7];
     const int nsel = select_moves(I, D, M, s, multi, sm, nrec);
@@ -396,7 +396,7 @@ __device__ void step_body(const DevInst &I, const DevSols &D, const DevMoves &M,
     if (threadIdx.x == 0) {
         long long *stt = D.stats + (size_t)s * 16;
         stt[0] += (long long)M.nscored[s];
-        stt[8 + D.ops[s]] += (long long)M.nscored[s];
+        stt[8 + (D.ops[s] & MD_OP_MASK)] += (long long)M.nscored[s];
         M.nscored[s] = 0;
         stt[1] += 1;
         if (nsel > 0) { stt[2] += 1; stt[3] += nsel; st[2] = 1; }
@@ -410,7 +410,10 @@ __device__ void step_body(const DevInst &I, const DevSols &D, const DevMoves &M,
         }
         st[0] = pass;
         st[1] = slot;
-        D.ops[s] = st[3] ? -1 : (int)D.perm[((size_t)s * max_pass + pass) * n_ops + slot];
+        // full plain sweep on every sweep-th step (st[8] = period, st[9] = steps done)
+        const int step = ++st[9];
+        const bool sweep = st[8] > 0 && (step + 1) % st[8] == 0;
+        D.ops[s] = st[3] ? -1 : ((int)D.perm[((size_t)s * max_pass + pass) * n_ops + slot] | (sweep ? MD_OP_SWEEP : 0));
     }
 }
 

@@ -114,12 +114,12 @@ extern "C" md_status md_solutions_create(const md_instance *inst, int32_t n_sol,
     MDA(cudaMalloc(&d.lam, sizeof(float) * (size_t)n_sol * 4));
     MDA(cudaMalloc(&d.w, sizeof(double) * (size_t)n_sol * 4));
     MDA(cudaMalloc(&d.ops, sizeof(int32_t) * n_sol));
-    MDA(cudaMalloc(&d.state, sizeof(int32_t) * (size_t)n_sol * 8));
+    MDA(cudaMalloc(&d.state, sizeof(int32_t) * (size_t)n_sol * MD_STATE));
     MDA(cudaMalloc(&d.stats, sizeof(long long) * (size_t)n_sol * 16));
     MDA(cudaMalloc(&d.err, sizeof(int32_t)));
     MDA(cudaMemset(d.rhdr, 0, sizeof(int4) * SR));
     MDA(cudaMemset(d.ops, 0xff, sizeof(int32_t) * n_sol));
-    MDA(cudaMemset(d.state, 0, sizeof(int32_t) * (size_t)n_sol * 8));
+    MDA(cudaMemset(d.state, 0, sizeof(int32_t) * (size_t)n_sol * MD_STATE));
     MDA(cudaMemset(d.stats, 0, sizeof(long long) * (size_t)n_sol * 16));
     MDA(cudaMemset(d.err, 0, sizeof(int32_t)));
     MDA(cudaMemset(d.tot, 0, sizeof(long long) * (size_t)n_sol * 8));
@@ -147,7 +147,7 @@ static md_status finish_load(md_solutions *S, cudaStream_t st) {
     k_fill_lambda<<<(S->n_sol * 4 + 255) / 256, 256, 0, st>>>(S->d, 1.0f);
     MD_CUDA(cudaGetLastError());
     MD_CUDA(cudaMemsetAsync(S->d.ops, 0xff, sizeof(int32_t) * S->n_sol, st));
-    MD_CUDA(cudaMemsetAsync(S->d.state, 0, sizeof(int32_t) * (size_t)S->n_sol * 8, st));
+    MD_CUDA(cudaMemsetAsync(S->d.state, 0, sizeof(int32_t) * (size_t)S->n_sol * MD_STATE, st));
     MD_CUDA(cudaMemsetAsync(S->d.err, 0, sizeof(int32_t), st));
     md_status r = md_launch_rebuild_all(S, st);
     if (r != MD_OK) return r;

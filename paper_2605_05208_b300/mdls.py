@@ -32,7 +32,8 @@ EXPORTED = (
     "md_moves_destroy", "md_eval_neighborhood", "md_moves_read_leaders", "md_moves_read_dump",
     "md_select_multimove", "md_selection_read", "md_apply_and_rebuild", "md_descend",
     "md_solutions_stats", "md_eval_leaders_noalloc", "md_batch_create", "md_batch_destroy",
-    "md_batch_tune", "md_batch_tuning", "md_batch_descend",
+    "md_batch_tune", "md_batch_tuning", "md_batch_descend", "md_instance_build_neighbors",
+    "md_instance_set_neighbors",
 )
 
 
@@ -66,7 +67,8 @@ class Config(C.Structure):
     _fields_ = [("n_ops", C.c_int32), ("max_pass", C.c_int32), ("op_perm", C.POINTER(C.c_uint8)),
                 ("lambda0", C.POINTER(C.c_float)), ("multi_move", C.c_int32),
                 ("lambda_update", C.c_int32), ("use_graph", C.c_int32), ("poll_every", C.c_int32),
-                ("op_perm_device", C.c_int32), ("time_eval", C.c_int32), ("n_groups", C.c_int32)]
+                ("op_perm_device", C.c_int32), ("time_eval", C.c_int32), ("n_groups", C.c_int32),
+                ("sweep_every", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -113,6 +115,8 @@ def lib() -> C.CDLL:
             "md_descend": [P, C.POINTER(Config), C.POINTER(Stats), P],
             "md_solutions_stats": [P, P, P],
             "md_eval_leaders_noalloc": [P, P, P, P, P, P],
+            "md_instance_build_neighbors": [P, C.c_int32],
+            "md_instance_set_neighbors": [P, P, P, C.c_int32],
             "md_batch_create": [P, C.c_int32, PP],
             "md_batch_destroy": [P],
             "md_batch_tune": [P, P],
@@ -184,8 +188,19 @@ class Instance:
         _check(lib().md_instance_read_dist(self.h, _ptr(out)))
         return out.reshape(self.nn, self.nn)
 
+    def build_neighbors(self, theta: int):
+        _check(lib().md_instance_build_neighbors(self.h, int(theta)))
+        self.theta = int(theta)
+
+    def set_neighbors(self, nbr, cnt):
+        nbr = np.ascontiguousarray(nbr, dtype=np.int32)
+        cnt = np.ascontiguousarray(cnt, dtype=np.int32)
+        theta = nbr.shape[1] if nbr.ndim == 2 else 0
+        _check(lib().md_instance_set_neighbors(self.h, _ptr(nbr), _ptr(cnt), theta))
+        self.theta = theta
+
     def neighbors(self):
-        th = self.spec.theta
+        th = getattr(self, "theta", self.spec.theta)
         nb = np.zeros(self.nc * th, dtype=np.int32)
         cnt = np.zeros(self.nc, dtype=np.int32)
         _check(lib().md_instance_read_neighbors(self.h, _ptr(nb), _ptr(cnt)))
@@ -288,7 +303,8 @@ class Solutions:
 
     def descend(self, perm, max_pass: int, multi: bool = True, lambda_update: bool = False,
                 lambda0=None, use_graph: bool = False, poll_every: int = 1, stream=None,
-                n_ops: int | None = None, time_eval: bool = False, n_groups: int = 1) -> DescendStats:
+                n_ops: int | None = None, time_eval: bool = False, n_groups: int = 1,
+                sweep_every: int = 0) -> DescendStats:
         """MDFIS descent.  perm: uint8 host array [n_sol, >= max_pass, n_ops], or an int device
         pointer to a [n_sol, max_pass, n_ops] uint8 buffer (then n_ops must be given)."""
         if isinstance(perm, int):
@@ -304,7 +320,7 @@ class Solutions:
         cfg = Config(n_ops, max_pass, pptr,
                      lam.ctypes.data_as(C.POINTER(C.c_float)) if lam is not None else None,
                      int(multi), int(lambda_update), int(use_graph), int(poll_every), on_dev,
-                     int(time_eval), int(n_groups))
+                     int(time_eval), int(n_groups), int(sweep_every))
         st = Stats()
         _check(lib().md_descend(self.h, C.byref(cfg), C.byref(st), _stream(stream)))
         return DescendStats(st.moves_scored, st.steps, st.accepted_steps, st.applied_moves,
@@ -402,7 +418,7 @@ class Batch:
 
     def descend(self, perm, max_pass: int, multi: bool = True, lambda_update: bool = False,
                 use_graph: bool = True, poll_every: int = 1, stream=None, n_ops: int | None = None,
-                time_eval: bool = False) -> DescendStats:
+                time_eval: bool = False, sweep_every: int = 0) -> DescendStats:
         """perm: uint8 host array [sum n_sol, >= max_pass, n_ops] in the order the solution sets
         were given, or an int device pointer (then n_ops must be given)."""
         if isinstance(perm, int):
@@ -413,7 +429,7 @@ class Batch:
             n_ops = perm.shape[2]
             pptr, on_dev = perm.ctypes.data_as(C.POINTER(C.c_uint8)), 0
         cfg = Config(n_ops, max_pass, pptr, None, int(multi), int(lambda_update), int(use_graph),
-                     int(poll_every), on_dev, int(time_eval), 1)
+                     int(poll_every), on_dev, int(time_eval), 1, int(sweep_every))
         st = Stats()
         _check(lib().md_batch_descend(self.h, C.byref(cfg), C.byref(st), _stream(stream)))
         return DescendStats(st.moves_scored, st.steps, st.accepted_steps, st.applied_moves,

@@ -39,3 +39,18 @@ def random_solution(spec, seed, max_len=4):
         routes.append([ds] + order[i:i + k] + [de])
         i += k
     return routes
+
+
+def random_neighbor_lists(spec, k, seed):
+    """k distinct random other customers per customer (seeded), as [nc, k] node ids and counts."""
+    st = W.Stream(seed, 55)
+    nd, nc = spec.n_depots, spec.n_customers
+    k = min(k, nc - 1)
+    nbr = np.zeros((nc, max(k, 1)), dtype=np.int32)
+    for cu in range(nc):
+        others = [v for v in range(nd, nd + nc) if v != nd + cu]
+        keys = st.u64(len(others))
+        order = [v for _, v in sorted(zip(keys.tolist(), others))]
+        nbr[cu, :k] = order[:k]
+    return nbr[:, :k], np.full(nc, k, dtype=np.int32)
+

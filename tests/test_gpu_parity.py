@@ -9,7 +9,7 @@ import pytest
 
 from paper_2605_05208_b300 import workloads as W
 
-from _util import random_solution, tiny_spec
+from _util import random_neighbor_lists, random_solution, tiny_spec
 
 pytestmark = pytest.mark.gpu
 
@@ -267,6 +267,27 @@ def test_timed_graph_descent_matches_untimed(md, stream):
         assert sol0 == runs[0][1] and np.array_equal(per, runs[0][2])
         assert (st.eval_ms > 0) == timed and st.eval_launches >= st.steps // 8
         assert sum(st.moves_by_op) == st.moves_scored
+
+
+@pytest.mark.parametrize("sweep", [0, 3])
+def test_installed_lists_and_sweep_schedule_match_oracle(md, oracle_lib, stream, sweep):
+    # Caller-chosen candidate lists (seeded random here) with a full sweep every `sweep` steps.
+    spec = W.gen_mdvrptw(58, n_depots=3, n_customers=90, theta=10)
+    sols = W.initial_solutions(spec, 58, 3)
+    nbr, cnt = random_neighbor_lists(spec, 12, 5)
+    inst, S = setup(md, spec, sols)
+    inst.set_neighbors(nbr, cnt)
+    gnb, gcnt = inst.neighbors()
+    assert np.array_equal(gnb, nbr) and np.array_equal(gcnt, cnt)
+    perm = W.op_permutations(9, 3, 60)
+    S.descend(perm, 60, use_graph=True, stream=stream, sweep_every=sweep)
+    got, per = S.read(), S.stats()
+    o = oracle_lib.Instance(spec)
+    o.set_neighbors(nbr, cnt)
+    for s, sol in enumerate(sols):
+        d = o.descend(sol, perm[s], 60, sweep_every=sweep)
+        assert canon(spec, got[s]) == canon(spec, d.solution)
+        assert list(per[s]) == [d.moves_scored, d.steps, d.accepted_steps, d.applied_moves, d.passes]
 
 
 # ------------------------------------------------------------------------------------------

@@ -16,7 +16,7 @@ import pytest
 
 from paper_2605_05208_b300 import workloads as W
 
-from _util import random_solution, tiny_spec
+from _util import random_neighbor_lists, random_solution, tiny_spec
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -622,3 +622,24 @@ def test_descent_reaches_local_optimum(oracle_lib, mk, multi):
     assert d.steps == d.passes * W.N_OPS
     flat = sorted(n for r in d.solution for n in r[1:-1])
     assert flat == list(range(spec.n_depots, spec.n_nodes))
+
+
+def test_sweep_every_step_equals_full_neighbourhood(oracle_lib):
+    # With a full sweep on every step, installed lists play no part: the descent is the
+    # full-neighbourhood descent.  With no sweep, only listed pairs are ever scored.
+    spec = tiny_spec(57, nd=2, nc=20, tw=True, Q=40, NV=3, D=300, horizon=2000, wmin=100, wmax=800)
+    sol = random_solution(spec, 57)
+    perm = W.op_permutations(57, 1, 60)[0]
+    full = oracle_lib.Instance(spec).descend(sol, perm, 60)
+    I = oracle_lib.Instance(spec)
+    nbr, cnt = random_neighbor_lists(spec, 4, 3)
+    I.set_neighbors(nbr, cnt)
+    swept = I.descend(sol, perm, 60, sweep_every=1)
+    assert W.canonical(swept.solution) == W.canonical(full.solution)
+    assert swept.moves_scored == full.moves_scored
+    I0 = oracle_lib.Instance(spec)
+    I0.set_neighbors(nbr, cnt)
+    mv, _ = I0.eval_op(sol, W.OP_RELOCATE)
+    allowed = {(spec.n_depots + cu, int(v)) for cu in range(spec.n_customers) for v in nbr[cu]}
+    assert all(((int(m["id"]) >> 18) & 0x3FFF, (int(m["id"]) >> 4) & 0x3FFF) in allowed for m in mv)
+
