@@ -296,6 +296,41 @@ md_status md_batch_tuning(const md_batch *batch, int32_t *upw, int32_t *grid);
  * ([sum n_sol * 4]) or NULL.  cfg->n_groups is ignored. */
 md_status md_batch_descend(md_batch *batch, const md_config *cfg, md_stats *out, void *stream);
 
+/* Learned move-proposal pruner (not in the paper: an extension that replaces the static
+ * granular lists of Section 3.2.3 by learned ones; every kept candidate is still evaluated exactly,
+ * and md_config.sweep_every supplies the periodic full sweep that catches what the lists miss).
+ * Model: 32 pair features -> 128 -> ReLU -> 128 -> ReLU -> 1 logit.  Parameters, FP32, in this
+ * order: W1 [128 x 32] (row = hidden unit), b1 [128], W2 [128 x 128], b2 [128], w3 [128], b3 [1]
+ * (MD_PRUNER_PARAMS values).  Inference runs on the tensor cores with BF16 operands and FP32
+ * accumulation; training keeps FP32 master weights with Adam (beta1 0.9, beta2 0.999, eps 1e-8).
+ * The features of a pair (u, v) depend on the instance only. */
+#define MD_PRUNER_PARAMS 20865
+typedef struct md_pruner md_pruner;
+md_status md_pruner_create(const float *params, md_pruner **out);
+md_status md_pruner_destroy(md_pruner *pruner);
+md_status md_pruner_params(md_pruner *pruner, float *params);
+
+/* The 32 features of every (customer, listed candidate) pair of the instance's current lists:
+ * feats [n_customers * theta * 32] (zeros for empty list slots). */
+md_status md_pruner_features(md_pruner *pruner, md_instance *inst, float *feats, void *stream);
+
+/* Logits of every (customer, listed candidate) pair: scores [n_customers * theta] (-inf for empty
+ * slots). */
+md_status md_pruner_score(md_pruner *pruner, md_instance *inst, float *scores, void *stream);
+
+/* Scores the instance's current lists (the candidate pool, e.g. from md_instance_build_neighbors)
+ * and installs, per customer, the k best candidates by (score descending, node id ascending) as
+ * the instance's neighbour lists (theta becomes k). */
+md_status md_pruner_prune(md_pruner *pruner, md_instance *inst, int32_t k, void *stream);
+
+/* Trains on every (customer, listed candidate) pair of the instance's current lists, with labels
+ * [n_customers * theta] (1: the pair took part in a selected move of a plain descent): `epochs`
+ * passes in order, in mini-batches of `batch` pairs (a multiple of 32), binary cross-entropy
+ * with positive pairs weighted by pos_weight, Adam with learning rate lr.  mean_loss (may be
+ * NULL) receives the weighted mean loss of the last epoch. */
+md_status md_pruner_train(md_pruner *pruner, md_instance *inst, const uint8_t *labels, int32_t epochs,
+                          int32_t batch, float lr, float pos_weight, float *mean_loss, void *stream);
+
 /* Allocation-free variant of md_eval_neighborhood + md_moves_read_leaders.  The paper has no
  * counterpart: it exists for callers that cannot call cudaMalloc (device memory budgeted up front,
  * latency-critical loops that must not enter the allocator, code handed only raw device buffers).

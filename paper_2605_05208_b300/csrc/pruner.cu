@@ -1,0 +1,593 @@
+// pruner.cu -- learned move-proposal pruner: a small MLP scores each customer's candidate pool
+// (its eta-ranked neighbour list) and the best k candidates become the instance's neighbour
+// lists; every kept candidate is then evaluated exactly by the ordinary neighbourhood kernels, and
+// a periodic full sweep (md_config.sweep_every) catches what the lists miss.
+//
+// Model: 32 features -> 128 -> ReLU -> 128 -> ReLU -> 1 logit.  Inference runs on the tensor
+// cores (mma.sync m16n8k16, BF16 operands, FP32 accumulation): one warp scores 16 pairs, the
+// layer-1 accumulators are turned into the layer-2 A fragments in registers.  Training keeps FP32
+// master weights: hand-written forward/backward (binary cross-entropy with a positive-class
+// weight) with gradients accumulated per block, and an Adam update kernel.  The features depend
+// on the instance only (distance, rank, windows, service, demand, depot relations), so one
+// scoring serves every solution of the instance.
+#include <cuda_bf16.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <vector>
+
+#include "mdls_internal.cuh"
+
+#define PR_F 32     // features
+#define PR_H 128    // hidden width
+#define PR_W1 0
+#define PR_B1 (PR_W1 + PR_H * PR_F)
+#define PR_W2 (PR_B1 + PR_H)
+#define PR_B2 (PR_W2 + PR_H * PR_H)
+#define PR_W3 (PR_B2 + PR_H)
+#define PR_B3 (PR_W3 + PR_H)
+#define PR_NPARAM (PR_B3 + 1)
+
+struct md_pruner {
+    float *P, *G, *M, *V;        // parameters, gradients, Adam moments (FP32, PR_NPARAM each)
+    __nv_bfloat16 *w1h, *w2h;    // BF16 copies of W1 [128x32] and W2 [128x128] for inference
+    float *loss;                 // [2] summed loss, summed weight of the last training call
+    long long step;              // Adam step counter
+};
+
+namespace {
+
+// Per-customer side information for the features.
+struct Aux {
+    int *near_depot;   // [nc] nearest depot
+    int *near_depot_c; // [nc] distance to it
+    int *near_cust_c;  // [nc] smallest distance among its candidates
+};
+
+__device__ __forceinline__ int dist_of(const DevInst &I, int a, int b) { return __ldg(&I.dist[(size_t)a * I.nn + b]); }
+
+__global__ void k_aux(DevInst I, const int32_t *lists, const int32_t *cnt, int pool, Aux A) {
+    const int cu = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cu >= I.nc) return;
+    const int u = I.nd + cu;
+    int bd = 0, bc = INT_MAX;
+    for (int d = 0; d < I.nd; d++) {
+        const int c = dist_of(I, u, d);
+        if (c < bc) { bc = c; bd = d; }
+    }
+    int mc = INT_MAX;
+    for (int i = 0; i < cnt[cu]; i++) mc = min(mc, dist_of(I, u, lists[(size_t)cu * pool + i]));
+    A.near_depot[cu] = bd;
+    A.near_depot_c[cu] = bc;
+    A.near_cust_c[cu] = mc == INT_MAX ? 1 : max(mc, 1);
+}
+
+// The 32 features of candidate v (rank-th in u's pool of size pool).
+__device__ void pair_features(const DevInst &I, const Aux &A, float horizon, int u, int v, int rank, int pool,
+                              float *f) {
+    const int cu = u - I.nd, cv = v - I.nd;
+    const int4 nu = __ldg(&I.node[u]), nv = __ldg(&I.node[v]);
+    const bool tw = (I.variant & MD_VARIANT_TW) != 0;
+    const float sc = fmaxf((float)I.Theta * 0.5f, 1.0f);
+    const float H = tw ? fmaxf(horizon, 1.0f) : 1.0f;
+    const int cuv = dist_of(I, u, v);
+    const int du = A.near_depot[cu], dv = A.near_depot[cv];
+    const float early = tw ? (float)max(nv.z - nu.w - nu.y - cuv, 0) / H : 0.0f;
+    const float late = tw ? (float)max(nu.w + nu.y + cuv - nv.w, 0) / H : 0.0f;
+    f[0] = (float)cuv / sc;
+    f[1] = (float)rank / (float)max(pool, 1);
+    f[2] = fminf((float)cuv / (float)A.near_cust_c[cu], 10.0f) / 10.0f;
+    f[3] = early;
+    f[4] = late;
+    f[5] = tw ? (float)max(min(nu.w, nv.w) - max(nu.z, nv.z), 0) / H : 1.0f;
+    f[6] = tw ? (float)(nv.z - nu.z) / H : 0.0f;
+    f[7] = tw ? (float)(nv.w - nu.w) / H : 0.0f;
+    f[8] = (float)nu.y / H;
+    f[9] = (float)nv.y / H;
+    f[10] = (float)nu.x / (float)I.Q;
+    f[11] = (float)nv.x / (float)I.Q;
+    f[12] = (float)(nu.x + nv.x) / (float)I.Q;
+    f[13] = (float)A.near_depot_c[cu] / sc;
+    f[14] = (float)A.near_depot_c[cv] / sc;
+    f[15] = du == dv ? 1.0f : 0.0f;
+    f[16] = (float)dist_of(I, v, du) / sc;
+    f[17] = (float)dist_of(I, u, dv) / sc;
+    f[18] = tw ? 1.0f : 0.0f;
+    f[19] = (I.variant & MD_VARIANT_OPEN) ? 1.0f : 0.0f;
+    f[20] = (tw && nu.z + nu.y + cuv > nv.w) ? 1.0f : 0.0f;
+    f[21] = (tw && nv.z + nv.y + cuv > nu.w) ? 1.0f : 0.0f;
+    f[22] = (float)(cuv + A.near_depot_c[cu] - dist_of(I, v, du)) / sc;
+    f[23] = sqrtf(f[0]);
+    f[24] = f[1] * f[1];
+    f[25] = (float)I.nd / 32.0f;
+    f[26] = I.D > 0 ? (float)cuv / (float)I.D : 0.0f;
+    f[27] = tw ? (float)(nu.w - nu.z) / H : 1.0f;
+    f[28] = tw ? (float)(nv.w - nv.z) / H : 1.0f;
+    f[29] = fminf(early, late);
+    f[30] = 0.0f;
+    f[31] = 0.0f;
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t *>(&h);
+}
+
+__device__ __forceinline__ void mma_bf16(float *d, const uint32_t *a, uint32_t b0, uint32_t b1) {
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                 "{%0,%1,%2,%3};\n"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// Tensor-core scoring: each warp scores 16 (u, candidate) pairs; 4 warps per block.
+__global__ void __launch_bounds__(128) k_score(DevInst I, const int32_t *lists, const int32_t *cnt, int pool, Aux A,
+                                               float horizon, const __nv_bfloat16 *w1h, const __nv_bfloat16 *w2h,
+                                               const float *P, float *scores, long long n_pairs) {
+    __shared__ __align__(16) __nv_bfloat16 sW1[PR_H * PR_F];
+    __shared__ __align__(16) __nv_bfloat16 sW2[PR_H * PR_H];
+    __shared__ float sB1[PR_H], sB2[PR_H], sW3[PR_H];
+    __shared__ __align__(16) __nv_bfloat16 sF[4][16][PR_F + 8];
+    for (int i = threadIdx.x; i < PR_H * PR_F; i += blockDim.x) sW1[i] = w1h[i];
+    for (int i = threadIdx.x; i < PR_H * PR_H; i += blockDim.x) sW2[i] = w2h[i];
+    for (int i = threadIdx.x; i < PR_H; i += blockDim.x) {
+        sB1[i] = P[PR_B1 + i];
+        sB2[i] = P[PR_B2 + i];
+        sW3[i] = P[PR_W3 + i];
+    }
+    __syncthreads();
+    const float b3 = P[PR_B3];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const long long tiles = (n_pairs + 15) / 16;
+    for (long long tile = (long long)blockIdx.x * 4 + warp; tile < tiles; tile += (long long)gridDim.x * 4) {
+        // features of the 16 rows, as BF16, in this warp's shared tile
+        if (lane < 16) {
+            const long long p = tile * 16 + lane;
+            float f[PR_F];
+            bool ok = false;
+            if (p < n_pairs) {
+                const int cu = (int)(p / pool), i = (int)(p % pool);
+                if (i < cnt[cu]) {
+                    pair_features(I, A, horizon, I.nd + cu, lists[(size_t)cu * pool + i], i, pool, f);
+                    ok = true;
+                }
+            }
+            for (int k = 0; k < PR_F; k++) sF[warp][lane][k] = __float2bfloat16_rn(ok ? f[k] : 0.0f);
+        }
+        __syncwarp();
+        // layer 1: [16 x 32] x [32 x 128]
+        float acc[16][4];
+#pragma unroll
+        for (int j = 0; j < 16; j++) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.0f;
+#pragma unroll
+        for (int kk = 0; kk < 2; kk++) {
+            uint32_t a[4];
+            a[0] = *reinterpret_cast<const uint32_t *>(&sF[warp][g][16 * kk + 2 * t]);
+            a[1] = *reinterpret_cast<const uint32_t *>(&sF[warp][g + 8][16 * kk + 2 * t]);
+            a[2] = *reinterpret_cast<const uint32_t *>(&sF[warp][g][16 * kk + 2 * t + 8]);
+            a[3] = *reinterpret_cast<const uint32_t *>(&sF[warp][g + 8][16 * kk + 2 * t + 8]);
+#pragma unroll
+            for (int j = 0; j < 16; j++) {
+                const __nv_bfloat16 *wr = &sW1[(8 * j + g) * PR_F + 16 * kk + 2 * t];
+                mma_bf16(acc[j], a, *reinterpret_cast<const uint32_t *>(wr), *reinterpret_cast<const uint32_t *>(wr + 8));
+            }
+        }
+        // bias + ReLU, repacked as the A fragments of layer 2
+        uint32_t a2[8][4];
+#pragma unroll
+        for (int kk = 0; kk < 8; kk++) {
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const int j = 2 * kk + h, c = 8 * j + 2 * t;
+                const float x0 = fmaxf(acc[j][0] + sB1[c], 0.0f), x1 = fmaxf(acc[j][1] + sB1[c + 1], 0.0f);
+                const float x2 = fmaxf(acc[j][2] + sB1[c], 0.0f), x3 = fmaxf(acc[j][3] + sB1[c + 1], 0.0f);
+                a2[kk][2 * h + 0] = pack_bf16(x0, x1);  // row g
+                a2[kk][2 * h + 1] = pack_bf16(x2, x3);  // row g + 8
+            }
+        }
+        // layer 2: [16 x 128] x [128 x 128]
+#pragma unroll
+        for (int j = 0; j < 16; j++) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.0f;
+#pragma unroll
+        for (int kk = 0; kk < 8; kk++) {
+            const uint32_t a[4] = {a2[kk][0], a2[kk][1], a2[kk][2], a2[kk][3]};
+#pragma unroll
+            for (int j = 0; j < 16; j++) {
+                const __nv_bfloat16 *wr = &sW2[(8 * j + g) * PR_H + 16 * kk + 2 * t];
+                mma_bf16(acc[j], a, *reinterpret_cast<const uint32_t *>(wr), *reinterpret_cast<const uint32_t *>(wr + 8));
+            }
+        }
+        // bias + ReLU + output layer
+        float s0 = 0.0f, s8 = 0.0f;
+#pragma unroll
+        for (int j = 0; j < 16; j++) {
+            const int c = 8 * j + 2 * t;
+            s0 += sW3[c] * fmaxf(acc[j][0] + sB2[c], 0.0f) + sW3[c + 1] * fmaxf(acc[j][1] + sB2[c + 1], 0.0f);
+            s8 += sW3[c] * fmaxf(acc[j][2] + sB2[c], 0.0f) + sW3[c + 1] * fmaxf(acc[j][3] + sB2[c + 1], 0.0f);
+        }
+        s0 += __shfl_xor_sync(0xffffffffu, s0, 1);
+        s0 += __shfl_xor_sync(0xffffffffu, s0, 2);
+        s8 += __shfl_xor_sync(0xffffffffu, s8, 1);
+        s8 += __shfl_xor_sync(0xffffffffu, s8, 2);
+        if (t == 0) {
+            const long long p0 = tile * 16 + g, p8 = p0 + 8;
+            if (p0 < n_pairs) scores[p0] = (int)(p0 % pool) < cnt[p0 / pool] ? s0 + b3 : -INFINITY;
+            if (p8 < n_pairs) scores[p8] = (int)(p8 % pool) < cnt[p8 / pool] ? s8 + b3 : -INFINITY;
+        }
+        __syncwarp();
+    }
+}
+
+// Best k of each customer's pool by (score descending, node id ascending); one block per customer.
+__global__ void k_topk(int nc, const int32_t *lists, const int32_t *cnt, int pool, int P2, const float *scores, int k,
+                       int32_t *out, int32_t *out_cnt) {
+    extern __shared__ unsigned char sm[];
+    float *key = reinterpret_cast<float *>(sm);
+    int *val = reinterpret_cast<int *>(key + P2);
+    const int cu = blockIdx.x;
+    const int n = cnt[cu];
+    for (int i = threadIdx.x; i < P2; i += blockDim.x) {
+        key[i] = i < n ? scores[(size_t)cu * pool + i] : -INFINITY;
+        val[i] = i < n ? lists[(size_t)cu * pool + i] : INT_MAX;
+    }
+    __syncthreads();
+    for (int kk = 2; kk <= P2; kk <<= 1) {
+        for (int j = kk >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < P2; i += blockDim.x) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const float ka = key[i], kb = key[ixj];
+                    const int va = val[i], vb = val[ixj];
+                    const bool a_after = (ka < kb) || (ka == kb && va > vb);  // a ranks after b
+                    const bool up = (i & kk) == 0;
+                    if (a_after == up) {
+                        key[i] = kb; key[ixj] = ka;
+                        val[i] = vb; val[ixj] = va;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    const int keep = min(n, k);
+    for (int i = threadIdx.x; i < k; i += blockDim.x) out[(size_t)cu * k + i] = i < keep ? val[i] : MD_NONE;
+    if (threadIdx.x == 0) out_cnt[cu] = keep;
+}
+
+// Training: 32 samples per block, 128 threads (thread n owns hidden unit n of both layers).
+// Gradients of the mean weighted binary cross-entropy are accumulated per block in shared memory
+// and added to G once per block.
+__global__ void __launch_bounds__(128) k_train(DevInst I, const int32_t *lists, const int32_t *cnt, int pool, Aux A,
+                                               float horizon, const float *P, float *G, const uint8_t *labels,
+                                               long long first, long long count, float pos_weight, float inv_norm,
+                                               float *loss) {
+    extern __shared__ __align__(16) float sh[];
+    float *sW2 = sh;                       // [128 x 128]
+    float *sX = sW2 + PR_H * PR_H;         // [32 x 32]
+    float *sH1 = sX + 32 * PR_F;           // [32 x 128]
+    float *sH2 = sH1 + 32 * PR_H;          // [32 x 128]
+    float *sD2 = sH2 + 32 * PR_H;          // [32 x 128] dL/d(pre-activation 2)
+    float *sZ = sD2 + 32 * PR_H;           // [32] logits, then dL/dz
+    float *sWt = sZ + 32;                  // [32] sample weights
+    __shared__ float s_loss, s_wsum;
+    const int n = threadIdx.x;
+    const long long base = first + (long long)blockIdx.x * 32;
+    for (int i = n; i < PR_H * PR_H; i += 128) sW2[i] = P[PR_W2 + i];
+    if (n < 32) {
+        const long long p = base + n;
+        float f[PR_F];
+        float w = 0.0f;
+        if (p < first + count) {
+            const int cu = (int)(p / pool), i = (int)(p % pool);
+            if (i < cnt[cu]) {
+                pair_features(I, A, horizon, I.nd + cu, lists[(size_t)cu * pool + i], i, pool, f);
+                w = labels[p] ? pos_weight : 1.0f;
+            }
+        }
+        for (int k = 0; k < PR_F; k++) sX[n * PR_F + k] = w > 0.0f ? f[k] : 0.0f;
+        sWt[n] = w;
+        sZ[n] = 0.0f;
+    }
+    if (n == 0) { s_loss = 0.0f; s_wsum = 0.0f; }
+    __syncthreads();
+    // forward, layer 1 (thread n = unit n)
+    float w1[PR_F];
+    for (int k = 0; k < PR_F; k++) w1[k] = P[PR_W1 + n * PR_F + k];
+    const float b1 = P[PR_B1 + n], b2 = P[PR_B2 + n], w3 = P[PR_W3 + n];
+    for (int s = 0; s < 32; s++) {
+        float a = b1;
+        for (int k = 0; k < PR_F; k++) a += w1[k] * sX[s * PR_F + k];
+        sH1[s * PR_H + n] = fmaxf(a, 0.0f);
+    }
+    __syncthreads();
+    for (int s = 0; s < 32; s++) {
+        float a = b2;
+        for (int m = 0; m < PR_H; m++) a += sW2[n * PR_H + m] * sH1[s * PR_H + m];
+        sH2[s * PR_H + n] = fmaxf(a, 0.0f);
+        atomicAdd(&sZ[s], w3 * fmaxf(a, 0.0f));
+    }
+    __syncthreads();
+    if (n < 32) {
+        const float z = sZ[n] + P[PR_B3];
+        const float y = (sWt[n] > 0.0f && labels[base + n]) ? 1.0f : 0.0f;
+        const float w = sWt[n];
+        // weighted BCE with logits: w * (softplus(z) - y z); derivative w * (sigmoid(z) - y)
+        const float sp = z > 0.0f ? z + log1pf(expf(-z)) : log1pf(expf(z));
+        const float sig = 1.0f / (1.0f + expf(-z));
+        atomicAdd(&s_loss, w * (sp - y * z));
+        atomicAdd(&s_wsum, w);
+        sZ[n] = w * (sig - y) * inv_norm;
+    }
+    __syncthreads();
+    // backward: output layer and layer 2 (thread n = unit n)
+    float g_w3 = 0.0f, g_b2 = 0.0f;
+    for (int s = 0; s < 32; s++) {
+        const float dz = sZ[s];
+        const float h2 = sH2[s * PR_H + n];
+        g_w3 += dz * h2;
+        const float d2 = h2 > 0.0f ? dz * w3 : 0.0f;
+        sD2[s * PR_H + n] = d2;
+        g_b2 += d2;
+    }
+    __syncthreads();
+    for (int m = 0; m < PR_H; m++) {
+        float g = 0.0f;
+        for (int s = 0; s < 32; s++) g += sD2[s * PR_H + n] * sH1[s * PR_H + m];
+        atomicAdd(&G[PR_W2 + n * PR_H + m], g);
+    }
+    atomicAdd(&G[PR_W3 + n], g_w3);
+    atomicAdd(&G[PR_B2 + n], g_b2);
+    if (n == 0) {
+        float gb3 = 0.0f;
+        for (int s = 0; s < 32; s++) gb3 += sZ[s];
+        atomicAdd(&G[PR_B3], gb3);
+        atomicAdd(&loss[0], s_loss);
+        atomicAdd(&loss[1], s_wsum);
+    }
+    // layer 1 (thread n = unit n of the first hidden layer)
+    float g_w1[PR_F];
+    for (int k = 0; k < PR_F; k++) g_w1[k] = 0.0f;
+    float g_b1 = 0.0f;
+    for (int s = 0; s < 32; s++) {
+        if (sH1[s * PR_H + n] <= 0.0f) continue;
+        float d1 = 0.0f;
+        for (int j = 0; j < PR_H; j++) d1 += sD2[s * PR_H + j] * sW2[j * PR_H + n];
+        g_b1 += d1;
+        for (int k = 0; k < PR_F; k++) g_w1[k] += d1 * sX[s * PR_F + k];
+    }
+    for (int k = 0; k < PR_F; k++) atomicAdd(&G[PR_W1 + n * PR_F + k], g_w1[k]);
+    atomicAdd(&G[PR_B1 + n], g_b1);
+}
+
+// Adam (Kingma & Ba 2015) on every parameter, then the gradients are cleared.
+__global__ void k_adam(float *P, float *G, float *M, float *V, int n, float lr, float b1, float b2, float eps,
+                       float c1, float c2) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float g = G[i];
+    const float m = b1 * M[i] + (1.0f - b1) * g;
+    const float v = b2 * V[i] + (1.0f - b2) * g * g;
+    M[i] = m;
+    V[i] = v;
+    P[i] -= lr * (m / c1) / (sqrtf(v / c2) + eps);
+    G[i] = 0.0f;
+}
+
+__global__ void k_to_bf16(const float *P, __nv_bfloat16 *w1h, __nv_bfloat16 *w2h) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < PR_H * PR_F) w1h[i] = __float2bfloat16_rn(P[PR_W1 + i]);
+    if (i < PR_H * PR_H) w2h[i] = __float2bfloat16_rn(P[PR_W2 + i]);
+}
+
+// Features of every (customer, candidate) pair, for inspection: out [n_pairs x 32].
+__global__ void k_features(DevInst I, const int32_t *lists, const int32_t *cnt, int pool, Aux A, float horizon,
+                           float *out, long long n_pairs) {
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n_pairs) return;
+    const int cu = (int)(p / pool), i = (int)(p % pool);
+    float f[PR_F];
+    if (i < cnt[cu]) pair_features(I, A, horizon, I.nd + cu, lists[(size_t)cu * pool + i], i, pool, f);
+    else
+        for (int k = 0; k < PR_F; k++) f[k] = 0.0f;
+    for (int k = 0; k < PR_F; k++) out[p * PR_F + k] = f[k];
+}
+
+struct AuxBuf {
+    Aux a;
+    md_status make(const md_instance *inst, cudaStream_t st) {
+        const int nc = inst->d.nc;
+        a.near_depot = a.near_depot_c = a.near_cust_c = nullptr;
+        MD_CUDA(cudaMallocAsync(&a.near_depot, sizeof(int) * nc, st));
+        MD_CUDA(cudaMallocAsync(&a.near_depot_c, sizeof(int) * nc, st));
+        MD_CUDA(cudaMallocAsync(&a.near_cust_c, sizeof(int) * nc, st));
+        k_aux<<<(nc + 127) / 128, 128, 0, st>>>(inst->d, inst->nbr, inst->nnbr, inst->d.theta, a);
+        MD_CUDA(cudaGetLastError());
+        return MD_OK;
+    }
+    void release(cudaStream_t st) {
+        cudaFreeAsync(a.near_depot, st);
+        cudaFreeAsync(a.near_depot_c, st);
+        cudaFreeAsync(a.near_cust_c, st);
+    }
+};
+
+float horizon_of(const md_instance *inst) { return inst->max_l > 0 ? (float)inst->max_l : 1.0f; }
+
+md_status score_pool(md_pruner *p, md_instance *inst, float *scores_d, cudaStream_t st) {
+    const int pool = inst->d.theta;
+    const long long n_pairs = (long long)inst->d.nc * pool;
+    AuxBuf aux;
+    md_status r = aux.make(inst, st);
+    if (r != MD_OK) return r;
+    const long long tiles = (n_pairs + 15) / 16;
+    const int grid = (int)((tiles + 3) / 4 < 148 * 8 ? (tiles + 3) / 4 : 148 * 8);
+    k_score<<<grid, 128, 0, st>>>(inst->d, inst->nbr, inst->nnbr, pool, aux.a, horizon_of(inst), p->w1h, p->w2h, p->P,
+                                  scores_d, n_pairs);
+    cudaError_t e = cudaGetLastError();
+    aux.release(st);
+    if (e != cudaSuccess) return md_cuda_check(e, "k_score");
+    return MD_OK;
+}
+
+}  // namespace
+
+extern "C" md_status md_pruner_create(const float *params, md_pruner **out) {
+    if (!params || !out) { md_set_error("md_pruner_create: null argument"); return MD_ERR_ARG; }
+    *out = nullptr;
+    md_pruner *p = (md_pruner *)calloc(1, sizeof(md_pruner));
+    cudaError_t e = cudaSuccess;
+#define MDP(call) do { if (e == cudaSuccess) e = (call); } while (0)
+    MDP(cudaMalloc(&p->P, sizeof(float) * PR_NPARAM));
+    MDP(cudaMalloc(&p->G, sizeof(float) * PR_NPARAM));
+    MDP(cudaMalloc(&p->M, sizeof(float) * PR_NPARAM));
+    MDP(cudaMalloc(&p->V, sizeof(float) * PR_NPARAM));
+    MDP(cudaMalloc(&p->w1h, sizeof(__nv_bfloat16) * PR_H * PR_F));
+    MDP(cudaMalloc(&p->w2h, sizeof(__nv_bfloat16) * PR_H * PR_H));
+    MDP(cudaMalloc(&p->loss, sizeof(float) * 2));
+    MDP(cudaMemcpy(p->P, params, sizeof(float) * PR_NPARAM, cudaMemcpyHostToDevice));
+    MDP(cudaMemset(p->G, 0, sizeof(float) * PR_NPARAM));
+    MDP(cudaMemset(p->M, 0, sizeof(float) * PR_NPARAM));
+    MDP(cudaMemset(p->V, 0, sizeof(float) * PR_NPARAM));
+#undef MDP
+    if (e == cudaSuccess) {
+        k_to_bf16<<<(PR_H * PR_H + 255) / 256, 256>>>(p->P, p->w1h, p->w2h);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        cudaFree(p->P); cudaFree(p->G); cudaFree(p->M); cudaFree(p->V);
+        cudaFree(p->w1h); cudaFree(p->w2h); cudaFree(p->loss);
+        free(p);
+        return md_cuda_check(e, "md_pruner_create");
+    }
+    *out = p;
+    return MD_OK;
+}
+
+extern "C" md_status md_pruner_destroy(md_pruner *p) {
+    if (!p) return MD_OK;
+    cudaFree(p->P); cudaFree(p->G); cudaFree(p->M); cudaFree(p->V);
+    cudaFree(p->w1h); cudaFree(p->w2h); cudaFree(p->loss);
+    free(p);
+    return MD_OK;
+}
+
+extern "C" md_status md_pruner_params(md_pruner *p, float *params) {
+    if (!p || !params) { md_set_error("md_pruner_params: null argument"); return MD_ERR_ARG; }
+    MD_CUDA(cudaMemcpy(params, p->P, sizeof(float) * PR_NPARAM, cudaMemcpyDeviceToHost));
+    return MD_OK;
+}
+
+extern "C" md_status md_pruner_features(md_pruner *p, md_instance *inst, float *feats, void *stream) {
+    if (!p || !inst || !feats || inst->d.theta <= 0) { md_set_error("md_pruner_features: needs neighbour lists"); return MD_ERR_ARG; }
+    cudaStream_t st = (cudaStream_t)stream;
+    const int pool = inst->d.theta;
+    const long long n = (long long)inst->d.nc * pool;
+    float *d = nullptr;
+    AuxBuf aux;
+    md_status r = aux.make(inst, st);
+    if (r != MD_OK) return r;
+    MD_CUDA(cudaMallocAsync(&d, sizeof(float) * n * PR_F, st));
+    k_features<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(inst->d, inst->nbr, inst->nnbr, pool, aux.a,
+                                                            horizon_of(inst), d, n);
+    MD_CUDA(cudaGetLastError());
+    MD_CUDA(cudaMemcpyAsync(feats, d, sizeof(float) * n * PR_F, cudaMemcpyDeviceToHost, st));
+    MD_CUDA(cudaFreeAsync(d, st));
+    aux.release(st);
+    MD_CUDA(cudaStreamSynchronize(st));
+    return MD_OK;
+}
+
+extern "C" md_status md_pruner_score(md_pruner *p, md_instance *inst, float *scores, void *stream) {
+    if (!p || !inst || !scores || inst->d.theta <= 0) { md_set_error("md_pruner_score: needs neighbour lists"); return MD_ERR_ARG; }
+    cudaStream_t st = (cudaStream_t)stream;
+    const long long n = (long long)inst->d.nc * inst->d.theta;
+    float *d = nullptr;
+    MD_CUDA(cudaMallocAsync(&d, sizeof(float) * n, st));
+    md_status r = score_pool(p, inst, d, st);
+    if (r == MD_OK) {
+        MD_CUDA(cudaMemcpyAsync(scores, d, sizeof(float) * n, cudaMemcpyDeviceToHost, st));
+    }
+    MD_CUDA(cudaFreeAsync(d, st));
+    MD_CUDA(cudaStreamSynchronize(st));
+    return r;
+}
+
+extern "C" md_status md_pruner_prune(md_pruner *p, md_instance *inst, int32_t k, void *stream) {
+    if (!p || !inst || k < 1 || inst->d.theta <= 0) { md_set_error("md_pruner_prune: needs a candidate pool and k >= 1"); return MD_ERR_ARG; }
+    if (k > inst->d.theta) k = inst->d.theta;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int pool = inst->d.theta, nc = inst->d.nc;
+    float *sc = nullptr;
+    int32_t *nb = nullptr, *cnt = nullptr;
+    MD_CUDA(cudaMallocAsync(&sc, sizeof(float) * (size_t)nc * pool, st));
+    md_status r = score_pool(p, inst, sc, st);
+    if (r != MD_OK) return r;
+    MD_CUDA(cudaMalloc(&nb, sizeof(int32_t) * (size_t)nc * k));
+    MD_CUDA(cudaMalloc(&cnt, sizeof(int32_t) * nc));
+    int P2 = 1;
+    while (P2 < pool) P2 <<= 1;
+    const size_t smb = (size_t)P2 * (sizeof(float) + sizeof(int));
+    MD_CUDA(cudaFuncSetAttribute(k_topk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb));
+    k_topk<<<nc, 256, smb, st>>>(nc, inst->nbr, inst->nnbr, pool, P2, sc, k, nb, cnt);
+    MD_CUDA(cudaGetLastError());
+    MD_CUDA(cudaFreeAsync(sc, st));
+    MD_CUDA(cudaStreamSynchronize(st));
+    // the kept candidates become the instance's neighbour lists
+    cudaFree(inst->nbr);
+    cudaFree(inst->nnbr);
+    inst->nbr = nb;
+    inst->nnbr = cnt;
+    inst->d.nbr = nb;
+    inst->d.nnbr = cnt;
+    inst->d.theta = k;
+    return MD_OK;
+}
+
+// Trains on every (customer, candidate) pair of the instance's current lists: labels [nc x theta]
+// (1 = the pair was part of a selected move of a plain descent), `epochs` passes in mini-batches
+// of `batch` pairs (a multiple of 32), Adam with learning rate lr, positive pairs weighted by
+// pos_weight.  mean_loss receives the weighted mean loss of the last epoch.
+extern "C" md_status md_pruner_train(md_pruner *p, md_instance *inst, const uint8_t *labels, int32_t epochs,
+                                     int32_t batch, float lr, float pos_weight, float *mean_loss, void *stream) {
+    if (!p || !inst || !labels || inst->d.theta <= 0 || epochs < 1 || batch < 32 || batch % 32) {
+        md_set_error("md_pruner_train: invalid argument (needs lists, epochs >= 1, batch a multiple of 32)");
+        return MD_ERR_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const int pool = inst->d.theta;
+    const long long n = (long long)inst->d.nc * pool;
+    uint8_t *dl = nullptr;
+    MD_CUDA(cudaMallocAsync(&dl, n, st));
+    MD_CUDA(cudaMemcpyAsync(dl, labels, n, cudaMemcpyHostToDevice, st));
+    AuxBuf aux;
+    md_status r = aux.make(inst, st);
+    if (r != MD_OK) return r;
+    const size_t smb = sizeof(float) * (PR_H * PR_H + 32 * PR_F + 3 * 32 * PR_H + 64);
+    MD_CUDA(cudaFuncSetAttribute(k_train, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb));
+    float hl[2] = {0.0f, 0.0f};
+    for (int e = 0; e < epochs; e++) {
+        MD_CUDA(cudaMemsetAsync(p->loss, 0, sizeof(float) * 2, st));
+        for (long long first = 0; first < n; first += batch) {
+            const long long count = n - first < batch ? n - first : batch;
+            k_train<<<(unsigned)((count + 31) / 32), 128, smb, st>>>(inst->d, inst->nbr, inst->nnbr, pool, aux.a,
+                                                                    horizon_of(inst), p->P, p->G, dl, first, count,
+                                                                    pos_weight, 1.0f / (float)count, p->loss);
+            MD_CUDA(cudaGetLastError());
+            p->step++;
+            const float c1 = 1.0f - powf(0.9f, (float)p->step), c2 = 1.0f - powf(0.999f, (float)p->step);
+            k_adam<<<(PR_NPARAM + 255) / 256, 256, 0, st>>>(p->P, p->G, p->M, p->V, PR_NPARAM, lr, 0.9f, 0.999f, 1e-8f,
+                                                            c1, c2);
+            MD_CUDA(cudaGetLastError());
+        }
+        MD_CUDA(cudaMemcpyAsync(hl, p->loss, sizeof(hl), cudaMemcpyDeviceToHost, st));
+    }
+    k_to_bf16<<<(PR_H * PR_H + 255) / 256, 256, 0, st>>>(p->P, p->w1h, p->w2h);
+    MD_CUDA(cudaGetLastError());
+    aux.release(st);
+    MD_CUDA(cudaFreeAsync(dl, st));
+    MD_CUDA(cudaStreamSynchronize(st));
+    if (mean_loss) *mean_loss = hl[1] > 0.0f ? hl[0] / hl[1] : 0.0f;
+    return MD_OK;
+}

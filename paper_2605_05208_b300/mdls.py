@@ -33,8 +33,11 @@ EXPORTED = (
     "md_select_multimove", "md_selection_read", "md_apply_and_rebuild", "md_descend",
     "md_solutions_stats", "md_eval_leaders_noalloc", "md_batch_create", "md_batch_destroy",
     "md_batch_tune", "md_batch_tuning", "md_batch_descend", "md_instance_build_neighbors",
-    "md_instance_set_neighbors",
+    "md_instance_set_neighbors", "md_pruner_create", "md_pruner_destroy", "md_pruner_params",
+    "md_pruner_features", "md_pruner_score", "md_pruner_prune", "md_pruner_train",
 )
+
+PRUNER_PARAMS = 20865
 
 
 class MdError(RuntimeError):
@@ -117,6 +120,13 @@ def lib() -> C.CDLL:
             "md_eval_leaders_noalloc": [P, P, P, P, P, P],
             "md_instance_build_neighbors": [P, C.c_int32],
             "md_instance_set_neighbors": [P, P, P, C.c_int32],
+            "md_pruner_create": [P, PP],
+            "md_pruner_destroy": [P],
+            "md_pruner_params": [P, P],
+            "md_pruner_features": [P, P, P, P],
+            "md_pruner_score": [P, P, P, P],
+            "md_pruner_prune": [P, P, C.c_int32, P],
+            "md_pruner_train": [P, P, P, C.c_int32, C.c_int32, C.c_float, C.c_float, P, P],
             "md_batch_create": [P, C.c_int32, PP],
             "md_batch_destroy": [P],
             "md_batch_tune": [P, P],
@@ -435,4 +445,54 @@ class Batch:
         return DescendStats(st.moves_scored, st.steps, st.accepted_steps, st.applied_moves,
                             st.passes_max, st.launches, st.eval_launches, st.eval_ms,
                             tuple(st.moves_by_op))
+
+
+class Pruner:
+    """Learned candidate pruner (md_pruner_*): an MLP 32 -> 128 -> 128 -> 1 over pair features."""
+
+    def __init__(self, params):
+        params = np.ascontiguousarray(params, dtype=np.float32)
+        assert params.size == PRUNER_PARAMS
+        h = C.c_void_p()
+        _check(lib().md_pruner_create(_ptr(params), C.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().md_pruner_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self) -> np.ndarray:
+        out = np.zeros(PRUNER_PARAMS, dtype=np.float32)
+        _check(lib().md_pruner_params(self.h, _ptr(out)))
+        return out
+
+    def features(self, inst: Instance, stream=None) -> np.ndarray:
+        th = inst.neighbors()[0].shape[1]
+        out = np.zeros(inst.nc * th * 32, dtype=np.float32)
+        _check(lib().md_pruner_features(self.h, inst.h, _ptr(out), _stream(stream)))
+        return out.reshape(inst.nc, th, 32)
+
+    def score(self, inst: Instance, stream=None) -> np.ndarray:
+        th = inst.neighbors()[0].shape[1]
+        out = np.zeros(inst.nc * th, dtype=np.float32)
+        _check(lib().md_pruner_score(self.h, inst.h, _ptr(out), _stream(stream)))
+        return out.reshape(inst.nc, th)
+
+    def prune(self, inst: Instance, k: int, stream=None):
+        _check(lib().md_pruner_prune(self.h, inst.h, int(k), _stream(stream)))
+        inst.theta = min(int(k), getattr(inst, "theta", inst.spec.theta))
+
+    def train(self, inst: Instance, labels, epochs=1, batch=1024, lr=1e-3, pos_weight=1.0, stream=None) -> float:
+        labels = np.ascontiguousarray(labels, dtype=np.uint8)
+        loss = C.c_float()
+        _check(lib().md_pruner_train(self.h, inst.h, _ptr(labels), int(epochs), int(batch), float(lr),
+                                     float(pos_weight), C.byref(loss), _stream(stream)))
+        return float(loss.value)
 

@@ -398,3 +398,17 @@ def op_permutations(seed: int, n_solutions: int, max_pass: int, op_list=tuple(ra
                 a[i], a[j] = a[j], a[i]
             out[s, p] = a
     return out
+
+
+def mlp_init_params(seed: int, widths=(32, 128, 128, 1)) -> np.ndarray:
+    """Seeded initial parameters of the pruner MLP, flattened layer by layer as
+    W1 [128 x 32], b1, W2 [128 x 128], b2, w3 [128], b3: weights uniform on +-sqrt(6/(fan_in +
+    fan_out)) (Glorot & Bengio 2010), biases zero."""
+    st = Stream(seed, 30)
+    out = []
+    for fin, fout in zip(widths[:-1], widths[1:]):
+        bound = math.sqrt(6.0 / (fin + fout))
+        out.append((st.uniform(fin * fout) * 2.0 - 1.0) * bound)
+        out.append(np.zeros(fout))
+    return np.concatenate(out).astype(np.float32)
+
