@@ -399,6 +399,199 @@ def run_batch(args):
     }))
 
 
+LEARNED_SOL = 8
+LEARNED_POOL = 256      # eta-ranked candidate pool per customer that the MLP scores
+LEARNED_TOPK = 64
+LEARNED_SWEEP = 20      # full plain sweep every 20 steps
+
+
+def learned_workload(n_sol: int):
+    spec = W.mdvrptw_20x10000(SEED, theta=0)
+    sols = W.initial_solutions(spec, SEED, n_sol, order="window")
+    perm = W.op_permutations(SEED, n_sol, MAX_PASS)
+    return spec, sols, perm
+
+
+def _oracle_learned(args):
+    idx, n_sol, nbr, cnt, max_pass = args
+    from oracle import oracle as O
+    spec, sols, perm = learned_workload(n_sol)
+    inst = O.Instance(spec)
+    inst.set_neighbors(nbr, cnt)
+    t0 = time.perf_counter()
+    d = inst.descend(sols[idx], perm[idx], max_pass, multi=True, sweep_every=LEARNED_SWEEP)
+    return d.moves_scored, time.perf_counter() - t0
+
+
+def run_learned(args):
+    """Learned-pruned descents of the 20-depot, 10000-customer MDVRPTW instance beside the plain
+    full-neighbourhood descents of the same solutions (and the static eta top-64 lists).
+
+    Untimed set-up: labels logged from plain descents of three smaller instances, MLP training,
+    then the MLP scores each customer's 256 eta-nearest candidates and keeps the top 64.  One
+    timed step descends all solutions from their initial routes to a local optimum of the full
+    neighbourhood (the verification pass confirms it) with a full sweep every 20 steps."""
+    import torch
+    from paper_2605_05208_b300 import build, learned, mdls
+    n_sol = args.solutions or LEARNED_SOL
+    pool = None
+    if not args.no_cpu_baseline:
+        ncores = min(os.cpu_count() or 1, 16)
+        pool = make_pool(ncores)
+    build.build()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    sptr = stream.cuda_stream
+
+    t0 = time.perf_counter()
+    data = learned.training_set(stream=sptr)
+    t_log = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    pr, losses = learned.train(data, epochs=20, stream=sptr)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+
+    spec, sols, perm = learned_workload(n_sol)
+    routes = max(len(x) for x in sols)
+    longest = max(len(r) - 2 for x in sols for r in x)
+    R = max(64, 2 * routes, spec.n_depots * spec.N_V + 8)
+    K = max(64, 2 * longest)
+    perm_dev = torch.from_numpy(np.ascontiguousarray(perm)).to(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
+
+    inst_l = mdls.Instance(spec)
+    inst_l.build_neighbors(LEARNED_POOL)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    pr.prune(inst_l, LEARNED_TOPK, stream=sptr)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    prune_ms = e0.elapsed_time(e1)
+    inst_e = mdls.Instance(spec)
+    inst_e.build_neighbors(LEARNED_TOPK)
+    inst_p = mdls.Instance(spec)  # theta = 0: every customer is a candidate
+
+    def arm(inst, sweep, warmup, steps, time_eval=False):
+        init = mdls.Solutions(inst, n_sol, R, K)
+        work = mdls.Solutions(inst, n_sol, R, K)
+        init.load(sols)
+
+        def one(te=False, max_pass=MAX_PASS):
+            work.copy_from(init, stream=sptr)
+            return work.descend(perm_dev.data_ptr(), max_pass, multi=True, use_graph=True,
+                                poll_every=1, stream=sptr, n_ops=W.N_OPS, time_eval=te,
+                                n_groups=args.groups, sweep_every=sweep)
+        for _ in range(warmup):
+            one(max_pass=MAX_PASS if sweep else 2)
+        torch.cuda.synchronize()
+        ms, sts = 0.0, []
+        with ClockSampler(0) as clk:
+            for k in range(steps):
+                flush.fill_(k)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                sts.append(one(te=time_eval))
+                b.record(stream)
+                torch.cuda.synchronize()
+                ms += a.elapsed_time(b)
+        comps, F = work.cost(stream=sptr)
+        per = work.stats(stream=sptr)
+        return dict(ms=ms, stats=sts, F=F.astype(np.float64), clocks=clk.summary(),
+                    passes=[int(x[4]) for x in per]), work
+
+    res_l, work_l = arm(inst_l, LEARNED_SWEEP, args.warmup, args.steps, time_eval=True)
+    res_p, _ = arm(inst_p, 0, 1, args.plain_steps)
+    res_e, _ = arm(inst_e, LEARNED_SWEEP, 1, 1)
+
+    def summary(r, steps):
+        moves = sum(x.moves_scored for x in r["stats"])
+        return {"descents_per_s": n_sol * steps / (r["ms"] / 1e3), "ms_per_step": r["ms"] / steps,
+                "moves_per_s": moves / (r["ms"] / 1e3), "moves_per_descent": moves / (n_sol * steps),
+                "F_mean": float(r["F"].mean()) / W.SCALE, "passes_max": max(r["passes"]),
+                "passes_mean": float(np.mean(r["passes"]))}
+    L, P, E = summary(res_l, args.steps), summary(res_p, args.plain_steps), summary(res_e, 1)
+    gap = (L["F_mean"] - P["F_mean"]) / P["F_mean"]
+    per_gap = (res_l["F"] - res_p["F"]) / res_p["F"]
+
+    # dominant kernel: the neighbourhood evaluation of the learned descents, timed live
+    sts = res_l["stats"]
+    eval_ms = sum(x.eval_ms for x in sts)
+    eval_launches = sum(x.eval_launches for x in sts)
+    by_op = np.sum([x.moves_by_op for x in sts], axis=0)
+    alg_bytes = float(sum(int(by_op[o]) * ALG_BYTES[o] for o in range(W.N_OPS)))
+    achieved = alg_bytes / (eval_ms / 1e3) / 1e9
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    peak = float(peaks.get("hbm_gbs", 6400.0))
+
+    # end to end with host buffers: routes and operator order H2D, descent, costs D2H
+    nodes, offs, per = mdls.flatten(sols)
+    h_perm = np.ascontiguousarray(perm)
+    e2e_ms = []
+    for k in range(min(args.steps, 3)):
+        flush.fill_(k)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        work_l.load_flat(nodes, offs, per, stream=sptr)
+        work_l.descend(h_perm, MAX_PASS, multi=True, use_graph=True, poll_every=1, stream=sptr,
+                       n_groups=args.groups, sweep_every=LEARNED_SWEEP)
+        comps, F = work_l.cost(stream=sptr)
+        e2e_ms.append(1e3 * (time.perf_counter() - t0))
+    h2d = nodes.nbytes + 16 * int(per.sum()) + h_perm.nbytes
+    d2h = comps.nbytes + F.nbytes
+
+    cpu = None
+    if pool is not None:
+        nbr, cnt = inst_l.neighbors()
+        nproc = pool._processes
+        t0 = time.perf_counter()
+        out = pool.map(_oracle_learned, [(i % n_sol, n_sol, nbr, cnt, 1) for i in range(nproc)])
+        wall = time.perf_counter() - t0
+        m = sum(o[0] for o in out)
+        cpu_s = sum(o[1] for o in out)
+        desc = (f"{nproc} processes, each the first pass (5 pruned steps) of one learned descent "
+                f"with the same top-64 lists; {m} moves in {cpu_s:.1f} s CPU, {wall:.1f} s wall; "
+                f"descents/s = oracle moves/s / the GPU's moves per learned descent")
+        cpu = {"value": (m / wall) / L["moves_per_descent"], "unit": "descents/s", "cores": nproc,
+               "kind": "oracle", "sample": desc, "moves_per_s": m / wall}
+        pool.close()
+
+    print(json.dumps({
+        "metric": "LS descents/s", "value": L["descents_per_s"], "unit": "descents/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": L["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32/f64 (bf16 MLP)",
+        "data": "synthetic",
+        "config": {"workload": f"learned-20x10000: MDVRPTW 20 depots x 10000 customers on "
+                               f"[-1000,1000]^2, horizon 4000, Q=200, N_V=60, D=4000; {n_sol} "
+                               f"solutions (window-ordered sweep routes) descended to a local "
+                               f"optimum (delta={MAX_PASS}), multi-move; learned top-{LEARNED_TOPK} "
+                               f"of a {LEARNED_POOL} eta pool, full sweep every {LEARNED_SWEEP} steps",
+                   "l2": "flushed between timed steps (256 MB write)", "route_slots": R, "k_max": K,
+                   "stream_groups": args.groups},
+        "learned": L, "plain_full": P, "eta_top64": E,
+        "speedup_vs_plain": L["descents_per_s"] / P["descents_per_s"],
+        "cost_gap_vs_plain": gap, "cost_gap_per_solution_max": float(per_gap.max()),
+        "speedup_vs_eta_top64": L["descents_per_s"] / E["descents_per_s"],
+        "cost_gap_vs_eta_top64": (L["F_mean"] - E["F_mean"]) / E["F_mean"],
+        "setup": {"label_logging_s": t_log, "training_s": t_train, "train_loss_first_last": [losses[0], losses[-1]],
+                  "positives": [int(d[2].sum()) for d in data], "prune_ms": prune_ms},
+        "roofline": {"kernel": "k_eval (neighbourhood evaluation, learned descents)", "bound": "hbm",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "peak_source": "measured" if "hbm_gbs" in peaks else "fallback", "traffic": None,
+                     "eval_ms_per_launch": eval_ms / max(eval_launches, 1),
+                     "alg_bytes_per_launch": alg_bytes / max(eval_launches, 1)},
+        "cpu_baseline": cpu,
+        "e2e": {"value": n_sol / (statistics.mean(e2e_ms) / 1e3), "unit": "descents/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": statistics.mean(e2e_ms)},
+        "gpu_launches": int(sum(x.launches for x in sts) + 3 * args.steps),
+        "clocks": res_l["clocks"], "clocks_plain": res_p["clocks"],
+    }))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -406,7 +599,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["mdvrptw-6x288", "batch16-uneven"], default="mdvrptw-6x288")
+    ap.add_argument("--workload", choices=["mdvrptw-6x288", "batch16-uneven", "learned-20x10000"],
+                    default="mdvrptw-6x288")
+    ap.add_argument("--solutions", type=int, default=0, help="solutions of the learned workload (0: 8)")
+    ap.add_argument("--plain-steps", type=int, default=1,
+                    help="timed plain full-neighbourhood descents beside the learned workload")
     ap.add_argument("--max-pass", type=int, default=4, help="passes per step of the batch workload")
     ap.add_argument("--groups", type=int, default=2,
                     help="solution groups advancing on concurrent streams inside the graph")
@@ -415,6 +612,8 @@ def main():
         run_reference(args)
     elif args.workload == "batch16-uneven":
         run_batch(args)
+    elif args.workload == "learned-20x10000":
+        run_learned(args)
     else:
         run_ours(args)
 

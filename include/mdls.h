@@ -129,7 +129,11 @@ typedef struct md_config {
                                (needs a non-NULL stream); results do not depend on it */
     int32_t sweep_every;    /* > 0: every sweep_every-th step of a solution evaluates the full
                                neighbourhood (all customers) instead of the neighbour lists; the
-                               fallback of pruned lists.  0: never */
+                               fallback of pruned lists.  A pass that applies nothing is then
+                               followed by a verification pass whose steps evaluate the full
+                               neighbourhood until one applies a move; the descent ends only
+                               when a verification pass applies nothing (or at max_pass).
+                               0: never (the descent ends at the first pass applying nothing) */
 } md_config;
 
 /* Totals over all solutions of one md_descend call. */

@@ -848,7 +848,10 @@ typedef struct {
 
 /* MDFIS (Alg. 2): repeat passes over the operators in the given order per pass until a pass
    applies nothing or max_pass passes ran.  perm is [max_pass * n_ops] operator indices.
-   sweep_every > 0: every sweep_every-th step evaluates all customers instead of the lists. */
+   sweep_every > 0: every sweep_every-th step evaluates all customers instead of the lists, and
+   a pass that applies nothing does not end the descent at once: the next pass evaluates all
+   customers in each step until a step applies a move, and only a pass that applied nothing
+   this way ends it (the full neighbourhood confirms the local optimum the lists reached). */
 int or_descend(const OInst *I, const int32_t *nodes, const int64_t *off, int nr,
                const uint8_t *perm, int n_ops, int max_pass, int multi, int lambda_update,
                float *lam, int32_t *out_nodes, int64_t *out_off, int64_t node_cap, int route_cap,
@@ -859,6 +862,7 @@ int or_descend(const OInst *I, const int32_t *nodes, const int64_t *off, int nr,
     OMove *mv = (OMove *)malloc(sizeof(OMove) * cap);
     int *sel = NULL;
     int ntrace = 0;
+    int verify = 0;
     for (int pass = 0; pass < max_pass; pass++) {
         int improved = 0;
         for (int t = 0; t < n_ops; t++) {
@@ -868,7 +872,7 @@ int or_descend(const OInst *I, const int32_t *nodes, const int64_t *off, int nr,
             double w[4];
             weights(I, lam, w);
             int64_t scored = 0;
-            const int full = sweep_every > 0 && (st->steps + 1) % sweep_every == 0;
+            const int full = (sweep_every > 0 && (st->steps + 1) % sweep_every == 0) || verify;
             int64_t n = enumerate(&C, op, w, mv, cap, &scored, full);
             if (n > cap) {
                 free(mv);
@@ -889,6 +893,7 @@ int or_descend(const OInst *I, const int32_t *nodes, const int64_t *off, int nr,
                 sol_free(S);
                 S = N;
                 improved = 1;
+                verify = 0;
                 st->accepted_steps++;
                 st->applied_moves += ns;
                 if (lambda_update) {
@@ -904,7 +909,10 @@ int or_descend(const OInst *I, const int32_t *nodes, const int64_t *off, int nr,
             }
         }
         st->passes++;
-        if (!improved) break;
+        if (!improved) {
+            if (sweep_every > 0 && !verify) verify = 1;
+            else break;
+        }
     }
     int r = sol_to_flat(S, out_nodes, out_off, node_cap, route_cap);
     free(mv);

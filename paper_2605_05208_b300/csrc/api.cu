@@ -45,7 +45,7 @@ __global__ void k_descend_init(DevSols D, int n_ops, int max_pass, int multi, in
     int *st = D.state + (size_t)s * MD_STATE;
     st[0] = 0; st[1] = 0; st[2] = 0; st[3] = 0;
     st[4] = n_ops; st[5] = max_pass; st[6] = multi; st[7] = lup;
-    st[8] = sweep; st[9] = 0;
+    st[8] = sweep; st[9] = 0; st[10] = 0;
     for (int k = 0; k < 16; k++) D.stats[(size_t)s * 16 + k] = 0;
     D.ops[s] = (int)D.perm[(size_t)s * max_pass * n_ops] | (sweep == 1 ? MD_OP_SWEEP : 0);
 }

@@ -67,7 +67,7 @@ struct DevSols {
     double *w;
     int32_t *ops;      // [S] operator of the current step (-1 = none)
     int32_t *state;    // [S * 16] pass, slot, improved, done, n_ops, max_pass, multi, lambda_update,
-                       // sweep period (0: never), step index
+                       // sweep period (0: never), step index, verification pass
     long long *stats;  // [S * 16] moves scored, steps, accepted, applied, passes; [8+op] moves per op
     int32_t *err;      // [1] first error code raised on the device
     const uint8_t *perm; // [S * max_pass * n_ops] operator order (descent only)

@@ -399,20 +399,28 @@ __device__ void step_body(const DevInst &I, const DevSols &D, const DevMoves &M,
         stt[8 + (D.ops[s] & MD_OP_MASK)] += (long long)M.nscored[s];
         M.nscored[s] = 0;
         stt[1] += 1;
-        if (nsel > 0) { stt[2] += 1; stt[3] += nsel; st[2] = 1; }
+        if (nsel > 0) { stt[2] += 1; stt[3] += nsel; st[2] = 1; st[10] = 0; }
         int pass = st[0], slot = st[1] + 1;
         if (slot == n_ops) {
             stt[4] += 1;
             pass += 1;
             slot = 0;
-            if (!st[2] || pass >= max_pass) st[3] = 1;
+            // with pruned lists (sweep period > 0) a pass that applied nothing is followed by a
+            // verification pass whose steps evaluate the full neighbourhood until one applies a
+            // move (st[10]); the descent ends when a whole verification pass applies nothing
+            if (!st[2]) {
+                if (st[8] > 0 && !st[10]) st[10] = 1;
+                else st[3] = 1;
+            }
+            if (pass >= max_pass) st[3] = 1;
             st[2] = 0;
         }
         st[0] = pass;
         st[1] = slot;
-        // full plain sweep on every sweep-th step (st[8] = period, st[9] = steps done)
+        // full plain sweep on every sweep-th step (st[8] = period, st[9] = steps done) and on
+        // the steps of a verification pass
         const int step = ++st[9];
-        const bool sweep = st[8] > 0 && (step + 1) % st[8] == 0;
+        const bool sweep = (st[8] > 0 && (step + 1) % st[8] == 0) || st[10];
         D.ops[s] = st[3] ? -1 : ((int)D.perm[((size_t)s * max_pass + pass) * n_ops + slot] | (sweep ? MD_OP_SWEEP : 0));
     }
 }

@@ -307,12 +307,14 @@ def _depot_sweeps(inst: InstanceSpec) -> list[list[int]]:
 
 
 def initial_solution(inst: InstanceSpec, seed: int, sol_index: int, n_random: int = 10,
-                     shuffle_start: bool = True) -> list[list[int]]:
+                     shuffle_start: bool = True, order: str = "sweep") -> list[list[int]]:
     """One seeded initial solution as a list of routes [ds, c1..cL, de] (node ids).
 
     Nearest depot by squared integer distance (tie -> lower depot id); per depot an angular
-    sweep (start angle rotated per solution when shuffle_start) split greedily at Q; then
-    n_random uniformly random relocations (customer, target route, position)."""
+    sweep (start angle rotated per solution when shuffle_start) split greedily at Q; with
+    order="window" each route's customers are then visited by window midpoint (tie -> id)
+    instead of by angle; then n_random uniformly random relocations (customer, target route,
+    position)."""
     nd, nc = inst.n_depots, inst.n_customers
     st = Stream(seed, 10, sol_index)
     routes: list[list[int]] = []
@@ -334,6 +336,11 @@ def initial_solution(inst: InstanceSpec, seed: int, sol_index: int, n_random: in
             load += qc
         if cur:
             routes.append([d] + cur + [d])
+    if order == "window":
+        mid = inst.tw_early + inst.tw_late
+        routes = [[r[0]] + sorted(r[1:-1], key=lambda c: (int(mid[c]), c)) + [r[-1]] for r in routes]
+    elif order != "sweep":
+        raise ValueError(f"unknown route order {order!r}")
     for _ in range(n_random):
         c = int(st.randint(nd, nd + nc - 1, 1)[0])
         ri = next(i for i, r in enumerate(routes) if c in r[1:-1])
@@ -347,9 +354,9 @@ def initial_solution(inst: InstanceSpec, seed: int, sol_index: int, n_random: in
 
 
 def initial_solutions(inst: InstanceSpec, seed: int, n: int | None = None,
-                      n_random: int = 10) -> list[list[list[int]]]:
+                      n_random: int = 10, order: str = "sweep") -> list[list[list[int]]]:
     n = inst.n_solutions if n is None else n
-    return [initial_solution(inst, seed, i, n_random=n_random) for i in range(n)]
+    return [initial_solution(inst, seed, i, n_random=n_random, order=order) for i in range(n)]
 
 
 def flatten_solutions(sols: list[list[list[int]]]):

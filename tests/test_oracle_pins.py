@@ -635,11 +635,37 @@ def test_sweep_every_step_equals_full_neighbourhood(oracle_lib):
     nbr, cnt = random_neighbor_lists(spec, 4, 3)
     I.set_neighbors(nbr, cnt)
     swept = I.descend(sol, perm, 60, sweep_every=1)
+    assert full.passes < 60
     assert W.canonical(swept.solution) == W.canonical(full.solution)
-    assert swept.moves_scored == full.moves_scored
+    # the same passes, then one verification pass over the (unchanged) local optimum, which
+    # scores exactly what the last pass of the plain descent scored
+    assert swept.passes == full.passes + 1 and swept.steps == full.steps + W.N_OPS
+    assert swept.applied_moves == full.applied_moves
     I0 = oracle_lib.Instance(spec)
     I0.set_neighbors(nbr, cnt)
     mv, _ = I0.eval_op(sol, W.OP_RELOCATE)
     allowed = {(spec.n_depots + cu, int(v)) for cu in range(spec.n_customers) for v in nbr[cu]}
     assert all(((int(m["id"]) >> 18) & 0x3FFF, (int(m["id"]) >> 4) & 0x3FFF) in allowed for m in mv)
 
+
+
+@pytest.mark.parametrize("sweep", [3, 50])
+def test_pruned_descent_ends_at_a_full_neighbourhood_local_optimum(oracle_lib, sweep):
+    # Lists of 2 random candidates miss most improving moves; the verification pass makes the
+    # descent end only where no operator has an improving move over all customers.
+    spec = tiny_spec(59, nd=2, nc=24, tw=True, Q=40, NV=3, D=300, horizon=2000, wmin=100, wmax=800)
+    sol = random_solution(spec, 59)
+    perm = W.op_permutations(59, 1, 200)[0]
+    nbr, cnt = random_neighbor_lists(spec, 2, 8)
+    I = oracle_lib.Instance(spec)
+    I.set_neighbors(nbr, cnt)
+    d = I.descend(sol, perm, 200, sweep_every=sweep)
+    assert d.passes < 200
+    full = oracle_lib.Instance(spec)
+    for op in range(W.N_OPS):
+        mv, _ = full.eval_op(d.solution, op)
+        assert len(mv) == 0 or mv["dF"].min() >= 0.0
+    # without the sweep the same lists stop earlier, at a point the full neighbourhood improves
+    d0 = I.descend(sol, perm, 200, sweep_every=0)
+    best = min((full.eval_op(d0.solution, op)[0]["dF"].min(initial=0.0) for op in range(W.N_OPS)))
+    assert best < 0.0
