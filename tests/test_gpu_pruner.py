@@ -197,3 +197,36 @@ def test_pruned_descent_serves_everyone(md):
     for sol in S.read():
         assert sorted(c for r in sol for c in r[1:-1]) == list(range(spec.n_depots, spec.n_nodes))
     assert st.moves_scored > 0
+
+
+def test_logged_pairs_match_oracle_steps(md, oracle_lib):
+    # Training labels: the (u, v) pairs of every Relocate / Swap / 2-opt* move that the plain
+    # full-neighbourhood multi-move descent applies, stepped here by the oracle.
+    from paper_2605_05208_b300 import learned
+    spec = W.gen_mdvrptw(67, n_depots=2, n_customers=40, theta=0)
+    sols = W.initial_solutions(spec, 67, 3)
+    perm = W.op_permutations(68, 3, 50)
+    got = learned.plain_selected_pairs(spec, sols, perm, 50)
+    o = oracle_lib.Instance(spec)
+    want = set()
+    for s, sol in enumerate(sols):
+        for p in range(50):
+            improved = False
+            for t in range(W.N_OPS):
+                mv, _ = o.eval_op(sol, int(perm[s, p, t]))
+                ids = o.select(mv, len(sol), multi=True)
+                if ids:
+                    improved = True
+                    sol = o.apply(sol, ids)
+                want |= {((i >> 18) & 0x3FFF, (i >> 4) & 0x3FFF) for i in ids
+                         if (i >> 32) <= W.OP_TWO_OPT_STAR}
+            if not improved:
+                break
+    assert len(want) > 10 and got == want
+    inst = md.Instance(spec)
+    inst.build_neighbors(12)
+    lab = learned.pool_labels(inst, got)
+    nbr, cnt = inst.neighbors()
+    for cu in range(spec.n_customers):
+        for i in range(cnt[cu]):
+            assert lab[cu, i] == ((spec.n_depots + cu, int(nbr[cu, i])) in want)
