@@ -7,8 +7,9 @@
 // 1- and 2-node sequences -- is computed once per warp) and its 32 lanes walk u's candidate
 // list v.  An inter-route move costs O(1): two or four concatenations of prefix/suffix
 // summaries gathered by customer id.  An intra-route move (u and v on one route) takes the
-// prefix before and the suffix after the rearranged part from the same summaries and folds only
-// the customers strictly between u's and v's sequences.
+// prefix before and the suffix after the rearranged part from the same summaries and the
+// customers strictly between u's and v's sequences from the route's subsequence tables, so it
+// costs O(1) as well.
 //
 // The FP64 penalised delta dF is needed only for the leader (Section 3.2.5): a move whose
 // integer deltas make dF >= 0 certain, or whose FP32 estimate (with a margin ten times its
@@ -18,7 +19,8 @@
 #include "mdls_internal.cuh"
 
 #ifndef MD_EVAL_MIN_BLOCKS
-#define MD_EVAL_MIN_BLOCKS 2  // evaluation blocks resident per SM (register budget 65536 / (256 x this))
+// evaluation blocks resident per SM: 16 warps per SM, a register budget of 128 per thread
+#define MD_EVAL_MIN_BLOCKS (16 / MD_EVAL_WARPS)
 #endif
 
 namespace {
@@ -191,17 +193,16 @@ __device__ __forceinline__ SN sn_suffix(const Ctx &C, int n) {
     return n == MD_NONE ? sn_none() : sn(suffix_from(C, n), n, n);
 }
 
-// Customers at positions lo..hi (1-based, lo <= hi) of route row rn, folded left to right.
-template <bool TW>
-__device__ SN fold_mid(const Ctx &C, const int32_t *rn, int lo, int hi) {
-    int n = rn[lo - 1];
-    SN r = sn(nseg(C, n), n, n);
-    for (int k = lo + 1; k <= hi; k++) {
-        const int m = rn[k - 1];
-        r.s = seg_cat<TW>(r.s, nseg(C, m), cost(C.I, r.l, m));
-        r.l = m;
-    }
-    return r;
+// The customers from c's position to t positions later (sub_fwd) or earlier (sub_bwd) on c's
+// route, from the subsequence tables the route rebuild keeps.
+__device__ __forceinline__ SN sub_fwd(const Ctx &C, int c, int t) {
+    const Seg8 e = ldg_seg8(&C.D.csubf[((size_t)C.s * C.I.nc + (c - C.I.nd)) * C.D.K + t]);
+    return sn(seg_of(e), e.a, e.b);
+}
+
+__device__ __forceinline__ SN sub_bwd(const Ctx &C, int c, int t) {
+    const Seg8 e = ldg_seg8(&C.D.csubb[((size_t)C.s * C.I.nc + (c - C.I.nd)) * C.D.K + t]);
+    return sn(seg_of(e), e.a, e.b);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -240,8 +241,8 @@ __device__ void eval_relocate(const Ctx &C, int cu, int lane, Best &b) {
         const Seg8 Pv = pre8(C, v), Sv = suf8(C, v);
         const int B = Pv.a, j = Pv.b, sv = Sv.b;
         if (B == A) {
-            // intra-route: prefix before and suffix after the rearranged part, middle folded
-            const int32_t *rn = C.D.rnodes + sA * C.D.K;
+            // intra-route: prefix before and suffix after the rearranged part, the customers
+            // between them from the subsequence tables
             for (int var = 0; var < 6; var++) {
                 const int k = var >= 2 ? 2 : 1;
                 const bool rev = var >= 4, before = var & 1;
@@ -255,10 +256,10 @@ __device__ void eval_relocate(const Ctx &C, int cu, int lane, Best &b) {
                 SN g;
                 if (at < p) {
                     const SN head = at == 0 ? sn(nseg(C, dsA), dsA, dsA) : sn(seg_of(Pv), dsA, v);
-                    const SN mid = at + 1 <= p - 1 ? fold_mid<TW>(C, rn, at + 1, p - 1) : sn_none();
+                    const SN mid = at + 1 <= p - 1 ? sub_bwd(C, pu, p - 2 - at) : sn_none();  // at+1..p-1
                     g = sn_cat<TW>(C, sn_cat<TW>(C, sn_cat<TW>(C, head, q), mid), sn_suffix(C, k == 1 ? su : sx));
                 } else {
-                    const SN mid = fold_mid<TW>(C, rn, p + k, at);
+                    const SN mid = sub_fwd(C, k == 1 ? su : sx, at - p - k);  // p+k..at
                     g = sn_cat<TW>(C, sn_cat<TW>(C, sn_cat<TW>(C, sn(PP, dsA, pu), mid), q), sn_suffix(C, sv));
                 }
                 const RT nA = rt_of(g.s, I);
@@ -343,7 +344,6 @@ __device__ void eval_swap(const Ctx &C, int cu, int lane, Best &b) {
         }
         if (B == A) {
             // intra-route: prefix, one sequence, the customers between them, the other sequence, suffix
-            const int32_t *rn = C.D.rnodes + sA * C.D.K;
             for (int var = 0; var < nvar; var++) {
                 const int ku = SW_KU[var], kv = SW_KV[var];
                 const bool ru = SW_RU[var], rvv = SW_RV[var];
@@ -353,11 +353,11 @@ __device__ void eval_swap(const Ctx &C, int cu, int lane, Best &b) {
                 const SN qu = ku == 1 ? sn(u1, u, u) : (ru ? sn(u2r, x, u) : sn(u2, u, x));
                 SN g;
                 if (p < j) {
-                    const SN mid = p + ku <= j - 1 ? fold_mid<TW>(C, rn, p + ku, j - 1) : sn_none();
+                    const SN mid = p + ku <= j - 1 ? sub_fwd(C, ku == 1 ? su : sx, j - 1 - p - ku) : sn_none();
                     g = sn_cat<TW>(C, sn(PU, dsA, pu), qv);
                     g = sn_cat<TW>(C, sn_cat<TW>(C, sn_cat<TW>(C, g, mid), qu), sn_suffix(C, kv == 1 ? sv : sy));
                 } else {
-                    const SN mid = j + kv <= p - 1 ? fold_mid<TW>(C, rn, j + kv, p - 1) : sn_none();
+                    const SN mid = j + kv <= p - 1 ? sub_bwd(C, pu, p - 1 - j - kv) : sn_none();
                     g = sn_cat<TW>(C, sn(prefix_through(C, pv), dsA, pv), qu);
                     g = sn_cat<TW>(C, sn_cat<TW>(C, sn_cat<TW>(C, g, mid), qv), sn_suffix(C, ku == 1 ? su : sx));
                 }
@@ -549,7 +549,7 @@ __device__ __forceinline__ void warp_commit(const Ctx &C, Best &b, size_t slot, 
 }
 
 template <bool TW>
-__global__ void __launch_bounds__(256, MD_EVAL_MIN_BLOCKS) k_eval(DevInst I, DevSols D, DevMoves M, uint32_t flags, int s0) {
+__global__ void __launch_bounds__(32 * MD_EVAL_WARPS, MD_EVAL_MIN_BLOCKS) k_eval(DevInst I, DevSols D, DevMoves M, uint32_t flags, int s0) {
     Ctx C;
     C.I = I; C.D = D; C.M = M; C.flags = flags;
     C.s = s0 + blockIdx.y;
@@ -574,7 +574,7 @@ __global__ void __launch_bounds__(256, MD_EVAL_MIN_BLOCKS) k_eval(DevInst I, Dev
 // instances of uneven size.  Tiles are taken in grid-stride order over the global work list.
 // TW_ANY: at least one item has time windows; items without them take the TW = false path.
 template <bool TW_ANY>
-__global__ void __launch_bounds__(256, MD_EVAL_MIN_BLOCKS) k_eval_batch(const BatchItem *__restrict__ items, int n_items, int total_tiles,
+__global__ void __launch_bounds__(32 * MD_EVAL_WARPS, MD_EVAL_MIN_BLOCKS) k_eval_batch(const BatchItem *__restrict__ items, int n_items, int total_tiles,
                                                       uint32_t flags, int *next_tile) {
     // Each warp keeps the context of its current tile in its own shared-memory slot: the
     // instance, solution and scratch descriptors are read from there when needed instead of
@@ -634,9 +634,13 @@ __global__ void __launch_bounds__(256, MD_EVAL_MIN_BLOCKS) k_eval_batch(const Ba
 
 }  // namespace
 
+#ifndef MD_EVAL_UPW
+#define MD_EVAL_UPW 1  // customers per warp of one evaluation launch
+#endif
+
 int md_eval_blocks(const md_solutions *s) {
     int nc = s->inst->d.nc;
-    int b = (nc + MD_EVAL_WARPS - 1) / MD_EVAL_WARPS;
+    int b = (nc + MD_EVAL_WARPS * MD_EVAL_UPW - 1) / (MD_EVAL_WARPS * MD_EVAL_UPW);
     return b < 1024 ? b : 1024;
 }
 

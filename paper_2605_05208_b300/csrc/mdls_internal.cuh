@@ -10,6 +10,9 @@
 //   rcore   Seg8  [S * R]           summary of [c_1..c_L]
 //   cpre    Seg8  [S * nc]          summary of [ds..c] plus {route slot, position} of c
 //   csuf    Seg8  [S * nc]          summary of [c..de] ([c..c_L] if open) plus {pred, succ}
+//   csubf   Seg8  [S * nc * K]      csubf[c][t]: customers at positions p(c)..p(c)+t of c's route
+//   csubb   Seg8  [S * nc * K]      csubb[c][t]: customers at positions p(c)-t..p(c)
+//                                   (both with {first node, last node}; for intra-route moves)
 //   dcount  int32 [S * nd]          non-empty routes departing from each depot
 //   tot     int64 [S * 8]           D, TW, LoadEx, DurEx, closures, vehicle excess, V4, routes
 //   lam     float [S * 4], w double [S * 4]  penalty coefficients and FP64 weights
@@ -26,7 +29,9 @@
 #define MD_NONE (-1)
 #define MD_MAX_OPS 8
 #define MD_EMPTY_KEY 0xFFFFFFFFFFFFFFFFull
+#ifndef MD_EVAL_WARPS
 #define MD_EVAL_WARPS 8  // warps per evaluation block; one leader record per warp
+#endif
 #define MD_STATE 16      // ints of per-solution descent state
 #define MD_OP_SWEEP 0x100  // set in ops[s]: this step evaluates the full neighbourhood
 #define MD_OP_MASK 0xff
@@ -61,6 +66,8 @@ struct DevSols {
     Seg8 *rcore;
     Seg8 *cpre;
     Seg8 *csuf;
+    Seg8 *csubf;
+    Seg8 *csubb;
     int32_t *dcount;
     long long *tot;
     float *lam;

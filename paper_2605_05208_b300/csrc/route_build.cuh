@@ -3,6 +3,7 @@
 // For route [ds, c_1..c_L, de] one warp writes, for every customer c_k,
 //   cpre[c_k] = [ds, c_1..c_k]                 and {route slot, k}
 //   csuf[c_k] = [c_k..c_L, de] ([c_k..c_L] open) and {pred node, succ node (MD_NONE: none)}
+//   csubf[c_k][t] = [c_k..c_{k+t}], csubb[c_k][t] = [c_{k-t}..c_k]   and {first, last node}
 // plus rterm = the whole route and rcore = [c_1..c_L].  The concatenation is associative and
 // exact in integers, so the scan tree gives the same summaries as a left-to-right fold.
 #pragma once
@@ -113,6 +114,72 @@ __device__ void rebuild_route(const DevInst &I, const DevSols &D, int s, int r) 
         const int tail = min(31, end - 1);
         rc = shfl_segn(sfx, tail);
         have_rc = true;
+    }
+    // subsequence tables: lane i folds from position k = i + 1 to the route's end and to its
+    // start.  Up to 32 customers, the lanes hold the route's node summaries and arcs and pass
+    // them by shuffles; longer routes fold from memory in chunks of 32 starting positions.
+    if (L <= 32) {
+        const bool act = lane < L;
+        const int c = act ? nodes[lane] : nodes[0];
+        const Seg cs = node_seg(I.node[c]);
+        const int prev = __shfl_up_sync(0xffffffffu, c, 1);
+        const int arc = lane > 0 ? I.dist[(size_t)prev * I.nn + c] : 0;  // arc into position lane
+        const size_t row = ((size_t)s * I.nc + (c - I.nd)) * D.K;
+        Seg8 *F = D.csubf + row;
+        Seg8 *Bk = D.csubb + row;
+        Seg g = cs;
+        if (act) st_seg8(&F[0], g, c, c);
+        for (int t = 1; t < L; t++) {
+            const int src = min(lane + t, 31);
+            SegN x;
+            x.s = cs; x.first = c; x.last = arc;  // last carries the arc into the position
+            x = shfl_segn(x, src);
+            if (lane + t < L) {
+                g = seg_cat<TW>(g, x.s, x.last);
+                st_seg8(&F[t], g, c, x.first);
+            }
+        }
+        g = cs;
+        int nxt_arc = __shfl_down_sync(0xffffffffu, arc, 1);  // arc out of position lane
+        if (act) st_seg8(&Bk[0], g, c, c);
+        for (int t = 1; t < L; t++) {
+            const int src = max(lane - t, 0);
+            SegN x;
+            x.s = cs; x.first = c; x.last = nxt_arc;
+            x = shfl_segn(x, src);
+            if (act && lane - t >= 0) {
+                g = seg_cat<TW>(x.s, g, x.last);
+                st_seg8(&Bk[t], g, x.first, c);
+            }
+        }
+    } else for (int base = 0; base < L; base += 32) {
+        const int k0 = base + lane;  // 0-based position
+        if (k0 >= L) break;
+        const int c = nodes[k0];
+        const size_t row = ((size_t)s * I.nc + (c - I.nd)) * D.K;
+        Seg8 *F = D.csubf + row;
+        Seg8 *Bk = D.csubb + row;
+        const Seg cs = node_seg(I.node[c]);
+        Seg g = cs;
+        int last = c;
+        st_seg8(&F[0], g, c, c);
+#pragma unroll 4
+        for (int t = 1; k0 + t < L; t++) {
+            const int m = nodes[k0 + t];
+            g = seg_cat<TW>(g, node_seg(I.node[m]), I.dist[(size_t)last * I.nn + m]);
+            last = m;
+            st_seg8(&F[t], g, c, m);
+        }
+        g = cs;
+        int first = c;
+        st_seg8(&Bk[0], g, c, c);
+#pragma unroll 4
+        for (int t = 1; k0 - t >= 0; t++) {
+            const int m = nodes[k0 - t];
+            g = seg_cat<TW>(node_seg(I.node[m]), g, I.dist[(size_t)m * I.nn + first]);
+            first = m;
+            st_seg8(&Bk[t], g, m, c);
+        }
     }
     if (lane == 0) {
         SegN whole = open ? carry : segn_cat<TW>(I, carry, segn_node(I, de));

@@ -73,7 +73,8 @@ static void free_sols(md_solutions *S) {
     md_moves_destroy(S->scratch);
     DevSols &d = S->d;
     cudaFree(d.rnodes); cudaFree(d.rhdr); cudaFree(d.rterm); cudaFree(d.rcore);
-    cudaFree(d.cpre); cudaFree(d.csuf); cudaFree(d.dcount); cudaFree(d.tot);
+    cudaFree(d.cpre); cudaFree(d.csuf); cudaFree(d.csubf); cudaFree(d.csubb);
+    cudaFree(d.dcount); cudaFree(d.tot);
     cudaFree(d.lam); cudaFree(d.w); cudaFree(d.ops); cudaFree(d.state); cudaFree(d.stats);
     cudaFree(d.err); cudaFree(S->perm_dev);
     free(S);
@@ -109,6 +110,8 @@ extern "C" md_status md_solutions_create(const md_instance *inst, int32_t n_sol,
     MDA(cudaMalloc(&d.rcore, sizeof(Seg8) * SR));
     MDA(cudaMalloc(&d.cpre, sizeof(Seg8) * (size_t)n_sol * nc));
     MDA(cudaMalloc(&d.csuf, sizeof(Seg8) * (size_t)n_sol * nc));
+    MDA(cudaMalloc(&d.csubf, sizeof(Seg8) * (size_t)n_sol * nc * k_max));
+    MDA(cudaMalloc(&d.csubb, sizeof(Seg8) * (size_t)n_sol * nc * k_max));
     MDA(cudaMalloc(&d.dcount, sizeof(int32_t) * (size_t)n_sol * nd));
     MDA(cudaMalloc(&d.tot, sizeof(long long) * (size_t)n_sol * 8));
     MDA(cudaMalloc(&d.lam, sizeof(float) * (size_t)n_sol * 4));
