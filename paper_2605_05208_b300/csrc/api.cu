@@ -19,7 +19,7 @@ __global__ void k_leaders(DevSols D, DevMoves M, unsigned long long *ids, double
     int valid = 0;
     for (int k = tid; k < M.nblk; k += blockDim.x) {
         LeadRec r = M.lpart[(size_t)s * M.nblk + k];
-        if (r.valid && (!valid || r.f < f || (r.f == f && r.id < id))) { f = r.f; id = r.id; valid = 1; }
+        if (r.id != MD_NO_ID && (!valid || r.f < f || (r.f == f && r.id < id))) { f = r.f; id = r.id; valid = 1; }
     }
     for (int o = 16; o > 0; o >>= 1) {
         const double of = __shfl_xor_sync(0xffffffffu, f, o);

@@ -33,6 +33,7 @@ struct Best {
     double f;
     uint32_t id;
     int valid;
+    uint32_t routes;  // rA | rB << 16 of the best move
     unsigned long long n;
     float fb;  // f rounded towards +inf (0 while there is no candidate): the pruning bound
 };
@@ -140,6 +141,7 @@ __device__ __forceinline__ void offer(const Ctx &C, uint32_t id, int dD, int dTW
         b.f = f;
         b.id = id;
         b.valid = 1;
+        b.routes = (uint32_t)rA | ((uint32_t)rB << 16);
         b.fb = __double2float_ru(f);
     }
     if (C.flags & MD_EVAL_DUMP) {
@@ -516,7 +518,7 @@ __device__ void eval_depot_replace(const Ctx &C, int cu, int lane, Best &b) {
 }
 
 __device__ __forceinline__ void best_init(Best &b) {
-    b.f = 0.0; b.id = 0xffffffffu; b.valid = 0; b.n = 0; b.fb = 0.0f;
+    b.f = 0.0; b.id = MD_NO_ID; b.valid = 0; b.routes = 0; b.n = 0; b.fb = 0.0f;
 }
 
 template <bool TW>
@@ -537,12 +539,13 @@ __device__ __forceinline__ void warp_commit(const Ctx &C, Best &b, size_t slot, 
         const double of = __shfl_xor_sync(0xffffffffu, b.f, o);
         const uint32_t oi = __shfl_xor_sync(0xffffffffu, b.id, o);
         const int ov = __shfl_xor_sync(0xffffffffu, b.valid, o);
+        const uint32_t ort = __shfl_xor_sync(0xffffffffu, b.routes, o);
         b.n += __shfl_xor_sync(0xffffffffu, b.n, o);
-        if (ov && (!b.valid || of < b.f || (of == b.f && oi < b.id))) { b.f = of; b.id = oi; b.valid = 1; }
+        if (ov && (!b.valid || of < b.f || (of == b.f && oi < b.id))) { b.f = of; b.id = oi; b.valid = 1; b.routes = ort; }
     }
     if (lane == 0) {
         LeadRec r;
-        r.f = b.f; r.id = b.id; r.valid = b.valid;
+        r.f = b.f; r.id = b.valid ? b.id : MD_NO_ID; r.routes = b.routes;
         C.M.lpart[(size_t)C.s * C.M.nblk + slot] = r;
         if (b.n) atomicAdd(&C.M.nscored[C.s], b.n);
     }

@@ -83,9 +83,10 @@ struct DevSols {
 // Leader candidate of one block: smallest (dF, id) with dF < 0.
 struct __align__(16) LeadRec {
     double f;
-    uint32_t id;
-    uint32_t valid;
+    uint32_t id;      // MD_NO_ID: no candidate
+    uint32_t routes;  // route slots of the candidate's move: rA | rB << 16
 };
+#define MD_NO_ID 0xffffffffu
 
 struct DevMoves {
     int nblk;              // leader records per solution (evaluation blocks x MD_EVAL_WARPS)

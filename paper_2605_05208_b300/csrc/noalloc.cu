@@ -43,7 +43,7 @@ __global__ void k_noalloc_leaders(DevSols D, const LeadRec *lpart, int nblk, con
     int valid = 0;
     for (int k = tid; k < nblk; k += blockDim.x) {
         const LeadRec r = lpart[(size_t)s * nblk + k];
-        if (r.valid && (!valid || r.f < f || (r.f == f && r.id < id))) { f = r.f; id = r.id; valid = 1; }
+        if (r.id != MD_NO_ID && (!valid || r.f < f || (r.f == f && r.id < id))) { f = r.f; id = r.id; valid = 1; }
     }
     for (int o = 16; o > 0; o >>= 1) {
         const double of = __shfl_xor_sync(0xffffffffu, f, o);

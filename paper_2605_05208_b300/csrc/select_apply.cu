@@ -36,48 +36,41 @@ __device__ __forceinline__ StepSmem carve(unsigned char *base, int R, int nd, in
     return m;
 }
 
-__device__ __forceinline__ void move_routes(const DevInst &I, const DevSols &D, int s, int op, uint32_t id,
-                                            int &rA, int &rB) {
-    const int u = (id >> 18) & 0x3fff, v = (id >> 4) & 0x3fff;
-    rA = D.cpre[(size_t)s * I.nc + (u - I.nd)].a;
-    rB = (op <= MD_OP_TWO_OPT_STAR) ? D.cpre[(size_t)s * I.nc + (v - I.nd)].a : rA;
-}
-
 // Leader + followers of solution s into M.sel / M.nsel.  Returns the number selected.
 __device__ int select_moves(const DevInst &I, const DevSols &D, const DevMoves &M, int s, int multi,
                             const StepSmem &sm, int nrec) {
     __shared__ double lf[32];
-    __shared__ uint32_t lid[32];
+    __shared__ uint32_t lid[32], lrt[32];
     __shared__ int lv[32];
     __shared__ int s_n, s_ncand, s_rA, s_rB;
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
     const int R = D.R;
     // leader
     double f = 0.0;
-    uint32_t id = 0xffffffffu;
+    uint32_t id = MD_NO_ID, rt = 0;
     int valid = 0;
     for (int k = tid; k < nrec; k += nt) {
         LeadRec r = M.lpart[(size_t)s * M.nblk + k];
-        if (r.valid && (!valid || r.f < f || (r.f == f && r.id < id))) { f = r.f; id = r.id; valid = 1; }
+        if (r.id != MD_NO_ID && (!valid || r.f < f || (r.f == f && r.id < id))) { f = r.f; id = r.id; rt = r.routes; valid = 1; }
     }
     for (int o = 16; o > 0; o >>= 1) {
         const double of = __shfl_xor_sync(0xffffffffu, f, o);
         const uint32_t oi = __shfl_xor_sync(0xffffffffu, id, o);
+        const uint32_t ort = __shfl_xor_sync(0xffffffffu, rt, o);
         const int ov = __shfl_xor_sync(0xffffffffu, valid, o);
-        if (ov && (!valid || of < f || (of == f && oi < id))) { f = of; id = oi; valid = 1; }
+        if (ov && (!valid || of < f || (of == f && oi < id))) { f = of; id = oi; rt = ort; valid = 1; }
     }
-    if (lane == 0) { lf[warp] = f; lid[warp] = id; lv[warp] = valid; }
+    if (lane == 0) { lf[warp] = f; lid[warp] = id; lrt[warp] = rt; lv[warp] = valid; }
     __syncthreads();
     if (tid == 0) {
-        f = 0.0; id = 0xffffffffu; valid = 0;
+        f = 0.0; id = MD_NO_ID; rt = 0; valid = 0;
         for (int k = 0; k < (nt + 31) / 32; k++)
-            if (lv[k] && (!valid || lf[k] < f || (lf[k] == f && lid[k] < id))) { f = lf[k]; id = lid[k]; valid = 1; }
+            if (lv[k] && (!valid || lf[k] < f || (lf[k] == f && lid[k] < id))) { f = lf[k]; id = lid[k]; rt = lrt[k]; valid = 1; }
         s_n = 0;
         s_ncand = 0;
         if (valid) {
-            int rA, rB;
-            move_routes(I, D, s, D.ops[s] & MD_OP_MASK, id, rA, rB);
-            s_rA = rA; s_rB = rB;
+            s_rA = (int)(rt & 0xffffu);  // the leader's routes, as the evaluation recorded them
+            s_rB = (int)(rt >> 16);
             M.sel[(size_t)s * R] = id;
             s_n = 1;
         }
@@ -342,7 +335,7 @@ __device__ void apply_selection(const DevInst &I, const DevSols &D, const DevMov
     __syncthreads();
     for (int k = warp; k < s_ntouch; k += nwarps) rebuild_route<TW>(I, D, s, sm.touched[k]);
     __syncthreads();
-    solution_totals(I, D, s, sm.cnt);
+    solution_totals(I, D, s, sm.cnt, false);
 }
 
 // lambda_i <- lambda_i / kappa if term i is violated, else lambda_i * kappa, clamped to
@@ -388,40 +381,57 @@ __device__ void step_body(const DevInst &I, const DevSols &D, const DevMoves &M,
     int *st = D.state + (size_t)s * MD_STATE;
     if (st[3]) return;
     const int n_ops = st[4], max_pass = st[5], multi = st[6], lup = st[7];
+    // thread 0 loads the step's bookkeeping now, so that its loads overlap the selection: the
+    // state, the counters, the scored count and the operator of the next slot
+    long long *stt = D.stats + (size_t)s * 16;
+    int pass = 0, slot = 0, improved = 0, period = 0, step = 0, verify = 0, op = 0, nxt = -1;
+    long long c_sc = 0, c_steps = 0, c_acc = 0, c_app = 0, c_pass = 0, c_op = 0, nsc = 0;
+    if (threadIdx.x == 0) {
+        pass = st[0]; slot = st[1] + 1; improved = st[2];
+        period = st[8]; step = st[9]; verify = st[10];
+        op = D.ops[s] & MD_OP_MASK;
+        c_sc = stt[0]; c_steps = stt[1]; c_acc = stt[2]; c_app = stt[3]; c_pass = stt[4];
+        c_op = stt[8 + op];
+        nsc = (long long)M.nscored[s];
+        if (slot < n_ops) nxt = D.perm[((size_t)s * max_pass + pass) * n_ops + slot];
+        else if (pass + 1 < max_pass) nxt = D.perm[((size_t)s * max_pass + pass + 1) * n_ops];
+    }
     const int nsel = select_moves(I, D, M, s, multi, sm, nrec);
     if (nsel > 0) {
         apply_selection<TW>(I, D, M, s, nsel, sm);
         if (lup) update_lambda(I, D, s);
     }
     if (threadIdx.x == 0) {
-        long long *stt = D.stats + (size_t)s * 16;
-        stt[0] += (long long)M.nscored[s];
-        stt[8 + (D.ops[s] & MD_OP_MASK)] += (long long)M.nscored[s];
+        stt[0] = c_sc + nsc;
+        stt[8 + op] = c_op + nsc;
         M.nscored[s] = 0;
-        stt[1] += 1;
-        if (nsel > 0) { stt[2] += 1; stt[3] += nsel; st[2] = 1; st[10] = 0; }
-        int pass = st[0], slot = st[1] + 1;
+        stt[1] = c_steps + 1;
+        if (nsel > 0) { stt[2] = c_acc + 1; stt[3] = c_app + nsel; improved = 1; verify = 0; }
+        int done = 0;
         if (slot == n_ops) {
-            stt[4] += 1;
+            stt[4] = c_pass + 1;
             pass += 1;
             slot = 0;
             // with pruned lists (sweep period > 0) a pass that applied nothing is followed by a
             // verification pass whose steps evaluate the full neighbourhood until one applies a
-            // move (st[10]); the descent ends when a whole verification pass applies nothing
-            if (!st[2]) {
-                if (st[8] > 0 && !st[10]) st[10] = 1;
-                else st[3] = 1;
+            // move; the descent ends when a whole verification pass applies nothing
+            if (!improved) {
+                if (period > 0 && !verify) verify = 1;
+                else done = 1;
             }
-            if (pass >= max_pass) st[3] = 1;
-            st[2] = 0;
+            if (pass >= max_pass) done = 1;
+            improved = 0;
         }
         st[0] = pass;
         st[1] = slot;
-        // full plain sweep on every sweep-th step (st[8] = period, st[9] = steps done) and on
-        // the steps of a verification pass
-        const int step = ++st[9];
-        const bool sweep = (st[8] > 0 && (step + 1) % st[8] == 0) || st[10];
-        D.ops[s] = st[3] ? -1 : ((int)D.perm[((size_t)s * max_pass + pass) * n_ops + slot] | (sweep ? MD_OP_SWEEP : 0));
+        st[2] = improved;
+        st[3] = done;
+        st[10] = verify;
+        // full plain sweep on every period-th step (st[8], st[9] = steps done) and on the steps
+        // of a verification pass
+        st[9] = ++step;
+        const bool sweep = (period > 0 && (step + 1) % period == 0) || verify;
+        D.ops[s] = done ? -1 : (nxt | (sweep ? MD_OP_SWEEP : 0));
     }
 }
 

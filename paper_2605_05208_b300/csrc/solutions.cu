@@ -29,7 +29,7 @@ __global__ void k_rebuild_all(DevInst I, DevSols D) {
 
 __global__ void k_totals(DevInst I, DevSols D) {
     extern __shared__ int cnt_sm[];
-    solution_totals(I, D, blockIdx.x, cnt_sm);
+    solution_totals(I, D, blockIdx.x, cnt_sm, true);
 }
 
 __global__ void k_fill_lambda(DevSols D, float v) {

@@ -12,8 +12,10 @@ static __device__ void compute_weights(const DevInst &I, const float *lam, doubl
     w[3] = __dmul_rn((double)lam[3], (double)I.Theta);
 }
 
-// Solution totals from the route summaries: one block per solution.
-static __device__ void solution_totals(const DevInst &I, const DevSols &D, int s, int *cnt_sm) {
+// Solution totals from the route summaries: one block per solution.  weights: also recompute the
+// FP64 weights (after lambda changed outside a descent step; a step that updates lambda
+// recomputes them itself).
+static __device__ void solution_totals(const DevInst &I, const DevSols &D, int s, int *cnt_sm, bool weights) {
     __shared__ long long red[8][32];
     const int tid = threadIdx.x, nt = blockDim.x;
     for (int d = tid; d < I.nd; d += nt) cnt_sm[d] = 0;
@@ -51,7 +53,7 @@ static __device__ void solution_totals(const DevInst &I, const DevSols &D, int s
         long long *T = D.tot + (size_t)s * 8;
         T[0] = t[0]; T[1] = t[1]; T[2] = t[2]; T[3] = t[3];
         T[4] = t[4]; T[5] = vex; T[6] = t[4] + vex; T[7] = t[5];
-        compute_weights(I, D.lam + 4 * s, D.w + 4 * s);
+        if (weights) compute_weights(I, D.lam + 4 * s, D.w + 4 * s);
     }
     __syncthreads();
 }
