@@ -207,11 +207,43 @@ __device__ __forceinline__ SN sub_bwd(const Ctx &C, int c, int t) {
     return sn(seg_of(e), e.a, e.b);
 }
 
+// Candidates i0 .. i0 + 63 of customer u (node ids; v = u left out) into the warp's list wl[64]:
+// those on another route than u's route A at the front (ni of them), those on A (when
+// want_intra) at the back (na), so that the warp can run each kind in passes of its own instead
+// of taking both paths in every pass.  Called by all 32 lanes.
+__device__ __forceinline__ void split_candidates(const Ctx &C, int cu, int u, int A, int lane, int *wl,
+                                                 bool want_intra, int i0, int ncand, int &ni, int &na) {
+    const DevInst &I = C.I;
+    const unsigned lt = (1u << lane) - 1u;
+    ni = 0;
+    na = 0;
+#pragma unroll
+    for (int h = 0; h < 64; h += 32) {
+        const int i = i0 + h + lane;
+        bool inter = false, intra = false;
+        int v = 0;
+        if (i < ncand) {
+            v = C.lists ? __ldg(&I.nbr[(size_t)cu * I.theta + i]) : I.nd + i;
+            if (v != u) {
+                const int B = __ldg(&C.D.cpre[(size_t)C.s * I.nc + (v - I.nd)].a);
+                inter = B != A;
+                intra = want_intra && B == A;
+            }
+        }
+        const unsigned mi = __ballot_sync(0xffffffffu, inter), ma = __ballot_sync(0xffffffffu, intra);
+        if (inter) wl[ni + __popc(mi & lt)] = v;
+        if (intra) wl[63 - na - __popc(ma & lt)] = v;
+        ni += __popc(mi);
+        na += __popc(ma);
+    }
+    __syncwarp();
+}
+
 // ------------------------------------------------------------------------------------------
 // Relocate: seq(u) (1 or 2 nodes, possibly reversed) after v, or before v when v is first.
 // ------------------------------------------------------------------------------------------
 template <bool TW>
-__device__ void eval_relocate(const Ctx &C, int cu, int lane, Best &b) {
+__device__ void eval_relocate(const Ctx &C, int cu, int lane, Best &b, int *wl) {
     const DevInst &I = C.I;
     const int u = I.nd + cu;
     const Seg8 Pu = pre8(C, u), Su = suf8(C, u);
@@ -237,68 +269,74 @@ __device__ void eval_relocate(const Ctx &C, int cu, int lane, Best &b) {
     const int dV_empty = ((!C.open && dsA != deA) ? -1 : 0) +
                          veh_delta(C.D.dcount[(size_t)C.s * I.nd + dsA], I.NV, -1);
     const int ncand = C.lists ? I.nnbr[cu] : I.nc;
-    for (int i = lane; i < ncand; i += 32) {
-        const int v = C.lists ? __ldg(&I.nbr[(size_t)cu * I.theta + i]) : I.nd + i;
-        if (v == u) continue;
-        const Seg8 Pv = pre8(C, v), Sv = suf8(C, v);
-        const int B = Pv.a, j = Pv.b, sv = Sv.b;
-        if (B == A) {
-            // intra-route: prefix before and suffix after the rearranged part, the customers
-            // between them from the subsequence tables
+    for (int i0 = 0; i0 < ncand; i0 += 64) {
+        int ni, na;
+        split_candidates(C, cu, u, A, lane, wl, true, i0, ncand, ni, na);
+        const int ni_pad = (ni + 31) & ~31;  // passes run inter-route or intra-route candidates only
+        for (int k = lane; k < ni_pad + na; k += 32) {
+            const int v = k < ni ? wl[k] : (k >= ni_pad ? wl[63 - (k - ni_pad)] : -1);
+            if (v < 0) continue;
+            const Seg8 Pv = pre8(C, v), Sv = suf8(C, v);
+            const int B = Pv.a, j = Pv.b, sv = Sv.b;
+            if (B == A) {
+                // intra-route: prefix before and suffix after the rearranged part, the customers
+                // between them from the subsequence tables
+                for (int var = 0; var < 6; var++) {
+                    const int k = var >= 2 ? 2 : 1;
+                    const bool rev = var >= 4, before = var & 1;
+                    if (rev && !C.sym) continue;
+                    if (k == 2 && !has2) continue;
+                    if (k == 2 && v == x) continue;
+                    if (before && j != 1) continue;
+                    if (!before && !rev && j == p - 1) continue;  // already right after v
+                    const int at = before ? 0 : j;  // seq(u) goes right after this position
+                    const SN q = k == 1 ? sn(q1, u, u) : (rev ? sn(q2r, x, u) : sn(q2, u, x));
+                    SN g;
+                    if (at < p) {
+                        const SN head = at == 0 ? sn(nseg(C, dsA), dsA, dsA) : sn(seg_of(Pv), dsA, v);
+                        const SN mid = at + 1 <= p - 1 ? sub_bwd(C, pu, p - 2 - at) : sn_none();  // at+1..p-1
+                        g = sn_cat<TW>(C, sn_cat<TW>(C, sn_cat<TW>(C, head, q), mid), sn_suffix(C, k == 1 ? su : sx));
+                    } else {
+                        const SN mid = sub_fwd(C, k == 1 ? su : sx, at - p - k);  // p+k..at
+                        g = sn_cat<TW>(C, sn_cat<TW>(C, sn_cat<TW>(C, sn(PP, dsA, pu), mid), q), sn_suffix(C, sv));
+                    }
+                    const RT nA = rt_of(g.s, I);
+                    sink(C, make_id32(u, v, var), nA.dist - oldA.dist, nA.tw - oldA.tw, nA.lex - oldA.lex,
+                         nA.dex - oldA.dex, 0, A, A, b);
+                }
+                continue;
+            }
+            const size_t sB = (size_t)C.s * C.D.R + B;
+            const int dsB = C.D.rhdr[sB].y;
+            const RT oldB = rt_of(seg_of(ldg_seg8(&C.D.rterm[sB])), I);
+            const Seg PV = seg_of(Pv);
+            const bool vfirst = j == 1;
             for (int var = 0; var < 6; var++) {
                 const int k = var >= 2 ? 2 : 1;
                 const bool rev = var >= 4, before = var & 1;
                 if (rev && !C.sym) continue;
                 if (k == 2 && !has2) continue;
-                if (k == 2 && v == x) continue;
-                if (before && j != 1) continue;
-                if (!before && !rev && j == p - 1) continue;  // already right after v
-                const int at = before ? 0 : j;  // seq(u) goes right after this position
-                const SN q = k == 1 ? sn(q1, u, u) : (rev ? sn(q2r, x, u) : sn(q2, u, x));
-                SN g;
-                if (at < p) {
-                    const SN head = at == 0 ? sn(nseg(C, dsA), dsA, dsA) : sn(seg_of(Pv), dsA, v);
-                    const SN mid = at + 1 <= p - 1 ? sub_bwd(C, pu, p - 2 - at) : sn_none();  // at+1..p-1
-                    g = sn_cat<TW>(C, sn_cat<TW>(C, sn_cat<TW>(C, head, q), mid), sn_suffix(C, k == 1 ? su : sx));
+                if (before && !vfirst) continue;
+                const Seg &q = k == 1 ? q1 : (rev ? q2r : q2);
+                const int qf = k == 1 ? u : (rev ? x : u);
+                const int ql = k == 1 ? u : (rev ? u : x);
+                Seg nb;
+                if (before) {
+                    nb = join<TW>(C, nseg(C, dsB), dsB, q, qf);
+                    nb = join<TW>(C, nb, ql, seg_of(Sv), v);
                 } else {
-                    const SN mid = sub_fwd(C, k == 1 ? su : sx, at - p - k);  // p+k..at
-                    g = sn_cat<TW>(C, sn_cat<TW>(C, sn_cat<TW>(C, sn(PP, dsA, pu), mid), q), sn_suffix(C, sv));
+                    nb = join<TW>(C, PV, v, q, qf);
+                    nb = join_opt<TW>(C, nb, ql, sv);
                 }
-                const RT nA = rt_of(g.s, I);
-                sink(C, make_id32(u, v, var), nA.dist - oldA.dist, nA.tw - oldA.tw, nA.lex - oldA.lex,
-                     nA.dex - oldA.dex, 0, A, A, b);
+                const RT nB = rt_of(nb, I);
+                const RT nA = k == 1 ? A1 : A2;
+                const bool emp = LA == k;
+                sink(C, make_id32(u, v, var), nA.dist + nB.dist - oldA.dist - oldB.dist,
+                     nA.tw + nB.tw - oldA.tw - oldB.tw, nA.lex + nB.lex - oldA.lex - oldB.lex,
+                     nA.dex + nB.dex - oldA.dex - oldB.dex, emp ? dV_empty : 0, A, B, b);
             }
-            continue;
         }
-        const size_t sB = (size_t)C.s * C.D.R + B;
-        const int dsB = C.D.rhdr[sB].y;
-        const RT oldB = rt_of(seg_of(ldg_seg8(&C.D.rterm[sB])), I);
-        const Seg PV = seg_of(Pv);
-        const bool vfirst = j == 1;
-        for (int var = 0; var < 6; var++) {
-            const int k = var >= 2 ? 2 : 1;
-            const bool rev = var >= 4, before = var & 1;
-            if (rev && !C.sym) continue;
-            if (k == 2 && !has2) continue;
-            if (before && !vfirst) continue;
-            const Seg &q = k == 1 ? q1 : (rev ? q2r : q2);
-            const int qf = k == 1 ? u : (rev ? x : u);
-            const int ql = k == 1 ? u : (rev ? u : x);
-            Seg nb;
-            if (before) {
-                nb = join<TW>(C, nseg(C, dsB), dsB, q, qf);
-                nb = join<TW>(C, nb, ql, seg_of(Sv), v);
-            } else {
-                nb = join<TW>(C, PV, v, q, qf);
-                nb = join_opt<TW>(C, nb, ql, sv);
-            }
-            const RT nB = rt_of(nb, I);
-            const RT nA = k == 1 ? A1 : A2;
-            const bool emp = LA == k;
-            sink(C, make_id32(u, v, var), nA.dist + nB.dist - oldA.dist - oldB.dist,
-                 nA.tw + nB.tw - oldA.tw - oldB.tw, nA.lex + nB.lex - oldA.lex - oldB.lex,
-                 nA.dex + nB.dex - oldA.dex - oldB.dex, emp ? dV_empty : 0, A, B, b);
-        }
+        __syncwarp();  // the list is read before the next batch overwrites it
     }
 }
 
@@ -311,7 +349,7 @@ __device__ __constant__ int SW_RU[9] = {0, 0, 0, 0, 1, 0, 1, 0, 1};
 __device__ __constant__ int SW_RV[9] = {0, 0, 0, 0, 0, 1, 0, 1, 1};
 
 template <bool TW>
-__device__ void eval_swap(const Ctx &C, int cu, int lane, Best &b) {
+__device__ void eval_swap(const Ctx &C, int cu, int lane, Best &b, int *wl) {
     const DevInst &I = C.I;
     const int u = I.nd + cu;
     const Seg8 Pu = pre8(C, u), Su = suf8(C, u);
@@ -331,66 +369,72 @@ __device__ void eval_swap(const Ctx &C, int cu, int lane, Best &b) {
     }
     const int nvar = C.sym ? 9 : 4;
     const int ncand = C.lists ? I.nnbr[cu] : I.nc;
-    for (int i = lane; i < ncand; i += 32) {
-        const int v = C.lists ? __ldg(&I.nbr[(size_t)cu * I.theta + i]) : I.nd + i;
-        if (v == u) continue;
-        const Seg8 Pv = pre8(C, v), Sv = suf8(C, v);
-        const int B = Pv.a, j = Pv.b, pv = Sv.a, sv = Sv.b;
-        const bool hasy = sv >= I.nd;
-        const int y = hasy ? sv : -1;
-        const int sy = hasy ? suf8(C, y).b : MD_NONE;
-        Seg v1 = nseg(C, v), v2, v2r;
-        if (hasy) {
-            v2 = join<TW>(C, nseg(C, v), v, nseg(C, y), y);
-            v2r = join<TW>(C, nseg(C, y), y, nseg(C, v), v);
-        }
-        if (B == A) {
-            // intra-route: prefix, one sequence, the customers between them, the other sequence, suffix
+    for (int i0 = 0; i0 < ncand; i0 += 64) {
+        int ni, na;
+        split_candidates(C, cu, u, A, lane, wl, true, i0, ncand, ni, na);
+        const int ni_pad = (ni + 31) & ~31;  // passes run inter-route or intra-route candidates only
+        for (int k = lane; k < ni_pad + na; k += 32) {
+            const int v = k < ni ? wl[k] : (k >= ni_pad ? wl[63 - (k - ni_pad)] : -1);
+            if (v < 0) continue;
+            const Seg8 Pv = pre8(C, v), Sv = suf8(C, v);
+            const int B = Pv.a, j = Pv.b, pv = Sv.a, sv = Sv.b;
+            const bool hasy = sv >= I.nd;
+            const int y = hasy ? sv : -1;
+            const int sy = hasy ? suf8(C, y).b : MD_NONE;
+            Seg v1 = nseg(C, v), v2, v2r;
+            if (hasy) {
+                v2 = join<TW>(C, nseg(C, v), v, nseg(C, y), y);
+                v2r = join<TW>(C, nseg(C, y), y, nseg(C, v), v);
+            }
+            if (B == A) {
+                // intra-route: prefix, one sequence, the customers between them, the other sequence, suffix
+                for (int var = 0; var < nvar; var++) {
+                    const int ku = SW_KU[var], kv = SW_KV[var];
+                    const bool ru = SW_RU[var], rvv = SW_RV[var];
+                    if ((ku == 2 && !hasx) || (kv == 2 && !hasy)) continue;
+                    if (!(p + ku - 1 < j || j + kv - 1 < p)) continue;  // overlapping sequences
+                    const SN qv = kv == 1 ? sn(v1, v, v) : (rvv ? sn(v2r, y, v) : sn(v2, v, y));
+                    const SN qu = ku == 1 ? sn(u1, u, u) : (ru ? sn(u2r, x, u) : sn(u2, u, x));
+                    SN g;
+                    if (p < j) {
+                        const SN mid = p + ku <= j - 1 ? sub_fwd(C, ku == 1 ? su : sx, j - 1 - p - ku) : sn_none();
+                        g = sn_cat<TW>(C, sn(PU, dsA, pu), qv);
+                        g = sn_cat<TW>(C, sn_cat<TW>(C, sn_cat<TW>(C, g, mid), qu), sn_suffix(C, kv == 1 ? sv : sy));
+                    } else {
+                        const SN mid = j + kv <= p - 1 ? sub_bwd(C, pu, p - 1 - j - kv) : sn_none();
+                        g = sn_cat<TW>(C, sn(prefix_through(C, pv), dsA, pv), qu);
+                        g = sn_cat<TW>(C, sn_cat<TW>(C, sn_cat<TW>(C, g, mid), qv), sn_suffix(C, ku == 1 ? su : sx));
+                    }
+                    const RT nA = rt_of(g.s, I);
+                    sink(C, make_id32(u, v, var), nA.dist - oldA.dist, nA.tw - oldA.tw, nA.lex - oldA.lex,
+                         nA.dex - oldA.dex, 0, A, A, b);
+                }
+                continue;
+            }
+            const size_t sB = (size_t)C.s * C.D.R + B;
+            const RT oldB = rt_of(seg_of(ldg_seg8(&C.D.rterm[sB])), I);
+            const Seg PV = prefix_through(C, pv);
             for (int var = 0; var < nvar; var++) {
                 const int ku = SW_KU[var], kv = SW_KV[var];
                 const bool ru = SW_RU[var], rvv = SW_RV[var];
                 if ((ku == 2 && !hasx) || (kv == 2 && !hasy)) continue;
-                if (!(p + ku - 1 < j || j + kv - 1 < p)) continue;  // overlapping sequences
-                const SN qv = kv == 1 ? sn(v1, v, v) : (rvv ? sn(v2r, y, v) : sn(v2, v, y));
-                const SN qu = ku == 1 ? sn(u1, u, u) : (ru ? sn(u2r, x, u) : sn(u2, u, x));
-                SN g;
-                if (p < j) {
-                    const SN mid = p + ku <= j - 1 ? sub_fwd(C, ku == 1 ? su : sx, j - 1 - p - ku) : sn_none();
-                    g = sn_cat<TW>(C, sn(PU, dsA, pu), qv);
-                    g = sn_cat<TW>(C, sn_cat<TW>(C, sn_cat<TW>(C, g, mid), qu), sn_suffix(C, kv == 1 ? sv : sy));
-                } else {
-                    const SN mid = j + kv <= p - 1 ? sub_bwd(C, pu, p - 1 - j - kv) : sn_none();
-                    g = sn_cat<TW>(C, sn(prefix_through(C, pv), dsA, pv), qu);
-                    g = sn_cat<TW>(C, sn_cat<TW>(C, sn_cat<TW>(C, g, mid), qv), sn_suffix(C, ku == 1 ? su : sx));
-                }
-                const RT nA = rt_of(g.s, I);
-                sink(C, make_id32(u, v, var), nA.dist - oldA.dist, nA.tw - oldA.tw, nA.lex - oldA.lex,
-                     nA.dex - oldA.dex, 0, A, A, b);
+                // sequence of v placed in A, sequence of u placed in B
+                const Seg &qv = kv == 1 ? v1 : (rvv ? v2r : v2);
+                const int qvf = kv == 1 ? v : (rvv ? y : v), qvl = kv == 1 ? v : (rvv ? v : y);
+                const Seg &qu = ku == 1 ? u1 : (ru ? u2r : u2);
+                const int quf = ku == 1 ? u : (ru ? x : u), qul = ku == 1 ? u : (ru ? u : x);
+                const int afterU = ku == 1 ? su : sx, afterV = kv == 1 ? sv : sy;
+                Seg na = join<TW>(C, PU, pu, qv, qvf);
+                na = join_opt<TW>(C, na, qvl, afterU);
+                Seg nb = join<TW>(C, PV, pv, qu, quf);
+                nb = join_opt<TW>(C, nb, qul, afterV);
+                const RT nA = rt_of(na, I), nB = rt_of(nb, I);
+                sink(C, make_id32(u, v, var), nA.dist + nB.dist - oldA.dist - oldB.dist,
+                     nA.tw + nB.tw - oldA.tw - oldB.tw, nA.lex + nB.lex - oldA.lex - oldB.lex,
+                     nA.dex + nB.dex - oldA.dex - oldB.dex, 0, A, B, b);
             }
-            continue;
         }
-        const size_t sB = (size_t)C.s * C.D.R + B;
-        const RT oldB = rt_of(seg_of(ldg_seg8(&C.D.rterm[sB])), I);
-        const Seg PV = prefix_through(C, pv);
-        for (int var = 0; var < nvar; var++) {
-            const int ku = SW_KU[var], kv = SW_KV[var];
-            const bool ru = SW_RU[var], rvv = SW_RV[var];
-            if ((ku == 2 && !hasx) || (kv == 2 && !hasy)) continue;
-            // sequence of v placed in A, sequence of u placed in B
-            const Seg &qv = kv == 1 ? v1 : (rvv ? v2r : v2);
-            const int qvf = kv == 1 ? v : (rvv ? y : v), qvl = kv == 1 ? v : (rvv ? v : y);
-            const Seg &qu = ku == 1 ? u1 : (ru ? u2r : u2);
-            const int quf = ku == 1 ? u : (ru ? x : u), qul = ku == 1 ? u : (ru ? u : x);
-            const int afterU = ku == 1 ? su : sx, afterV = kv == 1 ? sv : sy;
-            Seg na = join<TW>(C, PU, pu, qv, qvf);
-            na = join_opt<TW>(C, na, qvl, afterU);
-            Seg nb = join<TW>(C, PV, pv, qu, quf);
-            nb = join_opt<TW>(C, nb, qul, afterV);
-            const RT nA = rt_of(na, I), nB = rt_of(nb, I);
-            sink(C, make_id32(u, v, var), nA.dist + nB.dist - oldA.dist - oldB.dist,
-                 nA.tw + nB.tw - oldA.tw - oldB.tw, nA.lex + nB.lex - oldA.lex - oldB.lex,
-                 nA.dex + nB.dex - oldA.dex - oldB.dex, 0, A, B, b);
-        }
+        __syncwarp();  // the list is read before the next batch overwrites it
     }
 }
 
@@ -398,7 +442,7 @@ __device__ void eval_swap(const Ctx &C, int cu, int lane, Best &b) {
 // 2-opt*: [ds_A..u] + [v..de_B] and [ds_B..pred v] + [succ u..de_A].
 // ------------------------------------------------------------------------------------------
 template <bool TW>
-__device__ void eval_2optstar(const Ctx &C, int cu, int lane, Best &b) {
+__device__ void eval_2optstar(const Ctx &C, int cu, int lane, Best &b, int *wl) {
     const DevInst &I = C.I;
     const int u = I.nd + cu;
     const Seg8 Pu = pre8(C, u), Su = suf8(C, u);
@@ -410,27 +454,33 @@ __device__ void eval_2optstar(const Ctx &C, int cu, int lane, Best &b) {
     const Seg PU = seg_of(Pu);
     const bool u_last = su < I.nd;  // depot or MD_NONE after u
     const int ncand = C.lists ? I.nnbr[cu] : I.nc;
-    for (int i = lane; i < ncand; i += 32) {
-        const int v = C.lists ? __ldg(&I.nbr[(size_t)cu * I.theta + i]) : I.nd + i;
-        if (v == u) continue;
-        const Seg8 Pv = pre8(C, v), Sv = suf8(C, v);
-        const int B = Pv.a, pv = Sv.a;
-        if (B == A) continue;
-        const size_t sB = (size_t)C.s * C.D.R + B;
-        const int4 hB = C.D.rhdr[sB];
-        const int dsB = hB.y, deB = hB.z;
-        const RT oldB = rt_of(seg_of(ldg_seg8(&C.D.rterm[sB])), I);
-        const RT nA = rt_of(join<TW>(C, PU, u, seg_of(Sv), v), I);
-        const bool b_empty = pv < I.nd && u_last;
-        RT nB = rt_zero();
-        if (!b_empty) nB = rt_of(join_opt<TW>(C, prefix_through(C, pv), pv, su), I);
-        int dV = 0;
-        if (!C.open) {
-            dV += (dsA != deB) + (b_empty ? 0 : (dsB != deA)) - (dsA != deA) - (dsB != deB);
+    for (int i0 = 0; i0 < ncand; i0 += 64) {
+        int ni, na;
+        split_candidates(C, cu, u, A, lane, wl, false, i0, ncand, ni, na);
+        const int ni_pad = (ni + 31) & ~31;  // passes run inter-route or intra-route candidates only
+        for (int k = lane; k < ni_pad + na; k += 32) {
+            const int v = k < ni ? wl[k] : (k >= ni_pad ? wl[63 - (k - ni_pad)] : -1);
+            if (v < 0) continue;
+            const Seg8 Pv = pre8(C, v), Sv = suf8(C, v);
+            const int B = Pv.a, pv = Sv.a;
+            if (B == A) continue;
+            const size_t sB = (size_t)C.s * C.D.R + B;
+            const int4 hB = C.D.rhdr[sB];
+            const int dsB = hB.y, deB = hB.z;
+            const RT oldB = rt_of(seg_of(ldg_seg8(&C.D.rterm[sB])), I);
+            const RT nA = rt_of(join<TW>(C, PU, u, seg_of(Sv), v), I);
+            const bool b_empty = pv < I.nd && u_last;
+            RT nB = rt_zero();
+            if (!b_empty) nB = rt_of(join_opt<TW>(C, prefix_through(C, pv), pv, su), I);
+            int dV = 0;
+            if (!C.open) {
+                dV += (dsA != deB) + (b_empty ? 0 : (dsB != deA)) - (dsA != deA) - (dsB != deB);
+            }
+            if (b_empty) dV += veh_delta(C.D.dcount[(size_t)C.s * I.nd + dsB], I.NV, -1);
+            sink(C, make_id32(u, v, 0), nA.dist + nB.dist - oldA.dist - oldB.dist, nA.tw + nB.tw - oldA.tw - oldB.tw,
+                 nA.lex + nB.lex - oldA.lex - oldB.lex, nA.dex + nB.dex - oldA.dex - oldB.dex, dV, A, B, b);
         }
-        if (b_empty) dV += veh_delta(C.D.dcount[(size_t)C.s * I.nd + dsB], I.NV, -1);
-        sink(C, make_id32(u, v, 0), nA.dist + nB.dist - oldA.dist - oldB.dist, nA.tw + nB.tw - oldA.tw - oldB.tw,
-             nA.lex + nB.lex - oldA.lex - oldB.lex, nA.dex + nB.dex - oldA.dex - oldB.dex, dV, A, B, b);
+        __syncwarp();  // the list is read before the next batch overwrites it
     }
 }
 
@@ -522,11 +572,11 @@ __device__ __forceinline__ void best_init(Best &b) {
 }
 
 template <bool TW>
-__device__ __forceinline__ void eval_customer(const Ctx &C, int op, int cu, int lane, Best &b) {
+__device__ __forceinline__ void eval_customer(const Ctx &C, int op, int cu, int lane, Best &b, int *wl) {
     switch (op) {
-    case MD_OP_RELOCATE: eval_relocate<TW>(C, cu, lane, b); break;
-    case MD_OP_SWAP: eval_swap<TW>(C, cu, lane, b); break;
-    case MD_OP_TWO_OPT_STAR: eval_2optstar<TW>(C, cu, lane, b); break;
+    case MD_OP_RELOCATE: eval_relocate<TW>(C, cu, lane, b, wl); break;
+    case MD_OP_SWAP: eval_swap<TW>(C, cu, lane, b, wl); break;
+    case MD_OP_TWO_OPT_STAR: eval_2optstar<TW>(C, cu, lane, b, wl); break;
     case MD_OP_DEPOT_INSERT: eval_depot_insert<TW>(C, cu, lane, b); break;
     case MD_OP_DEPOT_REPLACE: eval_depot_replace<TW>(C, cu, lane, b); break;
     default: break;
@@ -565,11 +615,13 @@ __global__ void __launch_bounds__(32 * MD_EVAL_WARPS, MD_EVAL_MIN_BLOCKS) k_eval
     const int op_raw = D.ops[C.s];
     const int op = op_raw < 0 ? -1 : (op_raw & MD_OP_MASK);
     C.lists = I.theta > 0 && !(op_raw >= 0 && (op_raw & MD_OP_SWEEP));
+    __shared__ int s_wl[MD_EVAL_WARPS][64];
     Best b;
     best_init(b);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
     if (op >= 0)
-        for (int cu = blockIdx.x * wpb + warp; cu < I.nc; cu += gridDim.x * wpb) eval_customer<TW>(C, op, cu, lane, b);
+        for (int cu = blockIdx.x * wpb + warp; cu < I.nc; cu += gridDim.x * wpb)
+            eval_customer<TW>(C, op, cu, lane, b, s_wl[warp]);
     warp_commit(C, b, (size_t)blockIdx.x * wpb + warp, lane);
 }
 
@@ -585,6 +637,7 @@ __global__ void __launch_bounds__(32 * MD_EVAL_WARPS, MD_EVAL_MIN_BLOCKS) k_eval
     // Tiles are claimed dynamically from a counter (zeroed before the launch), in work-list order:
     // largest instances first, so the long tiles start early and the short ones fill the gaps.
     __shared__ Ctx cs[MD_EVAL_WARPS];
+    __shared__ int s_wl[MD_EVAL_WARPS][64];
     __shared__ int s_tile;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     Ctx &C = cs[warp];
@@ -627,8 +680,8 @@ __global__ void __launch_bounds__(32 * MD_EVAL_WARPS, MD_EVAL_MIN_BLOCKS) k_eval
             for (int q = 0; q < upw; q++) {
                 const int cu = ws * upw + q;
                 if (cu >= C.I.nc) break;
-                if (tw) eval_customer<true>(C, op, cu, lane, b);
-                else eval_customer<false>(C, op, cu, lane, b);
+                if (tw) eval_customer<true>(C, op, cu, lane, b, s_wl[warp]);
+                else eval_customer<false>(C, op, cu, lane, b, s_wl[warp]);
             }
         warp_commit(C, b, ws, lane);
         __syncwarp();  // every lane is done with this tile's context

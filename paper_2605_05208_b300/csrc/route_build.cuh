@@ -71,6 +71,65 @@ __device__ void rebuild_route(const DevInst &I, const DevSols &D, int s, int r) 
     Seg8 *cpre = D.cpre + (size_t)s * I.nc;
     Seg8 *csuf = D.csuf + (size_t)s * I.nc;
 
+    if (L <= 32) {
+        // Lane k - 1 holds customer c_k: its node summary and the arc into it travel by shuffles.
+        // Its forward fold gives csubf[c_k][*] and ends at [c_k..c_L]; its backward fold gives
+        // csubb[c_k][*] and ends at [c_1..c_k]; the prefix, the suffix and the route terms follow
+        // with one concatenation each.
+        const bool act = lane < L;
+        const int c = act ? nodes[lane] : nodes[0];
+        const Seg cs = node_seg(I.node[c]);
+        const int prev = __shfl_up_sync(0xffffffffu, c, 1);
+        const int nextc = __shfl_down_sync(0xffffffffu, c, 1);
+        const int arc = lane > 0 ? I.dist[(size_t)prev * I.nn + c] : 0;  // arc into position lane
+        const int arc_out = __shfl_down_sync(0xffffffffu, arc, 1);       // arc out of it
+        const int cL = __shfl_sync(0xffffffffu, c, L - 1);
+        const size_t row = ((size_t)s * I.nc + (c - I.nd)) * D.K;
+        Seg8 *F = D.csubf + row;
+        Seg8 *Bk = D.csubb + row;
+        Seg gf = cs;
+        if (act) st_seg8(&F[0], gf, c, c);
+        for (int t = 1; t < L; t++) {
+            SegN x;
+            x.s = cs; x.first = c; x.last = arc;
+            x = shfl_segn(x, min(lane + t, 31));
+            if (lane + t < L) {
+                gf = seg_cat<TW>(gf, x.s, x.last);
+                st_seg8(&F[t], gf, c, x.first);
+            }
+        }
+        Seg gb = cs;
+        if (act) st_seg8(&Bk[0], gb, c, c);
+        for (int t = 1; t < L; t++) {
+            SegN x;
+            x.s = cs; x.first = c; x.last = arc_out;
+            x = shfl_segn(x, max(lane - t, 0));
+            if (act && lane - t >= 0) {
+                gb = seg_cat<TW>(x.s, gb, x.last);
+                st_seg8(&Bk[t], gb, x.first, c);
+            }
+        }
+        const Seg sds = node_seg(I.node[ds]);
+        const Seg pre = seg_cat<TW>(sds, gb, I.dist[(size_t)ds * I.nn + __shfl_sync(0xffffffffu, c, 0)]);
+        const Seg sde = node_seg(I.node[de]);
+        const int arc_de = I.dist[(size_t)cL * I.nn + de];
+        const Seg suf = open ? gf : seg_cat<TW>(gf, sde, arc_de);
+        if (act) {
+            st_seg8(&cpre[c - I.nd], pre, r, lane + 1);
+            st_seg8(&csuf[c - I.nd], suf, lane == 0 ? ds : prev,
+                    lane == L - 1 ? (open ? MD_NONE : de) : nextc);
+        }
+        if (lane == 0) {
+            // lane 0: gf = [c_1..c_L], pre = [ds, c_1]; the whole route is ds + gf (+ de)
+            const Seg head = seg_cat<TW>(sds, gf, I.dist[(size_t)ds * I.nn + c]);
+            const Seg whole = open ? head : seg_cat<TW>(head, sde, arc_de);
+            st_seg8(&D.rterm[sr], whole, ds, open ? cL : de);
+            st_seg8(&D.rcore[sr], gf, c, cL);
+            D.rhdr[sr] = make_int4(L, ds, de, cL);
+        }
+        return;
+    }
+
     // prefixes, chunks of 32 customers from the front
     SegN carry = segn_node(I, ds);
     SegN core;
@@ -115,44 +174,9 @@ __device__ void rebuild_route(const DevInst &I, const DevSols &D, int s, int r) 
         rc = shfl_segn(sfx, tail);
         have_rc = true;
     }
-    // subsequence tables: lane i folds from position k = i + 1 to the route's end and to its
-    // start.  Up to 32 customers, the lanes hold the route's node summaries and arcs and pass
-    // them by shuffles; longer routes fold from memory in chunks of 32 starting positions.
-    if (L <= 32) {
-        const bool act = lane < L;
-        const int c = act ? nodes[lane] : nodes[0];
-        const Seg cs = node_seg(I.node[c]);
-        const int prev = __shfl_up_sync(0xffffffffu, c, 1);
-        const int arc = lane > 0 ? I.dist[(size_t)prev * I.nn + c] : 0;  // arc into position lane
-        const size_t row = ((size_t)s * I.nc + (c - I.nd)) * D.K;
-        Seg8 *F = D.csubf + row;
-        Seg8 *Bk = D.csubb + row;
-        Seg g = cs;
-        if (act) st_seg8(&F[0], g, c, c);
-        for (int t = 1; t < L; t++) {
-            const int src = min(lane + t, 31);
-            SegN x;
-            x.s = cs; x.first = c; x.last = arc;  // last carries the arc into the position
-            x = shfl_segn(x, src);
-            if (lane + t < L) {
-                g = seg_cat<TW>(g, x.s, x.last);
-                st_seg8(&F[t], g, c, x.first);
-            }
-        }
-        g = cs;
-        int nxt_arc = __shfl_down_sync(0xffffffffu, arc, 1);  // arc out of position lane
-        if (act) st_seg8(&Bk[0], g, c, c);
-        for (int t = 1; t < L; t++) {
-            const int src = max(lane - t, 0);
-            SegN x;
-            x.s = cs; x.first = c; x.last = nxt_arc;
-            x = shfl_segn(x, src);
-            if (act && lane - t >= 0) {
-                g = seg_cat<TW>(x.s, g, x.last);
-                st_seg8(&Bk[t], g, x.first, c);
-            }
-        }
-    } else for (int base = 0; base < L; base += 32) {
+    // subsequence tables: lane i folds from position k = i + 1 (chunks of 32) to the route's
+    // end and to its start
+    for (int base = 0; base < L; base += 32) {
         const int k0 = base + lane;  // 0-based position
         if (k0 >= L) break;
         const int c = nodes[k0];

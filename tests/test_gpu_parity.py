@@ -129,6 +129,10 @@ def _eval_cases():
                                    "random", (1.0, 1.0, 1.0, 1.0)),
         "tiny-sym-theta": (tiny_spec(17, nd=3, nc=45, sym=True, Q=30, NV=2, theta=6), "random",
                            (1.0, 1.0, 1.0, 8.0)),
+        # routes of 33 to 60 customers: summaries and subsequence tables span two chunks of 32
+        "tiny-long-routes-tw": (tiny_spec(18, nd=3, nc=110, tw=True, sym=True, Q=400, NV=2, D=900,
+                                          horizon=4000, wmin=200, wmax=1500), "long",
+                                (1.0, 2.0, 0.5, 1.0)),
     }
 
 
@@ -137,6 +141,11 @@ def test_eval_every_move_matches_oracle(md, oracle_lib, case):
     spec, nsol, lam = _eval_cases()[case]
     if nsol == "random":
         sols = [random_solution(spec, 100 + i, max_len=5) for i in range(3)]
+    elif nsol == "long":
+        nd = spec.n_depots
+        c = list(range(nd, spec.n_nodes))
+        sols = [[[0] + c[:60] + [1], [2] + c[60:95] + [2], [1] + c[95:] + [0]],
+                [[1] + c[50:][::-1] + [1], [0] + c[:50] + [2]]]
     else:
         sols = W.initial_solutions(spec, 21, nsol)
     o = oracle_lib.Instance(spec)
