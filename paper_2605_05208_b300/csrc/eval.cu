@@ -30,12 +30,14 @@ struct RT {  // the four integer terms of one route (Eq. A1)
 };
 
 struct Best {
-    double f;
+    double f;         // exact FP64 dF of the best move, once formed (fx)
     uint32_t id;
     int valid;
+    int fx;
+    int dD, dT, dL, dU, dV;  // integer deltas of the best move
+    float lo, hi;     // lo <= dF(best) <= hi
     uint32_t routes;  // rA | rB << 16 of the best move
     unsigned long long n;
-    float fb;  // f rounded towards +inf (0 while there is no candidate): the pruning bound
 };
 
 struct Ctx {
@@ -119,32 +121,66 @@ __device__ __forceinline__ void offer(const Ctx &C, uint32_t id, int dD, int dTW
             else atomicCAS(C.D.err, 0, (int)MD_ERR_CAPACITY);
         }
     }
-    double f;
-    if (have_f) {
-        f = f_in;
-    } else if (C.flags & MD_EVAL_DUMP) {
-        f = combine_df(C.w, dD, dTW, dL, dU, dV);
+    // Leader candidate.  dF is bracketed by [lo, hi]; the exact FP64 value of a move (and of the
+    // lane's best) is formed only when the brackets cannot order them, so most comparisons need
+    // no FP64 arithmetic.  The dump records every move with its exact dF.
+    const bool dump = (C.flags & MD_EVAL_DUMP) != 0;
+    double f = 0.0;
+    bool fx = false;
+    float lo, hi;
+    if (have_f || dump) {
+        f = have_f ? f_in : combine_df(C.w, dD, dTW, dL, dU, dV);
+        fx = true;
+        lo = __double2float_rd(f);
+        hi = __double2float_ru(f);
     } else if (!pen) {
         if (dD >= 0) return;
-        if (__int2float_rd(dD) > b.fb) return;  // dF = dD > best for certain
-        f = (double)dD;
+        lo = __int2float_rd(dD);
+        hi = __int2float_ru(dD);
     } else {
         if (dD >= 0 && dTW >= 0 && dL >= 0 && dU >= 0 && dV >= 0) return;  // dF >= 0: never a leader
         const float est = __fmaf_rn(C.wf[3], (float)dV, __fmaf_rn(C.wf[2], (float)dU,
                           __fmaf_rn(C.wf[1], (float)dL, __fmaf_rn(C.wf[0], (float)dTW, (float)dD))));
         const float mag = fabsf((float)dD) + C.wf[0] * fabsf((float)dTW) + C.wf[1] * fabsf((float)dL) +
                           C.wf[2] * fabsf((float)dU) + C.wf[3] * fabsf((float)dV);
-        if (est - 4e-6f * mag > b.fb) return;  // dF > best for certain
-        f = combine_df(C.w, dD, dTW, dL, dU, dV);
+        const float m = 4e-6f * mag;  // at least nine times the estimate's rounding bound
+        lo = est - m;
+        hi = est + m;
+        if (lo >= 0.0f) return;  // dF >= 0 for certain
     }
-    if (f < 0.0 && (!b.valid || f < b.f || (f == b.f && id < b.id))) {
-        b.f = f;
-        b.id = id;
+    bool take;
+    if (b.valid && lo > b.hi) {
+        take = false;  // dF > dF(best) for certain
+    } else if (b.valid ? hi < b.lo : hi < 0.0f) {
+        take = true;   // dF < dF(best) (or < 0 without a best) for certain
+    } else if (b.valid && dD == b.dD && dTW == b.dT && dL == b.dL && dU == b.dU && dV == b.dV) {
+        take = id < b.id;  // the same deltas: the same dF
+    } else {
+        if (!fx) {
+            f = combine_df(C.w, dD, dTW, dL, dU, dV);
+            fx = true;
+        }
+        if (!b.valid) {
+            take = f < 0.0;
+        } else {
+            if (!b.fx) {
+                b.f = combine_df(C.w, b.dD, b.dT, b.dL, b.dU, b.dV);
+                b.fx = 1;
+            }
+            take = f < b.f || (f == b.f && id < b.id);
+        }
+    }
+    if (take && (fx ? f < 0.0 : true)) {
         b.valid = 1;
+        b.id = id;
         b.routes = (uint32_t)rA | ((uint32_t)rB << 16);
-        b.fb = __double2float_ru(f);
+        b.dD = dD; b.dT = dTW; b.dL = dL; b.dU = dU; b.dV = dV;
+        b.lo = lo;
+        b.hi = hi;
+        b.fx = fx;
+        b.f = f;
     }
-    if (C.flags & MD_EVAL_DUMP) {
+    if (dump) {
         const unsigned long long k = atomicAdd(C.M.dump_n, 1ull);
         if ((long long)k < C.M.dump_cap) {
             md_move m;
@@ -568,7 +604,9 @@ __device__ void eval_depot_replace(const Ctx &C, int cu, int lane, Best &b) {
 }
 
 __device__ __forceinline__ void best_init(Best &b) {
-    b.f = 0.0; b.id = MD_NO_ID; b.valid = 0; b.routes = 0; b.n = 0; b.fb = 0.0f;
+    b.f = 0.0; b.id = MD_NO_ID; b.valid = 0; b.fx = 0; b.routes = 0; b.n = 0;
+    b.dD = b.dT = b.dL = b.dU = b.dV = 0;
+    b.lo = b.hi = 0.0f;
 }
 
 template <bool TW>
@@ -585,6 +623,7 @@ __device__ __forceinline__ void eval_customer(const Ctx &C, int op, int cu, int 
 
 // Warp reduction of the lanes' leader candidates and scored counts; one record per warp slot.
 __device__ __forceinline__ void warp_commit(const Ctx &C, Best &b, size_t slot, int lane) {
+    if (b.valid && !b.fx) b.f = combine_df(C.w, b.dD, b.dT, b.dL, b.dU, b.dV);
     for (int o = 16; o > 0; o >>= 1) {
         const double of = __shfl_xor_sync(0xffffffffu, b.f, o);
         const uint32_t oi = __shfl_xor_sync(0xffffffffu, b.id, o);
