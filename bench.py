@@ -125,6 +125,19 @@ def run_reference(args):
 # GPU arm
 # ------------------------------------------------------------------------------------------
 
+def combine_ranks(total_ms: float, moves: float, world: int, device) -> tuple[float, float]:
+    """The slowest rank's timed milliseconds and the moves scored by all ranks.  Every rank
+    descends its own seeded solutions (weak scaling), so nothing else crosses ranks."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+    m = torch.tensor([moves], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(m, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(m.item())
+
+
 class ClockSampler:
     """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
 
@@ -232,15 +245,8 @@ def run_ours(args):
         dist.barrier()
     ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
     total_ms = float(sum(ms))
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms_max = float(t.item())
     moves = sum(s.moves_scored for s in stats)
-    mv = torch.tensor([float(moves)], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(mv, op=dist.ReduceOp.SUM)
-    moves_all = float(mv.item())
+    total_ms_max, moves_all = combine_ranks(total_ms, float(moves), world, dev)
     value = moves_all / (total_ms_max / 1e3)
     descents = N_SOL * world * args.steps / (total_ms_max / 1e3)
 
