@@ -611,7 +611,7 @@ def main():
     ap.add_argument("--plain-steps", type=int, default=1,
                     help="timed plain full-neighbourhood descents beside the learned workload")
     ap.add_argument("--max-pass", type=int, default=4, help="passes per step of the batch workload")
-    ap.add_argument("--groups", type=int, default=2,
+    ap.add_argument("--groups", type=int, default=4,
                     help="solution groups advancing on concurrent streams inside the graph")
     args = ap.parse_args()
     if args.impl == "reference":
