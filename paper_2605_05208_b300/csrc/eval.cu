@@ -56,6 +56,13 @@ __device__ __forceinline__ int cost(const DevInst &I, int a, int b) {
     return __ldg(&I.dist[(size_t)a * I.nn + b]);
 }
 
+// c(a, b) read from row b.  The matrix is symmetric (Euclidean, Eq. 1), so every arc is read
+// from the row of the node that is the same for all lanes of the warp (u and the nodes of its
+// route): a warp's reads then fall in one row, contiguous when the candidates are consecutive.
+__device__ __forceinline__ int cost_t(const DevInst &I, int a, int b) {
+    return __ldg(&I.dist[(size_t)b * I.nn + a]);
+}
+
 __device__ __forceinline__ RT rt_of(const Seg &g, const DevInst &I) {
     RT r;
     r.dist = g.dist;
@@ -97,11 +104,23 @@ __device__ __forceinline__ Seg join(const Ctx &C, const Seg &a, int a_last, cons
     return seg_cat<TW>(a, b, cost(C.I, a_last, b_first));
 }
 
+// join with the arc read from row b_first (b_first is the warp-uniform end)
+template <bool TW>
+__device__ __forceinline__ Seg join_t(const Ctx &C, const Seg &a, int a_last, const Seg &b, int b_first) {
+    return seg_cat<TW>(a, b, cost_t(C.I, a_last, b_first));
+}
+
 // head + tail, where tail_first = MD_NONE means there is no tail.
 template <bool TW>
 __device__ __forceinline__ Seg join_opt(const Ctx &C, const Seg &a, int a_last, int tail_first) {
     if (tail_first == MD_NONE) return a;
     return join<TW>(C, a, a_last, suffix_from(C, tail_first), tail_first);
+}
+
+template <bool TW>
+__device__ __forceinline__ Seg join_opt_t(const Ctx &C, const Seg &a, int a_last, int tail_first) {
+    if (tail_first == MD_NONE) return a;
+    return join_t<TW>(C, a, a_last, suffix_from(C, tail_first), tail_first);
 }
 
 // Records one scored move: follower table, leader candidate of the lane, dump.  f_in is the FP64
@@ -226,6 +245,13 @@ __device__ __forceinline__ SN sn_cat(const Ctx &C, const SN &a, const SN &b) {
     return sn(seg_cat<TW>(a.s, b.s, cost(C.I, a.l, b.f)), a.f, b.l);
 }
 
+template <bool TW>
+__device__ __forceinline__ SN sn_cat_t(const Ctx &C, const SN &a, const SN &b) {
+    if (a.e) return b;
+    if (b.e) return a;
+    return sn(seg_cat<TW>(a.s, b.s, cost_t(C.I, a.l, b.f)), a.f, b.l);
+}
+
 // Summary of the route from node n to its end as an SN (empty after an open route's last customer).
 __device__ __forceinline__ SN sn_suffix(const Ctx &C, int n) {
     return n == MD_NONE ? sn_none() : sn(suffix_from(C, n), n, n);
@@ -331,10 +357,10 @@ __device__ void eval_relocate(const Ctx &C, int cu, int lane, Best &b, int *wl) 
                     if (at < p) {
                         const SN head = at == 0 ? sn(nseg(C, dsA), dsA, dsA) : sn(seg_of(Pv), dsA, v);
                         const SN mid = at + 1 <= p - 1 ? sub_bwd(C, pu, p - 2 - at) : sn_none();  // at+1..p-1
-                        g = sn_cat<TW>(C, sn_cat<TW>(C, sn_cat<TW>(C, head, q), mid), sn_suffix(C, k == 1 ? su : sx));
+                        g = sn_cat<TW>(C, sn_cat<TW>(C, sn_cat_t<TW>(C, head, q), mid), sn_suffix(C, k == 1 ? su : sx));
                     } else {
                         const SN mid = sub_fwd(C, k == 1 ? su : sx, at - p - k);  // p+k..at
-                        g = sn_cat<TW>(C, sn_cat<TW>(C, sn_cat<TW>(C, sn(PP, dsA, pu), mid), q), sn_suffix(C, sv));
+                        g = sn_cat<TW>(C, sn_cat_t<TW>(C, sn_cat<TW>(C, sn(PP, dsA, pu), mid), q), sn_suffix(C, sv));
                     }
                     const RT nA = rt_of(g.s, I);
                     sink(C, make_id32(u, v, var), nA.dist - oldA.dist, nA.tw - oldA.tw, nA.lex - oldA.lex,
@@ -358,10 +384,10 @@ __device__ void eval_relocate(const Ctx &C, int cu, int lane, Best &b, int *wl) 
                 const int ql = k == 1 ? u : (rev ? u : x);
                 Seg nb;
                 if (before) {
-                    nb = join<TW>(C, nseg(C, dsB), dsB, q, qf);
+                    nb = join_t<TW>(C, nseg(C, dsB), dsB, q, qf);
                     nb = join<TW>(C, nb, ql, seg_of(Sv), v);
                 } else {
-                    nb = join<TW>(C, PV, v, q, qf);
+                    nb = join_t<TW>(C, PV, v, q, qf);
                     nb = join_opt<TW>(C, nb, ql, sv);
                 }
                 const RT nB = rt_of(nb, I);
@@ -435,11 +461,11 @@ __device__ void eval_swap(const Ctx &C, int cu, int lane, Best &b, int *wl) {
                     if (p < j) {
                         const SN mid = p + ku <= j - 1 ? sub_fwd(C, ku == 1 ? su : sx, j - 1 - p - ku) : sn_none();
                         g = sn_cat<TW>(C, sn(PU, dsA, pu), qv);
-                        g = sn_cat<TW>(C, sn_cat<TW>(C, sn_cat<TW>(C, g, mid), qu), sn_suffix(C, kv == 1 ? sv : sy));
+                        g = sn_cat<TW>(C, sn_cat_t<TW>(C, sn_cat_t<TW>(C, g, mid), qu), sn_suffix(C, kv == 1 ? sv : sy));
                     } else {
                         const SN mid = j + kv <= p - 1 ? sub_bwd(C, pu, p - 1 - j - kv) : sn_none();
-                        g = sn_cat<TW>(C, sn(prefix_through(C, pv), dsA, pv), qu);
-                        g = sn_cat<TW>(C, sn_cat<TW>(C, sn_cat<TW>(C, g, mid), qv), sn_suffix(C, ku == 1 ? su : sx));
+                        g = sn_cat_t<TW>(C, sn(prefix_through(C, pv), dsA, pv), qu);
+                        g = sn_cat_t<TW>(C, sn_cat<TW>(C, sn_cat<TW>(C, g, mid), qv), sn_suffix(C, ku == 1 ? su : sx));
                     }
                     const RT nA = rt_of(g.s, I);
                     sink(C, make_id32(u, v, var), nA.dist - oldA.dist, nA.tw - oldA.tw, nA.lex - oldA.lex,
@@ -461,8 +487,8 @@ __device__ void eval_swap(const Ctx &C, int cu, int lane, Best &b, int *wl) {
                 const int quf = ku == 1 ? u : (ru ? x : u), qul = ku == 1 ? u : (ru ? u : x);
                 const int afterU = ku == 1 ? su : sx, afterV = kv == 1 ? sv : sy;
                 Seg na = join<TW>(C, PU, pu, qv, qvf);
-                na = join_opt<TW>(C, na, qvl, afterU);
-                Seg nb = join<TW>(C, PV, pv, qu, quf);
+                na = join_opt_t<TW>(C, na, qvl, afterU);
+                Seg nb = join_t<TW>(C, PV, pv, qu, quf);
                 nb = join_opt<TW>(C, nb, qul, afterV);
                 const RT nA = rt_of(na, I), nB = rt_of(nb, I);
                 sink(C, make_id32(u, v, var), nA.dist + nB.dist - oldA.dist - oldB.dist,
@@ -507,7 +533,7 @@ __device__ void eval_2optstar(const Ctx &C, int cu, int lane, Best &b, int *wl) 
             const RT nA = rt_of(join<TW>(C, PU, u, seg_of(Sv), v), I);
             const bool b_empty = pv < I.nd && u_last;
             RT nB = rt_zero();
-            if (!b_empty) nB = rt_of(join_opt<TW>(C, prefix_through(C, pv), pv, su), I);
+            if (!b_empty) nB = rt_of(join_opt_t<TW>(C, prefix_through(C, pv), pv, su), I);
             int dV = 0;
             if (!C.open) {
                 dV += (dsA != deB) + (b_empty ? 0 : (dsB != deA)) - (dsA != deA) - (dsB != deB);
@@ -537,7 +563,7 @@ __device__ void eval_depot_insert(const Ctx &C, int cu, int lane, Best &b) {
     const Seg PU = seg_of(Pu), SX = seg_of(suf8(C, su));
     for (int d = lane; d < I.nd; d += 32) {
         const Seg r1 = C.open ? PU : join<TW>(C, PU, u, nseg(C, d), d);
-        const Seg r2 = join<TW>(C, nseg(C, d), d, SX, su);
+        const Seg r2 = join_t<TW>(C, nseg(C, d), d, SX, su);
         const RT n1 = rt_of(r1, I), n2 = rt_of(r2, I);
         int dV = veh_delta(C.D.dcount[(size_t)C.s * I.nd + d], I.NV, +1);
         if (!C.open) dV += (dsA != d) + (d != deA) - (dsA != deA);
@@ -577,7 +603,7 @@ __device__ void eval_depot_replace(const Ctx &C, int cu, int lane, Best &b) {
             Seg g;
             int clo, veh;
             if (cs == 0) {
-                g = join<TW>(C, nseg(C, d), d, SU, u);  // SU already ends at the arrival depot
+                g = join_t<TW>(C, nseg(C, d), d, SU, u);  // SU already ends at the arrival depot
                 clo = (!C.open && d != deA) ? 1 : 0;
                 veh = dveh;
             } else if (cs == 1) {
@@ -585,7 +611,7 @@ __device__ void eval_depot_replace(const Ctx &C, int cu, int lane, Best &b) {
                 clo = dsA != d ? 1 : 0;
                 veh = 0;
             } else {
-                g = join<TW>(C, nseg(C, d), d, CORE, u);
+                g = join_t<TW>(C, nseg(C, d), d, CORE, u);
                 g = join<TW>(C, g, cL, nseg(C, d), d);
                 clo = 0;
                 veh = dveh;
