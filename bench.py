@@ -326,10 +326,11 @@ def run_ours(args):
 def run_batch(args):
     """Batched uneven instances: 16 instances (100..2000 customers, MDVRP / MDVRPTW / MDOVRP),
     16 solutions each, one persistent evaluation launch and one select/apply launch per descent
-    step for all 256 solutions.  A step runs args.max_pass passes of every solution; it is timed
+    step for all 256 solutions.  A step runs max_pass passes of every solution; it is timed
     beside the same solutions descended instance by instance."""
     import torch
     from paper_2605_05208_b300 import build, mdls
+    max_pass = args.max_pass or 4
     build.build()
     dev = torch.device("cuda", 0)
     stream = torch.cuda.Stream(dev)
@@ -348,7 +349,7 @@ def run_batch(args):
         a.load(sols)
         b.load(sols)
         insts.append(inst); inits.append(a); works.append(b)
-        perms.append(W.op_permutations(SEED + i, 16, args.max_pass))
+        perms.append(W.op_permutations(SEED + i, 16, max_pass))
     perm_all = np.concatenate(perms)
     perm_dev = torch.from_numpy(perm_all).to(dev)
     perm_devs = [torch.from_numpy(p).to(dev) for p in perms]
@@ -361,12 +362,12 @@ def run_batch(args):
             b.copy_from(a, stream=sptr)
 
     def batched():
-        return B.descend(perm_dev.data_ptr(), args.max_pass, use_graph=True, stream=sptr, n_ops=W.N_OPS)
+        return B.descend(perm_dev.data_ptr(), max_pass, use_graph=True, stream=sptr, n_ops=W.N_OPS)
 
     def unbatched():
         out = []
         for b, p in zip(works, perm_devs):
-            out.append(b.descend(p.data_ptr(), args.max_pass, use_graph=True, stream=sptr, n_ops=W.N_OPS))
+            out.append(b.descend(p.data_ptr(), max_pass, use_graph=True, stream=sptr, n_ops=W.N_OPS))
         return out
 
     res = {}
@@ -397,7 +398,7 @@ def run_batch(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32/f64",
         "data": "synthetic",
         "config": {"workload": f"batch16-uneven: 16 instances ({', '.join(sp.name for sp in specs)}), "
-                               f"16 solutions each, {args.max_pass} passes per step, multi-move",
+                               f"16 solutions each, {max_pass} passes per step, multi-move",
                    "l2": "flushed between timed steps (256 MB write)",
                    "tuning": {"customers_per_warp": upw.tolist(), "grid": grid}},
         "batched": res["batched"], "per_instance": res["per_instance"],
@@ -598,6 +599,80 @@ def run_learned(args):
     }))
 
 
+def run_plain_large(args):
+    """Plain full-neighbourhood descents of the 20-depot, 10000-customer MDVRPTW instance (every
+    customer a candidate of every customer; the 401.6 MB distance matrix does not fit in L2).
+    One step descends args.solutions (default 8) solutions for args.max_pass passes from their
+    initial routes (500 passes: to the local optimum)."""
+    import torch
+    from paper_2605_05208_b300 import build, mdls
+    n_sol = args.solutions or LEARNED_SOL
+    max_pass = args.max_pass or MAX_PASS
+    build.build()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    sptr = stream.cuda_stream
+    spec, sols, perm = learned_workload(n_sol)
+    routes = max(len(x) for x in sols)
+    longest = max(len(r) - 2 for x in sols for r in x)
+    R = max(64, 2 * routes, spec.n_depots * spec.N_V + 8)
+    K = max(64, 2 * longest)
+    inst = mdls.Instance(spec)
+    init = mdls.Solutions(inst, n_sol, R, K)
+    work = mdls.Solutions(inst, n_sol, R, K)
+    init.load(sols)
+    perm_dev = torch.from_numpy(np.ascontiguousarray(perm)).to(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
+
+    def one(te=False):
+        work.copy_from(init, stream=sptr)
+        return work.descend(perm_dev.data_ptr(), max_pass, multi=True, use_graph=True, poll_every=1,
+                            stream=sptr, n_ops=W.N_OPS, time_eval=te, n_groups=args.groups)
+    for _ in range(args.warmup):
+        one()
+    torch.cuda.synchronize()
+    ms, sts = 0.0, []
+    with ClockSampler(0) as clk:
+        for k in range(args.steps):
+            flush.fill_(k)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            sts.append(one(te=True))
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms += a.elapsed_time(b)
+    moves = sum(x.moves_scored for x in sts)
+    eval_ms = sum(x.eval_ms for x in sts)
+    eval_launches = sum(x.eval_launches for x in sts)
+    by_op = np.sum([x.moves_by_op for x in sts], axis=0)
+    alg_bytes = float(sum(int(by_op[o]) * ALG_BYTES[o] for o in range(W.N_OPS)))
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    peak = float(peaks.get("hbm_gbs", 6400.0))
+    achieved = alg_bytes / (eval_ms / 1e3) / 1e9 if eval_ms > 0 else None
+    print(json.dumps({
+        "metric": METRIC, "value": moves / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / max(args.steps, 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32/f64", "data": "synthetic",
+        "config": {"workload": f"plain-20x10000: MDVRPTW 20 depots x 10000 customers, full "
+                               f"neighbourhood, {n_sol} solutions (window-ordered sweep routes), "
+                               f"{max_pass} passes at most, multi-move",
+                   "l2": "flushed between timed steps (256 MB write)", "route_slots": R, "k_max": K,
+                   "stream_groups": args.groups},
+        "descents_per_s": n_sol * args.steps / (ms / 1e3) if max_pass == MAX_PASS else None,
+        "passes_max": sts[-1].passes_max if sts else None,
+        "roofline": {"kernel": "k_eval (neighbourhood evaluation)", "bound": "hbm", "achieved": achieved,
+                     "peak": peak, "unit": "GB/s", "frac": achieved / peak if achieved else None,
+                     "peak_source": "measured" if "hbm_gbs" in peaks else "fallback", "traffic": None,
+                     "eval_ms_per_launch": eval_ms / max(eval_launches, 1)},
+        "clocks": clk.summary(),
+    }))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -605,12 +680,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["mdvrptw-6x288", "batch16-uneven", "learned-20x10000"],
-                    default="mdvrptw-6x288")
+    ap.add_argument("--workload", choices=["mdvrptw-6x288", "batch16-uneven", "learned-20x10000",
+                                           "plain-20x10000"], default="mdvrptw-6x288")
     ap.add_argument("--solutions", type=int, default=0, help="solutions of the learned workload (0: 8)")
     ap.add_argument("--plain-steps", type=int, default=1,
                     help="timed plain full-neighbourhood descents beside the learned workload")
-    ap.add_argument("--max-pass", type=int, default=4, help="passes per step of the batch workload")
+    ap.add_argument("--max-pass", type=int, default=None,
+                    help="passes per step: batch16-uneven 4, plain-20x10000 500 (to the local optimum)")
     ap.add_argument("--groups", type=int, default=4,
                     help="solution groups advancing on concurrent streams inside the graph")
     args = ap.parse_args()
@@ -620,6 +696,8 @@ def main():
         run_batch(args)
     elif args.workload == "learned-20x10000":
         run_learned(args)
+    elif args.workload == "plain-20x10000":
+        run_plain_large(args)
     else:
         run_ours(args)
 

@@ -87,26 +87,25 @@ __device__ void rebuild_route(const DevInst &I, const DevSols &D, int s, int r) 
         const size_t row = ((size_t)s * I.nc + (c - I.nd)) * D.K;
         Seg8 *F = D.csubf + row;
         Seg8 *Bk = D.csubb + row;
-        Seg gf = cs;
-        if (act) st_seg8(&F[0], gf, c, c);
-        for (int t = 1; t < L; t++) {
-            SegN x;
-            x.s = cs; x.first = c; x.last = arc;
-            x = shfl_segn(x, min(lane + t, 31));
-            if (lane + t < L) {
-                gf = seg_cat<TW>(gf, x.s, x.last);
-                st_seg8(&F[t], gf, c, x.first);
-            }
+        // the forward and the backward fold advance together: two independent chains per lane
+        Seg gf = cs, gb = cs;
+        if (act) {
+            st_seg8(&F[0], gf, c, c);
+            st_seg8(&Bk[0], gb, c, c);
         }
-        Seg gb = cs;
-        if (act) st_seg8(&Bk[0], gb, c, c);
         for (int t = 1; t < L; t++) {
-            SegN x;
-            x.s = cs; x.first = c; x.last = arc_out;
-            x = shfl_segn(x, max(lane - t, 0));
+            SegN xf, xb;
+            xf.s = cs; xf.first = c; xf.last = arc;
+            xb.s = cs; xb.first = c; xb.last = arc_out;
+            xf = shfl_segn(xf, min(lane + t, 31));
+            xb = shfl_segn(xb, max(lane - t, 0));
+            if (lane + t < L) {
+                gf = seg_cat<TW>(gf, xf.s, xf.last);
+                st_seg8(&F[t], gf, c, xf.first);
+            }
             if (act && lane - t >= 0) {
-                gb = seg_cat<TW>(x.s, gb, x.last);
-                st_seg8(&Bk[t], gb, x.first, c);
+                gb = seg_cat<TW>(xb.s, gb, xb.last);
+                st_seg8(&Bk[t], gb, xb.first, c);
             }
         }
         const Seg sds = node_seg(I.node[ds]);

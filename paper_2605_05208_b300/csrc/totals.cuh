@@ -24,9 +24,9 @@ static __device__ void solution_totals(const DevInst &I, const DevSols &D, int s
     const bool open = (I.variant & MD_VARIANT_OPEN) != 0;
     for (int r = tid; r < D.R; r += nt) {
         const size_t sr = (size_t)s * D.R + r;
-        int4 h = D.rhdr[sr];
+        const int4 h = D.rhdr[sr];
+        const Seg8 t = ld_seg8(&D.rterm[sr]);  // loaded with the header (unused for a free slot)
         if (h.x <= 0) continue;
-        Seg8 t = D.rterm[sr];
         a[0] += t.dist;
         a[1] += t.tw;
         a[2] += load_ex(t.load, I.Q);
@@ -41,19 +41,24 @@ static __device__ void solution_totals(const DevInst &I, const DevSols &D, int s
         if ((tid & 31) == 0) red[k][tid >> 5] = v;
     }
     __syncthreads();
-    if (tid == 0) {
-        long long t[6] = {0, 0, 0, 0, 0, 0};
-        for (int k = 0; k < 6; k++)
-            for (int i = 0; i < (nt + 31) / 32; i++) t[k] += red[k][i];
+    if (tid < 32) {
+        // warp 0: lane k < 6 sums quantity k over the warps, the lanes count the depots' routes
+        long long t = 0;
+        if (tid < 6)
+            for (int i = 0; i < (nt + 31) / 32; i++) t += red[tid][i];
         long long vex = 0;
-        for (int d = 0; d < I.nd; d++) {
+        for (int d = tid; d < I.nd; d += 32) {
             vex += max(cnt_sm[d] - I.NV, 0);
             D.dcount[(size_t)s * I.nd + d] = cnt_sm[d];
         }
+        for (int o = 16; o > 0; o >>= 1) vex += __shfl_xor_sync(0xffffffffu, vex, o);
         long long *T = D.tot + (size_t)s * 8;
-        T[0] = t[0]; T[1] = t[1]; T[2] = t[2]; T[3] = t[3];
-        T[4] = t[4]; T[5] = vex; T[6] = t[4] + vex; T[7] = t[5];
-        if (weights) compute_weights(I, D.lam + 4 * s, D.w + 4 * s);
+        const long long clo = __shfl_sync(0xffffffffu, t, 4), nr = __shfl_sync(0xffffffffu, t, 5);
+        if (tid < 4) T[tid] = t;
+        if (tid == 0) {
+            T[4] = clo; T[5] = vex; T[6] = clo + vex; T[7] = nr;
+            if (weights) compute_weights(I, D.lam + 4 * s, D.w + 4 * s);
+        }
     }
     __syncthreads();
 }
