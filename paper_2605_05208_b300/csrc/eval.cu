@@ -46,8 +46,8 @@ struct Ctx {
     DevMoves M;
     uint32_t flags;
     int s;
-    double w[4];
-    float wf[4];
+    const double *w;   // FP64 weights of the solution (shared memory)
+    const float *wf;   // the same rounded to FP32, for the brackets
     bool open, sym;
     bool lists;  // candidates from the neighbour lists (theta > 0 and not a full-sweep step)
 };
@@ -673,10 +673,15 @@ __global__ void __launch_bounds__(32 * MD_EVAL_WARPS, MD_EVAL_MIN_BLOCKS) k_eval
     C.s = s0 + blockIdx.y;
     C.open = (I.variant & MD_VARIANT_OPEN) != 0;
     C.sym = (I.variant & MD_VARIANT_SYMMETRIC) != 0;
-    for (int k = 0; k < 4; k++) {
-        C.w[k] = D.w[4 * C.s + k];
-        C.wf[k] = (float)C.w[k];
+    __shared__ double s_w[4];
+    __shared__ float s_wf[4];
+    if (threadIdx.x < 4) {
+        s_w[threadIdx.x] = D.w[4 * C.s + threadIdx.x];
+        s_wf[threadIdx.x] = (float)s_w[threadIdx.x];
     }
+    __syncthreads();
+    C.w = s_w;
+    C.wf = s_wf;
     const int op_raw = D.ops[C.s];
     const int op = op_raw < 0 ? -1 : (op_raw & MD_OP_MASK);
     C.lists = I.theta > 0 && !(op_raw >= 0 && (op_raw & MD_OP_SWEEP));
@@ -702,6 +707,8 @@ __global__ void __launch_bounds__(32 * MD_EVAL_WARPS, MD_EVAL_MIN_BLOCKS) k_eval
     // Tiles are claimed dynamically from a counter (zeroed before the launch), in work-list order:
     // largest instances first, so the long tiles start early and the short ones fill the gaps.
     __shared__ Ctx cs[MD_EVAL_WARPS];
+    __shared__ double s_w[MD_EVAL_WARPS][4];
+    __shared__ float s_wf[MD_EVAL_WARPS][4];
     __shared__ int s_wl[MD_EVAL_WARPS][64];
     __shared__ int s_tile;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -726,9 +733,11 @@ __global__ void __launch_bounds__(32 * MD_EVAL_WARPS, MD_EVAL_MIN_BLOCKS) k_eval
             C.open = (B.I.variant & MD_VARIANT_OPEN) != 0;
             C.sym = (B.I.variant & MD_VARIANT_SYMMETRIC) != 0;
             for (int k = 0; k < 4; k++) {
-                C.w[k] = B.D.w[4 * s + k];
-                C.wf[k] = (float)C.w[k];
+                s_w[warp][k] = B.D.w[4 * s + k];
+                s_wf[warp][k] = (float)s_w[warp][k];
             }
+            C.w = s_w[warp];
+            C.wf = s_wf[warp];
         }
         have_it = it;
         have_s = s;
