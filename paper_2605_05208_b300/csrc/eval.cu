@@ -18,6 +18,14 @@
 // candidate, so no warp waits for the others of its block.
 #include "mdls_internal.cuh"
 
+#ifndef MD_EVAL_WPC_MAX
+// Warps per evaluated customer when every customer is a candidate (no lists, or a full-sweep
+// step): each takes every wpc-th batch of 32 candidates, which shortens a warp's chain of
+// dependent gathers; wpc = min(MD_EVAL_WPC_MAX, nc / 256).  Granular lists keep one warp per
+// customer (the per-customer work would be duplicated for a few dozen candidates).
+#define MD_EVAL_WPC_MAX 8
+#endif
+
 #ifndef MD_EVAL_MIN_BLOCKS
 // evaluation blocks resident per SM: 16 warps per SM, a register budget of 128 per thread
 #define MD_EVAL_MIN_BLOCKS (16 / MD_EVAL_WARPS)
@@ -274,13 +282,12 @@ __device__ __forceinline__ SN sub_bwd(const Ctx &C, int c, int t) {
 // want_intra) at the back (na), so that the warp can run each kind in passes of its own instead
 // of taking both paths in every pass.  Called by all 32 lanes.
 __device__ __forceinline__ void split_candidates(const Ctx &C, int cu, int u, int A, int lane, int *wl,
-                                                 bool want_intra, int i0, int ncand, int &ni, int &na) {
+                                                 bool want_intra, int i0, int ncand, int nb, int &ni, int &na) {
     const DevInst &I = C.I;
     const unsigned lt = (1u << lane) - 1u;
     ni = 0;
     na = 0;
-#pragma unroll
-    for (int h = 0; h < 64; h += 32) {
+    for (int h = 0; h < nb; h += 32) {
         const int i = i0 + h + lane;
         bool inter = false, intra = false;
         int v = 0;
@@ -305,7 +312,7 @@ __device__ __forceinline__ void split_candidates(const Ctx &C, int cu, int u, in
 // Relocate: seq(u) (1 or 2 nodes, possibly reversed) after v, or before v when v is first.
 // ------------------------------------------------------------------------------------------
 template <bool TW>
-__device__ void eval_relocate(const Ctx &C, int cu, int lane, Best &b, int *wl) {
+__device__ void eval_relocate(const Ctx &C, int cu, int lane, Best &b, int *wl, int part, int wpc) {
     const DevInst &I = C.I;
     const int u = I.nd + cu;
     const Seg8 Pu = pre8(C, u), Su = suf8(C, u);
@@ -331,9 +338,12 @@ __device__ void eval_relocate(const Ctx &C, int cu, int lane, Best &b, int *wl) 
     const int dV_empty = ((!C.open && dsA != deA) ? -1 : 0) +
                          veh_delta(C.D.dcount[(size_t)C.s * I.nd + dsA], I.NV, -1);
     const int ncand = C.lists ? I.nnbr[cu] : I.nc;
-    for (int i0 = 0; i0 < ncand; i0 += 64) {
+    // batches of 64 candidates, or of 32 when wpc warps share the customer: warp part takes
+    // every wpc-th batch
+    const int nb = wpc == 1 ? 64 : 32;
+    for (int i0 = part * nb; i0 < ncand; i0 += nb * wpc) {
         int ni, na;
-        split_candidates(C, cu, u, A, lane, wl, true, i0, ncand, ni, na);
+        split_candidates(C, cu, u, A, lane, wl, true, i0, ncand, nb, ni, na);
         const int ni_pad = (ni + 31) & ~31;  // passes run inter-route or intra-route candidates only
         for (int k = lane; k < ni_pad + na; k += 32) {
             const int v = k < ni ? wl[k] : (k >= ni_pad ? wl[63 - (k - ni_pad)] : -1);
@@ -411,7 +421,7 @@ __device__ __constant__ int SW_RU[9] = {0, 0, 0, 0, 1, 0, 1, 0, 1};
 __device__ __constant__ int SW_RV[9] = {0, 0, 0, 0, 0, 1, 0, 1, 1};
 
 template <bool TW>
-__device__ void eval_swap(const Ctx &C, int cu, int lane, Best &b, int *wl) {
+__device__ void eval_swap(const Ctx &C, int cu, int lane, Best &b, int *wl, int part, int wpc) {
     const DevInst &I = C.I;
     const int u = I.nd + cu;
     const Seg8 Pu = pre8(C, u), Su = suf8(C, u);
@@ -431,9 +441,12 @@ __device__ void eval_swap(const Ctx &C, int cu, int lane, Best &b, int *wl) {
     }
     const int nvar = C.sym ? 9 : 4;
     const int ncand = C.lists ? I.nnbr[cu] : I.nc;
-    for (int i0 = 0; i0 < ncand; i0 += 64) {
+    // batches of 64 candidates, or of 32 when wpc warps share the customer: warp part takes
+    // every wpc-th batch
+    const int nb = wpc == 1 ? 64 : 32;
+    for (int i0 = part * nb; i0 < ncand; i0 += nb * wpc) {
         int ni, na;
-        split_candidates(C, cu, u, A, lane, wl, true, i0, ncand, ni, na);
+        split_candidates(C, cu, u, A, lane, wl, true, i0, ncand, nb, ni, na);
         const int ni_pad = (ni + 31) & ~31;  // passes run inter-route or intra-route candidates only
         for (int k = lane; k < ni_pad + na; k += 32) {
             const int v = k < ni ? wl[k] : (k >= ni_pad ? wl[63 - (k - ni_pad)] : -1);
@@ -504,7 +517,7 @@ __device__ void eval_swap(const Ctx &C, int cu, int lane, Best &b, int *wl) {
 // 2-opt*: [ds_A..u] + [v..de_B] and [ds_B..pred v] + [succ u..de_A].
 // ------------------------------------------------------------------------------------------
 template <bool TW>
-__device__ void eval_2optstar(const Ctx &C, int cu, int lane, Best &b, int *wl) {
+__device__ void eval_2optstar(const Ctx &C, int cu, int lane, Best &b, int *wl, int part, int wpc) {
     const DevInst &I = C.I;
     const int u = I.nd + cu;
     const Seg8 Pu = pre8(C, u), Su = suf8(C, u);
@@ -516,9 +529,12 @@ __device__ void eval_2optstar(const Ctx &C, int cu, int lane, Best &b, int *wl) 
     const Seg PU = seg_of(Pu);
     const bool u_last = su < I.nd;  // depot or MD_NONE after u
     const int ncand = C.lists ? I.nnbr[cu] : I.nc;
-    for (int i0 = 0; i0 < ncand; i0 += 64) {
+    // batches of 64 candidates, or of 32 when wpc warps share the customer: warp part takes
+    // every wpc-th batch
+    const int nb = wpc == 1 ? 64 : 32;
+    for (int i0 = part * nb; i0 < ncand; i0 += nb * wpc) {
         int ni, na;
-        split_candidates(C, cu, u, A, lane, wl, false, i0, ncand, ni, na);
+        split_candidates(C, cu, u, A, lane, wl, false, i0, ncand, nb, ni, na);
         const int ni_pad = (ni + 31) & ~31;  // passes run inter-route or intra-route candidates only
         for (int k = lane; k < ni_pad + na; k += 32) {
             const int v = k < ni ? wl[k] : (k >= ni_pad ? wl[63 - (k - ni_pad)] : -1);
@@ -550,7 +566,8 @@ __device__ void eval_2optstar(const Ctx &C, int cu, int lane, Best &b, int *wl) 
 // Depot-Insert (Fig. 1a): split after u = c_k, k < L, at depot d: [ds..u, d] and [d, succ u..de].
 // ------------------------------------------------------------------------------------------
 template <bool TW>
-__device__ void eval_depot_insert(const Ctx &C, int cu, int lane, Best &b) {
+__device__ void eval_depot_insert(const Ctx &C, int cu, int lane, Best &b, int part) {
+    if (part != 0) return;
     const DevInst &I = C.I;
     const int u = I.nd + cu;
     const Seg8 Pu = pre8(C, u), Su = suf8(C, u);
@@ -577,7 +594,8 @@ __device__ void eval_depot_insert(const Ctx &C, int cu, int lane, Best &b) {
 // arrival or both; the best case by (dF, case) is the move of (route, d).
 // ------------------------------------------------------------------------------------------
 template <bool TW>
-__device__ void eval_depot_replace(const Ctx &C, int cu, int lane, Best &b) {
+__device__ void eval_depot_replace(const Ctx &C, int cu, int lane, Best &b, int part) {
+    if (part != 0) return;
     const DevInst &I = C.I;
     const int u = I.nd + cu;
     const Seg8 Pu = pre8(C, u);
@@ -636,13 +654,14 @@ __device__ __forceinline__ void best_init(Best &b) {
 }
 
 template <bool TW>
-__device__ __forceinline__ void eval_customer(const Ctx &C, int op, int cu, int lane, Best &b, int *wl) {
+__device__ __forceinline__ void eval_customer(const Ctx &C, int op, int cu, int lane, Best &b, int *wl,
+                                              int part = 0, int wpc = 1) {
     switch (op) {
-    case MD_OP_RELOCATE: eval_relocate<TW>(C, cu, lane, b, wl); break;
-    case MD_OP_SWAP: eval_swap<TW>(C, cu, lane, b, wl); break;
-    case MD_OP_TWO_OPT_STAR: eval_2optstar<TW>(C, cu, lane, b, wl); break;
-    case MD_OP_DEPOT_INSERT: eval_depot_insert<TW>(C, cu, lane, b); break;
-    case MD_OP_DEPOT_REPLACE: eval_depot_replace<TW>(C, cu, lane, b); break;
+    case MD_OP_RELOCATE: eval_relocate<TW>(C, cu, lane, b, wl, part, wpc); break;
+    case MD_OP_SWAP: eval_swap<TW>(C, cu, lane, b, wl, part, wpc); break;
+    case MD_OP_TWO_OPT_STAR: eval_2optstar<TW>(C, cu, lane, b, wl, part, wpc); break;
+    case MD_OP_DEPOT_INSERT: eval_depot_insert<TW>(C, cu, lane, b, part); break;
+    case MD_OP_DEPOT_REPLACE: eval_depot_replace<TW>(C, cu, lane, b, part); break;
     default: break;
     }
 }
@@ -667,7 +686,8 @@ __device__ __forceinline__ void warp_commit(const Ctx &C, Best &b, size_t slot, 
 }
 
 template <bool TW>
-__global__ void __launch_bounds__(32 * MD_EVAL_WARPS, MD_EVAL_MIN_BLOCKS) k_eval(DevInst I, DevSols D, DevMoves M, uint32_t flags, int s0) {
+__global__ void __launch_bounds__(32 * MD_EVAL_WARPS, MD_EVAL_MIN_BLOCKS) k_eval(DevInst I, DevSols D, DevMoves M, uint32_t flags, int s0,
+                                                                                 int wpc_full) {
     Ctx C;
     C.I = I; C.D = D; C.M = M; C.flags = flags;
     C.s = s0 + blockIdx.y;
@@ -689,9 +709,10 @@ __global__ void __launch_bounds__(32 * MD_EVAL_WARPS, MD_EVAL_MIN_BLOCKS) k_eval
     Best b;
     best_init(b);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    const int wpc = C.lists ? 1 : wpc_full;
     if (op >= 0)
-        for (int cu = blockIdx.x * wpb + warp; cu < I.nc; cu += gridDim.x * wpb)
-            eval_customer<TW>(C, op, cu, lane, b, s_wl[warp]);
+        for (int gw = blockIdx.x * wpb + warp; gw < I.nc * wpc; gw += gridDim.x * wpb)
+            eval_customer<TW>(C, op, gw / wpc, lane, b, s_wl[warp], gw % wpc, wpc);
     warp_commit(C, b, (size_t)blockIdx.x * wpb + warp, lane);
 }
 
@@ -768,9 +789,14 @@ __global__ void __launch_bounds__(32 * MD_EVAL_WARPS, MD_EVAL_MIN_BLOCKS) k_eval
 #define MD_EVAL_UPW 1  // customers per warp of one evaluation launch
 #endif
 
+static int eval_wpc_full(const md_solutions *s) {
+    const int w = s->inst->d.nc / 256;
+    return w < 1 ? 1 : (w > MD_EVAL_WPC_MAX ? MD_EVAL_WPC_MAX : w);
+}
+
 int md_eval_blocks(const md_solutions *s) {
     int nc = s->inst->d.nc;
-    int b = (nc + MD_EVAL_WARPS * MD_EVAL_UPW - 1) / (MD_EVAL_WARPS * MD_EVAL_UPW);
+    int b = (nc * eval_wpc_full(s) + MD_EVAL_WARPS * MD_EVAL_UPW - 1) / (MD_EVAL_WARPS * MD_EVAL_UPW);
     return b < 1024 ? b : 1024;
 }
 
@@ -781,8 +807,9 @@ md_status md_launch_eval(md_solutions *s, md_moves *m, uint32_t flags, cudaStrea
     if (count < 0) count = s->n_sol - s0;
     if (count <= 0) return MD_OK;
     dim3 grid(m->d.nblk / MD_EVAL_WARPS, count);
-    if (I.variant & MD_VARIANT_TW) k_eval<true><<<grid, 32 * MD_EVAL_WARPS, 0, st>>>(I, s->d, m->d, flags, s0);
-    else k_eval<false><<<grid, 32 * MD_EVAL_WARPS, 0, st>>>(I, s->d, m->d, flags, s0);
+    const int wpc = eval_wpc_full(s);
+    if (I.variant & MD_VARIANT_TW) k_eval<true><<<grid, 32 * MD_EVAL_WARPS, 0, st>>>(I, s->d, m->d, flags, s0, wpc);
+    else k_eval<false><<<grid, 32 * MD_EVAL_WARPS, 0, st>>>(I, s->d, m->d, flags, s0, wpc);
     MD_CUDA(cudaGetLastError());
     return MD_OK;
 }

@@ -129,6 +129,8 @@ def _eval_cases():
                                    "random", (1.0, 1.0, 1.0, 1.0)),
         "tiny-sym-theta": (tiny_spec(17, nd=3, nc=45, sym=True, Q=30, NV=2, theta=6), "random",
                            (1.0, 1.0, 1.0, 8.0)),
+        # 1100 customers, full neighbourhood: several warps share each customer's candidates
+        "mdovrp-5x1100-full": (W.gen_mdovrp(19, n_depots=5, n_customers=1100), 1, (1.0, 1.0, 1.0, 1.0)),
         # routes of 33 to 60 customers: summaries and subsequence tables span two chunks of 32
         "tiny-long-routes-tw": (tiny_spec(18, nd=3, nc=110, tw=True, sym=True, Q=400, NV=2, D=900,
                                           horizon=4000, wmin=200, wmax=1500), "long",
@@ -297,6 +299,23 @@ def test_installed_lists_and_sweep_schedule_match_oracle(md, oracle_lib, stream,
         d = o.descend(sol, perm[s], 60, sweep_every=sweep)
         assert canon(spec, got[s]) == canon(spec, d.solution)
         assert list(per[s]) == [d.moves_scored, d.steps, d.accepted_steps, d.applied_moves, d.passes]
+
+
+def test_sweep_steps_of_a_large_instance_match_oracle(md, oracle_lib, stream):
+    # 600 customers with short random lists and a full sweep every third step: the sweep steps
+    # spread each customer's candidates over several warps
+    spec = W.gen_mdvrptw(59, n_depots=4, n_customers=600, theta=12)
+    sols = W.initial_solutions(spec, 59, 1)
+    nbr, cnt = random_neighbor_lists(spec, 12, 6)
+    inst, S = setup(md, spec, sols, R=200, K=120)
+    inst.set_neighbors(nbr, cnt)
+    perm = W.op_permutations(10, 1, 6)
+    S.descend(perm, 6, use_graph=True, stream=stream, sweep_every=3)
+    o = oracle_lib.Instance(spec)
+    o.set_neighbors(nbr, cnt)
+    d = o.descend(sols[0], perm[0], 6, sweep_every=3)
+    assert canon(spec, S.read()[0]) == canon(spec, d.solution)
+    assert list(S.stats()[0]) == [d.moves_scored, d.steps, d.accepted_steps, d.applied_moves, d.passes]
 
 
 # ------------------------------------------------------------------------------------------
