@@ -354,7 +354,7 @@ def run_batch(args):
     perm_dev = torch.from_numpy(perm_all).to(dev)
     perm_devs = [torch.from_numpy(p).to(dev) for p in perms]
     B = mdls.Batch(works)
-    upw, grid = B.tune(stream=sptr)
+    upw, wpc, grid = B.tune(stream=sptr)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
 
     def restore():
@@ -400,7 +400,8 @@ def run_batch(args):
         "config": {"workload": f"batch16-uneven: 16 instances ({', '.join(sp.name for sp in specs)}), "
                                f"16 solutions each, {max_pass} passes per step, multi-move",
                    "l2": "flushed between timed steps (256 MB write)",
-                   "tuning": {"customers_per_warp": upw.tolist(), "grid": grid}},
+                   "tuning": {"customer_parts_per_warp": upw.tolist(), "warps_per_customer": wpc.tolist(),
+                              "grid": grid}},
         "batched": res["batched"], "per_instance": res["per_instance"],
         "speedup_vs_per_instance": res["batched"]["moves_per_s"] / res["per_instance"]["moves_per_s"],
     }))

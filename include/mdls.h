@@ -285,14 +285,23 @@ typedef struct md_batch md_batch;
 md_status md_batch_create(md_solutions *const *sols, int32_t n, md_batch **out);
 md_status md_batch_destroy(md_batch *batch);
 
-/* Autotuner of the batch's tile shapes: per instance, the customers per warp of an evaluation
- * tile (1, 2 or 4), timed with CUDA events on that instance alone; then the persistent grid
- * (1, 2, 4 or 8 blocks per SM), timed on the whole batch.  Uses the loaded solutions and sets
- * every solution's operator to a fixed mix for the timings.  Results only change speed. */
+/* Autotuner of the batch's tile shapes: per instance, the customer parts per warp of an
+ * evaluation tile (1, 2 or 4) and, for an instance without neighbour lists, the warps that share
+ * one customer's candidates (1, 2, 4 or 8, at most n_customers / 256), timed with CUDA events on
+ * that instance alone; then the persistent grid (1, 2, 4 or 8 blocks per SM), timed on the whole
+ * batch.  Uses the loaded solutions and sets every solution's operator to a fixed mix for the
+ * timings.  Results only change speed. */
 md_status md_batch_tune(md_batch *batch, void *stream);
 
-/* The chosen shapes: upw [n] customers per warp per instance (caller order), grid blocks. */
-md_status md_batch_tuning(const md_batch *batch, int32_t *upw, int32_t *grid);
+/* The chosen shapes (caller order, [n] each; any pointer may be NULL): upw customer parts per
+ * warp, wpc warps per customer, grid blocks of the evaluation launch. */
+md_status md_batch_tuning(const md_batch *batch, int32_t *upw, int32_t *wpc, int32_t *grid);
+
+/* Sets the shapes by hand (host arrays [n] in caller order; NULL keeps the current ones; grid
+ * <= 0 keeps it): upw >= 1; wpc in 1..8, above 1 only for an instance without neighbour lists
+ * and at most n_customers / 256.  MD_ERR_ARG otherwise (nothing changed).  Results only change
+ * speed. */
+md_status md_batch_set_tuning(md_batch *batch, const int32_t *upw, const int32_t *wpc, int32_t grid);
 
 /* MDFIS descent (Alg. 2) of every solution of every instance, as md_descend per instance would
  * do it (identical results).  cfg->op_perm covers the solutions of all instances in the order

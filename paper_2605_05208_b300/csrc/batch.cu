@@ -27,7 +27,8 @@ struct md_batch {
     int n;
     std::vector<md_solutions *> sols;  // in the caller's order
     std::vector<int> order;            // item order on the device: largest instances first
-    std::vector<int> upw;              // customers per warp, per caller item
+    std::vector<int> upw;              // customer parts per warp, per caller item
+    std::vector<int> wpc;              // warps per customer, per caller item
     int grid;                          // persistent evaluation grid
     bool tw;
     size_t smem;
@@ -59,10 +60,13 @@ static std::vector<BatchItem> build_items(md_batch *b, const std::vector<int> &o
         it.M = s->scratch->d;
         const int nc = it.I.nc;
         int u = b->upw[k];
-        const int cap = (nc + 8 * 1024 - 1) / (8 * 1024);  // leader records are capped at 1024 * 8
+        const int w = b->wpc[k];
+        const int parts = nc * w;
+        const int cap = (parts + 8 * 1024 - 1) / (8 * 1024);  // leader records are capped at 1024 * 8
         if (u < cap) u = cap;
         it.upw = u;
-        it.tiles_per_sol = (nc + 8 * u - 1) / (8 * u);
+        it.wpc = w;
+        it.tiles_per_sol = (parts + 8 * u - 1) / (8 * u);
         it.nrec = it.tiles_per_sol * MD_EVAL_WARPS;
         it.tile_base = tb;
         it.sol_base = sb;
@@ -87,6 +91,7 @@ extern "C" md_status md_batch_create(md_solutions *const *sols, int32_t n, md_ba
     b->n = n;
     b->sols.assign(sols, sols + n);
     b->upw.assign(n, 1);
+    b->wpc.assign(n, 1);
     b->grid = 2 * sm_count();
     b->tw = false;
     b->smem = 0;
@@ -126,10 +131,29 @@ extern "C" md_status md_batch_destroy(md_batch *b) {
     return MD_OK;
 }
 
-extern "C" md_status md_batch_tuning(const md_batch *b, int32_t *upw, int32_t *grid) {
+extern "C" md_status md_batch_tuning(const md_batch *b, int32_t *upw, int32_t *wpc, int32_t *grid) {
     if (!b) { md_set_error("md_batch_tuning: null batch"); return MD_ERR_ARG; }
     if (upw) for (int i = 0; i < b->n; i++) upw[i] = b->upw[i];
+    if (wpc) for (int i = 0; i < b->n; i++) wpc[i] = b->wpc[i];
     if (grid) *grid = b->grid;
+    return MD_OK;
+}
+
+extern "C" md_status md_batch_set_tuning(md_batch *b, const int32_t *upw, const int32_t *wpc, int32_t grid) {
+    if (!b) { md_set_error("md_batch_set_tuning: null batch"); return MD_ERR_ARG; }
+    for (int i = 0; i < b->n; i++) {
+        const DevInst &I = b->sols[i]->inst->d;
+        const int wmax = I.theta > 0 ? 1 : std::max(1, std::min(8, I.nc / 256));
+        if ((upw && upw[i] < 1) || (wpc && (wpc[i] < 1 || wpc[i] > wmax))) {
+            md_set_error("md_batch_set_tuning: item %d: need upw >= 1 and 1 <= wpc <= %d", i, wmax);
+            return MD_ERR_ARG;
+        }
+    }
+    for (int i = 0; i < b->n; i++) {
+        if (upw) b->upw[i] = upw[i];
+        if (wpc) b->wpc[i] = wpc[i];
+    }
+    if (grid > 0) b->grid = grid;
     return MD_OK;
 }
 
@@ -171,8 +195,10 @@ md_status time_eval(md_batch *b, const std::vector<int> &order, int grid, int re
 
 }  // namespace
 
-// Autotuner: per instance, the customers per warp of an evaluation tile (1, 2 or 4), timed on
-// that instance alone; then the persistent grid (1, 2, 4 or 8 blocks per SM) for the whole batch.
+// Autotuner: per instance, the customer parts per warp of an evaluation tile (1, 2 or 4) and,
+// for instances without neighbour lists, the warps per customer (1, 2, 4 or 8, at most nc / 256
+// so that the records fit the evaluation scratch), timed on that instance alone; then the
+// persistent grid (1, 2, 4 or 8 blocks per SM) for the whole batch.
 // Every solution's operator is set to a fixed mix (s mod 5) for the timings; md_batch_descend
 // resets it.
 extern "C" md_status md_batch_tune(md_batch *b, void *stream) {
@@ -185,15 +211,21 @@ extern "C" md_status md_batch_tune(md_batch *b, void *stream) {
     const int sms = sm_count();
     for (int i = 0; i < b->n; i++) {
         float best = 1e30f;
-        int bu = 1;
+        int bu = 1, bw = 1;
+        const DevInst &I = b->sols[i]->inst->d;
+        const int wmax = I.theta > 0 ? 1 : std::max(1, std::min(8, I.nc / 256));
         for (int u : {1, 2, 4}) {
-            b->upw[i] = u;
-            float ms = 0.0f;
-            md_status r = time_eval(b, std::vector<int>{i}, 2 * sms, 3, st, &ms);
-            if (r != MD_OK) return r;
-            if (ms < best) { best = ms; bu = u; }
+            for (int w = 1; w <= wmax; w *= 2) {
+                b->upw[i] = u;
+                b->wpc[i] = w;
+                float ms = 0.0f;
+                md_status r = time_eval(b, std::vector<int>{i}, 2 * sms, 3, st, &ms);
+                if (r != MD_OK) return r;
+                if (ms < best) { best = ms; bu = u; bw = w; }
+            }
         }
         b->upw[i] = bu;
+        b->wpc[i] = bw;
     }
     float best = 1e30f;
     int bg = 2 * sms;

@@ -771,12 +771,13 @@ __global__ void __launch_bounds__(32 * MD_EVAL_WARPS, MD_EVAL_MIN_BLOCKS) k_eval
         best_init(b);
         const int ws = t * MD_EVAL_WARPS + warp;  // warp slot within the solution
         const bool tw = TW_ANY && (C.I.variant & MD_VARIANT_TW) != 0;
+        const int wpc = B.wpc;  // > 1 only for items without lists
         if (op >= 0)
             for (int q = 0; q < upw; q++) {
-                const int cu = ws * upw + q;
-                if (cu >= C.I.nc) break;
-                if (tw) eval_customer<true>(C, op, cu, lane, b, s_wl[warp]);
-                else eval_customer<false>(C, op, cu, lane, b, s_wl[warp]);
+                const int gw = ws * upw + q;
+                if (gw >= C.I.nc * wpc) break;
+                if (tw) eval_customer<true>(C, op, gw / wpc, lane, b, s_wl[warp], gw % wpc, wpc);
+                else eval_customer<false>(C, op, gw / wpc, lane, b, s_wl[warp], gw % wpc, wpc);
             }
         warp_commit(C, b, ws, lane);
         __syncwarp();  // every lane is done with this tile's context

@@ -223,17 +223,19 @@ struct md_moves {
 };
 
 // One instance of a batch (md_batch_*): its tensors, solutions and scratch, and its place in the
-// batch's work lists.  A tile is 8 warps x upw customers of one solution.
+// batch's work lists.  A tile is 8 warps x upw customer parts (wpc parts per customer) of one
+// solution.
 struct BatchItem {
     DevInst I;
     DevSols D;
     DevMoves M;
     int tile_base;      // first global tile of this item
-    int tiles_per_sol;  // ceil(nc / (8 * upw))
-    int upw;            // customers per warp in a tile
+    int tiles_per_sol;  // ceil(nc * wpc / (8 * upw))
+    int upw;            // customer parts per warp in a tile
+    int wpc;            // warps (parts) per customer: > 1 only without neighbour lists
     int nrec;           // leader records per solution in use (tiles_per_sol * 8)
     int sol_base;       // first global solution index of this item
-    int pad[3];
+    int pad[2];
 };
 
 void md_set_error(const char *fmt, ...);

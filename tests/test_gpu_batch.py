@@ -52,8 +52,8 @@ def test_batch_descent_matches_per_instance(case, tuned, graph):
     B = md.Batch([S for _, S in loaded])
     stream = torch.cuda.Stream().cuda_stream
     if tuned:
-        upw, grid = B.tune(stream=stream)
-        assert set(upw.tolist()) <= {1, 2, 4} and grid > 0
+        upw, wpc, grid = B.tune(stream=stream)
+        assert set(upw.tolist()) <= {1, 2, 4} and set(wpc.tolist()) <= {1} and grid > 0
         for (_, S), so in zip(loaded, sols):
             S.load(so)  # tuning leaves the solutions untouched; reload anyway to start clean
     st = B.descend(np.concatenate(perms), MAX_PASS, use_graph=graph, stream=stream)
@@ -81,3 +81,30 @@ def test_batch_matches_oracle(case, oracle_lib):
             op = bool(sp.variant & W.VAR_OPEN)
             assert W.canonical(got[s], op) == W.canonical(d.solution, op)
             assert list(per[s]) == [d.moves_scored, d.steps, d.accepted_steps, d.applied_moves, d.passes]
+
+
+def test_batch_with_shared_customers_matches_per_instance():
+    # a 600-customer instance without lists evaluated with two warps per customer (and two
+    # customer parts per warp) inside the batch, beside a small instance with lists
+    import torch
+    from paper_2605_05208_b300 import build, mdls as md
+    build.build()
+    specs = [W.gen_mdovrp(85, n_depots=4, n_customers=600, n_solutions=2),
+             W.gen_mdvrptw(86, n_depots=2, n_customers=90, theta=15, n_solutions=2)]
+    sols = [W.initial_solutions(sp, 97 + i, 2) for i, sp in enumerate(specs)]
+    perms = [W.op_permutations(98 + i, 2, 6) for i in range(2)]
+    ref = []
+    for sp, so, pe in zip(specs, sols, perms):
+        inst, S = _load(md, sp, so)
+        S.descend(pe, 6)
+        ref.append(([W.canonical(r, bool(sp.variant & W.VAR_OPEN)) for r in S.read()], S.stats()))
+    loaded = [_load(md, sp, so) for sp, so in zip(specs, sols)]
+    B = md.Batch([S for _, S in loaded])
+    with pytest.raises(md.MdError):
+        B.set_tuning(wpc=[2, 2])  # the listed instance keeps one warp per customer
+    B.set_tuning(upw=[2, 1], wpc=[2, 1], grid=296)
+    assert [x.tolist() if hasattr(x, "tolist") else x for x in B.tuning()] == [[2, 1], [2, 1], 296]
+    B.descend(np.concatenate(perms), 6, stream=torch.cuda.Stream().cuda_stream)
+    for (_, S), sp, (want, stats) in zip(loaded, specs, ref):
+        assert [W.canonical(r, bool(sp.variant & W.VAR_OPEN)) for r in S.read()] == want
+        assert np.array_equal(S.stats(), stats)
