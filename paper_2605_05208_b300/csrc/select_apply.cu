@@ -46,7 +46,10 @@ static size_t step_smem(const md_solutions *s, int threads) {
     return step_smem_bytes(s->R, s->inst->d.nd, s->K, threads);
 }
 
-static const int STEP_THREADS = 256;
+#ifndef MD_STEP_THREADS
+#define MD_STEP_THREADS 256  // threads of a step CTA
+#endif
+static const int STEP_THREADS = MD_STEP_THREADS;
 
 size_t md_step_smem(const md_solutions *s) { return step_smem(s, STEP_THREADS); }
 
