@@ -40,6 +40,11 @@ THETA = 50
 # second route for 2-opt* and the depot operators); u-independent summaries are amortised.
 ALG_BYTES = {W.OP_RELOCATE: 8, W.OP_SWAP: 16, W.OP_TWO_OPT_STAR: 56, W.OP_DEPOT_INSERT: 32,
              W.OP_DEPOT_REPLACE: 32}
+# DRAM bytes (read + write) per k_eval launch of the default workload, averaged over 200
+# launches of `python bench.py --steps 1 --warmup 3 --no-cpu-baseline` under ncu
+# (dram__bytes_read.sum + dram__bytes_write.sum).  It describes the evaluation kernel as committed
+# with it; a change to that kernel makes it stale.
+EVAL_TRAFFIC_6X288 = 879995
 CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -307,7 +312,7 @@ def run_ours(args):
             "passes_max": last.passes_max, "steps_per_descent": last.steps / N_SOL,
             "roofline": {"kernel": "k_eval (neighbourhood evaluation)", "bound": "hbm",
                          "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                         "peak_source": peak_src, "traffic": None,
+                         "peak_source": peak_src, "traffic": EVAL_TRAFFIC_6X288,
                          "eval_ms_per_launch": eval_ms / max(eval_launches, 1),
                          "alg_bytes_per_launch": alg_bytes / max(eval_launches, 1),
                          "eval_ms_summed_per_step": eval_ms / args.steps,
