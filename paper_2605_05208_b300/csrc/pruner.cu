@@ -33,6 +33,7 @@ struct md_pruner {
     float *P, *G, *M, *V;        // parameters, gradients, Adam moments (FP32, PR_NPARAM each)
     __nv_bfloat16 *w1h, *w2h;    // BF16 copies of W1 [128x32] and W2 [128x128] for inference
     float *loss;                 // [2] summed loss, summed weight of the last training call
+    int *err;                    // [1] set when a wait for the tensor cores timed out
     long long step;              // Adam step counter
 };
 
@@ -114,109 +115,207 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     return *reinterpret_cast<uint32_t *>(&h);
 }
 
-__device__ __forceinline__ void mma_bf16(float *d, const uint32_t *a, uint32_t b0, uint32_t b1) {
-    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-                 "{%0,%1,%2,%3};\n"
-                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+// ------------------------------------------------------------------------------------------
+// 5th-generation tensor cores (tcgen05): operands in shared memory, accumulators in TMEM.
+// ------------------------------------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Byte offset of element (r, k) of a BF16 tile with K columns stored as K-major core matrices
+// without swizzle: a core matrix is 8 rows x 16 bytes (128 contiguous bytes); core matrices
+// adjacent along K are 128 bytes apart, adjacent along the rows K * 16 bytes apart.
+__device__ __forceinline__ int tc_off(int r, int k, int K) {
+    return (r >> 3) * (K * 16) + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
 }
 
-// Tensor-core scoring: each warp scores 16 (u, candidate) pairs; 4 warps per block.
-__global__ void __launch_bounds__(128) k_score(DevInst I, const int32_t *lists, const int32_t *cnt, int pool, Aux A,
-                                               float horizon, const __nv_bfloat16 *w1h, const __nv_bfloat16 *w2h,
-                                               const float *P, float *scores, long long n_pairs) {
-    __shared__ __align__(16) __nv_bfloat16 sW1[PR_H * PR_F];
-    __shared__ __align__(16) __nv_bfloat16 sW2[PR_H * PR_H];
-    __shared__ float sB1[PR_H], sB2[PR_H], sW3[PR_H];
-    __shared__ __align__(16) __nv_bfloat16 sF[4][16][PR_F + 8];
-    for (int i = threadIdx.x; i < PR_H * PR_F; i += blockDim.x) sW1[i] = w1h[i];
-    for (int i = threadIdx.x; i < PR_H * PR_H; i += blockDim.x) sW2[i] = w2h[i];
-    for (int i = threadIdx.x; i < PR_H; i += blockDim.x) {
+// Shared-memory matrix descriptor: start address, byte offset between core matrices along K
+// (leading) and along the rows (stride), descriptor version 1, no swizzle.
+__device__ __forceinline__ uint64_t tc_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+
+// Instruction descriptor of kind::f16 with an FP32 accumulator, BF16 A and B, both K-major.
+__device__ __forceinline__ uint32_t tc_idesc(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// D[tmem] (+)= A * B^T, issued by one thread.
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, int accumulate) {
+    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                 :: "r"(d), "l"(a), "l"(b), "r"(idesc), "r"(accumulate) : "memory");
+}
+
+// Arrival on the mbarrier once the thread's issued MMAs have completed.
+__device__ __forceinline__ void tc_commit(uint64_t *mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                 :: "r"(smem_u32(mbar)) : "memory");
+}
+
+// Waits for the mbarrier phase with the given parity; gives up after `limit` polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity, int limit) {
+    uint32_t done = 0;
+    for (int it = 0; it < limit && !done; it++)
+        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                     "selp.u32 %0, 1, 0, p;\n}\n" : "=r"(done) : "r"(smem_u32(mbar)), "r"(parity) : "memory");
+    return done != 0;
+}
+
+__device__ __forceinline__ void tc_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void async_proxy_fence() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// 32 consecutive FP32 columns of the thread's TMEM lane (warp w reads lanes 32w .. 32w + 31).
+__device__ __forceinline__ void tc_ld32(uint32_t taddr, float *out) {
+    uint32_t v[32];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                   "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+                   "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+                   "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 32; j++) out[j] = __uint_as_float(v[j]);
+}
+
+#define TC_ROWS 128           // pairs per tile = MMA M = TMEM lanes
+#define TC_WAIT (1 << 20)     // polls before a wait for the tensor cores gives up
+#define TC_SMEM (TC_ROWS * PR_F * 2 + PR_H * PR_F * 2 + TC_ROWS * PR_H * 2 + PR_H * PR_H * 2 + 3 * PR_H * 4)
+
+// Tensor-core scoring, one tile of 128 (u, candidate) pairs at a time per CTA of 128 threads
+// (thread r owns row r, i.e. TMEM lane r):
+//   layer 1: X [128 x 32] (features, BF16) x W1^T -> TMEM columns 0..127 (FP32);
+//   bias + ReLU, rounded to BF16 into H [128 x 128] in shared memory;
+//   layer 2: H x W2^T -> TMEM columns 128..255; bias + ReLU and the output layer in FP32.
+// W1 and W2 stay in shared memory for every tile.  Waits for the tensor cores are bounded: on a
+// timeout the CTA sets *err, stops, and releases its TMEM.
+__global__ void __launch_bounds__(TC_ROWS) k_score_tc(DevInst I, const int32_t *lists, const int32_t *cnt, int pool,
+                                                     Aux A, float horizon, const __nv_bfloat16 *w1h,
+                                                     const __nv_bfloat16 *w2h, const float *P, float *scores,
+                                                     long long n_pairs, int *err) {
+    extern __shared__ __align__(1024) unsigned char tsm[];
+    unsigned char *sX = tsm;                                  // 128 x 32
+    unsigned char *sW1 = sX + TC_ROWS * PR_F * 2;             // 128 x 32
+    unsigned char *sH = sW1 + PR_H * PR_F * 2;                // 128 x 128
+    unsigned char *sW2 = sH + TC_ROWS * PR_H * 2;             // 128 x 128
+    float *sB1 = reinterpret_cast<float *>(sW2 + PR_H * PR_H * 2);
+    float *sB2 = sB1 + PR_H, *sW3 = sB2 + PR_H;
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t s_tmem;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    for (int e = tid; e < PR_H * PR_F; e += TC_ROWS)
+        *reinterpret_cast<__nv_bfloat16 *>(sW1 + tc_off(e / PR_F, e % PR_F, PR_F)) = w1h[e];
+    for (int e = tid; e < PR_H * PR_H; e += TC_ROWS)
+        *reinterpret_cast<__nv_bfloat16 *>(sW2 + tc_off(e / PR_H, e % PR_H, PR_H)) = w2h[e];
+    for (int i = tid; i < PR_H; i += TC_ROWS) {
         sB1[i] = P[PR_B1 + i];
         sB2[i] = P[PR_B2 + i];
         sW3[i] = P[PR_W3 + i];
     }
-    __syncthreads();
-    const float b3 = P[PR_B3];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    const long long tiles = (n_pairs + 15) / 16;
-    for (long long tile = (long long)blockIdx.x * 4 + warp; tile < tiles; tile += (long long)gridDim.x * 4) {
-        // features of the 16 rows, as BF16, in this warp's shared tile
-        if (lane < 16) {
-            const long long p = tile * 16 + lane;
-            float f[PR_F];
-            bool ok = false;
-            if (p < n_pairs) {
-                const int cu = (int)(p / pool), i = (int)(p % pool);
-                if (i < cnt[cu]) {
-                    pair_features(I, A, horizon, I.nd + cu, lists[(size_t)cu * pool + i], i, pool, f);
-                    ok = true;
-                }
-            }
-            for (int k = 0; k < PR_F; k++) sF[warp][lane][k] = __float2bfloat16_rn(ok ? f[k] : 0.0f);
-        }
-        __syncwarp();
-        // layer 1: [16 x 32] x [32 x 128]
-        float acc[16][4];
-#pragma unroll
-        for (int j = 0; j < 16; j++) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.0f;
-#pragma unroll
-        for (int kk = 0; kk < 2; kk++) {
-            uint32_t a[4];
-            a[0] = *reinterpret_cast<const uint32_t *>(&sF[warp][g][16 * kk + 2 * t]);
-            a[1] = *reinterpret_cast<const uint32_t *>(&sF[warp][g + 8][16 * kk + 2 * t]);
-            a[2] = *reinterpret_cast<const uint32_t *>(&sF[warp][g][16 * kk + 2 * t + 8]);
-            a[3] = *reinterpret_cast<const uint32_t *>(&sF[warp][g + 8][16 * kk + 2 * t + 8]);
-#pragma unroll
-            for (int j = 0; j < 16; j++) {
-                const __nv_bfloat16 *wr = &sW1[(8 * j + g) * PR_F + 16 * kk + 2 * t];
-                mma_bf16(acc[j], a, *reinterpret_cast<const uint32_t *>(wr), *reinterpret_cast<const uint32_t *>(wr + 8));
-            }
-        }
-        // bias + ReLU, repacked as the A fragments of layer 2
-        uint32_t a2[8][4];
-#pragma unroll
-        for (int kk = 0; kk < 8; kk++) {
-#pragma unroll
-            for (int h = 0; h < 2; h++) {
-                const int j = 2 * kk + h, c = 8 * j + 2 * t;
-                const float x0 = fmaxf(acc[j][0] + sB1[c], 0.0f), x1 = fmaxf(acc[j][1] + sB1[c + 1], 0.0f);
-                const float x2 = fmaxf(acc[j][2] + sB1[c], 0.0f), x3 = fmaxf(acc[j][3] + sB1[c + 1], 0.0f);
-                a2[kk][2 * h + 0] = pack_bf16(x0, x1);  // row g
-                a2[kk][2 * h + 1] = pack_bf16(x2, x3);  // row g + 8
-            }
-        }
-        // layer 2: [16 x 128] x [128 x 128]
-#pragma unroll
-        for (int j = 0; j < 16; j++) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.0f;
-#pragma unroll
-        for (int kk = 0; kk < 8; kk++) {
-            const uint32_t a[4] = {a2[kk][0], a2[kk][1], a2[kk][2], a2[kk][3]};
-#pragma unroll
-            for (int j = 0; j < 16; j++) {
-                const __nv_bfloat16 *wr = &sW2[(8 * j + g) * PR_H + 16 * kk + 2 * t];
-                mma_bf16(acc[j], a, *reinterpret_cast<const uint32_t *>(wr), *reinterpret_cast<const uint32_t *>(wr + 8));
-            }
-        }
-        // bias + ReLU + output layer
-        float s0 = 0.0f, s8 = 0.0f;
-#pragma unroll
-        for (int j = 0; j < 16; j++) {
-            const int c = 8 * j + 2 * t;
-            s0 += sW3[c] * fmaxf(acc[j][0] + sB2[c], 0.0f) + sW3[c + 1] * fmaxf(acc[j][1] + sB2[c + 1], 0.0f);
-            s8 += sW3[c] * fmaxf(acc[j][2] + sB2[c], 0.0f) + sW3[c + 1] * fmaxf(acc[j][3] + sB2[c + 1], 0.0f);
-        }
-        s0 += __shfl_xor_sync(0xffffffffu, s0, 1);
-        s0 += __shfl_xor_sync(0xffffffffu, s0, 2);
-        s8 += __shfl_xor_sync(0xffffffffu, s8, 1);
-        s8 += __shfl_xor_sync(0xffffffffu, s8, 2);
-        if (t == 0) {
-            const long long p0 = tile * 16 + g, p8 = p0 + 8;
-            if (p0 < n_pairs) scores[p0] = (int)(p0 % pool) < cnt[p0 / pool] ? s0 + b3 : -INFINITY;
-            if (p8 < n_pairs) scores[p8] = (int)(p8 % pool) < cnt[p8 / pool] ? s8 + b3 : -INFINITY;
-        }
-        __syncwarp();
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(smem_u32(&s_tmem)), "r"(2 * PR_H) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
+    if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(&mbar)), "r"(1) : "memory");
+    async_proxy_fence();
+    tc_before_sync();
+    __syncthreads();
+    tc_after_sync();
+    const uint32_t d1 = s_tmem, d2 = s_tmem + PR_H, lane_base = (uint32_t)(32 * warp) << 16;
+    const uint32_t idesc = tc_idesc(TC_ROWS, PR_H);
+    const float b3 = P[PR_B3];
+    uint32_t parity = 0;
+    const long long tiles = (n_pairs + TC_ROWS - 1) / TC_ROWS;
+    for (long long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        // features of this thread's pair into X
+        const long long p = tile * TC_ROWS + tid;
+        float f[PR_F];
+        bool ok = false;
+        if (p < n_pairs) {
+            const int cu = (int)(p / pool), i = (int)(p % pool);
+            if (i < cnt[cu]) {
+                pair_features(I, A, horizon, I.nd + cu, lists[(size_t)cu * pool + i], i, pool, f);
+                ok = true;
+            }
+        }
+#pragma unroll
+        for (int kb = 0; kb < PR_F / 8; kb++) {
+            uint4 q;
+            q.x = pack_bf16(ok ? f[8 * kb + 0] : 0.0f, ok ? f[8 * kb + 1] : 0.0f);
+            q.y = pack_bf16(ok ? f[8 * kb + 2] : 0.0f, ok ? f[8 * kb + 3] : 0.0f);
+            q.z = pack_bf16(ok ? f[8 * kb + 4] : 0.0f, ok ? f[8 * kb + 5] : 0.0f);
+            q.w = pack_bf16(ok ? f[8 * kb + 6] : 0.0f, ok ? f[8 * kb + 7] : 0.0f);
+            *reinterpret_cast<uint4 *>(sX + tc_off(tid, 8 * kb, PR_F)) = q;
+        }
+        async_proxy_fence();
+        tc_before_sync();
+        __syncthreads();
+        tc_after_sync();
+        if (tid == 0) {
+#pragma unroll
+            for (int kk = 0; kk < PR_F / 16; kk++)
+                tc_mma(d1, tc_desc(smem_u32(sX) + kk * 256, 128, PR_F * 16), tc_desc(smem_u32(sW1) + kk * 256, 128, PR_F * 16),
+                       idesc, kk);
+            tc_commit(&mbar);
+        }
+        if (__syncthreads_or(!mbar_wait(&mbar, parity, TC_WAIT))) {
+            if (tid == 0) atomicExch(err, 1);
+            break;
+        }
+        parity ^= 1u;
+        tc_after_sync();
+        // first hidden layer: bias + ReLU, BF16, into H
+#pragma unroll 1
+        for (int c0 = 0; c0 < PR_H; c0 += 32) {
+            float v[32];
+            tc_ld32(d1 + lane_base + c0, v);
+#pragma unroll
+            for (int j = 0; j < 32; j += 8) {
+                uint4 q;
+                q.x = pack_bf16(fmaxf(v[j + 0] + sB1[c0 + j + 0], 0.0f), fmaxf(v[j + 1] + sB1[c0 + j + 1], 0.0f));
+                q.y = pack_bf16(fmaxf(v[j + 2] + sB1[c0 + j + 2], 0.0f), fmaxf(v[j + 3] + sB1[c0 + j + 3], 0.0f));
+                q.z = pack_bf16(fmaxf(v[j + 4] + sB1[c0 + j + 4], 0.0f), fmaxf(v[j + 5] + sB1[c0 + j + 5], 0.0f));
+                q.w = pack_bf16(fmaxf(v[j + 6] + sB1[c0 + j + 6], 0.0f), fmaxf(v[j + 7] + sB1[c0 + j + 7], 0.0f));
+                *reinterpret_cast<uint4 *>(sH + tc_off(tid, c0 + j, PR_H)) = q;
+            }
+        }
+        async_proxy_fence();
+        tc_before_sync();
+        __syncthreads();
+        tc_after_sync();
+        if (tid == 0) {
+#pragma unroll
+            for (int kk = 0; kk < PR_H / 16; kk++)
+                tc_mma(d2, tc_desc(smem_u32(sH) + kk * 256, 128, PR_H * 16), tc_desc(smem_u32(sW2) + kk * 256, 128, PR_H * 16),
+                       idesc, kk);
+            tc_commit(&mbar);
+        }
+        if (__syncthreads_or(!mbar_wait(&mbar, parity, TC_WAIT))) {
+            if (tid == 0) atomicExch(err, 1);
+            break;
+        }
+        parity ^= 1u;
+        tc_after_sync();
+        // second hidden layer: bias + ReLU, then the output layer
+        float s = 0.0f;
+#pragma unroll 1
+        for (int c0 = 0; c0 < PR_H; c0 += 32) {
+            float v[32];
+            tc_ld32(d2 + lane_base + c0, v);
+#pragma unroll
+            for (int j = 0; j < 32; j++) s += sW3[c0 + j] * fmaxf(v[j] + sB2[c0 + j], 0.0f);
+        }
+        if (p < n_pairs) scores[p] = ok ? s + b3 : -INFINITY;
+        tc_before_sync();  // this tile's TMEM reads precede the next tile's MMAs
+    }
+    tc_before_sync();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(s_tmem), "r"(2 * PR_H) : "memory");
 }
 
 // Best k of each customer's pool by (score descending, node id ascending); one block per customer.
@@ -420,13 +519,23 @@ md_status score_pool(md_pruner *p, md_instance *inst, float *scores_d, cudaStrea
     AuxBuf aux;
     md_status r = aux.make(inst, st);
     if (r != MD_OK) return r;
-    const long long tiles = (n_pairs + 15) / 16;
-    const int grid = (int)((tiles + 3) / 4 < 148 * 8 ? (tiles + 3) / 4 : 148 * 8);
-    k_score<<<grid, 128, 0, st>>>(inst->d, inst->nbr, inst->nnbr, pool, aux.a, horizon_of(inst), p->w1h, p->w2h, p->P,
-                                  scores_d, n_pairs);
+    const long long tiles = (n_pairs + TC_ROWS - 1) / TC_ROWS;
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = (int)(tiles < 2LL * sms ? tiles : 2LL * sms);  // two CTAs (2 x 256 TMEM columns) per SM
+    MD_CUDA(cudaFuncSetAttribute(k_score_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
+    MD_CUDA(cudaMemsetAsync(p->err, 0, sizeof(int), st));
+    if (grid > 0)
+        k_score_tc<<<grid, TC_ROWS, TC_SMEM, st>>>(inst->d, inst->nbr, inst->nnbr, pool, aux.a, horizon_of(inst), p->w1h,
+                                                   p->w2h, p->P, scores_d, n_pairs, p->err);
     cudaError_t e = cudaGetLastError();
     aux.release(st);
-    if (e != cudaSuccess) return md_cuda_check(e, "k_score");
+    if (e != cudaSuccess) return md_cuda_check(e, "k_score_tc");
+    int herr = 0;
+    MD_CUDA(cudaMemcpyAsync(&herr, p->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    MD_CUDA(cudaStreamSynchronize(st));
+    if (herr) { md_set_error("pruner scoring: a wait for the tensor cores timed out"); return MD_ERR_TIMEOUT; }
     return MD_OK;
 }
 
@@ -445,6 +554,7 @@ extern "C" md_status md_pruner_create(const float *params, md_pruner **out) {
     MDP(cudaMalloc(&p->w1h, sizeof(__nv_bfloat16) * PR_H * PR_F));
     MDP(cudaMalloc(&p->w2h, sizeof(__nv_bfloat16) * PR_H * PR_H));
     MDP(cudaMalloc(&p->loss, sizeof(float) * 2));
+    MDP(cudaMalloc(&p->err, sizeof(int)));
     MDP(cudaMemcpy(p->P, params, sizeof(float) * PR_NPARAM, cudaMemcpyHostToDevice));
     MDP(cudaMemset(p->G, 0, sizeof(float) * PR_NPARAM));
     MDP(cudaMemset(p->M, 0, sizeof(float) * PR_NPARAM));
@@ -457,7 +567,7 @@ extern "C" md_status md_pruner_create(const float *params, md_pruner **out) {
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         cudaFree(p->P); cudaFree(p->G); cudaFree(p->M); cudaFree(p->V);
-        cudaFree(p->w1h); cudaFree(p->w2h); cudaFree(p->loss);
+        cudaFree(p->w1h); cudaFree(p->w2h); cudaFree(p->loss); cudaFree(p->err);
         free(p);
         return md_cuda_check(e, "md_pruner_create");
     }
@@ -468,7 +578,7 @@ extern "C" md_status md_pruner_create(const float *params, md_pruner **out) {
 extern "C" md_status md_pruner_destroy(md_pruner *p) {
     if (!p) return MD_OK;
     cudaFree(p->P); cudaFree(p->G); cudaFree(p->M); cudaFree(p->V);
-    cudaFree(p->w1h); cudaFree(p->w2h); cudaFree(p->loss);
+    cudaFree(p->w1h); cudaFree(p->w2h); cudaFree(p->loss); cudaFree(p->err);
     free(p);
     return MD_OK;
 }
