@@ -3,9 +3,9 @@
 // lists; every kept candidate is then evaluated exactly by the ordinary neighbourhood kernels, and
 // a periodic full sweep (md_config.sweep_every) catches what the lists miss.
 //
-// Model: 32 features -> 128 -> ReLU -> 128 -> ReLU -> 1 logit.  Inference runs on the tensor
-// cores (mma.sync m16n8k16, BF16 operands, FP32 accumulation): one warp scores 16 pairs, the
-// layer-1 accumulators are turned into the layer-2 A fragments in registers.  Training keeps FP32
+// Model: 32 features -> 128 -> ReLU -> 128 -> ReLU -> 1 logit.  Inference runs on the
+// 5th-generation tensor cores (tcgen05.mma kind::f16, BF16 operands from shared memory, FP32
+// accumulators in TMEM), 128 pairs per tile.  Training keeps FP32
 // master weights: hand-written forward/backward (binary cross-entropy with a positive-class
 // weight) with gradients accumulated per block, and an Adam update kernel.  The features depend
 // on the instance only (distance, rank, windows, service, demand, depot relations), so one
