@@ -40,11 +40,12 @@ THETA = 50
 # second route for 2-opt* and the depot operators); u-independent summaries are amortised.
 ALG_BYTES = {W.OP_RELOCATE: 8, W.OP_SWAP: 16, W.OP_TWO_OPT_STAR: 56, W.OP_DEPOT_INSERT: 32,
              W.OP_DEPOT_REPLACE: 32}
-# DRAM bytes (read + write) per k_eval launch of the default workload, averaged over 200
-# launches of `python bench.py --steps 1 --warmup 3 --no-cpu-baseline` under ncu
-# (dram__bytes_read.sum + dram__bytes_write.sum).  It describes the evaluation kernel as committed
-# with it; a change to that kernel makes it stale.
-EVAL_TRAFFIC_6X288 = 879995
+# DRAM bytes (read + write) per launch of the dominant kernel of the default workload, from ncu
+# (dram__bytes_read.sum + dram__bytes_write.sum) on `python bench.py --steps 1 --warmup 3
+# --no-cpu-baseline`: the persistent descent kernel (one launch per descent) and, for
+# --persistent 0, the evaluation kernel.  They describe the kernels as committed with them; a
+# change to a kernel makes its figure stale (None: not measured for the current kernel).
+TRAFFIC_6X288 = {"persistent": None, "eval": None}
 CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -225,10 +226,13 @@ def run_ours(args):
     perm_dev = torch.from_numpy(np.ascontiguousarray(perm)).to(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)  # > 126 MB L2
 
+    persistent = bool(args.persistent) if args.persistent >= 0 else True
+
     def step(time_eval=False):
         work.copy_from(init, stream=sptr)
         return work.descend(perm_dev.data_ptr(), MAX_PASS, multi=True, use_graph=True, poll_every=1,
-                            stream=sptr, n_ops=W.N_OPS, time_eval=time_eval, n_groups=args.groups)
+                            stream=sptr, n_ops=W.N_OPS, time_eval=time_eval, n_groups=args.groups,
+                            persistent=persistent)
 
     for _ in range(args.warmup):
         step()
@@ -255,7 +259,8 @@ def run_ours(args):
     value = moves_all / (total_ms_max / 1e3)
     descents = N_SOL * world * args.steps / (total_ms_max / 1e3)
 
-    # dominant kernel: the neighbourhood evaluation, timed live with events around each launch
+    # dominant kernel, timed live with CUDA events: the persistent descent kernel (evaluation and
+    # steps of all solutions, one launch per descent), else every evaluation launch
     eval_ms = sum(s.eval_ms for s in stats)
     eval_launches = sum(s.eval_launches for s in stats)
     by_op = np.sum([s.moves_by_op for s in stats], axis=0)
@@ -282,7 +287,7 @@ def run_ours(args):
         t0 = time.perf_counter()
         work.load_flat(h_nodes.numpy(), h_offs.numpy(), h_per.numpy(), stream=sptr)
         work.descend(h_perm, MAX_PASS, multi=True, use_graph=True, poll_every=1, stream=sptr,
-                     n_groups=args.groups)
+                     n_groups=args.groups, persistent=persistent)
         comps, F = work.cost(stream=sptr)
         e2e_ms.append(1e3 * (time.perf_counter() - t0))
     n_routes = int(per.sum())
@@ -305,18 +310,23 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32/f64", "data": "synthetic",
             "config": {"workload": workload_name(), "l2": "flushed between timed steps (256 MB write)",
-                       "route_slots": R, "k_max": K, "stream_groups": args.groups,
+                       "route_slots": R, "k_max": K,
+                       "launch": ("one persistent launch per descent" if persistent else
+                                  f"CUDA graph per pass, {args.groups} concurrent solution groups"),
                        "parallelism": f"{world} independent replicas"},
             "descents_per_s": descents,
             "moves_per_step": moves / args.steps,
             "passes_max": last.passes_max, "steps_per_descent": last.steps / N_SOL,
-            "roofline": {"kernel": "k_eval (neighbourhood evaluation)", "bound": "hbm",
+            "roofline": {"kernel": ("k_descend_persistent (evaluation and steps, one launch per descent)"
+                                    if persistent else "k_eval (neighbourhood evaluation)"),
+                         "bound": "hbm",
                          "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                         "peak_source": peak_src, "traffic": EVAL_TRAFFIC_6X288,
-                         "eval_ms_per_launch": eval_ms / max(eval_launches, 1),
+                         "peak_source": peak_src,
+                         "traffic": TRAFFIC_6X288["persistent" if persistent else "eval"],
+                         "ms_per_launch": eval_ms / max(eval_launches, 1),
                          "alg_bytes_per_launch": alg_bytes / max(eval_launches, 1),
-                         "eval_ms_summed_per_step": eval_ms / args.steps,
-                         "note": "launch times summed over the concurrent solution groups"},
+                         "note": ("the launch also runs the steps (selection, apply, rebuild)" if persistent
+                                  else "launch times summed over the concurrent solution groups")},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": statistics.mean(e2e_ms)},
@@ -494,7 +504,8 @@ def run_learned(args):
             work.copy_from(init, stream=sptr)
             return work.descend(perm_dev.data_ptr(), max_pass, multi=True, use_graph=True,
                                 poll_every=1, stream=sptr, n_ops=W.N_OPS, time_eval=te,
-                                n_groups=args.groups, sweep_every=sweep)
+                                n_groups=args.groups, sweep_every=sweep,
+                                persistent=args.persistent > 0)
         for _ in range(warmup):
             one(max_pass=MAX_PASS if sweep else 2)
         torch.cuda.synchronize()
@@ -551,7 +562,8 @@ def run_learned(args):
         t0 = time.perf_counter()
         work_l.load_flat(nodes, offs, per, stream=sptr)
         work_l.descend(h_perm, MAX_PASS, multi=True, use_graph=True, poll_every=1, stream=sptr,
-                       n_groups=args.groups, sweep_every=LEARNED_SWEEP)
+                       n_groups=args.groups, sweep_every=LEARNED_SWEEP,
+                       persistent=args.persistent > 0)
         comps, F = work_l.cost(stream=sptr)
         e2e_ms.append(1e3 * (time.perf_counter() - t0))
     h2d = nodes.nbytes + 16 * int(per.sum()) + h_perm.nbytes
@@ -634,7 +646,7 @@ def run_plain_large(args):
     def one(te=False):
         work.copy_from(init, stream=sptr)
         return work.descend(perm_dev.data_ptr(), max_pass, multi=True, use_graph=True, poll_every=1,
-                            stream=sptr, n_ops=W.N_OPS, time_eval=te, n_groups=args.groups)
+                            stream=sptr, n_ops=W.N_OPS, time_eval=te, n_groups=args.groups, persistent=args.persistent > 0)
     for _ in range(args.warmup):
         one()
     torch.cuda.synchronize()
@@ -693,6 +705,10 @@ def main():
                     help="timed plain full-neighbourhood descents beside the learned workload")
     ap.add_argument("--max-pass", type=int, default=None,
                     help="passes per step: batch16-uneven 4, plain-20x10000 500 (to the local optimum)")
+    ap.add_argument("--persistent", type=int, default=-1,
+                    help="1: each descent in one persistent launch (device-side task queue); 0: a CUDA "
+                         "graph per pass with concurrent solution groups; -1 (default): 1 for "
+                         "mdvrptw-6x288, 0 for the 20x10000 workloads")
     ap.add_argument("--groups", type=int, default=4,
                     help="solution groups advancing on concurrent streams inside the graph")
     args = ap.parse_args()

@@ -308,6 +308,29 @@ md_status md_descend_prepare(md_solutions *s, const md_config *cfg, const uint8_
     return MD_OK;
 }
 
+// Totals of the per-solution counters of the last descent into *out (if not NULL).
+static md_status descend_stats(md_solutions *s, md_stats *out, long long launches, long long eval_launches,
+                               double eval_ms, cudaStream_t st) {
+    if (!out) return MD_OK;
+    std::vector<long long> h((size_t)s->n_sol * 16);
+    MD_CUDA(cudaMemcpyAsync(h.data(), s->d.stats, sizeof(long long) * 16 * s->n_sol, cudaMemcpyDeviceToHost, st));
+    MD_CUDA(cudaStreamSynchronize(st));
+    memset(out, 0, sizeof(*out));
+    for (int i = 0; i < s->n_sol; i++) {
+        const long long *x = &h[(size_t)i * 16];
+        out->moves_scored += x[0];
+        out->steps += x[1];
+        out->accepted_steps += x[2];
+        out->applied_moves += x[3];
+        if (x[4] > out->passes_max) out->passes_max = x[4];
+        for (int o = 0; o < MD_N_OPS; o++) out->moves_by_op[o] += x[8 + o];
+    }
+    out->launches = launches;
+    out->eval_launches = eval_launches;
+    out->eval_ms = eval_ms;
+    return MD_OK;
+}
+
 extern "C" md_status md_descend(md_solutions *s, const md_config *cfg, md_stats *out, void *stream) {
     if (!s || !cfg || !cfg->op_perm) { md_set_error("md_descend: null argument"); return MD_ERR_ARG; }
     if (cfg->n_ops < 1 || cfg->n_ops > MD_MAX_OPS || cfg->max_pass < 1) {
@@ -324,6 +347,23 @@ extern "C" md_status md_descend(md_solutions *s, const md_config *cfg, md_stats 
     if (r != MD_OK) return r;
     md_moves *m = s->scratch;
     const uint32_t eflags = cfg->multi_move ? MD_EVAL_FOLLOWERS : 0u;
+    if (cfg->persistent) {
+        if (!st) { md_set_error("md_descend: the persistent descent needs a stream"); return MD_ERR_ARG; }
+        float ms = 0.0f;
+        r = md_descend_persistent(s, m, eflags, cfg->max_pass * cfg->n_ops, st, cfg->time_eval != 0, &ms);
+        if (r != MD_OK) return r;
+        r = check_err(s, st);
+        if (r != MD_OK) return r;
+        std::vector<int32_t> stt((size_t)s->n_sol * MD_STATE);
+        MD_CUDA(cudaMemcpyAsync(stt.data(), s->d.state, sizeof(int32_t) * MD_STATE * s->n_sol, cudaMemcpyDeviceToHost, st));
+        MD_CUDA(cudaStreamSynchronize(st));
+        for (int i = 0; i < s->n_sol; i++)
+            if (stt[(size_t)i * MD_STATE + 3] == 0) {
+                md_set_error("md_descend: solutions still running after max_pass passes");
+                return MD_ERR_STATE;
+            }
+        return descend_stats(s, out, launches + 1, 1, ms, st);
+    }
     const int poll = cfg->poll_every > 0 ? cfg->poll_every : 1;
     const int steps_per_poll = cfg->n_ops * poll;
     // Solutions are independent: with n_groups > 1 they advance in groups on concurrent streams
@@ -440,23 +480,5 @@ extern "C" md_status md_descend(md_solutions *s, const md_config *cfg, md_stats 
     r = check_err(s, st);
     if (r != MD_OK) return r;
     if (!all_done) { md_set_error("md_descend: solutions still running after max_pass passes"); return MD_ERR_STATE; }
-    if (out) {
-        std::vector<long long> h((size_t)s->n_sol * 16);
-        MD_CUDA(cudaMemcpyAsync(h.data(), s->d.stats, sizeof(long long) * 16 * s->n_sol, cudaMemcpyDeviceToHost, st));
-        MD_CUDA(cudaStreamSynchronize(st));
-        memset(out, 0, sizeof(*out));
-        for (int i = 0; i < s->n_sol; i++) {
-            const long long *x = &h[(size_t)i * 16];
-            out->moves_scored += x[0];
-            out->steps += x[1];
-            out->accepted_steps += x[2];
-            out->applied_moves += x[3];
-            if (x[4] > out->passes_max) out->passes_max = x[4];
-            for (int o = 0; o < MD_N_OPS; o++) out->moves_by_op[o] += x[8 + o];
-        }
-        out->launches = launches;
-        out->eval_launches = eval_launches;
-        out->eval_ms = eval_ms;
-    }
-    return MD_OK;
+    return descend_stats(s, out, launches, eval_launches, eval_ms, st);
 }

@@ -1,0 +1,695 @@
+// eval_core.cuh -- neighbourhood evaluation of Relocate, Swap, 2-opt*, Depot-Insert and Depot-Replace
+// (Section 3.2.2) under the multi-penalty function F (Eq. 2 / Eq. A1), for many solutions at
+// once, with the per-solution leader and the per-route-pair best follower (Section 3.2.5).
+//
+// Device code shared by the evaluation kernels (eval.cu) and the persistent descent kernel
+// (persist.cu).  One warp owns a customer u
+// (everything that depends on u only -- its route, the route left after removing seq(u), the
+// 1- and 2-node sequences -- is computed once per warp) and its 32 lanes walk u's candidate
+// list v.  An inter-route move costs O(1): two or four concatenations of prefix/suffix
+// summaries gathered by customer id.  An intra-route move (u and v on one route) takes the
+// prefix before and the suffix after the rearranged part from the same summaries and the
+// customers strictly between u's and v's sequences from the route's subsequence tables, so it
+// costs O(1) as well.
+//
+// The FP64 penalised delta dF is needed only for the leader (Section 3.2.5): a move whose
+// integer deltas make dF >= 0 certain, or whose FP32 estimate (with a margin ten times its
+// rounding bound) is above the lane's best dF so far, cannot be the leader and skips FP64.  B300
+// runs FP64 at a small fraction of its integer rate.  Every warp writes its own leader
+// candidate, so no warp waits for the others of its block.
+//
+// Solution data (summaries, routes, weights) is read with coherent loads: in the persistent
+// descent a block may evaluate summaries that another block's step rewrote in the same launch.
+// Instance data (distances, nodes, neighbour lists) is read-only and goes through __ldg.
+#pragma once
+
+#include "mdls_internal.cuh"
+
+#ifndef MD_EVAL_WPC_MAX
+// Warps per evaluated customer when every customer is a candidate (no lists, or a full-sweep
+// step): each takes every wpc-th batch of 32 candidates, which shortens a warp's chain of
+// dependent gathers; wpc = min(MD_EVAL_WPC_MAX, nc / 256).  Granular lists keep one warp per
+// customer (the per-customer work would be duplicated for a few dozen candidates).
+#define MD_EVAL_WPC_MAX 8
+#endif
+
+#ifndef MD_EVAL_MIN_BLOCKS
+// evaluation blocks resident per SM: 16 warps per SM, a register budget of 128 per thread
+#define MD_EVAL_MIN_BLOCKS (16 / MD_EVAL_WARPS)
+#endif
+
+namespace {
+
+struct RT {  // the four integer terms of one route (Eq. A1)
+    int dist, tw, lex, dex;
+};
+
+struct Best {
+    double f;         // exact FP64 dF of the best move, once formed (fx)
+    uint32_t id;
+    int valid;
+    int fx;
+    int dD, dT, dL, dU, dV;  // integer deltas of the best move
+    float lo, hi;     // lo <= dF(best) <= hi
+    uint32_t routes;  // rA | rB << 16 of the best move
+    unsigned long long n;
+};
+
+struct Ctx {
+    DevInst I;
+    DevSols D;
+    DevMoves M;
+    uint32_t flags;
+    int s;
+    const double *w;   // FP64 weights of the solution (shared memory)
+    const float *wf;   // the same rounded to FP32, for the brackets
+    bool open, sym;
+    bool lists;  // candidates from the neighbour lists (theta > 0 and not a full-sweep step)
+};
+
+__device__ __forceinline__ int cost(const DevInst &I, int a, int b) {
+    return __ldg(&I.dist[(size_t)a * I.nn + b]);
+}
+
+// c(a, b) read from row b.  The matrix is symmetric (Euclidean, Eq. 1), so every arc is read
+// from the row of the node that is the same for all lanes of the warp (u and the nodes of its
+// route): a warp's reads then fall in one row, contiguous when the candidates are consecutive.
+__device__ __forceinline__ int cost_t(const DevInst &I, int a, int b) {
+    return __ldg(&I.dist[(size_t)b * I.nn + a]);
+}
+
+__device__ __forceinline__ RT rt_of(const Seg &g, const DevInst &I) {
+    RT r;
+    r.dist = g.dist;
+    r.tw = g.tw;
+    r.lex = load_ex(g.load, I.Q);
+    r.dex = dur_ex(g.dur, I.D);
+    return r;
+}
+
+__device__ __forceinline__ RT rt_zero() {
+    RT r;
+    r.dist = 0; r.tw = 0; r.lex = 0; r.dex = 0;
+    return r;
+}
+
+__device__ __forceinline__ Seg8 pre8(const Ctx &C, int n) {
+    return ld_seg8(&C.D.cpre[(size_t)C.s * C.I.nc + (n - C.I.nd)]);
+}
+
+__device__ __forceinline__ Seg8 suf8(const Ctx &C, int n) {
+    return ld_seg8(&C.D.csuf[(size_t)C.s * C.I.nc + (n - C.I.nd)]);
+}
+
+__device__ __forceinline__ Seg nseg(const Ctx &C, int n) { return node_seg(__ldg(&C.I.node[n])); }
+
+// Summary of the route up to and including node n (n may be the route's departure depot).
+__device__ __forceinline__ Seg prefix_through(const Ctx &C, int n) {
+    return n < C.I.nd ? nseg(C, n) : seg_of(pre8(C, n));
+}
+
+// Summary of the route from node n to its end (n may be the arrival depot); n = MD_NONE is the
+// empty sequence after the last customer of an open route.
+__device__ __forceinline__ Seg suffix_from(const Ctx &C, int n) {
+    return n < C.I.nd ? nseg(C, n) : seg_of(suf8(C, n));
+}
+
+template <bool TW>
+__device__ __forceinline__ Seg join(const Ctx &C, const Seg &a, int a_last, const Seg &b, int b_first) {
+    return seg_cat<TW>(a, b, cost(C.I, a_last, b_first));
+}
+
+// join with the arc read from row b_first (b_first is the warp-uniform end)
+template <bool TW>
+__device__ __forceinline__ Seg join_t(const Ctx &C, const Seg &a, int a_last, const Seg &b, int b_first) {
+    return seg_cat<TW>(a, b, cost_t(C.I, a_last, b_first));
+}
+
+// head + tail, where tail_first = MD_NONE means there is no tail.
+template <bool TW>
+__device__ __forceinline__ Seg join_opt(const Ctx &C, const Seg &a, int a_last, int tail_first) {
+    if (tail_first == MD_NONE) return a;
+    return join<TW>(C, a, a_last, suffix_from(C, tail_first), tail_first);
+}
+
+template <bool TW>
+__device__ __forceinline__ Seg join_opt_t(const Ctx &C, const Seg &a, int a_last, int tail_first) {
+    if (tail_first == MD_NONE) return a;
+    return join_t<TW>(C, a, a_last, suffix_from(C, tail_first), tail_first);
+}
+
+// Records one scored move: follower table, leader candidate of the lane, dump.  f_in is the FP64
+// dF when the caller already has it (have_f), otherwise it is computed here only if needed.
+__device__ __forceinline__ void offer(const Ctx &C, uint32_t id, int dD, int dTW, int dL, int dU, int dV,
+                                      int rA, int rB, Best &b, bool count, bool have_f, double f_in) {
+    if (count) b.n++;
+    const bool pen = (dTW | dL | dU | dV) != 0;
+    if ((C.flags & MD_EVAL_FOLLOWERS) && dD < 0 && !pen) {
+        const int lo = min(rA, rB), hi = max(rA, rB);
+        const unsigned long long key = ((unsigned long long)((uint32_t)dD ^ 0x80000000u) << 32) | id;
+        const uint32_t pair = (uint32_t)lo * (uint32_t)C.D.R + (uint32_t)hi;
+        const unsigned long long old = atomicMin(&C.M.foltab[(size_t)C.s * C.D.R * C.D.R + pair], key);
+        if (old == MD_EMPTY_KEY) {  // first follower of this route pair: list the pair once
+            const uint32_t k = atomicAdd(&C.M.fcount[C.s], 1u);
+            if (k < (uint32_t)C.M.ncap) C.M.flist[(size_t)C.s * C.M.ncap + k] = pair;
+            else atomicCAS(C.D.err, 0, (int)MD_ERR_CAPACITY);
+        }
+    }
+    // Leader candidate.  dF is bracketed by [lo, hi]; the exact FP64 value of a move (and of the
+    // lane's best) is formed only when the brackets cannot order them, so most comparisons need
+    // no FP64 arithmetic.  The dump records every move with its exact dF.
+    const bool dump = (C.flags & MD_EVAL_DUMP) != 0;
+    double f = 0.0;
+    bool fx = false;
+    float lo, hi;
+    if (have_f || dump) {
+        f = have_f ? f_in : combine_df(C.w, dD, dTW, dL, dU, dV);
+        fx = true;
+        lo = __double2float_rd(f);
+        hi = __double2float_ru(f);
+    } else if (!pen) {
+        if (dD >= 0) return;
+        lo = __int2float_rd(dD);
+        hi = __int2float_ru(dD);
+    } else {
+        if (dD >= 0 && dTW >= 0 && dL >= 0 && dU >= 0 && dV >= 0) return;  // dF >= 0: never a leader
+        const float est = __fmaf_rn(C.wf[3], (float)dV, __fmaf_rn(C.wf[2], (float)dU,
+                          __fmaf_rn(C.wf[1], (float)dL, __fmaf_rn(C.wf[0], (float)dTW, (float)dD))));
+        const float mag = fabsf((float)dD) + C.wf[0] * fabsf((float)dTW) + C.wf[1] * fabsf((float)dL) +
+                          C.wf[2] * fabsf((float)dU) + C.wf[3] * fabsf((float)dV);
+        const float m = 4e-6f * mag;  // at least nine times the estimate's rounding bound
+        lo = est - m;
+        hi = est + m;
+        if (lo >= 0.0f) return;  // dF >= 0 for certain
+    }
+    bool take;
+    if (b.valid && lo > b.hi) {
+        take = false;  // dF > dF(best) for certain
+    } else if (b.valid ? hi < b.lo : hi < 0.0f) {
+        take = true;   // dF < dF(best) (or < 0 without a best) for certain
+    } else if (b.valid && dD == b.dD && dTW == b.dT && dL == b.dL && dU == b.dU && dV == b.dV) {
+        take = id < b.id;  // the same deltas: the same dF
+    } else {
+        if (!fx) {
+            f = combine_df(C.w, dD, dTW, dL, dU, dV);
+            fx = true;
+        }
+        if (!b.valid) {
+            take = f < 0.0;
+        } else {
+            if (!b.fx) {
+                b.f = combine_df(C.w, b.dD, b.dT, b.dL, b.dU, b.dV);
+                b.fx = 1;
+            }
+            take = f < b.f || (f == b.f && id < b.id);
+        }
+    }
+    if (take && (fx ? f < 0.0 : true)) {
+        b.valid = 1;
+        b.id = id;
+        b.routes = (uint32_t)rA | ((uint32_t)rB << 16);
+        b.dD = dD; b.dT = dTW; b.dL = dL; b.dU = dU; b.dV = dV;
+        b.lo = lo;
+        b.hi = hi;
+        b.fx = fx;
+        b.f = f;
+    }
+    if (dump) {
+        const unsigned long long k = atomicAdd(C.M.dump_n, 1ull);
+        if ((long long)k < C.M.dump_cap) {
+            md_move m;
+            m.id = ((uint64_t)(C.D.ops[C.s] & MD_OP_MASK) << 32) | id;
+            m.dD = dD; m.dTW = dTW; m.dLoad = dL; m.dDur = dU; m.dV4 = dV;
+            m.dF = f;
+            m.sol = C.s;
+            m.pad = 0;
+            C.M.dump[k] = m;
+        }
+    }
+}
+
+__device__ __forceinline__ void sink(const Ctx &C, uint32_t id, int dD, int dTW, int dL, int dU, int dV,
+                                     int rA, int rB, Best &b) {
+    offer(C, id, dD, dTW, dL, dU, dV, rA, rB, b, true, false, 0.0);
+}
+
+// A summary with its end nodes; e marks the empty sequence.
+struct SN {
+    Seg s;
+    int f, l;
+    bool e;
+};
+
+__device__ __forceinline__ SN sn(const Seg &g, int f, int l) {
+    SN r;
+    r.s = g; r.f = f; r.l = l; r.e = false;
+    return r;
+}
+
+__device__ __forceinline__ SN sn_none() {
+    SN r;
+    r.s = Seg{0, 0, 0, 0, 0, MD_NO_LATE};
+    r.f = -1; r.l = -1; r.e = true;
+    return r;
+}
+
+template <bool TW>
+__device__ __forceinline__ SN sn_cat(const Ctx &C, const SN &a, const SN &b) {
+    if (a.e) return b;
+    if (b.e) return a;
+    return sn(seg_cat<TW>(a.s, b.s, cost(C.I, a.l, b.f)), a.f, b.l);
+}
+
+template <bool TW>
+__device__ __forceinline__ SN sn_cat_t(const Ctx &C, const SN &a, const SN &b) {
+    if (a.e) return b;
+    if (b.e) return a;
+    return sn(seg_cat<TW>(a.s, b.s, cost_t(C.I, a.l, b.f)), a.f, b.l);
+}
+
+// Summary of the route from node n to its end as an SN (empty after an open route's last customer).
+__device__ __forceinline__ SN sn_suffix(const Ctx &C, int n) {
+    return n == MD_NONE ? sn_none() : sn(suffix_from(C, n), n, n);
+}
+
+// The customers from c's position to t positions later (sub_fwd) or earlier (sub_bwd) on c's
+// route, from the subsequence tables the route rebuild keeps.
+__device__ __forceinline__ SN sub_fwd(const Ctx &C, int c, int t) {
+    const Seg8 e = ld_seg8(&C.D.csubf[((size_t)C.s * C.I.nc + (c - C.I.nd)) * C.D.K + t]);
+    return sn(seg_of(e), e.a, e.b);
+}
+
+__device__ __forceinline__ SN sub_bwd(const Ctx &C, int c, int t) {
+    const Seg8 e = ld_seg8(&C.D.csubb[((size_t)C.s * C.I.nc + (c - C.I.nd)) * C.D.K + t]);
+    return sn(seg_of(e), e.a, e.b);
+}
+
+// Candidates i0 .. i0 + 63 of customer u (node ids; v = u left out) into the warp's list wl[64]:
+// those on another route than u's route A at the front (ni of them), those on A (when
+// want_intra) at the back (na), so that the warp can run each kind in passes of its own instead
+// of taking both paths in every pass.  Called by all 32 lanes.
+__device__ __forceinline__ void split_candidates(const Ctx &C, int cu, int u, int A, int lane, int *wl,
+                                                 bool want_intra, int i0, int ncand, int nb, int &ni, int &na) {
+    const DevInst &I = C.I;
+    const unsigned lt = (1u << lane) - 1u;
+    ni = 0;
+    na = 0;
+    for (int h = 0; h < nb; h += 32) {
+        const int i = i0 + h + lane;
+        bool inter = false, intra = false;
+        int v = 0;
+        if (i < ncand) {
+            v = C.lists ? __ldg(&I.nbr[(size_t)cu * I.theta + i]) : I.nd + i;
+            if (v != u) {
+                const int B = C.D.cpre[(size_t)C.s * I.nc + (v - I.nd)].a;
+                inter = B != A;
+                intra = want_intra && B == A;
+            }
+        }
+        const unsigned mi = __ballot_sync(0xffffffffu, inter), ma = __ballot_sync(0xffffffffu, intra);
+        if (inter) wl[ni + __popc(mi & lt)] = v;
+        if (intra) wl[63 - na - __popc(ma & lt)] = v;
+        ni += __popc(mi);
+        na += __popc(ma);
+    }
+    __syncwarp();
+}
+
+// ------------------------------------------------------------------------------------------
+// Relocate: seq(u) (1 or 2 nodes, possibly reversed) after v, or before v when v is first.
+// ------------------------------------------------------------------------------------------
+template <bool TW>
+__device__ void eval_relocate(const Ctx &C, int cu, int lane, Best &b, int *wl, int part, int wpc) {
+    const DevInst &I = C.I;
+    const int u = I.nd + cu;
+    const Seg8 Pu = pre8(C, u), Su = suf8(C, u);
+    const int A = Pu.a, p = Pu.b, pu = Su.a, su = Su.b;
+    const size_t sA = (size_t)C.s * C.D.R + A;
+    const int4 hA = C.D.rhdr[sA];
+    const int LA = hA.x, dsA = hA.y, deA = hA.z;
+    const RT oldA = rt_of(seg_of(ld_seg8(&C.D.rterm[sA])), I);
+    const Seg PP = prefix_through(C, pu);
+    // route A without seq(u)
+    const RT A1 = LA == 1 ? rt_zero() : rt_of(join_opt<TW>(C, PP, pu, su), I);
+    const bool has2 = su >= I.nd;
+    const int x = has2 ? su : -1;
+    const int sx = has2 ? suf8(C, x).b : MD_NONE;
+    RT A2 = rt_zero();
+    Seg q2, q2r;
+    if (has2) {
+        if (LA > 2) A2 = rt_of(join_opt<TW>(C, PP, pu, sx), I);
+        q2 = join<TW>(C, nseg(C, u), u, nseg(C, x), x);
+        q2r = join<TW>(C, nseg(C, x), x, nseg(C, u), u);
+    }
+    const Seg q1 = nseg(C, u);
+    const int dV_empty = ((!C.open && dsA != deA) ? -1 : 0) +
+                         veh_delta(C.D.dcount[(size_t)C.s * I.nd + dsA], I.NV, -1);
+    const int ncand = C.lists ? I.nnbr[cu] : I.nc;
+    // batches of 64 candidates, or of 32 when wpc warps share the customer: warp part takes
+    // every wpc-th batch
+    const int nb = wpc == 1 ? 64 : 32;
+    for (int i0 = part * nb; i0 < ncand; i0 += nb * wpc) {
+        int ni, na;
+        split_candidates(C, cu, u, A, lane, wl, true, i0, ncand, nb, ni, na);
+        const int ni_pad = (ni + 31) & ~31;  // passes run inter-route or intra-route candidates only
+        for (int k = lane; k < ni_pad + na; k += 32) {
+            const int v = k < ni ? wl[k] : (k >= ni_pad ? wl[63 - (k - ni_pad)] : -1);
+            if (v < 0) continue;
+            const Seg8 Pv = pre8(C, v), Sv = suf8(C, v);
+            const int B = Pv.a, j = Pv.b, sv = Sv.b;
+            if (B == A) {
+                // intra-route: prefix before and suffix after the rearranged part, the customers
+                // between them from the subsequence tables
+                for (int var = 0; var < 6; var++) {
+                    const int k = var >= 2 ? 2 : 1;
+                    const bool rev = var >= 4, before = var & 1;
+                    if (rev && !C.sym) continue;
+                    if (k == 2 && !has2) continue;
+                    if (k == 2 && v == x) continue;
+                    if (before && j != 1) continue;
+                    if (!before && !rev && j == p - 1) continue;  // already right after v
+                    const int at = before ? 0 : j;  // seq(u) goes right after this position
+                    const SN q = k == 1 ? sn(q1, u, u) : (rev ? sn(q2r, x, u) : sn(q2, u, x));
+                    SN g;
+                    if (at < p) {
+                        const SN head = at == 0 ? sn(nseg(C, dsA), dsA, dsA) : sn(seg_of(Pv), dsA, v);
+                        const SN mid = at + 1 <= p - 1 ? sub_bwd(C, pu, p - 2 - at) : sn_none();  // at+1..p-1
+                        g = sn_cat<TW>(C, sn_cat<TW>(C, sn_cat_t<TW>(C, head, q), mid), sn_suffix(C, k == 1 ? su : sx));
+                    } else {
+                        const SN mid = sub_fwd(C, k == 1 ? su : sx, at - p - k);  // p+k..at
+                        g = sn_cat<TW>(C, sn_cat_t<TW>(C, sn_cat<TW>(C, sn(PP, dsA, pu), mid), q), sn_suffix(C, sv));
+                    }
+                    const RT nA = rt_of(g.s, I);
+                    sink(C, make_id32(u, v, var), nA.dist - oldA.dist, nA.tw - oldA.tw, nA.lex - oldA.lex,
+                         nA.dex - oldA.dex, 0, A, A, b);
+                }
+                continue;
+            }
+            const size_t sB = (size_t)C.s * C.D.R + B;
+            const int dsB = C.D.rhdr[sB].y;
+            const RT oldB = rt_of(seg_of(ld_seg8(&C.D.rterm[sB])), I);
+            const Seg PV = seg_of(Pv);
+            const bool vfirst = j == 1;
+            for (int var = 0; var < 6; var++) {
+                const int k = var >= 2 ? 2 : 1;
+                const bool rev = var >= 4, before = var & 1;
+                if (rev && !C.sym) continue;
+                if (k == 2 && !has2) continue;
+                if (before && !vfirst) continue;
+                const Seg &q = k == 1 ? q1 : (rev ? q2r : q2);
+                const int qf = k == 1 ? u : (rev ? x : u);
+                const int ql = k == 1 ? u : (rev ? u : x);
+                Seg nb;
+                if (before) {
+                    nb = join_t<TW>(C, nseg(C, dsB), dsB, q, qf);
+                    nb = join<TW>(C, nb, ql, seg_of(Sv), v);
+                } else {
+                    nb = join_t<TW>(C, PV, v, q, qf);
+                    nb = join_opt<TW>(C, nb, ql, sv);
+                }
+                const RT nB = rt_of(nb, I);
+                const RT nA = k == 1 ? A1 : A2;
+                const bool emp = LA == k;
+                sink(C, make_id32(u, v, var), nA.dist + nB.dist - oldA.dist - oldB.dist,
+                     nA.tw + nB.tw - oldA.tw - oldB.tw, nA.lex + nB.lex - oldA.lex - oldB.lex,
+                     nA.dex + nB.dex - oldA.dex - oldB.dex, emp ? dV_empty : 0, A, B, b);
+            }
+        }
+        __syncwarp();  // the list is read before the next batch overwrites it
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Swap: seq(u) and seq(v) exchange places (1 or 2 nodes each, reversible when symmetric).
+// ------------------------------------------------------------------------------------------
+__device__ __constant__ int SW_KU[9] = {1, 2, 1, 2, 2, 1, 2, 2, 2};
+__device__ __constant__ int SW_KV[9] = {1, 1, 2, 2, 1, 2, 2, 2, 2};
+__device__ __constant__ int SW_RU[9] = {0, 0, 0, 0, 1, 0, 1, 0, 1};
+__device__ __constant__ int SW_RV[9] = {0, 0, 0, 0, 0, 1, 0, 1, 1};
+
+template <bool TW>
+__device__ void eval_swap(const Ctx &C, int cu, int lane, Best &b, int *wl, int part, int wpc) {
+    const DevInst &I = C.I;
+    const int u = I.nd + cu;
+    const Seg8 Pu = pre8(C, u), Su = suf8(C, u);
+    const int A = Pu.a, p = Pu.b, pu = Su.a, su = Su.b;
+    const size_t sA = (size_t)C.s * C.D.R + A;
+    const int4 hA = C.D.rhdr[sA];
+    const int dsA = hA.y;
+    const RT oldA = rt_of(seg_of(ld_seg8(&C.D.rterm[sA])), I);
+    const Seg PU = prefix_through(C, pu);
+    const bool hasx = su >= I.nd;
+    const int x = hasx ? su : -1;
+    const int sx = hasx ? suf8(C, x).b : MD_NONE;
+    Seg u1 = nseg(C, u), u2, u2r;
+    if (hasx) {
+        u2 = join<TW>(C, nseg(C, u), u, nseg(C, x), x);
+        u2r = join<TW>(C, nseg(C, x), x, nseg(C, u), u);
+    }
+    const int nvar = C.sym ? 9 : 4;
+    const int ncand = C.lists ? I.nnbr[cu] : I.nc;
+    // batches of 64 candidates, or of 32 when wpc warps share the customer: warp part takes
+    // every wpc-th batch
+    const int nb = wpc == 1 ? 64 : 32;
+    for (int i0 = part * nb; i0 < ncand; i0 += nb * wpc) {
+        int ni, na;
+        split_candidates(C, cu, u, A, lane, wl, true, i0, ncand, nb, ni, na);
+        const int ni_pad = (ni + 31) & ~31;  // passes run inter-route or intra-route candidates only
+        for (int k = lane; k < ni_pad + na; k += 32) {
+            const int v = k < ni ? wl[k] : (k >= ni_pad ? wl[63 - (k - ni_pad)] : -1);
+            if (v < 0) continue;
+            const Seg8 Pv = pre8(C, v), Sv = suf8(C, v);
+            const int B = Pv.a, j = Pv.b, pv = Sv.a, sv = Sv.b;
+            const bool hasy = sv >= I.nd;
+            const int y = hasy ? sv : -1;
+            const int sy = hasy ? suf8(C, y).b : MD_NONE;
+            Seg v1 = nseg(C, v), v2, v2r;
+            if (hasy) {
+                v2 = join<TW>(C, nseg(C, v), v, nseg(C, y), y);
+                v2r = join<TW>(C, nseg(C, y), y, nseg(C, v), v);
+            }
+            if (B == A) {
+                // intra-route: prefix, one sequence, the customers between them, the other sequence, suffix
+                for (int var = 0; var < nvar; var++) {
+                    const int ku = SW_KU[var], kv = SW_KV[var];
+                    const bool ru = SW_RU[var], rvv = SW_RV[var];
+                    if ((ku == 2 && !hasx) || (kv == 2 && !hasy)) continue;
+                    if (!(p + ku - 1 < j || j + kv - 1 < p)) continue;  // overlapping sequences
+                    const SN qv = kv == 1 ? sn(v1, v, v) : (rvv ? sn(v2r, y, v) : sn(v2, v, y));
+                    const SN qu = ku == 1 ? sn(u1, u, u) : (ru ? sn(u2r, x, u) : sn(u2, u, x));
+                    SN g;
+                    if (p < j) {
+                        const SN mid = p + ku <= j - 1 ? sub_fwd(C, ku == 1 ? su : sx, j - 1 - p - ku) : sn_none();
+                        g = sn_cat<TW>(C, sn(PU, dsA, pu), qv);
+                        g = sn_cat<TW>(C, sn_cat_t<TW>(C, sn_cat_t<TW>(C, g, mid), qu), sn_suffix(C, kv == 1 ? sv : sy));
+                    } else {
+                        const SN mid = j + kv <= p - 1 ? sub_bwd(C, pu, p - 1 - j - kv) : sn_none();
+                        g = sn_cat_t<TW>(C, sn(prefix_through(C, pv), dsA, pv), qu);
+                        g = sn_cat_t<TW>(C, sn_cat<TW>(C, sn_cat<TW>(C, g, mid), qv), sn_suffix(C, ku == 1 ? su : sx));
+                    }
+                    const RT nA = rt_of(g.s, I);
+                    sink(C, make_id32(u, v, var), nA.dist - oldA.dist, nA.tw - oldA.tw, nA.lex - oldA.lex,
+                         nA.dex - oldA.dex, 0, A, A, b);
+                }
+                continue;
+            }
+            const size_t sB = (size_t)C.s * C.D.R + B;
+            const RT oldB = rt_of(seg_of(ld_seg8(&C.D.rterm[sB])), I);
+            const Seg PV = prefix_through(C, pv);
+            for (int var = 0; var < nvar; var++) {
+                const int ku = SW_KU[var], kv = SW_KV[var];
+                const bool ru = SW_RU[var], rvv = SW_RV[var];
+                if ((ku == 2 && !hasx) || (kv == 2 && !hasy)) continue;
+                // sequence of v placed in A, sequence of u placed in B
+                const Seg &qv = kv == 1 ? v1 : (rvv ? v2r : v2);
+                const int qvf = kv == 1 ? v : (rvv ? y : v), qvl = kv == 1 ? v : (rvv ? v : y);
+                const Seg &qu = ku == 1 ? u1 : (ru ? u2r : u2);
+                const int quf = ku == 1 ? u : (ru ? x : u), qul = ku == 1 ? u : (ru ? u : x);
+                const int afterU = ku == 1 ? su : sx, afterV = kv == 1 ? sv : sy;
+                Seg na = join<TW>(C, PU, pu, qv, qvf);
+                na = join_opt_t<TW>(C, na, qvl, afterU);
+                Seg nb = join_t<TW>(C, PV, pv, qu, quf);
+                nb = join_opt<TW>(C, nb, qul, afterV);
+                const RT nA = rt_of(na, I), nB = rt_of(nb, I);
+                sink(C, make_id32(u, v, var), nA.dist + nB.dist - oldA.dist - oldB.dist,
+                     nA.tw + nB.tw - oldA.tw - oldB.tw, nA.lex + nB.lex - oldA.lex - oldB.lex,
+                     nA.dex + nB.dex - oldA.dex - oldB.dex, 0, A, B, b);
+            }
+        }
+        __syncwarp();  // the list is read before the next batch overwrites it
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// 2-opt*: [ds_A..u] + [v..de_B] and [ds_B..pred v] + [succ u..de_A].
+// ------------------------------------------------------------------------------------------
+template <bool TW>
+__device__ void eval_2optstar(const Ctx &C, int cu, int lane, Best &b, int *wl, int part, int wpc) {
+    const DevInst &I = C.I;
+    const int u = I.nd + cu;
+    const Seg8 Pu = pre8(C, u), Su = suf8(C, u);
+    const int A = Pu.a, su = Su.b;
+    const size_t sA = (size_t)C.s * C.D.R + A;
+    const int4 hA = C.D.rhdr[sA];
+    const int dsA = hA.y, deA = hA.z;
+    const RT oldA = rt_of(seg_of(ld_seg8(&C.D.rterm[sA])), I);
+    const Seg PU = seg_of(Pu);
+    const bool u_last = su < I.nd;  // depot or MD_NONE after u
+    const int ncand = C.lists ? I.nnbr[cu] : I.nc;
+    // batches of 64 candidates, or of 32 when wpc warps share the customer: warp part takes
+    // every wpc-th batch
+    const int nb = wpc == 1 ? 64 : 32;
+    for (int i0 = part * nb; i0 < ncand; i0 += nb * wpc) {
+        int ni, na;
+        split_candidates(C, cu, u, A, lane, wl, false, i0, ncand, nb, ni, na);
+        const int ni_pad = (ni + 31) & ~31;  // passes run inter-route or intra-route candidates only
+        for (int k = lane; k < ni_pad + na; k += 32) {
+            const int v = k < ni ? wl[k] : (k >= ni_pad ? wl[63 - (k - ni_pad)] : -1);
+            if (v < 0) continue;
+            const Seg8 Pv = pre8(C, v), Sv = suf8(C, v);
+            const int B = Pv.a, pv = Sv.a;
+            if (B == A) continue;
+            const size_t sB = (size_t)C.s * C.D.R + B;
+            const int4 hB = C.D.rhdr[sB];
+            const int dsB = hB.y, deB = hB.z;
+            const RT oldB = rt_of(seg_of(ld_seg8(&C.D.rterm[sB])), I);
+            const RT nA = rt_of(join<TW>(C, PU, u, seg_of(Sv), v), I);
+            const bool b_empty = pv < I.nd && u_last;
+            RT nB = rt_zero();
+            if (!b_empty) nB = rt_of(join_opt_t<TW>(C, prefix_through(C, pv), pv, su), I);
+            int dV = 0;
+            if (!C.open) {
+                dV += (dsA != deB) + (b_empty ? 0 : (dsB != deA)) - (dsA != deA) - (dsB != deB);
+            }
+            if (b_empty) dV += veh_delta(C.D.dcount[(size_t)C.s * I.nd + dsB], I.NV, -1);
+            sink(C, make_id32(u, v, 0), nA.dist + nB.dist - oldA.dist - oldB.dist, nA.tw + nB.tw - oldA.tw - oldB.tw,
+                 nA.lex + nB.lex - oldA.lex - oldB.lex, nA.dex + nB.dex - oldA.dex - oldB.dex, dV, A, B, b);
+        }
+        __syncwarp();  // the list is read before the next batch overwrites it
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Depot-Insert (Fig. 1a): split after u = c_k, k < L, at depot d: [ds..u, d] and [d, succ u..de].
+// ------------------------------------------------------------------------------------------
+template <bool TW>
+__device__ void eval_depot_insert(const Ctx &C, int cu, int lane, Best &b, int part) {
+    if (part != 0) return;
+    const DevInst &I = C.I;
+    const int u = I.nd + cu;
+    const Seg8 Pu = pre8(C, u), Su = suf8(C, u);
+    const int A = Pu.a, su = Su.b;
+    if (su < I.nd) return;  // u is last: only interior edges split a route
+    const size_t sA = (size_t)C.s * C.D.R + A;
+    const int4 hA = C.D.rhdr[sA];
+    const int dsA = hA.y, deA = hA.z;
+    const RT oldA = rt_of(seg_of(ld_seg8(&C.D.rterm[sA])), I);
+    const Seg PU = seg_of(Pu), SX = seg_of(suf8(C, su));
+    for (int d = lane; d < I.nd; d += 32) {
+        const Seg r1 = C.open ? PU : join<TW>(C, PU, u, nseg(C, d), d);
+        const Seg r2 = join_t<TW>(C, nseg(C, d), d, SX, su);
+        const RT n1 = rt_of(r1, I), n2 = rt_of(r2, I);
+        int dV = veh_delta(C.D.dcount[(size_t)C.s * I.nd + d], I.NV, +1);
+        if (!C.open) dV += (dsA != d) + (d != deA) - (dsA != deA);
+        sink(C, make_id32(u, d, 0), n1.dist + n2.dist - oldA.dist, n1.tw + n2.tw - oldA.tw,
+             n1.lex + n2.lex - oldA.lex, n1.dex + n2.dex - oldA.dex, dV, A, A, b);
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Depot-Replace (Fig. 1b): the route whose first customer is u takes depot d as departure,
+// arrival or both; the best case by (dF, case) is the move of (route, d).
+// ------------------------------------------------------------------------------------------
+template <bool TW>
+__device__ void eval_depot_replace(const Ctx &C, int cu, int lane, Best &b, int part) {
+    if (part != 0) return;
+    const DevInst &I = C.I;
+    const int u = I.nd + cu;
+    const Seg8 Pu = pre8(C, u);
+    if (Pu.b != 1) return;  // u must be the route's first customer
+    const int A = Pu.a;
+    const size_t sA = (size_t)C.s * C.D.R + A;
+    const int4 hA = C.D.rhdr[sA];
+    const int dsA = hA.y, deA = hA.z, cL = hA.w;
+    const RT oldA = rt_of(seg_of(ld_seg8(&C.D.rterm[sA])), I);
+    const Seg SU = seg_of(suf8(C, u));
+    const Seg PL = seg_of(pre8(C, cL));
+    const Seg CORE = seg_of(ld_seg8(&C.D.rcore[sA]));
+    const int oldc = (!C.open && dsA != deA) ? 1 : 0;
+    const int *cnt = C.D.dcount + (size_t)C.s * I.nd;
+    for (int d = lane; d < I.nd; d += 32) {
+        double bf = 0.0;
+        int bcase = -1, bD = 0, bT = 0, bL = 0, bU = 0, bV = 0;
+        const int dveh = d != dsA ? veh_delta(cnt[dsA], I.NV, -1) + veh_delta(cnt[d], I.NV, +1) : 0;
+        for (int cs = 0; cs < 3; cs++) {
+            if (cs == 0 && d == dsA) continue;
+            if (cs == 1 && (C.open || d == deA)) continue;
+            if (cs == 2 && (C.open || (d == dsA && d == deA))) continue;
+            Seg g;
+            int clo, veh;
+            if (cs == 0) {
+                g = join_t<TW>(C, nseg(C, d), d, SU, u);  // SU already ends at the arrival depot
+                clo = (!C.open && d != deA) ? 1 : 0;
+                veh = dveh;
+            } else if (cs == 1) {
+                g = join<TW>(C, PL, cL, nseg(C, d), d);
+                clo = dsA != d ? 1 : 0;
+                veh = 0;
+            } else {
+                g = join_t<TW>(C, nseg(C, d), d, CORE, u);
+                g = join<TW>(C, g, cL, nseg(C, d), d);
+                clo = 0;
+                veh = dveh;
+            }
+            const RT n = rt_of(g, I);
+            const int dD = n.dist - oldA.dist, dT = n.tw - oldA.tw, dL = n.lex - oldA.lex, dU = n.dex - oldA.dex;
+            const int dV = clo - oldc + veh;
+            const double f = combine_df(C.w, dD, dT, dL, dU, dV);
+            b.n++;
+            if (bcase < 0 || f < bf) {
+                bf = f; bcase = cs; bD = dD; bT = dT; bL = dL; bU = dU; bV = dV;
+            }
+        }
+        if (bcase >= 0) offer(C, make_id32(u, d, bcase), bD, bT, bL, bU, bV, A, A, b, false, true, bf);
+    }
+}
+
+__device__ __forceinline__ void best_init(Best &b) {
+    b.f = 0.0; b.id = MD_NO_ID; b.valid = 0; b.fx = 0; b.routes = 0; b.n = 0;
+    b.dD = b.dT = b.dL = b.dU = b.dV = 0;
+    b.lo = b.hi = 0.0f;
+}
+
+template <bool TW>
+__device__ __forceinline__ void eval_customer(const Ctx &C, int op, int cu, int lane, Best &b, int *wl,
+                                              int part = 0, int wpc = 1) {
+    switch (op) {
+    case MD_OP_RELOCATE: eval_relocate<TW>(C, cu, lane, b, wl, part, wpc); break;
+    case MD_OP_SWAP: eval_swap<TW>(C, cu, lane, b, wl, part, wpc); break;
+    case MD_OP_TWO_OPT_STAR: eval_2optstar<TW>(C, cu, lane, b, wl, part, wpc); break;
+    case MD_OP_DEPOT_INSERT: eval_depot_insert<TW>(C, cu, lane, b, part); break;
+    case MD_OP_DEPOT_REPLACE: eval_depot_replace<TW>(C, cu, lane, b, part); break;
+    default: break;
+    }
+}
+
+// Warp reduction of the lanes' leader candidates and scored counts; one record per warp slot.
+__device__ __forceinline__ void warp_commit(const Ctx &C, Best &b, size_t slot, int lane) {
+    if (b.valid && !b.fx) b.f = combine_df(C.w, b.dD, b.dT, b.dL, b.dU, b.dV);
+    for (int o = 16; o > 0; o >>= 1) {
+        const double of = __shfl_xor_sync(0xffffffffu, b.f, o);
+        const uint32_t oi = __shfl_xor_sync(0xffffffffu, b.id, o);
+        const int ov = __shfl_xor_sync(0xffffffffu, b.valid, o);
+        const uint32_t ort = __shfl_xor_sync(0xffffffffu, b.routes, o);
+        b.n += __shfl_xor_sync(0xffffffffu, b.n, o);
+        if (ov && (!b.valid || of < b.f || (of == b.f && oi < b.id))) { b.f = of; b.id = oi; b.valid = 1; b.routes = ort; }
+    }
+    if (lane == 0) {
+        LeadRec r;
+        r.f = b.f; r.id = b.valid ? b.id : MD_NO_ID; r.routes = b.routes;
+        C.M.lpart[(size_t)C.s * C.M.nblk + slot] = r;
+        if (b.n) atomicAdd(&C.M.nscored[C.s], b.n);
+    }
+}
+
+}  // namespace

@@ -263,4 +263,9 @@ size_t md_step_smem(const md_solutions *s);
 md_status md_descend_prepare(md_solutions *s, const md_config *cfg, const uint8_t *perm_dev, cudaStream_t st,
                              long long *launches);
 int md_eval_blocks(const md_solutions *s);
+int md_eval_wpc_full(const md_solutions *s);
+// The whole descent of every solution in one persistent launch (persist.cu); *ms: its duration
+// when timed.
+md_status md_descend_persistent(md_solutions *s, md_moves *m, uint32_t eflags, int max_steps, cudaStream_t st,
+                                bool timed, float *ms);
 int md_eval_partials(const md_solutions *s);

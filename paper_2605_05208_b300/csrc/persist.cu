@@ -1,0 +1,189 @@
+// persist.cu -- the whole MDFIS descent (Alg. 2) of every solution in ONE persistent launch.
+//
+// The work of a descent is a sequence of tasks taken in order from a device-side counter: for
+// step k = 0, 1, ... and solution s = 0 .. S-1, the T evaluation tiles of s (tile t: warp slots
+// 8t .. 8t + 7 of the neighbourhood evaluation, eval_core.cuh) and then the step of s (selection,
+// apply + rebuild, totals, state; step.cuh).  A tile of step k waits until s has completed k
+// steps; the step waits until all T tiles of its evaluation are in.  Every task waits only on
+// tasks taken before it, and a block runs the task it took to the end before taking another, so
+// the descent always progresses (once every solution's descent has ended, blocks stop taking
+// tasks and drop the one they took: a task still waiting sees its solution's end and stops
+// waiting); each solution advances as soon as its own work is done instead
+// of waiting for a launch of all solutions, and one solution's step overlaps the others'
+// evaluation.  Waits are bounded: on a timeout the kernel raises a flag and every block stops at
+// its next task.
+//
+// Ordering: a task publishes its writes (every thread fences, the block synchronises, thread 0
+// adds to the solution's counter); the waiting thread reads the counter with acquire semantics
+// and the block synchronises before reading, with coherent loads for all solution data.
+#include "eval_core.cuh"
+#include "step.cuh"
+
+namespace {
+
+struct PCtl {
+    int next;   // task counter
+    int ndone;  // solutions whose descent has ended
+    int err;    // a wait timed out
+    int pad;
+};
+
+__device__ __forceinline__ int ld_acquire(const int *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Thread 0 waits until *p >= target (1) or the solution's descent has ended (2: nothing left to
+// do for it; the task it waits for may then never run); 0 after about `limit` polls.
+__device__ __forceinline__ int wait_geq(const int *p, int target, const int *done, int limit) {
+    for (int it = 0; it < limit; it++) {
+        if (ld_acquire(p) >= target) return 1;
+        if (ld_acquire(done) != 0) return 2;
+        __nanosleep(it < 64 ? 32 : 256);
+    }
+    return 0;
+}
+
+#define PERSIST_WAIT (1 << 22)  // polls (at most about a second) before a wait gives up
+
+template <bool TW>
+__global__ void __launch_bounds__(32 * MD_EVAL_WARPS, MD_EVAL_MIN_BLOCKS)
+k_descend_persistent(DevInst I, DevSols D, DevMoves M, uint32_t flags, int T, int kmax, int wpc_full, PCtl *ctl,
+                     int *step_count, int *tile_count) {
+    __shared__ int s_task, s_stop, s_skip;
+    __shared__ int s_wl[MD_EVAL_WARPS][64];
+    __shared__ double s_w[4];
+    __shared__ float s_wf[4];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int S = D.S;
+    const long long total = (long long)kmax * S * (T + 1);
+    for (;;) {
+        if (tid == 0) {
+            const int task = atomicAdd(&ctl->next, 1);
+            s_task = task;
+            s_stop = task >= total || ld_acquire(&ctl->ndone) >= S || ld_acquire(&ctl->err) != 0;
+        }
+        __syncthreads();
+        if (s_stop) break;
+        const int task = s_task;
+        const int t = task % (T + 1), ks = task / (T + 1);
+        const int s = ks % S, k = ks / S;
+        int *st = D.state + (size_t)s * MD_STATE;
+        if (t < T) {
+            // evaluation tile t of the solution's step k, once its k-th step is complete
+            if (tid == 0) {
+                const int w = wait_geq(&step_count[s], k, st + 3, PERSIST_WAIT);
+                if (w == 0) atomicExch(&ctl->err, 1);
+                s_skip = w != 1 || st[3] != 0;
+                if (!s_skip) {
+                    for (int q = 0; q < 4; q++) {
+                        s_w[q] = D.w[4 * s + q];
+                        s_wf[q] = (float)s_w[q];
+                    }
+                }
+            }
+            __syncthreads();
+            if (!s_skip) {
+                Ctx C;
+                C.I = I; C.D = D; C.M = M; C.flags = flags;
+                C.s = s;
+                C.open = (I.variant & MD_VARIANT_OPEN) != 0;
+                C.sym = (I.variant & MD_VARIANT_SYMMETRIC) != 0;
+                C.w = s_w;
+                C.wf = s_wf;
+                const int op_raw = D.ops[s];
+                const int op = op_raw < 0 ? -1 : (op_raw & MD_OP_MASK);
+                C.lists = I.theta > 0 && !(op_raw >= 0 && (op_raw & MD_OP_SWEEP));
+                const int wpc = C.lists ? 1 : wpc_full;
+                Best b;
+                best_init(b);
+                if (op >= 0)
+                    for (int gw = t * MD_EVAL_WARPS + warp; gw < I.nc * wpc; gw += T * MD_EVAL_WARPS)
+                        eval_customer<TW>(C, op, gw / wpc, lane, b, s_wl[warp], gw % wpc, wpc);
+                warp_commit(C, b, (size_t)t * MD_EVAL_WARPS + warp, lane);
+            }
+            __threadfence();
+            __syncthreads();
+            if (tid == 0) atomicAdd(&tile_count[s], 1);
+        } else {
+            // the step, once the T tiles of the evaluation are in
+            if (tid == 0) {
+                const int w = wait_geq(&tile_count[s], T * (k + 1), st + 3, PERSIST_WAIT);
+                if (w == 0) atomicExch(&ctl->err, 1);
+                s_skip = w != 1 || st[3] != 0;
+            }
+            __syncthreads();
+            if (!s_skip) step_body<TW>(I, D, M, s, T * MD_EVAL_WARPS);
+            __threadfence();
+            __syncthreads();
+            if (tid == 0) {
+                if (!s_skip && st[3] != 0) atomicAdd(&ctl->ndone, 1);
+                atomicAdd(&step_count[s], 1);
+            }
+        }
+    }
+}
+
+}  // namespace
+
+md_status md_descend_persistent(md_solutions *s, md_moves *m, uint32_t eflags, int max_steps, cudaStream_t st,
+                                bool timed, float *ms) {
+    const DevInst &I = s->inst->d;
+    const int S = s->n_sol;
+    const int T = m->d.nblk / MD_EVAL_WARPS;
+    const int wpc = md_eval_wpc_full(s);
+    const size_t smem = md_step_smem(s);
+    char *buf = nullptr;
+    const size_t bytes = sizeof(PCtl) + sizeof(int) * 2 * (size_t)S;
+    MD_CUDA(cudaMallocAsync((void **)&buf, bytes, st));
+    MD_CUDA(cudaMemsetAsync(buf, 0, bytes, st));
+    PCtl *ctl = reinterpret_cast<PCtl *>(buf);
+    int *step_count = reinterpret_cast<int *>(buf + sizeof(PCtl));
+    int *tile_count = step_count + S;
+    int dev = 0, sms = 148, per_sm = 0;
+    MD_CUDA(cudaGetDevice(&dev));
+    MD_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const bool tw = (I.variant & MD_VARIANT_TW) != 0;
+    if (tw) {
+        MD_CUDA(cudaFuncSetAttribute(k_descend_persistent<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        MD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_descend_persistent<true>, 32 * MD_EVAL_WARPS, smem));
+    } else {
+        MD_CUDA(cudaFuncSetAttribute(k_descend_persistent<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        MD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_descend_persistent<false>, 32 * MD_EVAL_WARPS, smem));
+    }
+    if (per_sm < 1) { md_set_error("md_descend: the persistent kernel does not fit an SM"); return MD_ERR_STATE; }
+    if (per_sm > MD_EVAL_MIN_BLOCKS) per_sm = MD_EVAL_MIN_BLOCKS;
+    const int grid = per_sm * sms;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (timed) {
+        MD_CUDA(cudaEventCreate(&e0));
+        MD_CUDA(cudaEventCreate(&e1));
+        MD_CUDA(cudaEventRecord(e0, st));
+    }
+    if (tw)
+        k_descend_persistent<true><<<grid, 32 * MD_EVAL_WARPS, smem, st>>>(I, s->d, m->d, eflags, T, max_steps, wpc, ctl,
+                                                                          step_count, tile_count);
+    else
+        k_descend_persistent<false><<<grid, 32 * MD_EVAL_WARPS, smem, st>>>(I, s->d, m->d, eflags, T, max_steps, wpc, ctl,
+                                                                           step_count, tile_count);
+    cudaError_t ce = cudaGetLastError();
+    if (ce != cudaSuccess) {
+        cudaFreeAsync(buf, st);
+        return md_cuda_check(ce, "k_descend_persistent");
+    }
+    if (timed) MD_CUDA(cudaEventRecord(e1, st));
+    int herr = 0;
+    MD_CUDA(cudaMemcpyAsync(&herr, &ctl->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    MD_CUDA(cudaFreeAsync(buf, st));
+    MD_CUDA(cudaStreamSynchronize(st));
+    if (timed) {
+        float x = 0.0f;
+        MD_CUDA(cudaEventElapsedTime(&x, e0, e1));
+        *ms = x;
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+    }
+    if (herr) { md_set_error("md_descend: a wait of the persistent descent timed out"); return MD_ERR_TIMEOUT; }
+    return MD_OK;
+}

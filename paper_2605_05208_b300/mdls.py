@@ -71,7 +71,7 @@ class Config(C.Structure):
                 ("lambda0", C.POINTER(C.c_float)), ("multi_move", C.c_int32),
                 ("lambda_update", C.c_int32), ("use_graph", C.c_int32), ("poll_every", C.c_int32),
                 ("op_perm_device", C.c_int32), ("time_eval", C.c_int32), ("n_groups", C.c_int32),
-                ("sweep_every", C.c_int32)]
+                ("sweep_every", C.c_int32), ("persistent", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -315,9 +315,10 @@ class Solutions:
     def descend(self, perm, max_pass: int, multi: bool = True, lambda_update: bool = False,
                 lambda0=None, use_graph: bool = False, poll_every: int = 1, stream=None,
                 n_ops: int | None = None, time_eval: bool = False, n_groups: int = 1,
-                sweep_every: int = 0) -> DescendStats:
+                sweep_every: int = 0, persistent: bool = False) -> DescendStats:
         """MDFIS descent.  perm: uint8 host array [n_sol, >= max_pass, n_ops], or an int device
-        pointer to a [n_sol, max_pass, n_ops] uint8 buffer (then n_ops must be given)."""
+        pointer to a [n_sol, max_pass, n_ops] uint8 buffer (then n_ops must be given).
+        persistent: the whole descent in one persistent launch."""
         if isinstance(perm, int):
             assert n_ops is not None
             pptr, on_dev = C.cast(C.c_void_p(perm), C.POINTER(C.c_uint8)), 1
@@ -331,7 +332,7 @@ class Solutions:
         cfg = Config(n_ops, max_pass, pptr,
                      lam.ctypes.data_as(C.POINTER(C.c_float)) if lam is not None else None,
                      int(multi), int(lambda_update), int(use_graph), int(poll_every), on_dev,
-                     int(time_eval), int(n_groups), int(sweep_every))
+                     int(time_eval), int(n_groups), int(sweep_every), int(persistent))
         st = Stats()
         _check(lib().md_descend(self.h, C.byref(cfg), C.byref(st), _stream(stream)))
         return DescendStats(st.moves_scored, st.steps, st.accepted_steps, st.applied_moves,
@@ -447,7 +448,7 @@ class Batch:
             n_ops = perm.shape[2]
             pptr, on_dev = perm.ctypes.data_as(C.POINTER(C.c_uint8)), 0
         cfg = Config(n_ops, max_pass, pptr, None, int(multi), int(lambda_update), int(use_graph),
-                     int(poll_every), on_dev, int(time_eval), 1, int(sweep_every))
+                     int(poll_every), on_dev, int(time_eval), 1, int(sweep_every), 0)
         st = Stats()
         _check(lib().md_batch_descend(self.h, C.byref(cfg), C.byref(st), _stream(stream)))
         return DescendStats(st.moves_scored, st.steps, st.accepted_steps, st.applied_moves,

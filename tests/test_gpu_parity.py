@@ -359,3 +359,47 @@ def test_capacity_error_is_reported(md):
     with pytest.raises(md.MdError) as e:
         S.load([[[0, 2, 3, 0], [1, 4, 4, 1]]])  # repeated customer
     assert e.value.status == md.MD_ERR_ARG
+
+
+@pytest.mark.parametrize("case", ["mdvrptw-6x288-theta50", "mdovrp-4x600-full", "lists-sweep", "single-lambda"])
+def test_persistent_descent_matches_graph_descent(md, oracle_lib, stream, case):
+    # the whole descent in one persistent launch gives the same solutions and counters as the
+    # pass-by-pass graph form (and, on the smaller cases, as the oracle)
+    kw = dict(multi=True, lambda_update=False, sweep_every=0)
+    nbr = None
+    if case == "mdvrptw-6x288-theta50":
+        spec, nsol, max_pass = W.mdvrptw_6x288(71), 8, 500
+    elif case == "mdovrp-4x600-full":
+        spec, nsol, max_pass = W.gen_mdovrp(72, n_depots=4, n_customers=600), 3, 8
+    elif case == "lists-sweep":
+        spec, nsol, max_pass = W.gen_mdvrptw(73, n_depots=3, n_customers=300, theta=10), 3, 60
+        nbr, cnt = random_neighbor_lists(spec, 10, 7)
+        kw["sweep_every"] = 4
+    else:
+        spec, nsol, max_pass = W.gen_mdvrptw(74, n_depots=3, n_customers=150, theta=20), 3, 60
+        kw.update(multi=False, lambda_update=True)
+    sols = W.initial_solutions(spec, 75, nsol)
+    perm = W.op_permutations(76, nsol, max_pass)
+    runs = []
+    for persistent in (False, True):
+        inst, S = setup(md, spec, sols, R=min(spec.n_customers, 2 * max(len(x) for x in sols) + 64),
+                        K=min(spec.n_customers, 2 * max(len(r) - 2 for x in sols for r in x) + 32))
+        if nbr is not None:
+            inst.set_neighbors(nbr, cnt)
+        st = S.descend(perm, max_pass, use_graph=not persistent, stream=stream, persistent=persistent,
+                       time_eval=True, **kw)
+        runs.append((canon_all(spec, S.read()), S.stats(), S.lam(), st))
+    assert runs[0][0] == runs[1][0]
+    assert np.array_equal(runs[0][1], runs[1][1]) and np.array_equal(runs[0][2], runs[1][2])
+    assert runs[1][3].moves_scored == runs[0][3].moves_scored and runs[1][3].eval_ms > 0
+    if case != "mdvrptw-6x288-theta50":
+        o = oracle_lib.Instance(spec)
+        if nbr is not None:
+            o.set_neighbors(nbr, cnt)
+        d = o.descend(sols[0], perm[0], max_pass, multi=kw["multi"], lambda_update=kw["lambda_update"],
+                      sweep_every=kw["sweep_every"])
+        assert runs[1][0][0] == canon(spec, d.solution)
+
+
+def canon_all(spec, sols):
+    return [canon(spec, s) for s in sols]
