@@ -2,35 +2,45 @@
 //
 // The work of a descent is a sequence of tasks taken in order from a device-side counter: for
 // step k = 0, 1, ... and solution s = 0 .. S-1, the T evaluation tiles of s (tile t: warp slots
-// 8t .. 8t + 7 of the neighbourhood evaluation, eval_core.cuh) and, a few solutions later, the
-// step of s (selection, apply + rebuild, totals, state; step.cuh).  A tile of step k waits until s has completed k
-// steps; the step waits until all T tiles of its evaluation are in.  Every task waits only on
-// tasks taken before it, and a block runs the task it took to the end before taking another, so
-// the descent always progresses (once every solution's descent has ended, blocks stop taking
-// tasks and drop the one they took: a task still waiting sees its solution's end and stops
-// waiting); each solution advances as soon as its own work is done instead
-// of waiting for a launch of all solutions, and one solution's step overlaps the others'
-// evaluation.  Waits are bounded: on a timeout the kernel raises a flag and every block stops at
-// its next task.
+// 8t .. 8t + 7 of the neighbourhood evaluation, eval_core.cuh) and, half a round later, the
+// step of s (selection, apply + rebuild, totals, state; step.cuh).  A tile of step k waits until
+// s has completed k steps; the step waits until all T tiles of its evaluation are in.  Each
+// solution advances as soon as its own work is done instead of waiting for a launch of all
+// solutions, and one solution's step overlaps the others' evaluation.
 //
-// Ordering: a task publishes its writes (every thread fences, the block synchronises, thread 0
-// adds to the solution's counter); the waiting thread reads the counter with acquire semantics
-// and the block synchronises before reading, with coherent loads for all solution data.
+// A block takes its next task while it finishes the current one: the first of its warps done
+// with a tile takes the number, decodes it and checks its counter, so that these round trips
+// overlap the other warps' last customers.  The descent always progresses: the earliest-taken
+// unfinished task is the current task of its block (a block takes its next task only while its
+// current one, taken earlier, is unfinished), and it waits only on tasks taken before it, which
+// are all finished.  Once every solution's descent has ended, blocks stop taking tasks and drop
+// the ones they took; a task still waiting sees its solution's end and stops waiting.  Waits are
+// bounded: on a timeout the kernel raises a flag and every block stops at its next task.
+//
+// Ordering: a task publishes its writes by a block barrier, then a fence and an add to the
+// solution's counter by thread 0; the thread that waits reads the counter with acquire
+// semantics before the block barrier that starts the task, and all solution data is read with
+// coherent loads.
 #include "eval_core.cuh"
 #include "step.cuh"
 
 namespace {
 
 struct PCtl {
-    int next;   // task counter
-    int ndone;  // solutions whose descent has ended
-    int err;    // a wait timed out
-    int pad;
+    unsigned long long next;  // task counter
+    int ndone;                // solutions whose descent has ended
+    int err;                  // a wait timed out
 };
 
 __device__ __forceinline__ int ld_acquire(const int *p) {
     int v;
     asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ int ld_relaxed(const int *p) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
 
@@ -62,53 +72,99 @@ __device__ __forceinline__ void round_task(int j, int S, int T, int L, int &s, i
     t = T;
 }
 
+// The next task of a block, as thread 0 prepares it in shared memory while the block still
+// works on the current one.
+struct NextTask {
+    int k, s, t;
+    int stop;   // nothing left to take
+    int ready;  // its wait was already satisfied (and skip, w and wf are loaded)
+    int skip;   // its solution's descent has ended
+};
+
+// Thread 0: decode task number nt and, if its counter already allows it, load what the task
+// needs (the solution's state and weights, into buffer wb).  The stop flags and the counter are
+// loaded together, and the state and weights together after the counter's acquire.
+__device__ __forceinline__ void prepare(NextTask &nx, unsigned long long nt, unsigned long long total, int S, int T,
+                                        int L, const PCtl *ctl, const int *step_count, const int *tile_count,
+                                        const DevSols &D, double *wb, float *wfb) {
+    const int nd = ld_relaxed(&ctl->ndone), er = ld_relaxed(&ctl->err);
+    nx.ready = 0;
+    if (nt >= total) { nx.stop = 1; return; }
+    const unsigned round_len = (unsigned)S * (T + 1);
+    int k, s, t;
+    if (nt < 0x80000000ULL) {
+        k = (int)((unsigned)nt / round_len);
+        round_task((int)((unsigned)nt - (unsigned)k * round_len), S, T, L, s, t);
+    } else {
+        k = (int)(nt / round_len);
+        round_task((int)(nt - (unsigned long long)k * round_len), S, T, L, s, t);
+    }
+    nx.k = k; nx.s = s; nx.t = t;
+    const int c = ld_acquire(t < T ? &step_count[s] : &tile_count[s]);
+    const int st3 = D.state[(size_t)s * MD_STATE + 3];
+    double w[4];
+    for (int q = 0; q < 4; q++) w[q] = D.w[4 * s + q];
+    nx.stop = nd >= S || er != 0;
+    if (nx.stop || c < (t < T ? k : T * (k + 1))) return;
+    nx.ready = 1;
+    nx.skip = st3 != 0;
+    if (t < T)
+        for (int q = 0; q < 4; q++) {
+            wb[q] = w[q];
+            wfb[q] = (float)w[q];
+        }
+}
+
 template <bool TW>
 __global__ void __launch_bounds__(32 * MD_EVAL_WARPS, MD_EVAL_MIN_BLOCKS)
 k_descend_persistent(DevInst I, DevSols D, DevMoves M, uint32_t flags, int T, int kmax, int wpc_full, int lag,
                      PCtl *ctl, int *step_count, int *tile_count) {
-    __shared__ int s_task, s_stop, s_skip;
+    __shared__ NextTask s_nx;
+    __shared__ int s_s, s_t, s_stop, s_skip, s_first;
     __shared__ int s_wl[MD_EVAL_WARPS][64];
-    __shared__ double s_w[4];
-    __shared__ float s_wf[4];
+    __shared__ double s_w[2][4];  // weights of the current and of the next task
+    __shared__ float s_wf[2][4];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int S = D.S;
-    const long long total = (long long)kmax * S * (T + 1);
-    for (;;) {
+    const unsigned long long total = (unsigned long long)kmax * S * (T + 1);
+    if (tid == 0)
+        prepare(s_nx, atomicAdd(&ctl->next, 1ULL), total, S, T, lag, ctl, step_count, tile_count, D, s_w[0], s_wf[0]);
+    for (int it = 0;; it++) {
+        const int cb = it & 1;  // weight buffer of this task
         if (tid == 0) {
-            const int task = atomicAdd(&ctl->next, 1);
-            s_task = task;
-            s_stop = task >= total || ld_acquire(&ctl->ndone) >= S || ld_acquire(&ctl->err) != 0;
+            const NextTask nx = s_nx;
+            s_stop = nx.stop;
+            if (!nx.stop) {
+                int skip = nx.skip;
+                if (!nx.ready) {
+                    int *st = D.state + (size_t)nx.s * MD_STATE;
+                    const int w = nx.t < T ? wait_geq(&step_count[nx.s], nx.k, st + 3, PERSIST_WAIT)
+                                           : wait_geq(&tile_count[nx.s], T * (nx.k + 1), st + 3, PERSIST_WAIT);
+                    if (w == 0) atomicExch(&ctl->err, 1);
+                    skip = w != 1 || st[3] != 0;
+                    if (!skip && nx.t < T)
+                        for (int q = 0; q < 4; q++) {
+                            s_w[cb][q] = D.w[4 * nx.s + q];
+                            s_wf[cb][q] = (float)s_w[cb][q];
+                        }
+                }
+                s_s = nx.s; s_t = nx.t; s_skip = skip;
+            }
+            s_first = 0;
         }
         __syncthreads();
         if (s_stop) break;
-        const int task = s_task;
-        const int round_len = S * (T + 1);
-        const int k = task / round_len;
-        int s, t;
-        round_task(task - k * round_len, S, T, lag, s, t);
-        int *st = D.state + (size_t)s * MD_STATE;
+        const int s = s_s, t = s_t, skip = s_skip;
         if (t < T) {
-            // evaluation tile t of the solution's step k, once its k-th step is complete
-            if (tid == 0) {
-                const int w = wait_geq(&step_count[s], k, st + 3, PERSIST_WAIT);
-                if (w == 0) atomicExch(&ctl->err, 1);
-                s_skip = w != 1 || st[3] != 0;
-                if (!s_skip) {
-                    for (int q = 0; q < 4; q++) {
-                        s_w[q] = D.w[4 * s + q];
-                        s_wf[q] = (float)s_w[q];
-                    }
-                }
-            }
-            __syncthreads();
-            if (!s_skip) {
+            // evaluation tile t of the solution's step k
+            if (!skip) {
                 Ctx C;
                 C.I = I; C.D = D; C.M = M; C.flags = flags;
                 C.s = s;
                 C.open = (I.variant & MD_VARIANT_OPEN) != 0;
                 C.sym = (I.variant & MD_VARIANT_SYMMETRIC) != 0;
-                C.w = s_w;
-                C.wf = s_wf;
+                C.w = s_w[cb];
+                C.wf = s_wf[cb];
                 const int op_raw = D.ops[s];
                 const int op = op_raw < 0 ? -1 : (op_raw & MD_OP_MASK);
                 C.lists = I.theta > 0 && !(op_raw >= 0 && (op_raw & MD_OP_SWEEP));
@@ -120,23 +176,24 @@ k_descend_persistent(DevInst I, DevSols D, DevMoves M, uint32_t flags, int T, in
                         eval_customer<TW>(C, op, gw / wpc, lane, b, s_wl[warp], gw % wpc, wpc);
                 warp_commit(C, b, (size_t)t * MD_EVAL_WARPS + warp, lane);
             }
-            __threadfence();
+            // the first warp done takes and prepares the block's next task while the others finish
+            if (lane == 0 && atomicAdd(&s_first, 1) == 0)
+                prepare(s_nx, atomicAdd(&ctl->next, 1ULL), total, S, T, lag, ctl, step_count, tile_count, D,
+                        s_w[cb ^ 1], s_wf[cb ^ 1]);
             __syncthreads();
-            if (tid == 0) atomicAdd(&tile_count[s], 1);
-        } else {
-            // the step, once the T tiles of the evaluation are in
             if (tid == 0) {
-                const int w = wait_geq(&tile_count[s], T * (k + 1), st + 3, PERSIST_WAIT);
-                if (w == 0) atomicExch(&ctl->err, 1);
-                s_skip = w != 1 || st[3] != 0;
+                __threadfence();
+                atomicAdd(&tile_count[s], 1);
             }
-            __syncthreads();
-            if (!s_skip) step_body<TW>(I, D, M, s, T * MD_EVAL_WARPS);
-            __threadfence();
+        } else {
+            // the step, once the T tiles of its evaluation are in
+            if (!skip) step_body<TW>(I, D, M, s, T * MD_EVAL_WARPS);
             __syncthreads();
             if (tid == 0) {
-                if (!s_skip && st[3] != 0) atomicAdd(&ctl->ndone, 1);
+                __threadfence();
+                if (!skip && D.state[(size_t)s * MD_STATE + 3] != 0) atomicAdd(&ctl->ndone, 1);
                 atomicAdd(&step_count[s], 1);
+                prepare(s_nx, atomicAdd(&ctl->next, 1ULL), total, S, T, lag, ctl, step_count, tile_count, D, s_w[cb ^ 1], s_wf[cb ^ 1]);
             }
         }
     }

@@ -1,8 +1,9 @@
 """Parity at the workloads' full sizes, in the launch configuration the benchmark times, on
 outputs the oracle can compute one at a time:
 
-- MDVRPTW 6x288 (theta = 50, 32 solutions): complete descents with CUDA graphs, two concurrent
-  solution groups and event timing, against oracle descents of sampled solutions;
+- MDVRPTW 6x288 (theta = 50, 32 solutions): complete descents, both with CUDA graphs, two
+  concurrent solution groups and event timing, and as the one persistent launch per descent that
+  the benchmark times, against oracle descents of sampled solutions;
 - MDOVRP 12x4000 (full neighbourhood, 64 solutions) and MDVRPTW 20x10000 (64 eta-nearest
   candidates, 8 solutions): every solution's leader of every operator, checked by applying it in
   the oracle and recomputing the solution's F from scratch; on sampled solutions the leader and
@@ -37,7 +38,8 @@ def _slots(spec, sols):
     return R, K
 
 
-def test_bench_descent_sampled_against_oracle(md, oracle_lib, stream):
+@pytest.mark.parametrize("form", ["graph", "persistent"])
+def test_bench_descent_sampled_against_oracle(md, oracle_lib, stream, form):
     spec = W.mdvrptw_6x288(1, theta=50)
     sols = W.initial_solutions(spec, 1, 32)
     perm = W.op_permutations(1, 32, 500)
@@ -45,8 +47,12 @@ def test_bench_descent_sampled_against_oracle(md, oracle_lib, stream):
     R, K = min(spec.n_customers, max(64, 2 * max(len(s) for s in sols), spec.n_depots * spec.N_V + 8)), 64
     S = md.Solutions(inst, 32, R, K)
     S.load(sols)
-    S.descend(perm, 500, multi=True, use_graph=True, poll_every=1, stream=stream.cuda_stream,
-              time_eval=True, n_groups=2)
+    if form == "graph":
+        S.descend(perm, 500, multi=True, use_graph=True, poll_every=1, stream=stream.cuda_stream,
+                  time_eval=True, n_groups=2)
+    else:
+        S.descend(perm, 500, multi=True, use_graph=False, persistent=True, stream=stream.cuda_stream,
+                  time_eval=True)
     got, per = S.read(stream=stream.cuda_stream), S.stats(stream=stream.cuda_stream)
     everyone = list(range(spec.n_depots, spec.n_nodes))
     for sol in got:
