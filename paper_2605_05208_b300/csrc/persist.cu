@@ -17,10 +17,12 @@
 // the ones they took; a task still waiting sees its solution's end and stops waiting.  Waits are
 // bounded: on a timeout the kernel raises a flag and every block stops at its next task.
 //
-// Ordering: a task publishes its writes by a block barrier, then a fence and an add to the
-// solution's counter by thread 0; the thread that waits reads the counter with acquire
-// semantics before the block barrier that starts the task, and all solution data is read with
-// coherent loads.
+// Ordering: a task publishes its writes by the block barrier, then a fence and an add to the
+// solution's counter by thread 0 (after a tile, the other warps go on to the next task
+// meanwhile).  The thread that reads a counter does so with acquire semantics before the
+// block barrier that starts the task, and all solution data is read with coherent loads.  The
+// block's next task is prepared in the other half of double-buffered shared memory, so one
+// barrier per tile both ends it and hands the next task to every warp.
 #include "eval_core.cuh"
 #include "step.cuh"
 
@@ -119,44 +121,47 @@ template <bool TW>
 __global__ void __launch_bounds__(32 * MD_EVAL_WARPS, MD_EVAL_MIN_BLOCKS)
 k_descend_persistent(DevInst I, DevSols D, DevMoves M, uint32_t flags, int T, int kmax, int wpc_full, int lag,
                      PCtl *ctl, int *step_count, int *tile_count) {
-    __shared__ NextTask s_nx;
-    __shared__ int s_s, s_t, s_stop, s_skip, s_first;
-    __shared__ int s_wl[MD_EVAL_WARPS][64];
-    __shared__ double s_w[2][4];  // weights of the current and of the next task
+    // double-buffered by the parity of the block's task: the current task and the next one
+    __shared__ NextTask s_nx[2];
+    __shared__ int s_first[2], s_skip[2];
+    __shared__ double s_w[2][4];
     __shared__ float s_wf[2][4];
+    __shared__ int s_wl[MD_EVAL_WARPS][64];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int S = D.S;
     const unsigned long long total = (unsigned long long)kmax * S * (T + 1);
-    if (tid == 0)
-        prepare(s_nx, atomicAdd(&ctl->next, 1ULL), total, S, T, lag, ctl, step_count, tile_count, D, s_w[0], s_wf[0]);
+    if (tid == 0) {
+        s_first[0] = 0;
+        prepare(s_nx[0], atomicAdd(&ctl->next, 1ULL), total, S, T, lag, ctl, step_count, tile_count, D, s_w[0],
+                s_wf[0]);
+    }
+    __syncthreads();
     for (int it = 0;; it++) {
-        const int cb = it & 1;  // weight buffer of this task
-        if (tid == 0) {
-            const NextTask nx = s_nx;
-            s_stop = nx.stop;
-            if (!nx.stop) {
-                int skip = nx.skip;
-                if (!nx.ready) {
-                    int *st = D.state + (size_t)nx.s * MD_STATE;
-                    const int w = nx.t < T ? wait_geq(&step_count[nx.s], nx.k, st + 3, PERSIST_WAIT)
-                                           : wait_geq(&tile_count[nx.s], T * (nx.k + 1), st + 3, PERSIST_WAIT);
-                    if (w == 0) atomicExch(&ctl->err, 1);
-                    skip = w != 1 || st[3] != 0;
-                    if (!skip && nx.t < T)
-                        for (int q = 0; q < 4; q++) {
-                            s_w[cb][q] = D.w[4 * nx.s + q];
-                            s_wf[cb][q] = (float)s_w[cb][q];
-                        }
-                }
-                s_s = nx.s; s_t = nx.t; s_skip = skip;
+        const int cb = it & 1, nb = cb ^ 1;
+        const NextTask nx = s_nx[cb];
+        if (nx.stop) break;
+        int skip = nx.skip;
+        if (!nx.ready) {
+            // the task's counter was short when it was prepared: thread 0 waits for it
+            if (tid == 0) {
+                int *st = D.state + (size_t)nx.s * MD_STATE;
+                const int w = nx.t < T ? wait_geq(&step_count[nx.s], nx.k, st + 3, PERSIST_WAIT)
+                                       : wait_geq(&tile_count[nx.s], T * (nx.k + 1), st + 3, PERSIST_WAIT);
+                if (w == 0) atomicExch(&ctl->err, 1);
+                const int sk = w != 1 || st[3] != 0;
+                if (!sk && nx.t < T)
+                    for (int q = 0; q < 4; q++) {
+                        s_w[cb][q] = D.w[4 * nx.s + q];
+                        s_wf[cb][q] = (float)s_w[cb][q];
+                    }
+                s_skip[cb] = sk;
             }
-            s_first = 0;
+            __syncthreads();
+            skip = s_skip[cb];
         }
-        __syncthreads();
-        if (s_stop) break;
-        const int s = s_s, t = s_t, skip = s_skip;
+        const int s = nx.s, t = nx.t;
         if (t < T) {
-            // evaluation tile t of the solution's step k
+            // evaluation tile t of the solution's current step
             if (!skip) {
                 Ctx C;
                 C.I = I; C.D = D; C.M = M; C.flags = flags;
@@ -176,10 +181,15 @@ k_descend_persistent(DevInst I, DevSols D, DevMoves M, uint32_t flags, int T, in
                         eval_customer<TW>(C, op, gw / wpc, lane, b, s_wl[warp], gw % wpc, wpc);
                 warp_commit(C, b, (size_t)t * MD_EVAL_WARPS + warp, lane);
             }
-            // the first warp done takes and prepares the block's next task while the others finish
-            if (lane == 0 && atomicAdd(&s_first, 1) == 0)
-                prepare(s_nx, atomicAdd(&ctl->next, 1ULL), total, S, T, lag, ctl, step_count, tile_count, D,
-                        s_w[cb ^ 1], s_wf[cb ^ 1]);
+            if (lane == 0) {
+                // the first warp done takes and prepares the block's next task while the others
+                // finish
+                if (atomicAdd(&s_first[cb], 1) == 0) {
+                    s_first[nb] = 0;
+                    prepare(s_nx[nb], atomicAdd(&ctl->next, 1ULL), total, S, T, lag, ctl, step_count, tile_count,
+                            D, s_w[nb], s_wf[nb]);
+                }
+            }
             __syncthreads();
             if (tid == 0) {
                 __threadfence();
@@ -193,8 +203,11 @@ k_descend_persistent(DevInst I, DevSols D, DevMoves M, uint32_t flags, int T, in
                 __threadfence();
                 if (!skip && D.state[(size_t)s * MD_STATE + 3] != 0) atomicAdd(&ctl->ndone, 1);
                 atomicAdd(&step_count[s], 1);
-                prepare(s_nx, atomicAdd(&ctl->next, 1ULL), total, S, T, lag, ctl, step_count, tile_count, D, s_w[cb ^ 1], s_wf[cb ^ 1]);
+                s_first[nb] = 0;
+                prepare(s_nx[nb], atomicAdd(&ctl->next, 1ULL), total, S, T, lag, ctl, step_count, tile_count, D,
+                        s_w[nb], s_wf[nb]);
             }
+            __syncthreads();
         }
     }
 }
