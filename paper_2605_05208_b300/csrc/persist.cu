@@ -1,26 +1,30 @@
 // persist.cu -- the whole MDFIS descent (Alg. 2) of every solution in ONE persistent launch.
 //
-// The work of a descent is a sequence of tasks taken in order from a device-side counter: for
-// step k = 0, 1, ... and solution s = 0 .. S-1, the T evaluation tiles of s (tile t: warp slots
-// 8t .. 8t + 7 of the neighbourhood evaluation, eval_core.cuh) and, half a round later, the
-// step of s (selection, apply + rebuild, totals, state; step.cuh).  A tile of step k waits until
-// s has completed k steps; the step waits until all T tiles of its evaluation are in.  Each
-// solution advances as soon as its own work is done instead of waiting for a launch of all
-// solutions, and one solution's step overlaps the others' evaluation.
+// The work of a descent is split into tasks that are queued only once they can run: the T
+// evaluation tiles of a solution's step k (tile t: warp slots 8t .. 8t + 7 of the neighbourhood
+// evaluation, eval_core.cuh) and the step itself (selection, apply + rebuild, totals, state;
+// step.cuh).  Two device-side ring queues hold them.  The block that finishes the last tile of
+// a solution's evaluation queues the solution's step; the block that runs the step queues the T
+// tiles of the solution's next evaluation, unless the descent has ended.  The tiles of every
+// solution's first evaluation are queued implicitly: tile index i < S T is tile i % T of
+// solution i / T.  Blocks take steps first, then tiles, so a step starts as soon as its
+// evaluation is in, and a block never holds a task that waits on another.  Each solution
+// advances as soon as its own work is done, and one solution's step overlaps the others'
+// evaluation.
 //
 // A block takes its next task while it finishes the current one: the first of its warps done
-// with a tile takes the number, decodes it and checks its counter, so that these round trips
-// overlap the other warps' last customers.  The descent always progresses: the earliest-taken
-// unfinished task is the current task of its block (a block takes its next task only while its
-// current one, taken earlier, is unfinished), and it waits only on tasks taken before it, which
-// are all finished.  Once every solution's descent has ended, blocks stop taking tasks and drop
-// the ones they took; a task still waiting sees its solution's end and stops waiting.  Waits are
-// bounded: on a timeout the kernel raises a flag and every block stops at its next task.
+// with a tile tries to take it, so that the queue's round trips overlap the other warps' last
+// customers (a tile only from a long queue: from a short one, an idle block starts it sooner);
+// when it took nothing, thread 0 waits for work at the top of the block's next task.  A block may claim a tile index before it is filled (the claim is a plain add); it
+// keeps the claim, runs steps meanwhile, and takes the tile once it is filled.  Progress: a
+// queued task needs nothing but a block, and every block that waits for work also takes steps,
+// so tiles and steps keep flowing until every solution's descent has ended.  Waits are bounded
+// and restart while the descent progresses: on a timeout the kernel raises a flag and every block
+// stops at its next task.
 //
-// Ordering: a task publishes its writes by the block barrier, then a fence and an add to the
-// solution's counter by thread 0 (after a tile, the other warps go on to the next task
-// meanwhile).  The thread that reads a counter does so with acquire semantics before the
-// block barrier that starts the task, and all solution data is read with coherent loads.  The
+// Ordering: a task's writes are published by the block barrier, then a fence by thread 0 and the
+// queue write; a queue entry is written, fenced, and marked with its index (the consumer reads
+// the mark with acquire semantics), and all solution data is read with coherent loads.  The
 // block's next task is prepared in the other half of double-buffered shared memory, so one
 // barrier per tile both ends it and hands the next task to every warp.
 #include "eval_core.cuh"
@@ -28,10 +32,21 @@
 
 namespace {
 
-struct PCtl {
-    unsigned long long next;  // task counter
-    int ndone;                // solutions whose descent has ended
-    int err;                  // a wait timed out
+struct RQ {
+    unsigned long long tile_head;  // tile indices claimed
+    unsigned long long tile_res;   // tile indices reserved by steps (beyond the S T initial ones)
+    int step_head;                 // step indices claimed
+    int step_res;                  // step indices reserved
+    int ndone;                     // solutions whose descent has ended
+    int err;                       // a wait timed out
+    int progress;                  // steps completed
+    int pad;
+};
+
+// A queue entry: its index once filled (-1 before), the task, and the index it last held once
+// its consumer has read it.
+struct QSlot {
+    int seq, s, t, k, consumed, pad0, pad1, pad2;
 };
 
 __device__ __forceinline__ int ld_acquire(const int *p) {
@@ -46,123 +61,166 @@ __device__ __forceinline__ int ld_relaxed(const int *p) {
     return v;
 }
 
-// Thread 0 waits until *p >= target (1) or the solution's descent has ended (2: nothing left to
-// do for it; the task it waits for may then never run); 0 after about `limit` polls.
-__device__ __forceinline__ int wait_geq(const int *p, int target, const int *done, int limit) {
+__device__ __forceinline__ unsigned long long ld_relaxed64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(int *p, int v) {
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+#define PERSIST_WAIT (1 << 22)  // polls without progress (about a second) before a wait gives up
+
+// Waits until *p == want; 0 after `limit` polls.  Used for the short waits on a queue entry
+// that a running block is writing or reading.
+__device__ __forceinline__ int wait_eq(const int *p, int want, int limit) {
     for (int it = 0; it < limit; it++) {
-        if (ld_acquire(p) >= target) return 1;
-        if (ld_acquire(done) != 0) return 2;
-        __nanosleep(it < 64 ? 32 : 256);
+        if (ld_acquire(p) == want) return 1;
+        __nanosleep(32);
     }
     return 0;
 }
 
-#define PERSIST_WAIT (1 << 22)  // polls (at most about a second) before a wait gives up
+enum { TK_NONE = 0, TK_TILE = 1, TK_STEP = 2, TK_STOP = 3 };
 
-// Task j of a round of S (T + 1) tasks: the tiles of solutions 0 .. S-1 in order, the step of
-// solution q - L right after the tiles of solution q (q >= L), the last L steps at the end
-// (0 <= L <= S).  Every step comes after its own tiles.  Sets s and t (t == T: the step).
-__device__ __forceinline__ void round_task(int j, int S, int T, int L, int &s, int &t) {
-    if (j < L * T) { s = j / T; t = j % T; return; }
-    j -= L * T;
-    if (j < (S - L) * (T + 1)) {
-        const int q = L + j / (T + 1), r = j % (T + 1);
-        if (r < T) { s = q; t = r; } else { s = q - L; t = T; }
-        return;
-    }
-    s = S - L + (j - (S - L) * (T + 1));
-    t = T;
-}
-
-// The next task of a block, as thread 0 prepares it in shared memory while the block still
-// works on the current one.
+// The next task of a block, as one thread prepares it in shared memory.
 struct NextTask {
-    int k, s, t;
-    int stop;   // nothing left to take
-    int ready;  // its wait was already satisfied (and skip, w and wf are loaded)
-    int skip;   // its solution's descent has ended
+    int kind, s, t, k, skip;
 };
 
-// Thread 0: decode task number nt and, if its counter already allows it, load what the task
-// needs (the solution's state and weights, into buffer wb).  The stop flags and the counter are
-// loaded together, and the state and weights together after the counter's acquire.
-__device__ __forceinline__ void prepare(NextTask &nx, unsigned long long nt, unsigned long long total, int S, int T,
-                                        int L, const PCtl *ctl, const int *step_count, const int *tile_count,
-                                        const DevSols &D, double *wb, float *wfb) {
-    const int nd = ld_relaxed(&ctl->ndone), er = ld_relaxed(&ctl->err);
-    nx.ready = 0;
-    if (nt >= total) { nx.stop = 1; return; }
-    const unsigned round_len = (unsigned)S * (T + 1);
-    int k, s, t;
-    if (nt < 0x80000000ULL) {
-        k = (int)((unsigned)nt / round_len);
-        round_task((int)((unsigned)nt - (unsigned)k * round_len), S, T, L, s, t);
+struct Queues {
+    RQ *q;
+    QSlot *tq, *sq;   // tile and step rings
+    int ct, cs;       // their sizes
+    int *tile_count;  // [S] tiles done
+    int S, T, kmax;
+    int lookahead;  // queued tiles needed before a busy block claims one ahead
+};
+
+// Takes tile index i once it is filled (or implicit); 0 if it is not filled yet.
+__device__ __forceinline__ int take_tile(const Queues &Q, const DevSols &D, NextTask &nx, long long i, double *wb,
+                                         float *wfb) {
+    int s, t, k;
+    QSlot &e = Q.tq[i % Q.ct];
+    if (i < (long long)Q.S * Q.T) {
+        s = (int)(i / Q.T); t = (int)(i % Q.T); k = 0;
     } else {
-        k = (int)(nt / round_len);
-        round_task((int)(nt - (unsigned long long)k * round_len), S, T, L, s, t);
+        if (ld_acquire(&e.seq) != (int)i) return 0;
+        s = e.s; t = e.t; k = e.k;
     }
-    nx.k = k; nx.s = s; nx.t = t;
-    const int c = ld_acquire(t < T ? &step_count[s] : &tile_count[s]);
-    const int st3 = D.state[(size_t)s * MD_STATE + 3];
-    double w[4];
-    for (int q = 0; q < 4; q++) w[q] = D.w[4 * s + q];
-    nx.stop = nd >= S || er != 0;
-    if (nx.stop || c < (t < T ? k : T * (k + 1))) return;
-    nx.ready = 1;
-    nx.skip = st3 != 0;
-    if (t < T)
-        for (int q = 0; q < 4; q++) {
-            wb[q] = w[q];
-            wfb[q] = (float)w[q];
+    st_release(&e.consumed, (int)i);
+    nx.kind = TK_TILE; nx.s = s; nx.t = t; nx.k = k;
+    nx.skip = D.state[(size_t)s * MD_STATE + 3] != 0;
+    for (int q = 0; q < 4; q++) {
+        wb[q] = D.w[4 * s + q];
+        wfb[q] = (float)wb[q];
+    }
+    return 1;
+}
+
+// One try at taking a task: a tile the block claimed earlier once it is filled (its solution
+// waits for it), else a step, else a new tile -- claimed only while at least min_queued tiles
+// are queued.  *pend holds a claimed tile index not yet filled (-1: none).  Fills nx (TK_NONE if
+// nothing could be taken) and the tile's weights.
+__device__ void try_take(const Queues &Q, const DevSols &D, NextTask &nx, long long *pend, double *wb, float *wfb,
+                         int min_queued) {
+    nx.kind = TK_NONE;
+    if (*pend >= 0) {
+        if (take_tile(Q, D, nx, *pend, wb, wfb)) *pend = -1;
+        if (nx.kind != TK_NONE) return;
+    }
+    const int sh = ld_relaxed(&Q.q->step_head);
+    if (sh < ld_relaxed(&Q.q->step_res) && atomicCAS(&Q.q->step_head, sh, sh + 1) == sh) {
+        QSlot &e = Q.sq[sh % Q.cs];
+        if (!wait_eq(&e.seq, sh, PERSIST_WAIT)) atomicExch(&Q.q->err, 1);
+        nx.kind = TK_STEP; nx.s = e.s; nx.t = Q.T; nx.k = e.k; nx.skip = 0;
+        st_release(&e.consumed, sh);
+        return;
+    }
+    if (*pend >= 0) return;
+    const unsigned long long th = ld_relaxed64(&Q.q->tile_head);
+    if (th + (unsigned long long)min_queued > (unsigned long long)Q.S * Q.T + ld_relaxed64(&Q.q->tile_res)) return;
+    const long long i = (long long)atomicAdd(&Q.q->tile_head, 1ULL);
+    if (!take_tile(Q, D, nx, i, wb, wfb)) *pend = i;  // claimed before it was filled
+}
+
+// Thread 0: waits for a task; TK_STOP once every descent has ended or a wait timed out.
+__device__ void take(const Queues &Q, const DevSols &D, NextTask &nx, long long *pend, double *wb, float *wfb) {
+    int seen = -1, it = 0;
+    for (;;) {
+        try_take(Q, D, nx, pend, wb, wfb, 1);
+        if (nx.kind != TK_NONE) return;
+        if (ld_relaxed(&Q.q->ndone) >= Q.S || ld_relaxed(&Q.q->err) != 0) { nx.kind = TK_STOP; return; }
+        const int pr = ld_relaxed(&Q.q->progress);
+        if (pr != seen) { seen = pr; it = 0; }
+        if (++it > PERSIST_WAIT) {
+            atomicExch(&Q.q->err, 1);
+            nx.kind = TK_STOP;
+            return;
         }
+        __nanosleep(it < 64 ? 32 : 256);
+    }
+}
+
+// Thread 0: queues the step of solution s (its evaluation k is complete).
+__device__ void queue_step(const Queues &Q, int s, int k) {
+    const int r = atomicAdd(&Q.q->step_res, 1);
+    QSlot &e = Q.sq[r % Q.cs];
+    if (r >= Q.cs && !wait_eq(&e.consumed, r - Q.cs, PERSIST_WAIT)) atomicExch(&Q.q->err, 1);
+    e.s = s; e.t = Q.T; e.k = k;
+    __threadfence();
+    st_release(&e.seq, r);
+}
+
+// Warp 0: queues the T tiles of solution s's evaluation k.
+__device__ void queue_tiles(const Queues &Q, int s, int k, int lane) {
+    unsigned long long r0 = 0;
+    if (lane == 0) r0 = (unsigned long long)Q.S * Q.T + atomicAdd(&Q.q->tile_res, (unsigned long long)Q.T);
+    r0 = __shfl_sync(0xffffffffu, r0, 0);
+    for (int j = lane; j < Q.T; j += 32) {
+        const long long i = (long long)(r0 + j);
+        QSlot &e = Q.tq[i % Q.ct];
+        if (i >= Q.ct && !wait_eq(&e.consumed, (int)(i - Q.ct), PERSIST_WAIT)) atomicExch(&Q.q->err, 1);
+        e.s = s; e.t = j; e.k = k;
+        __threadfence();
+        st_release(&e.seq, (int)i);
+    }
 }
 
 template <bool TW>
 __global__ void __launch_bounds__(32 * MD_EVAL_WARPS, MD_EVAL_MIN_BLOCKS)
-k_descend_persistent(DevInst I, DevSols D, DevMoves M, uint32_t flags, int T, int kmax, int wpc_full, int lag,
-                     PCtl *ctl, int *step_count, int *tile_count) {
+k_descend_persistent(DevInst I, DevSols D, DevMoves M, uint32_t flags, int wpc_full, Queues Q) {
     // double-buffered by the parity of the block's task: the current task and the next one
     __shared__ NextTask s_nx[2];
-    __shared__ int s_first[2], s_skip[2];
+    __shared__ int s_first[2];
+    __shared__ long long s_pend;  // a claimed tile index not yet filled, or -1
     __shared__ double s_w[2][4];
     __shared__ float s_wf[2][4];
     __shared__ int s_wl[MD_EVAL_WARPS][64];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int S = D.S;
-    const unsigned long long total = (unsigned long long)kmax * S * (T + 1);
+    const int T = Q.T;
     if (tid == 0) {
         s_first[0] = 0;
-        prepare(s_nx[0], atomicAdd(&ctl->next, 1ULL), total, S, T, lag, ctl, step_count, tile_count, D, s_w[0],
-                s_wf[0]);
+        s_pend = -1;
+        take(Q, D, s_nx[0], &s_pend, s_w[0], s_wf[0]);
     }
     __syncthreads();
     for (int it = 0;; it++) {
         const int cb = it & 1, nb = cb ^ 1;
-        const NextTask nx = s_nx[cb];
-        if (nx.stop) break;
-        int skip = nx.skip;
-        if (!nx.ready) {
-            // the task's counter was short when it was prepared: thread 0 waits for it
-            if (tid == 0) {
-                int *st = D.state + (size_t)nx.s * MD_STATE;
-                const int w = nx.t < T ? wait_geq(&step_count[nx.s], nx.k, st + 3, PERSIST_WAIT)
-                                       : wait_geq(&tile_count[nx.s], T * (nx.k + 1), st + 3, PERSIST_WAIT);
-                if (w == 0) atomicExch(&ctl->err, 1);
-                const int sk = w != 1 || st[3] != 0;
-                if (!sk && nx.t < T)
-                    for (int q = 0; q < 4; q++) {
-                        s_w[cb][q] = D.w[4 * nx.s + q];
-                        s_wf[cb][q] = (float)s_w[cb][q];
-                    }
-                s_skip[cb] = sk;
-            }
+        NextTask nx = s_nx[cb];
+        if (nx.kind == TK_NONE) {
+            // nothing was queued when the block looked ahead: thread 0 waits for work
+            if (tid == 0) take(Q, D, s_nx[cb], &s_pend, s_w[cb], s_wf[cb]);
             __syncthreads();
-            skip = s_skip[cb];
+            nx = s_nx[cb];
         }
+        if (nx.kind == TK_STOP) break;
         const int s = nx.s, t = nx.t;
-        if (t < T) {
-            // evaluation tile t of the solution's current step
-            if (!skip) {
+        if (nx.kind == TK_TILE) {
+            // evaluation tile t of the solution's step nx.k
+            if (!nx.skip) {
                 Ctx C;
                 C.I = I; C.D = D; C.M = M; C.flags = flags;
                 C.s = s;
@@ -182,30 +240,38 @@ k_descend_persistent(DevInst I, DevSols D, DevMoves M, uint32_t flags, int T, in
                 warp_commit(C, b, (size_t)t * MD_EVAL_WARPS + warp, lane);
             }
             if (lane == 0) {
-                // the first warp done takes and prepares the block's next task while the others
-                // finish
+                // the first warp done tries to take the block's next task while the others finish;
+                // it claims a tile only from a long queue, and leaves a short one to idle blocks,
+                // which would otherwise wait while the tile waits for this block's current one
                 if (atomicAdd(&s_first[cb], 1) == 0) {
                     s_first[nb] = 0;
-                    prepare(s_nx[nb], atomicAdd(&ctl->next, 1ULL), total, S, T, lag, ctl, step_count, tile_count,
-                            D, s_w[nb], s_wf[nb]);
+                    try_take(Q, D, s_nx[nb], &s_pend, s_w[nb], s_wf[nb], Q.lookahead);
                 }
             }
             __syncthreads();
             if (tid == 0) {
                 __threadfence();
-                atomicAdd(&tile_count[s], 1);
+                if (nx.skip) {
+                    // a solution whose descent had ended before the launch: counted once
+                    if (t == 0 && nx.k == 0) atomicAdd(&Q.q->ndone, 1);
+                } else if (atomicAdd(&Q.tile_count[s], 1) == T * (nx.k + 1) - 1) {
+                    queue_step(Q, s, nx.k);
+                }
             }
         } else {
-            // the step, once the T tiles of its evaluation are in
-            if (!skip) step_body<TW>(I, D, M, s, T * MD_EVAL_WARPS);
+            // the step of evaluation nx.k, then the next evaluation's tiles
+            step_body<TW>(I, D, M, s, T * MD_EVAL_WARPS);
             __syncthreads();
+            const bool ended = D.state[(size_t)s * MD_STATE + 3] != 0 || nx.k + 1 >= Q.kmax;
             if (tid == 0) {
                 __threadfence();
-                if (!skip && D.state[(size_t)s * MD_STATE + 3] != 0) atomicAdd(&ctl->ndone, 1);
-                atomicAdd(&step_count[s], 1);
+                if (ended) atomicAdd(&Q.q->ndone, 1);
+                atomicAdd(&Q.q->progress, 1);
+            }
+            if (!ended && warp == 0) queue_tiles(Q, s, nx.k + 1, lane);
+            if (tid == 0) {
                 s_first[nb] = 0;
-                prepare(s_nx[nb], atomicAdd(&ctl->next, 1ULL), total, S, T, lag, ctl, step_count, tile_count, D,
-                        s_w[nb], s_wf[nb]);
+                try_take(Q, D, s_nx[nb], &s_pend, s_w[nb], s_wf[nb], 1);
             }
             __syncthreads();
         }
@@ -221,13 +287,6 @@ md_status md_descend_persistent(md_solutions *s, md_moves *m, uint32_t eflags, i
     const int T = m->d.nblk / MD_EVAL_WARPS;
     const int wpc = md_eval_wpc_full(s);
     const size_t smem = md_step_smem(s);
-    char *buf = nullptr;
-    const size_t bytes = sizeof(PCtl) + sizeof(int) * 2 * (size_t)S;
-    MD_CUDA(cudaMallocAsync((void **)&buf, bytes, st));
-    MD_CUDA(cudaMemsetAsync(buf, 0, bytes, st));
-    PCtl *ctl = reinterpret_cast<PCtl *>(buf);
-    int *step_count = reinterpret_cast<int *>(buf + sizeof(PCtl));
-    int *tile_count = step_count + S;
     int dev = 0, sms = 148, per_sm = 0;
     MD_CUDA(cudaGetDevice(&dev));
     MD_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -242,21 +301,42 @@ md_status md_descend_persistent(md_solutions *s, md_moves *m, uint32_t eflags, i
     if (per_sm < 1) { md_set_error("md_descend: the persistent kernel does not fit an SM"); return MD_ERR_STATE; }
     if (per_sm > MD_EVAL_MIN_BLOCKS) per_sm = MD_EVAL_MIN_BLOCKS;
     const int grid = per_sm * sms;
+    // ring sizes: at most T tiles (one step) of each solution are queued or being read at once,
+    // and each block holds at most one claimed index; twice that, so that a block never waits to
+    // fill a slot whose previous tile it has claimed itself
+    Queues Q;
+    Q.S = S; Q.T = T; Q.kmax = max_steps;
+    // a busy block claims its next tile ahead only while four solutions' evaluations are queued
+    // (on 32 solutions of 6 x 288 customers: 1, 1 T, 4 T, 16 T and never were measured)
+    Q.lookahead = 4 * T;
+    Q.ct = 2 * (S * T + grid) + 64;
+    Q.cs = 2 * (S + grid) + 64;
+    if ((long long)S * T + (long long)max_steps * S * T >= 0x7fffffffLL) {
+        md_set_error("md_descend: too many tiles for the persistent descent");
+        return MD_ERR_ARG;
+    }
+    char *buf = nullptr;
+    const size_t off_tc = sizeof(RQ);
+    const size_t off_tq = (off_tc + sizeof(int) * S + 31) / 32 * 32;
+    const size_t off_sq = off_tq + sizeof(QSlot) * Q.ct;
+    const size_t bytes = off_sq + sizeof(QSlot) * Q.cs;
+    MD_CUDA(cudaMallocAsync((void **)&buf, bytes, st));
+    MD_CUDA(cudaMemsetAsync(buf, 0, off_tq, st));
+    MD_CUDA(cudaMemsetAsync(buf + off_tq, 0xff, bytes - off_tq, st));  // seq = consumed = -1
+    Q.q = reinterpret_cast<RQ *>(buf);
+    Q.tile_count = reinterpret_cast<int *>(buf + off_tc);
+    Q.tq = reinterpret_cast<QSlot *>(buf + off_tq);
+    Q.sq = reinterpret_cast<QSlot *>(buf + off_sq);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (timed) {
         MD_CUDA(cudaEventCreate(&e0));
         MD_CUDA(cudaEventCreate(&e1));
         MD_CUDA(cudaEventRecord(e0, st));
     }
-    // a solution's step is taken half a round after its tiles (measured best on 32 solutions
-    // against 0, 1, 2, 4, 8, 24 and 32), so that they have finished by then
-    const int lag = S / 2;
     if (tw)
-        k_descend_persistent<true><<<grid, 32 * MD_EVAL_WARPS, smem, st>>>(I, s->d, m->d, eflags, T, max_steps, wpc, lag,
-                                                                          ctl, step_count, tile_count);
+        k_descend_persistent<true><<<grid, 32 * MD_EVAL_WARPS, smem, st>>>(I, s->d, m->d, eflags, wpc, Q);
     else
-        k_descend_persistent<false><<<grid, 32 * MD_EVAL_WARPS, smem, st>>>(I, s->d, m->d, eflags, T, max_steps, wpc, lag,
-                                                                           ctl, step_count, tile_count);
+        k_descend_persistent<false><<<grid, 32 * MD_EVAL_WARPS, smem, st>>>(I, s->d, m->d, eflags, wpc, Q);
     cudaError_t ce = cudaGetLastError();
     if (ce != cudaSuccess) {
         cudaFreeAsync(buf, st);
@@ -264,7 +344,7 @@ md_status md_descend_persistent(md_solutions *s, md_moves *m, uint32_t eflags, i
     }
     if (timed) MD_CUDA(cudaEventRecord(e1, st));
     int herr = 0;
-    MD_CUDA(cudaMemcpyAsync(&herr, &ctl->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    MD_CUDA(cudaMemcpyAsync(&herr, &Q.q->err, sizeof(int), cudaMemcpyDeviceToHost, st));
     MD_CUDA(cudaFreeAsync(buf, st));
     MD_CUDA(cudaStreamSynchronize(st));
     if (timed) {
