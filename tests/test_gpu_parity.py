@@ -403,3 +403,41 @@ def test_persistent_descent_matches_graph_descent(md, oracle_lib, stream, case):
 
 def canon_all(spec, sols):
     return [canon(spec, s) for s in sols]
+
+
+@pytest.mark.parametrize("case", ["one-solution", "tiny-many-solutions", "one-pass", "descend-twice"])
+def test_persistent_descent_edge_cases(md, stream, case):
+    # the queued persistent descent at the edges of its task queues: a single solution (one
+    # evaluation in flight), more solutions than blocks of a tiny instance (two tiles per
+    # evaluation, many steps queued at once), a descent cut off after one pass, and a second
+    # descent of solutions that already sit at a local optimum; each against the graph form
+    kw = dict(multi=True, lambda_update=False, sweep_every=0)
+    max_pass = 60
+    if case == "one-solution":
+        spec, nsol = W.gen_mdvrptw(81, n_depots=3, n_customers=200, theta=20), 1
+    elif case == "tiny-many-solutions":
+        spec, nsol = W.gen_mdvrp(82, n_depots=2, n_customers=12, Q=40, N_V=3), 400
+    elif case == "one-pass":
+        spec, nsol, max_pass = W.gen_mdvrptw(83, n_depots=4, n_customers=150, theta=20), 6, 1
+    else:
+        spec, nsol = W.gen_mdvrptw(84, n_depots=3, n_customers=120, theta=20), 5
+    sols = W.initial_solutions(spec, 85, nsol)
+    perm = W.op_permutations(86, nsol, max_pass)
+    runs = []
+    for persistent in (False, True):
+        inst, S = setup(md, spec, sols, R=min(spec.n_customers, 2 * max(len(x) for x in sols) + 64),
+                        K=min(spec.n_customers, 2 * max(len(r) - 2 for x in sols for r in x) + 32))
+        st = first = S.descend(perm, max_pass, use_graph=not persistent, stream=stream, persistent=persistent, **kw)
+        if case == "descend-twice":
+            assert first.passes_max < max_pass  # the first descent reached a local optimum
+            st = S.descend(perm, max_pass, use_graph=not persistent, stream=stream, persistent=persistent, **kw)
+        runs.append((canon_all(spec, S.read()), S.stats(), st))
+    assert runs[0][0] == runs[1][0]
+    assert np.array_equal(runs[0][1], runs[1][1])
+    assert runs[1][2].moves_scored == runs[0][2].moves_scored
+    assert runs[1][2].steps == runs[0][2].steps
+    if case == "one-pass":
+        assert runs[1][2].passes_max == 1
+    if case == "descend-twice":
+        # the second descent starts at a local optimum: one pass that applies nothing
+        assert runs[1][2].accepted_steps == 0
