@@ -416,7 +416,7 @@ def run_batch(args):
                                f"16 solutions each, {max_pass} passes per step, multi-move",
                    "l2": "flushed between timed steps (256 MB write)",
                    "tuning": {"customer_parts_per_warp": upw.tolist(), "warps_per_customer": wpc.tolist(),
-                              "grid": grid}},
+                              "solo": B.solo().tolist(), "grid": grid}},
         "batched": res["batched"], "per_instance": res["per_instance"],
         "speedup_vs_per_instance": res["batched"]["moves_per_s"] / res["per_instance"]["moves_per_s"],
     }))

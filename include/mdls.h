@@ -294,8 +294,8 @@ md_status md_batch_destroy(md_batch *batch);
 /* Autotuner of the batch's tile shapes: per instance, the customer parts per warp of an
  * evaluation tile (1, 2 or 4) and, for an instance without neighbour lists, the warps that share
  * one customer's candidates (1, 2, 4 or 8, at most n_customers / 256), timed with CUDA events on
- * that instance alone; then the persistent grid (1, 2, 4 or 8 blocks per SM), timed on the whole
- * batch.  Uses the loaded solutions and sets every solution's operator to a fixed mix for the
+ * that instance alone, and whether the instance runs solo (md_batch_solo); then the persistent
+ * grid (1, 2, 4 or 8 blocks per SM), timed on the instances left in the batched launch.  Uses the loaded solutions and sets every solution's operator to a fixed mix for the
  * timings.  Results only change speed. */
 md_status md_batch_tune(md_batch *batch, void *stream);
 
@@ -308,6 +308,16 @@ md_status md_batch_tuning(const md_batch *batch, int32_t *upw, int32_t *wpc, int
  * and at most n_customers / 256.  MD_ERR_ARG otherwise (nothing changed).  Results only change
  * speed. */
 md_status md_batch_set_tuning(md_batch *batch, const int32_t *upw, const int32_t *wpc, int32_t grid);
+
+/* Which instances run on their own (caller order, host array [n]; 1 = solo): a solo instance
+ * keeps its single-instance evaluation and select/apply launches (as md_descend would make them)
+ * on a stream of its own, forked from the batch's stream inside the same graph, instead of
+ * joining the batched launches.  md_batch_tune sets an instance solo when its own evaluation
+ * launch is faster than the batched one on it alone; none is solo before.  md_batch_set_solo
+ * sets the flags by hand (nonzero = solo).  MD_ERR_ARG on a null argument.  Results only change
+ * speed. */
+md_status md_batch_solo(const md_batch *batch, int32_t *solo);
+md_status md_batch_set_solo(md_batch *batch, const int32_t *solo);
 
 /* MDFIS descent (Alg. 2) of every solution of every instance, as md_descend per instance would
  * do it (identical results).  cfg->op_perm covers the solutions of all instances in the order

@@ -1,6 +1,8 @@
 // batch.cu -- batches of instances of uneven size: every solution of every instance advances
 // with one persistent evaluation launch and one select/apply launch per descent step, replayed
-// from a CUDA graph per pass, with tile shapes chosen by an autotuner.
+// from a CUDA graph per pass, with tile shapes chosen by an autotuner.  An instance the autotuner
+// finds faster on its own ("solo") keeps its single-instance launches instead, on a stream of
+// its own forked from the batch's inside the same graph.
 #include <stdlib.h>
 #include <string.h>
 
@@ -29,6 +31,7 @@ struct md_batch {
     std::vector<int> order;            // item order on the device: largest instances first
     std::vector<int> upw;              // customer parts per warp, per caller item
     std::vector<int> wpc;              // warps per customer, per caller item
+    std::vector<int> solo;             // 1: the item runs its own single-instance launches
     int grid;                          // persistent evaluation grid
     bool tw;
     size_t smem;
@@ -92,6 +95,7 @@ extern "C" md_status md_batch_create(md_solutions *const *sols, int32_t n, md_ba
     b->sols.assign(sols, sols + n);
     b->upw.assign(n, 1);
     b->wpc.assign(n, 1);
+    b->solo.assign(n, 0);
     b->grid = 2 * sm_count();
     b->tw = false;
     b->smem = 0;
@@ -136,6 +140,18 @@ extern "C" md_status md_batch_tuning(const md_batch *b, int32_t *upw, int32_t *w
     if (upw) for (int i = 0; i < b->n; i++) upw[i] = b->upw[i];
     if (wpc) for (int i = 0; i < b->n; i++) wpc[i] = b->wpc[i];
     if (grid) *grid = b->grid;
+    return MD_OK;
+}
+
+extern "C" md_status md_batch_solo(const md_batch *b, int32_t *solo) {
+    if (!b || !solo) { md_set_error("md_batch_solo: null argument"); return MD_ERR_ARG; }
+    for (int i = 0; i < b->n; i++) solo[i] = b->solo[i];
+    return MD_OK;
+}
+
+extern "C" md_status md_batch_set_solo(md_batch *b, const int32_t *solo) {
+    if (!b || !solo) { md_set_error("md_batch_set_solo: null argument"); return MD_ERR_ARG; }
+    for (int i = 0; i < b->n; i++) b->solo[i] = solo[i] != 0;
     return MD_OK;
 }
 
@@ -193,12 +209,39 @@ md_status time_eval(md_batch *b, const std::vector<int> &order, int grid, int re
     return MD_OK;
 }
 
+// Median device time of `reps` single-instance evaluation launches of solutions s.
+md_status time_solo(md_solutions *s, int reps, cudaStream_t st, float *ms) {
+    std::vector<float> t;
+    cudaEvent_t e0, e1;
+    MD_CUDA(cudaEventCreate(&e0));
+    MD_CUDA(cudaEventCreate(&e1));
+    md_status r = MD_OK;
+    for (int k = 0; k < reps + 1; k++) {
+        cudaEventRecord(e0, st);
+        r = md_launch_eval(s, s->scratch, 0u, st, 0, -1);
+        cudaEventRecord(e1, st);
+        if (r != MD_OK) break;
+        cudaError_t ce = cudaEventSynchronize(e1);
+        float x = 0.0f;
+        if (ce == cudaSuccess) ce = cudaEventElapsedTime(&x, e0, e1);
+        if (ce != cudaSuccess) { r = md_cuda_check(ce, "md_batch_tune timing"); break; }
+        if (k > 0) t.push_back(x);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (r != MD_OK) return r;
+    std::sort(t.begin(), t.end());
+    *ms = t[t.size() / 2];
+    return MD_OK;
+}
+
 }  // namespace
 
 // Autotuner: per instance, the customer parts per warp of an evaluation tile (1, 2 or 4) and,
 // for instances without neighbour lists, the warps per customer (1, 2, 4 or 8, at most nc / 256
-// so that the records fit the evaluation scratch), timed on that instance alone; then the
-// persistent grid (1, 2, 4 or 8 blocks per SM) for the whole batch.
+// so that the records fit the evaluation scratch), timed on that instance alone, against the
+// instance's own single-instance evaluation launch (solo when that is faster); then the
+// persistent grid (1, 2, 4 or 8 blocks per SM) for the instances left in the batch.
 // Every solution's operator is set to a fixed mix (s mod 5) for the timings; md_batch_descend
 // resets it.
 extern "C" md_status md_batch_tune(md_batch *b, void *stream) {
@@ -226,12 +269,19 @@ extern "C" md_status md_batch_tune(md_batch *b, void *stream) {
         }
         b->upw[i] = bu;
         b->wpc[i] = bw;
+        float solo_ms = 0.0f;
+        md_status r = time_solo(b->sols[i], 3, st, &solo_ms);
+        if (r != MD_OK) return r;
+        b->solo[i] = solo_ms < best;
     }
+    std::vector<int> batched;
+    for (int k : b->order) if (!b->solo[k]) batched.push_back(k);
     float best = 1e30f;
     int bg = 2 * sms;
     for (int mult : {1, 2, 4, 8}) {
+        if (batched.empty()) break;
         float ms = 0.0f;
-        md_status r = time_eval(b, b->order, mult * sms, 3, st, &ms);
+        md_status r = time_eval(b, batched, mult * sms, 3, st, &ms);
         if (r != MD_OK) return r;
         if (ms < best) { best = ms; bg = mult * sms; }
     }
@@ -274,19 +324,69 @@ extern "C" md_status md_batch_descend(md_batch *b, const md_config *cfg, md_stat
         if (r != MD_OK) return r;
         off += b->sols[i]->n_sol;
     }
-    int tiles = 0, sols = 0;
-    std::vector<BatchItem> v = build_items(b, b->order, &tiles, &sols);
+    // the batched items first (largest first), then the solo ones; the work list covers all of
+    // them (the running check reads every item), the batched launches only the first nb
+    std::vector<int> ord, solo_items;
+    for (int k : b->order) if (!b->solo[k]) ord.push_back(k);
+    const int nb = (int)ord.size();
+    for (int k : b->order) if (b->solo[k]) { ord.push_back(k); solo_items.push_back(k); }
+    int tiles_all = 0, sols = 0;
+    std::vector<BatchItem> v = build_items(b, ord, &tiles_all, &sols);
+    const int tiles = nb < b->n ? v[nb].tile_base : tiles_all;
+    const int sols_b = nb < b->n ? v[nb].sol_base : sols;
     md_status r = upload_items(b, v, st);
     if (r != MD_OK) return r;
     const uint32_t eflags = cfg->multi_move ? MD_EVAL_FOLLOWERS : 0u;
     const int poll = cfg->poll_every > 0 ? cfg->poll_every : 1;
     const int steps = cfg->n_ops * poll;
+    // one stream per solo item, forked from and joined back to `stream` (with no stream, the
+    // solo launches go to the default stream in order)
+    const int G = st ? (int)solo_items.size() : 0;
+    std::vector<cudaStream_t> side(G, nullptr);
+    std::vector<cudaEvent_t> joins(G, nullptr);
+    cudaEvent_t fork = nullptr;
+    auto release = [&]() {
+        for (auto &e : joins) if (e) cudaEventDestroy(e);
+        for (auto &q : side) if (q) cudaStreamDestroy(q);
+        if (fork) cudaEventDestroy(fork);
+        joins.clear();
+        side.clear();
+        fork = nullptr;
+    };
+    if (G > 0) {
+        cudaError_t ce = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+        for (int g = 0; g < G && ce == cudaSuccess; g++) {
+            ce = cudaStreamCreateWithFlags(&side[g], cudaStreamNonBlocking);
+            if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&joins[g], cudaEventDisableTiming);
+        }
+        if (ce != cudaSuccess) { release(); return md_cuda_check(ce, "md_batch_descend streams"); }
+    }
     auto enqueue = [&]() -> md_status {
+        if (G > 0) {
+            MD_CUDA(cudaEventRecord(fork, st));
+            for (int g = 0; g < G; g++) MD_CUDA(cudaStreamWaitEvent(side[g], fork, 0));
+        }
         for (int k = 0; k < steps; k++) {
-            md_status q = md_launch_eval_batch(b->items_d, b->n, tiles, b->grid, b->tw, eflags, b->next_tile_d, st);
-            if (q != MD_OK) return q;
-            q = md_launch_step_batch(b->items_d, b->n, sols, b->smem, b->tw, st);
-            if (q != MD_OK) return q;
+            if (nb > 0) {
+                md_status q = md_launch_eval_batch(b->items_d, nb, tiles, b->grid, b->tw, eflags, b->next_tile_d, st);
+                if (q != MD_OK) return q;
+                q = md_launch_step_batch(b->items_d, nb, sols_b, b->smem, b->tw, st);
+                if (q != MD_OK) return q;
+            }
+            for (int g = 0; g < (int)solo_items.size(); g++) {
+                md_solutions *s = b->sols[solo_items[g]];
+                cudaStream_t sg = G > 0 ? side[g] : st;
+                md_status q = md_launch_eval(s, s->scratch, eflags, sg, 0, -1);
+                if (q != MD_OK) return q;
+                q = md_launch_step(s, s->scratch, sg, 0, -1);
+                if (q != MD_OK) return q;
+            }
+        }
+        if (G > 0) {
+            for (int g = 0; g < G; g++) {
+                MD_CUDA(cudaEventRecord(joins[g], side[g]));
+                MD_CUDA(cudaStreamWaitEvent(st, joins[g], 0));
+            }
         }
         return MD_OK;
     };
@@ -294,13 +394,14 @@ extern "C" md_status md_batch_descend(md_batch *b, const md_config *cfg, md_stat
     cudaGraphExec_t exec = nullptr;
     const bool use_graph = cfg->use_graph && st != nullptr;
     if (use_graph) {
-        MD_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        cudaError_t ce = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+        if (ce != cudaSuccess) { release(); return md_cuda_check(ce, "cudaStreamBeginCapture"); }
         md_status cr = enqueue();
-        cudaError_t ce = cudaStreamEndCapture(st, &graph);
-        if (cr != MD_OK) { if (graph) cudaGraphDestroy(graph); return cr; }
-        MD_CUDA(ce);
+        ce = cudaStreamEndCapture(st, &graph);
+        if (cr != MD_OK) { if (graph) cudaGraphDestroy(graph); release(); return cr; }
+        if (ce != cudaSuccess) { release(); return md_cuda_check(ce, "cudaStreamEndCapture"); }
         ce = cudaGraphInstantiate(&exec, graph, 0);
-        if (ce != cudaSuccess) { cudaGraphDestroy(graph); return md_cuda_check(ce, "cudaGraphInstantiate"); }
+        if (ce != cudaSuccess) { cudaGraphDestroy(graph); release(); return md_cuda_check(ce, "cudaGraphInstantiate"); }
     }
     int passes = 0, running = 1;
     long long iters = 0;
@@ -313,7 +414,7 @@ extern "C" md_status md_batch_descend(md_batch *b, const md_config *cfg, md_stat
             rr = enqueue();
             if (rr != MD_OK) break;
         }
-        launches += 2LL * steps + 1;
+        launches += 2LL * steps * ((nb > 0 ? 1 : 0) + (long long)solo_items.size()) + 1;
         iters++;
         passes += poll;
         cudaError_t ce = cudaMemsetAsync(b->running_d, 0, sizeof(int), st);
@@ -327,6 +428,7 @@ extern "C" md_status md_batch_descend(md_batch *b, const md_config *cfg, md_stat
     }
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
+    release();
     if (rr != MD_OK) return rr;
     if (running > 0) { md_set_error("md_batch_descend: solutions still running after max_pass passes"); return MD_ERR_STATE; }
     if (out) memset(out, 0, sizeof(*out));
@@ -355,7 +457,7 @@ extern "C" md_status md_batch_descend(md_batch *b, const md_config *cfg, md_stat
     }
     if (out) {
         out->launches = launches;
-        out->eval_launches = iters * steps;
+        out->eval_launches = iters * steps * ((nb > 0 ? 1 : 0) + (long long)solo_items.size());
     }
     return MD_OK;
 }

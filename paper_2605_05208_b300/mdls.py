@@ -32,7 +32,8 @@ EXPORTED = (
     "md_moves_destroy", "md_eval_neighborhood", "md_moves_read_leaders", "md_moves_read_dump",
     "md_select_multimove", "md_selection_read", "md_apply_and_rebuild", "md_descend",
     "md_solutions_stats", "md_eval_leaders_noalloc", "md_batch_create", "md_batch_destroy",
-    "md_batch_tune", "md_batch_tuning", "md_batch_set_tuning", "md_batch_descend", "md_instance_build_neighbors",
+    "md_batch_tune", "md_batch_tuning", "md_batch_set_tuning", "md_batch_solo", "md_batch_set_solo",
+    "md_batch_descend", "md_instance_build_neighbors",
     "md_instance_set_neighbors", "md_pruner_create", "md_pruner_destroy", "md_pruner_params",
     "md_pruner_features", "md_pruner_score", "md_pruner_prune", "md_pruner_train",
 )
@@ -132,6 +133,8 @@ def lib() -> C.CDLL:
             "md_batch_tune": [P, P],
             "md_batch_tuning": [P, P, P, P],
             "md_batch_set_tuning": [P, P, P, C.c_int32],
+            "md_batch_solo": [P, P],
+            "md_batch_set_solo": [P, P],
             "md_batch_descend": [P, C.POINTER(Config), C.POINTER(Stats), P],
         }
         for name, args in sigs.items():
@@ -429,6 +432,17 @@ class Batch:
         g = np.zeros(1, dtype=np.int32)
         _check(lib().md_batch_tuning(self.h, _ptr(upw), _ptr(wpc), _ptr(g)))
         return upw, wpc, int(g[0])
+
+    def solo(self):
+        """Which instances run their own single-instance launches (caller order)."""
+        out = np.zeros(len(self.sols_list), np.int32)
+        _check(lib().md_batch_solo(self.h, _ptr(out)))
+        return out
+
+    def set_solo(self, solo):
+        x = np.ascontiguousarray(solo, dtype=np.int32)
+        assert x.shape == (len(self.sols_list),)
+        _check(lib().md_batch_set_solo(self.h, _ptr(x)))
 
     def set_tuning(self, upw=None, wpc=None, grid: int = 0):
         u = None if upw is None else np.ascontiguousarray(upw, dtype=np.int32)

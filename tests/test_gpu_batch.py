@@ -108,3 +108,42 @@ def test_batch_with_shared_customers_matches_per_instance():
     for (_, S), sp, (want, stats) in zip(loaded, specs, ref):
         assert [W.canonical(r, bool(sp.variant & W.VAR_OPEN)) for r in S.read()] == want
         assert np.array_equal(S.stats(), stats)
+
+
+@pytest.mark.parametrize("solo,graph", [([1, 0, 1, 0], True), ([1, 1, 1, 1], True), ([0, 1, 0, 1], False)])
+def test_batch_with_solo_instances_matches_per_instance(case, solo, graph):
+    # instances set solo keep their single-instance launches on streams of their own inside the
+    # batch's graph (or in order on the stream without one); results do not change
+    import torch
+    md, specs, sols, perms = case
+    ref = _reference(md, specs, sols, perms)
+    loaded = [_load(md, sp, so) for sp, so in zip(specs, sols)]
+    B = md.Batch([S for _, S in loaded])
+    assert B.solo().tolist() == [0, 0, 0, 0]
+    B.set_solo(solo)
+    assert B.solo().tolist() == solo
+    st = B.descend(np.concatenate(perms), MAX_PASS, use_graph=graph, stream=torch.cuda.Stream().cuda_stream)
+    total = 0
+    for (_, S), sp, (want_routes, want_stats) in zip(loaded, specs, ref):
+        assert [W.canonical(r, bool(sp.variant & W.VAR_OPEN)) for r in S.read()] == want_routes
+        assert np.array_equal(S.stats(), want_stats)
+        total += int(want_stats[:, 0].sum())
+    assert st.moves_scored == total
+
+
+def test_batch_tune_sets_solo_flags(case):
+    # the autotuner leaves each instance batched or solo; either way the descent is unchanged
+    import torch
+    md, specs, sols, perms = case
+    loaded = [_load(md, sp, so) for sp, so in zip(specs, sols)]
+    B = md.Batch([S for _, S in loaded])
+    stream = torch.cuda.Stream().cuda_stream
+    B.tune(stream=stream)
+    assert set(B.solo().tolist()) <= {0, 1}
+    for (_, S), so in zip(loaded, sols):
+        S.load(so)
+    B.descend(np.concatenate(perms), MAX_PASS, stream=stream)
+    ref = _reference(md, specs, sols, perms)
+    for (_, S), sp, (want_routes, want_stats) in zip(loaded, specs, ref):
+        assert [W.canonical(r, bool(sp.variant & W.VAR_OPEN)) for r in S.read()] == want_routes
+        assert np.array_equal(S.stats(), want_stats)
