@@ -521,6 +521,283 @@ __device__ void eval_swap(const Ctx &C, int cu, int lane, Best &b, int *wl, int 
 }
 
 // ------------------------------------------------------------------------------------------
+// Tile-cooperative Relocate and Swap on neighbour lists.  Each warp of a block prepares one
+// customer u -- what depends on u only goes to a context in shared memory, and u's candidates
+// (at most 64) are split into those on another route and those on u's own route -- and then
+// every thread of the block walks the block's candidates of one kind after the other, each
+// lane reading its candidate's customer context.  The lanes stay busy whatever the customers'
+// list lengths and mixes of the two kinds, and no warp waits idle for the block's slowest
+// customer.  The per-candidate arithmetic is that of eval_relocate and eval_swap.
+// ------------------------------------------------------------------------------------------
+struct RelocCtx {
+    Seg PP, q1, q2, q2r;  // prefix through pred(u); seq(u) of 1 and 2 nodes, and reversed
+    RT oldA, A1, A2;      // u's route now, and without seq(u) of 1 or 2 nodes
+    int u, A, p, pu, su, x, sx, LA, dsA, dV_empty, has2, pad;
+};
+
+struct SwapCtx {
+    Seg PU, u1, u2, u2r;  // prefix through pred(u); seq(u) of 1 and 2 nodes, and reversed
+    RT oldA;
+    int u, A, p, pu, su, x, sx, dsA, hasx, pad;
+};
+
+union TileCtx {
+    RelocCtx r;
+    SwapCtx w;
+};
+
+template <bool TW>
+__device__ __forceinline__ void reloc_setup(const Ctx &C, int cu, RelocCtx &r) {
+    const DevInst &I = C.I;
+    r.u = I.nd + cu;
+    const Seg8 Pu = pre8(C, r.u), Su = suf8(C, r.u);
+    r.A = Pu.a; r.p = Pu.b; r.pu = Su.a; r.su = Su.b;
+    const size_t sA = (size_t)C.s * C.D.R + r.A;
+    const int4 hA = C.D.rhdr[sA];
+    r.LA = hA.x; r.dsA = hA.y;
+    const int deA = hA.z;
+    r.oldA = rt_of(seg_of(ld_seg8(&C.D.rterm[sA])), I);
+    r.PP = prefix_through(C, r.pu);
+    r.A1 = r.LA == 1 ? rt_zero() : rt_of(join_opt<TW>(C, r.PP, r.pu, r.su), I);
+    r.has2 = r.su >= I.nd;
+    r.x = r.has2 ? r.su : -1;
+    r.sx = r.has2 ? suf8(C, r.x).b : MD_NONE;
+    r.A2 = rt_zero();
+    r.q1 = nseg(C, r.u);
+    r.q2 = r.q1;
+    r.q2r = r.q1;
+    if (r.has2) {
+        if (r.LA > 2) r.A2 = rt_of(join_opt<TW>(C, r.PP, r.pu, r.sx), I);
+        r.q2 = join<TW>(C, nseg(C, r.u), r.u, nseg(C, r.x), r.x);
+        r.q2r = join<TW>(C, nseg(C, r.x), r.x, nseg(C, r.u), r.u);
+    }
+    r.dV_empty = ((!C.open && r.dsA != deA) ? -1 : 0) + veh_delta(C.D.dcount[(size_t)C.s * I.nd + r.dsA], I.NV, -1);
+    r.pad = 0;
+}
+
+// candidate v on another route than u's
+template <bool TW>
+__device__ __forceinline__ void reloc_inter(const Ctx &C, const RelocCtx &r, int v, Best &b) {
+    const DevInst &I = C.I;
+    const Seg8 Pv = pre8(C, v), Sv = suf8(C, v);
+    const int B = Pv.a, j = Pv.b, sv = Sv.b;
+    const size_t sB = (size_t)C.s * C.D.R + B;
+    const int dsB = C.D.rhdr[sB].y;
+    const RT oldB = rt_of(seg_of(ld_seg8(&C.D.rterm[sB])), I);
+    const Seg PV = seg_of(Pv);
+    const bool vfirst = j == 1;
+    for (int var = 0; var < 6; var++) {
+        const int k = var >= 2 ? 2 : 1;
+        const bool rev = var >= 4, before = var & 1;
+        if (rev && !C.sym) continue;
+        if (k == 2 && !r.has2) continue;
+        if (before && !vfirst) continue;
+        const Seg &q = k == 1 ? r.q1 : (rev ? r.q2r : r.q2);
+        const int qf = k == 1 ? r.u : (rev ? r.x : r.u);
+        const int ql = k == 1 ? r.u : (rev ? r.u : r.x);
+        Seg nb;
+        if (before) {
+            nb = join_t<TW>(C, nseg(C, dsB), dsB, q, qf);
+            nb = join<TW>(C, nb, ql, seg_of(Sv), v);
+        } else {
+            nb = join_t<TW>(C, PV, v, q, qf);
+            nb = join_opt<TW>(C, nb, ql, sv);
+        }
+        const RT nB = rt_of(nb, I);
+        const RT &nA = k == 1 ? r.A1 : r.A2;
+        const bool emp = r.LA == k;
+        sink(C, make_id32(r.u, v, var), nA.dist + nB.dist - r.oldA.dist - oldB.dist,
+             nA.tw + nB.tw - r.oldA.tw - oldB.tw, nA.lex + nB.lex - r.oldA.lex - oldB.lex,
+             nA.dex + nB.dex - r.oldA.dex - oldB.dex, emp ? r.dV_empty : 0, r.A, B, b);
+    }
+}
+
+// candidate v on u's route
+template <bool TW>
+__device__ __forceinline__ void reloc_intra(const Ctx &C, const RelocCtx &r, int v, Best &b) {
+    const DevInst &I = C.I;
+    const Seg8 Pv = pre8(C, v), Sv = suf8(C, v);
+    const int j = Pv.b, sv = Sv.b;
+    for (int var = 0; var < 6; var++) {
+        const int k = var >= 2 ? 2 : 1;
+        const bool rev = var >= 4, before = var & 1;
+        if (rev && !C.sym) continue;
+        if (k == 2 && !r.has2) continue;
+        if (k == 2 && v == r.x) continue;
+        if (before && j != 1) continue;
+        if (!before && !rev && j == r.p - 1) continue;  // already right after v
+        const int at = before ? 0 : j;  // seq(u) goes right after this position
+        const SN q = k == 1 ? sn(r.q1, r.u, r.u) : (rev ? sn(r.q2r, r.x, r.u) : sn(r.q2, r.u, r.x));
+        SN g;
+        if (at < r.p) {
+            const SN head = at == 0 ? sn(nseg(C, r.dsA), r.dsA, r.dsA) : sn(seg_of(Pv), r.dsA, v);
+            const SN mid = at + 1 <= r.p - 1 ? sub_bwd(C, r.pu, r.p - 2 - at) : sn_none();  // at+1..p-1
+            g = sn_cat<TW>(C, sn_cat<TW>(C, sn_cat_t<TW>(C, head, q), mid), sn_suffix(C, k == 1 ? r.su : r.sx));
+        } else {
+            const SN mid = sub_fwd(C, k == 1 ? r.su : r.sx, at - r.p - k);  // p+k..at
+            g = sn_cat<TW>(C, sn_cat_t<TW>(C, sn_cat<TW>(C, sn(r.PP, r.dsA, r.pu), mid), q), sn_suffix(C, sv));
+        }
+        const RT nA = rt_of(g.s, I);
+        sink(C, make_id32(r.u, v, var), nA.dist - r.oldA.dist, nA.tw - r.oldA.tw, nA.lex - r.oldA.lex,
+             nA.dex - r.oldA.dex, 0, r.A, r.A, b);
+    }
+}
+
+template <bool TW>
+__device__ __forceinline__ void swap_setup(const Ctx &C, int cu, SwapCtx &w) {
+    const DevInst &I = C.I;
+    w.u = I.nd + cu;
+    const Seg8 Pu = pre8(C, w.u), Su = suf8(C, w.u);
+    w.A = Pu.a; w.p = Pu.b; w.pu = Su.a; w.su = Su.b;
+    const size_t sA = (size_t)C.s * C.D.R + w.A;
+    w.dsA = C.D.rhdr[sA].y;
+    w.oldA = rt_of(seg_of(ld_seg8(&C.D.rterm[sA])), I);
+    w.PU = prefix_through(C, w.pu);
+    w.hasx = w.su >= I.nd;
+    w.x = w.hasx ? w.su : -1;
+    w.sx = w.hasx ? suf8(C, w.x).b : MD_NONE;
+    w.u1 = nseg(C, w.u);
+    w.u2 = w.u1;
+    w.u2r = w.u1;
+    if (w.hasx) {
+        w.u2 = join<TW>(C, nseg(C, w.u), w.u, nseg(C, w.x), w.x);
+        w.u2r = join<TW>(C, nseg(C, w.x), w.x, nseg(C, w.u), w.u);
+    }
+    w.pad = 0;
+}
+
+// candidate v on another route than u's (inter) or on u's route (intra)
+template <bool TW, bool INTRA>
+__device__ __forceinline__ void swap_cand(const Ctx &C, const SwapCtx &w, int v, Best &b) {
+    const DevInst &I = C.I;
+    const Seg8 Pv = pre8(C, v), Sv = suf8(C, v);
+    const int B = Pv.a, j = Pv.b, pv = Sv.a, sv = Sv.b;
+    const bool hasy = sv >= I.nd;
+    const int y = hasy ? sv : -1;
+    const int sy = hasy ? suf8(C, y).b : MD_NONE;
+    Seg v1 = nseg(C, v), v2 = v1, v2r = v1;
+    if (hasy) {
+        v2 = join<TW>(C, nseg(C, v), v, nseg(C, y), y);
+        v2r = join<TW>(C, nseg(C, y), y, nseg(C, v), v);
+    }
+    const int nvar = C.sym ? 9 : 4;
+    if (INTRA) {
+        // prefix, one sequence, the customers between them, the other sequence, suffix
+        for (int var = 0; var < nvar; var++) {
+            const int ku = SW_KU[var], kv = SW_KV[var];
+            const bool ru = SW_RU[var], rvv = SW_RV[var];
+            if ((ku == 2 && !w.hasx) || (kv == 2 && !hasy)) continue;
+            if (!(w.p + ku - 1 < j || j + kv - 1 < w.p)) continue;  // overlapping sequences
+            const SN qv = kv == 1 ? sn(v1, v, v) : (rvv ? sn(v2r, y, v) : sn(v2, v, y));
+            const SN qu = ku == 1 ? sn(w.u1, w.u, w.u) : (ru ? sn(w.u2r, w.x, w.u) : sn(w.u2, w.u, w.x));
+            SN g;
+            if (w.p < j) {
+                const SN mid = w.p + ku <= j - 1 ? sub_fwd(C, ku == 1 ? w.su : w.sx, j - 1 - w.p - ku) : sn_none();
+                g = sn_cat<TW>(C, sn(w.PU, w.dsA, w.pu), qv);
+                g = sn_cat<TW>(C, sn_cat_t<TW>(C, sn_cat_t<TW>(C, g, mid), qu), sn_suffix(C, kv == 1 ? sv : sy));
+            } else {
+                const SN mid = j + kv <= w.p - 1 ? sub_bwd(C, w.pu, w.p - 1 - j - kv) : sn_none();
+                g = sn_cat_t<TW>(C, sn(prefix_through(C, pv), w.dsA, pv), qu);
+                g = sn_cat_t<TW>(C, sn_cat<TW>(C, sn_cat<TW>(C, g, mid), qv), sn_suffix(C, ku == 1 ? w.su : w.sx));
+            }
+            const RT nA = rt_of(g.s, I);
+            sink(C, make_id32(w.u, v, var), nA.dist - w.oldA.dist, nA.tw - w.oldA.tw, nA.lex - w.oldA.lex,
+                 nA.dex - w.oldA.dex, 0, w.A, w.A, b);
+        }
+        return;
+    }
+    const size_t sB = (size_t)C.s * C.D.R + B;
+    const RT oldB = rt_of(seg_of(ld_seg8(&C.D.rterm[sB])), I);
+    const Seg PV = prefix_through(C, pv);
+    for (int var = 0; var < nvar; var++) {
+        const int ku = SW_KU[var], kv = SW_KV[var];
+        const bool ru = SW_RU[var], rvv = SW_RV[var];
+        if ((ku == 2 && !w.hasx) || (kv == 2 && !hasy)) continue;
+        // sequence of v placed in A, sequence of u placed in B
+        const Seg &qv = kv == 1 ? v1 : (rvv ? v2r : v2);
+        const int qvf = kv == 1 ? v : (rvv ? y : v), qvl = kv == 1 ? v : (rvv ? v : y);
+        const Seg &qu = ku == 1 ? w.u1 : (ru ? w.u2r : w.u2);
+        const int quf = ku == 1 ? w.u : (ru ? w.x : w.u), qul = ku == 1 ? w.u : (ru ? w.u : w.x);
+        const int afterU = ku == 1 ? w.su : w.sx, afterV = kv == 1 ? sv : sy;
+        Seg na = join<TW>(C, w.PU, w.pu, qv, qvf);
+        na = join_opt_t<TW>(C, na, qvl, afterU);
+        Seg nb = join_t<TW>(C, PV, pv, qu, quf);
+        nb = join_opt<TW>(C, nb, qul, afterV);
+        const RT nA = rt_of(na, I), nB = rt_of(nb, I);
+        sink(C, make_id32(w.u, v, var), nA.dist + nB.dist - w.oldA.dist - oldB.dist,
+             nA.tw + nB.tw - w.oldA.tw - oldB.tw, nA.lex + nB.lex - w.oldA.lex - oldB.lex,
+             nA.dex + nB.dex - w.oldA.dex - oldB.dex, 0, w.A, B, b);
+    }
+}
+
+// Which warp's customer holds flat index f of a kind, given the warps' counts cnt[0..W): returns
+// the warp and leaves f as the index within that warp's candidates.
+__device__ __forceinline__ int flat_owner(const int *cnt, int &f) {
+    int w = 0;
+    while (w < MD_EVAL_WARPS - 1 && f >= cnt[w]) f -= cnt[w++];
+    return w;
+}
+
+// Relocate or Swap of the customers c0 + warp, c0 + cstride + warp, ... of one solution, whose
+// neighbour lists hold at most 64 candidates, by the whole block.  Called by every thread of the
+// block (it synchronises the block); wl: [MD_EVAL_WARPS][64], tc: [MD_EVAL_WARPS] and
+// cnt: [2 MD_EVAL_WARPS] in shared memory.  The lanes' best moves accumulate in b.
+template <bool TW>
+__device__ void eval_tile_lists(const Ctx &C, int op, int c0, int cstride, Best &b, int (*wl)[64], TileCtx *tc,
+                                int *cnt) {
+    const DevInst &I = C.I;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nt = blockDim.x;
+    for (int base = c0; base < I.nc; base += cstride) {
+        const int cu = base + warp;
+        int ni = 0, na = 0;
+        if (cu < I.nc) {
+            int A;
+            if (op == MD_OP_RELOCATE) {
+                RelocCtx r;
+                reloc_setup<TW>(C, cu, r);
+                A = r.A;
+                if (lane == 0) tc[warp].r = r;
+            } else {
+                SwapCtx w;
+                swap_setup<TW>(C, cu, w);
+                A = w.A;
+                if (lane == 0) tc[warp].w = w;
+            }
+            split_candidates(C, cu, I.nd + cu, A, lane, wl[warp], true, 0, I.nnbr[cu], 64, ni, na);
+        }
+        if (lane == 0) {
+            cnt[warp] = ni;
+            cnt[MD_EVAL_WARPS + warp] = na;
+        }
+        __syncthreads();
+        int tot_i = 0, tot_a = 0;
+        for (int w = 0; w < MD_EVAL_WARPS; w++) {
+            tot_i += cnt[w];
+            tot_a += cnt[MD_EVAL_WARPS + w];
+        }
+        // one sweep over both kinds, the intra-route ones from the next warp boundary on, so
+        // that a warp takes one kind per pass and the block's passes are as few as can be
+        const int pad_i = (tot_i + 31) & ~31;
+        for (int f0 = tid; f0 < pad_i + tot_a; f0 += nt) {
+            if (f0 < tot_i) {
+                int f = f0;
+                const int w = flat_owner(cnt, f);
+                const int v = wl[w][f];
+                if (op == MD_OP_RELOCATE) reloc_inter<TW>(C, tc[w].r, v, b);
+                else swap_cand<TW, false>(C, tc[w].w, v, b);
+            } else if (f0 >= pad_i) {
+                int f = f0 - pad_i;
+                const int w = flat_owner(cnt + MD_EVAL_WARPS, f);
+                const int v = wl[w][63 - f];
+                if (op == MD_OP_RELOCATE) reloc_intra<TW>(C, tc[w].r, v, b);
+                else swap_cand<TW, true>(C, tc[w].w, v, b);
+            }
+        }
+        __syncthreads();  // the lists and contexts are read before the next customers overwrite them
+    }
+}
+
+// ------------------------------------------------------------------------------------------
 // 2-opt*: [ds_A..u] + [v..de_B] and [ds_B..pred v] + [succ u..de_A].
 // ------------------------------------------------------------------------------------------
 template <bool TW>

@@ -199,6 +199,8 @@ k_descend_persistent(DevInst I, DevSols D, DevMoves M, uint32_t flags, int wpc_f
     __shared__ double s_w[2][4];
     __shared__ float s_wf[2][4];
     __shared__ int s_wl[MD_EVAL_WARPS][64];
+    __shared__ TileCtx s_tc[MD_EVAL_WARPS];
+    __shared__ int s_cnt[2 * MD_EVAL_WARPS];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int T = Q.T;
     if (tid == 0) {
@@ -234,7 +236,9 @@ k_descend_persistent(DevInst I, DevSols D, DevMoves M, uint32_t flags, int wpc_f
                 const int wpc = C.lists ? 1 : wpc_full;
                 Best b;
                 best_init(b);
-                if (op >= 0)
+                if (C.lists && I.theta <= 64 && (op == MD_OP_RELOCATE || op == MD_OP_SWAP))
+                    eval_tile_lists<TW>(C, op, t * MD_EVAL_WARPS, T * MD_EVAL_WARPS, b, s_wl, s_tc, s_cnt);
+                else if (op >= 0)
                     for (int gw = t * MD_EVAL_WARPS + warp; gw < I.nc * wpc; gw += T * MD_EVAL_WARPS)
                         eval_customer<TW>(C, op, gw / wpc, lane, b, s_wl[warp], gw % wpc, wpc);
                 warp_commit(C, b, (size_t)t * MD_EVAL_WARPS + warp, lane);
