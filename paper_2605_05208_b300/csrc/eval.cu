@@ -26,11 +26,15 @@ __global__ void __launch_bounds__(32 * MD_EVAL_WARPS, MD_EVAL_MIN_BLOCKS) k_eval
     const int op = op_raw < 0 ? -1 : (op_raw & MD_OP_MASK);
     C.lists = I.theta > 0 && !(op_raw >= 0 && (op_raw & MD_OP_SWEEP));
     __shared__ int s_wl[MD_EVAL_WARPS][64];
+    __shared__ TileCtx s_tc[MD_EVAL_WARPS];
+    __shared__ int s_cnt[2 * MD_EVAL_WARPS];
     Best b;
     best_init(b);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
     const int wpc = C.lists ? 1 : wpc_full;
-    if (op >= 0)
+    if (C.lists && I.theta <= 64 && (op == MD_OP_RELOCATE || op == MD_OP_SWAP))
+        eval_tile_lists<TW>(C, op, blockIdx.x * wpb, gridDim.x * wpb, b, s_wl, s_tc, s_cnt);  // the whole block
+    else if (op >= 0)
         for (int gw = blockIdx.x * wpb + warp; gw < I.nc * wpc; gw += gridDim.x * wpb)
             eval_customer<TW>(C, op, gw / wpc, lane, b, s_wl[warp], gw % wpc, wpc);
     warp_commit(C, b, (size_t)blockIdx.x * wpb + warp, lane);
