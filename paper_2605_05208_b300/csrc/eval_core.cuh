@@ -10,7 +10,9 @@
 // summaries gathered by customer id.  An intra-route move (u and v on one route) takes the
 // prefix before and the suffix after the rearranged part from the same summaries and the
 // customers strictly between u's and v's sequences from the route's subsequence tables, so it
-// costs O(1) as well.
+// costs O(1) as well.  On neighbour lists (at most 64 candidates), Relocate and Swap run
+// tile-cooperatively instead: each warp prepares one customer, then the whole block walks the
+// block's candidates together (eval_tile_lists), which keeps the lanes busy.
 //
 // The FP64 penalised delta dF is needed only for the leader (Section 3.2.5): a move whose
 // integer deltas make dF >= 0 certain, or whose FP32 estimate (with a margin ten times its
