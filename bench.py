@@ -45,7 +45,7 @@ ALG_BYTES = {W.OP_RELOCATE: 8, W.OP_SWAP: 16, W.OP_TWO_OPT_STAR: 56, W.OP_DEPOT_
 # --no-cpu-baseline`: the persistent descent kernel (one launch per descent) and, for
 # --persistent 0, the evaluation kernel.  They describe the kernels as committed with them; a
 # change to a kernel makes its figure stale (None: not measured for the current kernel).
-TRAFFIC_6X288 = {"persistent": 6936064, "eval": 880059}
+TRAFFIC_6X288 = {"persistent": 6158438, "eval": None}
 CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -92,10 +92,19 @@ def oracle_sample(pool, n: int, rank: int = 0):
     return moves, wall, cpu
 
 
+def _pool_ready(_):
+    time.sleep(0.2)  # long enough that every worker takes one
+    return os.getpid()
+
+
 def make_pool(n: int):
     from oracle import oracle as O
     O.build()
-    return mp.get_context("spawn").Pool(n)
+    pool = mp.get_context("spawn").Pool(n)
+    # wait until every worker has started (imported this module), so that no worker start-up
+    # competes with the GPU timing for the host's cores
+    pool.map(_pool_ready, range(n), chunksize=1)
+    return pool
 
 
 def run_reference(args):
