@@ -753,6 +753,15 @@ __device__ void eval_tile_lists(const Ctx &C, int op, int c0, int cstride, Best 
         const int cu = base + warp;
         int ni = 0, na = 0;
         if (cu < I.nc) {
+            // the candidates and their routes first: these loads overlap the customer's
+            // preparation, on which they do not depend
+            const int u = I.nd + cu, ncand = I.nnbr[cu];
+            int v[2], B[2];
+            for (int h = 0; h < 2; h++) {
+                const int i = 32 * h + lane;
+                v[h] = i < ncand ? __ldg(&I.nbr[(size_t)cu * I.theta + i]) : u;
+                B[h] = v[h] != u ? C.D.cpre[(size_t)C.s * I.nc + (v[h] - I.nd)].a : -1;
+            }
             int A;
             if (op == MD_OP_RELOCATE) {
                 RelocCtx r;
@@ -765,7 +774,17 @@ __device__ void eval_tile_lists(const Ctx &C, int op, int c0, int cstride, Best 
                 A = w.A;
                 if (lane == 0) tc[warp].w = w;
             }
-            split_candidates(C, cu, I.nd + cu, A, lane, wl[warp], true, 0, I.nnbr[cu], 64, ni, na);
+            // inter-route candidates at the front of the warp's list, intra-route ones at the back
+            const unsigned lt = (1u << lane) - 1u;
+            for (int h = 0; h < 2; h++) {
+                const bool inter = B[h] >= 0 && B[h] != A, intra = B[h] == A;
+                const unsigned mi = __ballot_sync(0xffffffffu, inter), ma = __ballot_sync(0xffffffffu, intra);
+                if (inter) wl[warp][ni + __popc(mi & lt)] = v[h];
+                if (intra) wl[warp][63 - na - __popc(ma & lt)] = v[h];
+                ni += __popc(mi);
+                na += __popc(ma);
+            }
+            __syncwarp();
         }
         if (lane == 0) {
             cnt[warp] = ni;
