@@ -15,12 +15,14 @@
 // A block takes its next task while it finishes the current one: the first of its warps done
 // with a tile tries to take it, so that the queue's round trips overlap the other warps' last
 // customers (a tile only from a long queue: from a short one, an idle block starts it sooner);
-// when it took nothing, thread 0 waits for work at the top of the block's next task.  A block may claim a tile index before it is filled (the claim is a plain add); it
-// keeps the claim, runs steps meanwhile, and takes the tile once it is filled.  Progress: a
-// queued task needs nothing but a block, and every block that waits for work also takes steps,
-// so tiles and steps keep flowing until every solution's descent has ended.  Waits are bounded
-// and restart while the descent progresses: on a timeout the kernel raises a flag and every block
-// stops at its next task.
+// when it took nothing, thread 0 waits for work at the top of the block's next task.  (In a
+// tile-cooperative Relocate or Swap tile the warps finish their sweep together, so the take
+// comes at the tile's end.)  A block may claim a tile index before it is filled (the claim is a
+// plain add); it keeps the claim, runs steps meanwhile, and takes the tile once it is filled.
+// Progress: a queued task needs nothing but a block, and every block that waits for work also
+// takes steps, so tiles and steps keep flowing until every solution's descent has ended.  Waits
+// are bounded and restart while the descent progresses: on a timeout the kernel raises a flag
+// and every block stops at its next task.
 //
 // Ordering: a task's writes are published by the block barrier, then a fence by thread 0 and the
 // queue write; a queue entry is written, fenced, and marked with its index (the consumer reads
