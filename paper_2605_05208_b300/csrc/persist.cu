@@ -14,8 +14,7 @@
 //
 // A block takes its next task while it finishes the current one: the first of its warps done
 // with a tile tries to take it, so that the queue's round trips overlap the other warps' last
-// customers (a tile only from a long queue: from a short one, an idle block starts it sooner);
-// when it took nothing, thread 0 waits for work at the top of the block's next task.  (In a
+// customers; when it took nothing, thread 0 waits for work at the top of the block's next task.  (In a
 // tile-cooperative Relocate or Swap tile the warps finish their sweep together, so the take
 // comes at the tile's end.)  A block may claim a tile index before it is filled (the claim is a
 // plain add); it keeps the claim, runs steps meanwhile, and takes the tile once it is filled.
@@ -312,9 +311,10 @@ md_status md_descend_persistent(md_solutions *s, md_moves *m, uint32_t eflags, i
     // fill a slot whose previous tile it has claimed itself
     Queues Q;
     Q.S = S; Q.T = T; Q.kmax = max_steps;
-    // a busy block claims its next tile ahead only while four solutions' evaluations are queued
-    // (on 32 solutions of 6 x 288 customers: 1, 1 T, 4 T, 16 T and never were measured)
-    Q.lookahead = 4 * T;
+    // a busy block claims its next tile ahead whenever one is queued: on 32 solutions of 6 x 288
+    // customers, thresholds of 1, 2 T, 4 T, 8 T and 16 T queued tiles were measured and 1 was
+    // best (a cooperative tile claims only after its sweep, at the tile's end)
+    Q.lookahead = 1;
     Q.ct = 2 * (S * T + grid) + 64;
     Q.cs = 2 * (S + grid) + 64;
     if ((long long)S * T + (long long)max_steps * S * T >= 0x7fffffffLL) {
