@@ -18,7 +18,7 @@
 // integer deltas make dF >= 0 certain, or whose FP32 estimate (with a margin ten times its
 // rounding bound) is above the lane's best dF so far, cannot be the leader and skips FP64.  B300
 // runs FP64 at a small fraction of its integer rate.  Every warp writes its own leader
-// candidate, so no warp waits for the others of its block.
+// candidate, so on the per-warp path no warp waits for the others of its block.
 //
 // Solution data (summaries, routes, weights) is read with coherent loads: in the persistent
 // descent a block may evaluate summaries that another block's step rewrote in the same launch.
