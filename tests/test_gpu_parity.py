@@ -441,3 +441,27 @@ def test_persistent_descent_edge_cases(md, stream, case):
     if case == "descend-twice":
         # the second descent starts at a local optimum: one pass that applies nothing
         assert runs[1][2].accepted_steps == 0
+
+
+def test_cooperative_tiles_over_several_rounds_match_oracle(md, oracle_lib, stream):
+    # 8300 customers on lists: more customers than the warps of one evaluation (1024 blocks of 8
+    # warps), so the tile-cooperative Relocate and Swap take a second round of customers, in the
+    # graph form's k_eval and in the persistent descent; both against the oracle's descent
+    spec = W.gen_mdvrptw(91, n_depots=6, n_customers=8300, theta=20)
+    sols = W.initial_solutions(spec, 92, 2)
+    max_pass = 2
+    perm = W.op_permutations(93, 2, max_pass)
+    R = min(spec.n_customers, 2 * max(len(x) for x in sols) + 64)
+    K = min(spec.n_customers, 2 * max(len(r) - 2 for x in sols for r in x) + 32)
+    got = []
+    for persistent in (False, True):
+        inst, S = setup(md, spec, sols, R=R, K=K)
+        st = S.descend(perm, max_pass, use_graph=not persistent, stream=stream, persistent=persistent,
+                       multi=True)
+        got.append((canon_all(spec, S.read()), S.stats(), st.moves_scored))
+    assert got[0][0] == got[1][0]
+    assert np.array_equal(got[0][1], got[1][1]) and got[0][2] == got[1][2]
+    o = oracle_lib.Instance(spec)
+    d = o.descend(sols[0], perm[0], max_pass, multi=True)
+    assert got[1][0][0] == canon(spec, d.solution)
+    assert list(got[1][1][0]) == [d.moves_scored, d.steps, d.accepted_steps, d.applied_moves, d.passes]
