@@ -5,6 +5,9 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <mutex>
+#include <unordered_map>
+
 #include "mdls_internal.cuh"
 
 static thread_local char g_err[512] = "";
@@ -22,6 +25,20 @@ md_status md_cuda_check(cudaError_t e, const char *what) {
 }
 
 extern "C" const char *md_last_error(void) { return g_err; }
+
+// Per kernel, the largest dynamic shared memory allowed so far.  The maximum is only ever raised:
+// a launch captured in a graph (or queued) with a larger size than a later launch of the same
+// kernel must stay valid when the graph runs.
+cudaError_t md_allow_smem(const void *func, size_t bytes) {
+    static std::mutex mu;
+    static std::unordered_map<const void *, size_t> allowed;
+    std::lock_guard<std::mutex> lock(mu);
+    size_t &cur = allowed[func];
+    if (bytes <= cur) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) cur = bytes;
+    return e;
+}
 
 // c_ij = round(scale * sqrt(dx^2 + dy^2)), half away from zero, FP64 with no contraction; the
 // block also reduces max, min and sum of c over i != j for Theta and Gamma (Eq. A1).
@@ -214,7 +231,7 @@ extern "C" md_status md_instance_create(const md_instance_desc *desc, md_instanc
         int P = 1;
         while (P < nc) P <<= 1;
         size_t sm = (size_t)P * (sizeof(unsigned long long) + sizeof(int));
-        MDI(cudaFuncSetAttribute(k_nbrs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        MDI(md_allow_smem((const void *)k_nbrs, sm));
         if (e == cudaSuccess) {
             k_nbrs<<<nc, 1024, sm>>>(d, P, I->nbr, I->nnbr);
             e = cudaGetLastError();
@@ -289,7 +306,7 @@ extern "C" md_status md_instance_build_neighbors(md_instance *I, int32_t theta) 
     int P = 1;
     while (P < nc) P <<= 1;
     size_t sm = (size_t)P * (sizeof(unsigned long long) + sizeof(int));
-    MD_CUDA(cudaFuncSetAttribute(k_nbrs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    MD_CUDA(md_allow_smem((const void *)k_nbrs, sm));
     k_nbrs<<<nc, 1024, sm>>>(I->d, P, I->nbr, I->nnbr);
     MD_CUDA(cudaGetLastError());
     MD_CUDA(cudaDeviceSynchronize());

@@ -297,10 +297,10 @@ md_status md_descend_persistent(md_solutions *s, md_moves *m, uint32_t eflags, i
     MD_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const bool tw = (I.variant & MD_VARIANT_TW) != 0;
     if (tw) {
-        MD_CUDA(cudaFuncSetAttribute(k_descend_persistent<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        MD_CUDA(md_allow_smem((const void *)k_descend_persistent<true>, smem));
         MD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_descend_persistent<true>, 32 * MD_EVAL_WARPS, smem));
     } else {
-        MD_CUDA(cudaFuncSetAttribute(k_descend_persistent<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        MD_CUDA(md_allow_smem((const void *)k_descend_persistent<false>, smem));
         MD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_descend_persistent<false>, 32 * MD_EVAL_WARPS, smem));
     }
     if (per_sm < 1) { md_set_error("md_descend: the persistent kernel does not fit an SM"); return MD_ERR_STATE; }

@@ -524,7 +524,7 @@ md_status score_pool(md_pruner *p, md_instance *inst, float *scores_d, cudaStrea
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int grid = (int)(tiles < 2LL * sms ? tiles : 2LL * sms);  // two CTAs (2 x 256 TMEM columns) per SM
-    MD_CUDA(cudaFuncSetAttribute(k_score_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
+    MD_CUDA(md_allow_smem((const void *)k_score_tc, TC_SMEM));
     MD_CUDA(cudaMemsetAsync(p->err, 0, sizeof(int), st));
     if (grid > 0)
         k_score_tc<<<grid, TC_ROWS, TC_SMEM, st>>>(inst->d, inst->nbr, inst->nnbr, pool, aux.a, horizon_of(inst), p->w1h,
@@ -639,7 +639,7 @@ extern "C" md_status md_pruner_prune(md_pruner *p, md_instance *inst, int32_t k,
     int P2 = 1;
     while (P2 < pool) P2 <<= 1;
     const size_t smb = (size_t)P2 * (sizeof(float) + sizeof(int));
-    MD_CUDA(cudaFuncSetAttribute(k_topk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb));
+    MD_CUDA(md_allow_smem((const void *)k_topk, smb));
     k_topk<<<nc, 256, smb, st>>>(nc, inst->nbr, inst->nnbr, pool, P2, sc, k, nb, cnt);
     MD_CUDA(cudaGetLastError());
     MD_CUDA(cudaFreeAsync(sc, st));
@@ -675,7 +675,7 @@ extern "C" md_status md_pruner_train(md_pruner *p, md_instance *inst, const uint
     md_status r = aux.make(inst, st);
     if (r != MD_OK) return r;
     const size_t smb = sizeof(float) * (PR_H * PR_H + 32 * PR_F + 3 * 32 * PR_H + 64);
-    MD_CUDA(cudaFuncSetAttribute(k_train, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb));
+    MD_CUDA(md_allow_smem((const void *)k_train, smb));
     float hl[2] = {0.0f, 0.0f};
     for (int e = 0; e < epochs; e++) {
         MD_CUDA(cudaMemsetAsync(p->loss, 0, sizeof(float) * 2, st));

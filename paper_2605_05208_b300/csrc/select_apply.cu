@@ -57,10 +57,10 @@ md_status md_launch_step_batch(const BatchItem *items, int n_items, int total_so
                                cudaStream_t st) {
     if (total_sols <= 0) return MD_OK;
     if (tw) {
-        MD_CUDA(cudaFuncSetAttribute(k_step_batch<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        MD_CUDA(md_allow_smem((const void *)k_step_batch<true>, smem));
         k_step_batch<true><<<total_sols, STEP_THREADS, smem, st>>>(items, n_items);
     } else {
-        MD_CUDA(cudaFuncSetAttribute(k_step_batch<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        MD_CUDA(md_allow_smem((const void *)k_step_batch<false>, smem));
         k_step_batch<false><<<total_sols, STEP_THREADS, smem, st>>>(items, n_items);
     }
     MD_CUDA(cudaGetLastError());
@@ -69,7 +69,7 @@ md_status md_launch_step_batch(const BatchItem *items, int n_items, int total_so
 
 md_status md_launch_select(md_solutions *s, md_moves *m, int multi, cudaStream_t st) {
     const size_t sm = step_smem(s, STEP_THREADS);
-    MD_CUDA(cudaFuncSetAttribute(k_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    MD_CUDA(md_allow_smem((const void *)k_select, sm));
     k_select<<<s->n_sol, STEP_THREADS, sm, st>>>(s->inst->d, s->d, m->d, multi);
     MD_CUDA(cudaGetLastError());
     return MD_OK;
@@ -78,10 +78,10 @@ md_status md_launch_select(md_solutions *s, md_moves *m, int multi, cudaStream_t
 md_status md_launch_apply(md_solutions *s, md_moves *m, int update_lambda, cudaStream_t st) {
     const size_t sm = step_smem(s, STEP_THREADS);
     if (s->inst->d.variant & MD_VARIANT_TW) {
-        MD_CUDA(cudaFuncSetAttribute(k_apply<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        MD_CUDA(md_allow_smem((const void *)k_apply<true>, sm));
         k_apply<true><<<s->n_sol, STEP_THREADS, sm, st>>>(s->inst->d, s->d, m->d, update_lambda);
     } else {
-        MD_CUDA(cudaFuncSetAttribute(k_apply<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        MD_CUDA(md_allow_smem((const void *)k_apply<false>, sm));
         k_apply<false><<<s->n_sol, STEP_THREADS, sm, st>>>(s->inst->d, s->d, m->d, update_lambda);
     }
     MD_CUDA(cudaGetLastError());
@@ -93,10 +93,10 @@ md_status md_launch_step(md_solutions *s, md_moves *m, cudaStream_t st, int s0, 
     if (count < 0) count = s->n_sol - s0;
     if (count <= 0) return MD_OK;
     if (s->inst->d.variant & MD_VARIANT_TW) {
-        MD_CUDA(cudaFuncSetAttribute(k_step<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        MD_CUDA(md_allow_smem((const void *)k_step<true>, sm));
         k_step<true><<<count, STEP_THREADS, sm, st>>>(s->inst->d, s->d, m->d, s0);
     } else {
-        MD_CUDA(cudaFuncSetAttribute(k_step<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        MD_CUDA(md_allow_smem((const void *)k_step<false>, sm));
         k_step<false><<<count, STEP_THREADS, sm, st>>>(s->inst->d, s->d, m->d, s0);
     }
     MD_CUDA(cudaGetLastError());
