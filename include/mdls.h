@@ -134,11 +134,13 @@ typedef struct md_config {
                                neighbourhood until one applies a move; the descent ends only
                                when a verification pass applies nothing (or at max_pass).
                                0: never (the descent ends at the first pass applying nothing) */
-    int32_t persistent;     /* 1: the whole descent in ONE persistent launch: blocks take, in order
-                               from a device-side counter, each solution's evaluation tiles and
-                               then its step, so every solution advances on its own and steps
-                               overlap other solutions' evaluation; use_graph, poll_every and
-                               n_groups are then unused, and time_eval times the launch.  Same
+    int32_t persistent;     /* 1: the whole descent in ONE persistent launch: each solution's
+                               evaluation tiles and steps go through device-side task queues as
+                               soon as they can run (the last tile of an evaluation queues its
+                               step, a step queues the next evaluation's tiles), so every
+                               solution advances on its own and steps overlap other solutions'
+                               evaluation; use_graph, poll_every and n_groups are then unused,
+                               and time_eval times the launch.  Needs a non-NULL stream.  Same
                                results as 0.  MD_ERR_TIMEOUT if a bounded wait gives up. */
 } md_config;
 
