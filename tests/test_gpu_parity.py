@@ -416,7 +416,8 @@ def test_persistent_descent_edge_cases(md, stream, case):
     if case == "one-solution":
         spec, nsol = W.gen_mdvrptw(81, n_depots=3, n_customers=200, theta=20), 1
     elif case == "tiny-many-solutions":
-        spec, nsol = W.gen_mdvrp(82, n_depots=2, n_customers=12, Q=40, N_V=3), 400
+        # symmetric (reversal variants) on lists of 6: the tile-cooperative Relocate and Swap
+        spec, nsol = W.gen_mdvrp(82, n_depots=2, n_customers=12, Q=40, N_V=3, theta=6), 400
     elif case == "one-pass":
         spec, nsol, max_pass = W.gen_mdvrptw(83, n_depots=4, n_customers=150, theta=20), 6, 1
     else:
