@@ -13,9 +13,10 @@
  *   - route and solution terms of the multi-penalty evaluation function F (Eq. 2 / Eq. A1),
  *     with time windows handled by the time-warp concatenation the paper adopts (Appendix A1,
  *     citing Vidal et al. 2013);
- *   - every move of Relocate, Swap, 2-opt* (Section 3.2.2) and of the two depot operators
- *     Depot-Insert and Depot-Replace (Section 3.2.2, Fig. 1), each evaluated by its plain
- *     definition: the new routes are built explicitly and their terms recomputed from scratch;
+ *   - every move of Relocate, Swap, 2-opt*, 2-opt (Section 3.2.2) and of the two depot
+ *     operators Depot-Insert and Depot-Replace (Section 3.2.2, Fig. 1), each evaluated by its
+ *     plain definition: the new routes are built explicitly and their terms recomputed from
+ *     scratch;
  *   - the leader-follower multi-move selection (Section 3.2.5);
  *   - applying the selected moves and the penalty-coefficient update (Section 3.2.1);
  *   - the MDFIS descent loop of Alg. 2.
@@ -33,6 +34,10 @@
  *     route; Swap exchanges seq(u) and seq(v); 2-opt* joins head(..u) to tail(v..) and
  *     head(..pred v) to tail(succ u..);
  *   - 2-node reversals only when the instance is flagged symmetric;
+ *   - 2-opt (u, v), u and v on one route, the earlier of them at position a, the later at
+ *     b >= a + 2: the customers at a+1 .. b are reversed, so that the route takes the edges
+ *     (c_a, c_b) and (c_{a+1}, c_{b+1}); only on symmetric instances without time windows (the
+ *     paper does not apply 2-opt with time windows);
  *   - Depot-Replace keeps, per (route, depot), the best of its valid cases by (dF, case);
  *   - Depot-Insert splits at interior edges only.
  */
@@ -46,7 +51,7 @@
 #define OR_SYM 4u
 #define OR_NO_LATE (INT64_C(1) << 30)
 
-enum { OP_RELOCATE = 0, OP_SWAP = 1, OP_TWO_OPT_STAR = 2, OP_DEPOT_INSERT = 3, OP_DEPOT_REPLACE = 4 };
+enum { OP_RELOCATE = 0, OP_SWAP = 1, OP_TWO_OPT_STAR = 2, OP_DEPOT_INSERT = 3, OP_DEPOT_REPLACE = 4, OP_TWO_OPT = 5 };
 
 typedef struct OInst {
     int nd, nc, nn;
@@ -554,6 +559,30 @@ static int build_depot_replace(OCtx *C, int u, int d, int cs, OBuilt *B) {
     return 1;
 }
 
+/* 2-opt: on the route holding u and v, with a < b their positions, the customers at positions
+   a+1 .. b are reversed (edges (c_a, c_{a+1}) and (c_b, c_{b+1}) become (c_a, c_b) and
+   (c_{a+1}, c_{b+1}); an open route's last customer has no edge after it).  Symmetric instances
+   without time windows only. */
+static int build_2opt(OCtx *C, int u, int v, int var, OBuilt *B) {
+    const OInst *I = C->I;
+    const OSol *S = C->S;
+    if (var != 0 || u == v) return 0;
+    if (!(I->variant & OR_SYM) || (I->variant & OR_TW)) return 0;
+    int A = C->rt[u];
+    if (A != C->rt[v]) return 0;
+    int a = C->ps[u], b = C->ps[v];
+    if (a > b) { int t = a; a = b; b = t; }
+    if (b < a + 2) return 0; /* a single customer reversed changes nothing */
+    int *n = C->buf[0], nn = 0;
+    nn = put_range(n, nn, S->r[A], 0, a);
+    for (int i = b; i >= a + 1; i--) n[nn++] = S->r[A][i];
+    nn = put_range(n, nn, S->r[A], b + 1, S->len[A] - 1);
+    B->nrem = 0; B->nnew = 0;
+    B->rem[B->nrem++] = A;
+    add_new(B, n, nn);
+    return 1;
+}
+
 static int build_move(OCtx *C, int op, int u, int v, int var, OBuilt *B) {
     B->op = op; B->u = u; B->v = v; B->var = var;
     switch (op) {
@@ -562,6 +591,7 @@ static int build_move(OCtx *C, int op, int u, int v, int var, OBuilt *B) {
     case OP_TWO_OPT_STAR: return build_2optstar(C, u, v, var, B);
     case OP_DEPOT_INSERT: return build_depot_insert(C, u, v, var, B);
     case OP_DEPOT_REPLACE: return build_depot_replace(C, u, v, var, B);
+    case OP_TWO_OPT: return build_2opt(C, u, v, var, B);
     }
     return 0;
 }
@@ -637,7 +667,7 @@ static int64_t enumerate(OCtx *C, int op, const double *w, OMove *out, int64_t c
     int64_t n = 0, scored = 0;
     OBuilt B;
     OMove m;
-    if (op == OP_RELOCATE || op == OP_SWAP || op == OP_TWO_OPT_STAR) {
+    if (op == OP_RELOCATE || op == OP_SWAP || op == OP_TWO_OPT_STAR || op == OP_TWO_OPT) {
         int nv = n_variants(op);
         for (int cu = 0; cu < I->nc; cu++) {
             int u = I->nd + cu;

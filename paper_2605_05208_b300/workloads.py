@@ -44,7 +44,9 @@ OP_SWAP = 1
 OP_TWO_OPT_STAR = 2
 OP_DEPOT_INSERT = 3
 OP_DEPOT_REPLACE = 4
-N_OPS = 5
+OP_TWO_OPT = 5  # intra-route 2-opt: symmetric instances without time windows only
+N_OPS = 5       # the operator set of the benchmark configurations (no 2-opt)
+N_OPS_ALL = 6   # with 2-opt
 
 SCALE = 100  # fixed-point factor for every time value (distances are scaled the same way)
 

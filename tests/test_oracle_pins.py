@@ -669,3 +669,53 @@ def test_pruned_descent_ends_at_a_full_neighbourhood_local_optimum(oracle_lib, s
     d0 = I.descend(sol, perm, 200, sweep_every=0)
     best = min((full.eval_op(d0.solution, op)[0]["dF"].min(initial=0.0) for op in range(W.N_OPS)))
     assert best < 0.0
+
+
+@pytest.mark.parametrize("open_", [False, True])
+def test_two_opt_closed_form_and_reversal(oracle_lib, open_):
+    # 2-opt (Section 3.2.2): on one route, the earlier of u, v at position a and the later at
+    # b >= a + 2, the customers a+1 .. b are reversed.  Against the textbook delta on a symmetric
+    # matrix, c(c_a, c_b) + c(c_a+1, c_b+1) - c(c_a, c_a+1) - c(c_b, c_b+1) (no edge after an open
+    # route's last customer), with the load, the windows and the depots unchanged, and against
+    # the route rebuilt by hand
+    spec = tiny_spec(21, nd=3, nc=30, sym=True, open_=open_, Q=400, NV=3, D=3000 if not open_ else 0)
+    I = oracle_lib.Instance(spec)
+    c = I.dist()
+    sol = random_solution(spec, 21)
+    rt, ps = _pos(sol)
+    lam = (1.0, 1.0, 1.0, 1.0)
+    mv, scored = I.eval_op(sol, W.OP_TWO_OPT, lam)
+    want_pairs = 0  # full neighbourhood: every ordered pair of customers
+    for u in range(spec.n_depots, spec.n_nodes):
+        for v in range(spec.n_depots, spec.n_nodes):
+            if v != u and rt[u] == rt[v] and abs(ps[u] - ps[v]) >= 2:
+                want_pairs += 1
+    assert len(mv) == want_pairs == scored and want_pairs > 10
+    T0, _ = I.solution_terms(sol, lam)
+    for m in mv:
+        op, u, v, var = oracle_lib.unpack_id(m["id"])
+        assert op == W.OP_TWO_OPT and var == 0
+        r = sol[rt[u]]
+        a, b = sorted((ps[u], ps[v]))
+        last = len(r) - 2
+        after_b = None if (open_ and b == last) else r[b + 1]
+        want = c[r[a], r[b]] - c[r[a], r[a + 1]]
+        if after_b is not None:
+            want += c[r[a + 1], after_b] - c[r[b], after_b]
+        assert m["dD"] == want
+        assert m["dLoad"] == 0 and m["dTW"] == 0 and m["dV4"] == 0
+        new = I.apply(sol, [int(m["id"])])
+        rebuilt = r[:a + 1] + r[a + 1:b + 1][::-1] + r[b + 1:]
+        others = [x for x in sol if x is not r]
+        assert W.canonical(new, open_) == W.canonical(others + [rebuilt], open_)
+        T1, _ = I.solution_terms(new, lam)
+        assert T1["D"] - T0["D"] == want and T1["DurEx"] - T0["DurEx"] == m["dDur"]
+
+
+def test_two_opt_only_on_symmetric_instances_without_windows(oracle_lib):
+    for spec in (tiny_spec(22, nd=2, nc=12, tw=True, sym=True, Q=100, NV=2, horizon=3000, wmin=500,
+                           wmax=2000, theta=6),
+                 tiny_spec(23, nd=2, nc=12, sym=False, Q=100, NV=2, theta=6)):
+        I = oracle_lib.Instance(spec)
+        mv, scored = I.eval_op(random_solution(spec, 22), W.OP_TWO_OPT)
+        assert len(mv) == 0 and scored == 0
