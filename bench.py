@@ -39,7 +39,7 @@ THETA = 50
 # must make (distance-matrix entries of the arcs a move creates, plus the route summaries of the
 # second route for 2-opt* and the depot operators); u-independent summaries are amortised.
 ALG_BYTES = {W.OP_RELOCATE: 8, W.OP_SWAP: 16, W.OP_TWO_OPT_STAR: 56, W.OP_DEPOT_INSERT: 32,
-             W.OP_DEPOT_REPLACE: 32}
+             W.OP_DEPOT_REPLACE: 32, W.OP_TWO_OPT: 8}
 # DRAM bytes (read + write) per launch of the dominant kernel of the default workload, from ncu
 # (dram__bytes_read.sum + dram__bytes_write.sum) on `python bench.py --steps 1 --warmup 3
 # --no-cpu-baseline`: the persistent descent kernel (one launch per descent) and, for
@@ -273,7 +273,7 @@ def run_ours(args):
     eval_ms = sum(s.eval_ms for s in stats)
     eval_launches = sum(s.eval_launches for s in stats)
     by_op = np.sum([s.moves_by_op for s in stats], axis=0)
-    alg_bytes = float(sum(int(by_op[o]) * ALG_BYTES[o] for o in range(W.N_OPS)))
+    alg_bytes = float(sum(int(by_op[o]) * ALG_BYTES[o] for o in range(W.N_OPS_ALL)))
     achieved = alg_bytes / (eval_ms / 1e3) / 1e9
     peaks = {}
     try:
@@ -552,7 +552,7 @@ def run_learned(args):
     eval_ms = sum(x.eval_ms for x in sts)
     eval_launches = sum(x.eval_launches for x in sts)
     by_op = np.sum([x.moves_by_op for x in sts], axis=0)
-    alg_bytes = float(sum(int(by_op[o]) * ALG_BYTES[o] for o in range(W.N_OPS)))
+    alg_bytes = float(sum(int(by_op[o]) * ALG_BYTES[o] for o in range(W.N_OPS_ALL)))
     achieved = alg_bytes / (eval_ms / 1e3) / 1e9
     peaks = {}
     try:
@@ -673,7 +673,7 @@ def run_plain_large(args):
     eval_ms = sum(x.eval_ms for x in sts)
     eval_launches = sum(x.eval_launches for x in sts)
     by_op = np.sum([x.moves_by_op for x in sts], axis=0)
-    alg_bytes = float(sum(int(by_op[o]) * ALG_BYTES[o] for o in range(W.N_OPS)))
+    alg_bytes = float(sum(int(by_op[o]) * ALG_BYTES[o] for o in range(W.N_OPS_ALL)))
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))

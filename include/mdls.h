@@ -64,7 +64,12 @@ typedef enum md_status {
 #define MD_OP_TWO_OPT_STAR 2
 #define MD_OP_DEPOT_INSERT 3
 #define MD_OP_DEPOT_REPLACE 4
-#define MD_N_OPS 5
+#define MD_OP_TWO_OPT 5  /* intra-route 2-opt (Section 3.2.2): on the route holding u and v, the
+                            customers from the one after the earlier of them through the later
+                            are reversed (at least two); symmetric instances without time windows
+                            only -- no moves otherwise, as the paper leaves 2-opt out with time
+                            windows.  Variant 0. */
+#define MD_N_OPS 6
 
 /* md_eval_neighborhood flags */
 #define MD_EVAL_DUMP 1u      /* also write every scored move to the moves object's dump list */

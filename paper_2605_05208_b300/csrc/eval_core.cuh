@@ -868,6 +868,41 @@ __device__ void eval_2optstar(const Ctx &C, int cu, int lane, Best &b, int *wl, 
 }
 
 // ------------------------------------------------------------------------------------------
+// 2-opt: on u's route, with a < b the positions of u and a candidate v (b >= a + 2), the
+// customers at a+1 .. b are reversed.  Symmetric instances without time windows only: the
+// reversed customers keep their distance, load and service, so the move changes the distance
+// by four arcs (three after an open route's last customer) and the duration by as much.
+// ------------------------------------------------------------------------------------------
+template <bool TW>
+__device__ void eval_2opt(const Ctx &C, int cu, int lane, Best &b, int *wl, int part, int wpc) {
+    if (TW || !C.sym) return;
+    const DevInst &I = C.I;
+    const int u = I.nd + cu;
+    const Seg8 Pu = pre8(C, u), Su = suf8(C, u);
+    const int A = Pu.a, p = Pu.b, su = Su.b;
+    const Seg oldA = seg_of(ld_seg8(&C.D.rterm[(size_t)C.s * C.D.R + A]));
+    const int dex0 = dur_ex(oldA.dur, I.D);
+    const int ncand = C.lists ? I.nnbr[cu] : I.nc;
+    const int nb = wpc == 1 ? 64 : 32;
+    for (int i0 = part * nb; i0 < ncand; i0 += nb * wpc) {
+        int ni, na;
+        split_candidates(C, cu, u, A, lane, wl, true, i0, ncand, nb, ni, na);
+        for (int k = lane; k < na; k += 32) {
+            const int v = wl[63 - k];
+            const int j = pre8(C, v).b, sv = suf8(C, v).b;
+            if (j - p < 2 && p - j < 2) continue;  // one customer reversed changes nothing
+            // the earlier customer ca with its successor, the later cb with its successor
+            const int ca = p < j ? u : v, na1 = p < j ? su : sv;
+            const int cb = p < j ? v : u, nb1 = p < j ? sv : su;
+            int dD = cost(I, ca, cb) - cost(I, ca, na1);
+            if (nb1 != MD_NONE) dD += cost(I, na1, nb1) - cost(I, cb, nb1);
+            sink(C, make_id32(u, v, 0), dD, 0, 0, dur_ex(oldA.dur + dD, I.D) - dex0, 0, A, A, b);
+        }
+        __syncwarp();  // the list is read before the next batch overwrites it
+    }
+}
+
+// ------------------------------------------------------------------------------------------
 // Depot-Insert (Fig. 1a): split after u = c_k, k < L, at depot d: [ds..u, d] and [d, succ u..de].
 // ------------------------------------------------------------------------------------------
 template <bool TW>
@@ -967,6 +1002,7 @@ __device__ __forceinline__ void eval_customer(const Ctx &C, int op, int cu, int 
     case MD_OP_TWO_OPT_STAR: eval_2optstar<TW>(C, cu, lane, b, wl, part, wpc); break;
     case MD_OP_DEPOT_INSERT: eval_depot_insert<TW>(C, cu, lane, b, part); break;
     case MD_OP_DEPOT_REPLACE: eval_depot_replace<TW>(C, cu, lane, b, part); break;
+    case MD_OP_TWO_OPT: eval_2opt<TW>(C, cu, lane, b, wl, part, wpc); break;
     default: break;
     }
 }

@@ -179,7 +179,7 @@ __device__ void apply_one(const DevInst &I, const DevSols &D, int s, int op, uin
     const int LA = hA.x;
     int B = A, j = 0, LB = 0;
     int4 hB = hA;
-    if (op <= MD_OP_TWO_OPT_STAR) {
+    if (op <= MD_OP_TWO_OPT_STAR || op == MD_OP_TWO_OPT) {
         const Seg8 Pv = D.cpre[(size_t)s * I.nc + (v - I.nd)];
         B = Pv.a;
         j = Pv.b;
@@ -281,6 +281,11 @@ __device__ void apply_one(const DevInst &I, const DevSols &D, int s, int op, uin
         int32_t *rowN = D.rnodes + ((size_t)s * D.R + newslot) * K;
         off = put_range(rowN, 0, S, 0, p + 1, LA, false, lane);
         // route A keeps c_1..c_p in place
+    } else if (op == MD_OP_TWO_OPT) {
+        const int a = p < j ? p : j, bpos = p < j ? j : p;
+        off = put_range(rowA, 0, S, 0, 1, a, false, lane);
+        off = put_range(rowA, off, S, 0, a + 1, bpos, true, lane);
+        off = put_range(rowA, off, S, 0, bpos + 1, LA, false, lane);
     } else {
         if (var == 0 || var == 2) dsA = v;
         if (var == 1 || var == 2) deA = v;

@@ -78,7 +78,7 @@ class Config(C.Structure):
 class Stats(C.Structure):
     _fields_ = [("moves_scored", C.c_int64), ("steps", C.c_int64), ("accepted_steps", C.c_int64),
                 ("applied_moves", C.c_int64), ("passes_max", C.c_int64), ("launches", C.c_int64),
-                ("eval_launches", C.c_int64), ("eval_ms", C.c_double), ("moves_by_op", C.c_int64 * 5)]
+                ("eval_launches", C.c_int64), ("eval_ms", C.c_double), ("moves_by_op", C.c_int64 * 6)]
 
 
 _lib = None

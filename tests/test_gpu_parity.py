@@ -153,7 +153,7 @@ def test_eval_every_move_matches_oracle(md, oracle_lib, case):
     o = oracle_lib.Instance(spec)
     inst, S = setup(md, spec, sols)
     lamv = np.tile(np.asarray(lam, np.float32), (len(sols), 1))
-    for op in range(W.N_OPS):
+    for op in range(W.N_OPS_ALL):
         want = [o.eval_op(sol, op, lam) for sol in sols]
         cap = sum(len(w[0]) for w in want) + 16
         M = md.Moves(S, dump_capacity=cap)
@@ -193,7 +193,7 @@ def test_select_and_apply_match_oracle(md, oracle_lib, case, multi):
         sols = W.initial_solutions(spec, 31, nsol or 4)
     o = oracle_lib.Instance(spec)
     lamv = np.tile(np.asarray(lam, np.float32), (len(sols), 1))
-    for op in range(W.N_OPS):
+    for op in range(W.N_OPS_ALL):
         inst, S = setup(md, spec, sols)
         M = md.Moves(S)
         M.evaluate(np.full(len(sols), op, np.int32), lamv, flags=md.EVAL_FOLLOWERS if multi else 0)
@@ -327,7 +327,7 @@ def test_single_customer_and_single_route(md, oracle_lib):
     sols = [[[0, 3, 1]], [[2, 3, 2]]]
     o = oracle_lib.Instance(spec)
     inst, S = setup(md, spec, sols, R=4, K=2)
-    for op in range(W.N_OPS):
+    for op in range(W.N_OPS_ALL):
         M = md.Moves(S, dump_capacity=64)
         M.evaluate(np.full(2, op, np.int32), flags=md.EVAL_DUMP)
         got = M.dump(64)
@@ -466,3 +466,58 @@ def test_cooperative_tiles_over_several_rounds_match_oracle(md, oracle_lib, stre
     d = o.descend(sols[0], perm[0], max_pass, multi=True)
     assert got[1][0][0] == canon(spec, d.solution)
     assert list(got[1][1][0]) == [d.moves_scored, d.steps, d.accepted_steps, d.applied_moves, d.passes]
+
+
+# ------------------------------------------------------------------------------------------
+# Intra-route 2-opt (Section 3.2.2) in the descent
+# ------------------------------------------------------------------------------------------
+
+def _two_opt_cases():
+    return {
+        "mdvrp-4x50": (W.mdvrp_4x50(101), 6, "initial"),
+        "mdovrp-4x150": (W.gen_mdovrp(102, n_depots=4, n_customers=150), 3, "initial"),
+        "mdvrp-3x300-theta20": (W.gen_mdvrp(103, n_depots=3, n_customers=300, theta=20), 4, "initial"),
+        # long random routes: many reversals of more than 32 customers
+        "tiny-sym-long": (tiny_spec(104, nd=3, nc=90, sym=True, Q=400, NV=2, theta=12), 3, "random"),
+    }
+
+
+@pytest.mark.parametrize("case", list(_two_opt_cases()))
+@pytest.mark.parametrize("form", ["graph", "persistent"])
+def test_descent_with_two_opt_matches_oracle(md, oracle_lib, stream, case, form):
+    # the six-operator set (the five of the benchmark configurations plus 2-opt) on symmetric
+    # instances without time windows: final solutions and every counter against the oracle
+    spec, nsol, init = _two_opt_cases()[case]
+    if init == "random":
+        sols = [random_solution(spec, 400 + i, max_len=40) for i in range(nsol)]
+    else:
+        sols = W.initial_solutions(spec, 105, nsol)
+    max_pass = 60
+    perm = W.op_permutations(106, nsol, max_pass, op_list=tuple(range(W.N_OPS_ALL)))
+    inst, S = setup(md, spec, sols)
+    st = S.descend(perm, max_pass, multi=True, use_graph=(form == "graph"), stream=stream,
+                   persistent=(form == "persistent"))
+    got = S.read()
+    per = S.stats()
+    o = oracle_lib.Instance(spec)
+    for s, sol in enumerate(sols):
+        d = o.descend(sol, perm[s], max_pass, multi=True)
+        assert canon(spec, got[s]) == canon(spec, d.solution), s
+        assert list(per[s]) == [d.moves_scored, d.steps, d.accepted_steps, d.applied_moves, d.passes], s
+    assert sum(st.moves_by_op) == st.moves_scored and st.moves_by_op[W.OP_TWO_OPT] > 0
+
+
+def test_two_opt_is_empty_with_time_windows_or_asymmetric_costs(md, oracle_lib):
+    # 2-opt scores nothing on an instance with time windows or on an asymmetric one; the leader
+    # stays empty on both sides
+    for spec in (tiny_spec(107, nd=3, nc=40, tw=True, Q=30, NV=2, D=250, horizon=1500, wmin=60, wmax=500),
+                 tiny_spec(108, nd=3, nc=40, Q=30, NV=2)):
+        sols = [random_solution(spec, 500 + i, max_len=8) for i in range(2)]
+        o = oracle_lib.Instance(spec)
+        inst, S = setup(md, spec, sols)
+        M = md.Moves(S, dump_capacity=64)
+        M.evaluate(np.full(2, W.OP_TWO_OPT, np.int32), flags=md.EVAL_DUMP)
+        ids, f, n = M.leaders()
+        assert len(M.dump(64)) == 0 and list(n) == [0, 0] and list(ids) == [0, 0]
+        assert all(len(o.eval_op(sol, W.OP_TWO_OPT)[0]) == 0 for sol in sols)
+        M.close()
