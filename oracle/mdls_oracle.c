@@ -950,3 +950,151 @@ int or_descend(const OInst *I, const int32_t *nodes, const int64_t *off, int nr,
     sol_free(S);
     return r;
 }
+
+/* ------------------------------------------------------------------------------------------ */
+/* Repair insertion (Section 3.3, the insertion step of the DCREX crossover, Alg. 3)           */
+/* ------------------------------------------------------------------------------------------ */
+
+enum { INS_FBI = 0, INS_IBI = 1, INS_FRI = 2, INS_IRI = 3 };
+
+/* Readings (the paper names the four rules and their intent only):
+   - an insertion puts customer u after position k of a route (k = 0: after the departure
+     depot; k = L: after the last customer); its cost is the change of the route's travel
+     distance, found by building the new route and recomputing its terms;
+   - it is feasible when the new route has no capacity excess, no time warp and no duration
+     excess;
+   - FBI / FRI consider feasible insertions only; IBI / IRI consider every insertion;
+   - best insertion (FBI, IBI) inserts, among all unrouted customers, the one with the cheapest
+     insertion, ties by the customer's place in the unrouted list, then route, then position;
+   - regret insertion (FRI, IRI): per customer, the best insertion and the best insertion into
+     any other route; the regret is their cost difference (unbounded when no other route can
+     take it); the customer of largest regret goes first, ties by the cheaper best insertion,
+     then by its place in the list; it is inserted at its best insertion;
+   - when no unrouted customer has a feasible insertion (FBI, FRI), or the solution has no
+     route at all, the first customer of the list opens a new route [d, u, d] at the depot d
+     with a free vehicle that is nearest to it (c(d, u) + c(u, d), open routes c(d, u) only),
+     any depot when none has a free vehicle, ties by depot index; the route is appended;
+   - IBI and IRI never open a route while one exists. */
+
+typedef struct { int64_t c; int r, k; } OIns;
+
+/* Cheapest insertion of u into route r (feasible only when feas); returns 0 if none. */
+static int best_in_route(const OInst *I, const OSol *S, int r, int u, int feas, OIns *out, int *buf) {
+    const int len = S->len[r];
+    const OTerms old = route_terms(I, S->r[r], len);
+    int found = 0;
+    for (int k = 0; k <= len - 2; k++) {
+        int n = 0;
+        n = put_range(buf, n, S->r[r], 0, k);
+        buf[n++] = u;
+        n = put_range(buf, n, S->r[r], k + 1, len - 1);
+        const OTerms t = route_terms(I, buf, n);
+        if (feas && (t.loadEx != 0 || t.tw != 0 || t.durEx != 0)) continue;
+        const int64_t c = t.dist - old.dist;
+        if (!found || c < out->c) { out->c = c; out->r = r; out->k = k; found = 1; }
+    }
+    return found;
+}
+
+static void open_route(const OInst *I, OSol *S, int u) {
+    int64_t *cnt = (int64_t *)calloc(I->nd, sizeof(int64_t));
+    for (int i = 0; i < S->nr; i++) cnt[S->r[i][0]]++;
+    int best = -1;
+    int64_t bc = 0;
+    for (int pass = 0; pass < 2 && best < 0; pass++)
+        for (int d = 0; d < I->nd; d++) {
+            if (pass == 0 && cnt[d] >= I->NV) continue;
+            int64_t c = I->c[(size_t)d * I->nn + u];
+            if (!(I->variant & OR_OPEN)) c += I->c[(size_t)u * I->nn + d];
+            if (best < 0 || c < bc) { best = d; bc = c; }
+        }
+    free(cnt);
+    if (S->nr == S->cap) {
+        S->cap = 2 * S->cap + 8;
+        S->r = (int **)realloc(S->r, sizeof(int *) * S->cap);
+        S->len = (int *)realloc(S->len, sizeof(int) * S->cap);
+    }
+    int *nr = (int *)malloc(sizeof(int) * 3);
+    nr[0] = best; nr[1] = u; nr[2] = best;
+    S->r[S->nr] = nr;
+    S->len[S->nr] = 3;
+    S->nr++;
+}
+
+/* Inserts the unrouted customers (in list order `unrouted`) into the partial solution by rule
+   op; writes the repaired solution and the customers in the order they were inserted.  Returns
+   the number of routes, or -1 if the output buffers are too small. */
+int or_repair(const OInst *I, const int32_t *nodes, const int64_t *off, int nr, const int32_t *unrouted,
+              int nu, int op, int32_t *out_nodes, int64_t *out_off, int64_t node_cap, int route_cap,
+              int32_t *order) {
+    OSol *S = sol_from_flat(nodes, off, nr);
+    int *U = (int *)malloc(sizeof(int) * (nu > 0 ? nu : 1));
+    for (int i = 0; i < nu; i++) U[i] = unrouted[i];
+    const int feas = op == INS_FBI || op == INS_FRI;
+    const int regret = op == INS_FRI || op == INS_IRI;
+    int *buf = (int *)malloc(sizeof(int) * (I->nc + 2));
+    int done = 0;
+    while (nu > 0) {
+        int pick = -1;
+        OIns pins;
+        int64_t pick_reg = 0;
+        int pick_inf = 0;
+        for (int i = 0; i < nu && S->nr > 0; i++) {
+            OIns b1, cur;
+            int have1 = 0, have2 = 0;
+            int64_t c2 = 0;
+            for (int r = 0; r < S->nr; r++) {
+                if (!best_in_route(I, S, r, U[i], feas, &cur, buf)) continue;
+                if (!have1 || cur.c < b1.c) {
+                    if (have1) { c2 = have2 && c2 < b1.c ? c2 : b1.c; have2 = 1; }
+                    b1 = cur;
+                    have1 = 1;
+                } else if (!have2 || cur.c < c2) {
+                    c2 = cur.c;
+                    have2 = 1;
+                }
+            }
+            if (!have1) continue;
+            int better;
+            if (!regret) {
+                better = pick < 0 || b1.c < pins.c;
+            } else {
+                const int inf = !have2;
+                const int64_t reg = have2 ? c2 - b1.c : 0;
+                if (pick < 0) better = 1;
+                else if (inf != pick_inf) better = inf;
+                else if (!inf && reg != pick_reg) better = reg > pick_reg;
+                else better = b1.c < pins.c;
+                if (better) { pick_inf = inf; pick_reg = reg; }
+            }
+            if (better) { pick = i; pins = b1; }
+        }
+        int u;
+        if (pick < 0) {
+            /* no route, or (FBI / FRI) no feasible insertion for any customer */
+            if (!feas && S->nr > 0) break; /* unreachable: every customer fits a route somewhere */
+            u = U[0];
+            pick = 0;
+            open_route(I, S, u);
+        } else {
+            u = U[pick];
+            const int r = pins.r, k = pins.k, len = S->len[r];
+            int *nrte = (int *)malloc(sizeof(int) * (len + 1));
+            int n = put_range(nrte, 0, S->r[r], 0, pins.k);
+            nrte[n++] = u;
+            n = put_range(nrte, n, S->r[r], k + 1, len - 1);
+            free(S->r[r]);
+            S->r[r] = nrte;
+            S->len[r] = n;
+        }
+        if (order) order[done] = u;
+        done++;
+        for (int i = pick; i + 1 < nu; i++) U[i] = U[i + 1];
+        nu--;
+    }
+    int r = sol_to_flat(S, out_nodes, out_off, node_cap, route_cap);
+    free(buf);
+    free(U);
+    sol_free(S);
+    return r;
+}

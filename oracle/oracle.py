@@ -90,8 +90,14 @@ def lib():
                                  f32p, i32p, i64p, C.c_int64, C.c_int, C.POINTER(OStats), P, C.c_int,
                                  C.c_int]
         L.or_inst_set_nbrs.argtypes = [P, i32p, i32p, C.c_int]
+        L.or_repair.restype = C.c_int
+        L.or_repair.argtypes = [P, i32p, i64p, C.c_int, i32p, C.c_int, C.c_int, i32p, i64p, C.c_int64,
+                                C.c_int, i32p]
         _lib = L
     return _lib
+
+
+INS_FBI, INS_IBI, INS_FRI, INS_IRI = 0, 1, 2, 3  # repair insertion rules (Section 3.3)
 
 
 def _flat(sol):
@@ -227,6 +233,22 @@ class Instance:
         lib().or_inst_set_nbrs(self.h, nbr.reshape(-1) if theta else np.zeros(1, np.int32),
                                cnt if theta else np.zeros(max(self.nc, 1), np.int32), theta)
         self.theta = theta
+
+    def repair(self, sol, unrouted, op):
+        """Repair insertion (Section 3.3): inserts the customers of `unrouted` (in that order of
+        preference) into the partial solution `sol` by rule op (INS_FBI, INS_IBI, INS_FRI,
+        INS_IRI).  Returns (repaired solution, customers in the order they were inserted)."""
+        nodes, off = _flat(sol) if sol else (np.zeros(1, np.int32), np.zeros(1, np.int64))
+        un = np.ascontiguousarray(unrouted if len(unrouted) else [0], dtype=np.int32)
+        cap_r = len(sol) + len(unrouted) + 8
+        cap_n = (len(nodes) if sol else 0) + 3 * len(unrouted) + 16
+        on = np.zeros(cap_n, dtype=np.int32)
+        oo = np.zeros(cap_r + 1, dtype=np.int64)
+        order = np.zeros(max(len(unrouted), 1), dtype=np.int32)
+        nr = lib().or_repair(self.h, nodes, off, len(sol), un, len(unrouted), int(op), on, oo, cap_n, cap_r,
+                             order)
+        assert nr >= 0
+        return _unflat(on, oo, nr), [int(x) for x in order[:len(unrouted)]]
 
     def descend(self, sol, perm, max_pass, multi=True, lambda_update=False, lam=(1, 1, 1, 1),
                 trace=False, sweep_every=0) -> Descent:

@@ -719,3 +719,176 @@ def test_two_opt_only_on_symmetric_instances_without_windows(oracle_lib):
         I = oracle_lib.Instance(spec)
         mv, scored = I.eval_op(random_solution(spec, 22), W.OP_TWO_OPT)
         assert len(mv) == 0 and scored == 0
+
+
+# ------------------------------------------------------------------------------------------
+# Repair insertion (Section 3.3): FBI, IBI, FRI, IRI
+# ------------------------------------------------------------------------------------------
+
+def _ins_cost(c, route, k, u, open_):
+    """Closed form of inserting u after position k of route [ds, c_1..c_L, de]."""
+    a = route[k]
+    if open_ and k == len(route) - 2:
+        return int(c[a, u])  # after the last customer of an open route: one new arc
+    b = route[k + 1]
+    return int(c[a, u] + c[u, b] - c[a, b])
+
+
+def _feasible(spec, c, route):
+    """Load, time warp and duration of a route checked without the oracle: sums of demands,
+    brute force over departure times with windows, the closed form travel + service without."""
+    q, s = spec.demand.astype(np.int64), spec.service.astype(np.int64)
+    open_ = bool(spec.variant & W.VAR_OPEN)
+    if sum(int(q[n]) for n in route[1:-1]) > spec.Q:
+        return False
+    if spec.variant & W.VAR_TW:
+        warp, dur, _ = brute_schedule(route, c, spec.tw_early.astype(np.int64), spec.tw_late.astype(np.int64),
+                                      s, open_)
+        if warp > 0:
+            return False
+    else:
+        last = len(route) - 2 if open_ else len(route) - 1
+        dur = sum(int(c[route[j], route[j + 1]]) for j in range(last)) + sum(int(s[n]) for n in route[:last + 1])
+    return not (spec.D > 0 and dur > spec.D)
+
+
+def _replay_repair(spec, c, sol, unrouted, op):
+    """The insertion rules restated over closed-form costs and independent feasibility checks."""
+    open_ = bool(spec.variant & W.VAR_OPEN)
+    feas_only = op in (0, 2)
+    regret = op in (2, 3)
+    S = [list(r) for r in sol]
+    U = list(unrouted)
+    order = []
+    while U:
+        pick = None
+        for i, u in enumerate(U):
+            per_route = []
+            for r, route in enumerate(S):
+                opts = []
+                for k in range(len(route) - 1):
+                    new = route[:k + 1] + [u] + route[k + 1:]
+                    if feas_only and not _feasible(spec, c, new):
+                        continue
+                    opts.append((_ins_cost(c, route, k, u, open_), k))
+                if opts:
+                    cost, k = min(opts)
+                    per_route.append((cost, r, k))
+            if not per_route:
+                continue
+            per_route.sort()
+            best = per_route[0]
+            if regret:
+                reg = math.inf if len(per_route) == 1 else per_route[1][0] - best[0]
+                key = (-reg, best[0], i)
+            else:
+                key = (best[0], i)
+            if pick is None or key < pick[0]:
+                pick = (key, i, best)
+        if pick is None:
+            u = U.pop(0)
+            cnt = [sum(1 for r in S if r[0] == d) for d in range(spec.n_depots)]
+            cost = lambda d: int(c[d, u]) + (0 if open_ else int(c[u, d]))
+            free = [d for d in range(spec.n_depots) if cnt[d] < spec.N_V] or list(range(spec.n_depots))
+            d = min(free, key=lambda x: (cost(x), x))
+            S.append([d, u, d])
+        else:
+            _, i, (cost, r, k) = pick
+            u = U.pop(i)
+            S[r] = S[r][:k + 1] + [u] + S[r][k + 1:]
+        order.append(u)
+    return S, order
+
+
+def _repair_case(which, seed):
+    if which == "mdvrp":
+        spec = tiny_spec(seed, nd=3, nc=24, Q=30, NV=3, D=0)
+    elif which == "mdovrp":
+        spec = tiny_spec(seed, nd=2, nc=22, open_=True, sym=True, Q=35, NV=3)
+    else:
+        spec = tiny_spec(seed, nd=2, nc=16, tw=True, Q=40, NV=3, D=160, horizon=250, wmin=30, wmax=150)
+    sol = random_solution(spec, seed + 7, max_len=5)
+    st = W.Stream(seed, 8)
+    # drop some routes whole and some single customers, as the route exchange leaves them
+    keep, unrouted = [], []
+    for r in sol:
+        if st.uniform(1)[0] < 0.3:
+            unrouted += r[1:-1]
+            continue
+        cs = [x for x in r[1:-1] if st.uniform(1)[0] >= 0.15 or len(r) == 3]
+        unrouted += [x for x in r[1:-1] if x not in cs]
+        keep.append([r[0]] + cs + [r[-1]])
+    perm = np.argsort(st.u64(len(unrouted)))
+    return spec, keep, [unrouted[i] for i in perm]
+
+
+@pytest.mark.parametrize("which", ["mdvrp", "mdovrp", "mdvrptw"])
+@pytest.mark.parametrize("op", [0, 1, 2, 3])
+def test_repair_matches_closed_form_replay(oracle_lib, which, op):
+    # every decision of the four rules replayed with closed-form insertion costs and
+    # feasibility checked by demand sums and brute force over departure times
+    for seed in (3, 4, 5):
+        spec, keep, unrouted = _repair_case(which, seed + 10 * op)
+        assert unrouted
+        c = cmat(spec)
+        got, order = oracle_lib.Instance(spec).repair(keep, unrouted, op)
+        want, worder = _replay_repair(spec, c, keep, unrouted, op)
+        assert order == worder and got == want, (seed, op)
+
+
+def test_repair_keeps_partial_routes_and_routes_every_customer(oracle_lib):
+    spec, keep, unrouted = _repair_case("mdvrptw", 21)
+    for op in range(4):
+        got, order = oracle_lib.Instance(spec).repair(keep, unrouted, op)
+        assert sorted(x for r in got for x in r[1:-1]) == list(range(spec.n_depots, spec.n_nodes))
+        assert sorted(order) == sorted(unrouted)
+        # removing the inserted customers gives the partial routes back, in order; new routes last
+        stripped = [[x for x in r if x not in set(unrouted)] for r in got]
+        assert stripped[:len(keep)] == keep
+        assert all(len(r) == 2 for r in stripped[len(keep):])
+        if op in (1, 3):
+            assert len(got) == len(keep)  # IBI and IRI open no route while one exists
+
+
+def test_repair_single_customer_is_cheapest_insertion(oracle_lib):
+    spec = tiny_spec(31, nd=3, nc=30, Q=10 ** 6, NV=5)
+    c = cmat(spec)
+    sol = random_solution(spec, 32, max_len=6)
+    for victim in (spec.n_depots, spec.n_depots + 11, spec.n_nodes - 1):
+        keep = [[x for x in r if x != victim] for r in sol]
+        keep = [r for r in keep if len(r) > 2]
+        opts = [(_ins_cost(c, r, k, victim, False), ri, k) for ri, r in enumerate(keep) for k in range(len(r) - 1)]
+        cost, ri, k = min(opts)
+        want = [list(r) for r in keep]
+        want[ri] = want[ri][:k + 1] + [victim] + want[ri][k + 1:]
+        for op in range(4):
+            got, _ = oracle_lib.Instance(spec).repair(keep, [victim], op)
+            assert got == want, op
+
+
+def test_repair_regret_on_one_route_is_best_insertion(oracle_lib):
+    # with a single route every regret is unbounded, so the regret rules fall back to the
+    # cheaper best insertion: IRI repeats IBI exactly
+    spec = tiny_spec(33, nd=2, nc=20, Q=10 ** 6, NV=2)
+    nd = spec.n_depots
+    keep = [[0, nd, nd + 1, 0]]
+    unrouted = list(range(nd + 2, spec.n_nodes))[::-1]
+    I = oracle_lib.Instance(spec)
+    assert I.repair(keep, unrouted, 3) == I.repair(keep, unrouted, 1)
+
+
+def test_repair_without_feasible_insertions_opens_routes_at_nearest_free_depot(oracle_lib):
+    # capacity below any two demands: every customer opens its own route, at the nearest depot
+    # while that depot has a vehicle left, else the nearest with one, else the nearest
+    spec = tiny_spec(34, nd=2, nc=5, Q=12, NV=2)
+    spec.demand[spec.n_depots:] = 7
+    c = cmat(spec)
+    unrouted = list(range(spec.n_depots, spec.n_nodes))
+    got, order = oracle_lib.Instance(spec).repair([], unrouted, 0)
+    assert order == unrouted and all(len(r) == 3 for r in got)
+    cnt = [0, 0]
+    for r, u in zip(got, unrouted):
+        free = [d for d in (0, 1) if cnt[d] < 2] or [0, 1]
+        d = min(free, key=lambda x: (int(c[x, u] + c[u, x]), x))
+        assert r == [d, u, d]
+        cnt[d] += 1
