@@ -288,6 +288,50 @@ md_status md_descend(md_solutions *sols, const md_config *cfg, md_stats *out, vo
  * steps, applied moves, passes. */
 md_status md_solutions_stats(md_solutions *sols, int64_t *per_sol, void *stream);
 
+/* Repair insertion rules (Section 3.3, the insertion step of the route-exchange crossover).
+ * The cost of inserting customer u after position k of a route is the change of its travel
+ * distance, c(c_k, u) + c(u, c_{k+1}) - c(c_k, c_{k+1}) (one arc c(c_L, u) after the last
+ * customer of an open route); an insertion is feasible when the new route has no load excess,
+ * no time warp and no duration excess.
+ *   MD_INSERT_FBI  feasible best insertion: the cheapest feasible insertion of any unrouted
+ *                  customer, ties by the customer's place in the list, then route slot, then
+ *                  position;
+ *   MD_INSERT_IBI  infeasible best insertion: the same over every insertion;
+ *   MD_INSERT_FRI  feasible regret insertion: per customer, its best feasible insertion and its
+ *                  best feasible insertion into any other route; the customer of largest regret
+ *                  (their cost difference, unbounded when no other route takes it) goes first,
+ *                  ties by the cheaper best insertion, then the list; it goes to its best
+ *                  insertion;
+ *   MD_INSERT_IRI  infeasible regret insertion: the same over every insertion.
+ * FBI and FRI open a route [d, u, d] for the first listed customer when no listed customer has
+ * a feasible insertion: d is the depot nearest to u (c(d, u) + c(u, d); c(d, u) for open
+ * routes) among those with fewer than N_V routes, else among all, ties by index.  IBI and IRI
+ * open a route only when the solution has none.  New routes take the first free slot. */
+#define MD_INSERT_FBI 0
+#define MD_INSERT_IBI 1
+#define MD_INSERT_FRI 2
+#define MD_INSERT_IRI 3
+
+/* Loads partial solutions and inserts their unrouted customers by `rule` (MD_INSERT_*), one
+ * CTA per solution on the device; on return sols holds complete solutions with every summary
+ * and total rebuilt (lambda reset to 1), ready for md_descend.
+ *   route_nodes / route_offsets / routes_per_sol: host, the md_solutions_load layout, except
+ *     that a solution may have no route (routes_per_sol[s] = 0) and leaves customers out;
+ *     route_nodes and route_offsets may be NULL when no solution has a route;
+ *   unrouted: host int32, solution s's unrouted customers at unrouted[unrouted_offsets[s] ..
+ *     unrouted_offsets[s + 1]) in order of preference (the tie-break); unrouted_offsets: host
+ *     int64 [n_sol + 1], unrouted_offsets[0] = 0;
+ *   order: optional host int32 [unrouted_offsets[n_sol]], receives per solution the customers in
+ *     the order they were inserted.
+ * MD_ERR_ARG unless every customer appears exactly once per solution (in a route or in its
+ * list) and the routes are well formed; MD_ERR_CAPACITY when a route would exceed k_max or a
+ * new route finds no free slot (the solution then holds a partial repair).  Synchronises the
+ * stream. */
+md_status md_repair_insert(md_solutions *sols, int32_t rule, const int32_t *route_nodes,
+                           const int64_t *route_offsets, const int32_t *routes_per_sol,
+                           const int32_t *unrouted, const int64_t *unrouted_offsets, int32_t *order,
+                           void *stream);
+
 /* Batches of instances of uneven size.  A batch groups solution sets of different instances
  * (each from md_solutions_create/load on the same device, each still owned by the caller) so
  * that every solution of every instance advances with ONE evaluation launch and ONE select/apply

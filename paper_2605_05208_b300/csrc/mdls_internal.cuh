@@ -253,6 +253,8 @@ cudaError_t md_allow_smem(const void *func, size_t bytes);
 // Launchers implemented in the .cu files.
 md_status md_launch_rebuild_all(md_solutions *s, cudaStream_t st);
 md_status md_launch_totals(md_solutions *s, cudaStream_t st);
+md_status md_load_routes(md_solutions *S, const int32_t *nodes, const int64_t *off, const int32_t *per_sol,
+                         bool partial, cudaStream_t st);
 // s0 / count restrict a launch to solutions s0 .. s0 + count - 1 (count < 0: all from s0).
 md_status md_launch_eval(md_solutions *s, md_moves *m, uint32_t flags, cudaStream_t st, int s0 = 0, int count = -1);
 md_status md_launch_select(md_solutions *s, md_moves *m, int multi, cudaStream_t st);

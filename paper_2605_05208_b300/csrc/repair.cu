@@ -1,0 +1,337 @@
+// repair.cu -- repair insertion (Section 3.3): the unrouted customers of partial solutions are
+// inserted one at a time by feasible / infeasible best insertion (FBI, IBI) or feasible /
+// infeasible regret insertion (FRI, IRI), for many solutions at once.
+//
+// One CTA per solution runs the whole repair.  Each round evaluates every insertion of every
+// unrouted customer: warp w takes customers w, w+8, ... of the list, its lanes take the route
+// slots, and a lane walks the L+1 positions of its route.  An insertion after position k joins
+// three summaries that already exist -- the prefix [ds..c_k] (cpre of c_k, or the depot), the
+// customer, the suffix [c_{k+1}..de] (csuf of c_{k+1}, or the depot) -- so its cost and its
+// feasibility (load, time warp, duration) take O(1) per position; the cost is the closed form
+// c(c_k, u) + c(u, c_{k+1}) - c(c_k, c_{k+1}).  Per customer the warp keeps the best insertion
+// and the best insertion into any other route (for the regret); the block then picks the
+// customer by the rule, warp 0 inserts it and rebuilds that route's summaries, and the next
+// round starts.  Ties break as the rules state: cost, then the customer's place in the list,
+// then route slot, then position.
+#include <limits.h>
+#include <string.h>
+
+#include <vector>
+
+#include "route_build.cuh"
+
+namespace {
+
+struct InsBest {  // one customer's best insertion and its best cost in another route
+    int c1, r1, k1, c2;  // r1 < 0: none; c2 = INT_MAX: no other route
+};
+
+__device__ __forceinline__ int dcost(const DevInst &I, int a, int b) { return __ldg(&I.dist[(size_t)a * I.nn + b]); }
+
+__device__ __forceinline__ Seg nodeseg(const DevInst &I, int n) { return node_seg(__ldg(&I.node[n])); }
+
+// Folds route best (c, r, k) into a lane's pair; routes arrive in increasing slot order.
+__device__ __forceinline__ void ins_push(InsBest &b, int c, int r, int k) {
+    if (b.r1 < 0 || c < b.c1) {
+        if (b.r1 >= 0) b.c2 = min(b.c2, b.c1);
+        b.c1 = c; b.r1 = r; b.k1 = k;
+    } else {
+        b.c2 = min(b.c2, c);
+    }
+}
+
+// Merges two lanes' pairs (disjoint route sets): the better best by (cost, slot); the second is
+// the smaller of the winner's second and the loser's best.
+__device__ __forceinline__ InsBest ins_merge(const InsBest &a, const InsBest &o) {
+    const bool take_o = o.r1 >= 0 && (a.r1 < 0 || o.c1 < a.c1 || (o.c1 == a.c1 && o.r1 < a.r1));
+    InsBest w = take_o ? o : a;
+    const InsBest &l = take_o ? a : o;
+    if (l.r1 >= 0) w.c2 = min(w.c2, l.c1);
+    return w;
+}
+
+// Selection key of customer i under the rule; smaller is better.  Best insertion: (cost, i).
+// Regret: unbounded regret first, then larger regret, then cheaper best, then i.
+struct PickKey {
+    int valid;
+    int inf;        // regret unbounded
+    long long reg;  // regret (c2 - c1)
+    int c1, i;
+};
+
+__device__ __forceinline__ bool pick_less(const PickKey &a, const PickKey &b, bool regret) {
+    if (a.valid != b.valid) return a.valid > b.valid;
+    if (!a.valid) return false;
+    if (regret) {
+        if (a.inf != b.inf) return a.inf > b.inf;
+        if (!a.inf && a.reg != b.reg) return a.reg > b.reg;
+    }
+    if (a.c1 != b.c1) return a.c1 < b.c1;
+    return a.i < b.i;
+}
+
+__device__ __forceinline__ PickKey pick_shfl(const PickKey &k, int o) {
+    PickKey r;
+    r.valid = __shfl_xor_sync(0xffffffffu, k.valid, o);
+    r.inf = __shfl_xor_sync(0xffffffffu, k.inf, o);
+    r.reg = __shfl_xor_sync(0xffffffffu, k.reg, o);
+    r.c1 = __shfl_xor_sync(0xffffffffu, k.c1, o);
+    r.i = __shfl_xor_sync(0xffffffffu, k.i, o);
+    return r;
+}
+
+// Best insertion of u over the lane's routes, warp-reduced (every lane returns the result).
+template <bool TW>
+__device__ InsBest eval_customer_ins(const DevInst &I, const DevSols &D, int s, int u, bool feas, int lane) {
+    const bool open = (I.variant & MD_VARIANT_OPEN) != 0;
+    const Seg su = nodeseg(I, u);
+    InsBest b;
+    b.c1 = INT_MAX; b.r1 = -1; b.k1 = -1; b.c2 = INT_MAX;
+    for (int r = lane; r < D.R; r += 32) {
+        const size_t sr = (size_t)s * D.R + r;
+        const int4 h = D.rhdr[sr];
+        const int L = h.x, ds = h.y, de = h.z;
+        if (L <= 0) continue;
+        const int32_t *row = D.rnodes + sr * D.K;
+        int rc = INT_MAX, rk = -1;
+        for (int k = 0; k <= L; k++) {
+            const int a = k > 0 ? row[k - 1] : ds;
+            const int bnode = k < L ? row[k] : (open ? MD_NONE : de);
+            const int cau = dcost(I, a, u);
+            const int cub = bnode != MD_NONE ? dcost(I, u, bnode) : 0;
+            const int c = bnode != MD_NONE ? cau + cub - dcost(I, a, bnode) : cau;
+            if (c >= rc) continue;  // ties keep the earlier position
+            if (feas) {
+                const Seg pre = k > 0 ? seg_of(ld_seg8(&D.cpre[(size_t)s * I.nc + (a - I.nd)])) : nodeseg(I, ds);
+                Seg g = seg_cat<TW>(pre, su, cau);
+                if (bnode != MD_NONE) {
+                    const Seg suf = k < L ? seg_of(ld_seg8(&D.csuf[(size_t)s * I.nc + (bnode - I.nd)])) : nodeseg(I, de);
+                    g = seg_cat<TW>(g, suf, cub);
+                }
+                if (g.load > I.Q || (TW && g.tw > 0) || (I.D > 0 && g.dur > I.D)) continue;
+            }
+            rc = c;
+            rk = k;
+        }
+        if (rk >= 0) ins_push(b, rc, r, rk);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        InsBest x;
+        x.c1 = __shfl_xor_sync(0xffffffffu, b.c1, o);
+        x.r1 = __shfl_xor_sync(0xffffffffu, b.r1, o);
+        x.k1 = __shfl_xor_sync(0xffffffffu, b.k1, o);
+        x.c2 = __shfl_xor_sync(0xffffffffu, b.c2, o);
+        b = ins_merge(b, x);
+    }
+    return b;
+}
+
+// One CTA per solution.  U: the solution's unrouted list (device copy, consumed in place);
+// res: per-list-entry scratch; order: the customers in insertion order.
+template <bool TW>
+__global__ void __launch_bounds__(256) k_repair(DevInst I, DevSols D, int32_t *ulist, const int64_t *uoff,
+                                                InsBest *res, int32_t *order, int rule) {
+    extern __shared__ int sm_dyn[];
+    int *s_dcount = sm_dyn;              // [nd] routes departing from each depot
+    int *s_stage = sm_dyn + I.nd;        // [K] staging of a route's tail
+    __shared__ PickKey s_red[8];
+    __shared__ int s_pick, s_stop;
+    const int s = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const bool feas = rule == MD_INSERT_FBI || rule == MD_INSERT_FRI;
+    const bool regret = rule == MD_INSERT_FRI || rule == MD_INSERT_IRI;
+    const bool open = (I.variant & MD_VARIANT_OPEN) != 0;
+    const int64_t u0 = uoff[s];
+    int32_t *U = ulist + u0;
+    InsBest *RS = res + u0;
+    int nU = (int)(uoff[s + 1] - u0);
+    for (int d = tid; d < I.nd; d += blockDim.x) s_dcount[d] = 0;
+    __syncthreads();
+    for (int r = tid; r < D.R; r += blockDim.x) {
+        const int4 h = D.rhdr[(size_t)s * D.R + r];
+        if (h.x > 0) atomicAdd(&s_dcount[h.y], 1);
+    }
+    if (tid == 0) s_stop = 0;
+    __syncthreads();
+    int done = 0;
+    while (nU > 0) {
+        // every insertion of every unrouted customer
+        for (int i = warp; i < nU; i += nw) {
+            const InsBest b = eval_customer_ins<TW>(I, D, s, U[i], feas, lane);
+            if (lane == 0) RS[i] = b;
+        }
+        __syncthreads();
+        // the customer the rule picks
+        PickKey best;
+        best.valid = 0; best.inf = 0; best.reg = 0; best.c1 = 0; best.i = INT_MAX;
+        for (int i = tid; i < nU; i += blockDim.x) {
+            const InsBest b = RS[i];
+            PickKey k;
+            k.valid = b.r1 >= 0;
+            k.inf = b.c2 == INT_MAX;
+            k.reg = k.inf ? 0 : (long long)b.c2 - b.c1;
+            k.c1 = b.c1;
+            k.i = i;
+            if (pick_less(k, best, regret)) best = k;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const PickKey x = pick_shfl(best, o);
+            if (pick_less(x, best, regret)) best = x;
+        }
+        if (lane == 0) s_red[warp] = best;
+        __syncthreads();
+        if (warp == 0) {
+            PickKey k = lane < nw ? s_red[lane] : s_red[0];
+            for (int o = 16; o > 0; o >>= 1) {
+                const PickKey x = pick_shfl(k, o);
+                if (pick_less(x, k, regret)) k = x;
+            }
+            const int i = k.valid ? k.i : 0;  // none: the first customer opens a route
+            const int u = U[i];
+            if (k.valid) {
+                const InsBest b = RS[i];
+                const int r = b.r1, pos = b.k1;
+                const size_t sr = (size_t)s * D.R + r;
+                const int4 h = D.rhdr[sr];
+                const int L = h.x;
+                if (L + 1 > D.K) {
+                    if (lane == 0) { atomicCAS(D.err, 0, (int)MD_ERR_CAPACITY); s_stop = 1; }
+                } else {
+                    int32_t *row = D.rnodes + sr * D.K;
+                    for (int t = pos + lane; t < L; t += 32) s_stage[t] = row[t];
+                    __syncwarp();
+                    for (int t = pos + lane; t < L; t += 32) row[t + 1] = s_stage[t];
+                    if (lane == 0) {
+                        row[pos] = u;
+                        D.rhdr[sr] = make_int4(L + 1, h.y, h.z, h.w);
+                    }
+                    __syncwarp();
+                    rebuild_route<TW>(I, D, s, r);
+                }
+            } else {
+                // a new route [d, u, d] at the nearest depot with a free vehicle (any depot if
+                // none has one), in the first free slot
+                long long bestd = LLONG_MAX;
+                for (int d = lane; d < I.nd; d += 32) {
+                    const long long c = (long long)dcost(I, d, u) + (open ? 0 : dcost(I, u, d));
+                    const long long key = ((long long)(s_dcount[d] >= I.NV) << 62) | (c << 20) | d;
+                    bestd = min(bestd, key);
+                }
+                for (int o = 16; o > 0; o >>= 1) bestd = min(bestd, __shfl_xor_sync(0xffffffffu, bestd, o));
+                const int d = (int)(bestd & 0xfffff);
+                int slot = -1;
+                for (int base = 0; base < D.R && slot < 0; base += 32) {
+                    const int r = base + lane;
+                    const bool fr = r < D.R && D.rhdr[(size_t)s * D.R + r].x == 0;
+                    const unsigned m = __ballot_sync(0xffffffffu, fr);
+                    if (m) slot = base + __ffs(m) - 1;
+                }
+                if (slot < 0) {
+                    if (lane == 0) { atomicCAS(D.err, 0, (int)MD_ERR_CAPACITY); s_stop = 1; }
+                } else {
+                    const size_t sr = (size_t)s * D.R + slot;
+                    if (lane == 0) {
+                        D.rnodes[sr * D.K] = u;
+                        D.rhdr[sr] = make_int4(1, d, d, u);
+                        s_dcount[d]++;
+                    }
+                    __syncwarp();
+                    rebuild_route<TW>(I, D, s, slot);
+                }
+            }
+            if (lane == 0) {
+                s_pick = i;
+                if (order) order[u0 + done] = u;
+            }
+        }
+        __syncthreads();
+        if (s_stop) break;
+        // drop entry s_pick from the list, keeping the order (warp 0, chunks of 32 from the front)
+        const int i = s_pick;
+        if (warp == 0) {
+            for (int base = i; base < nU - 1; base += 32) {
+                const int j = base + lane;
+                const int v = j < nU - 1 ? U[j + 1] : 0;
+                __syncwarp();
+                if (j < nU - 1) U[j] = v;
+            }
+        }
+        nU--;
+        done++;
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+extern "C" md_status md_repair_insert(md_solutions *S, int32_t rule, const int32_t *nodes, const int64_t *off,
+                                      const int32_t *per_sol, const int32_t *unrouted, const int64_t *unrouted_off,
+                                      int32_t *order, void *stream) {
+    if (!S || !per_sol || !unrouted_off) { md_set_error("md_repair_insert: null argument"); return MD_ERR_ARG; }
+    if (rule < MD_INSERT_FBI || rule > MD_INSERT_IRI) { md_set_error("md_repair_insert: unknown rule %d", rule); return MD_ERR_ARG; }
+    cudaStream_t st = (cudaStream_t)stream;
+    const DevInst &I = S->inst->d;
+    // every customer exactly once per solution, in a route or in the unrouted list
+    long long ri = 0;
+    std::vector<int> seen(I.nn, -1);
+    if (unrouted_off[0] != 0) { md_set_error("md_repair_insert: unrouted offsets must start at 0"); return MD_ERR_ARG; }
+    for (int s = 0; s < S->n_sol; s++) {
+        int n = 0;
+        if (per_sol[s] < 0) { md_set_error("md_repair_insert: negative route count"); return MD_ERR_ARG; }
+        if (per_sol[s] > 0 && (!nodes || !off)) { md_set_error("md_repair_insert: null routes"); return MD_ERR_ARG; }
+        for (int k = 0; k < per_sol[s]; k++, ri++)
+            for (long long j = off[ri] + 1; j < off[ri + 1] - 1; j++) {
+                const int c = nodes[j];
+                if (c < I.nd || c >= I.nn || seen[c] == s) { md_set_error("md_repair_insert: node %d invalid or repeated in solution %d", c, s); return MD_ERR_ARG; }
+                seen[c] = s;
+                n++;
+            }
+        if (unrouted_off[s + 1] < unrouted_off[s]) { md_set_error("md_repair_insert: unrouted offsets decrease"); return MD_ERR_ARG; }
+        for (long long j = unrouted_off[s]; j < unrouted_off[s + 1]; j++) {
+            const int c = unrouted[j];
+            if (c < I.nd || c >= I.nn || seen[c] == s) { md_set_error("md_repair_insert: unrouted node %d invalid or repeated in solution %d", c, s); return MD_ERR_ARG; }
+            seen[c] = s;
+            n++;
+        }
+        if (n != I.nc) { md_set_error("md_repair_insert: solution %d lists %d of %d customers", s, n, I.nc); return MD_ERR_ARG; }
+    }
+    md_status r = md_load_routes(S, nodes, off, per_sol, true, st);
+    if (r != MD_OK) return r;
+    const long long nu = unrouted_off[S->n_sol];
+    if (nu > 0) {
+        int32_t *du = nullptr;
+        int64_t *doff = nullptr;
+        InsBest *dres = nullptr;
+        int32_t *dord = nullptr;
+        MD_CUDA(cudaMallocAsync(&du, sizeof(int32_t) * nu, st));
+        MD_CUDA(cudaMallocAsync(&dord, sizeof(int32_t) * nu, st));
+        MD_CUDA(cudaMallocAsync(&dres, sizeof(InsBest) * nu, st));
+        MD_CUDA(cudaMallocAsync(&doff, sizeof(int64_t) * (S->n_sol + 1), st));
+        MD_CUDA(cudaMemcpyAsync(du, unrouted, sizeof(int32_t) * nu, cudaMemcpyHostToDevice, st));
+        MD_CUDA(cudaMemcpyAsync(doff, unrouted_off, sizeof(int64_t) * (S->n_sol + 1), cudaMemcpyHostToDevice, st));
+        const size_t smem = sizeof(int) * ((size_t)I.nd + S->K);
+        if (I.variant & MD_VARIANT_TW) {
+            MD_CUDA(md_allow_smem((const void *)k_repair<true>, smem));
+            k_repair<true><<<S->n_sol, 256, smem, st>>>(I, S->d, du, doff, dres, dord, rule);
+        } else {
+            MD_CUDA(md_allow_smem((const void *)k_repair<false>, smem));
+            k_repair<false><<<S->n_sol, 256, smem, st>>>(I, S->d, du, doff, dres, dord, rule);
+        }
+        MD_CUDA(cudaGetLastError());
+        r = md_launch_totals(S, st);
+        if (r != MD_OK) return r;
+        if (order) MD_CUDA(cudaMemcpyAsync(order, dord, sizeof(int32_t) * nu, cudaMemcpyDeviceToHost, st));
+        MD_CUDA(cudaFreeAsync(du, st));
+        MD_CUDA(cudaFreeAsync(dord, st));
+        MD_CUDA(cudaFreeAsync(dres, st));
+        MD_CUDA(cudaFreeAsync(doff, st));
+    }
+    int32_t err = 0;
+    MD_CUDA(cudaMemcpyAsync(&err, S->d.err, sizeof(err), cudaMemcpyDeviceToHost, st));
+    MD_CUDA(cudaStreamSynchronize(st));
+    if (err) {
+        MD_CUDA(cudaMemsetAsync(S->d.err, 0, sizeof(int32_t), st));
+        md_set_error("md_repair_insert: a route exceeded k_max or no route slot was free");
+        return MD_ERR_CAPACITY;
+    }
+    return MD_OK;
+}

@@ -157,16 +157,16 @@ static md_status finish_load(md_solutions *S, cudaStream_t st) {
     return md_launch_totals(S, st);
 }
 
-extern "C" md_status md_solutions_load(md_solutions *S, const int32_t *nodes, const int64_t *off,
-                                       const int32_t *per_sol, void *stream) {
-    if (!S || !nodes || !off || !per_sol) { md_set_error("md_solutions_load: null argument"); return MD_ERR_ARG; }
-    cudaStream_t st = (cudaStream_t)stream;
+// Loads the routes into their slots and rebuilds every summary.  partial: a solution may have
+// no route and may leave customers out (the repair insertion fills them in).
+md_status md_load_routes(md_solutions *S, const int32_t *nodes, const int64_t *off, const int32_t *per_sol,
+                         bool partial, cudaStream_t st) {
     const DevInst &I = S->inst->d;
     long long n_routes = 0;
     for (int s = 0; s < S->n_sol; s++) {
-        if (per_sol[s] < 1 || per_sol[s] > S->R) {
+        if (per_sol[s] < (partial ? 0 : 1) || per_sol[s] > S->R) {
             md_set_error("md_solutions_load: solution %d has %d routes (slots %d)", s, per_sol[s], S->R);
-            return per_sol[s] < 1 ? MD_ERR_ARG : MD_ERR_CAPACITY;
+            return per_sol[s] < 0 || (!partial && per_sol[s] < 1) ? MD_ERR_ARG : MD_ERR_CAPACITY;
         }
         n_routes += per_sol[s];
     }
@@ -190,26 +190,34 @@ extern "C" md_status md_solutions_load(md_solutions *S, const int32_t *nodes, co
             }
             rinfo[ri] = make_int4(s, k, (int)a, len - 2);
         }
-        if (ncust != I.nc) { md_set_error("md_solutions_load: solution %d serves %d of %d customers", s, ncust, I.nc); return MD_ERR_ARG; }
+        if (!partial && ncust != I.nc) { md_set_error("md_solutions_load: solution %d serves %d of %d customers", s, ncust, I.nc); return MD_ERR_ARG; }
     }
-    long long n_nodes = off[n_routes];
-    if (n_nodes >= (1LL << 31)) { md_set_error("md_solutions_load: too many nodes"); return MD_ERR_ARG; }
-    int32_t *dflat = nullptr;
-    int4 *dinfo = nullptr;
-    MD_CUDA(cudaMallocAsync(&dflat, sizeof(int32_t) * n_nodes, st));
-    MD_CUDA(cudaMallocAsync(&dinfo, sizeof(int4) * n_routes, st));
-    MD_CUDA(cudaMemcpyAsync(dflat, nodes, sizeof(int32_t) * n_nodes, cudaMemcpyHostToDevice, st));
-    MD_CUDA(cudaMemcpyAsync(dinfo, rinfo.data(), sizeof(int4) * n_routes, cudaMemcpyHostToDevice, st));
     MD_CUDA(cudaMemsetAsync(S->d.rhdr, 0, sizeof(int4) * (size_t)S->n_sol * S->R, st));
-    int blocks = (int)((n_routes * 32 + 255) / 256);
-    k_scatter<<<blocks, 256, 0, st>>>(S->d, dflat, dinfo, (int)n_routes);
-    MD_CUDA(cudaGetLastError());
+    if (n_routes > 0) {
+        long long n_nodes = off[n_routes];
+        if (n_nodes >= (1LL << 31)) { md_set_error("md_solutions_load: too many nodes"); return MD_ERR_ARG; }
+        int32_t *dflat = nullptr;
+        int4 *dinfo = nullptr;
+        MD_CUDA(cudaMallocAsync(&dflat, sizeof(int32_t) * n_nodes, st));
+        MD_CUDA(cudaMallocAsync(&dinfo, sizeof(int4) * n_routes, st));
+        MD_CUDA(cudaMemcpyAsync(dflat, nodes, sizeof(int32_t) * n_nodes, cudaMemcpyHostToDevice, st));
+        MD_CUDA(cudaMemcpyAsync(dinfo, rinfo.data(), sizeof(int4) * n_routes, cudaMemcpyHostToDevice, st));
+        int blocks = (int)((n_routes * 32 + 255) / 256);
+        k_scatter<<<blocks, 256, 0, st>>>(S->d, dflat, dinfo, (int)n_routes);
+        MD_CUDA(cudaGetLastError());
+        MD_CUDA(cudaFreeAsync(dflat, st));
+        MD_CUDA(cudaFreeAsync(dinfo, st));
+    }
     md_status r = finish_load(S, st);
-    MD_CUDA(cudaFreeAsync(dflat, st));
-    MD_CUDA(cudaFreeAsync(dinfo, st));
     if (r != MD_OK) return r;
     MD_CUDA(cudaStreamSynchronize(st));
     return MD_OK;
+}
+
+extern "C" md_status md_solutions_load(md_solutions *S, const int32_t *nodes, const int64_t *off,
+                                       const int32_t *per_sol, void *stream) {
+    if (!S || !nodes || !off || !per_sol) { md_set_error("md_solutions_load: null argument"); return MD_ERR_ARG; }
+    return md_load_routes(S, nodes, off, per_sol, false, (cudaStream_t)stream);
 }
 
 extern "C" md_status md_solutions_copy(md_solutions *dst, const md_solutions *src, void *stream) {

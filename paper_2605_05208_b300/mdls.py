@@ -19,8 +19,9 @@ LIB_PATH = os.path.join(_HERE, "libmdls.so")
 
 MD_OK, MD_ERR_ARG, MD_ERR_CUDA, MD_ERR_CAPACITY, MD_ERR_TIMEOUT, MD_ERR_STATE = range(6)
 VARIANT_TW, VARIANT_OPEN, VARIANT_SYMMETRIC = 1, 2, 4
-OP_RELOCATE, OP_SWAP, OP_TWO_OPT_STAR, OP_DEPOT_INSERT, OP_DEPOT_REPLACE = range(5)
-N_OPS = 5
+OP_RELOCATE, OP_SWAP, OP_TWO_OPT_STAR, OP_DEPOT_INSERT, OP_DEPOT_REPLACE, OP_TWO_OPT = range(6)
+N_OPS = 5      # the operators of the benchmark configurations
+N_OPS_ALL = 6  # with the intra-route 2-opt
 EVAL_DUMP, EVAL_FOLLOWERS = 1, 2
 APPLY_UPDATE_LAMBDA = 1
 
@@ -36,7 +37,9 @@ EXPORTED = (
     "md_batch_descend", "md_instance_build_neighbors",
     "md_instance_set_neighbors", "md_pruner_create", "md_pruner_destroy", "md_pruner_params",
     "md_pruner_features", "md_pruner_score", "md_pruner_prune", "md_pruner_train",
+    "md_repair_insert",
 )
+INSERT_FBI, INSERT_IBI, INSERT_FRI, INSERT_IRI = 0, 1, 2, 3  # repair insertion rules (Section 3.3)
 
 PRUNER_PARAMS = 20865
 
@@ -103,6 +106,7 @@ def lib() -> C.CDLL:
             "md_solutions_create": [P, C.c_int32, C.c_int32, C.c_int32, PP],
             "md_solutions_destroy": [P],
             "md_solutions_load": [P, P, P, P, P],
+            "md_repair_insert": [P, C.c_int32, P, P, P, P, P, P, P],
             "md_solutions_copy": [P, P, P],
             "md_solutions_read": [P, P, P, P, C.c_int64, C.c_int64, P],
             "md_solution_cost": [P, P, P, P],
@@ -272,6 +276,22 @@ class Solutions:
 
     def load_flat(self, nodes, offs, per, stream=None):
         _check(lib().md_solutions_load(self.h, _ptr(nodes), _ptr(offs), _ptr(per), _stream(stream)))
+
+    def repair(self, partial, unrouted, rule, stream=None):
+        """Loads the partial solutions `partial` (lists of routes; a solution may have none) and
+        inserts each solution's unrouted customers (`unrouted[s]`, in order of preference) by
+        `rule` (INSERT_FBI, INSERT_IBI, INSERT_FRI, INSERT_IRI), on the device (Section 3.3).
+        Returns per solution the customers in the order they were inserted."""
+        assert len(partial) == self.n_sol == len(unrouted)
+        nodes, offs, per = flatten(partial)
+        un = np.asarray([c for u in unrouted for c in u] or [0], dtype=np.int32)
+        uoff = np.zeros(self.n_sol + 1, dtype=np.int64)
+        uoff[1:] = np.cumsum([len(u) for u in unrouted])
+        order = np.zeros(max(int(uoff[-1]), 1), dtype=np.int32)
+        _check(lib().md_repair_insert(self.h, int(rule), _ptr(nodes) if len(nodes) else None,
+                                      _ptr(offs) if len(nodes) else None, _ptr(per), _ptr(un), _ptr(uoff),
+                                      _ptr(order), _stream(stream)))
+        return [[int(x) for x in order[uoff[s]:uoff[s + 1]]] for s in range(self.n_sol)]
 
     def copy_from(self, other: "Solutions", stream=None):
         _check(lib().md_solutions_copy(self.h, other.h, _stream(stream)))

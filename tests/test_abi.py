@@ -50,6 +50,10 @@ def test_header_constants_match_binding_and_workloads():
     assert int(consts["MD_OP_TWO_OPT_STAR"]) == mdls.OP_TWO_OPT_STAR == W.OP_TWO_OPT_STAR
     assert int(consts["MD_OP_DEPOT_INSERT"]) == mdls.OP_DEPOT_INSERT == W.OP_DEPOT_INSERT
     assert int(consts["MD_OP_DEPOT_REPLACE"]) == mdls.OP_DEPOT_REPLACE == W.OP_DEPOT_REPLACE
+    assert int(consts["MD_OP_TWO_OPT"]) == mdls.OP_TWO_OPT == W.OP_TWO_OPT
+    assert int(consts["MD_N_OPS"]) == mdls.N_OPS_ALL == W.N_OPS_ALL == len(mdls.Stats().moves_by_op)
+    assert [int(consts[f"MD_INSERT_{r}"]) for r in ("FBI", "IBI", "FRI", "IRI")] == [
+        mdls.INSERT_FBI, mdls.INSERT_IBI, mdls.INSERT_FRI, mdls.INSERT_IRI] == [0, 1, 2, 3]
     assert int(consts["MD_VARIANT_TW"]) == mdls.VARIANT_TW == W.VAR_TW
     assert int(consts["MD_VARIANT_OPEN"]) == mdls.VARIANT_OPEN == W.VAR_OPEN
     assert int(consts["MD_VARIANT_SYMMETRIC"]) == mdls.VARIANT_SYMMETRIC == W.VAR_SYMMETRIC
@@ -85,3 +89,4 @@ def test_descend_rejects_bad_config_without_device(built):
     st = mdls.Stats()
     assert L.md_descend(None, None, C.byref(st), None) == mdls.MD_ERR_ARG
     assert L.md_moves_create(None, 0, C.byref(C.c_void_p())) == mdls.MD_ERR_ARG
+    assert L.md_repair_insert(None, 0, None, None, None, None, None, None, None) == mdls.MD_ERR_ARG
