@@ -626,6 +626,103 @@ def run_learned(args):
     }))
 
 
+REPAIR_RULES = ("FBI", "IBI", "FRI", "IRI")
+
+
+def repair_workload(rank: int = 0):
+    """The bench instance's 32 initial solutions with a quarter of their routes and a tenth of
+    the remaining customers removed, as a route exchange leaves them."""
+    spec, sols, _ = workload_spec(rank)
+    parts = [W.partial_solution(sol, SEED + 500 + i, p_route=0.25, p_cust=0.1) for i, sol in enumerate(sols)]
+    return spec, [p[0] for p in parts], [p[1] for p in parts]
+
+
+def _oracle_repair(args):
+    rank, idx, rule = args
+    from oracle import oracle as O
+    key = ("repair", rank)
+    if key not in _ORACLE_CACHE:
+        spec, keep, un = repair_workload(rank)
+        _ORACLE_CACHE[key] = (O.Instance(spec), keep, un)
+    inst, keep, un = _ORACLE_CACHE[key]
+    t0 = time.perf_counter()
+    inst.repair(keep[idx], un[idx], rule)
+    return len(un[idx]), time.perf_counter() - t0
+
+
+def run_repair(args):
+    """Repair insertion (Section 3.3) of 32 partial solutions of the bench instance: one step
+    repairs every solution once under each of the four rules (FBI, IBI, FRI, IRI) through
+    md_repair_insert, whose call includes loading the partial routes from host buffers."""
+    import torch
+    from paper_2605_05208_b300 import build, mdls
+    pool = None
+    if not args.no_cpu_baseline:
+        pool = make_pool(min(os.cpu_count() or 1, 16))
+    build.build()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    sptr = stream.cuda_stream
+    spec, keep, un = repair_workload()
+    inst = mdls.Instance(spec)
+    S = mdls.Solutions(inst, N_SOL, spec.n_customers + 1, spec.n_customers)
+    inserted = sum(len(u) for u in un)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
+
+    def one():
+        for rule in range(len(REPAIR_RULES)):
+            S.repair(keep, un, rule, stream=sptr)
+    for _ in range(args.warmup):
+        one()
+    torch.cuda.synchronize()
+    ms = []
+    per_rule = [0.0] * len(REPAIR_RULES)
+    with ClockSampler(0) as clk:
+        for k in range(args.steps):
+            flush.fill_(k)
+            torch.cuda.synchronize()
+            for rule in range(len(REPAIR_RULES)):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                S.repair(keep, un, rule, stream=sptr)
+                b.record(stream)
+                torch.cuda.synchronize()
+                t = a.elapsed_time(b)
+                per_rule[rule] += t / args.steps
+                ms.append(t)
+    total_ms = sum(ms)
+    value = inserted * len(REPAIR_RULES) * args.steps / (total_ms / 1e3)
+    cpu = None
+    if pool is not None:
+        jobs = [(0, i, r) for r in range(len(REPAIR_RULES)) for i in range(N_SOL)]
+        t0 = time.perf_counter()
+        res = pool.map(_oracle_repair, jobs)
+        wall = time.perf_counter() - t0
+        cpu = {"value": sum(r[0] for r in res) / wall, "unit": "insertions/s", "cores": pool._processes,
+               "kind": "oracle",
+               "sample": f"the {N_SOL} repairs under each rule (one step), one repair per task; "
+                         f"{sum(r[1] for r in res):.1f} s CPU, {wall:.1f} s wall"}
+        pool.close()
+    print(json.dumps({
+        "metric": "customers inserted/s", "value": value, "unit": "insertions/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / max(args.steps, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic",
+        "config": {"workload": f"repair-mdvrptw-6x288: {N_SOL} partial solutions of the mdvrptw-6x288 "
+                               f"bench instance ({inserted / N_SOL:.1f} unrouted customers each), one "
+                               f"repair per solution under each rule {'/'.join(REPAIR_RULES)}",
+                   "l2": "flushed between timed steps (256 MB write)",
+                   "timed": "md_repair_insert calls, including the H2D load of the partial routes"},
+        "ms_per_rule": dict(zip(REPAIR_RULES, per_rule)),
+        "repairs_per_s": N_SOL * len(REPAIR_RULES) * args.steps / (total_ms / 1e3),
+        "cpu_baseline": cpu,
+        # per call: k_scatter, k_fill_lambda, k_rebuild_all, k_totals (the load), k_repair, k_totals
+        "gpu_launches": 6 * len(REPAIR_RULES) * args.steps,
+        "clocks": clk.summary(),
+    }))
+
+
 def run_plain_large(args):
     """Plain full-neighbourhood descents of the 20-depot, 10000-customer MDVRPTW instance (every
     customer a candidate of every customer; the 401.6 MB distance matrix does not fit in L2).
@@ -708,7 +805,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", choices=["mdvrptw-6x288", "batch16-uneven", "learned-20x10000",
-                                           "plain-20x10000"], default="mdvrptw-6x288")
+                                           "plain-20x10000", "repair-mdvrptw-6x288"], default="mdvrptw-6x288")
     ap.add_argument("--solutions", type=int, default=0, help="solutions of the learned workload (0: 8)")
     ap.add_argument("--plain-steps", type=int, default=1,
                     help="timed plain full-neighbourhood descents beside the learned workload")
@@ -729,6 +826,8 @@ def main():
         run_learned(args)
     elif args.workload == "plain-20x10000":
         run_plain_large(args)
+    elif args.workload == "repair-mdvrptw-6x288":
+        run_repair(args)
     else:
         run_ours(args)
 

@@ -2,20 +2,21 @@
 // inserted one at a time by feasible / infeasible best insertion (FBI, IBI) or feasible /
 // infeasible regret insertion (FRI, IRI), for many solutions at once.
 //
-// One CTA per solution runs the whole repair.  Each round evaluates every insertion of every
-// unrouted customer: warp w takes customers w, w+8, ... of the list, its lanes take the route
-// slots, and a lane walks the L+1 positions of its route.  An insertion after position k joins
-// three summaries that already exist -- the prefix [ds..c_k] (cpre of c_k, or the depot), the
-// customer, the suffix [c_{k+1}..de] (csuf of c_{k+1}, or the depot) -- so its cost and its
-// feasibility (load, time warp, duration) take O(1) per position; the cost is the closed form
-// c(c_k, u) + c(u, c_{k+1}) - c(c_k, c_{k+1}).  Per customer the warp keeps the best insertion
-// and the best insertion into any other route (for the regret); the block then picks the
-// customer by the rule, warp 0 inserts it and rebuilds that route's summaries, and the next
-// round starts.  Ties break as the rules state: cost, then the customer's place in the list,
-// then route slot, then position.
+// One CTA per solution runs the whole repair.  An insertion after position k joins three
+// summaries that already exist -- the prefix [ds..c_k] (cpre of c_k, or the depot), the
+// customer, the suffix [c_{k+1}..de] (csuf of c_{k+1}, or the depot) -- so its feasibility
+// (load, time warp, duration) takes O(1) per position; its cost is the closed form
+// c(c_k, u) + c(u, c_{k+1}) - c(c_k, c_{k+1}).  The block keeps, per listed customer and route,
+// the route's cheapest insertion; an insertion changes one route, so each round rescans only
+// that route's positions for every listed customer (the first round scans all routes).  Per
+// customer the block then forms its best insertion and its best cost in another route (for the
+// regret), picks the customer by the rule; warp 0 inserts it and rebuilds that route's
+// summaries.  Ties break as the rules state: cost, then the customer's place in the list, then
+// route slot, then position.
 #include <limits.h>
 #include <string.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "route_build.cuh"
@@ -30,7 +31,7 @@ __device__ __forceinline__ int dcost(const DevInst &I, int a, int b) { return __
 
 __device__ __forceinline__ Seg nodeseg(const DevInst &I, int n) { return node_seg(__ldg(&I.node[n])); }
 
-// Folds route best (c, r, k) into a lane's pair; routes arrive in increasing slot order.
+// Folds route best (c, r, k) into a customer's pair; routes arrive in increasing slot order.
 __device__ __forceinline__ void ins_push(InsBest &b, int c, int r, int k) {
     if (b.r1 < 0 || c < b.c1) {
         if (b.r1 >= 0) b.c2 = min(b.c2, b.c1);
@@ -38,16 +39,6 @@ __device__ __forceinline__ void ins_push(InsBest &b, int c, int r, int k) {
     } else {
         b.c2 = min(b.c2, c);
     }
-}
-
-// Merges two lanes' pairs (disjoint route sets): the better best by (cost, slot); the second is
-// the smaller of the winner's second and the loser's best.
-__device__ __forceinline__ InsBest ins_merge(const InsBest &a, const InsBest &o) {
-    const bool take_o = o.r1 >= 0 && (a.r1 < 0 || o.c1 < a.c1 || (o.c1 == a.c1 && o.r1 < a.r1));
-    InsBest w = take_o ? o : a;
-    const InsBest &l = take_o ? a : o;
-    if (l.r1 >= 0) w.c2 = min(w.c2, l.c1);
-    return w;
 }
 
 // Selection key of customer i under the rule; smaller is better.  Best insertion: (cost, i).
@@ -80,62 +71,55 @@ __device__ __forceinline__ PickKey pick_shfl(const PickKey &k, int o) {
     return r;
 }
 
-// Best insertion of u over the lane's routes, warp-reduced (every lane returns the result).
+// Cheapest insertion of u into route slot r of solution s (feasible ones only when feas): {cost,
+// position}, position -1 when there is none.  Ties keep the earlier position.
 template <bool TW>
-__device__ InsBest eval_customer_ins(const DevInst &I, const DevSols &D, int s, int u, bool feas, int lane) {
+__device__ int2 route_best(const DevInst &I, const DevSols &D, int s, int r, int u, bool feas) {
     const bool open = (I.variant & MD_VARIANT_OPEN) != 0;
-    const Seg su = nodeseg(I, u);
-    InsBest b;
-    b.c1 = INT_MAX; b.r1 = -1; b.k1 = -1; b.c2 = INT_MAX;
-    for (int r = lane; r < D.R; r += 32) {
-        const size_t sr = (size_t)s * D.R + r;
-        const int4 h = D.rhdr[sr];
-        const int L = h.x, ds = h.y, de = h.z;
-        if (L <= 0) continue;
-        const int32_t *row = D.rnodes + sr * D.K;
-        int rc = INT_MAX, rk = -1;
-        for (int k = 0; k <= L; k++) {
-            const int a = k > 0 ? row[k - 1] : ds;
-            const int bnode = k < L ? row[k] : (open ? MD_NONE : de);
-            const int cau = dcost(I, a, u);
-            const int cub = bnode != MD_NONE ? dcost(I, u, bnode) : 0;
-            const int c = bnode != MD_NONE ? cau + cub - dcost(I, a, bnode) : cau;
-            if (c >= rc) continue;  // ties keep the earlier position
+    const size_t sr = (size_t)s * D.R + r;
+    const int4 h = D.rhdr[sr];
+    const int L = h.x, ds = h.y, de = h.z;
+    const int32_t *row = D.rnodes + sr * D.K;
+    int rc = INT_MAX, rk = -1;
+    int a = ds;
+    for (int k = 0; k <= L; k++) {
+        const int bnode = k < L ? row[k] : (open ? MD_NONE : de);
+        const int cau = dcost(I, a, u);
+        const int cub = bnode != MD_NONE ? dcost(I, u, bnode) : 0;
+        const int c = bnode != MD_NONE ? cau + cub - dcost(I, a, bnode) : cau;
+        if (c < rc) {
+            bool ok = true;
             if (feas) {
                 const Seg pre = k > 0 ? seg_of(ld_seg8(&D.cpre[(size_t)s * I.nc + (a - I.nd)])) : nodeseg(I, ds);
-                Seg g = seg_cat<TW>(pre, su, cau);
+                Seg g = seg_cat<TW>(pre, nodeseg(I, u), cau);
                 if (bnode != MD_NONE) {
                     const Seg suf = k < L ? seg_of(ld_seg8(&D.csuf[(size_t)s * I.nc + (bnode - I.nd)])) : nodeseg(I, de);
                     g = seg_cat<TW>(g, suf, cub);
                 }
-                if (g.load > I.Q || (TW && g.tw > 0) || (I.D > 0 && g.dur > I.D)) continue;
+                ok = !(g.load > I.Q || (TW && g.tw > 0) || (I.D > 0 && g.dur > I.D));
             }
-            rc = c;
-            rk = k;
+            if (ok) { rc = c; rk = k; }
         }
-        if (rk >= 0) ins_push(b, rc, r, rk);
+        a = bnode;
     }
-    for (int o = 16; o > 0; o >>= 1) {
-        InsBest x;
-        x.c1 = __shfl_xor_sync(0xffffffffu, b.c1, o);
-        x.r1 = __shfl_xor_sync(0xffffffffu, b.r1, o);
-        x.k1 = __shfl_xor_sync(0xffffffffu, b.k1, o);
-        x.c2 = __shfl_xor_sync(0xffffffffu, b.c2, o);
-        b = ins_merge(b, x);
-    }
-    return b;
+    return make_int2(rc, rk);
 }
 
-// One CTA per solution.  U: the solution's unrouted list (device copy, consumed in place);
-// res: per-list-entry scratch; order: the customers in insertion order.
+// One CTA per solution.  U: the solution's unrouted list (device copy; an inserted customer's
+// entry becomes -1, so the list keeps its order); RB: per (list entry, route slot) the route's
+// cheapest insertion, rows of rcap slots from rb_off[s]; RS: per list entry its best insertion;
+// order: the customers in insertion order.  Routes occupy slots 0..M-1 (loaded routes first,
+// new ones appended), so an insertion changes one column of RB: round 0 fills every column, each
+// later round refreshes the column of the route that changed.
 template <bool TW>
 __global__ void __launch_bounds__(256) k_repair(DevInst I, DevSols D, int32_t *ulist, const int64_t *uoff,
-                                                InsBest *res, int32_t *order, int rule) {
+                                                int2 *RB, const int64_t *rb_off, InsBest *res, int32_t *order,
+                                                int rule) {
     extern __shared__ int sm_dyn[];
     int *s_dcount = sm_dyn;              // [nd] routes departing from each depot
     int *s_stage = sm_dyn + I.nd;        // [K] staging of a route's tail
     __shared__ PickKey s_red[8];
-    __shared__ int s_pick, s_stop;
+    __shared__ int s_pick, s_stop, s_M, s_dirty;
     const int s = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
     const bool feas = rule == MD_INSERT_FBI || rule == MD_INSERT_FRI;
     const bool regret = rule == MD_INSERT_FRI || rule == MD_INSERT_IRI;
@@ -143,28 +127,41 @@ __global__ void __launch_bounds__(256) k_repair(DevInst I, DevSols D, int32_t *u
     const int64_t u0 = uoff[s];
     int32_t *U = ulist + u0;
     InsBest *RS = res + u0;
-    int nU = (int)(uoff[s + 1] - u0);
+    const int nU = (int)(uoff[s + 1] - u0);
+    if (nU == 0) return;
+    const int rcap = (int)((rb_off[s + 1] - rb_off[s]) / nU);
+    int2 *rb = RB + rb_off[s];
     for (int d = tid; d < I.nd; d += blockDim.x) s_dcount[d] = 0;
+    if (tid == 0) { s_stop = 0; s_M = 0; s_dirty = -1; }
     __syncthreads();
     for (int r = tid; r < D.R; r += blockDim.x) {
         const int4 h = D.rhdr[(size_t)s * D.R + r];
-        if (h.x > 0) atomicAdd(&s_dcount[h.y], 1);
+        if (h.x > 0) { atomicAdd(&s_dcount[h.y], 1); atomicAdd(&s_M, 1); }
     }
-    if (tid == 0) s_stop = 0;
     __syncthreads();
-    int done = 0;
-    while (nU > 0) {
-        // every insertion of every unrouted customer
-        for (int i = warp; i < nU; i += nw) {
-            const InsBest b = eval_customer_ins<TW>(I, D, s, U[i], feas, lane);
-            if (lane == 0) RS[i] = b;
+    for (int done = 0; done < nU; done++) {
+        const int M = s_M;
+        // refresh the columns of the routes that changed (round 0: all of them)
+        const int r_lo = done == 0 ? 0 : s_dirty, r_n = done == 0 ? M : (s_dirty >= 0 ? 1 : 0);
+        for (int t = tid; t < nU * r_n; t += blockDim.x) {
+            const int i = t / r_n, r = r_lo + t % r_n;
+            const int u = U[i];
+            if (u >= 0) rb[(size_t)i * rcap + r] = route_best<TW>(I, D, s, r, u, feas);
         }
         __syncthreads();
-        // the customer the rule picks
+        // per listed customer its best insertion and best cost in another route; the rule's pick
         PickKey best;
         best.valid = 0; best.inf = 0; best.reg = 0; best.c1 = 0; best.i = INT_MAX;
         for (int i = tid; i < nU; i += blockDim.x) {
-            const InsBest b = RS[i];
+            if (U[i] < 0) continue;
+            InsBest b;
+            b.c1 = INT_MAX; b.r1 = -1; b.k1 = -1; b.c2 = INT_MAX;
+            const int2 *row = rb + (size_t)i * rcap;
+            for (int r = 0; r < M; r++) {
+                const int2 e = row[r];
+                if (e.y >= 0) ins_push(b, e.x, r, e.y);
+            }
+            RS[i] = b;
             PickKey k;
             k.valid = b.r1 >= 0;
             k.inf = b.c2 == INT_MAX;
@@ -185,8 +182,16 @@ __global__ void __launch_bounds__(256) k_repair(DevInst I, DevSols D, int32_t *u
                 const PickKey x = pick_shfl(k, o);
                 if (pick_less(x, k, regret)) k = x;
             }
-            const int i = k.valid ? k.i : 0;  // none: the first customer opens a route
+            int i = k.i;
+            if (!k.valid) {  // none: the first listed customer opens a route
+                i = INT_MAX;
+                for (int base = 0; base < nU && i == INT_MAX; base += 32) {
+                    const unsigned m = __ballot_sync(0xffffffffu, base + lane < nU && U[base + lane] >= 0);
+                    if (m) i = base + __ffs(m) - 1;
+                }
+            }
             const int u = U[i];
+            int touched = -1;
             if (k.valid) {
                 const InsBest b = RS[i];
                 const int r = b.r1, pos = b.k1;
@@ -206,10 +211,11 @@ __global__ void __launch_bounds__(256) k_repair(DevInst I, DevSols D, int32_t *u
                     }
                     __syncwarp();
                     rebuild_route<TW>(I, D, s, r);
+                    touched = r;
                 }
             } else {
                 // a new route [d, u, d] at the nearest depot with a free vehicle (any depot if
-                // none has one), in the first free slot
+                // none has one), in the next slot
                 long long bestd = LLONG_MAX;
                 for (int d = lane; d < I.nd; d += 32) {
                     const long long c = (long long)dcost(I, d, u) + (open ? 0 : dcost(I, u, d));
@@ -218,14 +224,8 @@ __global__ void __launch_bounds__(256) k_repair(DevInst I, DevSols D, int32_t *u
                 }
                 for (int o = 16; o > 0; o >>= 1) bestd = min(bestd, __shfl_xor_sync(0xffffffffu, bestd, o));
                 const int d = (int)(bestd & 0xfffff);
-                int slot = -1;
-                for (int base = 0; base < D.R && slot < 0; base += 32) {
-                    const int r = base + lane;
-                    const bool fr = r < D.R && D.rhdr[(size_t)s * D.R + r].x == 0;
-                    const unsigned m = __ballot_sync(0xffffffffu, fr);
-                    if (m) slot = base + __ffs(m) - 1;
-                }
-                if (slot < 0) {
+                const int slot = M;
+                if (slot >= D.R || slot >= rcap) {
                     if (lane == 0) { atomicCAS(D.err, 0, (int)MD_ERR_CAPACITY); s_stop = 1; }
                 } else {
                     const size_t sr = (size_t)s * D.R + slot;
@@ -233,30 +233,22 @@ __global__ void __launch_bounds__(256) k_repair(DevInst I, DevSols D, int32_t *u
                         D.rnodes[sr * D.K] = u;
                         D.rhdr[sr] = make_int4(1, d, d, u);
                         s_dcount[d]++;
+                        s_M = M + 1;
                     }
                     __syncwarp();
                     rebuild_route<TW>(I, D, s, slot);
+                    touched = slot;
                 }
             }
             if (lane == 0) {
                 s_pick = i;
+                s_dirty = touched;
                 if (order) order[u0 + done] = u;
             }
         }
         __syncthreads();
         if (s_stop) break;
-        // drop entry s_pick from the list, keeping the order (warp 0, chunks of 32 from the front)
-        const int i = s_pick;
-        if (warp == 0) {
-            for (int base = i; base < nU - 1; base += 32) {
-                const int j = base + lane;
-                const int v = j < nU - 1 ? U[j + 1] : 0;
-                __syncwarp();
-                if (j < nU - 1) U[j] = v;
-            }
-        }
-        nU--;
-        done++;
+        if (tid == 0) U[s_pick] = -1;
         __syncthreads();
     }
 }
@@ -306,15 +298,26 @@ extern "C" md_status md_repair_insert(md_solutions *S, int32_t rule, const int32
         MD_CUDA(cudaMallocAsync(&dord, sizeof(int32_t) * nu, st));
         MD_CUDA(cudaMallocAsync(&dres, sizeof(InsBest) * nu, st));
         MD_CUDA(cudaMallocAsync(&doff, sizeof(int64_t) * (S->n_sol + 1), st));
+        // per solution, rows of min(R, routes + listed customers) route slots per listed customer
+        std::vector<int64_t> rboff(S->n_sol + 1, 0);
+        for (int s = 0; s < S->n_sol; s++) {
+            const long long n = unrouted_off[s + 1] - unrouted_off[s];
+            rboff[s + 1] = rboff[s] + n * std::min<long long>(S->R, per_sol[s] + n);
+        }
+        int2 *drb = nullptr;
+        int64_t *drboff = nullptr;
+        MD_CUDA(cudaMallocAsync(&drb, sizeof(int2) * std::max<int64_t>(rboff[S->n_sol], 1), st));
+        MD_CUDA(cudaMallocAsync(&drboff, sizeof(int64_t) * (S->n_sol + 1), st));
+        MD_CUDA(cudaMemcpyAsync(drboff, rboff.data(), sizeof(int64_t) * (S->n_sol + 1), cudaMemcpyHostToDevice, st));
         MD_CUDA(cudaMemcpyAsync(du, unrouted, sizeof(int32_t) * nu, cudaMemcpyHostToDevice, st));
         MD_CUDA(cudaMemcpyAsync(doff, unrouted_off, sizeof(int64_t) * (S->n_sol + 1), cudaMemcpyHostToDevice, st));
         const size_t smem = sizeof(int) * ((size_t)I.nd + S->K);
         if (I.variant & MD_VARIANT_TW) {
             MD_CUDA(md_allow_smem((const void *)k_repair<true>, smem));
-            k_repair<true><<<S->n_sol, 256, smem, st>>>(I, S->d, du, doff, dres, dord, rule);
+            k_repair<true><<<S->n_sol, 256, smem, st>>>(I, S->d, du, doff, drb, drboff, dres, dord, rule);
         } else {
             MD_CUDA(md_allow_smem((const void *)k_repair<false>, smem));
-            k_repair<false><<<S->n_sol, 256, smem, st>>>(I, S->d, du, doff, dres, dord, rule);
+            k_repair<false><<<S->n_sol, 256, smem, st>>>(I, S->d, du, doff, drb, drboff, dres, dord, rule);
         }
         MD_CUDA(cudaGetLastError());
         r = md_launch_totals(S, st);
@@ -324,6 +327,8 @@ extern "C" md_status md_repair_insert(md_solutions *S, int32_t rule, const int32
         MD_CUDA(cudaFreeAsync(dord, st));
         MD_CUDA(cudaFreeAsync(dres, st));
         MD_CUDA(cudaFreeAsync(doff, st));
+        MD_CUDA(cudaFreeAsync(drb, st));
+        MD_CUDA(cudaFreeAsync(drboff, st));
     }
     int32_t err = 0;
     MD_CUDA(cudaMemcpyAsync(&err, S->d.err, sizeof(err), cudaMemcpyDeviceToHost, st));

@@ -392,6 +392,24 @@ def canonical(sol: list[list[int]], open_routes: bool = False) -> list[tuple]:
     return sorted(rs)
 
 
+def partial_solution(sol, seed, p_route=0.3, p_cust=0.15):
+    """What a route exchange leaves to repair: some routes dropped whole, some single customers
+    dropped (a route left empty is dropped too); returns (kept routes, unrouted customers in a seeded
+    random order)."""
+    st = Stream(seed, 8)
+    keep, unrouted = [], []
+    for r in sol:
+        if st.uniform(1)[0] < p_route:
+            unrouted += r[1:-1]
+            continue
+        cs = [x for x in r[1:-1] if st.uniform(1)[0] >= p_cust or len(r) == 3]
+        unrouted += [x for x in r[1:-1] if x not in cs]
+        if cs:  # a route that lost every customer is dropped
+            keep.append([r[0]] + cs + [r[-1]])
+    perm = np.argsort(st.u64(len(unrouted)))
+    return keep, [unrouted[i] for i in perm]
+
+
 def op_permutations(seed: int, n_solutions: int, max_pass: int, op_list=tuple(range(N_OPS))) -> np.ndarray:
     """Random operator order for every (solution, pass) of Alg. 2: a Fisher-Yates shuffle of
     op_list driven by the stream (seed, 20, solution).  Returns uint8 [n_sol, max_pass, len]."""

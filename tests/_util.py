@@ -56,17 +56,4 @@ def random_neighbor_lists(spec, k, seed):
 
 
 
-def partial_solution(sol, seed, p_route=0.3, p_cust=0.15):
-    """What a route exchange leaves to repair: some routes dropped whole, some single customers
-    dropped; returns (kept routes, unrouted customers in a seeded random order)."""
-    st = W.Stream(seed, 8)
-    keep, unrouted = [], []
-    for r in sol:
-        if st.uniform(1)[0] < p_route:
-            unrouted += r[1:-1]
-            continue
-        cs = [x for x in r[1:-1] if st.uniform(1)[0] >= p_cust or len(r) == 3]
-        unrouted += [x for x in r[1:-1] if x not in cs]
-        keep.append([r[0]] + cs + [r[-1]])
-    perm = np.argsort(st.u64(len(unrouted)))
-    return keep, [unrouted[i] for i in perm]
+partial_solution = W.partial_solution
