@@ -40,6 +40,25 @@ cudaError_t md_allow_smem(const void *func, size_t bytes) {
     return e;
 }
 
+// The library's scratch comes from the current device's default memory pool (cudaMallocAsync).
+// By default the pool hands its memory back to the driver at every synchronisation, so the next
+// call maps it again; keeping it (release threshold at the maximum) makes the stream-ordered
+// allocations of later calls reuse it.  This is a setting of this process's pool only.
+void md_keep_pool() {
+    static std::mutex mu;
+    static std::unordered_map<int, bool> done;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return;
+    std::lock_guard<std::mutex> lock(mu);
+    if (done[dev]) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t keep = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    done[dev] = true;
+}
+
 // c_ij = round(scale * sqrt(dx^2 + dy^2)), half away from zero, FP64 with no contraction; the
 // block also reduces max, min and sum of c over i != j for Theta and Gamma (Eq. A1).
 __global__ void k_dist(int nn, const double *x, const double *y, double scale, int32_t *dist,
@@ -148,6 +167,7 @@ __global__ void k_nbrs(DevInst I, int P, int32_t *nbr, int32_t *nnbr) {
 extern "C" md_status md_instance_create(const md_instance_desc *desc, md_instance **out) {
     if (!desc || !out) { md_set_error("md_instance_create: null argument"); return MD_ERR_ARG; }
     *out = nullptr;
+    md_keep_pool();
     int nd = desc->n_depots, nc = desc->n_customers;
     if (nd < 1 || nc < 1 || (long long)nd + nc > MD_MAX_NODES) {
         md_set_error("md_instance_create: need 1 <= n_depots, 1 <= n_customers, nodes <= %d", MD_MAX_NODES);

@@ -250,6 +250,9 @@ md_status md_cuda_check(cudaError_t e, const char *what);
 // Raises the kernel's maximum dynamic shared memory to at least `bytes` (never lowers it).
 cudaError_t md_allow_smem(const void *func, size_t bytes);
 
+// Keeps the memory of the current device's default pool between calls (once per device).
+void md_keep_pool();
+
 // Launchers implemented in the .cu files.
 md_status md_launch_rebuild_all(md_solutions *s, cudaStream_t st);
 md_status md_launch_totals(md_solutions *s, cudaStream_t st);

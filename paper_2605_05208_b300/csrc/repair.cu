@@ -71,18 +71,20 @@ __device__ __forceinline__ PickKey pick_shfl(const PickKey &k, int o) {
     return r;
 }
 
-// Cheapest insertion of u into route slot r of solution s (feasible ones only when feas): {cost,
-// position}, position -1 when there is none.  Ties keep the earlier position.
+// Cheapest insertion of u into route slot r of solution s over the positions k0, k0 + step, ...
+// (feasible ones only when feas): {cost, position}, position -1 when there is none.  Ties keep
+// the earlier position.
 template <bool TW>
-__device__ int2 route_best(const DevInst &I, const DevSols &D, int s, int r, int u, bool feas) {
+__device__ int2 route_best(const DevInst &I, const DevSols &D, int s, int r, int u, bool feas, int k0 = 0,
+                           int step = 1) {
     const bool open = (I.variant & MD_VARIANT_OPEN) != 0;
     const size_t sr = (size_t)s * D.R + r;
     const int4 h = D.rhdr[sr];
     const int L = h.x, ds = h.y, de = h.z;
     const int32_t *row = D.rnodes + sr * D.K;
     int rc = INT_MAX, rk = -1;
-    int a = ds;
-    for (int k = 0; k <= L; k++) {
+    for (int k = k0; k <= L; k += step) {
+        const int a = k > 0 ? row[k - 1] : ds;
         const int bnode = k < L ? row[k] : (open ? MD_NONE : de);
         const int cau = dcost(I, a, u);
         const int cub = bnode != MD_NONE ? dcost(I, u, bnode) : 0;
@@ -100,7 +102,6 @@ __device__ int2 route_best(const DevInst &I, const DevSols &D, int s, int r, int
             }
             if (ok) { rc = c; rk = k; }
         }
-        a = bnode;
     }
     return make_int2(rc, rk);
 }
@@ -119,7 +120,7 @@ __global__ void __launch_bounds__(256) k_repair(DevInst I, DevSols D, int32_t *u
     int *s_dcount = sm_dyn;              // [nd] routes departing from each depot
     int *s_stage = sm_dyn + I.nd;        // [K] staging of a route's tail
     __shared__ PickKey s_red[8];
-    __shared__ int s_pick, s_stop, s_M, s_dirty;
+    __shared__ int s_stop, s_M, s_dirty;
     const int s = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
     const bool feas = rule == MD_INSERT_FBI || rule == MD_INSERT_FRI;
     const bool regret = rule == MD_INSERT_FRI || rule == MD_INSERT_IRI;
@@ -141,12 +142,30 @@ __global__ void __launch_bounds__(256) k_repair(DevInst I, DevSols D, int32_t *u
     __syncthreads();
     for (int done = 0; done < nU; done++) {
         const int M = s_M;
-        // refresh the columns of the routes that changed (round 0: all of them)
-        const int r_lo = done == 0 ? 0 : s_dirty, r_n = done == 0 ? M : (s_dirty >= 0 ? 1 : 0);
-        for (int t = tid; t < nU * r_n; t += blockDim.x) {
-            const int i = t / r_n, r = r_lo + t % r_n;
-            const int u = U[i];
-            if (u >= 0) rb[(size_t)i * rcap + r] = route_best<TW>(I, D, s, r, u, feas);
+        if (done == 0) {
+            // round 0: every (listed customer, route), one thread each
+            for (int t = tid; t < nU * M; t += blockDim.x) {
+                const int i = t / M, r = t % M;
+                rb[(size_t)i * rcap + r] = route_best<TW>(I, D, s, r, U[i], feas);
+            }
+        } else {
+            // the route that changed, for every listed customer: g lanes per customer split its
+            // positions (g = 1..8, as many as the customers left allow)
+            const int r = s_dirty, left = nU - done;
+            int g = 1;
+            while (g < 8 && 2 * g * left <= (int)blockDim.x) g *= 2;
+            const int groups = blockDim.x / g, sub = tid & (g - 1), grp = tid / g;
+            for (int base = 0; base < nU; base += groups) {
+                const int i = base + grp;
+                const int u = i < nU ? U[i] : -1;
+                int2 e = make_int2(INT_MAX, -1);
+                if (u >= 0) e = route_best<TW>(I, D, s, r, u, feas, sub, g);
+                for (int o = 1; o < g; o <<= 1) {  // min by (cost, position) within the group
+                    const int oc = __shfl_xor_sync(0xffffffffu, e.x, o), ok = __shfl_xor_sync(0xffffffffu, e.y, o);
+                    if (ok >= 0 && (e.y < 0 || oc < e.x || (oc == e.x && ok < e.y))) e = make_int2(oc, ok);
+                }
+                if (u >= 0 && sub == 0) rb[(size_t)i * rcap + r] = e;
+            }
         }
         __syncthreads();
         // per listed customer its best insertion and best cost in another route; the rule's pick
@@ -241,15 +260,13 @@ __global__ void __launch_bounds__(256) k_repair(DevInst I, DevSols D, int32_t *u
                 }
             }
             if (lane == 0) {
-                s_pick = i;
+                U[i] = -1;
                 s_dirty = touched;
                 if (order) order[u0 + done] = u;
             }
         }
         __syncthreads();
         if (s_stop) break;
-        if (tid == 0) U[s_pick] = -1;
-        __syncthreads();
     }
 }
 

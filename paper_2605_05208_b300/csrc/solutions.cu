@@ -210,7 +210,7 @@ md_status md_load_routes(md_solutions *S, const int32_t *nodes, const int64_t *o
     }
     md_status r = finish_load(S, st);
     if (r != MD_OK) return r;
-    MD_CUDA(cudaStreamSynchronize(st));
+    if (!partial) MD_CUDA(cudaStreamSynchronize(st));  // the repair synchronises after its own work
     return MD_OK;
 }
 
