@@ -51,14 +51,27 @@ CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.a
                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
 
-def workload_spec(rank: int = 0):
-    spec = W.mdvrptw_6x288(SEED + rank, theta=THETA)
+def workload_spec(rank: int = 0, workload: str = "mdvrptw-6x288"):
+    if workload == "mdvrp-6x288-2opt":
+        # a symmetric instance without windows, where the intra-route 2-opt has moves: the MDVRP
+        # generator at the size of the MDVRPTW workload, the six operators in every pass
+        spec = W.gen_mdvrp(SEED + rank, n_depots=6, n_customers=288, Q=200, N_V=6, theta=THETA,
+                           name="mdvrp-6x288")
+        ops = tuple(range(W.N_OPS_ALL))
+    else:
+        spec = W.mdvrptw_6x288(SEED + rank, theta=THETA)
+        ops = tuple(range(W.N_OPS))
     sols = W.initial_solutions(spec, SEED + rank, N_SOL)
-    perm = W.op_permutations(SEED + rank, N_SOL, MAX_PASS)
+    perm = W.op_permutations(SEED + rank, N_SOL, MAX_PASS, op_list=ops)
     return spec, sols, perm
 
 
-def workload_name() -> str:
+def workload_name(workload: str = "mdvrptw-6x288") -> str:
+    if workload == "mdvrp-6x288-2opt":
+        return (f"mdvrp-6x288-2opt (6 depots, 288 customers on [0,100]^2, Q=200, N_V=6, no windows, "
+                f"symmetric), theta={THETA}, {N_SOL} solutions, Relocate, Swap, 2-opt*, Depot-Insert, "
+                f"Depot-Replace and 2-opt, full descent to local optimum (delta={MAX_PASS}), multi-move, "
+                f"lambda=(1,1,1,1)")
     return (f"mdvrptw-6x288 (6 depots, 288 customers, horizon 1000, Q=200, N_V=6, D=1000), "
             f"theta={THETA}, {N_SOL} solutions, full descent to local optimum (delta={MAX_PASS}), "
             f"multi-move, lambda=(1,1,1,1)")
@@ -72,20 +85,20 @@ _ORACLE_CACHE = {}
 
 
 def _oracle_descend(args):
-    rank, idx = args
+    rank, idx, workload = args
     from oracle import oracle as O
-    if rank not in _ORACLE_CACHE:
-        spec, sols, perm = workload_spec(rank)
-        _ORACLE_CACHE[rank] = (O.Instance(spec), sols, perm)
-    inst, sols, perm = _ORACLE_CACHE[rank]
+    if (rank, workload) not in _ORACLE_CACHE:
+        spec, sols, perm = workload_spec(rank, workload)
+        _ORACLE_CACHE[(rank, workload)] = (O.Instance(spec), sols, perm)
+    inst, sols, perm = _ORACLE_CACHE[(rank, workload)]
     t0 = time.perf_counter()
     d = inst.descend(sols[idx], perm[idx], MAX_PASS, multi=True)
     return d.moves_scored, time.perf_counter() - t0
 
 
-def oracle_sample(pool, n: int, rank: int = 0):
+def oracle_sample(pool, n: int, rank: int = 0, workload: str = "mdvrptw-6x288"):
     t0 = time.perf_counter()
-    res = pool.map(_oracle_descend, [(rank, i % N_SOL) for i in range(n)])
+    res = pool.map(_oracle_descend, [(rank, i % N_SOL, workload) for i in range(n)])
     wall = time.perf_counter() - t0
     moves = sum(r[0] for r in res)
     cpu = sum(r[1] for r in res)
@@ -113,12 +126,14 @@ def run_reference(args):
         return
     cores = min(os.cpu_count() or 1, 16)
     sample = cores
+    # the descent workloads; the others are timed against the default one's oracle
+    wl = args.workload if args.workload in ("mdvrptw-6x288", "mdvrp-6x288-2opt") else "mdvrptw-6x288"
     pool = make_pool(cores)
     for _ in range(args.warmup):
-        oracle_sample(pool, sample)
+        oracle_sample(pool, sample, workload=wl)
     tot_moves, tot_wall, tot_cpu = 0, 0.0, 0.0
     for _ in range(args.steps):
-        m, w, c = oracle_sample(pool, sample)
+        m, w, c = oracle_sample(pool, sample, workload=wl)
         tot_moves += m
         tot_wall += w
         tot_cpu += c
@@ -130,7 +145,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_wall / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64/f64",
-        "data": "synthetic", "config": {"workload": workload_name(), "sample": desc},
+        "data": "synthetic", "config": {"workload": workload_name(wl), "sample": desc},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
@@ -224,7 +239,8 @@ def run_ours(args):
         ncores = min(os.cpu_count() or 1, 16)
         pool = make_pool(ncores)
 
-    spec, sols, perm = workload_spec(rank)
+    spec, sols, perm = workload_spec(rank, args.workload)
+    n_ops = perm.shape[2]
     inst = mdls.Instance(spec)
     max_routes = max(len(s) for s in sols)
     R = min(spec.n_customers, max(64, 2 * max_routes, spec.n_depots * spec.N_V + 8))
@@ -240,7 +256,7 @@ def run_ours(args):
     def step(time_eval=False):
         work.copy_from(init, stream=sptr)
         return work.descend(perm_dev.data_ptr(), MAX_PASS, multi=True, use_graph=True, poll_every=1,
-                            stream=sptr, n_ops=W.N_OPS, time_eval=time_eval, n_groups=args.groups,
+                            stream=sptr, n_ops=n_ops, time_eval=time_eval, n_groups=args.groups,
                             persistent=persistent)
 
     for _ in range(args.warmup):
@@ -306,7 +322,7 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and pool is not None:
-        m, wall, cpu_s = oracle_sample(pool, pool._processes)
+        m, wall, cpu_s = oracle_sample(pool, pool._processes, workload=args.workload)
         desc = (f"{pool._processes} of the {N_SOL} descents of this workload, one per process; "
                 f"{cpu_s:.1f} s CPU, {wall:.1f} s wall")
         cpu = {"value": m / wall, "unit": UNIT, "cores": pool._processes, "kind": "oracle", "sample": desc}
@@ -318,7 +334,7 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32/f64", "data": "synthetic",
-            "config": {"workload": workload_name(), "l2": "flushed between timed steps (256 MB write)",
+            "config": {"workload": workload_name(args.workload), "l2": "flushed between timed steps (256 MB write)",
                        "route_slots": R, "k_max": K,
                        "launch": ("one persistent launch per descent" if persistent else
                                   f"CUDA graph per pass, {args.groups} concurrent solution groups"),
@@ -326,12 +342,14 @@ def run_ours(args):
             "descents_per_s": descents,
             "moves_per_step": moves / args.steps,
             "passes_max": last.passes_max, "steps_per_descent": last.steps / N_SOL,
+            "moves_per_step_by_op": [int(x) // args.steps for x in by_op],
             "roofline": {"kernel": ("k_descend_persistent (evaluation and steps, one launch per descent)"
                                     if persistent else "k_eval (neighbourhood evaluation)"),
                          "bound": "hbm",
                          "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "peak_source": peak_src,
-                         "traffic": TRAFFIC_6X288["persistent" if persistent else "eval"],
+                         "traffic": (TRAFFIC_6X288["persistent" if persistent else "eval"]
+                                     if args.workload == "mdvrptw-6x288" else None),
                          "ms_per_launch": eval_ms / max(eval_launches, 1),
                          "alg_bytes_per_launch": alg_bytes / max(eval_launches, 1),
                          "note": ("the launch also runs the steps (selection, apply, rebuild)" if persistent
@@ -805,7 +823,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", choices=["mdvrptw-6x288", "batch16-uneven", "learned-20x10000",
-                                           "plain-20x10000", "repair-mdvrptw-6x288"], default="mdvrptw-6x288")
+                                           "plain-20x10000", "repair-mdvrptw-6x288", "mdvrp-6x288-2opt"],
+                    default="mdvrptw-6x288")
     ap.add_argument("--solutions", type=int, default=0, help="solutions of the learned workload (0: 8)")
     ap.add_argument("--plain-steps", type=int, default=1,
                     help="timed plain full-neighbourhood descents beside the learned workload")

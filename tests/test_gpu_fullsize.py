@@ -65,6 +65,27 @@ def test_bench_descent_sampled_against_oracle(md, oracle_lib, stream, form):
         assert list(per[s]) == [d.moves_scored, d.steps, d.accepted_steps, d.applied_moves, d.passes]
 
 
+def test_six_operator_descent_sampled_against_oracle(md, oracle_lib, stream):
+    # the MDVRP 6x288 workload with the intra-route 2-opt in every pass, as the benchmark's
+    # persistent launch runs it, against oracle descents of sampled solutions
+    spec = W.gen_mdvrp(1, n_depots=6, n_customers=288, Q=200, N_V=6, theta=50, name="mdvrp-6x288")
+    sols = W.initial_solutions(spec, 1, 32)
+    perm = W.op_permutations(1, 32, 500, op_list=tuple(range(W.N_OPS_ALL)))
+    inst = md.Instance(spec)
+    R = min(spec.n_customers, max(64, 2 * max(len(s) for s in sols), spec.n_depots * spec.N_V + 8))
+    S = md.Solutions(inst, 32, R, 64)
+    S.load(sols)
+    st = S.descend(perm, 500, multi=True, use_graph=False, persistent=True, stream=stream.cuda_stream,
+                   time_eval=True)
+    assert st.moves_by_op[W.OP_TWO_OPT] > 0
+    got, per = S.read(stream=stream.cuda_stream), S.stats(stream=stream.cuda_stream)
+    o = oracle_lib.Instance(spec)
+    for s in (0, 31):
+        d = o.descend(sols[s], perm[s], 500, multi=True)
+        assert W.canonical(got[s]) == W.canonical(d.solution), s
+        assert list(per[s]) == [d.moves_scored, d.steps, d.accepted_steps, d.applied_moves, d.passes]
+
+
 def _check_leaders(md, oracle_lib, spec, sols, sampled, sampled_ops, lists=False):
     inst = md.Instance(spec)
     R, K = _slots(spec, sols)
