@@ -10,8 +10,9 @@
 // the route's cheapest insertion; an insertion changes one route, so each round rescans only
 // that route's positions for every listed customer (the first round scans all routes).  Per
 // customer the block then forms its best insertion and its best cost in another route (for the
-// regret), picks the customer by the rule; warp 0 inserts it and rebuilds that route's
-// summaries.  Ties break as the rules state: cost, then the customer's place in the list, then
+// regret), picks the customer by the rule; warp 0 inserts it and rebuilds that route's prefix
+// and suffix summaries (the subsequence tables, which only the descent reads, are rebuilt once
+// at the end).  Ties break as the rules state: cost, then the customer's place in the list, then
 // route slot, then position.
 #include <limits.h>
 #include <string.h>
@@ -229,7 +230,7 @@ __global__ void __launch_bounds__(256) k_repair(DevInst I, DevSols D, int32_t *u
                         D.rhdr[sr] = make_int4(L + 1, h.y, h.z, h.w);
                     }
                     __syncwarp();
-                    rebuild_route<TW>(I, D, s, r);
+                    rebuild_route<TW, false>(I, D, s, r);
                     touched = r;
                 }
             } else {
@@ -255,7 +256,7 @@ __global__ void __launch_bounds__(256) k_repair(DevInst I, DevSols D, int32_t *u
                         s_M = M + 1;
                     }
                     __syncwarp();
-                    rebuild_route<TW>(I, D, s, slot);
+                    rebuild_route<TW, false>(I, D, s, slot);
                     touched = slot;
                 }
             }
@@ -337,6 +338,8 @@ extern "C" md_status md_repair_insert(md_solutions *S, int32_t rule, const int32
             k_repair<false><<<S->n_sol, 256, smem, st>>>(I, S->d, du, doff, drb, drboff, dres, dord, rule);
         }
         MD_CUDA(cudaGetLastError());
+        r = md_launch_rebuild_all(S, st);  // the subsequence tables of the long routes
+        if (r != MD_OK) return r;
         r = md_launch_totals(S, st);
         if (r != MD_OK) return r;
         if (order) MD_CUDA(cudaMemcpyAsync(order, dord, sizeof(int32_t) * nu, cudaMemcpyDeviceToHost, st));

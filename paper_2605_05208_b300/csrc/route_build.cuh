@@ -59,7 +59,9 @@ __device__ __forceinline__ SegN segn_node(const DevInst &I, int n) {
 }
 
 // Rebuilds every summary of route slot r of solution s; called by all 32 lanes of one warp.
-template <bool TW>
+// SUBTABLES = false leaves the subsequence tables of routes longer than 32 customers stale (the
+// repair insertion, which reads only prefixes and suffixes, rebuilds them once at its end).
+template <bool TW, bool SUBTABLES = true>
 __device__ void rebuild_route(const DevInst &I, const DevSols &D, int s, int r) {
     const int lane = threadIdx.x & 31;
     const size_t sr = (size_t)s * D.R + r;
@@ -175,7 +177,7 @@ __device__ void rebuild_route(const DevInst &I, const DevSols &D, int s, int r) 
     }
     // subsequence tables: lane i folds from position k = i + 1 (chunks of 32) to the route's
     // end and to its start
-    for (int base = 0; base < L; base += 32) {
+    for (int base = 0; SUBTABLES && base < L; base += 32) {
         const int k0 = base + lane;  // 0-based position
         if (k0 >= L) break;
         const int c = nodes[k0];

@@ -86,6 +86,31 @@ def test_six_operator_descent_sampled_against_oracle(md, oracle_lib, stream):
         assert list(per[s]) == [d.moves_scored, d.steps, d.accepted_steps, d.applied_moves, d.passes]
 
 
+def test_repair_bench_configuration_against_oracle(md, oracle_lib):
+    # the repair benchmark's 32 partial solutions of the MDVRPTW 6x288 instance, every rule,
+    # every solution against the oracle; then a descent from the repaired solutions, which reads
+    # the summaries and subsequence tables the repair leaves
+    spec = W.mdvrptw_6x288(1, theta=50)
+    parts = [W.partial_solution(sol, 501 + i, p_route=0.25, p_cust=0.1)
+             for i, sol in enumerate(W.initial_solutions(spec, 1, 32))]
+    keep, un = [p[0] for p in parts], [p[1] for p in parts]
+    inst = md.Instance(spec)
+    S = md.Solutions(inst, 32, spec.n_customers + 1, spec.n_customers)
+    o = oracle_lib.Instance(spec)
+    for rule in range(4):
+        order = S.repair(keep, un, rule)
+        got = S.read()
+        for s in range(32):
+            want, worder = o.repair(keep[s], un[s], rule)
+            assert got[s] == want and order[s] == worder, (rule, s)
+    perm = W.op_permutations(2, 32, 40)
+    S.descend(perm, 40, multi=True)
+    after = S.read()
+    for s in (0, 17):
+        d = o.descend(got[s], perm[s], 40, multi=True)
+        assert W.canonical(after[s]) == W.canonical(d.solution), s
+
+
 def _check_leaders(md, oracle_lib, spec, sols, sampled, sampled_ops, lists=False):
     inst = md.Instance(spec)
     R, K = _slots(spec, sols)
