@@ -741,6 +741,86 @@ def run_repair(args):
     }))
 
 
+class _OracleBackend:
+    """The memetic loop's repair and descent through the oracle (the CPU baseline leg only)."""
+
+    def __init__(self, spec):
+        from oracle import oracle as O
+        self.o = O.Instance(spec)
+        self.Theta, self.Gamma = self.o.Theta, self.o.Gamma
+
+    def repair_descend(self, partials, unrouted, rules, perms, max_pass):
+        sols, comps = [], []
+        for k, (p, u, rule) in enumerate(zip(partials, unrouted, rules)):
+            rep = self.o.repair(p, u, int(rule))[0] if u else p
+            d = self.o.descend(rep, perms[k], max_pass, multi=True, lambda_update=True)
+            T, _ = self.o.solution_terms(d.solution)
+            sols.append(d.solution)
+            comps.append([T[x] for x in ("D", "TW", "LoadEx", "DurEx", "closure", "vehEx", "V4", "nroutes")])
+        return sols, np.asarray(comps, np.int64)
+
+
+MEMETIC_RUNS, MEMETIC_MU = 10, 20
+
+
+def run_memetic(args):
+    """MDFIHA (Alg. 1) on the bench instance: 10 independent runs in lockstep, population 20,
+    delta 500, adaptive lambda; one step is one generation of every run (10 offspring: DCREX on
+    the host, their repairs in one launch, their MDFIS descents in one persistent launch)."""
+    import torch
+    from paper_2605_05208_b300 import build, memetic as MM
+    build.build()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    spec, _, _ = workload_spec(0)
+    mm = MM.MDFIHA(spec, n_runs=MEMETIC_RUNS, mu=MEMETIC_MU, delta=MAX_PASS, seed=SEED,
+                   backend=MM.GpuBackend(spec, stream=stream.cuda_stream))
+    t0 = time.perf_counter()
+    mm.initialize()
+    init_s = time.perf_counter() - t0
+    for _ in range(args.warmup):
+        mm.generation()
+    torch.cuda.synchronize()
+    ms = []
+    with ClockSampler(0) as clk:
+        for _ in range(args.steps):
+            t = time.perf_counter()
+            mm.generation()
+            torch.cuda.synchronize()
+            ms.append(1e3 * (time.perf_counter() - t))
+    total_ms = sum(ms)
+    value = MEMETIC_RUNS * args.steps / (total_ms / 1e3)
+    cpu = None
+    if not args.no_cpu_baseline:
+        from paper_2605_05208_b300 import memetic as MM2
+        om = MM2.MDFIHA(spec, n_runs=1, mu=MEMETIC_MU, delta=MAX_PASS, seed=SEED, backend=_OracleBackend(spec))
+        om.initialize()
+        for _ in range(2):
+            om.generation()
+        t = time.perf_counter()
+        ng = 5
+        for _ in range(ng):
+            om.generation()
+        wall = time.perf_counter() - t
+        cpu = {"value": ng / wall, "unit": "offspring/s", "cores": 1, "kind": "oracle",
+               "sample": f"one run of the same loop with the oracle's repair and descent, {ng} generations "
+                         f"after its initialisation and 2 more, {wall:.1f} s"}
+    best = [r.best for r in mm.runs]
+    print(json.dumps({
+        "metric": "offspring/s", "value": value, "unit": "offspring/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / max(args.steps, 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32/f64", "data": "synthetic",
+        "config": {"workload": f"memetic-mdvrptw-6x288: MDFIHA on the mdvrptw-6x288 bench instance, "
+                               f"{MEMETIC_RUNS} independent runs in lockstep, population {MEMETIC_MU}, "
+                               f"delta={MAX_PASS}, adaptive lambda; a step is one generation of every run",
+                   "timed": "host DCREX and population update, GPU repair and descent, host readback"},
+        "init_s": init_s, "generations": mm.gen, "best_f_mean": float(np.mean(best)),
+        "cpu_baseline": cpu,
+        "clocks": clk.summary(),
+    }))
+
+
 def run_plain_large(args):
     """Plain full-neighbourhood descents of the 20-depot, 10000-customer MDVRPTW instance (every
     customer a candidate of every customer; the 401.6 MB distance matrix does not fit in L2).
@@ -823,7 +903,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", choices=["mdvrptw-6x288", "batch16-uneven", "learned-20x10000",
-                                           "plain-20x10000", "repair-mdvrptw-6x288", "mdvrp-6x288-2opt"],
+                                           "plain-20x10000", "repair-mdvrptw-6x288", "mdvrp-6x288-2opt",
+                                           "memetic-mdvrptw-6x288"],
                     default="mdvrptw-6x288")
     ap.add_argument("--solutions", type=int, default=0, help="solutions of the learned workload (0: 8)")
     ap.add_argument("--plain-steps", type=int, default=1,
@@ -847,6 +928,8 @@ def main():
         run_plain_large(args)
     elif args.workload == "repair-mdvrptw-6x288":
         run_repair(args)
+    elif args.workload == "memetic-mdvrptw-6x288":
+        run_memetic(args)
     else:
         run_ours(args)
 

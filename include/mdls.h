@@ -312,8 +312,8 @@ md_status md_solutions_stats(md_solutions *sols, int64_t *per_sol, void *stream)
 #define MD_INSERT_FRI 2
 #define MD_INSERT_IRI 3
 
-/* Loads partial solutions and inserts their unrouted customers by `rule` (MD_INSERT_*), one
- * CTA per solution on the device; on return sols holds complete solutions with every summary
+/* Loads partial solutions and inserts the unrouted customers of solution s by rules[s]
+ * (MD_INSERT_*; host int32 [n_sol]), one CTA per solution on the device; on return sols holds complete solutions with every summary
  * and total rebuilt (lambda reset to 1), ready for md_descend.
  *   route_nodes / route_offsets / routes_per_sol: host, the md_solutions_load layout, except
  *     that a solution may have no route (routes_per_sol[s] = 0) and leaves customers out;
@@ -327,7 +327,7 @@ md_status md_solutions_stats(md_solutions *sols, int64_t *per_sol, void *stream)
  * list) and the routes are well formed; MD_ERR_CAPACITY when a route would exceed k_max or a
  * new route finds no free slot (the solution then holds a partial repair).  Synchronises the
  * stream. */
-md_status md_repair_insert(md_solutions *sols, int32_t rule, const int32_t *route_nodes,
+md_status md_repair_insert(md_solutions *sols, const int32_t *rules, const int32_t *route_nodes,
                            const int64_t *route_offsets, const int32_t *routes_per_sol,
                            const int32_t *unrouted, const int64_t *unrouted_offsets, int32_t *order,
                            void *stream);

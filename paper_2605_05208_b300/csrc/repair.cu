@@ -116,13 +116,14 @@ __device__ int2 route_best(const DevInst &I, const DevSols &D, int s, int r, int
 template <bool TW>
 __global__ void __launch_bounds__(256) k_repair(DevInst I, DevSols D, int32_t *ulist, const int64_t *uoff,
                                                 int2 *RB, const int64_t *rb_off, InsBest *res, int32_t *order,
-                                                int rule) {
+                                                const int32_t *rules) {
     extern __shared__ int sm_dyn[];
     int *s_dcount = sm_dyn;              // [nd] routes departing from each depot
     int *s_stage = sm_dyn + I.nd;        // [K] staging of a route's tail
     __shared__ PickKey s_red[8];
     __shared__ int s_stop, s_M, s_dirty;
     const int s = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const int rule = rules[s];
     const bool feas = rule == MD_INSERT_FBI || rule == MD_INSERT_FRI;
     const bool regret = rule == MD_INSERT_FRI || rule == MD_INSERT_IRI;
     const bool open = (I.variant & MD_VARIANT_OPEN) != 0;
@@ -273,11 +274,15 @@ __global__ void __launch_bounds__(256) k_repair(DevInst I, DevSols D, int32_t *u
 
 }  // namespace
 
-extern "C" md_status md_repair_insert(md_solutions *S, int32_t rule, const int32_t *nodes, const int64_t *off,
+extern "C" md_status md_repair_insert(md_solutions *S, const int32_t *rules, const int32_t *nodes, const int64_t *off,
                                       const int32_t *per_sol, const int32_t *unrouted, const int64_t *unrouted_off,
                                       int32_t *order, void *stream) {
-    if (!S || !per_sol || !unrouted_off) { md_set_error("md_repair_insert: null argument"); return MD_ERR_ARG; }
-    if (rule < MD_INSERT_FBI || rule > MD_INSERT_IRI) { md_set_error("md_repair_insert: unknown rule %d", rule); return MD_ERR_ARG; }
+    if (!S || !rules || !per_sol || !unrouted_off) { md_set_error("md_repair_insert: null argument"); return MD_ERR_ARG; }
+    for (int s = 0; s < S->n_sol; s++)
+        if (rules[s] < MD_INSERT_FBI || rules[s] > MD_INSERT_IRI) {
+            md_set_error("md_repair_insert: unknown rule %d for solution %d", rules[s], s);
+            return MD_ERR_ARG;
+        }
     cudaStream_t st = (cudaStream_t)stream;
     const DevInst &I = S->inst->d;
     // every customer exactly once per solution, in a route or in the unrouted list
@@ -326,16 +331,19 @@ extern "C" md_status md_repair_insert(md_solutions *S, int32_t rule, const int32
         int64_t *drboff = nullptr;
         MD_CUDA(cudaMallocAsync(&drb, sizeof(int2) * std::max<int64_t>(rboff[S->n_sol], 1), st));
         MD_CUDA(cudaMallocAsync(&drboff, sizeof(int64_t) * (S->n_sol + 1), st));
+        int32_t *drules = nullptr;
+        MD_CUDA(cudaMallocAsync(&drules, sizeof(int32_t) * S->n_sol, st));
+        MD_CUDA(cudaMemcpyAsync(drules, rules, sizeof(int32_t) * S->n_sol, cudaMemcpyHostToDevice, st));
         MD_CUDA(cudaMemcpyAsync(drboff, rboff.data(), sizeof(int64_t) * (S->n_sol + 1), cudaMemcpyHostToDevice, st));
         MD_CUDA(cudaMemcpyAsync(du, unrouted, sizeof(int32_t) * nu, cudaMemcpyHostToDevice, st));
         MD_CUDA(cudaMemcpyAsync(doff, unrouted_off, sizeof(int64_t) * (S->n_sol + 1), cudaMemcpyHostToDevice, st));
         const size_t smem = sizeof(int) * ((size_t)I.nd + S->K);
         if (I.variant & MD_VARIANT_TW) {
             MD_CUDA(md_allow_smem((const void *)k_repair<true>, smem));
-            k_repair<true><<<S->n_sol, 256, smem, st>>>(I, S->d, du, doff, drb, drboff, dres, dord, rule);
+            k_repair<true><<<S->n_sol, 256, smem, st>>>(I, S->d, du, doff, drb, drboff, dres, dord, drules);
         } else {
             MD_CUDA(md_allow_smem((const void *)k_repair<false>, smem));
-            k_repair<false><<<S->n_sol, 256, smem, st>>>(I, S->d, du, doff, drb, drboff, dres, dord, rule);
+            k_repair<false><<<S->n_sol, 256, smem, st>>>(I, S->d, du, doff, drb, drboff, dres, dord, drules);
         }
         MD_CUDA(cudaGetLastError());
         r = md_launch_rebuild_all(S, st);  // the subsequence tables of the long routes
@@ -349,6 +357,7 @@ extern "C" md_status md_repair_insert(md_solutions *S, int32_t rule, const int32
         MD_CUDA(cudaFreeAsync(doff, st));
         MD_CUDA(cudaFreeAsync(drb, st));
         MD_CUDA(cudaFreeAsync(drboff, st));
+        MD_CUDA(cudaFreeAsync(drules, st));
     }
     int32_t err = 0;
     MD_CUDA(cudaMemcpyAsync(&err, S->d.err, sizeof(err), cudaMemcpyDeviceToHost, st));

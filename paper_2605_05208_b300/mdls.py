@@ -106,7 +106,7 @@ def lib() -> C.CDLL:
             "md_solutions_create": [P, C.c_int32, C.c_int32, C.c_int32, PP],
             "md_solutions_destroy": [P],
             "md_solutions_load": [P, P, P, P, P],
-            "md_repair_insert": [P, C.c_int32, P, P, P, P, P, P, P],
+            "md_repair_insert": [P, P, P, P, P, P, P, P, P],
             "md_solutions_copy": [P, P, P],
             "md_solutions_read": [P, P, P, P, C.c_int64, C.c_int64, P],
             "md_solution_cost": [P, P, P, P],
@@ -280,15 +280,17 @@ class Solutions:
     def repair(self, partial, unrouted, rule, stream=None):
         """Loads the partial solutions `partial` (lists of routes; a solution may have none) and
         inserts each solution's unrouted customers (`unrouted[s]`, in order of preference) by
-        `rule` (INSERT_FBI, INSERT_IBI, INSERT_FRI, INSERT_IRI), on the device (Section 3.3).
-        Returns per solution the customers in the order they were inserted."""
+        `rule` (INSERT_FBI, INSERT_IBI, INSERT_FRI, INSERT_IRI; one for all solutions, or one per
+        solution), on the device (Section 3.3).  Returns per solution the customers in the order
+        they were inserted."""
         assert len(partial) == self.n_sol == len(unrouted)
+        rules = np.ascontiguousarray(np.broadcast_to(np.asarray(rule, dtype=np.int32), (self.n_sol,)))
         nodes, offs, per = flatten(partial)
         un = np.asarray([c for u in unrouted for c in u] or [0], dtype=np.int32)
         uoff = np.zeros(self.n_sol + 1, dtype=np.int64)
         uoff[1:] = np.cumsum([len(u) for u in unrouted])
         order = np.zeros(max(int(uoff[-1]), 1), dtype=np.int32)
-        _check(lib().md_repair_insert(self.h, int(rule), _ptr(nodes) if len(nodes) else None,
+        _check(lib().md_repair_insert(self.h, _ptr(rules), _ptr(nodes) if len(nodes) else None,
                                       _ptr(offs) if len(nodes) else None, _ptr(per), _ptr(un), _ptr(uoff),
                                       _ptr(order), _stream(stream)))
         return [[int(x) for x in order[uoff[s]:uoff[s + 1]]] for s in range(self.n_sol)]

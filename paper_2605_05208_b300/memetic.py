@@ -1,0 +1,303 @@
+"""MDFIHA's memetic loop (Alg. 1) around the GPU hot path, for several independent runs at once.
+
+Every generation of Alg. 1 makes one offspring: the route-exchange crossover DCREX (Alg. 3,
+Section 3.3) builds a partial solution from a main parent and other parents, the repair
+insertion fills in its unrouted customers (Section 3.3), MDFIS (Alg. 2) descends from it with
+adaptive penalty coefficients, and the population update (Section 3.4) keeps the population's
+fitness and diversity.  One generation is sequential within a run, so the B300 form advances
+`n_runs` independent runs in lockstep (the paper solves each instance in several independent
+runs): each generation's repairs are one `md_repair_insert` launch and their descents one
+`md_descend` call for all runs.  The host part -- route-pair scores, route exchange, the
+discounted UCB1 choices (Eq. 6) and the fitness-and-distance ranking (Eq. 7-9) -- is small
+per run and stays on the CPU.
+
+Readings where the paper is silent:
+- DCREX scores route pairs (R_i, R_j) with R_i a route of the main parent still in the
+  offspring and R_j a route of the current other parent:
+  - E^I counts the distinct edges of R_j that the offspring does not have;
+  - N^R counts the customers of R_i that R_j does not visit;
+  - N^M counts the customers of R_j that the offspring visits outside R_i;
+  - N^C counts the customers of R_j that routes introduced earlier in this crossover visit.
+- The random pick among the five lowest scores is uniform, with ties ordered by (R_i, R_j).
+- R_j takes R_i's place in the offspring.
+- The other parents are visited in a random order.
+- Redundant customers keep their place in the earliest-introduced route that visits them and
+  leave every other route.  A route left empty is dropped.
+- The unrouted customers go to the repair in increasing node order.
+- Edges are undirected pairs of consecutive nodes, depots included; open routes have no
+  return edge.
+- f (ranking, rewards, the best solution) is F with unit penalty coefficients.
+- The random insertion RI is not among the bandit's arms: the four evaluated rules are.
+- When the population reaches 1.5 mu it is cut back to mu by removing the solution of lowest
+  chi, recomputing chi after each removal.
+- Unplayed bandit arms are tried first, in index order.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import workloads as W
+
+N_DEGREES = 20     # diversity degrees sigma_i = i / 20 (Alg. 3)
+N_RULES = 4        # FBI, IBI, FRI, IRI (Section 3.3)
+GAMMA_D = 0.99     # discount factor of the UCB1 bandits (Section 3.3)
+
+
+class DiscountedUCB1:
+    """Discounted UCB1 of Eq. (6): after each play every arm's discounted reward sum and count
+    are multiplied by gamma and the played arm adds (reward, 1)."""
+
+    def __init__(self, n_arms: int, gamma: float = GAMMA_D):
+        self.R = np.zeros(n_arms)
+        self.N = np.zeros(n_arms)
+        self.gamma = gamma
+
+    def select(self) -> int:
+        unplayed = np.flatnonzero(self.N == 0)
+        if len(unplayed):
+            return int(unplayed[0])
+        total = self.N.sum()
+        ucb = self.R / self.N + np.sqrt(2.0 * math.log(total) / self.N)
+        return int(np.argmax(ucb))
+
+    def update(self, arm: int, reward: float):
+        self.R *= self.gamma
+        self.N *= self.gamma
+        self.R[arm] += reward
+        self.N[arm] += 1.0
+
+
+def route_edges(route, open_routes: bool) -> set:
+    last = len(route) - 2 if open_routes else len(route) - 1
+    return {(min(a, b), max(a, b)) for a, b in zip(route[:last], route[1:last + 1])}
+
+
+def solution_edges(sol, open_routes: bool) -> set:
+    out = set()
+    for r in sol:
+        out |= route_edges(r, open_routes)
+    return out
+
+
+def solution_distance(e1: set, e2: set) -> float:
+    """D_S of Eq. (9): 100 (1 - |E1 & E2| / max(|E1|, |E2|))."""
+    m = max(len(e1), len(e2))
+    return 0.0 if m == 0 else 100.0 * (1.0 - len(e1 & e2) / m)
+
+
+def chi_scores(f: np.ndarray, edges: list, xi: float) -> np.ndarray:
+    """chi of Eq. (7) for every member: rank 1 is the lowest f, and the largest mean distance to
+    the five nearest other members (Eq. 8); ties by index."""
+    n = len(f)
+    d = np.zeros((n, n))
+    for a in range(n):
+        for b in range(a + 1, n):
+            d[a, b] = d[b, a] = solution_distance(edges[a], edges[b])
+    dp = np.zeros(n)
+    for a in range(n):
+        others = np.sort(np.delete(d[a], a))
+        dp[a] = others[:5].mean() if len(others) else 0.0
+    rank_f = np.empty(n)
+    rank_f[np.lexsort((np.arange(n), f))] = np.arange(1, n + 1)
+    rank_d = np.empty(n)
+    rank_d[np.lexsort((np.arange(n), -dp))] = np.arange(1, n + 1)
+    return (n - rank_f) / n + xi * (n - rank_d) / n
+
+
+def unit_f(comps: np.ndarray, Theta: int, Gamma: float, Q: int, D: int) -> float:
+    """F of Eq. (A1) with unit penalty coefficients, from the integer terms (D, TW, LoadEx,
+    DurEx, ..., V4 at index 6), combined left to right in FP64."""
+    w = (Gamma, Theta / Q, Theta / D if D > 0 else 0.0, float(Theta))
+    f = float(comps[0])
+    f = f + w[0] * float(comps[1])
+    f = f + w[1] * float(comps[2])
+    f = f + w[2] * float(comps[3])
+    f = f + w[3] * float(comps[6])
+    return f
+
+
+def dcrex(main, others, degree: int, st: W.Stream, n_depots: int, n_customers: int, open_routes: bool):
+    """Route exchange of Alg. 3 (its route-pair loop and the removal of redundant customers).
+    Returns (partial routes, unrouted customers in increasing order)."""
+    S = [list(r) for r in main]
+    intro = [-1] * len(S)  # introduction order of each route (-1: the main parent's)
+    m = len(main)
+    smin = degree / N_DEGREES * (n_customers + m)
+    smax = (degree + 1) / N_DEGREES * (n_customers + m)
+    cur = 0
+    intro_cust = set()
+    n_intro = 0
+    for P in others:
+        have = solution_edges(S, open_routes)
+        where = {c: i for i, r in enumerate(S) for c in r[1:-1]}
+        cand = []
+        for i, Ri in enumerate(S):
+            if intro[i] >= 0:
+                continue
+            Ci = set(Ri[1:-1])
+            for j, Rj in enumerate(P):
+                Cj = Rj[1:-1]
+                ei = sum(1 for e in route_edges(Rj, open_routes) if e not in have)
+                nr = len(Ci - set(Cj))
+                nm = sum(1 for c in Cj if c in where and where[c] != i)
+                nc = sum(1 for c in Cj if c in intro_cust)
+                cand.append((-(ei - nr - nm - 10 * nc), i, j, ei + nr + nm))
+        if not cand:
+            break
+        cand.sort()
+        k = int(st.randint(0, min(5, len(cand)) - 1, 1)[0])
+        _, i, j, dsig = cand[k]
+        S[i] = list(P[j])
+        intro[i] = n_intro
+        n_intro += 1
+        intro_cust |= set(P[j][1:-1])
+        cur += dsig
+        if cur >= smax:
+            continue
+        if cur >= smin:
+            break
+    # redundant customers stay in the earliest-introduced route that visits them
+    keep_in = {}
+    for i in sorted((i for i in range(len(S)) if intro[i] >= 0), key=lambda i: intro[i]):
+        for c in S[i][1:-1]:
+            keep_in.setdefault(c, i)
+    out = []
+    for i, r in enumerate(S):
+        cs = [c for c in r[1:-1] if keep_in.get(c, i) == i]
+        if cs:
+            out.append([r[0]] + cs + [r[-1]])
+    routed = {c for r in out for c in r[1:-1]}
+    return out, [c for c in range(n_depots, n_depots + n_customers) if c not in routed]
+
+
+class GpuBackend:
+    """Repairs and descends a batch of offspring through the C ABI (md_repair_insert,
+    md_descend with adaptive lambda)."""
+
+    def __init__(self, spec, stream=None, persistent: bool = True):
+        from . import mdls
+        self.mdls = mdls
+        self.spec = spec
+        self.inst = mdls.Instance(spec)
+        self.Theta, self.Gamma = self.inst.params()
+        self.stream = stream
+        self.persistent = persistent
+        self._sols = {}
+
+    def _solutions(self, n):
+        if n not in self._sols:
+            nc = self.spec.n_customers
+            self._sols[n] = self.mdls.Solutions(self.inst, n, nc + 1, nc)
+        return self._sols[n]
+
+    def repair_descend(self, partials, unrouted, rules, perms, max_pass):
+        S = self._solutions(len(partials))
+        S.repair(partials, unrouted, np.asarray(rules, np.int32), stream=self.stream)
+        S.descend(perms, max_pass, multi=True, lambda_update=True, use_graph=not self.persistent,
+                  persistent=self.persistent, stream=self.stream)
+        comps, _ = S.cost(stream=self.stream)
+        return S.read(stream=self.stream), comps
+
+
+@dataclass
+class Run:
+    pop: list = field(default_factory=list)    # routes of each member
+    f: list = field(default_factory=list)      # unit-lambda F of each member
+    best: float = math.inf
+    best_sol: list | None = None
+    stagnation: int = 0
+    deg: DiscountedUCB1 = field(default_factory=lambda: DiscountedUCB1(N_DEGREES))
+    rule: DiscountedUCB1 = field(default_factory=lambda: DiscountedUCB1(N_RULES))
+
+
+class MDFIHA:
+    """n_runs independent runs of Alg. 1 in lockstep.  backend: an object with repair_descend
+    (GpuBackend by default) and the instance's Theta and Gamma."""
+
+    def __init__(self, spec, n_runs: int, mu: int = 20, xi: float = 0.7, delta: int = 500, seed: int = 1,
+                 backend=None, n_ops: int = W.N_OPS):
+        self.spec = spec
+        self.n_runs = n_runs
+        self.mu = mu
+        self.xi = xi
+        self.delta = delta
+        self.seed = seed
+        self.n_ops = n_ops
+        self.open = bool(spec.variant & W.VAR_OPEN)
+        self.backend = backend if backend is not None else GpuBackend(spec)
+        self.gen = 0
+        self.runs = [Run() for _ in range(n_runs)]
+        self.streams = [W.Stream(seed, 40, r) for r in range(n_runs)]
+        self.offspring = 0
+
+    def _f(self, comps) -> float:
+        return unit_f(comps, self.backend.Theta, self.backend.Gamma, self.spec.Q, self.spec.D)
+
+    def _perms(self, n: int) -> np.ndarray:
+        ops = tuple(range(self.n_ops))
+        return W.op_permutations(self.seed * 100003 + self.gen, n, self.delta, op_list=ops)
+
+    def initialize(self):
+        """Initial populations (the seeded sweep construction stands in for Section 3.1), each
+        member descended by MDFIS, all runs in one batch."""
+        sols = []
+        for r in range(self.n_runs):
+            sols += W.initial_solutions(self.spec, self.seed * 1000 + r, self.mu)
+        self.gen = 0
+        got, comps = self.backend.repair_descend(sols, [[] for _ in sols], [0] * len(sols),
+                                                 self._perms(len(sols)), self.delta)
+        for r, run in enumerate(self.runs):
+            for k in range(self.mu):
+                i = r * self.mu + k
+                run.pop.append(got[i])
+                run.f.append(self._f(comps[i]))
+            b = int(np.argmin(run.f))
+            run.best, run.best_sol = run.f[b], run.pop[b]
+
+    def generation(self):
+        """One generation of Alg. 1 in every run: DCREX, repair, MDFIS, population update."""
+        self.gen += 1
+        partials, unrouted, rules, mains, degs = [], [], [], [], []
+        for r, run in enumerate(self.runs):
+            st = self.streams[r]
+            n = len(run.pop)
+            m = int(st.randint(0, n - 1, 1)[0])
+            order = [i for i in np.argsort(st.u64(n)).tolist() if i != m]
+            d = run.deg.select()
+            rule = run.rule.select()
+            part, un = dcrex(run.pop[m], [run.pop[i] for i in order], d, st, self.spec.n_depots,
+                             self.spec.n_customers, self.open)
+            partials.append(part)
+            unrouted.append(un)
+            rules.append(rule)
+            mains.append(m)
+            degs.append(d)
+        got, comps = self.backend.repair_descend(partials, unrouted, rules, self._perms(self.n_runs), self.delta)
+        for r, run in enumerate(self.runs):
+            f = self._f(comps[r])
+            fm = run.f[mains[r]]
+            reward = 100.0 * (fm - f) / fm if fm != 0 else 0.0
+            run.deg.update(degs[r], reward)
+            run.rule.update(rules[r], reward)
+            run.pop.append(got[r])
+            run.f.append(f)
+            if len(run.pop) >= math.ceil(1.5 * self.mu):
+                self._reduce(run)
+            if f < run.best:
+                run.best, run.best_sol, run.stagnation = f, got[r], 0
+            else:
+                run.stagnation += 1
+        self.offspring += self.n_runs
+
+    def _reduce(self, run: Run):
+        """Section 3.4: remove the member of lowest chi until mu remain."""
+        edges = [solution_edges(s, self.open) for s in run.pop]
+        while len(run.pop) > self.mu:
+            chi = chi_scores(np.asarray(run.f), edges, self.xi)
+            worst = int(np.lexsort((np.arange(len(chi)), chi))[0])
+            del run.pop[worst]
+            del run.f[worst]
+            del edges[worst]

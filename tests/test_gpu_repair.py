@@ -112,3 +112,17 @@ def test_repair_reports_full_routes_and_bad_lists(md):
         with pytest.raises(md.MdError) as e:
             S.repair(keep, un, md.INSERT_FBI)
         assert e.value.status == md.MD_ERR_ARG
+
+
+def test_repair_rules_differ_per_solution_in_one_launch(md, oracle_lib):
+    spec = W.mdvrptw_6x288(251)
+    parts = _partials(spec, "initial", 8, 252)
+    rules = [0, 1, 2, 3, 3, 2, 1, 0]
+    inst = md.Instance(spec)
+    S = md.Solutions(inst, 8, spec.n_customers + 1, spec.n_customers)
+    order = S.repair([p[0] for p in parts], [p[1] for p in parts], rules)
+    got = S.read()
+    o = oracle_lib.Instance(spec)
+    for s in range(8):
+        want, worder = o.repair(parts[s][0], parts[s][1], rules[s])
+        assert got[s] == want and order[s] == worder, s
