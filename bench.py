@@ -783,6 +783,7 @@ def run_memetic(args):
         mm.generation()
     torch.cuda.synchronize()
     ms = []
+    mm.t_backend = mm.t_total = 0.0
     with ClockSampler(0) as clk:
         for _ in range(args.steps):
             t = time.perf_counter()
@@ -816,6 +817,8 @@ def run_memetic(args):
                                f"delta={MAX_PASS}, adaptive lambda; a step is one generation of every run",
                    "timed": "host DCREX and population update, GPU repair and descent, host readback"},
         "init_s": init_s, "generations": mm.gen, "best_f_mean": float(np.mean(best)),
+        "ms_per_step_gpu_calls": 1e3 * mm.t_backend / max(args.steps, 1),
+        "ms_per_step_host": 1e3 * (mm.t_total - mm.t_backend) / max(args.steps, 1),
         "cpu_baseline": cpu,
         "clocks": clk.summary(),
     }))

@@ -13,10 +13,11 @@ per run and stays on the CPU.
 
 Readings where the paper is silent:
 - DCREX scores route pairs (R_i, R_j) with R_i a route of the main parent still in the
-  offspring and R_j a route of the current other parent:
+  offspring and R_j a route of the current other parent (as products of customer incidence
+  matrices):
   - E^I counts the distinct edges of R_j that the offspring does not have;
   - N^R counts the customers of R_i that R_j does not visit;
-  - N^M counts the customers of R_j that the offspring visits outside R_i;
+  - N^M counts the customers of R_j that the offspring visits in a route other than R_i;
   - N^C counts the customers of R_j that routes introduced earlier in this crossover visit.
 - The random pick among the five lowest scores is uniform, with ties ordered by (R_i, R_j).
 - R_j takes R_i's place in the offspring.
@@ -31,10 +32,13 @@ Readings where the paper is silent:
 - When the population reaches 1.5 mu it is cut back to mu by removing the solution of lowest
   chi, recomputing chi after each removal.
 - Unplayed bandit arms are tried first, in index order.
+- A solution is kept with its routes in sorted order (as node lists), so that the route
+  indices by which DCREX and the repair break ties do not depend on where a backend keeps them.
 """
 from __future__ import annotations
 
 import math
+import time
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -88,14 +92,30 @@ def solution_distance(e1: set, e2: set) -> float:
     return 0.0 if m == 0 else 100.0 * (1.0 - len(e1 & e2) / m)
 
 
-def chi_scores(f: np.ndarray, edges: list, xi: float) -> np.ndarray:
-    """chi of Eq. (7) for every member: rank 1 is the lowest f, and the largest mean distance to
-    the five nearest other members (Eq. 8); ties by index."""
+def distance_matrix(edges: list) -> np.ndarray:
+    """D_S of Eq. (9) between every pair of members, from a member x edge incidence matrix."""
+    n = len(edges)
+    cols = {}
+    for es in edges:
+        for e in es:
+            cols.setdefault(e, len(cols))
+    A = np.zeros((n, max(len(cols), 1)), np.float64)
+    for a, es in enumerate(edges):
+        A[a, [cols[e] for e in es]] = 1.0
+    inter = A @ A.T
+    size = A.sum(1)
+    m = np.maximum(size[:, None], size[None, :])
+    with np.errstate(invalid="ignore", divide="ignore"):
+        d = np.where(m > 0, 100.0 * (1.0 - inter / np.where(m > 0, m, 1.0)), 0.0)
+    np.fill_diagonal(d, 0.0)
+    return d
+
+
+def chi_scores(f: np.ndarray, d: np.ndarray, xi: float) -> np.ndarray:
+    """chi of Eq. (7) for every member, from the members' distance matrix d: rank 1 is the
+    lowest f, and the largest mean distance to the five nearest other members (Eq. 8); ties by
+    index."""
     n = len(f)
-    d = np.zeros((n, n))
-    for a in range(n):
-        for b in range(a + 1, n):
-            d[a, b] = d[b, a] = solution_distance(edges[a], edges[b])
     dp = np.zeros(n)
     for a in range(n):
         others = np.sort(np.delete(d[a], a))
@@ -119,6 +139,39 @@ def unit_f(comps: np.ndarray, Theta: int, Gamma: float, Q: int, D: int) -> float
     return f
 
 
+def _flat_nodes(routes):
+    """Every node of every route with its route index and its position in the route."""
+    lens = np.fromiter((len(r) for r in routes), np.int64, len(routes))
+    nodes = np.concatenate([np.asarray(r, np.int64) for r in routes]) if routes else np.zeros(0, np.int64)
+    rid = np.repeat(np.arange(len(routes)), lens)
+    pos = np.arange(len(nodes)) - np.repeat(np.cumsum(lens) - lens, lens)
+    return nodes, rid, pos, lens
+
+
+def _flat_customers(flat):
+    """(route index, customer) of every visit, from _flat_nodes."""
+    nodes, rid, pos, lens = flat
+    m = (pos > 0) & (pos < lens[rid] - 1)
+    return rid[m], nodes[m]
+
+
+def _edge_keys(flat, open_routes: bool, nn: int):
+    """(route index, undirected edge key min * nn + max) of every distinct edge of each route;
+    open routes have no edge into their arrival depot.  A route's edges are distinct except the
+    two of a closed one-customer route [d, c, d], whose second copy is dropped.  flat: from
+    _flat_nodes."""
+    nodes, rid, pos, lens = flat
+    a, b = nodes[:-1], nodes[1:]
+    m = rid[:-1] == rid[1:]
+    if open_routes:
+        m &= pos[1:] != lens[rid[1:]] - 1
+    else:
+        m &= ~((lens[rid[1:]] == 3) & (pos[1:] == 2) & (nodes[:-1] != nodes[1:]) &
+               (np.roll(nodes, 1)[:-1] == nodes[1:]))
+    key = np.minimum(a, b) * nn + np.maximum(a, b)
+    return rid[:-1][m], key[m]
+
+
 def dcrex(main, others, degree: int, st: W.Stream, n_depots: int, n_customers: int, open_routes: bool):
     """Route exchange of Alg. 3 (its route-pair loop and the removal of redundant customers).
     Returns (partial routes, unrouted customers in increasing order)."""
@@ -130,25 +183,54 @@ def dcrex(main, others, degree: int, st: W.Stream, n_depots: int, n_customers: i
     cur = 0
     intro_cust = set()
     n_intro = 0
+    nn = n_depots + n_customers
     for P in others:
-        have = solution_edges(S, open_routes)
-        where = {c: i for i, r in enumerate(S) for c in r[1:-1]}
-        cand = []
-        for i, Ri in enumerate(S):
-            if intro[i] >= 0:
-                continue
-            Ci = set(Ri[1:-1])
-            for j, Rj in enumerate(P):
-                Cj = Rj[1:-1]
-                ei = sum(1 for e in route_edges(Rj, open_routes) if e not in have)
-                nr = len(Ci - set(Cj))
-                nm = sum(1 for c in Cj if c in where and where[c] != i)
-                nc = sum(1 for c in Cj if c in intro_cust)
-                cand.append((-(ei - nr - nm - 10 * nc), i, j, ei + nr + nm))
-        if not cand:
+        orig = [i for i in range(len(S)) if intro[i] < 0]
+        if not orig or not P:
             break
-        cand.sort()
-        k = int(st.randint(0, min(5, len(cand)) - 1, 1)[0])
+        fS, fP = _flat_nodes(S), _flat_nodes(P)
+        is_orig = np.zeros(len(S), bool)
+        is_orig[orig] = True
+        row_of = np.cumsum(is_orig) - 1  # row of an original route in Am
+        # customer incidence of the offspring's original routes (Am) and the parent's routes (Ap),
+        # in FP64 so that the products go through BLAS (the counts are small, exact integers)
+        Am = np.zeros((len(orig), nn))
+        rs, cs = _flat_customers(fS)
+        keep = is_orig[rs]
+        Am[row_of[rs[keep]], cs[keep]] = 1
+        Ap = np.zeros((len(P), nn))
+        rj, cj = _flat_customers(fP)
+        Ap[rj, cj] = 1
+        visits = np.bincount(cs, minlength=nn)
+        v1 = (visits == 1).astype(np.float64)
+        v2 = (visits >= 2).astype(np.float64)
+        iv = np.zeros(nn)
+        iv[list(intro_cust)] = 1
+        inter = Am @ Ap.T                                     # |C_i & C_j|
+        # distinct edges of each R_j that the offspring does not have
+        er, ek = _edge_keys(fP, open_routes, nn)
+        _, have = _edge_keys(fS, open_routes, nn)
+        if nn * nn <= (1 << 22):  # a lookup table over edge keys, else a sorted search
+            tab = np.zeros(nn * nn, bool)
+            tab[have] = True
+            new_e = ~tab[ek]
+        else:
+            new_e = ~np.isin(ek, have)
+        ei = np.bincount(er, weights=new_e, minlength=len(P)).astype(np.int64)
+        nr = Am.sum(1)[:, None] - inter                       # C_i not visited by R_j
+        # customers of R_j visited by the offspring outside R_i: visited twice or more, or once
+        # and not by R_i
+        nm = (Ap @ v2)[None, :] + (Ap @ v1)[None, :] - (Am * v1[None, :]) @ Ap.T
+        nc = (Ap @ iv)[None, :]
+        nr, nm, nc = (np.rint(x).astype(np.int64) for x in (nr, nm, nc))
+        score = -(ei[None, :] - nr - nm - 10 * nc)
+        dsig_all = ei[None, :] + nr + nm
+        ii = np.repeat(np.asarray(orig), len(P))
+        jj = np.tile(np.arange(len(P)), len(orig))
+        order = np.lexsort((jj, ii, score.reshape(-1)))
+        cand = [(int(score.reshape(-1)[q]), int(ii[q]), int(jj[q]), int(dsig_all.reshape(-1)[q]))
+                for q in order[:5]]
+        k = int(st.randint(0, len(cand) - 1, 1)[0])
         _, i, j, dsig = cand[k]
         S[i] = list(P[j])
         intro[i] = n_intro
@@ -232,6 +314,8 @@ class MDFIHA:
         self.runs = [Run() for _ in range(n_runs)]
         self.streams = [W.Stream(seed, 40, r) for r in range(n_runs)]
         self.offspring = 0
+        self.t_backend = 0.0  # seconds in the backend's repairs and descents (generations only)
+        self.t_total = 0.0    # seconds in generation()
 
     def _f(self, comps) -> float:
         return unit_f(comps, self.backend.Theta, self.backend.Gamma, self.spec.Q, self.spec.D)
@@ -249,6 +333,7 @@ class MDFIHA:
         self.gen = 0
         got, comps = self.backend.repair_descend(sols, [[] for _ in sols], [0] * len(sols),
                                                  self._perms(len(sols)), self.delta)
+        got = [sorted(x) for x in got]
         for r, run in enumerate(self.runs):
             for k in range(self.mu):
                 i = r * self.mu + k
@@ -259,6 +344,7 @@ class MDFIHA:
 
     def generation(self):
         """One generation of Alg. 1 in every run: DCREX, repair, MDFIS, population update."""
+        t0 = time.perf_counter()
         self.gen += 1
         partials, unrouted, rules, mains, degs = [], [], [], [], []
         for r, run in enumerate(self.runs):
@@ -275,7 +361,11 @@ class MDFIHA:
             rules.append(rule)
             mains.append(m)
             degs.append(d)
-        got, comps = self.backend.repair_descend(partials, unrouted, rules, self._perms(self.n_runs), self.delta)
+        perms = self._perms(self.n_runs)
+        t1 = time.perf_counter()
+        got, comps = self.backend.repair_descend(partials, unrouted, rules, perms, self.delta)
+        self.t_backend += time.perf_counter() - t1
+        got = [sorted(x) for x in got]
         for r, run in enumerate(self.runs):
             f = self._f(comps[r])
             fm = run.f[mains[r]]
@@ -291,13 +381,14 @@ class MDFIHA:
             else:
                 run.stagnation += 1
         self.offspring += self.n_runs
+        self.t_total += time.perf_counter() - t0
 
     def _reduce(self, run: Run):
         """Section 3.4: remove the member of lowest chi until mu remain."""
-        edges = [solution_edges(s, self.open) for s in run.pop]
+        d = distance_matrix([solution_edges(s, self.open) for s in run.pop])
         while len(run.pop) > self.mu:
-            chi = chi_scores(np.asarray(run.f), edges, self.xi)
+            chi = chi_scores(np.asarray(run.f), d, self.xi)
             worst = int(np.lexsort((np.arange(len(chi)), chi))[0])
             del run.pop[worst]
             del run.f[worst]
-            del edges[worst]
+            d = np.delete(np.delete(d, worst, 0), worst, 1)

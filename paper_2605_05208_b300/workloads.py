@@ -415,15 +415,17 @@ def op_permutations(seed: int, n_solutions: int, max_pass: int, op_list=tuple(ra
     op_list driven by the stream (seed, 20, solution).  Returns uint8 [n_sol, max_pass, len]."""
     k = len(op_list)
     out = np.zeros((n_solutions, max_pass, k), dtype=np.uint8)
+    rows = np.arange(max_pass)
     for s in range(n_solutions):
         st = Stream(seed, 20, s)
         draws = st.u64(max_pass * k).reshape(max_pass, k) >> np.uint64(32)
-        for p in range(max_pass):
-            a = list(op_list)
-            for i in range(k - 1, 0, -1):
-                j = int((int(draws[p, i]) * (i + 1)) >> 32)
-                a[i], a[j] = a[j], a[i]
-            out[s, p] = a
+        a = np.tile(np.asarray(op_list, dtype=np.uint8), (max_pass, 1))
+        for i in range(k - 1, 0, -1):  # the same shuffle for every pass at once
+            j = ((draws[:, i] * np.uint64(i + 1)) >> np.uint64(32)).astype(np.int64)
+            ai = a[:, i].copy()
+            a[:, i] = a[rows, j]
+            a[rows, j] = ai
+        out[s] = a
     return out
 
 

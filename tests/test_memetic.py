@@ -65,7 +65,9 @@ def test_solution_distance_and_chi_hand_example():
     # open routes drop the return edge: a's edges become {0,2} {2,3} {1,4} {4,5}
     assert MM.solution_edges(a, True) == {(0, 2), (2, 3), (1, 4), (4, 5)}
     f = np.array([10.0, 12.0, 11.0])
-    chi = MM.chi_scores(f, E, 0.7)
+    d = MM.distance_matrix(E)
+    assert np.allclose(d, [[0, 0, 100 * (1 - 2 / 6)], [0, 0, 100 * (1 - 2 / 6)], [100 * (1 - 2 / 6)] * 2 + [0]])
+    chi = MM.chi_scores(f, d, 0.7)
     # ranks by f: a 1, c 2, b 3; mean distance to the others: a 33.3, b 33.3, c 66.7
     # -> distance ranks c 1, a 2 (tie with b, lower index), b 3
     want = [(3 - 1) / 3 + 0.7 * (3 - 2) / 3, (3 - 3) / 3 + 0.7 * (3 - 3) / 3, (3 - 2) / 3 + 0.7 * (3 - 1) / 3]
@@ -91,6 +93,59 @@ def test_dcrex_exchanges_routes_and_lists_the_unrouted():
     part0, _ = MM.dcrex(main, others, 0, W.Stream(9, 0), spec.n_depots, spec.n_customers, False)
     assert sum(1 for r in part0 if r in others[0]) >= 1
     assert len(part0) <= len(main)
+
+
+def _dcrex_by_pairs(main, others, degree, st, nd, nc, open_):
+    """Alg. 3's route-pair loop with every score counted pair by pair from its definition."""
+    S = [list(r) for r in main]
+    intro = [-1] * len(S)
+    smin, smax = degree / 20 * (nc + len(main)), (degree + 1) / 20 * (nc + len(main))
+    cur, n_intro, intro_cust = 0, 0, set()
+    for P in others:
+        have = MM.solution_edges(S, open_)
+        cand = []
+        for i, Ri in enumerate(S):
+            if intro[i] >= 0:
+                continue
+            for j, Rj in enumerate(P):
+                ei = len([e for e in MM.route_edges(Rj, open_) if e not in have])
+                nr = len([c for c in Ri[1:-1] if c not in Rj[1:-1]])
+                nm = len([c for c in Rj[1:-1] if any(c in S[x][1:-1] for x in range(len(S)) if x != i)])
+                ncf = len([c for c in Rj[1:-1] if c in intro_cust])
+                cand.append((-(ei - nr - nm - 10 * ncf), i, j, ei + nr + nm))
+        if not cand:
+            break
+        cand.sort()
+        _, i, j, dsig = cand[int(st.randint(0, min(5, len(cand)) - 1, 1)[0])]
+        S[i], intro[i] = list(P[j]), n_intro
+        n_intro += 1
+        intro_cust |= set(P[j][1:-1])
+        cur += dsig
+        if cur >= smax:
+            continue
+        if cur >= smin:
+            break
+    keep = {}
+    for i in sorted((i for i in range(len(S)) if intro[i] >= 0), key=lambda i: intro[i]):
+        for c in S[i][1:-1]:
+            keep.setdefault(c, i)
+    out = [[r[0]] + [c for c in r[1:-1] if keep.get(c, i) == i] + [r[-1]] for i, r in enumerate(S)]
+    out = [r for r in out if len(r) > 2]
+    routed = {c for r in out for c in r[1:-1]}
+    return out, [c for c in range(nd, nd + nc) if c not in routed]
+
+
+@pytest.mark.parametrize("open_", [False, True])
+def test_dcrex_scores_match_pair_by_pair_counts(open_):
+    spec = tiny_spec(75, nd=3, nc=36, Q=40, NV=4, open_=open_, sym=open_)
+    for trial in range(6):
+        main = random_solution(spec, 80 + trial, max_len=7)
+        others = [random_solution(spec, 90 + 7 * trial + k, max_len=7) for k in range(5)]
+        for degree in (0, 3, 9, 19):
+            got = MM.dcrex(main, others, degree, W.Stream(11, trial, degree), spec.n_depots, spec.n_customers, open_)
+            want = _dcrex_by_pairs(main, others, degree, W.Stream(11, trial, degree), spec.n_depots,
+                                   spec.n_customers, open_)
+            assert got == want, (trial, degree)
 
 
 def test_memetic_loop_on_the_oracle(oracle_lib):
