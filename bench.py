@@ -792,6 +792,7 @@ def run_memetic(args):
             ms.append(1e3 * (time.perf_counter() - t))
     total_ms = sum(ms)
     value = MEMETIC_RUNS * args.steps / (total_ms / 1e3)
+    mm.close()
     cpu = None
     if not args.no_cpu_baseline:
         from paper_2605_05208_b300 import memetic as MM2

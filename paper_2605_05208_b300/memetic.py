@@ -255,6 +255,17 @@ def dcrex(main, others, degree: int, st: W.Stream, n_depots: int, n_customers: i
     return out, [c for c in range(n_depots, n_depots + n_customers) if c not in routed]
 
 
+def _dcrex_task(args):
+    """One run's parent choice and crossover (a process-pool task): returns the partial
+    solution, its unrouted customers, the main parent's index and the advanced stream."""
+    pop, st, degree, nd, nc, open_routes = args
+    n = len(pop)
+    m = int(st.randint(0, n - 1, 1)[0])
+    order = [i for i in np.argsort(st.u64(n)).tolist() if i != m]
+    part, un = dcrex(pop[m], [pop[i] for i in order], degree, st, nd, nc, open_routes)
+    return part, un, m, st
+
+
 class GpuBackend:
     """Repairs and descends a batch of offspring through the C ABI (md_repair_insert,
     md_descend with adaptive lambda)."""
@@ -300,7 +311,7 @@ class MDFIHA:
     (GpuBackend by default) and the instance's Theta and Gamma."""
 
     def __init__(self, spec, n_runs: int, mu: int = 20, xi: float = 0.7, delta: int = 500, seed: int = 1,
-                 backend=None, n_ops: int = W.N_OPS):
+                 backend=None, n_ops: int = W.N_OPS, host_workers: int = 0):
         self.spec = spec
         self.n_runs = n_runs
         self.mu = mu
@@ -316,6 +327,18 @@ class MDFIHA:
         self.offspring = 0
         self.t_backend = 0.0  # seconds in the backend's repairs and descents (generations only)
         self.t_total = 0.0    # seconds in generation()
+        # the runs' crossovers on a pool of spawned processes (0: in this process); spawned, so
+        # that no worker is forked from a process that has initialised CUDA.  With populations of
+        # 20 on the 6 x 288 instance, sending them to the workers costs more than it saves.
+        self.pool = None
+        if host_workers > 0:
+            import multiprocessing as mp
+            self.pool = mp.get_context("spawn").Pool(host_workers)
+
+    def close(self):
+        if self.pool is not None:
+            self.pool.close()
+            self.pool = None
 
     def _f(self, comps) -> float:
         return unit_f(comps, self.backend.Theta, self.backend.Gamma, self.spec.Q, self.spec.D)
@@ -346,21 +369,15 @@ class MDFIHA:
         """One generation of Alg. 1 in every run: DCREX, repair, MDFIS, population update."""
         t0 = time.perf_counter()
         self.gen += 1
-        partials, unrouted, rules, mains, degs = [], [], [], [], []
-        for r, run in enumerate(self.runs):
-            st = self.streams[r]
-            n = len(run.pop)
-            m = int(st.randint(0, n - 1, 1)[0])
-            order = [i for i in np.argsort(st.u64(n)).tolist() if i != m]
-            d = run.deg.select()
-            rule = run.rule.select()
-            part, un = dcrex(run.pop[m], [run.pop[i] for i in order], d, st, self.spec.n_depots,
-                             self.spec.n_customers, self.open)
-            partials.append(part)
-            unrouted.append(un)
-            rules.append(rule)
-            mains.append(m)
-            degs.append(d)
+        degs = [run.deg.select() for run in self.runs]
+        rules = [run.rule.select() for run in self.runs]
+        tasks = [(run.pop, self.streams[r], degs[r], self.spec.n_depots, self.spec.n_customers, self.open)
+                 for r, run in enumerate(self.runs)]
+        res = self.pool.map(_dcrex_task, tasks) if self.pool is not None else [_dcrex_task(t) for t in tasks]
+        partials = [x[0] for x in res]
+        unrouted = [x[1] for x in res]
+        mains = [x[2] for x in res]
+        self.streams = [x[3] for x in res]
         perms = self._perms(self.n_runs)
         t1 = time.perf_counter()
         got, comps = self.backend.repair_descend(partials, unrouted, rules, perms, self.delta)

@@ -163,6 +163,20 @@ def test_memetic_loop_on_the_oracle(oracle_lib):
         assert run.deg.N.sum() > 0 and run.rule.N.sum() > 0
 
 
+def test_memetic_crossovers_on_a_process_pool_change_nothing(oracle_lib):
+    spec = W.mdvrp_4x50(85)
+    out = []
+    for workers in (0, 2):
+        mm = MM.MDFIHA(spec, n_runs=3, mu=4, delta=20, seed=4, backend=OracleBackend(oracle_lib, spec),
+                       host_workers=workers)
+        mm.initialize()
+        for _ in range(4):
+            mm.generation()
+        mm.close()
+        out.append([(r.pop, r.f, r.deg.R.tolist(), r.rule.N.tolist()) for r in mm.runs])
+    assert out[0] == out[1]
+
+
 @pytest.mark.gpu
 def test_memetic_loop_gpu_matches_oracle_loop(oracle_lib):
     # the same runs, random draws and decisions: the GPU backend's repairs and descents must
