@@ -775,7 +775,7 @@ def run_memetic(args):
     torch.cuda.set_stream(stream)
     spec, _, _ = workload_spec(0)
     mm = MM.MDFIHA(spec, n_runs=MEMETIC_RUNS, mu=MEMETIC_MU, delta=MAX_PASS, seed=SEED,
-                   backend=MM.GpuBackend(spec, stream=stream.cuda_stream))
+                   backend=MM.GpuBackend(spec, stream=stream.cuda_stream, multi=not args.single_move))
     t0 = time.perf_counter()
     mm.initialize()
     init_s = time.perf_counter() - t0
@@ -815,7 +815,9 @@ def run_memetic(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "int32/f64", "data": "synthetic",
         "config": {"workload": f"memetic-mdvrptw-6x288: MDFIHA on the mdvrptw-6x288 bench instance, "
                                f"{MEMETIC_RUNS} independent runs in lockstep, population {MEMETIC_MU}, "
-                               f"delta={MAX_PASS}, adaptive lambda; a step is one generation of every run",
+                               f"delta={MAX_PASS}, adaptive lambda, "
+                               f"{'single-move' if args.single_move else 'multi-move'} MDFIS; "
+                               f"a step is one generation of every run",
                    "timed": "host DCREX and population update, GPU repair and descent, host readback"},
         "init_s": init_s, "generations": mm.gen, "best_f_mean": float(np.mean(best)),
         "ms_per_step_gpu_calls": 1e3 * mm.t_backend / max(args.steps, 1),
@@ -919,6 +921,8 @@ def main():
                     help="1: each descent in one persistent launch (device-side task queue); 0: a CUDA "
                          "graph per pass with concurrent solution groups; -1 (default): 1 for "
                          "mdvrptw-6x288, 0 for the 20x10000 workloads")
+    ap.add_argument("--single-move", action="store_true",
+                    help="memetic-mdvrptw-6x288: MDFIS applies the leader only (no followers)")
     ap.add_argument("--groups", type=int, default=4,
                     help="solution groups advancing on concurrent streams inside the graph")
     args = ap.parse_args()

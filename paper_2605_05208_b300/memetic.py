@@ -270,7 +270,7 @@ class GpuBackend:
     """Repairs and descends a batch of offspring through the C ABI (md_repair_insert,
     md_descend with adaptive lambda)."""
 
-    def __init__(self, spec, stream=None, persistent: bool = True):
+    def __init__(self, spec, stream=None, persistent: bool = True, multi: bool = True):
         from . import mdls
         self.mdls = mdls
         self.spec = spec
@@ -278,6 +278,7 @@ class GpuBackend:
         self.Theta, self.Gamma = self.inst.params()
         self.stream = stream
         self.persistent = persistent
+        self.multi = multi  # leader-follower multi-move steps (Section 3.2.5), else the leader only
         self._sols = {}
 
     def _solutions(self, n):
@@ -289,7 +290,7 @@ class GpuBackend:
     def repair_descend(self, partials, unrouted, rules, perms, max_pass):
         S = self._solutions(len(partials))
         S.repair(partials, unrouted, np.asarray(rules, np.int32), stream=self.stream)
-        S.descend(perms, max_pass, multi=True, lambda_update=True, use_graph=not self.persistent,
+        S.descend(perms, max_pass, multi=self.multi, lambda_update=True, use_graph=not self.persistent,
                   persistent=self.persistent, stream=self.stream)
         comps, _ = S.cost(stream=self.stream)
         return S.read(stream=self.stream), comps
