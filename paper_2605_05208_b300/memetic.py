@@ -172,9 +172,22 @@ def _edge_keys(flat, open_routes: bool, nn: int):
     return rid[:-1][m], key[m]
 
 
-def dcrex(main, others, degree: int, st: W.Stream, n_depots: int, n_customers: int, open_routes: bool):
+def parent_arrays(sol, nn: int, open_routes: bool):
+    """What DCREX needs of a parent, computed once per population member: its routes' customer
+    incidence (FP64 rows) and the (route, edge key) pairs of its distinct edges."""
+    f = _flat_nodes(sol)
+    rj, cj = _flat_customers(f)
+    Ap = np.zeros((len(sol), nn))
+    Ap[rj, cj] = 1
+    er, ek = _edge_keys(f, open_routes, nn)
+    return Ap, er, ek
+
+
+def dcrex(main, others, degree: int, st: W.Stream, n_depots: int, n_customers: int, open_routes: bool,
+          others_pre=None):
     """Route exchange of Alg. 3 (its route-pair loop and the removal of redundant customers).
-    Returns (partial routes, unrouted customers in increasing order)."""
+    others_pre: parent_arrays of each other parent, if the caller keeps them.  Returns (partial
+    routes, unrouted customers in increasing order)."""
     S = [list(r) for r in main]
     intro = [-1] * len(S)  # introduction order of each route (-1: the main parent's)
     m = len(main)
@@ -184,11 +197,12 @@ def dcrex(main, others, degree: int, st: W.Stream, n_depots: int, n_customers: i
     intro_cust = set()
     n_intro = 0
     nn = n_depots + n_customers
-    for P in others:
+    for pi, P in enumerate(others):
         orig = [i for i in range(len(S)) if intro[i] < 0]
         if not orig or not P:
             break
-        fS, fP = _flat_nodes(S), _flat_nodes(P)
+        fS = _flat_nodes(S)
+        Ap, er, ek = others_pre[pi] if others_pre is not None else parent_arrays(P, nn, open_routes)
         is_orig = np.zeros(len(S), bool)
         is_orig[orig] = True
         row_of = np.cumsum(is_orig) - 1  # row of an original route in Am
@@ -198,9 +212,6 @@ def dcrex(main, others, degree: int, st: W.Stream, n_depots: int, n_customers: i
         rs, cs = _flat_customers(fS)
         keep = is_orig[rs]
         Am[row_of[rs[keep]], cs[keep]] = 1
-        Ap = np.zeros((len(P), nn))
-        rj, cj = _flat_customers(fP)
-        Ap[rj, cj] = 1
         visits = np.bincount(cs, minlength=nn)
         v1 = (visits == 1).astype(np.float64)
         v2 = (visits >= 2).astype(np.float64)
@@ -208,7 +219,6 @@ def dcrex(main, others, degree: int, st: W.Stream, n_depots: int, n_customers: i
         iv[list(intro_cust)] = 1
         inter = Am @ Ap.T                                     # |C_i & C_j|
         # distinct edges of each R_j that the offspring does not have
-        er, ek = _edge_keys(fP, open_routes, nn)
         _, have = _edge_keys(fS, open_routes, nn)
         if nn * nn <= (1 << 22):  # a lookup table over edge keys, else a sorted search
             tab = np.zeros(nn * nn, bool)
@@ -258,11 +268,12 @@ def dcrex(main, others, degree: int, st: W.Stream, n_depots: int, n_customers: i
 def _dcrex_task(args):
     """One run's parent choice and crossover (a process-pool task): returns the partial
     solution, its unrouted customers, the main parent's index and the advanced stream."""
-    pop, st, degree, nd, nc, open_routes = args
+    pop, pre, st, degree, nd, nc, open_routes = args
     n = len(pop)
     m = int(st.randint(0, n - 1, 1)[0])
     order = [i for i in np.argsort(st.u64(n)).tolist() if i != m]
-    part, un = dcrex(pop[m], [pop[i] for i in order], degree, st, nd, nc, open_routes)
+    part, un = dcrex(pop[m], [pop[i] for i in order], degree, st, nd, nc, open_routes,
+                     [pre[i] for i in order] if pre is not None else None)
     return part, un, m, st
 
 
@@ -299,6 +310,7 @@ class GpuBackend:
 @dataclass
 class Run:
     pop: list = field(default_factory=list)    # routes of each member
+    pre: list = field(default_factory=list)    # parent_arrays of each member
     f: list = field(default_factory=list)      # unit-lambda F of each member
     best: float = math.inf
     best_sol: list | None = None
@@ -362,6 +374,7 @@ class MDFIHA:
             for k in range(self.mu):
                 i = r * self.mu + k
                 run.pop.append(got[i])
+                run.pre.append(parent_arrays(got[i], self.spec.n_nodes, self.open))
                 run.f.append(self._f(comps[i]))
             b = int(np.argmin(run.f))
             run.best, run.best_sol = run.f[b], run.pop[b]
@@ -372,8 +385,9 @@ class MDFIHA:
         self.gen += 1
         degs = [run.deg.select() for run in self.runs]
         rules = [run.rule.select() for run in self.runs]
-        tasks = [(run.pop, self.streams[r], degs[r], self.spec.n_depots, self.spec.n_customers, self.open)
-                 for r, run in enumerate(self.runs)]
+        # the workers rebuild the parents' arrays rather than receive them
+        tasks = [(run.pop, None if self.pool is not None else run.pre, self.streams[r], degs[r],
+                  self.spec.n_depots, self.spec.n_customers, self.open) for r, run in enumerate(self.runs)]
         res = self.pool.map(_dcrex_task, tasks) if self.pool is not None else [_dcrex_task(t) for t in tasks]
         partials = [x[0] for x in res]
         unrouted = [x[1] for x in res]
@@ -391,6 +405,7 @@ class MDFIHA:
             run.deg.update(degs[r], reward)
             run.rule.update(rules[r], reward)
             run.pop.append(got[r])
+            run.pre.append(parent_arrays(got[r], self.spec.n_nodes, self.open))
             run.f.append(f)
             if len(run.pop) >= math.ceil(1.5 * self.mu):
                 self._reduce(run)
@@ -408,5 +423,6 @@ class MDFIHA:
             chi = chi_scores(np.asarray(run.f), d, self.xi)
             worst = int(np.lexsort((np.arange(len(chi)), chi))[0])
             del run.pop[worst]
+            del run.pre[worst]
             del run.f[worst]
             d = np.delete(np.delete(d, worst, 0), worst, 1)
