@@ -175,9 +175,11 @@ extern "C" md_status md_batch_set_tuning(md_batch *b, const int32_t *upw, const 
 
 namespace {
 
+// The tuner's timing launches cycle the solutions through the operators 0..4 (Relocate, Swap,
+// 2-opt*, Depot-Insert, Depot-Replace): the intra-route 2-opt scores nothing on most instances.
 __global__ void k_tune_ops(DevSols D) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s < D.S) D.ops[s] = s % MD_N_OPS;
+    if (s < D.S) D.ops[s] = s % (MD_OP_DEPOT_REPLACE + 1);
 }
 
 // Median device time of `reps` evaluation launches over the given items.

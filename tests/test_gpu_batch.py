@@ -147,3 +147,24 @@ def test_batch_tune_sets_solo_flags(case):
     for (_, S), sp, (want_routes, want_stats) in zip(loaded, specs, ref):
         assert [W.canonical(r, bool(sp.variant & W.VAR_OPEN)) for r in S.read()] == want_routes
         assert np.array_equal(S.stats(), want_stats)
+
+
+def test_batch_descent_with_two_opt_matches_oracle(case, oracle_lib):
+    # the six-operator set through the batched launches (MDVRP and MDOVRP items: symmetric, so
+    # 2-opt has moves; the MDVRPTW items score none of it) against the oracle
+    import torch
+    md, specs, sols, _ = case
+    perms = [W.op_permutations(97 + i, sp.n_solutions, MAX_PASS, op_list=tuple(range(W.N_OPS_ALL)))
+             for i, sp in enumerate(specs)]
+    loaded = [_load(md, sp, so) for sp, so in zip(specs, sols)]
+    B = md.Batch([S for _, S in loaded])
+    st = B.descend(np.concatenate(perms), MAX_PASS, use_graph=True, stream=torch.cuda.Stream().cuda_stream)
+    assert st.moves_by_op[W.OP_TWO_OPT] > 0
+    for (_, S), sp, so, pe in zip(loaded, specs, sols, perms):
+        o = oracle_lib.Instance(sp)
+        got, per = S.read(), S.stats()
+        op = bool(sp.variant & W.VAR_OPEN)
+        for s in range(len(so)):
+            d = o.descend(so[s], pe[s], MAX_PASS, multi=True)
+            assert W.canonical(got[s], op) == W.canonical(d.solution, op), (sp.name, s)
+            assert list(per[s]) == [d.moves_scored, d.steps, d.accepted_steps, d.applied_moves, d.passes]
