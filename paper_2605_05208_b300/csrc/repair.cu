@@ -313,37 +313,43 @@ extern "C" md_status md_repair_insert(md_solutions *S, const int32_t *rules, con
     if (r != MD_OK) return r;
     const long long nu = unrouted_off[S->n_sol];
     if (nu > 0) {
-        int32_t *du = nullptr;
-        int64_t *doff = nullptr;
-        InsBest *dres = nullptr;
-        int32_t *dord = nullptr;
-        MD_CUDA(cudaMallocAsync(&du, sizeof(int32_t) * nu, st));
-        MD_CUDA(cudaMallocAsync(&dord, sizeof(int32_t) * nu, st));
-        MD_CUDA(cudaMallocAsync(&dres, sizeof(InsBest) * nu, st));
-        MD_CUDA(cudaMallocAsync(&doff, sizeof(int64_t) * (S->n_sol + 1), st));
         // per solution, rows of min(R, routes + listed customers) route slots per listed customer
-        std::vector<int64_t> rboff(S->n_sol + 1, 0);
-        for (int s = 0; s < S->n_sol; s++) {
-            const long long n = unrouted_off[s + 1] - unrouted_off[s];
-            rboff[s + 1] = rboff[s] + n * std::min<long long>(S->R, per_sol[s] + n);
+        const int n = S->n_sol;
+        std::vector<int64_t> rboff(n + 1, 0);
+        for (int s = 0; s < n; s++) {
+            const long long m = unrouted_off[s + 1] - unrouted_off[s];
+            rboff[s + 1] = rboff[s] + m * std::min<long long>(S->R, per_sol[s] + m);
         }
-        int2 *drb = nullptr;
-        int64_t *drboff = nullptr;
-        MD_CUDA(cudaMallocAsync(&drb, sizeof(int2) * std::max<int64_t>(rboff[S->n_sol], 1), st));
-        MD_CUDA(cudaMallocAsync(&drboff, sizeof(int64_t) * (S->n_sol + 1), st));
-        int32_t *drules = nullptr;
-        MD_CUDA(cudaMallocAsync(&drules, sizeof(int32_t) * S->n_sol, st));
-        MD_CUDA(cudaMemcpyAsync(drules, rules, sizeof(int32_t) * S->n_sol, cudaMemcpyHostToDevice, st));
-        MD_CUDA(cudaMemcpyAsync(drboff, rboff.data(), sizeof(int64_t) * (S->n_sol + 1), cudaMemcpyHostToDevice, st));
-        MD_CUDA(cudaMemcpyAsync(du, unrouted, sizeof(int32_t) * nu, cudaMemcpyHostToDevice, st));
-        MD_CUDA(cudaMemcpyAsync(doff, unrouted_off, sizeof(int64_t) * (S->n_sol + 1), cudaMemcpyHostToDevice, st));
+        // one device block: the inputs (list offsets, cache offsets, lists, rules; copied in one
+        // transfer), then the scratch (per-entry bests, insertion order, cache)
+        auto up = [](size_t b) { return (b + 15) & ~(size_t)15; };
+        const size_t o_off = 0, o_rboff = o_off + up(sizeof(int64_t) * (n + 1));
+        const size_t o_u = o_rboff + up(sizeof(int64_t) * (n + 1));
+        const size_t o_rules = o_u + up(sizeof(int32_t) * nu);
+        const size_t in_bytes = o_rules + up(sizeof(int32_t) * n);
+        const size_t o_res = in_bytes, o_ord = o_res + up(sizeof(InsBest) * nu);
+        const size_t o_rb = o_ord + up(sizeof(int32_t) * nu);
+        const size_t bytes = o_rb + up(sizeof(int2) * std::max<int64_t>(rboff[n], 1));
+        std::vector<unsigned char> host(in_bytes);
+        memcpy(host.data() + o_off, unrouted_off, sizeof(int64_t) * (n + 1));
+        memcpy(host.data() + o_rboff, rboff.data(), sizeof(int64_t) * (n + 1));
+        memcpy(host.data() + o_u, unrouted, sizeof(int32_t) * nu);
+        memcpy(host.data() + o_rules, rules, sizeof(int32_t) * n);
+        unsigned char *dbuf = nullptr;
+        MD_CUDA(cudaMallocAsync(&dbuf, bytes, st));
+        MD_CUDA(cudaMemcpyAsync(dbuf, host.data(), in_bytes, cudaMemcpyHostToDevice, st));
+        int64_t *doff = (int64_t *)(dbuf + o_off), *drboff = (int64_t *)(dbuf + o_rboff);
+        int32_t *du = (int32_t *)(dbuf + o_u), *drules = (int32_t *)(dbuf + o_rules);
+        InsBest *dres = (InsBest *)(dbuf + o_res);
+        int32_t *dord = (int32_t *)(dbuf + o_ord);
+        int2 *drb = (int2 *)(dbuf + o_rb);
         const size_t smem = sizeof(int) * ((size_t)I.nd + S->K);
         if (I.variant & MD_VARIANT_TW) {
             MD_CUDA(md_allow_smem((const void *)k_repair<true>, smem));
-            k_repair<true><<<S->n_sol, 256, smem, st>>>(I, S->d, du, doff, drb, drboff, dres, dord, drules);
+            k_repair<true><<<n, 256, smem, st>>>(I, S->d, du, doff, drb, drboff, dres, dord, drules);
         } else {
             MD_CUDA(md_allow_smem((const void *)k_repair<false>, smem));
-            k_repair<false><<<S->n_sol, 256, smem, st>>>(I, S->d, du, doff, drb, drboff, dres, dord, drules);
+            k_repair<false><<<n, 256, smem, st>>>(I, S->d, du, doff, drb, drboff, dres, dord, drules);
         }
         MD_CUDA(cudaGetLastError());
         r = md_launch_rebuild_all(S, st);  // the subsequence tables of the long routes
@@ -351,13 +357,7 @@ extern "C" md_status md_repair_insert(md_solutions *S, const int32_t *rules, con
         r = md_launch_totals(S, st);
         if (r != MD_OK) return r;
         if (order) MD_CUDA(cudaMemcpyAsync(order, dord, sizeof(int32_t) * nu, cudaMemcpyDeviceToHost, st));
-        MD_CUDA(cudaFreeAsync(du, st));
-        MD_CUDA(cudaFreeAsync(dord, st));
-        MD_CUDA(cudaFreeAsync(dres, st));
-        MD_CUDA(cudaFreeAsync(doff, st));
-        MD_CUDA(cudaFreeAsync(drb, st));
-        MD_CUDA(cudaFreeAsync(drboff, st));
-        MD_CUDA(cudaFreeAsync(drules, st));
+        MD_CUDA(cudaFreeAsync(dbuf, st));
     }
     int32_t err = 0;
     MD_CUDA(cudaMemcpyAsync(&err, S->d.err, sizeof(err), cudaMemcpyDeviceToHost, st));
