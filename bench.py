@@ -647,10 +647,14 @@ def run_learned(args):
 REPAIR_RULES = ("FBI", "IBI", "FRI", "IRI")
 
 
-def repair_workload(rank: int = 0):
-    """The bench instance's 32 initial solutions with a quarter of their routes and a tenth of
-    the remaining customers removed, as a route exchange leaves them."""
-    spec, sols, _ = workload_spec(rank)
+def repair_workload(rank: int = 0, large: bool = False):
+    """The bench instance's 32 initial solutions (large: the 20 x 10000 instance's 8) with a
+    quarter of their routes and a tenth of the remaining customers removed, as a route exchange
+    leaves them."""
+    if large:
+        spec, sols, _ = learned_workload(LEARNED_SOL)
+    else:
+        spec, sols, _ = workload_spec(rank)
     parts = [W.partial_solution(sol, SEED + 500 + i, p_route=0.25, p_cust=0.1) for i, sol in enumerate(sols)]
     return spec, [p[0] for p in parts], [p[1] for p in parts]
 
@@ -682,9 +686,14 @@ def run_repair(args):
     stream = torch.cuda.Stream(dev)
     torch.cuda.set_stream(stream)
     sptr = stream.cuda_stream
-    spec, keep, un = repair_workload()
+    large = args.workload == "repair-mdvrptw-20x10000"
+    spec, keep, un = repair_workload(large=large)
+    n_sol = len(keep)
     inst = mdls.Instance(spec)
-    S = mdls.Solutions(inst, N_SOL, spec.n_customers + 1, spec.n_customers)
+    if large:  # slots for twice the routes; 256 customers per route (IBI lengthens routes)
+        S = mdls.Solutions(inst, n_sol, 2 * max(len(k) for k in keep) + 64, 256)
+    else:
+        S = mdls.Solutions(inst, n_sol, spec.n_customers + 1, spec.n_customers)
     inserted = sum(len(u) for u in un)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
 
@@ -712,7 +721,7 @@ def run_repair(args):
     total_ms = sum(ms)
     value = inserted * len(REPAIR_RULES) * args.steps / (total_ms / 1e3)
     cpu = None
-    if pool is not None:
+    if pool is not None and not large:
         jobs = [(0, i, r) for r in range(len(REPAIR_RULES)) for i in range(N_SOL)]
         t0 = time.perf_counter()
         res = pool.map(_oracle_repair, jobs)
@@ -727,13 +736,14 @@ def run_repair(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / max(args.steps, 1),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic",
-        "config": {"workload": f"repair-mdvrptw-6x288: {N_SOL} partial solutions of the mdvrptw-6x288 "
-                               f"bench instance ({inserted / N_SOL:.1f} unrouted customers each), one "
-                               f"repair per solution under each rule {'/'.join(REPAIR_RULES)}",
+        "config": {"workload": (f"{args.workload}: {n_sol} partial solutions of the "
+                                f"{'20x10000 MDVRPTW' if large else 'mdvrptw-6x288 bench'} instance "
+                                f"({inserted / n_sol:.1f} unrouted customers each), one repair per solution "
+                                f"under each rule {'/'.join(REPAIR_RULES)}"),
                    "l2": "flushed between timed steps (256 MB write)",
                    "timed": "md_repair_insert calls, including the H2D load of the partial routes"},
         "ms_per_rule": dict(zip(REPAIR_RULES, per_rule)),
-        "repairs_per_s": N_SOL * len(REPAIR_RULES) * args.steps / (total_ms / 1e3),
+        "repairs_per_s": n_sol * len(REPAIR_RULES) * args.steps / (total_ms / 1e3),
         "cpu_baseline": cpu,
         # per call: k_scatter, k_fill_lambda, k_rebuild_all, k_totals (the load), k_repair, k_totals
         "gpu_launches": 6 * len(REPAIR_RULES) * args.steps,
@@ -910,7 +920,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", choices=["mdvrptw-6x288", "batch16-uneven", "learned-20x10000",
                                            "plain-20x10000", "repair-mdvrptw-6x288", "mdvrp-6x288-2opt",
-                                           "memetic-mdvrptw-6x288"],
+                                           "memetic-mdvrptw-6x288", "repair-mdvrptw-20x10000"],
                     default="mdvrptw-6x288")
     ap.add_argument("--solutions", type=int, default=0, help="solutions of the learned workload (0: 8)")
     ap.add_argument("--plain-steps", type=int, default=1,
@@ -934,7 +944,7 @@ def main():
         run_learned(args)
     elif args.workload == "plain-20x10000":
         run_plain_large(args)
-    elif args.workload == "repair-mdvrptw-6x288":
+    elif args.workload in ("repair-mdvrptw-6x288", "repair-mdvrptw-20x10000"):
         run_repair(args)
     elif args.workload == "memetic-mdvrptw-6x288":
         run_memetic(args)

@@ -22,10 +22,15 @@
 
 #include "route_build.cuh"
 
+#ifndef MD_REPAIR_THREADS
+#define MD_REPAIR_THREADS 512  // threads of a repair CTA (one CTA per solution)
+#endif
+
 namespace {
 
 struct InsBest {  // one customer's best insertion and its best cost in another route
     int c1, r1, k1, c2;  // r1 < 0: none; c2 = INT_MAX: no other route
+    int r2, pad[3];      // the route of c2 (-1: none)
 };
 
 __device__ __forceinline__ int dcost(const DevInst &I, int a, int b) { return __ldg(&I.dist[(size_t)a * I.nn + b]); }
@@ -34,12 +39,18 @@ __device__ __forceinline__ Seg nodeseg(const DevInst &I, int n) { return node_se
 
 // Folds route best (c, r, k) into a customer's pair; routes arrive in increasing slot order.
 __device__ __forceinline__ void ins_push(InsBest &b, int c, int r, int k) {
-    if (b.r1 < 0 || c < b.c1) {
-        if (b.r1 >= 0) b.c2 = min(b.c2, b.c1);
+    if (b.r1 < 0 || c < b.c1 || (c == b.c1 && r < b.r1)) {
+        if (b.r1 >= 0 && (b.c1 < b.c2 || (b.c1 == b.c2 && b.r1 < b.r2))) { b.c2 = b.c1; b.r2 = b.r1; }
         b.c1 = c; b.r1 = r; b.k1 = k;
-    } else {
-        b.c2 = min(b.c2, c);
+    } else if (c < b.c2 || (c == b.c2 && r < b.r2)) {
+        b.c2 = c; b.r2 = r;
     }
+}
+
+__device__ __forceinline__ InsBest ins_none() {
+    InsBest b;
+    b.c1 = INT_MAX; b.r1 = -1; b.k1 = -1; b.c2 = INT_MAX; b.r2 = -1;
+    return b;
 }
 
 // Selection key of customer i under the rule; smaller is better.  Best insertion: (cost, i).
@@ -75,21 +86,27 @@ __device__ __forceinline__ PickKey pick_shfl(const PickKey &k, int o) {
 // Cheapest insertion of u into route slot r of solution s over the positions k0, k0 + step, ...
 // (feasible ones only when feas): {cost, position}, position -1 when there is none.  Ties keep
 // the earlier position.
+// arc: the route's arc costs c(c_k, c_{k+1}) (k = 0..L, c_0 = ds, c_{L+1} = de) staged in shared
+// memory, or nullptr.  With step 1 the cost c(u, c_{k+1}) of position k is carried over as
+// c(c_{k+1}, u) of position k + 1 (the matrix is symmetric), so a position reads one new entry.
 template <bool TW>
 __device__ int2 route_best(const DevInst &I, const DevSols &D, int s, int r, int u, bool feas, int k0 = 0,
-                           int step = 1) {
+                           int step = 1, const int *arc = nullptr) {
     const bool open = (I.variant & MD_VARIANT_OPEN) != 0;
     const size_t sr = (size_t)s * D.R + r;
     const int4 h = D.rhdr[sr];
     const int L = h.x, ds = h.y, de = h.z;
     const int32_t *row = D.rnodes + sr * D.K;
     int rc = INT_MAX, rk = -1;
+    int carry = -1;  // c(u, a) of this position when step is 1, else -1
     for (int k = k0; k <= L; k += step) {
         const int a = k > 0 ? row[k - 1] : ds;
         const int bnode = k < L ? row[k] : (open ? MD_NONE : de);
-        const int cau = dcost(I, a, u);
+        const int cau = carry >= 0 ? carry : dcost(I, a, u);
         const int cub = bnode != MD_NONE ? dcost(I, u, bnode) : 0;
-        const int c = bnode != MD_NONE ? cau + cub - dcost(I, a, bnode) : cau;
+        const int cab = bnode != MD_NONE ? (arc ? arc[k] : dcost(I, a, bnode)) : 0;
+        const int c = bnode != MD_NONE ? cau + cub - cab : cau;
+        if (step == 1) carry = cub;
         if (c < rc) {
             bool ok = true;
             if (feas) {
@@ -114,13 +131,14 @@ __device__ int2 route_best(const DevInst &I, const DevSols &D, int s, int r, int
 // new ones appended), so an insertion changes one column of RB: round 0 fills every column, each
 // later round refreshes the column of the route that changed.
 template <bool TW>
-__global__ void __launch_bounds__(256) k_repair(DevInst I, DevSols D, int32_t *ulist, const int64_t *uoff,
+__global__ void __launch_bounds__(MD_REPAIR_THREADS, 1) k_repair(DevInst I, DevSols D, int32_t *ulist, const int64_t *uoff,
                                                 int2 *RB, const int64_t *rb_off, InsBest *res, int32_t *order,
                                                 const int32_t *rules) {
     extern __shared__ int sm_dyn[];
     int *s_dcount = sm_dyn;              // [nd] routes departing from each depot
     int *s_stage = sm_dyn + I.nd;        // [K] staging of a route's tail
-    __shared__ PickKey s_red[8];
+    int *s_arc = s_stage + D.K;          // [K + 1] arc costs of the route that changed
+    __shared__ PickKey s_red[32];
     __shared__ int s_stop, s_M, s_dirty;
     const int s = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
     const int rule = rules[s];
@@ -154,6 +172,16 @@ __global__ void __launch_bounds__(256) k_repair(DevInst I, DevSols D, int32_t *u
             // the route that changed, for every listed customer: g lanes per customer split its
             // positions (g = 1..8, as many as the customers left allow)
             const int r = s_dirty, left = nU - done;
+            {
+                const int4 h = D.rhdr[(size_t)s * D.R + r];
+                const int32_t *row = D.rnodes + ((size_t)s * D.R + r) * D.K;
+                for (int k = tid; k <= h.x; k += blockDim.x) {
+                    const int a = k > 0 ? row[k - 1] : h.y;
+                    const int b = k < h.x ? row[k] : h.z;  // the arrival depot (unused when open)
+                    s_arc[k] = (k == h.x && open) ? 0 : dcost(I, a, b);
+                }
+                __syncthreads();
+            }
             int g = 1;
             while (g < 8 && 2 * g * left <= (int)blockDim.x) g *= 2;
             const int groups = blockDim.x / g, sub = tid & (g - 1), grp = tid / g;
@@ -161,7 +189,7 @@ __global__ void __launch_bounds__(256) k_repair(DevInst I, DevSols D, int32_t *u
                 const int i = base + grp;
                 const int u = i < nU ? U[i] : -1;
                 int2 e = make_int2(INT_MAX, -1);
-                if (u >= 0) e = route_best<TW>(I, D, s, r, u, feas, sub, g);
+                if (u >= 0) e = route_best<TW>(I, D, s, r, u, feas, sub, g, s_arc);
                 for (int o = 1; o < g; o <<= 1) {  // min by (cost, position) within the group
                     const int oc = __shfl_xor_sync(0xffffffffu, e.x, o), ok = __shfl_xor_sync(0xffffffffu, e.y, o);
                     if (ok >= 0 && (e.y < 0 || oc < e.x || (oc == e.x && ok < e.y))) e = make_int2(oc, ok);
@@ -175,12 +203,21 @@ __global__ void __launch_bounds__(256) k_repair(DevInst I, DevSols D, int32_t *u
         best.valid = 0; best.inf = 0; best.reg = 0; best.c1 = 0; best.i = INT_MAX;
         for (int i = tid; i < nU; i += blockDim.x) {
             if (U[i] < 0) continue;
-            InsBest b;
-            b.c1 = INT_MAX; b.r1 = -1; b.k1 = -1; b.c2 = INT_MAX;
             const int2 *row = rb + (size_t)i * rcap;
-            for (int r = 0; r < M; r++) {
-                const int2 e = row[r];
-                if (e.y >= 0) ins_push(b, e.x, r, e.y);
+            InsBest b;
+            const int rd = done == 0 ? -1 : s_dirty;
+            if (rd < 0 || RS[i].r1 == rd || RS[i].r2 == rd) {
+                // round 0, or the changed route held this customer's best or second best: rescan
+                b = ins_none();
+                for (int r = 0; r < M; r++) {
+                    const int2 e = row[r];
+                    if (e.y >= 0) ins_push(b, e.x, r, e.y);
+                }
+            } else {
+                // any other route kept its cost: fold in the changed one
+                b = RS[i];
+                const int2 e = row[rd];
+                if (e.y >= 0) ins_push(b, e.x, rd, e.y);
             }
             RS[i] = b;
             PickKey k;
@@ -343,13 +380,13 @@ extern "C" md_status md_repair_insert(md_solutions *S, const int32_t *rules, con
         InsBest *dres = (InsBest *)(dbuf + o_res);
         int32_t *dord = (int32_t *)(dbuf + o_ord);
         int2 *drb = (int2 *)(dbuf + o_rb);
-        const size_t smem = sizeof(int) * ((size_t)I.nd + S->K);
+        const size_t smem = sizeof(int) * ((size_t)I.nd + 2 * (size_t)S->K + 1);
         if (I.variant & MD_VARIANT_TW) {
             MD_CUDA(md_allow_smem((const void *)k_repair<true>, smem));
-            k_repair<true><<<n, 256, smem, st>>>(I, S->d, du, doff, drb, drboff, dres, dord, drules);
+            k_repair<true><<<n, MD_REPAIR_THREADS, smem, st>>>(I, S->d, du, doff, drb, drboff, dres, dord, drules);
         } else {
             MD_CUDA(md_allow_smem((const void *)k_repair<false>, smem));
-            k_repair<false><<<n, 256, smem, st>>>(I, S->d, du, doff, drb, drboff, dres, dord, drules);
+            k_repair<false><<<n, MD_REPAIR_THREADS, smem, st>>>(I, S->d, du, doff, drb, drboff, dres, dord, drules);
         }
         MD_CUDA(cudaGetLastError());
         r = md_launch_rebuild_all(S, st);  // the subsequence tables of the long routes
