@@ -111,6 +111,22 @@ def distance_matrix(edges: list) -> np.ndarray:
     return d
 
 
+def distance_matrix_keys(keys: list) -> np.ndarray:
+    """distance_matrix from each member's edge keys (int64 arrays of distinct undirected edges,
+    as parent_arrays returns them)."""
+    n = len(keys)
+    allk = np.concatenate(keys) if n else np.zeros(0, np.int64)
+    uniq, inv = np.unique(allk, return_inverse=True)
+    A = np.zeros((n, max(len(uniq), 1)))
+    A[np.repeat(np.arange(n), [len(k) for k in keys]), inv] = 1.0
+    inter = A @ A.T
+    size = A.sum(1)
+    m = np.maximum(size[:, None], size[None, :])
+    d = np.where(m > 0, 100.0 * (1.0 - inter / np.where(m > 0, m, 1.0)), 0.0)
+    np.fill_diagonal(d, 0.0)
+    return d
+
+
 def chi_scores(f: np.ndarray, d: np.ndarray, xi: float) -> np.ndarray:
     """chi of Eq. (7) for every member, from the members' distance matrix d: rank 1 is the
     lowest f, and the largest mean distance to the five nearest other members (Eq. 8); ties by
@@ -418,7 +434,7 @@ class MDFIHA:
 
     def _reduce(self, run: Run):
         """Section 3.4: remove the member of lowest chi until mu remain."""
-        d = distance_matrix([solution_edges(s, self.open) for s in run.pop])
+        d = distance_matrix_keys([pre[2] for pre in run.pre])
         while len(run.pop) > self.mu:
             chi = chi_scores(np.asarray(run.f), d, self.xi)
             worst = int(np.lexsort((np.arange(len(chi)), chi))[0])

@@ -74,6 +74,16 @@ def test_solution_distance_and_chi_hand_example():
     assert np.allclose(chi, want)
 
 
+@pytest.mark.parametrize("open_", [False, True])
+def test_distance_from_edge_keys_matches_edge_sets(open_):
+    spec = tiny_spec(77, nd=3, nc=30, Q=40, NV=4, open_=open_, sym=open_)
+    pop = [random_solution(spec, 200 + k, max_len=6) for k in range(9)] + [[[0, 3, 0], [1, 4, 1]] + [
+        [2] + list(range(5, spec.n_nodes)) + [2]]]
+    keys = [MM.parent_arrays(x, spec.n_nodes, open_)[2] for x in pop]
+    want = MM.distance_matrix([MM.solution_edges(x, open_) for x in pop])
+    assert np.allclose(MM.distance_matrix_keys(keys), want, rtol=0, atol=1e-9)
+
+
 def test_dcrex_exchanges_routes_and_lists_the_unrouted():
     spec = tiny_spec(71, nd=3, nc=30, Q=40, NV=4)
     main = random_solution(spec, 72, max_len=6)
