@@ -295,9 +295,13 @@ def _dcrex_task(args):
 
 class GpuBackend:
     """Repairs and descends a batch of offspring through the C ABI (md_repair_insert,
-    md_descend with adaptive lambda)."""
+    md_descend with adaptive lambda).  route_slots / k_max size the solutions' route slots; the
+    default (n_customers + 1 slots of n_customers) fits any solution, but its subsequence
+    tables take n x n_customers^2 x 64 bytes for n solutions, so large instances pass smaller
+    ones (a repair that outgrows them raises MD_ERR_CAPACITY)."""
 
-    def __init__(self, spec, stream=None, persistent: bool = True, multi: bool = True):
+    def __init__(self, spec, stream=None, persistent: bool = True, multi: bool = True,
+                 route_slots: int | None = None, k_max: int | None = None):
         from . import mdls
         self.mdls = mdls
         self.spec = spec
@@ -307,11 +311,12 @@ class GpuBackend:
         self.persistent = persistent
         self.multi = multi  # leader-follower multi-move steps (Section 3.2.5), else the leader only
         self._sols = {}
+        self.R = route_slots or spec.n_customers + 1
+        self.K = k_max or spec.n_customers
 
     def _solutions(self, n):
         if n not in self._sols:
-            nc = self.spec.n_customers
-            self._sols[n] = self.mdls.Solutions(self.inst, n, nc + 1, nc)
+            self._sols[n] = self.mdls.Solutions(self.inst, n, self.R, self.K)
         return self._sols[n]
 
     def repair_descend(self, partials, unrouted, rules, perms, max_pass):
