@@ -95,8 +95,9 @@ def test_timewarp_hand_golden(oracle_lib):
     g = json.load(open(os.path.join(GOLDEN, "timewarp_hand.json")))
     n = g["nodes"]
     for case in g["cases"]:
+        var = W.VAR_TW | (W.VAR_OPEN if case.get("open") else 0)
         spec = W._assemble("g", 1, 2, n["x"], n["y"], [0, 1, 1], n["service"], case["tw_early"],
-                           case["tw_late"], 10, 1, 0, W.VAR_TW, 0, 1)
+                           case["tw_late"], 10, 1, 0, var, 0, 1)
         t = oracle_lib.Instance(spec).route_terms(case["route"])
         assert (t["dist"], t["tw"], t["dur"]) == (case["dist"], case["tw"], case["dur"]), case["name"]
 
