@@ -147,6 +147,13 @@ typedef struct md_config {
                                evaluation; use_graph, poll_every and n_groups are then unused,
                                and time_eval times the launch.  Needs a non-NULL stream.  Same
                                results as 0.  MD_ERR_TIMEOUT if a bounded wait gives up. */
+    int32_t wide_step;      /* graph form (persistent = 0; in md_batch_descend the instances that
+                               run solo) only: how a step selects, applies and
+                               rebuilds.  1: spread over the grid in four launches (one CTA per
+                               solution selects, one warp per selected move applies it, one warp
+                               per touched route rebuilds it, one CTA per solution finishes);
+                               -1: one CTA per solution does it all; 0: 1 when the solutions
+                               have at least 256 route slots, else -1.  Same results. */
 } md_config;
 
 /* Totals over all solutions of one md_descend call. */
@@ -160,6 +167,10 @@ typedef struct md_stats {
     int64_t eval_launches;  /* evaluation kernel launches */
     double eval_ms;         /* summed device time of the evaluation launches (time_eval = 1) */
     int64_t moves_by_op[MD_N_OPS]; /* scored move tuples per operator */
+    int64_t moves_exact;    /* moves whose concatenations were formed: on full neighbourhoods the
+                               others are decided by an exact lower bound (neither leader nor
+                               follower), so moves_scored - moves_exact were counted unformed */
+    int64_t moves_exact_by_op[MD_N_OPS];
 } md_stats;
 
 /* Message for the calling thread's last failing call ("" if none). */
@@ -414,12 +425,14 @@ md_status md_pruner_train(md_pruner *pruner, md_instance *inst, const uint8_t *l
 /* Allocation-free variant of md_eval_neighborhood + md_moves_read_leaders.  The paper has no
  * counterpart: it exists for callers that cannot call cudaMalloc (device memory budgeted up front,
  * latency-critical loops that must not enter the allocator, code handed only raw device buffers).
- * Evaluates operator ops_dev[s] (device int32 [n_sol]; < 0 skips the solution) for every solution
- * with its current lambda and writes, to device buffers the caller owns, the leader id (0 when
- * none) ids_dev [n_sol], its dF dF_dev [n_sol] and the scored-move count n_scored_dev [n_sol].
- * No follower table and no dump.  Scratch: a static device array of 1 MiB that every GPU loading
- * the library holds until exit; it must hold n_sol * (128 * min(ceil(n_customers / 8), 1024) + 8)
- * bytes, else MD_ERR_CAPACITY.  The first call on each device looks up the array's device
+ * Evaluates operator ops_dev[s] (device int32 [n_sol]; a value outside [0, MD_N_OPS) skips the
+ * solution, which then reads id 0, dF 0 and count 0) for every solution with its current lambda
+ * and writes, to device buffers the caller owns, the leader id (0 when none) ids_dev [n_sol], its
+ * dF dF_dev [n_sol] and the scored-move count n_scored_dev [n_sol].  No follower table and no
+ * dump.  Scratch: a static device array of 1 MiB that every GPU loading the library holds until
+ * exit; it must hold n_sol * (16 * 8 * min(ceil(n_customers * wpc / 8), 1024) + 8) bytes, with
+ * wpc = min(max(floor(n_customers / 256), 1), 8), else MD_ERR_CAPACITY (for example 21 solutions
+ * of 1000 customers fit: 48 008 bytes each).  The first call on each device looks up the array's device
  * address, so make that first call before any stream capture.  All calls share the array: calls
  * that overlap on the GPU (other streams, other threads) race and must be serialised by the
  * caller.  Calls no cudaMalloc or cudaFree. */

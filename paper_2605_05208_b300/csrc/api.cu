@@ -10,29 +10,12 @@ namespace {
 
 // Leader per solution from the per-block candidates (one block per solution).
 __global__ void k_leaders(DevSols D, DevMoves M, unsigned long long *ids, double *fs) {
-    __shared__ double lf[32];
-    __shared__ uint32_t lid[32];
-    __shared__ int lv[32];
-    const int s = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    double f = 0.0;
-    uint32_t id = 0xffffffffu;
-    int valid = 0;
-    for (int k = tid; k < M.nblk; k += blockDim.x) {
-        LeadRec r = M.lpart[(size_t)s * M.nblk + k];
-        if (r.id != MD_NO_ID && (!valid || r.f < f || (r.f == f && r.id < id))) { f = r.f; id = r.id; valid = 1; }
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        const double of = __shfl_xor_sync(0xffffffffu, f, o);
-        const uint32_t oi = __shfl_xor_sync(0xffffffffu, id, o);
-        const int ov = __shfl_xor_sync(0xffffffffu, valid, o);
-        if (ov && (!valid || of < f || (of == f && oi < id))) { f = of; id = oi; valid = 1; }
-    }
-    if (lane == 0) { lf[warp] = f; lid[warp] = id; lv[warp] = valid; }
-    __syncthreads();
-    if (tid == 0) {
-        f = 0.0; id = 0xffffffffu; valid = 0;
-        for (int k = 0; k < (int)(blockDim.x + 31) / 32; k++)
-            if (lv[k] && (!valid || lf[k] < f || (lf[k] == f && lid[k] < id))) { f = lf[k]; id = lid[k]; valid = 1; }
+    const int s = blockIdx.x;
+    double f;
+    uint32_t id;
+    int valid;
+    block_leader(M.lpart + (size_t)s * M.nblk, M.nblk, f, id, valid);
+    if (threadIdx.x == 0) {
         ids[s] = valid ? (((unsigned long long)(D.ops[s] & MD_OP_MASK) << 32) | id) : 0ull;
         fs[s] = valid ? f : 0.0;
     }
@@ -46,7 +29,7 @@ __global__ void k_descend_init(DevSols D, int n_ops, int max_pass, int multi, in
     st[0] = 0; st[1] = 0; st[2] = 0; st[3] = 0;
     st[4] = n_ops; st[5] = max_pass; st[6] = multi; st[7] = lup;
     st[8] = sweep; st[9] = 0; st[10] = 0;
-    for (int k = 0; k < 16; k++) D.stats[(size_t)s * 16 + k] = 0;
+    for (int k = 0; k < MD_STATS; k++) D.stats[(size_t)s * MD_STATS + k] = 0;
     D.ops[s] = (int)D.perm[(size_t)s * max_pass * n_ops] | (sweep == 1 ? MD_OP_SWEEP : 0);
 }
 
@@ -70,9 +53,9 @@ static size_t moves_ncap(const md_solutions *s) {
 static void free_moves(md_moves *m) {
     if (!m) return;
     DevMoves &d = m->d;
-    cudaFree(d.lpart); cudaFree(d.nscored); cudaFree(d.foltab); cudaFree(d.cand_key);
+    cudaFree(d.lpart); cudaFree(d.nscored); cudaFree(d.nexact); cudaFree(d.foltab); cudaFree(d.cand_key);
     cudaFree(d.cand_rt); cudaFree(d.sel); cudaFree(d.nsel); cudaFree(d.dump); cudaFree(d.dump_n);
-    cudaFree(d.flist); cudaFree(d.fcount);
+    cudaFree(d.flist); cudaFree(d.fcount); cudaFree(d.wfree); cudaFree(d.wtouch); cudaFree(d.wcnt);
     free(m);
 }
 
@@ -91,6 +74,8 @@ extern "C" md_status md_moves_create(const md_solutions *sols, int64_t dump_capa
 #define MDM(call) do { if (e == cudaSuccess) e = (call); } while (0)
     MDM(cudaMalloc(&d.lpart, sizeof(LeadRec) * S * d.nblk));
     MDM(cudaMalloc(&d.nscored, sizeof(unsigned long long) * S));
+    MDM(cudaMalloc(&d.nexact, sizeof(unsigned long long) * S));
+    MDM(cudaMemset(d.nexact, 0, sizeof(unsigned long long) * S));
     MDM(cudaMalloc(&d.foltab, sizeof(unsigned long long) * S * R * R));
     MDM(cudaMalloc(&d.cand_key, sizeof(unsigned long long) * S * d.ncap));
     MDM(cudaMalloc(&d.cand_rt, sizeof(uint32_t) * S * d.ncap));
@@ -99,6 +84,10 @@ extern "C" md_status md_moves_create(const md_solutions *sols, int64_t dump_capa
     MDM(cudaMemset(d.fcount, 0, sizeof(uint32_t) * S));
     MDM(cudaMalloc(&d.sel, sizeof(uint32_t) * S * R));
     MDM(cudaMalloc(&d.nsel, sizeof(int32_t) * S));
+    MDM(cudaMalloc(&d.wfree, sizeof(int32_t) * S * R));
+    MDM(cudaMalloc(&d.wtouch, sizeof(int32_t) * S * R));
+    MDM(cudaMalloc(&d.wcnt, sizeof(int32_t) * S * 2));
+    MDM(cudaMemset(d.wcnt, 0, sizeof(int32_t) * S * 2));
     MDM(cudaMalloc(&d.dump_n, sizeof(unsigned long long)));
     if (dump_capacity > 0) MDM(cudaMalloc(&d.dump, sizeof(md_move) * dump_capacity));
     MDM(cudaMemset(d.nscored, 0, sizeof(unsigned long long) * S));
@@ -143,6 +132,7 @@ extern "C" md_status md_eval_neighborhood(md_solutions *s, const int32_t *ops, c
     md_status r = upload_lambda(s, lambda, st);
     if (r != MD_OK) return r;
     MD_CUDA(cudaMemsetAsync(m->d.nscored, 0, sizeof(unsigned long long) * s->n_sol, st));
+    MD_CUDA(cudaMemsetAsync(m->d.nexact, 0, sizeof(unsigned long long) * s->n_sol, st));
     MD_CUDA(cudaMemsetAsync(m->d.dump_n, 0, sizeof(unsigned long long), st));
     if (m->pending) {  // a follower table no selection consumed: start from an empty one
         MD_CUDA(cudaMemsetAsync(m->d.foltab, 0xff, sizeof(unsigned long long) * s->n_sol * s->R * s->R, st));
@@ -312,18 +302,20 @@ md_status md_descend_prepare(md_solutions *s, const md_config *cfg, const uint8_
 static md_status descend_stats(md_solutions *s, md_stats *out, long long launches, long long eval_launches,
                                double eval_ms, cudaStream_t st) {
     if (!out) return MD_OK;
-    std::vector<long long> h((size_t)s->n_sol * 16);
-    MD_CUDA(cudaMemcpyAsync(h.data(), s->d.stats, sizeof(long long) * 16 * s->n_sol, cudaMemcpyDeviceToHost, st));
+    std::vector<long long> h((size_t)s->n_sol * MD_STATS);
+    MD_CUDA(cudaMemcpyAsync(h.data(), s->d.stats, sizeof(long long) * MD_STATS * s->n_sol, cudaMemcpyDeviceToHost, st));
     MD_CUDA(cudaStreamSynchronize(st));
     memset(out, 0, sizeof(*out));
     for (int i = 0; i < s->n_sol; i++) {
-        const long long *x = &h[(size_t)i * 16];
+        const long long *x = &h[(size_t)i * MD_STATS];
         out->moves_scored += x[0];
         out->steps += x[1];
         out->accepted_steps += x[2];
         out->applied_moves += x[3];
         if (x[4] > out->passes_max) out->passes_max = x[4];
         for (int o = 0; o < MD_N_OPS; o++) out->moves_by_op[o] += x[8 + o];
+        out->moves_exact += x[5];
+        for (int o = 0; o < MD_N_OPS; o++) out->moves_exact_by_op[o] += x[16 + o];
     }
     out->launches = launches;
     out->eval_launches = eval_launches;
@@ -364,6 +356,8 @@ extern "C" md_status md_descend(md_solutions *s, const md_config *cfg, md_stats 
             }
         return descend_stats(s, out, launches + 1, 1, ms, st);
     }
+    const bool wide = md_wide_step(s, cfg->wide_step);
+    const int step_launches = wide ? 4 : 1;
     const int poll = cfg->poll_every > 0 ? cfg->poll_every : 1;
     const int steps_per_poll = cfg->n_ops * poll;
     // Solutions are independent: with n_groups > 1 they advance in groups on concurrent streams
@@ -420,7 +414,7 @@ extern "C" md_status md_descend(md_solutions *s, const md_config *cfg, md_stats 
                 md_status q = md_launch_eval(s, m, eflags, sg, a, b - a);
                 if (q != MD_OK) return q;
                 if (e) MD_CUDA(cudaEventRecordWithFlags(e[1], sg, rf));
-                q = md_launch_step(s, m, sg, a, b - a);
+                q = wide ? md_launch_step_wide(s, m, sg, a, b - a) : md_launch_step(s, m, sg, a, b - a);
                 if (q != MD_OK) return q;
             }
         }
@@ -457,7 +451,7 @@ extern "C" md_status md_descend(md_solutions *s, const md_config *cfg, md_stats 
             rr = enqueue(false);
             if (rr != MD_OK) break;
         }
-        launches += 2LL * steps_per_poll * G;
+        launches += (1LL + step_launches) * steps_per_poll * G;
         eval_launches += (long long)steps_per_poll * G;
         passes_done += poll;
         cudaError_t ce = cudaMemcpyAsync(state.data(), s->d.state, sizeof(int32_t) * MD_STATE * s->n_sol, cudaMemcpyDeviceToHost, st);

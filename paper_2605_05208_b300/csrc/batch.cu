@@ -380,7 +380,8 @@ extern "C" md_status md_batch_descend(md_batch *b, const md_config *cfg, md_stat
                 cudaStream_t sg = G > 0 ? side[g] : st;
                 md_status q = md_launch_eval(s, s->scratch, eflags, sg, 0, -1);
                 if (q != MD_OK) return q;
-                q = md_launch_step(s, s->scratch, sg, 0, -1);
+                q = md_wide_step(s, cfg->wide_step) ? md_launch_step_wide(s, s->scratch, sg, 0, -1)
+                                                    : md_launch_step(s, s->scratch, sg, 0, -1);
                 if (q != MD_OK) return q;
             }
         }
@@ -416,7 +417,8 @@ extern "C" md_status md_batch_descend(md_batch *b, const md_config *cfg, md_stat
             rr = enqueue();
             if (rr != MD_OK) break;
         }
-        launches += 2LL * steps * ((nb > 0 ? 1 : 0) + (long long)solo_items.size()) + 1;
+        launches += 2LL * steps * (nb > 0 ? 1 : 0) + 1;
+        for (int i : solo_items) launches += (1LL + (md_wide_step(b->sols[i], cfg->wide_step) ? 4 : 1)) * steps;
         iters++;
         passes += poll;
         cudaError_t ce = cudaMemsetAsync(b->running_d, 0, sizeof(int), st);
@@ -438,8 +440,8 @@ extern "C" md_status md_batch_descend(md_batch *b, const md_config *cfg, md_stat
         md_solutions *s = b->sols[i];
         int32_t err = 0;
         MD_CUDA(cudaMemcpyAsync(&err, s->d.err, sizeof(err), cudaMemcpyDeviceToHost, st));
-        std::vector<long long> h((size_t)s->n_sol * 16);
-        MD_CUDA(cudaMemcpyAsync(h.data(), s->d.stats, sizeof(long long) * 16 * s->n_sol, cudaMemcpyDeviceToHost, st));
+        std::vector<long long> h((size_t)s->n_sol * MD_STATS);
+        MD_CUDA(cudaMemcpyAsync(h.data(), s->d.stats, sizeof(long long) * MD_STATS * s->n_sol, cudaMemcpyDeviceToHost, st));
         MD_CUDA(cudaStreamSynchronize(st));
         if (err) {
             MD_CUDA(cudaMemsetAsync(s->d.err, 0, sizeof(int32_t), st));
@@ -448,13 +450,15 @@ extern "C" md_status md_batch_descend(md_batch *b, const md_config *cfg, md_stat
         }
         if (!out) continue;
         for (int k = 0; k < s->n_sol; k++) {
-            const long long *x = &h[(size_t)k * 16];
+            const long long *x = &h[(size_t)k * MD_STATS];
             out->moves_scored += x[0];
             out->steps += x[1];
             out->accepted_steps += x[2];
             out->applied_moves += x[3];
             out->passes_max = std::max(out->passes_max, (int64_t)x[4]);
             for (int o = 0; o < MD_N_OPS; o++) out->moves_by_op[o] += x[8 + o];
+            out->moves_exact += x[5];
+            for (int o = 0; o < MD_N_OPS; o++) out->moves_exact_by_op[o] += x[16 + o];
         }
     }
     if (out) {

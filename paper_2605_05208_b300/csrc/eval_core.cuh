@@ -55,6 +55,7 @@ struct Best {
     float lo, hi;     // lo <= dF(best) <= hi
     uint32_t routes;  // rA | rB << 16 of the best move
     unsigned long long n;
+    unsigned long long nx;  // moves evaluated exactly (their concatenations formed)
 };
 
 struct Ctx {
@@ -145,6 +146,7 @@ __device__ __forceinline__ Seg join_opt_t(const Ctx &C, const Seg &a, int a_last
 __device__ __forceinline__ void offer(const Ctx &C, uint32_t id, int dD, int dTW, int dL, int dU, int dV,
                                       int rA, int rB, Best &b, bool count, bool have_f, double f_in) {
     if (count) b.n++;
+    b.nx++;
     const bool pen = (dTW | dL | dU | dV) != 0;
     if ((C.flags & MD_EVAL_FOLLOWERS) && dD < 0 && !pen) {
         const int lo = min(rA, rB), hi = max(rA, rB);
@@ -321,7 +323,14 @@ __device__ __forceinline__ void split_candidates(const Ctx &C, int cu, int u, in
 // Relocate: seq(u) (1 or 2 nodes, possibly reversed) after v, or before v when v is first.
 // ------------------------------------------------------------------------------------------
 template <bool TW>
+__device__ void eval_relocate_full(const Ctx &C, int cu, int lane, Best &b, int *wl, int part, int wpc);
+
+template <bool TW>
 __device__ void eval_relocate(const Ctx &C, int cu, int lane, Best &b, int *wl, int part, int wpc) {
+    if (!C.lists && !(C.flags & MD_EVAL_DUMP)) {
+        eval_relocate_full<TW>(C, cu, lane, b, wl, part, wpc);
+        return;
+    }
     const DevInst &I = C.I;
     const int u = I.nd + cu;
     const Seg8 Pu = pre8(C, u), Su = suf8(C, u);
@@ -430,7 +439,14 @@ __device__ __constant__ int SW_RU[9] = {0, 0, 0, 0, 1, 0, 1, 0, 1};
 __device__ __constant__ int SW_RV[9] = {0, 0, 0, 0, 0, 1, 0, 1, 1};
 
 template <bool TW>
+__device__ void eval_swap_full(const Ctx &C, int cu, int lane, Best &b, int *wl, int part, int wpc);
+
+template <bool TW>
 __device__ void eval_swap(const Ctx &C, int cu, int lane, Best &b, int *wl, int part, int wpc) {
+    if (!C.lists && !(C.flags & MD_EVAL_DUMP)) {
+        eval_swap_full<TW>(C, cu, lane, b, wl, part, wpc);
+        return;
+    }
     const DevInst &I = C.I;
     const int u = I.nd + cu;
     const Seg8 Pu = pre8(C, u), Su = suf8(C, u);
@@ -579,7 +595,7 @@ __device__ __forceinline__ void reloc_setup(const Ctx &C, int cu, RelocCtx &r) {
 
 // candidate v on another route than u's
 template <bool TW>
-__device__ __forceinline__ void reloc_inter(const Ctx &C, const RelocCtx &r, int v, Best &b) {
+__device__ __forceinline__ void reloc_inter(const Ctx &C, const RelocCtx &r, int v, Best &b, bool cnt = true) {
     const DevInst &I = C.I;
     const Seg8 Pv = pre8(C, v), Sv = suf8(C, v);
     const int B = Pv.a, j = Pv.b, sv = Sv.b;
@@ -608,9 +624,9 @@ __device__ __forceinline__ void reloc_inter(const Ctx &C, const RelocCtx &r, int
         const RT nB = rt_of(nb, I);
         const RT &nA = k == 1 ? r.A1 : r.A2;
         const bool emp = r.LA == k;
-        sink(C, make_id32(r.u, v, var), nA.dist + nB.dist - r.oldA.dist - oldB.dist,
-             nA.tw + nB.tw - r.oldA.tw - oldB.tw, nA.lex + nB.lex - r.oldA.lex - oldB.lex,
-             nA.dex + nB.dex - r.oldA.dex - oldB.dex, emp ? r.dV_empty : 0, r.A, B, b);
+        offer(C, make_id32(r.u, v, var), nA.dist + nB.dist - r.oldA.dist - oldB.dist,
+              nA.tw + nB.tw - r.oldA.tw - oldB.tw, nA.lex + nB.lex - r.oldA.lex - oldB.lex,
+              nA.dex + nB.dex - r.oldA.dex - oldB.dex, emp ? r.dV_empty : 0, r.A, B, b, cnt, false, 0.0);
     }
 }
 
@@ -670,7 +686,7 @@ __device__ __forceinline__ void swap_setup(const Ctx &C, int cu, SwapCtx &w) {
 
 // candidate v on another route than u's (inter) or on u's route (intra)
 template <bool TW, bool INTRA>
-__device__ __forceinline__ void swap_cand(const Ctx &C, const SwapCtx &w, int v, Best &b) {
+__device__ __forceinline__ void swap_cand(const Ctx &C, const SwapCtx &w, int v, Best &b, bool cnt = true) {
     const DevInst &I = C.I;
     const Seg8 Pv = pre8(C, v), Sv = suf8(C, v);
     const int B = Pv.a, j = Pv.b, pv = Sv.a, sv = Sv.b;
@@ -726,9 +742,9 @@ __device__ __forceinline__ void swap_cand(const Ctx &C, const SwapCtx &w, int v,
         Seg nb = join_t<TW>(C, PV, pv, qu, quf);
         nb = join_opt<TW>(C, nb, qul, afterV);
         const RT nA = rt_of(na, I), nB = rt_of(nb, I);
-        sink(C, make_id32(w.u, v, var), nA.dist + nB.dist - w.oldA.dist - oldB.dist,
-             nA.tw + nB.tw - w.oldA.tw - oldB.tw, nA.lex + nB.lex - w.oldA.lex - oldB.lex,
-             nA.dex + nB.dex - w.oldA.dex - oldB.dex, 0, w.A, B, b);
+        offer(C, make_id32(w.u, v, var), nA.dist + nB.dist - w.oldA.dist - oldB.dist,
+              nA.tw + nB.tw - w.oldA.tw - oldB.tw, nA.lex + nB.lex - w.oldA.lex - oldB.lex,
+              nA.dex + nB.dex - w.oldA.dex - oldB.dex, 0, w.A, B, b, cnt, false, 0.0);
     }
 }
 
@@ -821,47 +837,77 @@ __device__ void eval_tile_lists(const Ctx &C, int op, int c0, int cstride, Best 
 // ------------------------------------------------------------------------------------------
 // 2-opt*: [ds_A..u] + [v..de_B] and [ds_B..pred v] + [succ u..de_A].
 // ------------------------------------------------------------------------------------------
+struct O2Ctx {
+    Seg PU;       // [ds_A..u]
+    RT oldA;
+    int u, A, su, dsA, deA, u_last;
+};
+
+template <bool TW>
+__device__ __forceinline__ void o2_setup(const Ctx &C, int cu, O2Ctx &o) {
+    const DevInst &I = C.I;
+    o.u = I.nd + cu;
+    const Seg8 Pu = pre8(C, o.u), Su = suf8(C, o.u);
+    o.A = Pu.a;
+    o.su = Su.b;
+    const size_t sA = (size_t)C.s * C.D.R + o.A;
+    const int4 hA = C.D.rhdr[sA];
+    o.dsA = hA.y;
+    o.deA = hA.z;
+    o.oldA = rt_of(seg_of(ld_seg8(&C.D.rterm[sA])), I);
+    o.PU = seg_of(Pu);
+    o.u_last = o.su < I.nd;  // depot or MD_NONE after u
+}
+
+// candidate v on another route than u's (returns without scoring when v is on u's route)
+template <bool TW>
+__device__ __forceinline__ void o2_cand(const Ctx &C, const O2Ctx &o, int v, Best &b, bool cnt = true) {
+    const DevInst &I = C.I;
+    const Seg8 Pv = pre8(C, v), Sv = suf8(C, v);
+    const int B = Pv.a, pv = Sv.a;
+    if (B == o.A) return;
+    const size_t sB = (size_t)C.s * C.D.R + B;
+    const int4 hB = C.D.rhdr[sB];
+    const int dsB = hB.y, deB = hB.z;
+    const RT oldB = rt_of(seg_of(ld_seg8(&C.D.rterm[sB])), I);
+    const RT nA = rt_of(join<TW>(C, o.PU, o.u, seg_of(Sv), v), I);
+    const bool b_empty = pv < I.nd && o.u_last;
+    RT nB = rt_zero();
+    if (!b_empty) nB = rt_of(join_opt_t<TW>(C, prefix_through(C, pv), pv, o.su), I);
+    int dV = 0;
+    if (!C.open) {
+        dV += (o.dsA != deB) + (b_empty ? 0 : (dsB != o.deA)) - (o.dsA != o.deA) - (dsB != deB);
+    }
+    if (b_empty) dV += veh_delta(C.D.dcount[(size_t)C.s * I.nd + dsB], I.NV, -1);
+    offer(C, make_id32(o.u, v, 0), nA.dist + nB.dist - o.oldA.dist - oldB.dist, nA.tw + nB.tw - o.oldA.tw - oldB.tw,
+          nA.lex + nB.lex - o.oldA.lex - oldB.lex, nA.dex + nB.dex - o.oldA.dex - oldB.dex, dV, o.A, B, b, cnt,
+          false, 0.0);
+}
+
+template <bool TW>
+__device__ void eval_2optstar_full(const Ctx &C, int cu, int lane, Best &b, int *wl, int part, int wpc);
+
 template <bool TW>
 __device__ void eval_2optstar(const Ctx &C, int cu, int lane, Best &b, int *wl, int part, int wpc) {
+    if (!C.lists && !(C.flags & MD_EVAL_DUMP)) {
+        eval_2optstar_full<TW>(C, cu, lane, b, wl, part, wpc);
+        return;
+    }
     const DevInst &I = C.I;
-    const int u = I.nd + cu;
-    const Seg8 Pu = pre8(C, u), Su = suf8(C, u);
-    const int A = Pu.a, su = Su.b;
-    const size_t sA = (size_t)C.s * C.D.R + A;
-    const int4 hA = C.D.rhdr[sA];
-    const int dsA = hA.y, deA = hA.z;
-    const RT oldA = rt_of(seg_of(ld_seg8(&C.D.rterm[sA])), I);
-    const Seg PU = seg_of(Pu);
-    const bool u_last = su < I.nd;  // depot or MD_NONE after u
+    O2Ctx o;
+    o2_setup<TW>(C, cu, o);
     const int ncand = C.lists ? I.nnbr[cu] : I.nc;
     // batches of 64 candidates, or of 32 when wpc warps share the customer: warp part takes
     // every wpc-th batch
     const int nb = wpc == 1 ? 64 : 32;
     for (int i0 = part * nb; i0 < ncand; i0 += nb * wpc) {
         int ni, na;
-        split_candidates(C, cu, u, A, lane, wl, false, i0, ncand, nb, ni, na);
+        split_candidates(C, cu, o.u, o.A, lane, wl, false, i0, ncand, nb, ni, na);
         const int ni_pad = (ni + 31) & ~31;  // passes run inter-route or intra-route candidates only
         for (int k = lane; k < ni_pad + na; k += 32) {
             const int v = k < ni ? wl[k] : (k >= ni_pad ? wl[63 - (k - ni_pad)] : -1);
             if (v < 0) continue;
-            const Seg8 Pv = pre8(C, v), Sv = suf8(C, v);
-            const int B = Pv.a, pv = Sv.a;
-            if (B == A) continue;
-            const size_t sB = (size_t)C.s * C.D.R + B;
-            const int4 hB = C.D.rhdr[sB];
-            const int dsB = hB.y, deB = hB.z;
-            const RT oldB = rt_of(seg_of(ld_seg8(&C.D.rterm[sB])), I);
-            const RT nA = rt_of(join<TW>(C, PU, u, seg_of(Sv), v), I);
-            const bool b_empty = pv < I.nd && u_last;
-            RT nB = rt_zero();
-            if (!b_empty) nB = rt_of(join_opt_t<TW>(C, prefix_through(C, pv), pv, su), I);
-            int dV = 0;
-            if (!C.open) {
-                dV += (dsA != deB) + (b_empty ? 0 : (dsB != deA)) - (dsA != deA) - (dsB != deB);
-            }
-            if (b_empty) dV += veh_delta(C.D.dcount[(size_t)C.s * I.nd + dsB], I.NV, -1);
-            sink(C, make_id32(u, v, 0), nA.dist + nB.dist - oldA.dist - oldB.dist, nA.tw + nB.tw - oldA.tw - oldB.tw,
-                 nA.lex + nB.lex - oldA.lex - oldB.lex, nA.dex + nB.dex - oldA.dex - oldB.dex, dV, A, B, b);
+            o2_cand<TW>(C, o, v, b);
         }
         __syncwarp();  // the list is read before the next batch overwrites it
     }
@@ -987,8 +1033,338 @@ __device__ void eval_depot_replace(const Ctx &C, int cu, int lane, Best &b, int 
     }
 }
 
+// ------------------------------------------------------------------------------------------
+// Full neighbourhoods (every customer a candidate) with an exact lower-bound rejection.
+//
+// Inserting a sequence Q between the nodes v and w of a route, when its detour
+// c(v, q_first) + (dur_Q - tw_Q) + c(q_last, w) - c(v, w) is not negative, lowers neither the
+// route's time warp nor its duration (an induction over the time-warp concatenation: the
+// arrival at w moves by at least the detour minus the warp absorbed inside [v, Q]) nor its
+// load.  A concatenation X + Y has at least the time warp and the duration of its pieces
+// together, and their summed load.  So, with weights w >= 0:
+//   Relocate  dF >= dD + w . (penalty change of u's route when seq(u) leaves)
+//   Swap      dF >= dD + w . (the same for u's route) + w . (the same for v's route)
+//   2-opt*    dF >= dD + w . (the pieces' bounds on both new routes - the old routes' terms)
+// The FP32 bound below stays under the FP64 dF that the combination of Eq. A1 forms, with a
+// margin far above that combination's rounding.  A move with dD >= 0 (no follower) whose bound
+// is above the lane's best leader candidate (or not below zero) can neither be the leader nor a
+// follower: it is counted as scored and its concatenations are skipped.  Every other candidate
+// -- and every candidate on u's own route -- goes to the exact code of the list path, 32 at a
+// time (one per lane), so the leader, the followers and the counts are those of the exact
+// evaluation.  The per-candidate inputs of the bounds come from the link records (clink), read
+// in candidate order, so a warp's reads are contiguous.
+// ------------------------------------------------------------------------------------------
+
+// FP32 lower bound of the FP64 penalty part w . (dTW, dL, dU, dV) of dF.
+__device__ __forceinline__ float pen_lo(const Ctx &C, int dTW, int dL, int dU, int dV) {
+    const double t0 = __dmul_rn(C.w[0], (double)dTW), t1 = __dmul_rn(C.w[1], (double)dL);
+    const double t2 = __dmul_rn(C.w[2], (double)dU), t3 = __dmul_rn(C.w[3], (double)dV);
+    const double p = __dadd_rn(__dadd_rn(__dadd_rn(t0, t1), t2), t3);
+    const double mag = fabs(t0) + fabs(t1) + fabs(t2) + fabs(t3);
+    return __double2float_rd(p - 1e-6 * mag - 1e-7);
+}
+
+// FP32 lower bound of w . (dTW, dL, dU) from the FP32 copies of the weights (their products and
+// sums stay within a few FP32 roundings of the FP64 value; the margin is far above them).
+__device__ __forceinline__ float pen_lo32(const Ctx &C, int dTW, int dL, int dU) {
+    const float t0 = C.wf[0] * (float)dTW, t1 = C.wf[1] * (float)dL, t2 = C.wf[2] * (float)dU;
+    return ((t0 + t1) + t2) - 1e-5f * (fabsf(t0) + fabsf(t1) + fabsf(t2)) - 1e-6f;
+}
+
+// Decided without its concatenations: no follower (dD >= 0), and dF >= dD + pen rules it out as
+// the lane's leader candidate.
+__device__ __forceinline__ bool lb_reject(const Best &b, int dD, float pen) {
+    const float lb = __fadd_rd((float)dD, pen);
+    return dD >= 0 && (b.valid ? lb > b.hi : lb >= 0.0f);
+}
+
+// Queues v (when keep) in the warp's survivor list wl[0..63] (nq entries, warp-uniform) and
+// returns whether 32 or more are queued.
+__device__ __forceinline__ bool queue_survivor(int *wl, int &nq, bool keep, int v, int lane) {
+    const unsigned m = __ballot_sync(0xffffffffu, keep);
+    if (keep) wl[nq + __popc(m & ((1u << lane) - 1u))] = v;
+    nq += __popc(m);
+    __syncwarp();
+    return nq >= 32;
+}
+
+__device__ __forceinline__ void dequeue_32(int *wl, int &nq, int lane) {
+    __syncwarp();
+    nq -= 32;
+    const int t = lane < nq ? wl[32 + lane] : 0;
+    __syncwarp();
+    if (lane < nq) wl[lane] = t;
+    __syncwarp();
+}
+
+template <bool TW>
+__device__ void eval_relocate_full(const Ctx &C, int cu, int lane, Best &b, int *wl, int part, int wpc) {
+    const DevInst &I = C.I;
+    RelocCtx r;
+    reloc_setup<TW>(C, cu, r);
+    const int dA1 = r.A1.dist - r.oldA.dist, dA2 = r.A2.dist - r.oldA.dist;
+    const float pen1 = pen_lo(C, r.A1.tw - r.oldA.tw, r.A1.lex - r.oldA.lex, r.A1.dex - r.oldA.dex,
+                              r.LA == 1 ? r.dV_empty : 0);
+    const float pen2 = pen_lo(C, r.A2.tw - r.oldA.tw, r.A2.lex - r.oldA.lex, r.A2.dex - r.oldA.dex,
+                              r.LA == 2 ? r.dV_empty : 0);
+    const int gap1 = r.q1.dur - r.q1.tw, gap2 = r.q2.dur - r.q2.tw, gap2r = r.q2r.dur - r.q2r.tw;
+    const int dq2 = r.q2.dist, dq2r = r.q2r.dist;
+    const bool two = r.has2 != 0, rev = two && C.sym;
+    // v's route gains at least tw_Q + min(warp at Q's arrival, detour) of time warp: the warp
+    // arriving late at Q's first node after v's earliest completion, when the detour covers it
+    const float w1 = C.wf[0] * (1.0f - 1e-5f);
+    const int nvar = 1 + (two ? 1 : 0) + (rev ? 1 : 0);  // variants after v (as many before v when v is first)
+    const int32_t *rowU = I.dist + (size_t)r.u * I.nn;
+    const int32_t *rowX = I.dist + (size_t)(two ? r.x : r.u) * I.nn;
+    const int4 *lk = C.D.clink + (size_t)C.s * I.nc * MD_LINK;
+    int nq = 0;
+    for (int i0 = part * 32; i0 < I.nc; i0 += 32 * wpc) {
+        const int i = i0 + lane;
+        bool keep = false;
+        if (i < I.nc) {
+            const int4 l0 = lk[MD_LINK * (size_t)i];
+            if (l0.x != r.A) {
+                const int j = l0.y, sv = l0.w, v = I.nd + i;
+                const int aout = lk[MD_LINK * (size_t)i + 1].y;
+                const int dep = TW ? lk[MD_LINK * (size_t)i + 5].w : 0;  // earliest completion at v
+                const bool last = sv == MD_NONE;  // v ends an open route: nothing follows seq(u)
+                const int cvu = __ldg(rowU + v);
+                const int cus = last ? 0 : __ldg(rowU + sv);
+                const int det1 = last ? (1 << 30) : cvu + gap1 + cus - aout;
+                const float tw1 = TW ? w1 * (float)(r.q1.tw + min(max(dep + cvu - r.q1.L, 0), det1)) : 0.0f;
+                keep = det1 < 0 || !lb_reject(b, dA1 + cvu + cus - aout, __fadd_rd(pen1, tw1));
+                if (j == 1 && !keep) {
+                    // v first on its route: seq(u) also goes between the departure depot and v
+                    const int ds = l0.z, ain = lk[MD_LINK * (size_t)i + 1].x;  // c(ds, v)
+                    const int eds = TW ? __ldg(&I.node[ds]).z : 0;
+                    const int cdu = __ldg(rowU + ds);
+                    const int d1 = cdu + gap1 + cvu - ain;
+                    const float t1 = TW ? w1 * (float)(r.q1.tw + min(max(eds + cdu - r.q1.L, 0), d1)) : 0.0f;
+                    keep = d1 < 0 || !lb_reject(b, dA1 + cdu + cvu - ain, __fadd_rd(pen1, t1));
+                    if (two && !keep) {
+                        const int cxv = __ldg(rowX + v);
+                        const int d2 = cdu + gap2 + cxv - ain;
+                        const float t2 = TW ? w1 * (float)(r.q2.tw + min(max(eds + cdu - r.q2.L, 0), d2)) : 0.0f;
+                        keep = d2 < 0 || !lb_reject(b, dA2 + cdu + dq2 + cxv - ain, __fadd_rd(pen2, t2));
+                        if (rev && !keep) {
+                            const int cdx = __ldg(rowX + ds);
+                            const int d3 = cdx + gap2r + cvu - ain;
+                            const float t3 = TW ? w1 * (float)(r.q2r.tw + min(max(eds + cdx - r.q2r.L, 0), d3)) : 0.0f;
+                            keep = d3 < 0 || !lb_reject(b, dA2 + cdx + dq2r + cvu - ain, __fadd_rd(pen2, t3));
+                        }
+                    }
+                }
+                if (two && !keep) {
+                    const int cxs = last ? 0 : __ldg(rowX + sv);
+                    const int det2 = last ? (1 << 30) : cvu + gap2 + cxs - aout;
+                    const float tw2 = TW ? w1 * (float)(r.q2.tw + min(max(dep + cvu - r.q2.L, 0), det2)) : 0.0f;
+                    keep = det2 < 0 || !lb_reject(b, dA2 + cvu + dq2 + cxs - aout, __fadd_rd(pen2, tw2));
+                    if (rev && !keep) {
+                        const int cvx = __ldg(rowX + v);
+                        const int det3 = last ? (1 << 30) : cvx + gap2r + cus - aout;
+                        const float tw3 = TW ? w1 * (float)(r.q2r.tw + min(max(dep + cvx - r.q2r.L, 0), det3)) : 0.0f;
+                        keep = det3 < 0 || !lb_reject(b, dA2 + cvx + dq2r + cus - aout, __fadd_rd(pen2, tw3));
+                    }
+                }
+                b.n += (unsigned long long)(j == 1 ? 2 * nvar : nvar);
+            }
+        }
+        if (queue_survivor(wl, nq, keep, I.nd + i, lane)) {
+            reloc_inter<TW>(C, r, wl[lane], b, false);
+            dequeue_32(wl, nq, lane);
+        }
+    }
+    if (lane < nq) reloc_inter<TW>(C, r, wl[lane], b, false);
+    __syncwarp();
+    // the other customers of u's route, exactly
+    const int32_t *rowA = C.D.rnodes + ((size_t)C.s * C.D.R + r.A) * C.D.K;
+    for (int t = part * 32 + lane; t < r.LA; t += 32 * wpc) {
+        const int v = rowA[t];
+        if (v != r.u) reloc_intra<TW>(C, r, v, b);
+    }
+}
+
+template <bool TW>
+__device__ void eval_swap_full(const Ctx &C, int cu, int lane, Best &b, int *wl, int part, int wpc) {
+    const DevInst &I = C.I;
+    SwapCtx w;
+    swap_setup<TW>(C, cu, w);
+    // u's route without seq(u) of one or two customers: the base of the insertion bound on u's
+    // route; v's route without seq(v) (from v's link record) is the base on v's route
+    const RT A1 = rt_of(join_opt<TW>(C, w.PU, w.pu, w.su), I);
+    const RT A2 = w.hasx ? rt_of(join_opt<TW>(C, w.PU, w.pu, w.sx), I) : A1;
+    const float pen1 = pen_lo(C, A1.tw - w.oldA.tw, A1.lex - w.oldA.lex, A1.dex - w.oldA.dex, 0);
+    const float pen2 = pen_lo(C, A2.tw - w.oldA.tw, A2.lex - w.oldA.lex, A2.dex - w.oldA.dex, 0);
+    const int gu1 = w.u1.dur - w.u1.tw, gu2 = w.u2.dur - w.u2.tw, gu2r = w.u2r.dur - w.u2r.tw;
+    const int4 *lk = C.D.clink + (size_t)C.s * I.nc * MD_LINK;
+    const int4 lu = lk[MD_LINK * (size_t)cu + 1];
+    const int c_pu_u = lu.x, c_u_su = lu.y, c_x_sx = lu.w;  // arcs of u's route around seq(u)
+    const bool su_none = w.su == MD_NONE, sx_none = !w.hasx || w.sx == MD_NONE;
+    const int c_pu_su = su_none ? 0 : cost(I, w.pu, w.su), c_pu_sx = sx_none ? 0 : cost(I, w.pu, w.sx);
+    const int32_t *rowPU = I.dist + (size_t)w.pu * I.nn;
+    const int32_t *rowU = I.dist + (size_t)w.u * I.nn;
+    const int32_t *rowX = I.dist + (size_t)(w.hasx ? w.x : w.u) * I.nn;
+    const int32_t *rowSU = I.dist + (size_t)(su_none ? w.u : w.su) * I.nn;
+    const int32_t *rowSX = I.dist + (size_t)(sx_none ? w.u : w.sx) * I.nn;
+    const int nvar = C.sym ? 9 : 4;
+    int nq = 0;
+    for (int i0 = part * 32; i0 < I.nc; i0 += 32 * wpc) {
+        const int i = i0 + lane;
+        bool keep = false;
+        if (i < I.nc) {
+            const int4 l0 = lk[MD_LINK * (size_t)i];
+            if (l0.x != w.A) {
+                const int4 l1 = lk[MD_LINK * (size_t)i + 1], l2 = lk[MD_LINK * (size_t)i + 2];
+                const int4 l3 = lk[MD_LINK * (size_t)i + 3], l4 = lk[MD_LINK * (size_t)i + 4];
+                const int v = I.nd + i, pv = l0.z, sv = l0.w, sy = l1.z;
+                const bool hasy = sv >= I.nd;
+                const float penB1 = pen_lo32(C, l3.z, l3.w, l4.x);
+                const float penB2 = hasy ? pen_lo32(C, l4.y, l4.z, l4.w) : 0.0f;
+                int n = 0;
+                if (!C.sym) {
+                    // the four variants (1,1), (2,1), (1,2), (2,2) written out, sharing their arcs:
+                    // seq(v) of kv customers into u's route, seq(u) of ku into v's route
+                    const int c_pu_v = __ldg(rowPU + v), c_pv_u = __ldg(rowU + pv);
+                    const bool sv_none = sv == MD_NONE, sy_none = !hasy || sy == MD_NONE;
+                    const int base = c_pu_v + c_pv_u - c_pu_u - l1.x;
+                    {   // (1,1)
+                        const int b1 = su_none ? 0 : __ldg(rowSU + v), d1 = sv_none ? 0 : __ldg(rowU + sv);
+                        const int dD = base + b1 + d1 - c_u_su - l1.y;
+                        const int detA = su_none ? 0 : c_pu_v + l2.x + b1 - c_pu_su;
+                        const int detB = sv_none ? 0 : c_pv_u + gu1 + d1 - l3.x;
+                        keep = detA < 0 || detB < 0 || !lb_reject(b, dD, __fadd_rd(pen1, penB1));
+                        n = 1;
+                    }
+                    if (w.hasx) {  // (2,1)
+                        const int b2 = sx_none ? 0 : __ldg(rowSX + v), e1 = sv_none ? 0 : __ldg(rowX + sv);
+                        const int dD = base + b2 + e1 - c_x_sx - l1.y;
+                        const int detA = sx_none ? 0 : c_pu_v + l2.x + b2 - c_pu_sx;
+                        const int detB = sv_none ? 0 : c_pv_u + gu2 + e1 - l3.x;
+                        keep = keep || detA < 0 || detB < 0 || !lb_reject(b, dD, __fadd_rd(pen2, penB1));
+                        n++;
+                    }
+                    if (hasy) {  // (1,2)
+                        const int f1 = su_none ? 0 : __ldg(rowSU + sv), d2 = sy_none ? 0 : __ldg(rowU + sy);
+                        const int dD = base + f1 + d2 - c_u_su - l1.w;
+                        const int detA = su_none ? 0 : c_pu_v + l2.y + f1 - c_pu_su;
+                        const int detB = sy_none ? 0 : c_pv_u + gu1 + d2 - l3.y;
+                        keep = keep || detA < 0 || detB < 0 || !lb_reject(b, dD, __fadd_rd(pen1, penB2));
+                        n++;
+                    }
+                    if (w.hasx && hasy) {  // (2,2)
+                        const int f2 = sx_none ? 0 : __ldg(rowSX + sv), e2 = sy_none ? 0 : __ldg(rowX + sy);
+                        const int dD = base + f2 + e2 - c_x_sx - l1.w;
+                        const int detA = sx_none ? 0 : c_pu_v + l2.y + f2 - c_pu_sx;
+                        const int detB = sy_none ? 0 : c_pv_u + gu2 + e2 - l3.y;
+                        keep = keep || detA < 0 || detB < 0 || !lb_reject(b, dD, __fadd_rd(pen2, penB2));
+                        n++;
+                    }
+                } else
+                for (int var = 0; var < nvar; var++) {
+                    const int ku = SW_KU[var], kv = SW_KV[var];
+                    const bool ru = SW_RU[var], rv = SW_RV[var];
+                    if ((ku == 2 && !w.hasx) || (kv == 2 && !hasy)) continue;
+                    n++;
+                    if (keep) continue;
+                    if (TW && rv) { keep = true; continue; }  // a reversed time-window sequence: no gap at hand
+                    const int qvf = (kv == 2 && rv) ? sv : v, qvl = (kv == 2 && !rv) ? sv : v;
+                    const bool au_none = ku == 1 ? su_none : sx_none;   // nothing after seq(u)
+                    const int32_t *rowAU = ku == 1 ? rowSU : rowSX;
+                    const int av = kv == 1 ? sv : sy;                   // after seq(v)
+                    const bool av_none = av == MD_NONE;
+                    const int quf = (ku == 2 && ru) ? w.x : w.u, qul = (ku == 2 && !ru) ? w.x : w.u;
+                    const int c_pu_qvf = __ldg(rowPU + qvf);
+                    const int c_qvl_au = au_none ? 0 : __ldg(rowAU + qvl);
+                    const int c_pv_quf = __ldg((quf == w.u ? rowU : rowX) + pv);
+                    const int c_qul_av = av_none ? 0 : __ldg((qul == w.u ? rowU : rowX) + av);
+                    const int dD = c_pu_qvf + c_qvl_au + c_pv_quf + c_qul_av - c_pu_u - (ku == 1 ? c_u_su : c_x_sx) -
+                                   l1.x - (kv == 1 ? l1.y : l1.w);
+                    // seq(v) into u's route without seq(u), seq(u) into v's route without seq(v)
+                    const int gv = kv == 1 ? l2.x : l2.y;
+                    const int gu = ku == 1 ? gu1 : (ru ? gu2r : gu2);
+                    const int detA = au_none ? 0 : c_pu_qvf + gv + c_qvl_au - (ku == 1 ? c_pu_su : c_pu_sx);
+                    const int detB = av_none ? 0 : c_pv_quf + gu + c_qul_av - (kv == 1 ? l3.x : l3.y);
+                    keep = detA < 0 || detB < 0 ||
+                           !lb_reject(b, dD, __fadd_rd(ku == 1 ? pen1 : pen2, kv == 1 ? penB1 : penB2));
+                }
+                b.n += (unsigned long long)n;
+            }
+        }
+        if (queue_survivor(wl, nq, keep, I.nd + i, lane)) {
+            swap_cand<TW, false>(C, w, wl[lane], b, false);
+            dequeue_32(wl, nq, lane);
+        }
+    }
+    if (lane < nq) swap_cand<TW, false>(C, w, wl[lane], b, false);
+    __syncwarp();
+    const int32_t *rowA = C.D.rnodes + ((size_t)C.s * C.D.R + w.A) * C.D.K;
+    const int LA = C.D.rhdr[(size_t)C.s * C.D.R + w.A].x;
+    for (int t = part * 32 + lane; t < LA; t += 32 * wpc) {
+        const int v = rowA[t];
+        if (v != w.u) swap_cand<TW, true>(C, w, v, b);
+    }
+}
+
+template <bool TW>
+__device__ void eval_2optstar_full(const Ctx &C, int cu, int lane, Best &b, int *wl, int part, int wpc) {
+    const DevInst &I = C.I;
+    O2Ctx o;
+    o2_setup<TW>(C, cu, o);
+    // the new routes [ds_A..u] + [v..de_B] and [ds_B..pred v] + [succ u..de_A] each join two
+    // existing pieces
+    const bool su_none = o.su == MD_NONE;
+    const Seg Y2 = su_none ? Seg{0, 0, 0, 0, 0, MD_NO_LATE} : suffix_from(C, o.su);
+    const int4 *lk = C.D.clink + (size_t)C.s * I.nc * MD_LINK;
+    const int c_u_su = lk[MD_LINK * (size_t)cu + 1].y;
+    const int32_t *rowU = I.dist + (size_t)o.u * I.nn;
+    const int32_t *rowSU = I.dist + (size_t)(su_none ? o.u : o.su) * I.nn;
+    const Seg8 *csuf = C.D.csuf + (size_t)C.s * I.nc;
+    float penV[5];  // w4 dV4 for dV4 = -2 .. 2
+#pragma unroll
+    for (int k = 0; k < 5; k++) penV[k] = pen_lo(C, 0, 0, 0, k - 2);
+    int nq = 0;
+    for (int i0 = part * 32; i0 < I.nc; i0 += 32 * wpc) {
+        const int i = i0 + lane;
+        bool keep = false;
+        if (i < I.nc) {
+            const int4 l0 = lk[MD_LINK * (size_t)i];
+            if (l0.x != o.A) {
+                const int v = I.nd + i, pv = l0.z;
+                keep = pv < I.nd && o.u_last;  // v's route would empty: exact
+                if (!keep) {
+                    const int4 l1 = lk[MD_LINK * (size_t)i + 1], l2 = lk[MD_LINK * (size_t)i + 2];
+                    const int4 X2 = lk[MD_LINK * (size_t)i + 5];  // [ds_B .. pred v]: tw, load, dur
+                    const int4 Y1 = reinterpret_cast<const int4 *>(&csuf[i])[0];  // [v .. de_B]: dist, load, dur, tw
+                    const Seg oB = seg_of(ld_seg8(&C.D.rterm[(size_t)C.s * C.D.R + l0.x]));
+                    const int cuv = __ldg(rowU + v), cps = su_none ? 0 : __ldg(rowSU + pv);
+                    const int dD = cuv + cps - c_u_su - l1.x;
+                    const int dsB = l2.z & 0xffff, deB = l2.z >> 16;
+                    const int dV = C.open ? 0 : (o.dsA != deB) + (dsB != o.deA) - (o.dsA != o.deA) - (dsB != deB);
+                    const int dT = o.PU.tw + Y1.w + X2.x + Y2.tw - o.oldA.tw - oB.tw;
+                    const int dL = load_ex(o.PU.load + Y1.y, I.Q) + load_ex(X2.y + Y2.load, I.Q) - o.oldA.lex -
+                                   load_ex(oB.load, I.Q);
+                    const int dU = dur_ex(o.PU.dur + Y1.z + cuv, I.D) + dur_ex(X2.z + (su_none ? 0 : Y2.dur + cps), I.D) -
+                                   o.oldA.dex - dur_ex(oB.dur, I.D);
+                    float pv4 = penV[0];
+#pragma unroll
+                    for (int k = 1; k < 5; k++) pv4 = dV == k - 2 ? penV[k] : pv4;
+                    const float pen = __fadd_rd(pen_lo32(C, dT, dL, dU), pv4);
+                    keep = !lb_reject(b, dD, pen);
+                }
+                b.n += 1ull;
+            }
+        }
+        if (queue_survivor(wl, nq, keep, I.nd + i, lane)) {
+            o2_cand<TW>(C, o, wl[lane], b, false);
+            dequeue_32(wl, nq, lane);
+        }
+    }
+    if (lane < nq) o2_cand<TW>(C, o, wl[lane], b, false);
+    __syncwarp();
+}
+
 __device__ __forceinline__ void best_init(Best &b) {
-    b.f = 0.0; b.id = MD_NO_ID; b.valid = 0; b.fx = 0; b.routes = 0; b.n = 0;
+    b.f = 0.0; b.id = MD_NO_ID; b.valid = 0; b.fx = 0; b.routes = 0; b.n = 0; b.nx = 0;
     b.dD = b.dT = b.dL = b.dU = b.dV = 0;
     b.lo = b.hi = 0.0f;
 }
@@ -1016,6 +1392,7 @@ __device__ __forceinline__ void warp_commit(const Ctx &C, Best &b, size_t slot, 
         const int ov = __shfl_xor_sync(0xffffffffu, b.valid, o);
         const uint32_t ort = __shfl_xor_sync(0xffffffffu, b.routes, o);
         b.n += __shfl_xor_sync(0xffffffffu, b.n, o);
+        b.nx += __shfl_xor_sync(0xffffffffu, b.nx, o);
         if (ov && (!b.valid || of < b.f || (of == b.f && oi < b.id))) { b.f = of; b.id = oi; b.valid = 1; b.routes = ort; }
     }
     if (lane == 0) {
@@ -1023,6 +1400,7 @@ __device__ __forceinline__ void warp_commit(const Ctx &C, Best &b, size_t slot, 
         r.f = b.f; r.id = b.valid ? b.id : MD_NO_ID; r.routes = b.routes;
         C.M.lpart[(size_t)C.s * C.M.nblk + slot] = r;
         if (b.n) atomicAdd(&C.M.nscored[C.s], b.n);
+        if (b.nx && C.M.nexact) atomicAdd(&C.M.nexact[C.s], b.nx);
     }
 }
 

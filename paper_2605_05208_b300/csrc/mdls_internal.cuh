@@ -13,6 +13,19 @@
 //   csubf   Seg8  [S * nc * K]      csubf[c][t]: customers at positions p(c)..p(c)+t of c's route
 //   csubb   Seg8  [S * nc * K]      csubb[c][t]: customers at positions p(c)-t..p(c)
 //                                   (both with {first node, last node}; for intra-route moves)
+//   clink   int4  [S * nc * MD_LINK] per customer v, its links on its route (for the evaluation's
+//                                   exact lower-bound rejection on full neighbourhoods):
+//                                   {route slot, position, pred, succ},
+//                                   {c(pred, v), c(v, succ) (0: no succ), succ of succ (MD_NONE:
+//                                    none), c(succ, succ of succ) (0: none)},
+//                                   {s_v, dur - tw of [v, succ] (succ a customer), ds | de << 16,
+//                                    1 if the route has no time warp, load or duration excess},
+//                                   {c(pred, succ), c(pred, succ of succ) (0: none), and the
+//                                    changes of time warp, load excess, duration excess when v
+//                                    leaves: [.. pred] + [succ ..]},
+//                                   {..., the same three when v and succ leave}
+//                                   {time warp, load, duration of [ds .. pred], the earliest
+//                                    completion of v's service, E + dur - tw of [ds .. v]}
 //   dcount  int32 [S * nd]          non-empty routes departing from each depot
 //   tot     int64 [S * 8]           D, TW, LoadEx, DurEx, closures, vehicle excess, V4, routes
 //   lam     float [S * 4], w double [S * 4]  penalty coefficients and FP64 weights
@@ -33,6 +46,8 @@
 #define MD_EVAL_WARPS 8  // warps per evaluation block; one leader record per warp
 #endif
 #define MD_STATE 16      // ints of per-solution descent state
+#define MD_STATS 24      // counters per solution (DevSols.stats)
+#define MD_LINK 6        // int4 per customer link record (DevSols.clink)
 #define MD_OP_SWEEP 0x100  // set in ops[s]: this step evaluates the full neighbourhood
 #define MD_OP_MASK 0xff
 
@@ -68,6 +83,7 @@ struct DevSols {
     Seg8 *csuf;
     Seg8 *csubf;
     Seg8 *csubb;
+    int4 *clink;
     int32_t *dcount;
     long long *tot;
     float *lam;
@@ -75,7 +91,9 @@ struct DevSols {
     int32_t *ops;      // [S] operator of the current step (-1 = none)
     int32_t *state;    // [S * 16] pass, slot, improved, done, n_ops, max_pass, multi, lambda_update,
                        // sweep period (0: never), step index, verification pass
-    long long *stats;  // [S * 16] moves scored, steps, accepted, applied, passes; [8+op] moves per op
+    long long *stats;  // [S * MD_STATS] moves scored, steps, accepted, applied, passes, moves evaluated
+                       // exactly (concatenations formed); [8+op] moves scored per op; [16+op]
+                       // moves evaluated exactly per op
     int32_t *err;      // [1] first error code raised on the device
     const uint8_t *perm; // [S * max_pass * n_ops] operator order (descent only)
 };
@@ -88,10 +106,41 @@ struct __align__(16) LeadRec {
 };
 #define MD_NO_ID 0xffffffffu
 
+// The solution's leader from its n leader candidates: the smallest (dF, id) among the records
+// that hold one.  Called by every thread of the block (a multiple of 32 threads, at most 1024);
+// thread 0 returns the block's result (valid = 0: no candidate).
+__device__ __forceinline__ void block_leader(const LeadRec *rec, int n, double &f, uint32_t &id, int &valid) {
+    __shared__ double lf[32];
+    __shared__ uint32_t lid[32];
+    __shared__ int lv[32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    f = 0.0;
+    id = MD_NO_ID;
+    valid = 0;
+    for (int k = tid; k < n; k += blockDim.x) {
+        const LeadRec r = rec[k];
+        if (r.id != MD_NO_ID && (!valid || r.f < f || (r.f == f && r.id < id))) { f = r.f; id = r.id; valid = 1; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const double of = __shfl_xor_sync(0xffffffffu, f, o);
+        const uint32_t oi = __shfl_xor_sync(0xffffffffu, id, o);
+        const int ov = __shfl_xor_sync(0xffffffffu, valid, o);
+        if (ov && (!valid || of < f || (of == f && oi < id))) { f = of; id = oi; valid = 1; }
+    }
+    if (lane == 0) { lf[warp] = f; lid[warp] = id; lv[warp] = valid; }
+    __syncthreads();
+    if (tid == 0) {
+        f = 0.0; id = MD_NO_ID; valid = 0;
+        for (int k = 0; k < (int)(blockDim.x + 31) / 32; k++)
+            if (lv[k] && (!valid || lf[k] < f || (lf[k] == f && lid[k] < id))) { f = lf[k]; id = lid[k]; valid = 1; }
+    }
+}
+
 struct DevMoves {
     int nblk;              // leader records per solution (evaluation blocks x MD_EVAL_WARPS)
     LeadRec *lpart;        // [S * nblk]
     unsigned long long *nscored;   // [S]
+    unsigned long long *nexact;    // [S] moves evaluated exactly (NULL: not counted)
     unsigned long long *foltab;    // [S * R * R] best follower key per route pair (i <= j used)
     unsigned long long *cand_key;  // [S * ncap] follower candidates for the selection
     uint32_t *cand_rt;             // [S * ncap] packed route pair (i | j << 16)
@@ -100,6 +149,9 @@ struct DevMoves {
     uint32_t *fcount;              // [S] entries of flist
     uint32_t *sel;         // [S * R] selected move ids (32-bit part), leader first
     int32_t *nsel;         // [S]
+    int32_t *wfree;        // [S * R] free route slots of a wide step (Depot-Insert), slot order
+    int32_t *wtouch;       // [S * R] routes a wide step touched
+    int32_t *wcnt;         // [S * 2] {free slots listed, routes touched} of a wide step
     md_move *dump;         // [dump_cap]
     unsigned long long *dump_n;
     long long dump_cap;
@@ -263,6 +315,11 @@ md_status md_launch_eval(md_solutions *s, md_moves *m, uint32_t flags, cudaStrea
 md_status md_launch_select(md_solutions *s, md_moves *m, int multi, cudaStream_t st);
 md_status md_launch_apply(md_solutions *s, md_moves *m, int update_lambda, cudaStream_t st);
 md_status md_launch_step(md_solutions *s, md_moves *m, cudaStream_t st, int s0 = 0, int count = -1);
+// The step spread over the grid (4 launches); md_wide_step: whether md_descend uses it, given
+// md_config.wide_step (0: when the solutions have at least MD_WIDE_STEP_MIN_R route slots).
+#define MD_WIDE_STEP_MIN_R 256
+md_status md_launch_step_wide(md_solutions *s, md_moves *m, cudaStream_t st, int s0 = 0, int count = -1);
+bool md_wide_step(const md_solutions *s, int mode);
 md_status md_launch_eval_batch(const BatchItem *items, int n_items, int total_tiles, int grid, bool tw,
                                uint32_t flags, int *next_tile, cudaStream_t st);
 md_status md_launch_step_batch(const BatchItem *items, int n_items, int total_sols, size_t smem, bool tw,

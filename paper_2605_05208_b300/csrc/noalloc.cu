@@ -13,7 +13,8 @@
 #include "mdls_internal.cuh"
 
 // Upper bound of the scratch: n_sol * (leader records * 16 + 8) bytes must fit (1 MiB), with one
-// leader record per evaluation warp.
+// leader record per evaluation warp: 8 * min(ceil(n_customers * wpc / 8), 1024) records, where
+// wpc = min(max(n_customers / 256, 1), 8) warps share a customer on full neighbourhoods.
 #define MD_NOALLOC_SCRATCH_BYTES (1u << 20)
 #define MD_NOALLOC_MAX_DEVICES 64
 
@@ -26,38 +27,23 @@ namespace {
 std::mutex g_setup_mutex;
 void *g_scratch_ptr[MD_NOALLOC_MAX_DEVICES] = {nullptr};
 
+// Operators outside [0, MD_N_OPS) skip their solution, like a negative operator: the high
+// bits of ops[s] are the descent's internal flags and must not reach the evaluation.
 __global__ void k_noalloc_set_ops(DevSols D, const int32_t *ops) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s < D.S) D.ops[s] = ops[s];
+    if (s < D.S) D.ops[s] = (ops[s] >= 0 && ops[s] < MD_N_OPS) ? ops[s] : -1;
 }
 
-// Leader per solution (one block per solution) from the per-block candidates in the scratch.
+// Leader per solution (one block per solution) from the per-warp candidates in the scratch.
 __global__ void k_noalloc_leaders(DevSols D, const LeadRec *lpart, int nblk, const unsigned long long *nscored,
                                   uint64_t *ids, double *fs, int64_t *n_scored) {
-    __shared__ double lf[32];
-    __shared__ uint32_t lid[32];
-    __shared__ int lv[32];
-    const int s = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    double f = 0.0;
-    uint32_t id = 0xffffffffu;
-    int valid = 0;
-    for (int k = tid; k < nblk; k += blockDim.x) {
-        const LeadRec r = lpart[(size_t)s * nblk + k];
-        if (r.id != MD_NO_ID && (!valid || r.f < f || (r.f == f && r.id < id))) { f = r.f; id = r.id; valid = 1; }
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        const double of = __shfl_xor_sync(0xffffffffu, f, o);
-        const uint32_t oi = __shfl_xor_sync(0xffffffffu, id, o);
-        const int ov = __shfl_xor_sync(0xffffffffu, valid, o);
-        if (ov && (!valid || of < f || (of == f && oi < id))) { f = of; id = oi; valid = 1; }
-    }
-    if (lane == 0) { lf[warp] = f; lid[warp] = id; lv[warp] = valid; }
-    __syncthreads();
-    if (tid == 0) {
-        f = 0.0; id = 0xffffffffu; valid = 0;
-        for (int k = 0; k < (int)(blockDim.x + 31) / 32; k++)
-            if (lv[k] && (!valid || lf[k] < f || (lf[k] == f && lid[k] < id))) { f = lf[k]; id = lid[k]; valid = 1; }
-        ids[s] = valid ? (((uint64_t)D.ops[s] << 32) | id) : 0ull;
+    const int s = blockIdx.x;
+    double f;
+    uint32_t id;
+    int valid;
+    block_leader(lpart + (size_t)s * nblk, nblk, f, id, valid);
+    if (threadIdx.x == 0) {
+        ids[s] = valid ? (((uint64_t)(D.ops[s] & MD_OP_MASK) << 32) | id) : 0ull;
         fs[s] = valid ? f : 0.0;
         n_scored[s] = (int64_t)nscored[s];
     }

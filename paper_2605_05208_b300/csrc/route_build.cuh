@@ -58,6 +58,55 @@ __device__ __forceinline__ SegN segn_node(const DevInst &I, int n) {
     return r;
 }
 
+// The link records of the customers of route slot r (layout in mdls_internal.cuh), from the
+// route's nodes and the prefix and suffix summaries just written; whole: the route's summary.
+// Called by all 32 lanes of one warp.
+template <bool TW>
+__device__ __forceinline__ void write_links(const DevInst &I, const DevSols &D, int s, int r, const int32_t *nodes,
+                                            int L, int ds, int de, bool open, const Seg &whole) {
+    const int lane = threadIdx.x & 31;
+    __syncwarp();  // the route's prefixes and suffixes are written
+    int4 *lk = D.clink + (size_t)s * I.nc * MD_LINK;
+    const Seg8 *cpre = D.cpre + (size_t)s * I.nc;
+    const Seg8 *csuf = D.csuf + (size_t)s * I.nc;
+    const int wlex = load_ex(whole.load, I.Q), wdex = dur_ex(whole.dur, I.D);
+    const bool feasible = whole.tw == 0 && wlex == 0 && wdex == 0;
+    for (int k = lane; k < L; k += 32) {
+        const int c = nodes[k];
+        const int pred = k > 0 ? nodes[k - 1] : ds;
+        // succ: the next customer, else the arrival depot (MD_NONE after an open route's last)
+        const int succ = k + 1 < L ? nodes[k + 1] : (open ? MD_NONE : de);
+        const int succ2 = k + 2 < L ? nodes[k + 2] : (k + 2 == L && !open ? de : MD_NONE);
+        const int a_in = I.dist[(size_t)pred * I.nn + c];
+        const int a_out = succ == MD_NONE ? 0 : I.dist[(size_t)c * I.nn + succ];
+        const int a_out2 = succ2 == MD_NONE ? 0 : I.dist[(size_t)succ * I.nn + succ2];
+        const Seg cs = node_seg(I.node[c]);
+        int gap2 = 0;
+        if (k + 1 < L) {
+            const Seg two = seg_cat<TW>(cs, node_seg(I.node[succ]), a_out);
+            gap2 = two.dur - two.tw;
+        }
+        // the route without c, and without c and its successor: [ds .. pred] + [after ..]
+        const Seg P = k > 0 ? seg_of(ld_seg8(&cpre[pred - I.nd])) : node_seg(I.node[ds]);
+        const int c_ps = succ == MD_NONE ? 0 : I.dist[(size_t)pred * I.nn + succ];
+        const int c_ps2 = succ2 == MD_NONE ? 0 : I.dist[(size_t)pred * I.nn + succ2];
+        Seg r1 = P, r2 = P;
+        if (succ != MD_NONE)
+            r1 = seg_cat<TW>(P, succ < I.nd ? node_seg(I.node[succ]) : seg_of(ld_seg8(&csuf[succ - I.nd])), c_ps);
+        if (succ2 != MD_NONE && k + 1 < L)
+            r2 = seg_cat<TW>(P, succ2 < I.nd ? node_seg(I.node[succ2]) : seg_of(ld_seg8(&csuf[succ2 - I.nd])), c_ps2);
+        int4 *e = lk + (size_t)(c - I.nd) * MD_LINK;
+        e[0] = make_int4(r, k + 1, pred, succ);
+        e[1] = make_int4(a_in, a_out, succ2, a_out2);
+        e[2] = make_int4(cs.dur, gap2, ds | (de << 16), feasible ? 1 : 0);
+        e[3] = make_int4(c_ps, c_ps2, r1.tw - whole.tw, load_ex(r1.load, I.Q) - wlex);
+        e[4] = make_int4(dur_ex(r1.dur, I.D) - wdex, r2.tw - whole.tw, load_ex(r2.load, I.Q) - wlex,
+                         dur_ex(r2.dur, I.D) - wdex);
+        const Seg8 Pc = ld_seg8(&cpre[c - I.nd]);  // [ds .. c]
+        e[5] = make_int4(P.tw, P.load, P.dur, Pc.E + Pc.dur - Pc.tw);
+    }
+}
+
 // Rebuilds every summary of route slot r of solution s; called by all 32 lanes of one warp.
 // SUBTABLES = false leaves the subsequence tables of routes longer than 32 customers stale (the
 // repair insertion, which reads only prefixes and suffixes, rebuilds them once at its end).
@@ -120,14 +169,19 @@ __device__ void rebuild_route(const DevInst &I, const DevSols &D, int s, int r) 
             st_seg8(&csuf[c - I.nd], suf, lane == 0 ? ds : prev,
                     lane == L - 1 ? (open ? MD_NONE : de) : nextc);
         }
+        // lane 0: gf = [c_1..c_L], pre = [ds, c_1]; the whole route is ds + gf (+ de)
+        const Seg head = seg_cat<TW>(sds, gf, I.dist[(size_t)ds * I.nn + c]);
+        Seg whole = open ? head : seg_cat<TW>(head, sde, arc_de);
         if (lane == 0) {
-            // lane 0: gf = [c_1..c_L], pre = [ds, c_1]; the whole route is ds + gf (+ de)
-            const Seg head = seg_cat<TW>(sds, gf, I.dist[(size_t)ds * I.nn + c]);
-            const Seg whole = open ? head : seg_cat<TW>(head, sde, arc_de);
             st_seg8(&D.rterm[sr], whole, ds, open ? cL : de);
             st_seg8(&D.rcore[sr], gf, c, cL);
             D.rhdr[sr] = make_int4(L, ds, de, cL);
         }
+        whole.dist = __shfl_sync(0xffffffffu, whole.dist, 0);
+        whole.load = __shfl_sync(0xffffffffu, whole.load, 0);
+        whole.dur = __shfl_sync(0xffffffffu, whole.dur, 0);
+        whole.tw = __shfl_sync(0xffffffffu, whole.tw, 0);
+        write_links<TW>(I, D, s, r, nodes, L, ds, de, open, whole);
         return;
     }
 
@@ -206,10 +260,12 @@ __device__ void rebuild_route(const DevInst &I, const DevSols &D, int s, int r) 
             st_seg8(&Bk[t], g, m, c);
         }
     }
+    // carry and core are the same on every lane (shuffled from one lane)
+    SegN whole = open ? carry : segn_cat<TW>(I, carry, segn_node(I, de));
     if (lane == 0) {
-        SegN whole = open ? carry : segn_cat<TW>(I, carry, segn_node(I, de));
         st_seg8(&D.rterm[sr], whole.s, ds, whole.last);
         st_seg8(&D.rcore[sr], core.s, core.first, core.last);
         D.rhdr[sr] = make_int4(L, ds, de, nodes[L - 1]);
     }
+    write_links<TW>(I, D, s, r, nodes, L, ds, de, open, whole.s);
 }

@@ -73,7 +73,7 @@ static void free_sols(md_solutions *S) {
     md_moves_destroy(S->scratch);
     DevSols &d = S->d;
     cudaFree(d.rnodes); cudaFree(d.rhdr); cudaFree(d.rterm); cudaFree(d.rcore);
-    cudaFree(d.cpre); cudaFree(d.csuf); cudaFree(d.csubf); cudaFree(d.csubb);
+    cudaFree(d.cpre); cudaFree(d.csuf); cudaFree(d.csubf); cudaFree(d.csubb); cudaFree(d.clink);
     cudaFree(d.dcount); cudaFree(d.tot);
     cudaFree(d.lam); cudaFree(d.w); cudaFree(d.ops); cudaFree(d.state); cudaFree(d.stats);
     cudaFree(d.err); cudaFree(S->perm_dev);
@@ -112,18 +112,19 @@ extern "C" md_status md_solutions_create(const md_instance *inst, int32_t n_sol,
     MDA(cudaMalloc(&d.csuf, sizeof(Seg8) * (size_t)n_sol * nc));
     MDA(cudaMalloc(&d.csubf, sizeof(Seg8) * (size_t)n_sol * nc * k_max));
     MDA(cudaMalloc(&d.csubb, sizeof(Seg8) * (size_t)n_sol * nc * k_max));
+    MDA(cudaMalloc(&d.clink, sizeof(int4) * MD_LINK * (size_t)n_sol * nc));
     MDA(cudaMalloc(&d.dcount, sizeof(int32_t) * (size_t)n_sol * nd));
     MDA(cudaMalloc(&d.tot, sizeof(long long) * (size_t)n_sol * 8));
     MDA(cudaMalloc(&d.lam, sizeof(float) * (size_t)n_sol * 4));
     MDA(cudaMalloc(&d.w, sizeof(double) * (size_t)n_sol * 4));
     MDA(cudaMalloc(&d.ops, sizeof(int32_t) * n_sol));
     MDA(cudaMalloc(&d.state, sizeof(int32_t) * (size_t)n_sol * MD_STATE));
-    MDA(cudaMalloc(&d.stats, sizeof(long long) * (size_t)n_sol * 16));
+    MDA(cudaMalloc(&d.stats, sizeof(long long) * (size_t)n_sol * MD_STATS));
     MDA(cudaMalloc(&d.err, sizeof(int32_t)));
     MDA(cudaMemset(d.rhdr, 0, sizeof(int4) * SR));
     MDA(cudaMemset(d.ops, 0xff, sizeof(int32_t) * n_sol));
     MDA(cudaMemset(d.state, 0, sizeof(int32_t) * (size_t)n_sol * MD_STATE));
-    MDA(cudaMemset(d.stats, 0, sizeof(long long) * (size_t)n_sol * 16));
+    MDA(cudaMemset(d.stats, 0, sizeof(long long) * (size_t)n_sol * MD_STATS));
     MDA(cudaMemset(d.err, 0, sizeof(int32_t)));
     MDA(cudaMemset(d.tot, 0, sizeof(long long) * (size_t)n_sol * 8));
 #undef MDA
@@ -300,10 +301,10 @@ extern "C" md_status md_solutions_read_summaries(md_solutions *S, int32_t *pre, 
 extern "C" md_status md_solutions_stats(md_solutions *S, int64_t *per_sol, void *stream) {
     if (!S || !per_sol) { md_set_error("md_solutions_stats: null argument"); return MD_ERR_ARG; }
     cudaStream_t st = (cudaStream_t)stream;
-    std::vector<long long> h((size_t)S->n_sol * 16);
-    MD_CUDA(cudaMemcpyAsync(h.data(), S->d.stats, sizeof(long long) * 16 * S->n_sol, cudaMemcpyDeviceToHost, st));
+    std::vector<long long> h((size_t)S->n_sol * MD_STATS);
+    MD_CUDA(cudaMemcpyAsync(h.data(), S->d.stats, sizeof(long long) * MD_STATS * S->n_sol, cudaMemcpyDeviceToHost, st));
     MD_CUDA(cudaStreamSynchronize(st));
     for (int s = 0; s < S->n_sol; s++)
-        for (int k = 0; k < 5; k++) per_sol[(size_t)s * 5 + k] = h[(size_t)s * 16 + k];
+        for (int k = 0; k < 5; k++) per_sol[(size_t)s * 5 + k] = h[(size_t)s * MD_STATS + k];
     return MD_OK;
 }

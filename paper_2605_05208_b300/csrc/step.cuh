@@ -311,6 +311,22 @@ __device__ void apply_one(const DevInst &I, const DevSols &D, int s, int op, uin
     }
 }
 
+// Free route slots in slot order, as many as there are moves: the slots Depot-Insert moves of
+// rank 0, 1, ... take.  Called by one warp; returns the count on every lane.
+__device__ __forceinline__ int free_slots_in_order(const DevSols &D, int s, int need, int *out) {
+    const int lane = threadIdx.x & 31, R = D.R;
+    int nfree = 0;
+    for (int base = 0; base < R && nfree < need; base += 32) {
+        const int r = base + lane;
+        const bool fr = r < R && D.rhdr[(size_t)s * R + r].x == 0;
+        const unsigned m = __ballot_sync(0xffffffffu, fr);
+        const int pos = nfree + __popc(m & ((1u << lane) - 1u));
+        if (fr && pos < R) out[pos] = r;
+        nfree += __popc(m);
+    }
+    return nfree;
+}
+
 // Applies the selection of solution s and rebuilds its touched routes and totals.
 template <bool TW>
 __device__ void apply_selection(const DevInst &I, const DevSols &D, const DevMoves &M, int s, int nsel,
@@ -322,17 +338,8 @@ __device__ void apply_selection(const DevInst &I, const DevSols &D, const DevMov
     if (tid == 0) { s_nfree = 0; s_ntouch = 0; }
     __syncthreads();
     if (op == MD_OP_DEPOT_INSERT && warp == 0) {
-        // free slots in slot order, as many as there are moves
-        for (int base = 0; base < R && s_nfree < nsel; base += 32) {
-            const int r = base + lane;
-            const bool fr = r < R && D.rhdr[(size_t)s * R + r].x == 0;
-            const unsigned m = __ballot_sync(0xffffffffu, fr);
-            const int pos = s_nfree + __popc(m & ((1u << lane) - 1u));
-            if (fr && pos < R) sm.free_slots[pos] = r;
-            __syncwarp();
-            if (lane == 0) s_nfree += __popc(m);
-            __syncwarp();
-        }
+        const int nf = free_slots_in_order(D, s, nsel, sm.free_slots);
+        if (lane == 0) s_nfree = nf;
     }
     __syncthreads();
     for (int k = warp; k < nsel; k += nwarps) {
@@ -365,69 +372,150 @@ __device__ void update_lambda(const DevInst &I, const DevSols &D, int s) {
     __syncthreads();
 }
 
+// Bookkeeping of one descent step of solution s, kept by thread 0: the state, the counters, the
+// scored count and the operator of the next slot, loaded before the selection (so that the loads
+// overlap it) and stored after the apply.
+struct StepBook {
+    int pass, slot, improved, period, step, verify, op, nxt;
+    long long c_sc, c_steps, c_acc, c_app, c_pass, c_op, nsc, c_ex, c_exop, nex;
+};
+
+__device__ __forceinline__ void book_load(const DevSols &D, const DevMoves &M, int s, StepBook &b) {
+    const int *st = D.state + (size_t)s * MD_STATE;
+    const long long *stt = D.stats + (size_t)s * MD_STATS;
+    const int n_ops = st[4], max_pass = st[5];
+    b.pass = st[0]; b.slot = st[1] + 1; b.improved = st[2];
+    b.period = st[8]; b.step = st[9]; b.verify = st[10];
+    b.op = D.ops[s] & MD_OP_MASK;
+    b.c_sc = stt[0]; b.c_steps = stt[1]; b.c_acc = stt[2]; b.c_app = stt[3]; b.c_pass = stt[4];
+    b.c_op = stt[8 + b.op];
+    b.nsc = (long long)M.nscored[s];
+    b.c_ex = stt[5];
+    b.c_exop = stt[16 + b.op];
+    b.nex = M.nexact ? (long long)M.nexact[s] : 0;
+    b.nxt = -1;
+    if (b.slot < n_ops) b.nxt = D.perm[((size_t)s * max_pass + b.pass) * n_ops + b.slot];
+    else if (b.pass + 1 < max_pass) b.nxt = D.perm[((size_t)s * max_pass + b.pass + 1) * n_ops];
+}
+
+// Counters, (pass, slot), the stopping rule of Alg. 2 and the next operator, after a step that
+// applied nsel moves.
+__device__ __forceinline__ void book_store(const DevSols &D, const DevMoves &M, int s, StepBook &b, int nsel) {
+    int *st = D.state + (size_t)s * MD_STATE;
+    long long *stt = D.stats + (size_t)s * MD_STATS;
+    const int n_ops = st[4], max_pass = st[5];
+    stt[0] = b.c_sc + b.nsc;
+    stt[8 + b.op] = b.c_op + b.nsc;
+    M.nscored[s] = 0;
+    stt[5] = b.c_ex + b.nex;
+    stt[16 + b.op] = b.c_exop + b.nex;
+    if (M.nexact) M.nexact[s] = 0;
+    stt[1] = b.c_steps + 1;
+    int improved = b.improved, verify = b.verify, pass = b.pass, slot = b.slot;
+    if (nsel > 0) { stt[2] = b.c_acc + 1; stt[3] = b.c_app + nsel; improved = 1; verify = 0; }
+    int done = 0;
+    if (slot == n_ops) {
+        stt[4] = b.c_pass + 1;
+        pass += 1;
+        slot = 0;
+        // with pruned lists (sweep period > 0) a pass that applied nothing is followed by a
+        // verification pass whose steps evaluate the full neighbourhood until one applies a
+        // move; the descent ends when a whole verification pass applies nothing
+        if (!improved) {
+            if (b.period > 0 && !verify) verify = 1;
+            else done = 1;
+        }
+        if (pass >= max_pass) done = 1;
+        improved = 0;
+    }
+    st[0] = pass;
+    st[1] = slot;
+    st[2] = improved;
+    st[3] = done;
+    st[10] = verify;
+    // full plain sweep on every period-th step (st[8], st[9] = steps done) and on the steps of a
+    // verification pass
+    const int step = b.step + 1;
+    st[9] = step;
+    const bool sweep = (b.period > 0 && (step + 1) % b.period == 0) || verify;
+    D.ops[s] = done ? -1 : (b.nxt | (sweep ? MD_OP_SWEEP : 0));
+}
+
 // One step of the descent for every solution still running: select, apply, rebuild, update
 // counters and lambda, then advance (pass, slot) and set the next operator.
 template <bool TW>
 __device__ void step_body(const DevInst &I, const DevSols &D, const DevMoves &M, int s, int nrec) {
     extern __shared__ __align__(16) unsigned char smem[];
     const StepSmem sm = carve(smem, D.R, I.nd, D.K, blockDim.x >> 5);
-    int *st = D.state + (size_t)s * MD_STATE;
+    const int *st = D.state + (size_t)s * MD_STATE;
     if (st[3]) return;
-    const int n_ops = st[4], max_pass = st[5], multi = st[6], lup = st[7];
-    // thread 0 loads the step's bookkeeping now, so that its loads overlap the selection: the
-    // state, the counters, the scored count and the operator of the next slot
-    long long *stt = D.stats + (size_t)s * 16;
-    int pass = 0, slot = 0, improved = 0, period = 0, step = 0, verify = 0, op = 0, nxt = -1;
-    long long c_sc = 0, c_steps = 0, c_acc = 0, c_app = 0, c_pass = 0, c_op = 0, nsc = 0;
-    if (threadIdx.x == 0) {
-        pass = st[0]; slot = st[1] + 1; improved = st[2];
-        period = st[8]; step = st[9]; verify = st[10];
-        op = D.ops[s] & MD_OP_MASK;
-        c_sc = stt[0]; c_steps = stt[1]; c_acc = stt[2]; c_app = stt[3]; c_pass = stt[4];
-        c_op = stt[8 + op];
-        nsc = (long long)M.nscored[s];
-        if (slot < n_ops) nxt = D.perm[((size_t)s * max_pass + pass) * n_ops + slot];
-        else if (pass + 1 < max_pass) nxt = D.perm[((size_t)s * max_pass + pass + 1) * n_ops];
-    }
+    const int multi = st[6], lup = st[7];
+    StepBook bk;
+    if (threadIdx.x == 0) book_load(D, M, s, bk);
     const int nsel = select_moves(I, D, M, s, multi, sm, nrec);
     if (nsel > 0) {
         apply_selection<TW>(I, D, M, s, nsel, sm);
         if (lup) update_lambda(I, D, s);
     }
-    if (threadIdx.x == 0) {
-        stt[0] = c_sc + nsc;
-        stt[8 + op] = c_op + nsc;
-        M.nscored[s] = 0;
-        stt[1] = c_steps + 1;
-        if (nsel > 0) { stt[2] = c_acc + 1; stt[3] = c_app + nsel; improved = 1; verify = 0; }
-        int done = 0;
-        if (slot == n_ops) {
-            stt[4] = c_pass + 1;
-            pass += 1;
-            slot = 0;
-            // with pruned lists (sweep period > 0) a pass that applied nothing is followed by a
-            // verification pass whose steps evaluate the full neighbourhood until one applies a
-            // move; the descent ends when a whole verification pass applies nothing
-            if (!improved) {
-                if (period > 0 && !verify) verify = 1;
-                else done = 1;
-            }
-            if (pass >= max_pass) done = 1;
-            improved = 0;
+    if (threadIdx.x == 0) book_store(D, M, s, bk, nsel);
+}
+
+// ------------------------------------------------------------------------------------------
+// The same step spread over the grid, for solutions with many route slots: one CTA per solution
+// selects (wide_select), one warp per selected move applies it (wide_apply), one warp per
+// touched route rebuilds it (wide_rebuild), one CTA per solution takes the totals, lambda and
+// the bookkeeping (wide_finish).  The selected moves touch disjoint routes, so they apply in
+// any order; the result is the single-CTA step's.
+// ------------------------------------------------------------------------------------------
+
+__device__ void wide_select(const DevInst &I, const DevSols &D, const DevMoves &M, int s) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const StepSmem sm = carve(smem, D.R, I.nd, D.K, blockDim.x >> 5);
+    const int *st = D.state + (size_t)s * MD_STATE;
+    if (st[3]) {
+        if (threadIdx.x == 0) M.nsel[s] = 0;
+        return;
+    }
+    const int nsel = select_moves(I, D, M, s, st[6], sm, M.nblk);
+    if (threadIdx.x < 32) {
+        int nfree = 0;
+        if (nsel > 0 && (D.ops[s] & MD_OP_MASK) == MD_OP_DEPOT_INSERT)
+            nfree = free_slots_in_order(D, s, nsel, M.wfree + (size_t)s * D.R);
+        if (threadIdx.x == 0) {
+            M.wcnt[2 * s] = nfree;
+            M.wcnt[2 * s + 1] = 0;
         }
-        st[0] = pass;
-        st[1] = slot;
-        st[2] = improved;
-        st[3] = done;
-        st[10] = verify;
-        // full plain sweep on every period-th step (st[8], st[9] = steps done) and on the steps
-        // of a verification pass
-        st[9] = ++step;
-        const bool sweep = (period > 0 && (step + 1) % period == 0) || verify;
-        D.ops[s] = done ? -1 : (nxt | (sweep ? MD_OP_SWEEP : 0));
     }
 }
 
+// Selected move k of solution s, by one warp; stage: 2K ints of shared memory for the warp.
+__device__ void wide_apply(const DevInst &I, const DevSols &D, const DevMoves &M, int s, int k, int *stage) {
+    if (k >= M.nsel[s]) return;
+    const int op = D.ops[s] & MD_OP_MASK;
+    const uint32_t *sel = M.sel + (size_t)s * D.R;
+    const uint32_t id = sel[k];
+    int rank = 0;
+    if (op == MD_OP_DEPOT_INSERT)
+        for (int q = 0; q < M.nsel[s]; q++) rank += sel[q] < id;  // deterministic slot choice
+    StepSmem g = {};
+    g.free_slots = M.wfree + (size_t)s * D.R;
+    g.touched = M.wtouch + (size_t)s * D.R;
+    apply_one(I, D, s, op, id, rank, g, M.wcnt[2 * s], &M.wcnt[2 * s + 1], stage);
+}
+
+template <bool TW>
+__device__ void wide_finish(const DevInst &I, const DevSols &D, const DevMoves &M, int s, int *cnt_sm) {
+    const int *st = D.state + (size_t)s * MD_STATE;
+    if (st[3]) return;
+    StepBook bk;
+    if (threadIdx.x == 0) book_load(D, M, s, bk);
+    const int nsel = M.nsel[s];
+    if (nsel > 0) {
+        solution_totals(I, D, s, cnt_sm, false);
+        if (st[7]) update_lambda(I, D, s);
+    }
+    if (threadIdx.x == 0) book_store(D, M, s, bk, nsel);
+}
 
 // Dynamic shared memory of one step CTA (route claims, free slots, touched routes, depot
 // counts, per-warp staging of two routes).

@@ -75,13 +75,14 @@ class Config(C.Structure):
                 ("lambda0", C.POINTER(C.c_float)), ("multi_move", C.c_int32),
                 ("lambda_update", C.c_int32), ("use_graph", C.c_int32), ("poll_every", C.c_int32),
                 ("op_perm_device", C.c_int32), ("time_eval", C.c_int32), ("n_groups", C.c_int32),
-                ("sweep_every", C.c_int32), ("persistent", C.c_int32)]
+                ("sweep_every", C.c_int32), ("persistent", C.c_int32), ("wide_step", C.c_int32)]
 
 
 class Stats(C.Structure):
     _fields_ = [("moves_scored", C.c_int64), ("steps", C.c_int64), ("accepted_steps", C.c_int64),
                 ("applied_moves", C.c_int64), ("passes_max", C.c_int64), ("launches", C.c_int64),
-                ("eval_launches", C.c_int64), ("eval_ms", C.c_double), ("moves_by_op", C.c_int64 * 6)]
+                ("eval_launches", C.c_int64), ("eval_ms", C.c_double), ("moves_by_op", C.c_int64 * 6),
+                ("moves_exact", C.c_int64), ("moves_exact_by_op", C.c_int64 * 6)]
 
 
 _lib = None
@@ -247,6 +248,8 @@ class DescendStats:
     eval_launches: int
     eval_ms: float
     moves_by_op: tuple
+    moves_exact: int = 0
+    moves_exact_by_op: tuple = ()
 
 
 class Solutions:
@@ -340,10 +343,12 @@ class Solutions:
     def descend(self, perm, max_pass: int, multi: bool = True, lambda_update: bool = False,
                 lambda0=None, use_graph: bool = False, poll_every: int = 1, stream=None,
                 n_ops: int | None = None, time_eval: bool = False, n_groups: int = 1,
-                sweep_every: int = 0, persistent: bool = False) -> DescendStats:
+                sweep_every: int = 0, persistent: bool = False, wide_step: int = 0) -> DescendStats:
         """MDFIS descent.  perm: uint8 host array [n_sol, >= max_pass, n_ops], or an int device
         pointer to a [n_sol, max_pass, n_ops] uint8 buffer (then n_ops must be given).
-        persistent: the whole descent in one persistent launch."""
+        persistent: the whole descent in one persistent launch.  wide_step: md_config.wide_step
+        (1: each step's apply and rebuild spread over the grid, -1: one CTA per solution, 0: by
+        the number of route slots)."""
         if isinstance(perm, int):
             assert n_ops is not None
             pptr, on_dev = C.cast(C.c_void_p(perm), C.POINTER(C.c_uint8)), 1
@@ -357,12 +362,12 @@ class Solutions:
         cfg = Config(n_ops, max_pass, pptr,
                      lam.ctypes.data_as(C.POINTER(C.c_float)) if lam is not None else None,
                      int(multi), int(lambda_update), int(use_graph), int(poll_every), on_dev,
-                     int(time_eval), int(n_groups), int(sweep_every), int(persistent))
+                     int(time_eval), int(n_groups), int(sweep_every), int(persistent), int(wide_step))
         st = Stats()
         _check(lib().md_descend(self.h, C.byref(cfg), C.byref(st), _stream(stream)))
         return DescendStats(st.moves_scored, st.steps, st.accepted_steps, st.applied_moves,
                             st.passes_max, st.launches, st.eval_launches, st.eval_ms,
-                            tuple(st.moves_by_op))
+                            tuple(st.moves_by_op), st.moves_exact, tuple(st.moves_exact_by_op))
 
 
 class Moves:
@@ -489,7 +494,7 @@ class Batch:
         _check(lib().md_batch_descend(self.h, C.byref(cfg), C.byref(st), _stream(stream)))
         return DescendStats(st.moves_scored, st.steps, st.accepted_steps, st.applied_moves,
                             st.passes_max, st.launches, st.eval_launches, st.eval_ms,
-                            tuple(st.moves_by_op))
+                            tuple(st.moves_by_op), st.moves_exact, tuple(st.moves_exact_by_op))
 
 
 class Pruner:

@@ -176,6 +176,17 @@ def test_eval_every_move_matches_oracle(md, oracle_lib, case):
             else:
                 assert ids[s] == 0
         M.close()
+        # without the dump, full neighbourhoods take the exact lower-bound rejection: the same
+        # leaders, scored counts and selected moves (leader and followers)
+        M2 = md.Moves(S)
+        M2.evaluate(np.full(len(sols), op, np.int32), lamv, flags=md.EVAL_FOLLOWERS)
+        ids2, f2, n2 = M2.leaders()
+        assert np.array_equal(ids2, ids) and np.array_equal(f2, f) and np.array_equal(n2, n), op
+        M2.select(multi=True)
+        sel = M2.selection()
+        for s, (mv, _) in enumerate(want):
+            assert sorted(sel[s]) == sorted(o.select(mv, len(sols[s]), multi=True)), (op, s)
+        M2.close()
 
 
 # ------------------------------------------------------------------------------------------
@@ -521,3 +532,57 @@ def test_two_opt_is_empty_with_time_windows_or_asymmetric_costs(md, oracle_lib):
         assert len(M.dump(64)) == 0 and list(n) == [0, 0] and list(ids) == [0, 0]
         assert all(len(o.eval_op(sol, W.OP_TWO_OPT)[0]) == 0 for sol in sols)
         M.close()
+
+
+@pytest.mark.parametrize("case", ["mdvrptw-6x288-theta50", "tiny-mixed-tw-lambda", "mdovrp-4x600-full",
+                                  "lists-sweep-groups", "mdvrp-2opt-single"])
+def test_wide_step_matches_single_cta_step_and_oracle(md, oracle_lib, stream, case):
+    # the step spread over the grid (selection, one warp per applied move, one warp per rebuilt
+    # route, totals and bookkeeping: four launches) gives the single-CTA step's descent, which
+    # is the oracle's
+    kw = dict(multi=True, lambda_update=False, sweep_every=0, n_groups=1)
+    nbr, ops = None, tuple(range(W.N_OPS))
+    if case == "mdvrptw-6x288-theta50":
+        spec, nsol, max_pass = W.mdvrptw_6x288(81), 6, 500
+    elif case == "tiny-mixed-tw-lambda":
+        spec, nsol, max_pass = tiny_spec(82, nd=3, nc=40, tw=True, Q=30, NV=2, D=250, horizon=1500,
+                                         wmin=60, wmax=500), 4, 60
+        kw["lambda_update"] = True
+    elif case == "mdovrp-4x600-full":
+        spec, nsol, max_pass = W.gen_mdovrp(83, n_depots=4, n_customers=600), 2, 6
+    elif case == "lists-sweep-groups":
+        spec, nsol, max_pass = W.gen_mdvrptw(84, n_depots=3, n_customers=300, theta=10), 4, 60
+        nbr, cnt = random_neighbor_lists(spec, 10, 9)
+        kw.update(sweep_every=4, n_groups=2)
+    else:
+        spec = W.gen_mdvrp(85, n_depots=3, n_customers=120, Q=60, N_V=3, theta=20)
+        nsol, max_pass = 3, 60
+        ops = tuple(range(W.N_OPS_ALL))
+        kw["multi"] = False
+    if case.startswith("tiny"):
+        sols = [random_solution(spec, 400 + i, max_len=6) for i in range(nsol)]
+    else:
+        sols = W.initial_solutions(spec, 86, nsol)
+    perm = W.op_permutations(87, nsol, max_pass, op_list=ops)
+    runs = []
+    for wide in (-1, 1):
+        big = spec.n_customers > 200
+        inst, S = setup(md, spec, sols, R=min(spec.n_customers + 1, 2 * max(len(x) for x in sols) + 64) if big else None,
+                        K=min(spec.n_customers, 2 * max(len(r) - 2 for x in sols for r in x) + 32) if big else None)
+        if nbr is not None:
+            inst.set_neighbors(nbr, cnt)
+        st = S.descend(perm, max_pass, use_graph=True, stream=stream, wide_step=wide, **kw)
+        runs.append((canon_all(spec, S.read()), S.stats(), S.lam(), st, S.cost()))
+    assert runs[0][0] == runs[1][0]
+    assert np.array_equal(runs[0][1], runs[1][1]) and np.array_equal(runs[0][2], runs[1][2])
+    assert np.array_equal(runs[0][4][0], runs[1][4][0])
+    assert runs[1][3].applied_moves == runs[0][3].applied_moves > 0
+    assert runs[1][3].launches > runs[0][3].launches  # four launches per step instead of one
+    o = oracle_lib.Instance(spec)
+    if nbr is not None:
+        o.set_neighbors(nbr, cnt)
+    for s in range(min(nsol, 2)):
+        d = o.descend(sols[s], perm[s], max_pass, multi=kw["multi"], lambda_update=kw["lambda_update"],
+                      sweep_every=kw["sweep_every"])
+        assert runs[1][0][s] == canon(spec, d.solution), s
+        assert list(runs[1][1][s]) == [d.moves_scored, d.steps, d.accepted_steps, d.applied_moves, d.passes], s

@@ -893,3 +893,37 @@ def test_repair_without_feasible_insertions_opens_routes_at_nearest_free_depot(o
         d = min(free, key=lambda x: (int(c[x, u] + c[u, x]), x))
         assert r == [d, u, d]
         cnt[d] += 1
+
+
+# ------------------------------------------------------------------------------------------
+# Insertion lemma behind the evaluation's exact lower-bound rejection on full neighbourhoods:
+# inserting a sequence Q between consecutive nodes v and w of a route, with a detour
+# c(v, q_first) + (dur_Q - tw_Q) + c(q_last, w) - c(v, w) >= 0, lowers neither the route's time
+# warp nor its duration nor its load (time-warp concatenation of Appendix A1)
+# ------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("seed", range(6))
+def test_insertion_with_nonnegative_detour_never_lowers_warp_or_duration(oracle_lib, seed):
+    spec = tiny_spec(300 + seed, nd=2, nc=12, tw=True, horizon=400, wmin=10, wmax=120, D=0)
+    I = oracle_lib.Instance(spec)
+    c = I.dist()
+    st = W.Stream(seed, 5)
+    nd, nc = spec.n_depots, spec.n_customers
+    checked = 0
+    for trial in range(400):
+        perm = [int(x) for x in np.argsort(st.u64(nc))] 
+        k = int(st.randint(1, 6, 1)[0])
+        q = int(st.randint(1, 2, 1)[0])
+        route = [0] + [nd + x for x in perm[:k]] + [int(st.randint(0, nd - 1, 1)[0])]
+        Q = [nd + x for x in perm[k:k + q]]
+        pos = int(st.randint(0, k, 1)[0])  # Q goes between route[pos] and route[pos + 1]
+        a, b = route[pos], route[pos + 1]
+        tq = I.route_terms(Q)
+        det = c[a, Q[0]] + (tq["dur"] - tq["tw"]) + c[Q[-1], b] - c[a, b]
+        if det < 0:
+            continue
+        old = I.route_terms(route)
+        new = I.route_terms(route[:pos + 1] + Q + route[pos + 1:])
+        assert new["tw"] >= old["tw"] and new["dur"] >= old["dur"] and new["load"] >= old["load"], (route, Q, pos)
+        checked += 1
+    assert checked > 200
