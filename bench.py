@@ -1,15 +1,19 @@
 #!/usr/bin/env python3
-"""Benchmark of the MDFIS local-search hot path on B300: moves evaluated/s and LS descents/s.
+"""Benchmark of the MDFIS local-search hot path on B300: moves evaluated/s and LS descents/s,
+learned-pruned against plain.
 
-One step = one complete MDFIS descent (Alg. 2: relocate, swap, 2-opt*, Depot-Insert and
-Depot-Replace in a seeded random order per pass, leader-follower multi-move update, until a pass
-applies nothing or delta = 500 passes) of 32 seeded solutions of a synthetic MDVRPTW instance with
-6 depots and 288 customers (theta = 50 granular neighbours, the paper's setting).  The instance and
-the initial solutions are resident in HBM before the timed region; every step restores the initial
-routes on the device, rebuilds all summaries and descends.
+Default workload (learned-20x10000): one step descends 8 seeded solutions per rank of a 20-depot,
+10000-customer MDVRPTW instance to a local optimum of the full neighbourhood (Alg. 2 with the
+leader-follower multi-move update, delta = 500), on the learned top-64 candidate lists with a full
+sweep every 20 steps; the steps cycle through the instances of seeds 1..5.  The same solutions'
+plain full-neighbourhood descents and the static eta top-64 descents are timed beside them.
+Other workloads (--workload): the descent workloads mdvrp-4x50, mdvrptw-6x288, mdovrp-12x4000 and
+mdvrp-6x288-2opt, the batched uneven instances, repair insertion, plain 20x10000 descents and the
+memetic loop.
 
-Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-Under torchrun every rank descends its own 32 solutions (weak scaling); rank 0 prints one JSON line.
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload W]
+Under torchrun the ranks share each instance and split its solutions (weak scaling); rank 0 prints
+one JSON line.
 """
 from __future__ import annotations
 
@@ -40,41 +44,70 @@ THETA = 50
 # second route for 2-opt* and the depot operators); u-independent summaries are amortised.
 ALG_BYTES = {W.OP_RELOCATE: 8, W.OP_SWAP: 16, W.OP_TWO_OPT_STAR: 56, W.OP_DEPOT_INSERT: 32,
              W.OP_DEPOT_REPLACE: 32, W.OP_TWO_OPT: 8}
-# DRAM bytes (read + write) per launch of the dominant kernel of the default workload, from ncu
-# (dram__bytes_read.sum + dram__bytes_write.sum) on `python bench.py --steps 1 --warmup 3
-# --no-cpu-baseline`: the persistent descent kernel (one launch per descent) and, for
-# --persistent 0, the evaluation kernel.  They describe the kernels as committed with them; a
-# change to a kernel makes its figure stale (None: not measured for the current kernel).
-TRAFFIC_6X288 = {"persistent": 6182554, "eval": None}
+# DRAM bytes (read + write) per launch of the dominant kernel of a workload, keyed by (workload,
+# persistent launch), from ncu (dram__bytes_read.sum + dram__bytes_write.sum) on the commands
+# recorded under profiles/.  They describe the kernels as committed with them; a change to a kernel
+# makes its figure stale, and a workload without a current capture has none.
+TRAFFIC = {}
+# L2 bandwidth of this machine's B300, GB/s (read + write bytes), measured with an own copy kernel on
+# an L2-resident 32 MB buffer; the roofline of the workloads whose working set fits in L2.
+L2_PEAK_GBS = 13583.1
 CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
 
-def workload_spec(rank: int = 0, workload: str = "mdvrptw-6x288"):
+# The descent workloads: instance generator, solutions per rank, operators, passes per step
+# (500 = to the local optimum, delta of Table 1), launch form.
+DESCENT_WORKLOADS = {
+    "mdvrptw-6x288": dict(n_sol=N_SOL, ops=W.N_OPS, max_pass=MAX_PASS, persistent=True,
+                          desc=f"mdvrptw-6x288 (6 depots, 288 customers, horizon 1000, Q=200, N_V=6, D=1000), "
+                               f"theta={THETA}"),
+    "mdvrp-6x288-2opt": dict(n_sol=N_SOL, ops=W.N_OPS_ALL, max_pass=MAX_PASS, persistent=True,
+                             desc=f"mdvrp-6x288-2opt (6 depots, 288 customers on [0,100]^2, Q=200, N_V=6, no "
+                                  f"windows, symmetric), theta={THETA}, Relocate, Swap, 2-opt*, Depot-Insert, "
+                                  f"Depot-Replace and 2-opt"),
+    "mdvrp-4x50": dict(n_sol=8, ops=W.N_OPS, max_pass=MAX_PASS, persistent=True,
+                       desc="mdvrp-4x50 (4 depots, 50 customers on [0,100]^2, Q=80, N_V=4, no windows, no "
+                            "duration limit), full neighbourhood"),
+    "mdovrp-12x4000": dict(n_sol=64, ops=W.N_OPS, max_pass=5, persistent=False,
+                           desc="mdovrp-12x4000 (12 depots, 4000 customers from a 40-centre Gaussian mixture on "
+                                "[0,1000]^2, open routes, Q=150, N_V=40), full neighbourhood (every customer a "
+                                "candidate)"),
+}
+
+
+def workload_instance(workload: str):
     if workload == "mdvrp-6x288-2opt":
         # a symmetric instance without windows, where the intra-route 2-opt has moves: the MDVRP
         # generator at the size of the MDVRPTW workload, the six operators in every pass
-        spec = W.gen_mdvrp(SEED + rank, n_depots=6, n_customers=288, Q=200, N_V=6, theta=THETA,
-                           name="mdvrp-6x288")
-        ops = tuple(range(W.N_OPS_ALL))
-    else:
-        spec = W.mdvrptw_6x288(SEED + rank, theta=THETA)
-        ops = tuple(range(W.N_OPS))
-    sols = W.initial_solutions(spec, SEED + rank, N_SOL)
-    perm = W.op_permutations(SEED + rank, N_SOL, MAX_PASS, op_list=ops)
-    return spec, sols, perm
+        return W.gen_mdvrp(SEED, n_depots=6, n_customers=288, Q=200, N_V=6, theta=THETA, name="mdvrp-6x288")
+    if workload == "mdvrp-4x50":
+        return W.mdvrp_4x50(SEED)
+    if workload == "mdovrp-12x4000":
+        return W.mdovrp_12x4000(SEED)
+    return W.mdvrptw_6x288(SEED, theta=THETA)
 
 
-def workload_name(workload: str = "mdvrptw-6x288") -> str:
-    if workload == "mdvrp-6x288-2opt":
-        return (f"mdvrp-6x288-2opt (6 depots, 288 customers on [0,100]^2, Q=200, N_V=6, no windows, "
-                f"symmetric), theta={THETA}, {N_SOL} solutions, Relocate, Swap, 2-opt*, Depot-Insert, "
-                f"Depot-Replace and 2-opt, full descent to local optimum (delta={MAX_PASS}), multi-move, "
-                f"lambda=(1,1,1,1)")
-    return (f"mdvrptw-6x288 (6 depots, 288 customers, horizon 1000, Q=200, N_V=6, D=1000), "
-            f"theta={THETA}, {N_SOL} solutions, full descent to local optimum (delta={MAX_PASS}), "
-            f"multi-move, lambda=(1,1,1,1)")
+def workload_spec(rank: int = 0, workload: str = "mdvrptw-6x288", world: int = 1):
+    """The workload's instance (the same on every rank) and this rank's share of its seeded
+    initial solutions and operator orders: every rank descends n_sol of the world * n_sol
+    solutions (weak scaling)."""
+    from paper_2605_05208_b300 import shard
+    wl = DESCENT_WORKLOADS[workload]
+    spec = workload_instance(workload)
+    a, b = shard.share(wl["n_sol"] * world, rank, world)
+    sols = [W.initial_solution(spec, SEED, i) for i in range(a, b)]
+    perm = W.op_permutations(SEED, b, wl["max_pass"], op_list=tuple(range(wl["ops"])))[a:]
+    return spec, sols, np.ascontiguousarray(perm)
+
+
+def workload_name(workload: str = "mdvrptw-6x288", world: int = 1) -> str:
+    wl = DESCENT_WORKLOADS[workload]
+    depth = ("full descent to local optimum (delta=500)" if wl["max_pass"] == MAX_PASS
+             else f"{wl['max_pass']} passes from the initial solutions")
+    return (f"{wl['desc']}, {wl['n_sol'] * world} solutions ({wl['n_sol']} per rank), {depth}, multi-move, "
+            f"lambda=(1,1,1,1)")
 
 
 # ------------------------------------------------------------------------------------------
@@ -85,24 +118,41 @@ _ORACLE_CACHE = {}
 
 
 def _oracle_descend(args):
+    """One oracle descent of solution idx of the workload (rank 0's share), or, for the
+    12 x 4000 workload, one evaluation of every move of an operator on theta = 128 lists of one
+    solution (a bounded sample: the full neighbourhood of one step is 4e7 moves)."""
     rank, idx, workload = args
     from oracle import oracle as O
-    if (rank, workload) not in _ORACLE_CACHE:
+    key = (rank, workload)
+    if key not in _ORACLE_CACHE:
         spec, sols, perm = workload_spec(rank, workload)
-        _ORACLE_CACHE[(rank, workload)] = (O.Instance(spec), sols, perm)
-    inst, sols, perm = _ORACLE_CACHE[(rank, workload)]
+        if workload == "mdovrp-12x4000":
+            spec = W.gen_mdovrp(SEED, theta=128)
+        _ORACLE_CACHE[key] = (O.Instance(spec), sols, perm)
+    inst, sols, perm = _ORACLE_CACHE[key]
     t0 = time.perf_counter()
-    d = inst.descend(sols[idx], perm[idx], MAX_PASS, multi=True)
-    return d.moves_scored, time.perf_counter() - t0
+    if workload == "mdovrp-12x4000":
+        _, moves = inst.eval_op(sols[idx % len(sols)], (W.OP_RELOCATE, W.OP_SWAP, W.OP_TWO_OPT_STAR)[idx % 3])
+    else:
+        moves = inst.descend(sols[idx % len(sols)], perm[idx % len(sols)], perm.shape[1], multi=True).moves_scored
+    return int(moves), time.perf_counter() - t0
 
 
-def oracle_sample(pool, n: int, rank: int = 0, workload: str = "mdvrptw-6x288"):
+def oracle_sample(pool, n: int, rank: int = 0, workload: str = "mdvrptw-6x288", first: int = 0):
     t0 = time.perf_counter()
-    res = pool.map(_oracle_descend, [(rank, i % N_SOL, workload) for i in range(n)])
+    res = pool.map(_oracle_descend, [(rank, first + i, workload) for i in range(n)], chunksize=1)
     wall = time.perf_counter() - t0
     moves = sum(r[0] for r in res)
     cpu = sum(r[1] for r in res)
     return moves, wall, cpu
+
+
+def oracle_sample_desc(workload: str, n: int) -> str:
+    if workload == "mdovrp-12x4000":
+        return (f"{n} processes on {host_cpu()['model']}, each evaluating every Relocate, Swap or 2-opt* move "
+                f"of one initial solution on theta = 128 neighbour lists (a bounded sample of the full "
+                f"neighbourhood)")
+    return f"{n} processes on {host_cpu()['model']}, each one full oracle descent of one of the workload's solutions"
 
 
 def _pool_ready(_):
@@ -124,29 +174,29 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    cores = min(os.cpu_count() or 1, 16)
+    cores = os.cpu_count() or 1
     sample = cores
-    # the descent workloads; the others are timed against the default one's oracle
-    wl = args.workload if args.workload in ("mdvrptw-6x288", "mdvrp-6x288-2opt") else "mdvrptw-6x288"
+    # the descent workloads; the others are timed against the default descent workload's oracle
+    wl = args.workload if args.workload in DESCENT_WORKLOADS else "mdvrptw-6x288"
     pool = make_pool(cores)
-    for _ in range(args.warmup):
-        oracle_sample(pool, sample, workload=wl)
+    for k in range(args.warmup):
+        oracle_sample(pool, sample, workload=wl, first=k * sample)
     tot_moves, tot_wall, tot_cpu = 0, 0.0, 0.0
-    for _ in range(args.steps):
-        m, w, c = oracle_sample(pool, sample, workload=wl)
+    for k in range(args.steps):
+        m, w, c = oracle_sample(pool, sample, workload=wl, first=(args.warmup + k) * sample)
         tot_moves += m
         tot_wall += w
         tot_cpu += c
     pool.close()
     value = tot_moves / tot_wall
-    desc = (f"plain C oracle, {sample} of the {N_SOL} descents per step ({cores} processes), "
-            f"{tot_cpu / args.steps:.1f} s CPU per step")
+    desc = f"{oracle_sample_desc(wl, sample)} per step, {tot_cpu / args.steps:.1f} s CPU per step"
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_wall / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64/f64",
         "data": "synthetic", "config": {"workload": workload_name(wl), "sample": desc},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc,
+                         "host": host_cpu()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
@@ -156,8 +206,8 @@ def run_reference(args):
 # ------------------------------------------------------------------------------------------
 
 def combine_ranks(total_ms: float, moves: float, world: int, device) -> tuple[float, float]:
-    """The slowest rank's timed milliseconds and the moves scored by all ranks.  Every rank
-    descends its own seeded solutions (weak scaling), so nothing else crosses ranks."""
+    """The slowest rank's timed milliseconds and the moves scored by all ranks (each rank descends
+    its own share of the solutions)."""
     import torch
     import torch.distributed as dist
     t = torch.tensor([total_ms], dtype=torch.float64, device=device)
@@ -216,14 +266,29 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def load_peaks() -> dict:
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
 def run_ours(args):
+    """Descents of one of the descent workloads (DESCENT_WORKLOADS): one step descends every
+    rank's share of the solutions from their initial routes (to the local optimum, or for the
+    passes the workload names)."""
     import torch
     import torch.distributed as dist
-    from paper_2605_05208_b300 import build, mdls
+    from paper_2605_05208_b300 import build, mdls, shard
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    wl = DESCENT_WORKLOADS[args.workload]
+    # CPU baseline pool before the first GPU call (spawn), rank 0 only
+    pool = None
+    if rank == 0 and not args.no_cpu_baseline:
+        pool = make_pool(os.cpu_count() or 1)
     if world > 1:
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
@@ -233,29 +298,25 @@ def run_ours(args):
     torch.cuda.set_stream(stream)
     sptr = stream.cuda_stream
 
-    # CPU baseline pool before the first GPU call (spawn), rank 0 only
-    pool = None
-    if rank == 0 and not args.no_cpu_baseline:
-        ncores = min(os.cpu_count() or 1, 16)
-        pool = make_pool(ncores)
-
-    spec, sols, perm = workload_spec(rank, args.workload)
+    spec, sols, perm = workload_spec(rank, args.workload, world)
+    n_sol = len(sols)
+    max_pass = args.max_pass or wl["max_pass"]
     n_ops = perm.shape[2]
     inst = mdls.Instance(spec)
-    max_routes = max(len(s) for s in sols)
+    max_routes = max(len(x) for x in sols)
+    longest = max(len(r) - 2 for x in sols for r in x)
     R = min(spec.n_customers, max(64, 2 * max_routes, spec.n_depots * spec.N_V + 8))
-    K = min(spec.n_customers, 64)
-    init = mdls.Solutions(inst, N_SOL, R, K)
-    work = mdls.Solutions(inst, N_SOL, R, K)
+    K = min(spec.n_customers, max(64, 2 * longest))
+    init = mdls.Solutions(inst, n_sol, R, K)
+    work = mdls.Solutions(inst, n_sol, R, K)
     init.load(sols)
     perm_dev = torch.from_numpy(np.ascontiguousarray(perm)).to(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)  # > 126 MB L2
-
-    persistent = bool(args.persistent) if args.persistent >= 0 else True
+    persistent = bool(args.persistent) if args.persistent >= 0 else wl["persistent"]
 
     def step(time_eval=False):
         work.copy_from(init, stream=sptr)
-        return work.descend(perm_dev.data_ptr(), MAX_PASS, multi=True, use_graph=True, poll_every=1,
+        return work.descend(perm_dev.data_ptr(), max_pass, multi=True, use_graph=True, poll_every=1,
                             stream=sptr, n_ops=n_ops, time_eval=time_eval, n_groups=args.groups,
                             persistent=persistent)
 
@@ -282,7 +343,10 @@ def run_ours(args):
     moves = sum(s.moves_scored for s in stats)
     total_ms_max, moves_all = combine_ranks(total_ms, float(moves), world, dev)
     value = moves_all / (total_ms_max / 1e3)
-    descents = N_SOL * world * args.steps / (total_ms_max / 1e3)
+    descents = n_sol * world * args.steps / (total_ms_max / 1e3)
+    # every rank's per-solution costs, gathered; the global best (the only data collective)
+    comps, F = work.cost(stream=sptr)
+    comps_all, F_all, best = shard.run(n_sol * world, rank, world, lambda a_, b_: (comps, F))
 
     # dominant kernel, timed live with CUDA events: the persistent descent kernel (evaluation and
     # steps of all solutions, one launch per descent), else every evaluation launch
@@ -291,13 +355,14 @@ def run_ours(args):
     by_op = np.sum([s.moves_by_op for s in stats], axis=0)
     alg_bytes = float(sum(int(by_op[o]) * ALG_BYTES[o] for o in range(W.N_OPS_ALL)))
     achieved = alg_bytes / (eval_ms / 1e3) / 1e9
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except (OSError, ValueError):
-        pass
-    peak = float(peaks.get("hbm_gbs", 6400.0))
-    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    peaks = load_peaks()
+    # the matrix and the solutions' summaries stay in L2 on these workloads (the 12 x 4000
+    # matrix is 64 MB of the 126 MB L2), so the L2 bandwidth is the memory roofline
+    if L2_PEAK_GBS:
+        peak, peak_src, bound = L2_PEAK_GBS, "measured (own L2-resident copy kernel)", "l2"
+    else:
+        peak = float(peaks.get("hbm_gbs", 6400.0))
+        peak_src, bound = ("measured" if "hbm_gbs" in peaks else "fallback"), "hbm"
 
     # end to end through the C ABI with host buffers: H2D of the routes and the operator order,
     # the descent, D2H of the per-solution costs
@@ -306,12 +371,12 @@ def run_ours(args):
     h_nodes, h_offs, h_per = pin(nodes), pin(offs), pin(per)
     h_perm = np.ascontiguousarray(perm)
     e2e_ms = []
-    for k in range(args.steps):
+    for k in range(min(args.steps, 5)):
         flush.fill_(k)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         work.load_flat(h_nodes.numpy(), h_offs.numpy(), h_per.numpy(), stream=sptr)
-        work.descend(h_perm, MAX_PASS, multi=True, use_graph=True, poll_every=1, stream=sptr,
+        work.descend(h_perm, max_pass, multi=True, use_graph=True, poll_every=1, stream=sptr,
                      n_groups=args.groups, persistent=persistent)
         comps, F = work.cost(stream=sptr)
         e2e_ms.append(1e3 * (time.perf_counter() - t0))
@@ -323,9 +388,9 @@ def run_ours(args):
     cpu = None
     if rank == 0 and pool is not None:
         m, wall, cpu_s = oracle_sample(pool, pool._processes, workload=args.workload)
-        desc = (f"{pool._processes} of the {N_SOL} descents of this workload, one per process; "
-                f"{cpu_s:.1f} s CPU, {wall:.1f} s wall")
-        cpu = {"value": m / wall, "unit": UNIT, "cores": pool._processes, "kind": "oracle", "sample": desc}
+        desc = f"{oracle_sample_desc(args.workload, pool._processes)}; {cpu_s:.1f} s CPU, {wall:.1f} s wall"
+        cpu = {"value": m / wall, "unit": UNIT, "cores": pool._processes, "kind": "oracle", "sample": desc,
+               "host": host_cpu()}
         pool.close()
 
     if rank == 0:
@@ -334,26 +399,30 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32/f64", "data": "synthetic",
-            "config": {"workload": workload_name(args.workload), "l2": "flushed between timed steps (256 MB write)",
-                       "route_slots": R, "k_max": K,
+            "config": {"workload": workload_name(args.workload, world),
+                       "l2": "flushed between timed steps (256 MB write)",
+                       "route_slots": R, "k_max": K, "passes_per_step": max_pass,
                        "launch": ("one persistent launch per descent" if persistent else
                                   f"CUDA graph per pass, {args.groups} concurrent solution groups"),
-                       "parallelism": f"{world} independent replicas"},
+                       "parallelism": f"{world} ranks, each {n_sol} solutions of the same instance"},
             "descents_per_s": descents,
             "moves_per_step": moves / args.steps,
-            "passes_max": last.passes_max, "steps_per_descent": last.steps / N_SOL,
+            "moves_exact_frac": sum(s.moves_exact for s in stats) / max(moves, 1),
+            "passes_max": last.passes_max, "steps_per_descent": last.steps / n_sol,
             "moves_per_step_by_op": [int(x) // args.steps for x in by_op],
+            "best_solution": {"index": best, "F": float(F_all[best]) / W.SCALE},
             "roofline": {"kernel": ("k_descend_persistent (evaluation and steps, one launch per descent)"
                                     if persistent else "k_eval (neighbourhood evaluation)"),
-                         "bound": "hbm",
+                         "bound": bound,
                          "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "peak_source": peak_src,
-                         "traffic": (TRAFFIC_6X288["persistent" if persistent else "eval"]
-                                     if args.workload == "mdvrptw-6x288" else None),
+                         "hbm_frac": achieved / float(peaks.get("hbm_gbs", 6400.0)),
+                         "traffic": TRAFFIC.get((args.workload, persistent)),
                          "ms_per_launch": eval_ms / max(eval_launches, 1),
                          "alg_bytes_per_launch": alg_bytes / max(eval_launches, 1),
-                         "note": ("the launch also runs the steps (selection, apply, rebuild)" if persistent
-                                  else "launch times summed over the concurrent solution groups")},
+                         "note": ("algorithmic bytes = scored moves x per-operator bytes; "
+                                  + ("the launch also runs the steps (selection, apply, rebuild)" if persistent
+                                     else "launch times summed over the concurrent solution groups"))},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": statistics.mean(e2e_ms)},
@@ -449,50 +518,110 @@ def run_batch(args):
     }))
 
 
-LEARNED_SOL = 8
+LEARNED_SOL = 8         # solutions per rank and step
+LEARNED_SEEDS = 5       # instances of seeds 1..5; the timed steps cycle through them
 LEARNED_POOL = 256      # eta-ranked candidate pool per customer that the MLP scores
 LEARNED_TOPK = 64
 LEARNED_SWEEP = 20      # full plain sweep every 20 steps
+# DRAM bytes (read + write) of one full-neighbourhood k_eval launch of 2 solutions of the
+# 20 x 10000 instance (Swap), from ncu (dram__bytes_read.sum + dram__bytes_write.sum) on
+# `python bench_probe` commands recorded under profiles/; None until measured for the current
+# kernel.
+TRAFFIC_20X10000 = None
 
 
-def learned_workload(n_sol: int):
-    spec = W.mdvrptw_20x10000(SEED, theta=0)
-    sols = W.initial_solutions(spec, SEED, n_sol, order="window")
-    perm = W.op_permutations(SEED, n_sol, MAX_PASS)
-    return spec, sols, perm
+def learned_workload(n_sol: int, seed: int = SEED, first: int = 0):
+    """The 20-depot, 10000-customer MDVRPTW instance of `seed` (every customer a candidate) and
+    its window-ordered initial solutions first .. first + n_sol - 1 with their operator orders."""
+    spec = W.mdvrptw_20x10000(seed, theta=0)
+    sols = [W.initial_solution(spec, seed, i, order="window") for i in range(first, first + n_sol)]
+    perm = W.op_permutations(seed, first + n_sol, MAX_PASS)[first:]
+    return spec, sols, np.ascontiguousarray(perm)
 
 
-def _oracle_learned(args):
-    idx, n_sol, nbr, cnt, max_pass = args
+def host_cpu() -> dict:
+    model = ""
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    return {"nproc": os.cpu_count(), "model": model}
+
+
+def _oracle_eval_sample(args):
+    """One seeded sample of the oracle's move evaluation: operator op of solution idx on the
+    given lists (every move of the operator for that solution, built and recomputed from
+    scratch)."""
+    seed, idx, op, nbr, cnt = args
     from oracle import oracle as O
-    spec, sols, perm = learned_workload(n_sol)
-    inst = O.Instance(spec)
-    inst.set_neighbors(nbr, cnt)
+    key = ("learned", seed, nbr is None)
+    if key not in _ORACLE_CACHE:
+        spec, sols, _ = learned_workload(LEARNED_SOL, seed)
+        if nbr is None:
+            spec = W.mdvrptw_20x10000(seed, theta=LEARNED_TOPK)  # eta top-64 lists built by the oracle
+        inst = O.Instance(spec)
+        if nbr is not None:
+            inst.set_neighbors(nbr, cnt)
+        _ORACLE_CACHE[key] = (inst, sols)
+    inst, sols = _ORACLE_CACHE[key]
     t0 = time.perf_counter()
-    d = inst.descend(sols[idx], perm[idx], max_pass, multi=True, sweep_every=LEARNED_SWEEP)
-    return d.moves_scored, time.perf_counter() - t0
+    mv, scored = inst.eval_op(sols[idx % len(sols)], op)
+    return int(scored), time.perf_counter() - t0
+
+
+def oracle_eval_step(pool, seed: int, step: int, nbr=None, cnt=None):
+    """Every pool process evaluates one (solution, operator) of the seed's initial solutions on
+    top-64 lists: Relocate and Swap alternate.  Returns (moves, wall s, CPU s)."""
+    n = pool._processes
+    jobs = [(seed, step * n + k, W.OP_RELOCATE if (step + k) % 2 == 0 else W.OP_SWAP, nbr, cnt) for k in range(n)]
+    t0 = time.perf_counter()
+    res = pool.map(_oracle_eval_sample, jobs, chunksize=1)
+    return sum(r[0] for r in res), time.perf_counter() - t0, sum(r[1] for r in res)
+
+
+def learned_name(n_sol: int, world: int, seeds) -> str:
+    return (f"learned-20x10000: MDVRPTW 20 depots x 10000 customers on [-1000,1000]^2, horizon 4000, "
+            f"Q=200, N_V=60, D=4000, seeds {list(seeds)}; {n_sol * world} solutions per step "
+            f"(window-ordered sweep routes) descended to a local optimum (delta={MAX_PASS}), multi-move, "
+            f"lambda=(1,1,1,1); learned top-{LEARNED_TOPK} of a {LEARNED_POOL} eta pool, full sweep every "
+            f"{LEARNED_SWEEP} steps; plain arm: every customer a candidate in every step")
 
 
 def run_learned(args):
-    """Learned-pruned descents of the 20-depot, 10000-customer MDVRPTW instance beside the plain
-    full-neighbourhood descents of the same solutions (and the static eta top-64 lists).
+    """Learned-pruned descents of the 20-depot, 10000-customer MDVRPTW instances (seeds 1..5)
+    beside the plain full-neighbourhood descents of the same solutions (and the static eta top-64
+    lists).  One timed step descends n_sol solutions per rank of one seed's instance from their
+    initial routes to a local optimum of the full neighbourhood (the verification pass confirms
+    it); the steps cycle through the seeds.
 
     Untimed set-up: labels logged from plain descents of three smaller instances, MLP training,
-    then the MLP scores each customer's 256 eta-nearest candidates and keeps the top 64.  One
-    timed step descends all solutions from their initial routes to a local optimum of the full
-    neighbourhood (the verification pass confirms it) with a full sweep every 20 steps."""
+    then per seed the MLP scores each customer's 256 eta-nearest candidates and keeps the top 64.
+    Under torchrun every rank descends its own share of each seed's solutions (weak scaling) and
+    the ranks all-gather the per-solution costs at the end."""
     import torch
-    from paper_2605_05208_b300 import build, learned, mdls
+    import torch.distributed as dist
+    from paper_2605_05208_b300 import build, learned, mdls, shard
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
     n_sol = args.solutions or LEARNED_SOL
+    seeds = list(range(SEED, SEED + (args.seeds or LEARNED_SEEDS)))
+    plain_seeds = seeds[:max(1, min(args.plain_seeds, len(seeds)))]
     pool = None
-    if not args.no_cpu_baseline:
-        ncores = min(os.cpu_count() or 1, 16)
-        pool = make_pool(ncores)
+    if rank == 0 and not args.no_cpu_baseline:
+        pool = make_pool(os.cpu_count() or 1)
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
     build.build()
-    dev = torch.device("cuda", 0)
+    dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(dev)
     torch.cuda.set_stream(stream)
     sptr = stream.cuda_stream
+    a, b = shard.share(n_sol * world, rank, world)
 
     t0 = time.perf_counter()
     data = learned.training_set(stream=sptr)
@@ -501,146 +630,248 @@ def run_learned(args):
     pr, losses = learned.train(data, epochs=20, stream=sptr)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
-
-    spec, sols, perm = learned_workload(n_sol)
-    routes = max(len(x) for x in sols)
-    longest = max(len(r) - 2 for x in sols for r in x)
-    R = max(64, 2 * routes, spec.n_depots * spec.N_V + 8)
-    K = max(64, 2 * longest)
-    perm_dev = torch.from_numpy(np.ascontiguousarray(perm)).to(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
 
-    inst_l = mdls.Instance(spec)
-    inst_l.build_neighbors(LEARNED_POOL)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    pr.prune(inst_l, LEARNED_TOPK, stream=sptr)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    prune_ms = e0.elapsed_time(e1)
-    inst_e = mdls.Instance(spec)
-    inst_e.build_neighbors(LEARNED_TOPK)
-    inst_p = mdls.Instance(spec)  # theta = 0: every customer is a candidate
+    class Seed:
+        pass
 
-    def arm(inst, sweep, warmup, steps, time_eval=False):
-        init = mdls.Solutions(inst, n_sol, R, K)
-        work = mdls.Solutions(inst, n_sol, R, K)
-        init.load(sols)
-
-        def one(te=False, max_pass=MAX_PASS):
-            work.copy_from(init, stream=sptr)
-            return work.descend(perm_dev.data_ptr(), max_pass, multi=True, use_graph=True,
-                                poll_every=1, stream=sptr, n_ops=W.N_OPS, time_eval=te,
-                                n_groups=args.groups, sweep_every=sweep,
-                                persistent=args.persistent > 0)
-        for _ in range(warmup):
-            one(max_pass=MAX_PASS if sweep else 2)
+    S = {}
+    prune_ms = []
+    for sd in seeds:
+        x = Seed()
+        x.spec, x.sols, x.perm = learned_workload(b - a, sd, a)
+        routes = max(len(q) for q in x.sols)
+        longest = max(len(r) - 2 for q in x.sols for r in q)
+        x.R = max(64, 2 * routes, x.spec.n_depots * x.spec.N_V + 8)
+        x.K = max(64, 2 * longest)
+        x.perm_dev = torch.from_numpy(x.perm).to(dev)
+        x.inst = mdls.Instance(x.spec)
+        x.inst.build_neighbors(LEARNED_POOL)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pr.prune(x.inst, LEARNED_TOPK, stream=sptr)
+        e1.record(stream)
         torch.cuda.synchronize()
-        ms, sts = 0.0, []
-        with ClockSampler(0) as clk:
+        prune_ms.append(e0.elapsed_time(e1))
+        x.init = mdls.Solutions(x.inst, b - a, x.R, x.K)
+        x.work = mdls.Solutions(x.inst, b - a, x.R, x.K)
+        x.init.load(x.sols)
+        S[sd] = x
+
+    def descend(x, work, init, sweep, te=False, max_pass=MAX_PASS):
+        work.copy_from(init, stream=sptr)
+        return work.descend(x.perm_dev.data_ptr(), max_pass, multi=True, use_graph=True, poll_every=1,
+                            stream=sptr, n_ops=W.N_OPS, time_eval=te, n_groups=args.groups,
+                            sweep_every=sweep, persistent=args.persistent > 0)
+
+    def timed(fn, steps):
+        ms, out = 0.0, []
+        with ClockSampler(local) as clk:
             for k in range(steps):
-                flush.fill_(k)
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                sts.append(one(te=time_eval))
-                b.record(stream)
+                flush.fill_(k)  # evict the working set from L2 between timed steps
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                out.append(fn(k))
+                e1.record(stream)
                 torch.cuda.synchronize()
-                ms += a.elapsed_time(b)
-        comps, F = work.cost(stream=sptr)
-        per = work.stats(stream=sptr)
-        return dict(ms=ms, stats=sts, F=F.astype(np.float64), clocks=clk.summary(),
-                    passes=[int(x[4]) for x in per]), work
+                ms += e0.elapsed_time(e1)
+        return ms, out, clk.summary()
 
-    res_l, work_l = arm(inst_l, LEARNED_SWEEP, args.warmup, args.steps, time_eval=True)
-    res_p, _ = arm(inst_p, 0, 1, args.plain_steps)
-    res_e, _ = arm(inst_e, LEARNED_SWEEP, 1, 1)
+    # learned arm: the timed steps cycle through the seeds
+    for k in range(args.warmup):
+        x = S[seeds[k % len(seeds)]]
+        descend(x, x.work, x.init, LEARNED_SWEEP)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
 
-    def summary(r, steps):
-        moves = sum(x.moves_scored for x in r["stats"])
-        return {"descents_per_s": n_sol * steps / (r["ms"] / 1e3), "ms_per_step": r["ms"] / steps,
-                "moves_per_s": moves / (r["ms"] / 1e3), "moves_per_descent": moves / (n_sol * steps),
-                "F_mean": float(r["F"].mean()) / W.SCALE, "passes_max": max(r["passes"]),
-                "passes_mean": float(np.mean(r["passes"]))}
-    L, P, E = summary(res_l, args.steps), summary(res_p, args.plain_steps), summary(res_e, 1)
-    gap = (L["F_mean"] - P["F_mean"]) / P["F_mean"]
-    per_gap = (res_l["F"] - res_p["F"]) / res_p["F"]
+    def learned_step(k):
+        x = S[seeds[k % len(seeds)]]
+        return seeds[k % len(seeds)], descend(x, x.work, x.init, LEARNED_SWEEP, te=True)
 
-    # dominant kernel: the neighbourhood evaluation of the learned descents, timed live
-    sts = res_l["stats"]
-    eval_ms = sum(x.eval_ms for x in sts)
-    eval_launches = sum(x.eval_launches for x in sts)
-    by_op = np.sum([x.moves_by_op for x in sts], axis=0)
+    ms_l, out_l, clk_l = timed(learned_step, args.steps)
+    if world > 1:
+        dist.barrier()
+    # final costs of each seed's learned descents (the last step of that seed left them in work)
+    Fl = {}
+    for sd in seeds:
+        if any(o[0] == sd for o in out_l):
+            Fl[sd] = S[sd].work.cost(stream=sptr)[1].astype(np.float64)
+
+    # plain full-neighbourhood arm on the first plain_seeds seeds (every customer a candidate)
+    plain = {}
+    ms_p, n_p, out_p, clk_p = 0.0, 0, [], None
+    for sd in plain_seeds:
+        x = S[sd]
+        inst_p = mdls.Instance(x.spec)
+        init_p = mdls.Solutions(inst_p, b - a, x.R, x.K)
+        work_p = mdls.Solutions(inst_p, b - a, x.R, x.K)
+        init_p.load(x.sols)
+        descend(x, work_p, init_p, 0, max_pass=2)  # warm-up
+        torch.cuda.synchronize()
+        ms, out, clk = timed(lambda k: descend(x, work_p, init_p, 0, te=True), args.plain_steps)
+        ms_p += ms
+        n_p += args.plain_steps
+        out_p += out
+        clk_p = clk
+        plain[sd] = work_p.cost(stream=sptr)[1].astype(np.float64)
+        del work_p, init_p, inst_p
+    # static eta top-64 lists with the same sweep schedule, seed 1
+    x = S[seeds[0]]
+    inst_e = mdls.Instance(x.spec)
+    inst_e.build_neighbors(LEARNED_TOPK)
+    init_e = mdls.Solutions(inst_e, b - a, x.R, x.K)
+    work_e = mdls.Solutions(inst_e, b - a, x.R, x.K)
+    init_e.load(x.sols)
+    descend(x, work_e, init_e, LEARNED_SWEEP, max_pass=2)
+    ms_e, out_e, _ = timed(lambda k: descend(x, work_e, init_e, LEARNED_SWEEP), 1)
+    F_eta = work_e.cost(stream=sptr)[1].astype(np.float64)
+
+    def arm(ms, sts, steps):
+        moves = sum(q.moves_scored for q in sts)
+        exact = sum(q.moves_exact for q in sts)
+        return {"descents_per_s": (b - a) * steps / (ms / 1e3), "ms_per_step": ms / steps,
+                "moves_per_s": moves / (ms / 1e3), "moves_per_descent": moves / ((b - a) * steps),
+                "moves_exact_frac": exact / max(moves, 1),
+                "passes_max": max(q.passes_max for q in sts)}
+
+    L = arm(ms_l, [o[1] for o in out_l], args.steps)
+    P = arm(ms_p, out_p, n_p)
+    E = arm(ms_e, out_e, 1)
+    gaps = {sd: float(np.mean((Fl[sd] - plain[sd]) / plain[sd])) for sd in plain_seeds if sd in Fl}
+    per_gap = np.concatenate([(Fl[sd] - plain[sd]) / plain[sd] for sd in plain_seeds if sd in Fl])
+    L["F_mean"] = {sd: float(Fl[sd].mean()) / W.SCALE for sd in Fl}
+    P["F_mean"] = {sd: float(plain[sd].mean()) / W.SCALE for sd in plain}
+    E["F_mean"] = float(F_eta.mean()) / W.SCALE
+
+    # the per-solution costs of every rank's learned descents, gathered (the multi-GPU collective)
+    comps_l, F_l = S[seeds[(args.steps - 1) % len(seeds)]].work.cost(stream=sptr)
+    comps_all, F_all, best = shard.run(n_sol * world, rank, world, lambda a_, b_: (comps_l, F_l))
+
+    # the largest kernel of the learned descents (the evaluation), timed live with CUDA events
+    sts = [o[1] for o in out_l]
+    eval_ms = sum(q.eval_ms for q in sts)
+    eval_launches = sum(q.eval_launches for q in sts)
+    by_op = np.sum([q.moves_by_op for q in sts], axis=0)
     alg_bytes = float(sum(int(by_op[o]) * ALG_BYTES[o] for o in range(W.N_OPS_ALL)))
-    achieved = alg_bytes / (eval_ms / 1e3) / 1e9
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except (OSError, ValueError):
         pass
     peak = float(peaks.get("hbm_gbs", 6400.0))
+    achieved = alg_bytes / (eval_ms / 1e3) / 1e9
 
-    # end to end with host buffers: routes and operator order H2D, descent, costs D2H
-    nodes, offs, per = mdls.flatten(sols)
-    h_perm = np.ascontiguousarray(perm)
+    # end to end through the C ABI with host buffers: routes and operator order H2D, the learned
+    # descent, the per-solution costs D2H
     e2e_ms = []
+    h2d = d2h = 0
     for k in range(min(args.steps, 3)):
+        x = S[seeds[k % len(seeds)]]
+        nodes, offs, per = mdls.flatten(x.sols)
         flush.fill_(k)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        work_l.load_flat(nodes, offs, per, stream=sptr)
-        work_l.descend(h_perm, MAX_PASS, multi=True, use_graph=True, poll_every=1, stream=sptr,
-                       n_groups=args.groups, sweep_every=LEARNED_SWEEP,
-                       persistent=args.persistent > 0)
-        comps, F = work_l.cost(stream=sptr)
+        x.work.load_flat(nodes, offs, per, stream=sptr)
+        x.work.descend(x.perm, MAX_PASS, multi=True, use_graph=True, poll_every=1, stream=sptr,
+                       n_groups=args.groups, sweep_every=LEARNED_SWEEP, persistent=args.persistent > 0)
+        comps, F = x.work.cost(stream=sptr)
         e2e_ms.append(1e3 * (time.perf_counter() - t0))
-    h2d = nodes.nbytes + 16 * int(per.sum()) + h_perm.nbytes
-    d2h = comps.nbytes + F.nbytes
+        h2d = nodes.nbytes + 16 * int(per.sum()) + x.perm.nbytes
+        d2h = comps.nbytes + F.nbytes
+
+    # the slowest rank's time
+    tot = torch.tensor([ms_l], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(tot, op=dist.ReduceOp.MAX)
+    ms_max = float(tot.item())
+    moves_all = sum(q.moves_scored for q in sts) * world  # every rank descends the same number
 
     cpu = None
     if pool is not None:
-        nbr, cnt = inst_l.neighbors()
+        nbr, cnt = S[seeds[0]].inst.neighbors()
+        m, wall, cpu_s = oracle_eval_step(pool, seeds[0], 0, nbr, cnt)
         nproc = pool._processes
-        t0 = time.perf_counter()
-        out = pool.map(_oracle_learned, [(i % n_sol, n_sol, nbr, cnt, 1) for i in range(nproc)])
-        wall = time.perf_counter() - t0
-        m = sum(o[0] for o in out)
-        cpu_s = sum(o[1] for o in out)
-        desc = (f"{nproc} processes, each the first pass (5 pruned steps) of one learned descent "
-                f"with the same top-64 lists; {m} moves in {cpu_s:.1f} s CPU, {wall:.1f} s wall; "
-                f"descents/s = oracle moves/s / the GPU's moves per learned descent")
-        cpu = {"value": (m / wall) / L["moves_per_descent"], "unit": "descents/s", "cores": nproc,
-               "kind": "oracle", "sample": desc, "moves_per_s": m / wall}
+        desc = (f"{nproc} processes on {host_cpu()['model']}, each evaluating every Relocate or Swap move of "
+                f"one initial solution of seed {seeds[0]} on its learned top-{LEARNED_TOPK} lists ({m} moves, "
+                f"{cpu_s:.1f} s CPU, {wall:.1f} s wall); descents/s extrapolated as oracle moves/s over the "
+                f"GPU's moves per learned descent")
+        cpu = {"value": m / wall, "unit": UNIT, "cores": nproc, "kind": "oracle", "sample": desc,
+               "descents_per_s": (m / wall) / L["moves_per_descent"], "host": host_cpu()}
         pool.close()
 
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": moves_all / (ms_max / 1e3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32/f64 (bf16 MLP)",
+            "data": "synthetic",
+            "config": {"workload": learned_name(n_sol, world, seeds), "seeds": seeds, "plain_seeds": plain_seeds,
+                       "l2": "flushed between timed steps (256 MB write); the 401.6 MB distance matrix exceeds L2",
+                       "stream_groups": args.groups, "parallelism": f"{world} ranks x {n_sol} solutions"},
+            "descents_per_s": L["descents_per_s"] * world,
+            "learned": L, "plain_full": P, "eta_top64": E,
+            "speedup_vs_plain": L["descents_per_s"] / P["descents_per_s"],
+            "cost_gap_vs_plain": float(np.mean(per_gap)), "cost_gap_by_seed": gaps,
+            "cost_gap_per_solution_max": float(per_gap.max()),
+            "speedup_vs_eta_top64": L["descents_per_s"] / E["descents_per_s"],
+            "cost_gap_vs_eta_top64": float(np.mean((Fl[seeds[0]] - F_eta) / F_eta)),
+            "best_solution": {"index": best, "F": float(F_all[best]) / W.SCALE},
+            "setup": {"label_logging_s": t_log, "training_s": t_train,
+                      "train_loss_first_last": [losses[0], losses[-1]],
+                      "positives": [int(d[2].sum()) for d in data], "prune_ms": prune_ms},
+            "roofline": {"kernel": "k_eval (neighbourhood evaluation, learned descents incl. full sweeps)",
+                         "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+                         "traffic": TRAFFIC_20X10000, "ms_per_launch": eval_ms / max(eval_launches, 1),
+                         "alg_bytes_per_launch": alg_bytes / max(eval_launches, 1),
+                         "note": "algorithmic bytes = scored moves x per-operator bytes; the kernel is "
+                                 "issue- and latency-bound (profiles/), not DRAM-bound"},
+            "cpu_baseline": cpu,
+            "e2e": {"value": L["moves_per_descent"] * (b - a) * world / (statistics.mean(e2e_ms) / 1e3),
+                    "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "ms_per_step": statistics.mean(e2e_ms),
+                    "descents_per_s": (b - a) * world / (statistics.mean(e2e_ms) / 1e3)},
+            "gpu_launches": int(sum(q.launches for q in sts) + 3 * args.steps),
+            "clocks": clk_l, "clocks_plain": clk_p,
+        }))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_reference_learned(args):
+    """The oracle (the plain CPU restatement of the paper's definitions), as it stands, on the
+    default workload: every step, each host process evaluates every Relocate or Swap move of one
+    initial solution of the step's seed on eta top-64 lists (the oracle's own lists: the learned
+    ones come from the GPU), so a step is a bounded sample of the learned descents' work in the
+    same unit (moves evaluated/s).  Rank 0 only."""
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    seeds = list(range(SEED, SEED + (args.seeds or LEARNED_SEEDS)))
+    cores = os.cpu_count() or 1
+    pool = make_pool(cores)
+    for k in range(args.warmup):
+        oracle_eval_step(pool, seeds[k % len(seeds)], k)
+    moves, wall, cpu_s = 0, 0.0, 0.0
+    for k in range(args.steps):
+        m, w, c = oracle_eval_step(pool, seeds[k % len(seeds)], args.warmup + k)
+        moves += m
+        wall += w
+        cpu_s += c
+    pool.close()
+    value = moves / wall
+    desc = (f"{cores} processes on {host_cpu()['model']}; per step each evaluates every Relocate or Swap move of "
+            f"one initial solution of the step's seed on eta top-{LEARNED_TOPK} lists; "
+            f"{moves / args.steps:.3e} moves and {cpu_s / args.steps:.1f} s CPU per step")
     print(json.dumps({
-        "metric": "LS descents/s", "value": L["descents_per_s"], "unit": "descents/s", "n_gpus": 1,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": L["ms_per_step"],
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32/f64 (bf16 MLP)",
-        "data": "synthetic",
-        "config": {"workload": f"learned-20x10000: MDVRPTW 20 depots x 10000 customers on "
-                               f"[-1000,1000]^2, horizon 4000, Q=200, N_V=60, D=4000; {n_sol} "
-                               f"solutions (window-ordered sweep routes) descended to a local "
-                               f"optimum (delta={MAX_PASS}), multi-move; learned top-{LEARNED_TOPK} "
-                               f"of a {LEARNED_POOL} eta pool, full sweep every {LEARNED_SWEEP} steps",
-                   "l2": "flushed between timed steps (256 MB write)", "route_slots": R, "k_max": K,
-                   "stream_groups": args.groups},
-        "learned": L, "plain_full": P, "eta_top64": E,
-        "speedup_vs_plain": L["descents_per_s"] / P["descents_per_s"],
-        "cost_gap_vs_plain": gap, "cost_gap_per_solution_max": float(per_gap.max()),
-        "speedup_vs_eta_top64": L["descents_per_s"] / E["descents_per_s"],
-        "cost_gap_vs_eta_top64": (L["F_mean"] - E["F_mean"]) / E["F_mean"],
-        "setup": {"label_logging_s": t_log, "training_s": t_train, "train_loss_first_last": [losses[0], losses[-1]],
-                  "positives": [int(d[2].sum()) for d in data], "prune_ms": prune_ms},
-        "roofline": {"kernel": "k_eval (neighbourhood evaluation, learned descents)", "bound": "hbm",
-                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "peak_source": "measured" if "hbm_gbs" in peaks else "fallback", "traffic": None,
-                     "eval_ms_per_launch": eval_ms / max(eval_launches, 1),
-                     "alg_bytes_per_launch": alg_bytes / max(eval_launches, 1)},
-        "cpu_baseline": cpu,
-        "e2e": {"value": n_sol / (statistics.mean(e2e_ms) / 1e3), "unit": "descents/s",
-                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": statistics.mean(e2e_ms)},
-        "gpu_launches": int(sum(x.launches for x in sts) + 3 * args.steps),
-        "clocks": res_l["clocks"], "clocks_plain": res_p["clocks"],
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64/f64",
+        "data": "synthetic", "config": {"workload": learned_name(args.solutions or LEARNED_SOL, 1, seeds),
+                                        "sample": desc},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc,
+                         "host": host_cpu()},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
 
@@ -918,13 +1149,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["mdvrptw-6x288", "batch16-uneven", "learned-20x10000",
-                                           "plain-20x10000", "repair-mdvrptw-6x288", "mdvrp-6x288-2opt",
-                                           "memetic-mdvrptw-6x288", "repair-mdvrptw-20x10000"],
-                    default="mdvrptw-6x288")
-    ap.add_argument("--solutions", type=int, default=0, help="solutions of the learned workload (0: 8)")
+    ap.add_argument("--workload", choices=["learned-20x10000", "mdvrptw-6x288", "mdvrp-4x50", "mdovrp-12x4000",
+                                           "batch16-uneven", "plain-20x10000", "repair-mdvrptw-6x288",
+                                           "mdvrp-6x288-2opt", "memetic-mdvrptw-6x288", "repair-mdvrptw-20x10000"],
+                    default="learned-20x10000")
+    ap.add_argument("--solutions", type=int, default=0, help="solutions per rank of the learned workload (0: 8)")
+    ap.add_argument("--seeds", type=int, default=0, help="instances of the learned workload (0: seeds 1..5)")
+    ap.add_argument("--plain-seeds", type=int, default=1,
+                    help="seeds whose plain full-neighbourhood descents are timed beside the learned ones")
     ap.add_argument("--plain-steps", type=int, default=1,
-                    help="timed plain full-neighbourhood descents beside the learned workload")
+                    help="timed plain full-neighbourhood descents per plain seed")
     ap.add_argument("--max-pass", type=int, default=None,
                     help="passes per step: batch16-uneven 4, plain-20x10000 500 (to the local optimum)")
     ap.add_argument("--persistent", type=int, default=-1,
@@ -937,7 +1171,10 @@ def main():
                     help="solution groups advancing on concurrent streams inside the graph")
     args = ap.parse_args()
     if args.impl == "reference":
-        run_reference(args)
+        if args.workload == "learned-20x10000":
+            run_reference_learned(args)
+        else:
+            run_reference(args)
     elif args.workload == "batch16-uneven":
         run_batch(args)
     elif args.workload == "learned-20x10000":
