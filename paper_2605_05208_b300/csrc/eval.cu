@@ -32,11 +32,55 @@ __global__ void __launch_bounds__(32 * MD_EVAL_WARPS, MD_EVAL_MIN_BLOCKS) k_eval
     best_init(b);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
     const int wpc = C.lists ? 1 : wpc_full;
+    if (full_path(C, op)) return;  // k_eval_full scores this solution
     if (C.lists && I.theta <= 64 && (op == MD_OP_RELOCATE || op == MD_OP_SWAP))
         eval_tile_lists<TW>(C, op, blockIdx.x * wpb, gridDim.x * wpb, b, s_wl, s_tc, s_cnt);  // the whole block
     else if (op >= 0)
         for (int gw = blockIdx.x * wpb + warp; gw < I.nc * wpc; gw += gridDim.x * wpb)
-            eval_customer<TW>(C, op, gw / wpc, lane, b, s_wl[warp], gw % wpc, wpc);
+            eval_customer<TW>(C, op, gw / wpc, lane, b, s_wl[warp], gw % wpc, wpc, &s_tc[warp]);
+    warp_commit(C, b, (size_t)blockIdx.x * wpb + warp, lane);
+}
+
+#ifndef MD_FULL_MIN_BLOCKS
+// blocks of the full-neighbourhood kernel resident per SM: its candidate loop keeps the
+// customer's context in shared memory and needs fewer registers than the list paths
+#define MD_FULL_MIN_BLOCKS 2
+#endif
+
+// Full neighbourhoods of Relocate, Swap and 2-opt* (every customer a candidate, exact lower-bound
+// rejection): the solutions for which full_path holds; k_eval scores the others.  Same grid and
+// leader records as k_eval.
+template <bool TW>
+__global__ void __launch_bounds__(32 * MD_EVAL_WARPS, MD_FULL_MIN_BLOCKS) k_eval_full(DevInst I, DevSols D, DevMoves M,
+                                                                                     uint32_t flags, int s0, int wpc) {
+    Ctx C;
+    C.I = I; C.D = D; C.M = M; C.flags = flags;
+    C.s = s0 + blockIdx.y;
+    C.open = (I.variant & MD_VARIANT_OPEN) != 0;
+    C.sym = (I.variant & MD_VARIANT_SYMMETRIC) != 0;
+    const int op_raw = D.ops[C.s];
+    const int op = op_raw < 0 ? -1 : (op_raw & MD_OP_MASK);
+    C.lists = I.theta > 0 && !(op_raw >= 0 && (op_raw & MD_OP_SWEEP));
+    if (!full_path(C, op)) return;  // k_eval scores this solution
+    __shared__ double s_w[4];
+    __shared__ float s_wf[4];
+    if (threadIdx.x < 4) {
+        s_w[threadIdx.x] = D.w[4 * C.s + threadIdx.x];
+        s_wf[threadIdx.x] = (float)s_w[threadIdx.x];
+    }
+    __syncthreads();
+    C.w = s_w;
+    C.wf = s_wf;
+    __shared__ int s_wl[MD_EVAL_WARPS][64];
+    __shared__ TileCtx s_tc[MD_EVAL_WARPS];
+    Best b;
+    best_init(b);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    for (int gw = blockIdx.x * wpb + warp; gw < I.nc * wpc; gw += gridDim.x * wpb) {
+        if (op == MD_OP_RELOCATE) eval_relocate_full<TW>(C, gw / wpc, lane, b, s_wl[warp], gw % wpc, wpc, &s_tc[warp]);
+        else if (op == MD_OP_SWAP) eval_swap_full<TW>(C, gw / wpc, lane, b, s_wl[warp], gw % wpc, wpc, &s_tc[warp]);
+        else eval_2optstar_full<TW>(C, gw / wpc, lane, b, s_wl[warp], gw % wpc, wpc, &s_tc[warp]);
+    }
     warp_commit(C, b, (size_t)blockIdx.x * wpb + warp, lane);
 }
 
@@ -55,6 +99,7 @@ __global__ void __launch_bounds__(32 * MD_EVAL_WARPS, MD_EVAL_MIN_BLOCKS) k_eval
     __shared__ double s_w[MD_EVAL_WARPS][4];
     __shared__ float s_wf[MD_EVAL_WARPS][4];
     __shared__ int s_wl[MD_EVAL_WARPS][64];
+    __shared__ TileCtx s_tc[MD_EVAL_WARPS];
     __shared__ int s_tile;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     Ctx &C = cs[warp];
@@ -100,8 +145,8 @@ __global__ void __launch_bounds__(32 * MD_EVAL_WARPS, MD_EVAL_MIN_BLOCKS) k_eval
             for (int q = 0; q < upw; q++) {
                 const int gw = ws * upw + q;
                 if (gw >= C.I.nc * wpc) break;
-                if (tw) eval_customer<true>(C, op, gw / wpc, lane, b, s_wl[warp], gw % wpc, wpc);
-                else eval_customer<false>(C, op, gw / wpc, lane, b, s_wl[warp], gw % wpc, wpc);
+                if (tw) eval_customer<true>(C, op, gw / wpc, lane, b, s_wl[warp], gw % wpc, wpc, &s_tc[warp]);
+                else eval_customer<false>(C, op, gw / wpc, lane, b, s_wl[warp], gw % wpc, wpc, &s_tc[warp]);
             }
         warp_commit(C, b, ws, lane);
         __syncwarp();  // every lane is done with this tile's context
@@ -138,6 +183,11 @@ md_status md_launch_eval(md_solutions *s, md_moves *m, uint32_t flags, cudaStrea
     if (I.variant & MD_VARIANT_TW) k_eval<true><<<grid, 32 * MD_EVAL_WARPS, 0, st>>>(I, s->d, m->d, flags, s0, wpc);
     else k_eval<false><<<grid, 32 * MD_EVAL_WARPS, 0, st>>>(I, s->d, m->d, flags, s0, wpc);
     MD_CUDA(cudaGetLastError());
+    if (!(flags & MD_EVAL_DUMP)) {  // the solutions evaluated over the full neighbourhood
+        if (I.variant & MD_VARIANT_TW) k_eval_full<true><<<grid, 32 * MD_EVAL_WARPS, 0, st>>>(I, s->d, m->d, flags, s0, wpc);
+        else k_eval_full<false><<<grid, 32 * MD_EVAL_WARPS, 0, st>>>(I, s->d, m->d, flags, s0, wpc);
+        MD_CUDA(cudaGetLastError());
+    }
     return MD_OK;
 }
 

@@ -70,6 +70,8 @@ struct Ctx {
     bool lists;  // candidates from the neighbour lists (theta > 0 and not a full-sweep step)
 };
 
+union TileCtx;  // a warp's customer context in shared memory (below)
+
 __device__ __forceinline__ int cost(const DevInst &I, int a, int b) {
     return __ldg(&I.dist[(size_t)a * I.nn + b]);
 }
@@ -323,12 +325,12 @@ __device__ __forceinline__ void split_candidates(const Ctx &C, int cu, int u, in
 // Relocate: seq(u) (1 or 2 nodes, possibly reversed) after v, or before v when v is first.
 // ------------------------------------------------------------------------------------------
 template <bool TW>
-__device__ void eval_relocate_full(const Ctx &C, int cu, int lane, Best &b, int *wl, int part, int wpc);
+__device__ void eval_relocate_full(const Ctx &C, int cu, int lane, Best &b, int *wl, int part, int wpc, TileCtx *tc);
 
 template <bool TW>
-__device__ void eval_relocate(const Ctx &C, int cu, int lane, Best &b, int *wl, int part, int wpc) {
+__device__ void eval_relocate(const Ctx &C, int cu, int lane, Best &b, int *wl, int part, int wpc, TileCtx *tc) {
     if (!C.lists && !(C.flags & MD_EVAL_DUMP)) {
-        eval_relocate_full<TW>(C, cu, lane, b, wl, part, wpc);
+        eval_relocate_full<TW>(C, cu, lane, b, wl, part, wpc, tc);
         return;
     }
     const DevInst &I = C.I;
@@ -439,12 +441,12 @@ __device__ __constant__ int SW_RU[9] = {0, 0, 0, 0, 1, 0, 1, 0, 1};
 __device__ __constant__ int SW_RV[9] = {0, 0, 0, 0, 0, 1, 0, 1, 1};
 
 template <bool TW>
-__device__ void eval_swap_full(const Ctx &C, int cu, int lane, Best &b, int *wl, int part, int wpc);
+__device__ void eval_swap_full(const Ctx &C, int cu, int lane, Best &b, int *wl, int part, int wpc, TileCtx *tc);
 
 template <bool TW>
-__device__ void eval_swap(const Ctx &C, int cu, int lane, Best &b, int *wl, int part, int wpc) {
+__device__ void eval_swap(const Ctx &C, int cu, int lane, Best &b, int *wl, int part, int wpc, TileCtx *tc) {
     if (!C.lists && !(C.flags & MD_EVAL_DUMP)) {
-        eval_swap_full<TW>(C, cu, lane, b, wl, part, wpc);
+        eval_swap_full<TW>(C, cu, lane, b, wl, part, wpc, tc);
         return;
     }
     const DevInst &I = C.I;
@@ -559,10 +561,19 @@ struct SwapCtx {
     int u, A, p, pu, su, x, sx, dsA, hasx, pad;
 };
 
+struct O2Ctx {
+    Seg PU;       // [ds_A..u]
+    RT oldA;
+    int u, A, su, dsA, deA, u_last;
+};
+
+// A warp's customer context in shared memory (tile-cooperative lists, full neighbourhoods).
 union TileCtx {
     RelocCtx r;
     SwapCtx w;
+    O2Ctx o;
 };
+
 
 template <bool TW>
 __device__ __forceinline__ void reloc_setup(const Ctx &C, int cu, RelocCtx &r) {
@@ -837,11 +848,7 @@ __device__ void eval_tile_lists(const Ctx &C, int op, int c0, int cstride, Best 
 // ------------------------------------------------------------------------------------------
 // 2-opt*: [ds_A..u] + [v..de_B] and [ds_B..pred v] + [succ u..de_A].
 // ------------------------------------------------------------------------------------------
-struct O2Ctx {
-    Seg PU;       // [ds_A..u]
-    RT oldA;
-    int u, A, su, dsA, deA, u_last;
-};
+
 
 template <bool TW>
 __device__ __forceinline__ void o2_setup(const Ctx &C, int cu, O2Ctx &o) {
@@ -885,12 +892,12 @@ __device__ __forceinline__ void o2_cand(const Ctx &C, const O2Ctx &o, int v, Bes
 }
 
 template <bool TW>
-__device__ void eval_2optstar_full(const Ctx &C, int cu, int lane, Best &b, int *wl, int part, int wpc);
+__device__ void eval_2optstar_full(const Ctx &C, int cu, int lane, Best &b, int *wl, int part, int wpc, TileCtx *tc);
 
 template <bool TW>
-__device__ void eval_2optstar(const Ctx &C, int cu, int lane, Best &b, int *wl, int part, int wpc) {
+__device__ void eval_2optstar(const Ctx &C, int cu, int lane, Best &b, int *wl, int part, int wpc, TileCtx *tc) {
     if (!C.lists && !(C.flags & MD_EVAL_DUMP)) {
-        eval_2optstar_full<TW>(C, cu, lane, b, wl, part, wpc);
+        eval_2optstar_full<TW>(C, cu, lane, b, wl, part, wpc, tc);
         return;
     }
     const DevInst &I = C.I;
@@ -920,7 +927,7 @@ __device__ void eval_2optstar(const Ctx &C, int cu, int lane, Best &b, int *wl, 
 // by four arcs (three after an open route's last customer) and the duration by as much.
 // ------------------------------------------------------------------------------------------
 template <bool TW>
-__device__ void eval_2opt(const Ctx &C, int cu, int lane, Best &b, int *wl, int part, int wpc) {
+__device__ void eval_2opt(const Ctx &C, int cu, int lane, Best &b, int *wl, int part, int wpc, TileCtx *tc) {
     if (TW || !C.sym) return;
     const DevInst &I = C.I;
     const int u = I.nd + cu;
@@ -1098,10 +1105,18 @@ __device__ __forceinline__ void dequeue_32(int *wl, int &nq, int lane) {
 }
 
 template <bool TW>
-__device__ void eval_relocate_full(const Ctx &C, int cu, int lane, Best &b, int *wl, int part, int wpc) {
+__device__ void eval_relocate_full(const Ctx &C, int cu, int lane, Best &b, int *wl, int part, int wpc, TileCtx *tc) {
     const DevInst &I = C.I;
-    RelocCtx r;
-    reloc_setup<TW>(C, cu, r);
+    // the customer's context goes to the warp's shared-memory slot: the candidate loop reads it
+    // from there, which keeps the loop's registers few
+    {
+        RelocCtx rr;
+        reloc_setup<TW>(C, cu, rr);
+        __syncwarp();
+        if (lane == 0) tc->r = rr;
+        __syncwarp();
+    }
+    const RelocCtx &r = tc->r;
     const int dA1 = r.A1.dist - r.oldA.dist, dA2 = r.A2.dist - r.oldA.dist;
     const float pen1 = pen_lo(C, r.A1.tw - r.oldA.tw, r.A1.lex - r.oldA.lex, r.A1.dex - r.oldA.dex,
                               r.LA == 1 ? r.dV_empty : 0);
@@ -1185,10 +1200,16 @@ __device__ void eval_relocate_full(const Ctx &C, int cu, int lane, Best &b, int 
 }
 
 template <bool TW>
-__device__ void eval_swap_full(const Ctx &C, int cu, int lane, Best &b, int *wl, int part, int wpc) {
+__device__ void eval_swap_full(const Ctx &C, int cu, int lane, Best &b, int *wl, int part, int wpc, TileCtx *tc) {
     const DevInst &I = C.I;
-    SwapCtx w;
-    swap_setup<TW>(C, cu, w);
+    {
+        SwapCtx ww;
+        swap_setup<TW>(C, cu, ww);
+        __syncwarp();
+        if (lane == 0) tc->w = ww;
+        __syncwarp();
+    }
+    const SwapCtx &w = tc->w;
     // u's route without seq(u) of one or two customers: the base of the insertion bound on u's
     // route; v's route without seq(v) (from v's link record) is the base on v's route
     const RT A1 = rt_of(join_opt<TW>(C, w.PU, w.pu, w.su), I);
@@ -1306,10 +1327,16 @@ __device__ void eval_swap_full(const Ctx &C, int cu, int lane, Best &b, int *wl,
 }
 
 template <bool TW>
-__device__ void eval_2optstar_full(const Ctx &C, int cu, int lane, Best &b, int *wl, int part, int wpc) {
+__device__ void eval_2optstar_full(const Ctx &C, int cu, int lane, Best &b, int *wl, int part, int wpc, TileCtx *tc) {
     const DevInst &I = C.I;
-    O2Ctx o;
-    o2_setup<TW>(C, cu, o);
+    {
+        O2Ctx oo;
+        o2_setup<TW>(C, cu, oo);
+        __syncwarp();
+        if (lane == 0) tc->o = oo;
+        __syncwarp();
+    }
+    const O2Ctx &o = tc->o;
     // the new routes [ds_A..u] + [v..de_B] and [ds_B..pred v] + [succ u..de_A] each join two
     // existing pieces
     const bool su_none = o.su == MD_NONE;
@@ -1363,6 +1390,13 @@ __device__ void eval_2optstar_full(const Ctx &C, int cu, int lane, Best &b, int 
     __syncwarp();
 }
 
+// Whether this evaluation of the solution takes the full-neighbourhood path (k_eval_full): every
+// customer a candidate, no dump, and an operator with a bound (Relocate, Swap, 2-opt*).
+__device__ __forceinline__ bool full_path(const Ctx &C, int op) {
+    return !C.lists && !(C.flags & MD_EVAL_DUMP) &&
+           (op == MD_OP_RELOCATE || op == MD_OP_SWAP || op == MD_OP_TWO_OPT_STAR);
+}
+
 __device__ __forceinline__ void best_init(Best &b) {
     b.f = 0.0; b.id = MD_NO_ID; b.valid = 0; b.fx = 0; b.routes = 0; b.n = 0; b.nx = 0;
     b.dD = b.dT = b.dL = b.dU = b.dV = 0;
@@ -1371,14 +1405,14 @@ __device__ __forceinline__ void best_init(Best &b) {
 
 template <bool TW>
 __device__ __forceinline__ void eval_customer(const Ctx &C, int op, int cu, int lane, Best &b, int *wl,
-                                              int part = 0, int wpc = 1) {
+                                              int part, int wpc, TileCtx *tc) {
     switch (op) {
-    case MD_OP_RELOCATE: eval_relocate<TW>(C, cu, lane, b, wl, part, wpc); break;
-    case MD_OP_SWAP: eval_swap<TW>(C, cu, lane, b, wl, part, wpc); break;
-    case MD_OP_TWO_OPT_STAR: eval_2optstar<TW>(C, cu, lane, b, wl, part, wpc); break;
+    case MD_OP_RELOCATE: eval_relocate<TW>(C, cu, lane, b, wl, part, wpc, tc); break;
+    case MD_OP_SWAP: eval_swap<TW>(C, cu, lane, b, wl, part, wpc, tc); break;
+    case MD_OP_TWO_OPT_STAR: eval_2optstar<TW>(C, cu, lane, b, wl, part, wpc, tc); break;
     case MD_OP_DEPOT_INSERT: eval_depot_insert<TW>(C, cu, lane, b, part); break;
     case MD_OP_DEPOT_REPLACE: eval_depot_replace<TW>(C, cu, lane, b, part); break;
-    case MD_OP_TWO_OPT: eval_2opt<TW>(C, cu, lane, b, wl, part, wpc); break;
+    case MD_OP_TWO_OPT: eval_2opt<TW>(C, cu, lane, b, wl, part, wpc, tc); break;
     default: break;
     }
 }
