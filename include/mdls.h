@@ -39,7 +39,8 @@ typedef enum md_status {
     MD_ERR_CUDA = 2,     /* a CUDA runtime call failed */
     MD_ERR_CAPACITY = 3, /* a route or buffer capacity was exceeded */
     MD_ERR_TIMEOUT = 4,  /* a bounded device-side wait gave up */
-    MD_ERR_STATE = 5     /* calls made in an order the object does not allow */
+    MD_ERR_STATE = 5,    /* calls made in an order the object does not allow */
+    MD_ERR_BOUNDS = 6    /* a build with MD_DEBUG_BOUNDS found a device-side index out of range */
 } md_status;
 
 /* Instance variant flags (Section 1: MDVRP, MDVRPTW, MDOVRP). */
@@ -154,6 +155,10 @@ typedef struct md_config {
                                per touched route rebuilds it, one CTA per solution finishes);
                                -1: one CTA per solution does it all; 0: 1 when the solutions
                                have at least 256 route slots, else -1.  Same results. */
+    int32_t wait_limit;     /* persistent descent: polls without progress before one of its
+                               device-side waits gives up (the kernel then stops every CTA and
+                               the call returns MD_ERR_TIMEOUT); 0: the default, 2^22 (about a
+                               second).  Failure detection is tested with a budget of 1. */
 } md_config;
 
 /* Totals over all solutions of one md_descend call. */
@@ -421,6 +426,14 @@ md_status md_pruner_prune(md_pruner *pruner, md_instance *inst, int32_t k, void 
  * NULL) receives the weighted mean loss of the last epoch. */
 md_status md_pruner_train(md_pruner *pruner, md_instance *inst, const uint8_t *labels, int32_t epochs,
                           int32_t batch, float lr, float pos_weight, float *mean_loss, void *stream);
+
+/* Failure detection of the tensor-core scoring (md_pruner_score / md_pruner_prune): the number of
+ * polls a wait for the tensor cores makes before it gives up (0: every wait gives up at once);
+ * a negative value restores the default (2^20).  A wait that gives up sets the pruner's error
+ * flag, lets the MMAs in flight finish (a wait of the default length) before the CTA releases its
+ * tensor memory, and stops the CTA; the call then returns MD_ERR_TIMEOUT.  Not part of the
+ * paper's method: it exists to test that path.  MD_ERR_ARG for a null pruner. */
+md_status md_pruner_set_wait(md_pruner *pruner, int32_t polls);
 
 /* Allocation-free variant of md_eval_neighborhood + md_moves_read_leaders.  The paper has no
  * counterpart: it exists for callers that cannot call cudaMalloc (device memory budgeted up front,

@@ -235,6 +235,14 @@ extern "C" md_status md_selection_read(md_moves *m, uint64_t *ids, int32_t *coun
 
 static md_status check_err(md_solutions *s, cudaStream_t st) {
     int32_t err = 0;
+#ifdef MD_DEBUG_BOUNDS
+    MD_CUDA(cudaMemcpyAsync(&err, s->inst->d.err, sizeof(err), cudaMemcpyDeviceToHost, st));
+    MD_CUDA(cudaStreamSynchronize(st));
+    if (err) {
+        md_set_error("bounds-checked build: a device-side index was out of range");
+        return MD_ERR_BOUNDS;
+    }
+#endif
     MD_CUDA(cudaMemcpyAsync(&err, s->d.err, sizeof(err), cudaMemcpyDeviceToHost, st));
     MD_CUDA(cudaStreamSynchronize(st));
     if (err) {
@@ -342,7 +350,7 @@ extern "C" md_status md_descend(md_solutions *s, const md_config *cfg, md_stats 
     if (cfg->persistent) {
         if (!st) { md_set_error("md_descend: the persistent descent needs a stream"); return MD_ERR_ARG; }
         float ms = 0.0f;
-        r = md_descend_persistent(s, m, eflags, cfg->max_pass * cfg->n_ops, st, cfg->time_eval != 0, &ms);
+        r = md_descend_persistent(s, m, eflags, cfg->max_pass * cfg->n_ops, cfg->wait_limit, st, cfg->time_eval != 0, &ms);
         if (r != MD_OK) return r;
         r = check_err(s, st);
         if (r != MD_OK) return r;

@@ -73,14 +73,14 @@ struct Ctx {
 union TileCtx;  // a warp's customer context in shared memory (below)
 
 __device__ __forceinline__ int cost(const DevInst &I, int a, int b) {
-    return __ldg(&I.dist[(size_t)a * I.nn + b]);
+    return __ldg(&I.dist[md_ix(I.err, (size_t)a * I.nn + b, (size_t)I.nn * I.nn)]);
 }
 
 // c(a, b) read from row b.  The matrix is symmetric (Euclidean, Eq. 1), so every arc is read
 // from the row of the node that is the same for all lanes of the warp (u and the nodes of its
 // route): a warp's reads then fall in one row, contiguous when the candidates are consecutive.
 __device__ __forceinline__ int cost_t(const DevInst &I, int a, int b) {
-    return __ldg(&I.dist[(size_t)b * I.nn + a]);
+    return __ldg(&I.dist[md_ix(I.err, (size_t)b * I.nn + a, (size_t)I.nn * I.nn)]);
 }
 
 __device__ __forceinline__ RT rt_of(const Seg &g, const DevInst &I) {
@@ -99,14 +99,14 @@ __device__ __forceinline__ RT rt_zero() {
 }
 
 __device__ __forceinline__ Seg8 pre8(const Ctx &C, int n) {
-    return ld_seg8(&C.D.cpre[(size_t)C.s * C.I.nc + (n - C.I.nd)]);
+    return ld_seg8(&C.D.cpre[(size_t)C.s * C.I.nc + md_ix(C.I.err, n - C.I.nd, C.I.nc)]);
 }
 
 __device__ __forceinline__ Seg8 suf8(const Ctx &C, int n) {
-    return ld_seg8(&C.D.csuf[(size_t)C.s * C.I.nc + (n - C.I.nd)]);
+    return ld_seg8(&C.D.csuf[(size_t)C.s * C.I.nc + md_ix(C.I.err, n - C.I.nd, C.I.nc)]);
 }
 
-__device__ __forceinline__ Seg nseg(const Ctx &C, int n) { return node_seg(__ldg(&C.I.node[n])); }
+__device__ __forceinline__ Seg nseg(const Ctx &C, int n) { return node_seg(__ldg(&C.I.node[md_ix(C.I.err, n, C.I.nn)])); }
 
 // Summary of the route up to and including node n (n may be the route's departure depot).
 __device__ __forceinline__ Seg prefix_through(const Ctx &C, int n) {
@@ -281,12 +281,14 @@ __device__ __forceinline__ SN sn_suffix(const Ctx &C, int n) {
 // The customers from c's position to t positions later (sub_fwd) or earlier (sub_bwd) on c's
 // route, from the subsequence tables the route rebuild keeps.
 __device__ __forceinline__ SN sub_fwd(const Ctx &C, int c, int t) {
-    const Seg8 e = ld_seg8(&C.D.csubf[((size_t)C.s * C.I.nc + (c - C.I.nd)) * C.D.K + t]);
+    const Seg8 e = ld_seg8(&C.D.csubf[((size_t)C.s * C.I.nc + md_ix(C.I.err, c - C.I.nd, C.I.nc)) * C.D.K +
+                                      md_ix(C.I.err, t, C.D.K)]);
     return sn(seg_of(e), e.a, e.b);
 }
 
 __device__ __forceinline__ SN sub_bwd(const Ctx &C, int c, int t) {
-    const Seg8 e = ld_seg8(&C.D.csubb[((size_t)C.s * C.I.nc + (c - C.I.nd)) * C.D.K + t]);
+    const Seg8 e = ld_seg8(&C.D.csubb[((size_t)C.s * C.I.nc + md_ix(C.I.err, c - C.I.nd, C.I.nc)) * C.D.K +
+                                      md_ix(C.I.err, t, C.D.K)]);
     return sn(seg_of(e), e.a, e.b);
 }
 
@@ -305,9 +307,9 @@ __device__ __forceinline__ void split_candidates(const Ctx &C, int cu, int u, in
         bool inter = false, intra = false;
         int v = 0;
         if (i < ncand) {
-            v = C.lists ? __ldg(&I.nbr[(size_t)cu * I.theta + i]) : I.nd + i;
+            v = C.lists ? __ldg(&I.nbr[md_ix(I.err, (size_t)cu * I.theta + i, (size_t)I.nc * I.theta)]) : I.nd + i;
             if (v != u) {
-                const int B = C.D.cpre[(size_t)C.s * I.nc + (v - I.nd)].a;
+                const int B = C.D.cpre[md_ix(C.I.err, (size_t)C.s * I.nc + (v - I.nd), (size_t)C.D.S * C.I.nc)].a;
                 inter = B != A;
                 intra = want_intra && B == A;
             }
@@ -338,9 +340,9 @@ __device__ void eval_relocate(const Ctx &C, int cu, int lane, Best &b, int *wl, 
     const Seg8 Pu = pre8(C, u), Su = suf8(C, u);
     const int A = Pu.a, p = Pu.b, pu = Su.a, su = Su.b;
     const size_t sA = (size_t)C.s * C.D.R + A;
-    const int4 hA = C.D.rhdr[sA];
+    const int4 hA = C.D.rhdr[md_ix(C.I.err, sA, (size_t)C.D.S * C.D.R)];
     const int LA = hA.x, dsA = hA.y, deA = hA.z;
-    const RT oldA = rt_of(seg_of(ld_seg8(&C.D.rterm[sA])), I);
+    const RT oldA = rt_of(seg_of(ld_seg8(&C.D.rterm[md_ix(C.I.err, sA, (size_t)C.D.S * C.D.R)])), I);
     const Seg PP = prefix_through(C, pu);
     // route A without seq(u)
     const RT A1 = LA == 1 ? rt_zero() : rt_of(join_opt<TW>(C, PP, pu, su), I);
@@ -356,7 +358,7 @@ __device__ void eval_relocate(const Ctx &C, int cu, int lane, Best &b, int *wl, 
     }
     const Seg q1 = nseg(C, u);
     const int dV_empty = ((!C.open && dsA != deA) ? -1 : 0) +
-                         veh_delta(C.D.dcount[(size_t)C.s * I.nd + dsA], I.NV, -1);
+                         veh_delta(C.D.dcount[md_ix(C.I.err, (size_t)C.s * I.nd + dsA, (size_t)C.D.S * C.I.nd)], I.NV, -1);
     const int ncand = C.lists ? I.nnbr[cu] : I.nc;
     // batches of 64 candidates, or of 32 when wpc warps share the customer: warp part takes
     // every wpc-th batch
@@ -399,8 +401,8 @@ __device__ void eval_relocate(const Ctx &C, int cu, int lane, Best &b, int *wl, 
                 continue;
             }
             const size_t sB = (size_t)C.s * C.D.R + B;
-            const int dsB = C.D.rhdr[sB].y;
-            const RT oldB = rt_of(seg_of(ld_seg8(&C.D.rterm[sB])), I);
+            const int dsB = C.D.rhdr[md_ix(C.I.err, sB, (size_t)C.D.S * C.D.R)].y;
+            const RT oldB = rt_of(seg_of(ld_seg8(&C.D.rterm[md_ix(C.I.err, sB, (size_t)C.D.S * C.D.R)])), I);
             const Seg PV = seg_of(Pv);
             const bool vfirst = j == 1;
             for (int var = 0; var < 6; var++) {
@@ -454,9 +456,9 @@ __device__ void eval_swap(const Ctx &C, int cu, int lane, Best &b, int *wl, int 
     const Seg8 Pu = pre8(C, u), Su = suf8(C, u);
     const int A = Pu.a, p = Pu.b, pu = Su.a, su = Su.b;
     const size_t sA = (size_t)C.s * C.D.R + A;
-    const int4 hA = C.D.rhdr[sA];
+    const int4 hA = C.D.rhdr[md_ix(C.I.err, sA, (size_t)C.D.S * C.D.R)];
     const int dsA = hA.y;
-    const RT oldA = rt_of(seg_of(ld_seg8(&C.D.rterm[sA])), I);
+    const RT oldA = rt_of(seg_of(ld_seg8(&C.D.rterm[md_ix(C.I.err, sA, (size_t)C.D.S * C.D.R)])), I);
     const Seg PU = prefix_through(C, pu);
     const bool hasx = su >= I.nd;
     const int x = hasx ? su : -1;
@@ -514,7 +516,7 @@ __device__ void eval_swap(const Ctx &C, int cu, int lane, Best &b, int *wl, int 
                 continue;
             }
             const size_t sB = (size_t)C.s * C.D.R + B;
-            const RT oldB = rt_of(seg_of(ld_seg8(&C.D.rterm[sB])), I);
+            const RT oldB = rt_of(seg_of(ld_seg8(&C.D.rterm[md_ix(C.I.err, sB, (size_t)C.D.S * C.D.R)])), I);
             const Seg PV = prefix_through(C, pv);
             for (int var = 0; var < nvar; var++) {
                 const int ku = SW_KU[var], kv = SW_KV[var];
@@ -582,10 +584,10 @@ __device__ __forceinline__ void reloc_setup(const Ctx &C, int cu, RelocCtx &r) {
     const Seg8 Pu = pre8(C, r.u), Su = suf8(C, r.u);
     r.A = Pu.a; r.p = Pu.b; r.pu = Su.a; r.su = Su.b;
     const size_t sA = (size_t)C.s * C.D.R + r.A;
-    const int4 hA = C.D.rhdr[sA];
+    const int4 hA = C.D.rhdr[md_ix(C.I.err, sA, (size_t)C.D.S * C.D.R)];
     r.LA = hA.x; r.dsA = hA.y;
     const int deA = hA.z;
-    r.oldA = rt_of(seg_of(ld_seg8(&C.D.rterm[sA])), I);
+    r.oldA = rt_of(seg_of(ld_seg8(&C.D.rterm[md_ix(C.I.err, sA, (size_t)C.D.S * C.D.R)])), I);
     r.PP = prefix_through(C, r.pu);
     r.A1 = r.LA == 1 ? rt_zero() : rt_of(join_opt<TW>(C, r.PP, r.pu, r.su), I);
     r.has2 = r.su >= I.nd;
@@ -600,7 +602,7 @@ __device__ __forceinline__ void reloc_setup(const Ctx &C, int cu, RelocCtx &r) {
         r.q2 = join<TW>(C, nseg(C, r.u), r.u, nseg(C, r.x), r.x);
         r.q2r = join<TW>(C, nseg(C, r.x), r.x, nseg(C, r.u), r.u);
     }
-    r.dV_empty = ((!C.open && r.dsA != deA) ? -1 : 0) + veh_delta(C.D.dcount[(size_t)C.s * I.nd + r.dsA], I.NV, -1);
+    r.dV_empty = ((!C.open && r.dsA != deA) ? -1 : 0) + veh_delta(C.D.dcount[md_ix(C.I.err, (size_t)C.s * I.nd + r.dsA, (size_t)C.D.S * C.I.nd)], I.NV, -1);
     r.pad = 0;
 }
 
@@ -611,8 +613,8 @@ __device__ __forceinline__ void reloc_inter(const Ctx &C, const RelocCtx &r, int
     const Seg8 Pv = pre8(C, v), Sv = suf8(C, v);
     const int B = Pv.a, j = Pv.b, sv = Sv.b;
     const size_t sB = (size_t)C.s * C.D.R + B;
-    const int dsB = C.D.rhdr[sB].y;
-    const RT oldB = rt_of(seg_of(ld_seg8(&C.D.rterm[sB])), I);
+    const int dsB = C.D.rhdr[md_ix(C.I.err, sB, (size_t)C.D.S * C.D.R)].y;
+    const RT oldB = rt_of(seg_of(ld_seg8(&C.D.rterm[md_ix(C.I.err, sB, (size_t)C.D.S * C.D.R)])), I);
     const Seg PV = seg_of(Pv);
     const bool vfirst = j == 1;
     for (int var = 0; var < 6; var++) {
@@ -679,8 +681,8 @@ __device__ __forceinline__ void swap_setup(const Ctx &C, int cu, SwapCtx &w) {
     const Seg8 Pu = pre8(C, w.u), Su = suf8(C, w.u);
     w.A = Pu.a; w.p = Pu.b; w.pu = Su.a; w.su = Su.b;
     const size_t sA = (size_t)C.s * C.D.R + w.A;
-    w.dsA = C.D.rhdr[sA].y;
-    w.oldA = rt_of(seg_of(ld_seg8(&C.D.rterm[sA])), I);
+    w.dsA = C.D.rhdr[md_ix(C.I.err, sA, (size_t)C.D.S * C.D.R)].y;
+    w.oldA = rt_of(seg_of(ld_seg8(&C.D.rterm[md_ix(C.I.err, sA, (size_t)C.D.S * C.D.R)])), I);
     w.PU = prefix_through(C, w.pu);
     w.hasx = w.su >= I.nd;
     w.x = w.hasx ? w.su : -1;
@@ -736,7 +738,7 @@ __device__ __forceinline__ void swap_cand(const Ctx &C, const SwapCtx &w, int v,
         return;
     }
     const size_t sB = (size_t)C.s * C.D.R + B;
-    const RT oldB = rt_of(seg_of(ld_seg8(&C.D.rterm[sB])), I);
+    const RT oldB = rt_of(seg_of(ld_seg8(&C.D.rterm[md_ix(C.I.err, sB, (size_t)C.D.S * C.D.R)])), I);
     const Seg PV = prefix_through(C, pv);
     for (int var = 0; var < nvar; var++) {
         const int ku = SW_KU[var], kv = SW_KV[var];
@@ -786,8 +788,8 @@ __device__ void eval_tile_lists(const Ctx &C, int op, int c0, int cstride, Best 
             int v[2], B[2];
             for (int h = 0; h < 2; h++) {
                 const int i = 32 * h + lane;
-                v[h] = i < ncand ? __ldg(&I.nbr[(size_t)cu * I.theta + i]) : u;
-                B[h] = v[h] != u ? C.D.cpre[(size_t)C.s * I.nc + (v[h] - I.nd)].a : -1;
+                v[h] = i < ncand ? __ldg(&I.nbr[md_ix(I.err, (size_t)cu * I.theta + i, (size_t)I.nc * I.theta)]) : u;
+                B[h] = v[h] != u ? C.D.cpre[md_ix(C.I.err, (size_t)C.s * I.nc + (v[h] - I.nd), (size_t)C.D.S * C.I.nc)].a : -1;
             }
             int A;
             if (op == MD_OP_RELOCATE) {
@@ -858,10 +860,10 @@ __device__ __forceinline__ void o2_setup(const Ctx &C, int cu, O2Ctx &o) {
     o.A = Pu.a;
     o.su = Su.b;
     const size_t sA = (size_t)C.s * C.D.R + o.A;
-    const int4 hA = C.D.rhdr[sA];
+    const int4 hA = C.D.rhdr[md_ix(C.I.err, sA, (size_t)C.D.S * C.D.R)];
     o.dsA = hA.y;
     o.deA = hA.z;
-    o.oldA = rt_of(seg_of(ld_seg8(&C.D.rterm[sA])), I);
+    o.oldA = rt_of(seg_of(ld_seg8(&C.D.rterm[md_ix(C.I.err, sA, (size_t)C.D.S * C.D.R)])), I);
     o.PU = seg_of(Pu);
     o.u_last = o.su < I.nd;  // depot or MD_NONE after u
 }
@@ -874,9 +876,9 @@ __device__ __forceinline__ void o2_cand(const Ctx &C, const O2Ctx &o, int v, Bes
     const int B = Pv.a, pv = Sv.a;
     if (B == o.A) return;
     const size_t sB = (size_t)C.s * C.D.R + B;
-    const int4 hB = C.D.rhdr[sB];
+    const int4 hB = C.D.rhdr[md_ix(C.I.err, sB, (size_t)C.D.S * C.D.R)];
     const int dsB = hB.y, deB = hB.z;
-    const RT oldB = rt_of(seg_of(ld_seg8(&C.D.rterm[sB])), I);
+    const RT oldB = rt_of(seg_of(ld_seg8(&C.D.rterm[md_ix(C.I.err, sB, (size_t)C.D.S * C.D.R)])), I);
     const RT nA = rt_of(join<TW>(C, o.PU, o.u, seg_of(Sv), v), I);
     const bool b_empty = pv < I.nd && o.u_last;
     RT nB = rt_zero();
@@ -885,7 +887,7 @@ __device__ __forceinline__ void o2_cand(const Ctx &C, const O2Ctx &o, int v, Bes
     if (!C.open) {
         dV += (o.dsA != deB) + (b_empty ? 0 : (dsB != o.deA)) - (o.dsA != o.deA) - (dsB != deB);
     }
-    if (b_empty) dV += veh_delta(C.D.dcount[(size_t)C.s * I.nd + dsB], I.NV, -1);
+    if (b_empty) dV += veh_delta(C.D.dcount[md_ix(C.I.err, (size_t)C.s * I.nd + dsB, (size_t)C.D.S * C.I.nd)], I.NV, -1);
     offer(C, make_id32(o.u, v, 0), nA.dist + nB.dist - o.oldA.dist - oldB.dist, nA.tw + nB.tw - o.oldA.tw - oldB.tw,
           nA.lex + nB.lex - o.oldA.lex - oldB.lex, nA.dex + nB.dex - o.oldA.dex - oldB.dex, dV, o.A, B, b, cnt,
           false, 0.0);
@@ -933,7 +935,7 @@ __device__ void eval_2opt(const Ctx &C, int cu, int lane, Best &b, int *wl, int 
     const int u = I.nd + cu;
     const Seg8 Pu = pre8(C, u), Su = suf8(C, u);
     const int A = Pu.a, p = Pu.b, su = Su.b;
-    const Seg oldA = seg_of(ld_seg8(&C.D.rterm[(size_t)C.s * C.D.R + A]));
+    const Seg oldA = seg_of(ld_seg8(&C.D.rterm[md_ix(C.I.err, (size_t)C.s * C.D.R + A, (size_t)C.D.S * C.D.R)]));
     const int dex0 = dur_ex(oldA.dur, I.D);
     const int ncand = C.lists ? I.nnbr[cu] : I.nc;
     const int nb = wpc == 1 ? 64 : 32;
@@ -967,15 +969,15 @@ __device__ void eval_depot_insert(const Ctx &C, int cu, int lane, Best &b, int p
     const int A = Pu.a, su = Su.b;
     if (su < I.nd) return;  // u is last: only interior edges split a route
     const size_t sA = (size_t)C.s * C.D.R + A;
-    const int4 hA = C.D.rhdr[sA];
+    const int4 hA = C.D.rhdr[md_ix(C.I.err, sA, (size_t)C.D.S * C.D.R)];
     const int dsA = hA.y, deA = hA.z;
-    const RT oldA = rt_of(seg_of(ld_seg8(&C.D.rterm[sA])), I);
+    const RT oldA = rt_of(seg_of(ld_seg8(&C.D.rterm[md_ix(C.I.err, sA, (size_t)C.D.S * C.D.R)])), I);
     const Seg PU = seg_of(Pu), SX = seg_of(suf8(C, su));
     for (int d = lane; d < I.nd; d += 32) {
         const Seg r1 = C.open ? PU : join<TW>(C, PU, u, nseg(C, d), d);
         const Seg r2 = join_t<TW>(C, nseg(C, d), d, SX, su);
         const RT n1 = rt_of(r1, I), n2 = rt_of(r2, I);
-        int dV = veh_delta(C.D.dcount[(size_t)C.s * I.nd + d], I.NV, +1);
+        int dV = veh_delta(C.D.dcount[md_ix(C.I.err, (size_t)C.s * I.nd + d, (size_t)C.D.S * C.I.nd)], I.NV, +1);
         if (!C.open) dV += (dsA != d) + (d != deA) - (dsA != deA);
         sink(C, make_id32(u, d, 0), n1.dist + n2.dist - oldA.dist, n1.tw + n2.tw - oldA.tw,
              n1.lex + n2.lex - oldA.lex, n1.dex + n2.dex - oldA.dex, dV, A, A, b);
@@ -995,12 +997,12 @@ __device__ void eval_depot_replace(const Ctx &C, int cu, int lane, Best &b, int 
     if (Pu.b != 1) return;  // u must be the route's first customer
     const int A = Pu.a;
     const size_t sA = (size_t)C.s * C.D.R + A;
-    const int4 hA = C.D.rhdr[sA];
+    const int4 hA = C.D.rhdr[md_ix(C.I.err, sA, (size_t)C.D.S * C.D.R)];
     const int dsA = hA.y, deA = hA.z, cL = hA.w;
-    const RT oldA = rt_of(seg_of(ld_seg8(&C.D.rterm[sA])), I);
+    const RT oldA = rt_of(seg_of(ld_seg8(&C.D.rterm[md_ix(C.I.err, sA, (size_t)C.D.S * C.D.R)])), I);
     const Seg SU = seg_of(suf8(C, u));
     const Seg PL = seg_of(pre8(C, cL));
-    const Seg CORE = seg_of(ld_seg8(&C.D.rcore[sA]));
+    const Seg CORE = seg_of(ld_seg8(&C.D.rcore[md_ix(C.I.err, sA, (size_t)C.D.S * C.D.R)]));
     const int oldc = (!C.open && dsA != deA) ? 1 : 0;
     const int *cnt = C.D.dcount + (size_t)C.s * I.nd;
     for (int d = lane; d < I.nd; d += 32) {
@@ -1143,26 +1145,26 @@ __device__ void eval_relocate_full(const Ctx &C, int cu, int lane, Best &b, int 
                 const int aout = lk[MD_LINK * (size_t)i + 1].y;
                 const int dep = TW ? lk[MD_LINK * (size_t)i + 5].w : 0;  // earliest completion at v
                 const bool last = sv == MD_NONE;  // v ends an open route: nothing follows seq(u)
-                const int cvu = __ldg(rowU + v);
-                const int cus = last ? 0 : __ldg(rowU + sv);
+                const int cvu = __ldg(rowU + md_ix(C.I.err, v, C.I.nn));
+                const int cus = last ? 0 : __ldg(rowU + md_ix(C.I.err, sv, C.I.nn));
                 const int det1 = last ? (1 << 30) : cvu + gap1 + cus - aout;
                 const float tw1 = TW ? w1 * (float)(r.q1.tw + min(max(dep + cvu - r.q1.L, 0), det1)) : 0.0f;
                 keep = det1 < 0 || !lb_reject(b, dA1 + cvu + cus - aout, __fadd_rd(pen1, tw1));
                 if (j == 1 && !keep) {
                     // v first on its route: seq(u) also goes between the departure depot and v
                     const int ds = l0.z, ain = lk[MD_LINK * (size_t)i + 1].x;  // c(ds, v)
-                    const int eds = TW ? __ldg(&I.node[ds]).z : 0;
-                    const int cdu = __ldg(rowU + ds);
+                    const int eds = TW ? __ldg(&I.node[md_ix(C.I.err, ds, C.I.nn)]).z : 0;
+                    const int cdu = __ldg(rowU + md_ix(C.I.err, ds, C.I.nn));
                     const int d1 = cdu + gap1 + cvu - ain;
                     const float t1 = TW ? w1 * (float)(r.q1.tw + min(max(eds + cdu - r.q1.L, 0), d1)) : 0.0f;
                     keep = d1 < 0 || !lb_reject(b, dA1 + cdu + cvu - ain, __fadd_rd(pen1, t1));
                     if (two && !keep) {
-                        const int cxv = __ldg(rowX + v);
+                        const int cxv = __ldg(rowX + md_ix(C.I.err, v, C.I.nn));
                         const int d2 = cdu + gap2 + cxv - ain;
                         const float t2 = TW ? w1 * (float)(r.q2.tw + min(max(eds + cdu - r.q2.L, 0), d2)) : 0.0f;
                         keep = d2 < 0 || !lb_reject(b, dA2 + cdu + dq2 + cxv - ain, __fadd_rd(pen2, t2));
                         if (rev && !keep) {
-                            const int cdx = __ldg(rowX + ds);
+                            const int cdx = __ldg(rowX + md_ix(C.I.err, ds, C.I.nn));
                             const int d3 = cdx + gap2r + cvu - ain;
                             const float t3 = TW ? w1 * (float)(r.q2r.tw + min(max(eds + cdx - r.q2r.L, 0), d3)) : 0.0f;
                             keep = d3 < 0 || !lb_reject(b, dA2 + cdx + dq2r + cvu - ain, __fadd_rd(pen2, t3));
@@ -1170,12 +1172,12 @@ __device__ void eval_relocate_full(const Ctx &C, int cu, int lane, Best &b, int 
                     }
                 }
                 if (two && !keep) {
-                    const int cxs = last ? 0 : __ldg(rowX + sv);
+                    const int cxs = last ? 0 : __ldg(rowX + md_ix(C.I.err, sv, C.I.nn));
                     const int det2 = last ? (1 << 30) : cvu + gap2 + cxs - aout;
                     const float tw2 = TW ? w1 * (float)(r.q2.tw + min(max(dep + cvu - r.q2.L, 0), det2)) : 0.0f;
                     keep = det2 < 0 || !lb_reject(b, dA2 + cvu + dq2 + cxs - aout, __fadd_rd(pen2, tw2));
                     if (rev && !keep) {
-                        const int cvx = __ldg(rowX + v);
+                        const int cvx = __ldg(rowX + md_ix(C.I.err, v, C.I.nn));
                         const int det3 = last ? (1 << 30) : cvx + gap2r + cus - aout;
                         const float tw3 = TW ? w1 * (float)(r.q2r.tw + min(max(dep + cvx - r.q2r.L, 0), det3)) : 0.0f;
                         keep = det3 < 0 || !lb_reject(b, dA2 + cvx + dq2r + cus - aout, __fadd_rd(pen2, tw3));
@@ -1194,7 +1196,7 @@ __device__ void eval_relocate_full(const Ctx &C, int cu, int lane, Best &b, int 
     // the other customers of u's route, exactly
     const int32_t *rowA = C.D.rnodes + ((size_t)C.s * C.D.R + r.A) * C.D.K;
     for (int t = part * 32 + lane; t < r.LA; t += 32 * wpc) {
-        const int v = rowA[t];
+        const int v = rowA[md_ix(C.I.err, t, C.D.K)];
         if (v != r.u) reloc_intra<TW>(C, r, v, b);
     }
 }
@@ -1245,11 +1247,11 @@ __device__ void eval_swap_full(const Ctx &C, int cu, int lane, Best &b, int *wl,
                 if (!C.sym) {
                     // the four variants (1,1), (2,1), (1,2), (2,2) written out, sharing their arcs:
                     // seq(v) of kv customers into u's route, seq(u) of ku into v's route
-                    const int c_pu_v = __ldg(rowPU + v), c_pv_u = __ldg(rowU + pv);
+                    const int c_pu_v = __ldg(rowPU + md_ix(C.I.err, v, C.I.nn)), c_pv_u = __ldg(rowU + md_ix(C.I.err, pv, C.I.nn));
                     const bool sv_none = sv == MD_NONE, sy_none = !hasy || sy == MD_NONE;
                     const int base = c_pu_v + c_pv_u - c_pu_u - l1.x;
                     {   // (1,1)
-                        const int b1 = su_none ? 0 : __ldg(rowSU + v), d1 = sv_none ? 0 : __ldg(rowU + sv);
+                        const int b1 = su_none ? 0 : __ldg(rowSU + md_ix(C.I.err, v, C.I.nn)), d1 = sv_none ? 0 : __ldg(rowU + md_ix(C.I.err, sv, C.I.nn));
                         const int dD = base + b1 + d1 - c_u_su - l1.y;
                         const int detA = su_none ? 0 : c_pu_v + l2.x + b1 - c_pu_su;
                         const int detB = sv_none ? 0 : c_pv_u + gu1 + d1 - l3.x;
@@ -1257,7 +1259,7 @@ __device__ void eval_swap_full(const Ctx &C, int cu, int lane, Best &b, int *wl,
                         n = 1;
                     }
                     if (w.hasx) {  // (2,1)
-                        const int b2 = sx_none ? 0 : __ldg(rowSX + v), e1 = sv_none ? 0 : __ldg(rowX + sv);
+                        const int b2 = sx_none ? 0 : __ldg(rowSX + md_ix(C.I.err, v, C.I.nn)), e1 = sv_none ? 0 : __ldg(rowX + md_ix(C.I.err, sv, C.I.nn));
                         const int dD = base + b2 + e1 - c_x_sx - l1.y;
                         const int detA = sx_none ? 0 : c_pu_v + l2.x + b2 - c_pu_sx;
                         const int detB = sv_none ? 0 : c_pv_u + gu2 + e1 - l3.x;
@@ -1265,7 +1267,7 @@ __device__ void eval_swap_full(const Ctx &C, int cu, int lane, Best &b, int *wl,
                         n++;
                     }
                     if (hasy) {  // (1,2)
-                        const int f1 = su_none ? 0 : __ldg(rowSU + sv), d2 = sy_none ? 0 : __ldg(rowU + sy);
+                        const int f1 = su_none ? 0 : __ldg(rowSU + md_ix(C.I.err, sv, C.I.nn)), d2 = sy_none ? 0 : __ldg(rowU + md_ix(C.I.err, sy, C.I.nn));
                         const int dD = base + f1 + d2 - c_u_su - l1.w;
                         const int detA = su_none ? 0 : c_pu_v + l2.y + f1 - c_pu_su;
                         const int detB = sy_none ? 0 : c_pv_u + gu1 + d2 - l3.y;
@@ -1273,7 +1275,7 @@ __device__ void eval_swap_full(const Ctx &C, int cu, int lane, Best &b, int *wl,
                         n++;
                     }
                     if (w.hasx && hasy) {  // (2,2)
-                        const int f2 = sx_none ? 0 : __ldg(rowSX + sv), e2 = sy_none ? 0 : __ldg(rowX + sy);
+                        const int f2 = sx_none ? 0 : __ldg(rowSX + md_ix(C.I.err, sv, C.I.nn)), e2 = sy_none ? 0 : __ldg(rowX + md_ix(C.I.err, sy, C.I.nn));
                         const int dD = base + f2 + e2 - c_x_sx - l1.w;
                         const int detA = sx_none ? 0 : c_pu_v + l2.y + f2 - c_pu_sx;
                         const int detB = sy_none ? 0 : c_pv_u + gu2 + e2 - l3.y;
@@ -1294,10 +1296,10 @@ __device__ void eval_swap_full(const Ctx &C, int cu, int lane, Best &b, int *wl,
                     const int av = kv == 1 ? sv : sy;                   // after seq(v)
                     const bool av_none = av == MD_NONE;
                     const int quf = (ku == 2 && ru) ? w.x : w.u, qul = (ku == 2 && !ru) ? w.x : w.u;
-                    const int c_pu_qvf = __ldg(rowPU + qvf);
-                    const int c_qvl_au = au_none ? 0 : __ldg(rowAU + qvl);
-                    const int c_pv_quf = __ldg((quf == w.u ? rowU : rowX) + pv);
-                    const int c_qul_av = av_none ? 0 : __ldg((qul == w.u ? rowU : rowX) + av);
+                    const int c_pu_qvf = __ldg(rowPU + md_ix(C.I.err, qvf, C.I.nn));
+                    const int c_qvl_au = au_none ? 0 : __ldg(rowAU + md_ix(C.I.err, qvl, C.I.nn));
+                    const int c_pv_quf = __ldg((quf == w.u ? rowU : rowX) + md_ix(C.I.err, pv, C.I.nn));
+                    const int c_qul_av = av_none ? 0 : __ldg((qul == w.u ? rowU : rowX) + md_ix(C.I.err, av, C.I.nn));
                     const int dD = c_pu_qvf + c_qvl_au + c_pv_quf + c_qul_av - c_pu_u - (ku == 1 ? c_u_su : c_x_sx) -
                                    l1.x - (kv == 1 ? l1.y : l1.w);
                     // seq(v) into u's route without seq(u), seq(u) into v's route without seq(v)
@@ -1319,9 +1321,9 @@ __device__ void eval_swap_full(const Ctx &C, int cu, int lane, Best &b, int *wl,
     if (lane < nq) swap_cand<TW, false>(C, w, wl[lane], b, false);
     __syncwarp();
     const int32_t *rowA = C.D.rnodes + ((size_t)C.s * C.D.R + w.A) * C.D.K;
-    const int LA = C.D.rhdr[(size_t)C.s * C.D.R + w.A].x;
+    const int LA = C.D.rhdr[md_ix(C.I.err, (size_t)C.s * C.D.R + w.A, (size_t)C.D.S * C.D.R)].x;
     for (int t = part * 32 + lane; t < LA; t += 32 * wpc) {
-        const int v = rowA[t];
+        const int v = rowA[md_ix(C.I.err, t, C.D.K)];
         if (v != w.u) swap_cand<TW, true>(C, w, v, b);
     }
 }
@@ -1362,8 +1364,8 @@ __device__ void eval_2optstar_full(const Ctx &C, int cu, int lane, Best &b, int 
                     const int4 l1 = lk[MD_LINK * (size_t)i + 1], l2 = lk[MD_LINK * (size_t)i + 2];
                     const int4 X2 = lk[MD_LINK * (size_t)i + 5];  // [ds_B .. pred v]: tw, load, dur
                     const int4 Y1 = reinterpret_cast<const int4 *>(&csuf[i])[0];  // [v .. de_B]: dist, load, dur, tw
-                    const Seg oB = seg_of(ld_seg8(&C.D.rterm[(size_t)C.s * C.D.R + l0.x]));
-                    const int cuv = __ldg(rowU + v), cps = su_none ? 0 : __ldg(rowSU + pv);
+                    const Seg oB = seg_of(ld_seg8(&C.D.rterm[md_ix(C.I.err, (size_t)C.s * C.D.R + l0.x, (size_t)C.D.S * C.D.R)]));
+                    const int cuv = __ldg(rowU + md_ix(C.I.err, v, C.I.nn)), cps = su_none ? 0 : __ldg(rowSU + md_ix(C.I.err, pv, C.I.nn));
                     const int dD = cuv + cps - c_u_su - l1.x;
                     const int dsB = l2.z & 0xffff, deB = l2.z >> 16;
                     const int dV = C.open ? 0 : (o.dsA != deB) + (dsB != o.deA) - (o.dsA != o.deA) - (dsB != deB);

@@ -214,6 +214,8 @@ extern "C" md_status md_instance_create(const md_instance_desc *desc, md_instanc
 #define MDI(call) do { if (e == cudaSuccess) e = (call); } while (0)
     MDI(cudaMalloc(&I->dist, sizeof(int32_t) * (size_t)nn * nn));
     MDI(cudaMalloc(&I->node, sizeof(int4) * nn));
+    MDI(cudaMalloc(&I->err, sizeof(int)));
+    MDI(cudaMemset(I->err, 0, sizeof(int)));
     MDI(cudaMalloc(&dx, sizeof(double) * nn));
     MDI(cudaMalloc(&dy, sizeof(double) * nn));
     MDI(cudaMalloc(&red, sizeof(int) * 2));
@@ -243,6 +245,7 @@ extern "C" md_status md_instance_create(const md_instance_desc *desc, md_instanc
     I->max_l = max_l;
     d.dist = I->dist;
     d.node = I->node;
+    d.err = I->err;
     if (desc->theta > 0) {
         MDI(cudaMalloc(&I->nbr, sizeof(int32_t) * (size_t)nc * desc->theta));
         MDI(cudaMalloc(&I->nnbr, sizeof(int32_t) * nc));
@@ -262,7 +265,7 @@ extern "C" md_status md_instance_create(const md_instance_desc *desc, md_instanc
 #undef MDI
     if (e != cudaSuccess) {
         md_status st = md_cuda_check(e, "md_instance_create");
-        cudaFree(I->dist); cudaFree(I->node); cudaFree(I->nbr); cudaFree(I->nnbr);
+        cudaFree(I->dist); cudaFree(I->node); cudaFree(I->nbr); cudaFree(I->nnbr); cudaFree(I->err);
         free(I);
         return st;
     }
@@ -272,7 +275,7 @@ extern "C" md_status md_instance_create(const md_instance_desc *desc, md_instanc
 
 extern "C" md_status md_instance_destroy(md_instance *I) {
     if (!I) return MD_OK;
-    cudaFree(I->dist); cudaFree(I->node); cudaFree(I->nbr); cudaFree(I->nnbr);
+    cudaFree(I->dist); cudaFree(I->node); cudaFree(I->nbr); cudaFree(I->nnbr); cudaFree(I->err);
     free(I);
     return MD_OK;
 }

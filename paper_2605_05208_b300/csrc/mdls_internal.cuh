@@ -61,6 +61,7 @@ struct Seg {
 };
 
 struct DevInst {
+    int *err;  // [1] first index out of range seen by a bounds-checked (MD_DEBUG_BOUNDS) build
     int nd, nc, nn;
     int Q, NV, D;
     uint32_t variant;
@@ -157,6 +158,19 @@ struct DevMoves {
     long long dump_cap;
 };
 
+// Index i of an array of n elements.  A build with MD_DEBUG_BOUNDS checks it before the access:
+// out of range, it records MD_ERR_BOUNDS in *err (the first error stays) and returns 0, so the
+// kernel finishes and the call reports the error instead of touching memory it does not own.
+#ifdef MD_DEBUG_BOUNDS
+__device__ __forceinline__ size_t md_ix(int *err, long long i, long long n) {
+    if (i >= 0 && i < n) return (size_t)i;
+    atomicCAS(err, 0, (int)MD_ERR_BOUNDS);
+    return 0;
+}
+#else
+__device__ __forceinline__ size_t md_ix(int *, long long i, long long) { return (size_t)i; }
+#endif
+
 // ------------------------------------------------------------------------------------------
 // Segment arithmetic
 // ------------------------------------------------------------------------------------------
@@ -249,6 +263,7 @@ __device__ __forceinline__ int veh_delta(int cnt, int NV, int change) {
 
 struct md_instance {
     DevInst d;
+    int *err;  // [1] see DevInst.err
     int32_t *dist;
     int4 *node;
     int32_t *nbr;
@@ -331,6 +346,6 @@ int md_eval_blocks(const md_solutions *s);
 int md_eval_wpc_full(const md_solutions *s);
 // The whole descent of every solution in one persistent launch (persist.cu); *ms: its duration
 // when timed.
-md_status md_descend_persistent(md_solutions *s, md_moves *m, uint32_t eflags, int max_steps, cudaStream_t st,
+md_status md_descend_persistent(md_solutions *s, md_moves *m, uint32_t eflags, int max_steps, int wait_limit, cudaStream_t st,
                                 bool timed, float *ms);
 int md_eval_partials(const md_solutions *s);

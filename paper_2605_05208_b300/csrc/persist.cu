@@ -72,7 +72,9 @@ __device__ __forceinline__ void st_release(int *p, int v) {
     asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-#define PERSIST_WAIT (1 << 22)  // polls without progress (about a second) before a wait gives up
+// polls without progress (about a second) before a wait gives up, unless the caller sets a
+// budget of its own (md_config.wait_limit)
+#define PERSIST_WAIT (1 << 22)
 
 // Waits until *p == want; 0 after `limit` polls.  Used for the short waits on a queue entry
 // that a running block is writing or reading.
@@ -98,6 +100,7 @@ struct Queues {
     int *tile_count;  // [S] tiles done
     int S, T, kmax;
     int lookahead;  // queued tiles needed before a busy block claims one ahead
+    int wait;       // polls before a wait gives up
 };
 
 // Takes tile index i once it is filled (or implicit); 0 if it is not filled yet.
@@ -135,7 +138,7 @@ __device__ void try_take(const Queues &Q, const DevSols &D, NextTask &nx, long l
     const int sh = ld_relaxed(&Q.q->step_head);
     if (sh < ld_relaxed(&Q.q->step_res) && atomicCAS(&Q.q->step_head, sh, sh + 1) == sh) {
         QSlot &e = Q.sq[sh % Q.cs];
-        if (!wait_eq(&e.seq, sh, PERSIST_WAIT)) atomicExch(&Q.q->err, 1);
+        if (!wait_eq(&e.seq, sh, Q.wait)) atomicExch(&Q.q->err, 1);
         nx.kind = TK_STEP; nx.s = e.s; nx.t = Q.T; nx.k = e.k; nx.skip = 0;
         st_release(&e.consumed, sh);
         return;
@@ -156,7 +159,7 @@ __device__ void take(const Queues &Q, const DevSols &D, NextTask &nx, long long 
         if (ld_relaxed(&Q.q->ndone) >= Q.S || ld_relaxed(&Q.q->err) != 0) { nx.kind = TK_STOP; return; }
         const int pr = ld_relaxed(&Q.q->progress);
         if (pr != seen) { seen = pr; it = 0; }
-        if (++it > PERSIST_WAIT) {
+        if (++it > Q.wait) {
             atomicExch(&Q.q->err, 1);
             nx.kind = TK_STOP;
             return;
@@ -169,7 +172,7 @@ __device__ void take(const Queues &Q, const DevSols &D, NextTask &nx, long long 
 __device__ void queue_step(const Queues &Q, int s, int k) {
     const int r = atomicAdd(&Q.q->step_res, 1);
     QSlot &e = Q.sq[r % Q.cs];
-    if (r >= Q.cs && !wait_eq(&e.consumed, r - Q.cs, PERSIST_WAIT)) atomicExch(&Q.q->err, 1);
+    if (r >= Q.cs && !wait_eq(&e.consumed, r - Q.cs, Q.wait)) atomicExch(&Q.q->err, 1);
     e.s = s; e.t = Q.T; e.k = k;
     __threadfence();
     st_release(&e.seq, r);
@@ -183,7 +186,7 @@ __device__ void queue_tiles(const Queues &Q, int s, int k, int lane) {
     for (int j = lane; j < Q.T; j += 32) {
         const long long i = (long long)(r0 + j);
         QSlot &e = Q.tq[i % Q.ct];
-        if (i >= Q.ct && !wait_eq(&e.consumed, (int)(i - Q.ct), PERSIST_WAIT)) atomicExch(&Q.q->err, 1);
+        if (i >= Q.ct && !wait_eq(&e.consumed, (int)(i - Q.ct), Q.wait)) atomicExch(&Q.q->err, 1);
         e.s = s; e.t = j; e.k = k;
         __threadfence();
         st_release(&e.seq, (int)i);
@@ -285,7 +288,7 @@ k_descend_persistent(DevInst I, DevSols D, DevMoves M, uint32_t flags, int wpc_f
 
 }  // namespace
 
-md_status md_descend_persistent(md_solutions *s, md_moves *m, uint32_t eflags, int max_steps, cudaStream_t st,
+md_status md_descend_persistent(md_solutions *s, md_moves *m, uint32_t eflags, int max_steps, int wait_limit, cudaStream_t st,
                                 bool timed, float *ms) {
     const DevInst &I = s->inst->d;
     const int S = s->n_sol;
@@ -315,6 +318,7 @@ md_status md_descend_persistent(md_solutions *s, md_moves *m, uint32_t eflags, i
     // customers, thresholds of 1, 2 T, 4 T, 8 T and 16 T queued tiles were measured and 1 was
     // best (a cooperative tile claims only after its sweep, at the tile's end)
     Q.lookahead = 1;
+    Q.wait = wait_limit > 0 ? wait_limit : PERSIST_WAIT;
     Q.ct = 2 * (S * T + grid) + 64;
     Q.cs = 2 * (S + grid) + 64;
     if ((long long)S * T + (long long)max_steps * S * T >= 0x7fffffffLL) {

@@ -35,6 +35,7 @@ struct md_pruner {
     float *loss;                 // [2] summed loss, summed weight of the last training call
     int *err;                    // [1] set when a wait for the tensor cores timed out
     long long step;              // Adam step counter
+    int wait;                    // polls before a wait for the tensor cores gives up (< 0: default)
 };
 
 namespace {
@@ -195,7 +196,7 @@ __device__ __forceinline__ void tc_ld32(uint32_t taddr, float *out) {
 __global__ void __launch_bounds__(TC_ROWS) k_score_tc(DevInst I, const int32_t *lists, const int32_t *cnt, int pool,
                                                      Aux A, float horizon, const __nv_bfloat16 *w1h,
                                                      const __nv_bfloat16 *w2h, const float *P, float *scores,
-                                                     long long n_pairs, int *err) {
+                                                     long long n_pairs, int *err, int wait) {
     extern __shared__ __align__(1024) unsigned char tsm[];
     unsigned char *sX = tsm;                                  // 128 x 32
     unsigned char *sW1 = sX + TC_ROWS * PR_F * 2;             // 128 x 32
@@ -262,8 +263,11 @@ __global__ void __launch_bounds__(TC_ROWS) k_score_tc(DevInst I, const int32_t *
                        idesc, kk);
             tc_commit(&mbar);
         }
-        if (__syncthreads_or(!mbar_wait(&mbar, parity, TC_WAIT))) {
+        if (__syncthreads_or(!mbar_wait(&mbar, parity, wait))) {
+            // give up: flag it, let the MMAs in flight finish (a wait of the default length)
+            // before the TMEM they write is released, and stop
             if (tid == 0) atomicExch(err, 1);
+            mbar_wait(&mbar, parity, TC_WAIT);
             break;
         }
         parity ^= 1u;
@@ -294,8 +298,11 @@ __global__ void __launch_bounds__(TC_ROWS) k_score_tc(DevInst I, const int32_t *
                        idesc, kk);
             tc_commit(&mbar);
         }
-        if (__syncthreads_or(!mbar_wait(&mbar, parity, TC_WAIT))) {
+        if (__syncthreads_or(!mbar_wait(&mbar, parity, wait))) {
+            // give up: flag it, let the MMAs in flight finish (a wait of the default length)
+            // before the TMEM they write is released, and stop
             if (tid == 0) atomicExch(err, 1);
+            mbar_wait(&mbar, parity, TC_WAIT);
             break;
         }
         parity ^= 1u;
@@ -528,7 +535,8 @@ md_status score_pool(md_pruner *p, md_instance *inst, float *scores_d, cudaStrea
     MD_CUDA(cudaMemsetAsync(p->err, 0, sizeof(int), st));
     if (grid > 0)
         k_score_tc<<<grid, TC_ROWS, TC_SMEM, st>>>(inst->d, inst->nbr, inst->nnbr, pool, aux.a, horizon_of(inst), p->w1h,
-                                                   p->w2h, p->P, scores_d, n_pairs, p->err);
+                                                   p->w2h, p->P, scores_d, n_pairs, p->err,
+                                                   p->wait >= 0 ? p->wait : TC_WAIT);
     cudaError_t e = cudaGetLastError();
     aux.release(st);
     if (e != cudaSuccess) return md_cuda_check(e, "k_score_tc");
@@ -541,10 +549,17 @@ md_status score_pool(md_pruner *p, md_instance *inst, float *scores_d, cudaStrea
 
 }  // namespace
 
+extern "C" md_status md_pruner_set_wait(md_pruner *p, int32_t polls) {
+    if (!p) { md_set_error("md_pruner_set_wait: null pruner"); return MD_ERR_ARG; }
+    p->wait = polls < 0 ? -1 : polls;
+    return MD_OK;
+}
+
 extern "C" md_status md_pruner_create(const float *params, md_pruner **out) {
     if (!params || !out) { md_set_error("md_pruner_create: null argument"); return MD_ERR_ARG; }
     *out = nullptr;
     md_pruner *p = (md_pruner *)calloc(1, sizeof(md_pruner));
+    p->wait = -1;
     cudaError_t e = cudaSuccess;
 #define MDP(call) do { if (e == cudaSuccess) e = (call); } while (0)
     MDP(cudaMalloc(&p->P, sizeof(float) * PR_NPARAM));

@@ -1,8 +1,8 @@
 // route_build.cuh -- per-route summaries by warp scans of the sequence concatenation.
 //
 // For route [ds, c_1..c_L, de] one warp writes, for every customer c_k,
-//   cpre[c_k] = [ds, c_1..c_k]                 and {route slot, k}
-//   csuf[c_k] = [c_k..c_L, de] ([c_k..c_L] open) and {pred node, succ node (MD_NONE: none)}
+//   cpre[md_ix(I.err, c_k, (size_t)I.nc)] = [ds, c_1..c_k]                 and {route slot, k}
+//   csuf[md_ix(I.err, c_k, (size_t)I.nc)] = [c_k..c_L, de] ([c_k..c_L] open) and {pred node, succ node (MD_NONE: none)}
 //   csubf[c_k][t] = [c_k..c_{k+t}], csubb[c_k][t] = [c_{k-t}..c_k]   and {first, last node}
 // plus rterm = the whole route and rcore = [c_1..c_L].  The concatenation is associative and
 // exact in integers, so the scan tree gives the same summaries as a left-to-right fold.
@@ -44,7 +44,7 @@ __device__ __forceinline__ SegN shfl_segn(const SegN &x, int src) {
 template <bool TW>
 __device__ __forceinline__ SegN segn_cat(const DevInst &I, const SegN &a, const SegN &b) {
     SegN r;
-    r.s = seg_cat<TW>(a.s, b.s, I.dist[(size_t)a.last * I.nn + b.first]);
+    r.s = seg_cat<TW>(a.s, b.s, I.dist[md_ix(I.err, (size_t)a.last * I.nn + b.first, (size_t)I.nn * I.nn)]);
     r.first = a.first;
     r.last = b.last;
     return r;
@@ -52,7 +52,7 @@ __device__ __forceinline__ SegN segn_cat(const DevInst &I, const SegN &a, const 
 
 __device__ __forceinline__ SegN segn_node(const DevInst &I, int n) {
     SegN r;
-    r.s = node_seg(I.node[n]);
+    r.s = node_seg(I.node[md_ix(I.err, n, (size_t)I.nn)]);
     r.first = n;
     r.last = n;
     return r;
@@ -72,37 +72,37 @@ __device__ __forceinline__ void write_links(const DevInst &I, const DevSols &D, 
     const int wlex = load_ex(whole.load, I.Q), wdex = dur_ex(whole.dur, I.D);
     const bool feasible = whole.tw == 0 && wlex == 0 && wdex == 0;
     for (int k = lane; k < L; k += 32) {
-        const int c = nodes[k];
-        const int pred = k > 0 ? nodes[k - 1] : ds;
+        const int c = nodes[md_ix(I.err, k, (size_t)D.K)];
+        const int pred = k > 0 ? nodes[md_ix(I.err, k - 1, (size_t)D.K)] : ds;
         // succ: the next customer, else the arrival depot (MD_NONE after an open route's last)
-        const int succ = k + 1 < L ? nodes[k + 1] : (open ? MD_NONE : de);
-        const int succ2 = k + 2 < L ? nodes[k + 2] : (k + 2 == L && !open ? de : MD_NONE);
-        const int a_in = I.dist[(size_t)pred * I.nn + c];
-        const int a_out = succ == MD_NONE ? 0 : I.dist[(size_t)c * I.nn + succ];
-        const int a_out2 = succ2 == MD_NONE ? 0 : I.dist[(size_t)succ * I.nn + succ2];
-        const Seg cs = node_seg(I.node[c]);
+        const int succ = k + 1 < L ? nodes[md_ix(I.err, k + 1, (size_t)D.K)] : (open ? MD_NONE : de);
+        const int succ2 = k + 2 < L ? nodes[md_ix(I.err, k + 2, (size_t)D.K)] : (k + 2 == L && !open ? de : MD_NONE);
+        const int a_in = I.dist[md_ix(I.err, (size_t)pred * I.nn + c, (size_t)I.nn * I.nn)];
+        const int a_out = succ == MD_NONE ? 0 : I.dist[md_ix(I.err, (size_t)c * I.nn + succ, (size_t)I.nn * I.nn)];
+        const int a_out2 = succ2 == MD_NONE ? 0 : I.dist[md_ix(I.err, (size_t)succ * I.nn + succ2, (size_t)I.nn * I.nn)];
+        const Seg cs = node_seg(I.node[md_ix(I.err, c, (size_t)I.nn)]);
         int gap2 = 0;
         if (k + 1 < L) {
-            const Seg two = seg_cat<TW>(cs, node_seg(I.node[succ]), a_out);
+            const Seg two = seg_cat<TW>(cs, node_seg(I.node[md_ix(I.err, succ, (size_t)I.nn)]), a_out);
             gap2 = two.dur - two.tw;
         }
         // the route without c, and without c and its successor: [ds .. pred] + [after ..]
-        const Seg P = k > 0 ? seg_of(ld_seg8(&cpre[pred - I.nd])) : node_seg(I.node[ds]);
-        const int c_ps = succ == MD_NONE ? 0 : I.dist[(size_t)pred * I.nn + succ];
-        const int c_ps2 = succ2 == MD_NONE ? 0 : I.dist[(size_t)pred * I.nn + succ2];
+        const Seg P = k > 0 ? seg_of(ld_seg8(&cpre[md_ix(I.err, pred - I.nd, (size_t)I.nc)])) : node_seg(I.node[md_ix(I.err, ds, (size_t)I.nn)]);
+        const int c_ps = succ == MD_NONE ? 0 : I.dist[md_ix(I.err, (size_t)pred * I.nn + succ, (size_t)I.nn * I.nn)];
+        const int c_ps2 = succ2 == MD_NONE ? 0 : I.dist[md_ix(I.err, (size_t)pred * I.nn + succ2, (size_t)I.nn * I.nn)];
         Seg r1 = P, r2 = P;
         if (succ != MD_NONE)
-            r1 = seg_cat<TW>(P, succ < I.nd ? node_seg(I.node[succ]) : seg_of(ld_seg8(&csuf[succ - I.nd])), c_ps);
+            r1 = seg_cat<TW>(P, succ < I.nd ? node_seg(I.node[md_ix(I.err, succ, (size_t)I.nn)]) : seg_of(ld_seg8(&csuf[md_ix(I.err, succ - I.nd, (size_t)I.nc)])), c_ps);
         if (succ2 != MD_NONE && k + 1 < L)
-            r2 = seg_cat<TW>(P, succ2 < I.nd ? node_seg(I.node[succ2]) : seg_of(ld_seg8(&csuf[succ2 - I.nd])), c_ps2);
-        int4 *e = lk + (size_t)(c - I.nd) * MD_LINK;
+            r2 = seg_cat<TW>(P, succ2 < I.nd ? node_seg(I.node[md_ix(I.err, succ2, (size_t)I.nn)]) : seg_of(ld_seg8(&csuf[md_ix(I.err, succ2 - I.nd, (size_t)I.nc)])), c_ps2);
+        int4 *e = lk + md_ix(I.err, c - I.nd, I.nc) * MD_LINK;
         e[0] = make_int4(r, k + 1, pred, succ);
         e[1] = make_int4(a_in, a_out, succ2, a_out2);
         e[2] = make_int4(cs.dur, gap2, ds | (de << 16), feasible ? 1 : 0);
         e[3] = make_int4(c_ps, c_ps2, r1.tw - whole.tw, load_ex(r1.load, I.Q) - wlex);
         e[4] = make_int4(dur_ex(r1.dur, I.D) - wdex, r2.tw - whole.tw, load_ex(r2.load, I.Q) - wlex,
                          dur_ex(r2.dur, I.D) - wdex);
-        const Seg8 Pc = ld_seg8(&cpre[c - I.nd]);  // [ds .. c]
+        const Seg8 Pc = ld_seg8(&cpre[md_ix(I.err, c - I.nd, (size_t)I.nc)]);  // [ds .. c]
         e[5] = make_int4(P.tw, P.load, P.dur, Pc.E + Pc.dur - Pc.tw);
     }
 }
@@ -114,7 +114,7 @@ template <bool TW, bool SUBTABLES = true>
 __device__ void rebuild_route(const DevInst &I, const DevSols &D, int s, int r) {
     const int lane = threadIdx.x & 31;
     const size_t sr = (size_t)s * D.R + r;
-    const int4 h = D.rhdr[sr];
+    const int4 h = D.rhdr[md_ix(I.err, sr, (size_t)D.S * D.R)];
     const int L = h.x, ds = h.y, de = h.z;
     if (L <= 0) return;
     const bool open = (I.variant & MD_VARIANT_OPEN) != 0;
@@ -128,14 +128,14 @@ __device__ void rebuild_route(const DevInst &I, const DevSols &D, int s, int r) 
         // csubb[c_k][*] and ends at [c_1..c_k]; the prefix, the suffix and the route terms follow
         // with one concatenation each.
         const bool act = lane < L;
-        const int c = act ? nodes[lane] : nodes[0];
-        const Seg cs = node_seg(I.node[c]);
+        const int c = act ? nodes[md_ix(I.err, lane, (size_t)D.K)] : nodes[md_ix(I.err, 0, (size_t)D.K)];
+        const Seg cs = node_seg(I.node[md_ix(I.err, c, (size_t)I.nn)]);
         const int prev = __shfl_up_sync(0xffffffffu, c, 1);
         const int nextc = __shfl_down_sync(0xffffffffu, c, 1);
-        const int arc = lane > 0 ? I.dist[(size_t)prev * I.nn + c] : 0;  // arc into position lane
+        const int arc = lane > 0 ? I.dist[md_ix(I.err, (size_t)prev * I.nn + c, (size_t)I.nn * I.nn)] : 0;  // arc into position lane
         const int arc_out = __shfl_down_sync(0xffffffffu, arc, 1);       // arc out of it
         const int cL = __shfl_sync(0xffffffffu, c, L - 1);
-        const size_t row = ((size_t)s * I.nc + (c - I.nd)) * D.K;
+        const size_t row = ((size_t)s * I.nc + md_ix(I.err, c - I.nd, I.nc)) * D.K;
         Seg8 *F = D.csubf + row;
         Seg8 *Bk = D.csubb + row;
         // the forward and the backward fold advance together: two independent chains per lane
@@ -159,23 +159,23 @@ __device__ void rebuild_route(const DevInst &I, const DevSols &D, int s, int r) 
                 st_seg8(&Bk[t], gb, xb.first, c);
             }
         }
-        const Seg sds = node_seg(I.node[ds]);
-        const Seg pre = seg_cat<TW>(sds, gb, I.dist[(size_t)ds * I.nn + __shfl_sync(0xffffffffu, c, 0)]);
-        const Seg sde = node_seg(I.node[de]);
-        const int arc_de = I.dist[(size_t)cL * I.nn + de];
+        const Seg sds = node_seg(I.node[md_ix(I.err, ds, (size_t)I.nn)]);
+        const Seg pre = seg_cat<TW>(sds, gb, I.dist[md_ix(I.err, (size_t)ds * I.nn + __shfl_sync(0xffffffffu, c, 0), (size_t)I.nn * I.nn)]);
+        const Seg sde = node_seg(I.node[md_ix(I.err, de, (size_t)I.nn)]);
+        const int arc_de = I.dist[md_ix(I.err, (size_t)cL * I.nn + de, (size_t)I.nn * I.nn)];
         const Seg suf = open ? gf : seg_cat<TW>(gf, sde, arc_de);
         if (act) {
-            st_seg8(&cpre[c - I.nd], pre, r, lane + 1);
-            st_seg8(&csuf[c - I.nd], suf, lane == 0 ? ds : prev,
+            st_seg8(&cpre[md_ix(I.err, c - I.nd, (size_t)I.nc)], pre, r, lane + 1);
+            st_seg8(&csuf[md_ix(I.err, c - I.nd, (size_t)I.nc)], suf, lane == 0 ? ds : prev,
                     lane == L - 1 ? (open ? MD_NONE : de) : nextc);
         }
         // lane 0: gf = [c_1..c_L], pre = [ds, c_1]; the whole route is ds + gf (+ de)
-        const Seg head = seg_cat<TW>(sds, gf, I.dist[(size_t)ds * I.nn + c]);
+        const Seg head = seg_cat<TW>(sds, gf, I.dist[md_ix(I.err, (size_t)ds * I.nn + c, (size_t)I.nn * I.nn)]);
         Seg whole = open ? head : seg_cat<TW>(head, sde, arc_de);
         if (lane == 0) {
-            st_seg8(&D.rterm[sr], whole, ds, open ? cL : de);
-            st_seg8(&D.rcore[sr], gf, c, cL);
-            D.rhdr[sr] = make_int4(L, ds, de, cL);
+            st_seg8(&D.rterm[md_ix(I.err, sr, (size_t)D.S * D.R)], whole, ds, open ? cL : de);
+            st_seg8(&D.rcore[md_ix(I.err, sr, (size_t)D.S * D.R)], gf, c, cL);
+            D.rhdr[md_ix(I.err, sr, (size_t)D.S * D.R)] = make_int4(L, ds, de, cL);
         }
         whole.dist = __shfl_sync(0xffffffffu, whole.dist, 0);
         whole.load = __shfl_sync(0xffffffffu, whole.load, 0);
@@ -192,7 +192,7 @@ __device__ void rebuild_route(const DevInst &I, const DevSols &D, int s, int r) 
     for (int base = 0; base < L; base += 32) {
         const int k = base + lane;
         const bool act = k < L;
-        const int n = act ? nodes[k] : nodes[L - 1];
+        const int n = act ? nodes[md_ix(I.err, k, (size_t)D.K)] : nodes[md_ix(I.err, L - 1, (size_t)D.K)];
         SegN x = segn_node(I, n);
         for (int off = 1; off < 32; off <<= 1) {
             SegN y = shfl_up_segn(x, off);
@@ -201,7 +201,7 @@ __device__ void rebuild_route(const DevInst &I, const DevSols &D, int s, int r) 
         const int tail = min(31, L - 1 - base);
         SegN chunk = shfl_segn(x, tail);
         SegN p = segn_cat<TW>(I, carry, x);
-        if (act) st_seg8(&cpre[n - I.nd], p.s, r, k + 1);
+        if (act) st_seg8(&cpre[md_ix(I.err, n - I.nd, (size_t)I.nc)], p.s, r, k + 1);
         carry = shfl_segn(p, tail);
         core = have_core ? segn_cat<TW>(I, core, chunk) : chunk;
         have_core = true;
@@ -213,7 +213,7 @@ __device__ void rebuild_route(const DevInst &I, const DevSols &D, int s, int r) 
     for (int end = L; end > 0; end -= 32) {
         const int k = end - 1 - lane;
         const bool act = k >= 0;
-        const int n = act ? nodes[k] : nodes[0];
+        const int n = act ? nodes[md_ix(I.err, k, (size_t)D.K)] : nodes[md_ix(I.err, 0, (size_t)D.K)];
         SegN x = segn_node(I, n);
         for (int off = 1; off < 32; off <<= 1) {
             SegN y = shfl_up_segn(x, off);
@@ -221,9 +221,9 @@ __device__ void rebuild_route(const DevInst &I, const DevSols &D, int s, int r) 
         }
         SegN sfx = have_rc ? segn_cat<TW>(I, x, rc) : x;
         if (act) {
-            const int pred = k == 0 ? ds : nodes[k - 1];
-            const int succ = k == L - 1 ? (open ? MD_NONE : de) : nodes[k + 1];
-            st_seg8(&csuf[n - I.nd], sfx.s, pred, succ);
+            const int pred = k == 0 ? ds : nodes[md_ix(I.err, k - 1, (size_t)D.K)];
+            const int succ = k == L - 1 ? (open ? MD_NONE : de) : nodes[md_ix(I.err, k + 1, (size_t)D.K)];
+            st_seg8(&csuf[md_ix(I.err, n - I.nd, (size_t)I.nc)], sfx.s, pred, succ);
         }
         const int tail = min(31, end - 1);
         rc = shfl_segn(sfx, tail);
@@ -234,18 +234,18 @@ __device__ void rebuild_route(const DevInst &I, const DevSols &D, int s, int r) 
     for (int base = 0; SUBTABLES && base < L; base += 32) {
         const int k0 = base + lane;  // 0-based position
         if (k0 >= L) break;
-        const int c = nodes[k0];
-        const size_t row = ((size_t)s * I.nc + (c - I.nd)) * D.K;
+        const int c = nodes[md_ix(I.err, k0, (size_t)D.K)];
+        const size_t row = ((size_t)s * I.nc + md_ix(I.err, c - I.nd, I.nc)) * D.K;
         Seg8 *F = D.csubf + row;
         Seg8 *Bk = D.csubb + row;
-        const Seg cs = node_seg(I.node[c]);
+        const Seg cs = node_seg(I.node[md_ix(I.err, c, (size_t)I.nn)]);
         Seg g = cs;
         int last = c;
         st_seg8(&F[0], g, c, c);
 #pragma unroll 4
         for (int t = 1; k0 + t < L; t++) {
-            const int m = nodes[k0 + t];
-            g = seg_cat<TW>(g, node_seg(I.node[m]), I.dist[(size_t)last * I.nn + m]);
+            const int m = nodes[md_ix(I.err, k0 + t, (size_t)D.K)];
+            g = seg_cat<TW>(g, node_seg(I.node[md_ix(I.err, m, (size_t)I.nn)]), I.dist[md_ix(I.err, (size_t)last * I.nn + m, (size_t)I.nn * I.nn)]);
             last = m;
             st_seg8(&F[t], g, c, m);
         }
@@ -254,8 +254,8 @@ __device__ void rebuild_route(const DevInst &I, const DevSols &D, int s, int r) 
         st_seg8(&Bk[0], g, c, c);
 #pragma unroll 4
         for (int t = 1; k0 - t >= 0; t++) {
-            const int m = nodes[k0 - t];
-            g = seg_cat<TW>(node_seg(I.node[m]), g, I.dist[(size_t)m * I.nn + first]);
+            const int m = nodes[md_ix(I.err, k0 - t, (size_t)D.K)];
+            g = seg_cat<TW>(node_seg(I.node[md_ix(I.err, m, (size_t)I.nn)]), g, I.dist[md_ix(I.err, (size_t)m * I.nn + first, (size_t)I.nn * I.nn)]);
             first = m;
             st_seg8(&Bk[t], g, m, c);
         }
@@ -263,9 +263,9 @@ __device__ void rebuild_route(const DevInst &I, const DevSols &D, int s, int r) 
     // carry and core are the same on every lane (shuffled from one lane)
     SegN whole = open ? carry : segn_cat<TW>(I, carry, segn_node(I, de));
     if (lane == 0) {
-        st_seg8(&D.rterm[sr], whole.s, ds, whole.last);
-        st_seg8(&D.rcore[sr], core.s, core.first, core.last);
-        D.rhdr[sr] = make_int4(L, ds, de, nodes[L - 1]);
+        st_seg8(&D.rterm[md_ix(I.err, sr, (size_t)D.S * D.R)], whole.s, ds, whole.last);
+        st_seg8(&D.rcore[md_ix(I.err, sr, (size_t)D.S * D.R)], core.s, core.first, core.last);
+        D.rhdr[md_ix(I.err, sr, (size_t)D.S * D.R)] = make_int4(L, ds, de, nodes[md_ix(I.err, L - 1, (size_t)D.K)]);
     }
     write_links<TW>(I, D, s, r, nodes, L, ds, de, open, whole.s);
 }

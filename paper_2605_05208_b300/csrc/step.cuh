@@ -76,7 +76,7 @@ __device__ int select_moves(const DevInst &I, const DevSols &D, const DevMoves &
         if (valid) {
             s_rA = (int)(rt & 0xffffu);  // the leader's routes, as the evaluation recorded them
             s_rB = (int)(rt >> 16);
-            M.sel[(size_t)s * R] = id;
+            M.sel[md_ix(I.err, (size_t)s * R, (size_t)D.S * D.R)] = id;
             s_n = 1;
         }
     }
@@ -91,8 +91,8 @@ __device__ int select_moves(const DevInst &I, const DevSols &D, const DevMoves &
     const uint32_t *fl = M.flist + (size_t)s * M.ncap;
     for (int e = tid; e < nf; e += nt) {
         const uint32_t pair = fl[e];
-        const unsigned long long key = M.foltab[tab + pair];
-        M.foltab[tab + pair] = MD_EMPTY_KEY;
+        const unsigned long long key = M.foltab[md_ix(I.err, tab + pair, (size_t)D.S * D.R * D.R)];
+        M.foltab[md_ix(I.err, tab + pair, (size_t)D.S * D.R * D.R)] = MD_EMPTY_KEY;
         if (!use) continue;
         const int i = (int)(pair / (uint32_t)R), j = (int)(pair % (uint32_t)R);
         if (i == s_rA || i == s_rB || j == s_rA || j == s_rB) continue;  // blocked by the leader
@@ -107,21 +107,21 @@ __device__ int select_moves(const DevInst &I, const DevSols &D, const DevMoves &
         return have_leader;
     }
     const int ncand = min(s_ncand, M.ncap);
-    for (int r = tid; r < R; r += nt) sm.claimed[r] = 0;
+    for (int r = tid; r < R; r += nt) sm.claimed[md_ix(I.err, r, D.R)] = 0;
     __syncthreads();
-    if (tid == 0) { sm.claimed[s_rA] = 1; sm.claimed[s_rB] = 1; }
+    if (tid == 0) { sm.claimed[md_ix(I.err, s_rA, D.R)] = 1; sm.claimed[md_ix(I.err, s_rB, D.R)] = 1; }
     __syncthreads();
     for (int round = 0; round <= ncand; round++) {
-        for (int r = tid; r < R; r += nt) sm.rmin[r] = MD_EMPTY_KEY;
+        for (int r = tid; r < R; r += nt) sm.rmin[md_ix(I.err, r, D.R)] = MD_EMPTY_KEY;
         __syncthreads();
         int alive = 0;
         for (int k = tid; k < ncand; k += nt) {
             const unsigned long long key = ck[k];
             if (key == MD_EMPTY_KEY) continue;
             const int i = cr[k] & 0xffff, j = cr[k] >> 16;
-            if (sm.claimed[i] || sm.claimed[j]) { ck[k] = MD_EMPTY_KEY; continue; }
-            atomicMin(&sm.rmin[i], key);
-            atomicMin(&sm.rmin[j], key);
+            if (sm.claimed[md_ix(I.err, i, D.R)] || sm.claimed[md_ix(I.err, j, D.R)]) { ck[k] = MD_EMPTY_KEY; continue; }
+            atomicMin(&sm.rmin[md_ix(I.err, i, D.R)], key);
+            atomicMin(&sm.rmin[md_ix(I.err, j, D.R)], key);
             alive = 1;
         }
         __syncthreads();
@@ -129,11 +129,11 @@ __device__ int select_moves(const DevInst &I, const DevSols &D, const DevMoves &
             const unsigned long long key = ck[k];
             if (key == MD_EMPTY_KEY) continue;
             const int i = cr[k] & 0xffff, j = cr[k] >> 16;
-            if (sm.rmin[i] == key && sm.rmin[j] == key) {
+            if (sm.rmin[md_ix(I.err, i, D.R)] == key && sm.rmin[md_ix(I.err, j, D.R)] == key) {
                 const int n = atomicAdd(&s_n, 1);
-                M.sel[(size_t)s * R + n] = (uint32_t)(key & 0xffffffffu);
-                sm.claimed[i] = 1;
-                sm.claimed[j] = 1;
+                M.sel[md_ix(I.err, (size_t)s * R + n, (size_t)D.S * D.R)] = (uint32_t)(key & 0xffffffffu);
+                sm.claimed[md_ix(I.err, i, D.R)] = 1;
+                sm.claimed[md_ix(I.err, j, D.R)] = 1;
                 ck[k] = MD_EMPTY_KEY;
             }
         }
@@ -172,18 +172,18 @@ __device__ void apply_one(const DevInst &I, const DevSols &D, int s, int op, uin
     const int lane = threadIdx.x & 31;
     const int u = (id >> 18) & 0x3fff, v = (id >> 4) & 0x3fff, var = id & 0xf;
     const int K = D.K;
-    const Seg8 Pu = D.cpre[(size_t)s * I.nc + (u - I.nd)];
+    const Seg8 Pu = D.cpre[md_ix(I.err, (size_t)s * I.nc + (u - I.nd), (size_t)D.S * I.nc)];
     const int A = Pu.a, p = Pu.b;
     const size_t sA = (size_t)s * D.R + A;
-    const int4 hA = D.rhdr[sA];
+    const int4 hA = D.rhdr[md_ix(I.err, sA, (size_t)D.S * D.R)];
     const int LA = hA.x;
     int B = A, j = 0, LB = 0;
     int4 hB = hA;
     if (op <= MD_OP_TWO_OPT_STAR || op == MD_OP_TWO_OPT) {
-        const Seg8 Pv = D.cpre[(size_t)s * I.nc + (v - I.nd)];
+        const Seg8 Pv = D.cpre[md_ix(I.err, (size_t)s * I.nc + (v - I.nd), (size_t)D.S * I.nc)];
         B = Pv.a;
         j = Pv.b;
-        hB = D.rhdr[(size_t)s * D.R + B];
+        hB = D.rhdr[md_ix(I.err, (size_t)s * D.R + B, (size_t)D.S * D.R)];
         LB = hB.x;
     }
     int *stA = stage, *stB = stage + K;
@@ -212,7 +212,7 @@ __device__ void apply_one(const DevInst &I, const DevSols &D, int s, int op, uin
         nA = p;
         nN = LA - p;
         if (rank >= nfree) { if (lane == 0) set_err(D, MD_ERR_CAPACITY); return; }
-        newslot = sm.free_slots[rank];
+        newslot = sm.free_slots[md_ix(I.err, rank, D.R)];
     } else {
         nA = LA;
     }
@@ -293,19 +293,19 @@ __device__ void apply_one(const DevInst &I, const DevSols &D, int s, int op, uin
     __syncwarp();
     if (lane == 0) {
         if (op == MD_OP_DEPOT_INSERT) {
-            D.rhdr[sA] = make_int4(nA, dsA, v, 0);
-            D.rhdr[(size_t)s * D.R + newslot] = make_int4(nN, v, deA, 0);
+            D.rhdr[md_ix(I.err, sA, (size_t)D.S * D.R)] = make_int4(nA, dsA, v, 0);
+            D.rhdr[md_ix(I.err, (size_t)s * D.R + newslot, (size_t)D.S * D.R)] = make_int4(nN, v, deA, 0);
             int t = atomicAdd(s_ntouch, 2);
-            sm.touched[t] = A;
-            sm.touched[t + 1] = newslot;
+            sm.touched[md_ix(I.err, t, D.R)] = A;
+            sm.touched[md_ix(I.err, t + 1, D.R)] = newslot;
         } else {
-            D.rhdr[sA] = make_int4(nA, dsA, deA, 0);
+            D.rhdr[md_ix(I.err, sA, (size_t)D.S * D.R)] = make_int4(nA, dsA, deA, 0);
             int t = atomicAdd(s_ntouch, 1);
-            sm.touched[t] = A;
+            sm.touched[md_ix(I.err, t, D.R)] = A;
             if (B != A) {
-                D.rhdr[(size_t)s * D.R + B] = make_int4(nB, dsB, deB, 0);
+                D.rhdr[md_ix(I.err, (size_t)s * D.R + B, (size_t)D.S * D.R)] = make_int4(nB, dsB, deB, 0);
                 t = atomicAdd(s_ntouch, 1);
-                sm.touched[t] = B;
+                sm.touched[md_ix(I.err, t, D.R)] = B;
             }
         }
     }
@@ -350,7 +350,7 @@ __device__ void apply_selection(const DevInst &I, const DevSols &D, const DevMov
         apply_one(I, D, s, op, id, rank, sm, s_nfree, &s_ntouch, sm.stage + (size_t)warp * 2 * D.K);
     }
     __syncthreads();
-    for (int k = warp; k < s_ntouch; k += nwarps) rebuild_route<TW>(I, D, s, sm.touched[k]);
+    for (int k = warp; k < s_ntouch; k += nwarps) rebuild_route<TW>(I, D, s, sm.touched[md_ix(I.err, k, D.R)]);
     __syncthreads();
     solution_totals(I, D, s, sm.cnt, false);
 }

@@ -15,9 +15,10 @@ from dataclasses import dataclass
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libmdls.so")
+# the library; MDLS_LIBRARY selects another build of it (the bounds-checked libmdls_bounds.so)
+LIB_PATH = os.environ.get("MDLS_LIBRARY") or os.path.join(_HERE, "libmdls.so")
 
-MD_OK, MD_ERR_ARG, MD_ERR_CUDA, MD_ERR_CAPACITY, MD_ERR_TIMEOUT, MD_ERR_STATE = range(6)
+MD_OK, MD_ERR_ARG, MD_ERR_CUDA, MD_ERR_CAPACITY, MD_ERR_TIMEOUT, MD_ERR_STATE, MD_ERR_BOUNDS = range(7)
 VARIANT_TW, VARIANT_OPEN, VARIANT_SYMMETRIC = 1, 2, 4
 OP_RELOCATE, OP_SWAP, OP_TWO_OPT_STAR, OP_DEPOT_INSERT, OP_DEPOT_REPLACE, OP_TWO_OPT = range(6)
 N_OPS = 5      # the operators of the benchmark configurations
@@ -37,7 +38,7 @@ EXPORTED = (
     "md_batch_descend", "md_instance_build_neighbors",
     "md_instance_set_neighbors", "md_pruner_create", "md_pruner_destroy", "md_pruner_params",
     "md_pruner_features", "md_pruner_score", "md_pruner_prune", "md_pruner_train",
-    "md_repair_insert",
+    "md_pruner_set_wait", "md_repair_insert",
 )
 INSERT_FBI, INSERT_IBI, INSERT_FRI, INSERT_IRI = 0, 1, 2, 3  # repair insertion rules (Section 3.3)
 
@@ -75,7 +76,8 @@ class Config(C.Structure):
                 ("lambda0", C.POINTER(C.c_float)), ("multi_move", C.c_int32),
                 ("lambda_update", C.c_int32), ("use_graph", C.c_int32), ("poll_every", C.c_int32),
                 ("op_perm_device", C.c_int32), ("time_eval", C.c_int32), ("n_groups", C.c_int32),
-                ("sweep_every", C.c_int32), ("persistent", C.c_int32), ("wide_step", C.c_int32)]
+                ("sweep_every", C.c_int32), ("persistent", C.c_int32), ("wide_step", C.c_int32),
+                ("wait_limit", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -133,6 +135,7 @@ def lib() -> C.CDLL:
             "md_pruner_score": [P, P, P, P],
             "md_pruner_prune": [P, P, C.c_int32, P],
             "md_pruner_train": [P, P, P, C.c_int32, C.c_int32, C.c_float, C.c_float, P, P],
+            "md_pruner_set_wait": [P, C.c_int32],
             "md_batch_create": [P, C.c_int32, PP],
             "md_batch_destroy": [P],
             "md_batch_tune": [P, P],
@@ -343,12 +346,13 @@ class Solutions:
     def descend(self, perm, max_pass: int, multi: bool = True, lambda_update: bool = False,
                 lambda0=None, use_graph: bool = False, poll_every: int = 1, stream=None,
                 n_ops: int | None = None, time_eval: bool = False, n_groups: int = 1,
-                sweep_every: int = 0, persistent: bool = False, wide_step: int = 0) -> DescendStats:
+                sweep_every: int = 0, persistent: bool = False, wide_step: int = 0,
+                wait_limit: int = 0) -> DescendStats:
         """MDFIS descent.  perm: uint8 host array [n_sol, >= max_pass, n_ops], or an int device
         pointer to a [n_sol, max_pass, n_ops] uint8 buffer (then n_ops must be given).
         persistent: the whole descent in one persistent launch.  wide_step: md_config.wide_step
         (1: each step's apply and rebuild spread over the grid, -1: one CTA per solution, 0: by
-        the number of route slots)."""
+        the number of route slots).  wait_limit: md_config.wait_limit (0: the default)."""
         if isinstance(perm, int):
             assert n_ops is not None
             pptr, on_dev = C.cast(C.c_void_p(perm), C.POINTER(C.c_uint8)), 1
@@ -362,7 +366,8 @@ class Solutions:
         cfg = Config(n_ops, max_pass, pptr,
                      lam.ctypes.data_as(C.POINTER(C.c_float)) if lam is not None else None,
                      int(multi), int(lambda_update), int(use_graph), int(poll_every), on_dev,
-                     int(time_eval), int(n_groups), int(sweep_every), int(persistent), int(wide_step))
+                     int(time_eval), int(n_groups), int(sweep_every), int(persistent), int(wide_step),
+                     int(wait_limit))
         st = Stats()
         _check(lib().md_descend(self.h, C.byref(cfg), C.byref(st), _stream(stream)))
         return DescendStats(st.moves_scored, st.steps, st.accepted_steps, st.applied_moves,
@@ -522,6 +527,10 @@ class Pruner:
         out = np.zeros(PRUNER_PARAMS, dtype=np.float32)
         _check(lib().md_pruner_params(self.h, _ptr(out)))
         return out
+
+    def set_wait(self, polls: int):
+        """md_pruner_set_wait: polls before a wait for the tensor cores gives up (< 0: default)."""
+        _check(lib().md_pruner_set_wait(self.h, int(polls)))
 
     def features(self, inst: Instance, stream=None) -> np.ndarray:
         th = inst.neighbors()[0].shape[1]
