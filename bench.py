@@ -689,7 +689,9 @@ def run_learned(args):
         x = S[seeds[k % len(seeds)]]
         return seeds[k % len(seeds)], descend(x, x.work, x.init, LEARNED_SWEEP, te=True)
 
+    torch.cuda.profiler.start()  # a profiler started with --profile-from-start off sees the timed steps only
     ms_l, out_l, clk_l = timed(learned_step, args.steps)
+    torch.cuda.profiler.stop()
     if world > 1:
         dist.barrier()
     # final costs of each seed's learned descents (the last step of that seed left them in work)

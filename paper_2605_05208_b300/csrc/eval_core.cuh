@@ -1133,17 +1133,18 @@ __device__ void eval_relocate_full(const Ctx &C, int cu, int lane, Best &b, int 
     const int nvar = 1 + (two ? 1 : 0) + (rev ? 1 : 0);  // variants after v (as many before v when v is first)
     const int32_t *rowU = I.dist + (size_t)r.u * I.nn;
     const int32_t *rowX = I.dist + (size_t)(two ? r.x : r.u) * I.nn;
-    const int4 *lk = C.D.clink + (size_t)C.s * I.nc * MD_LINK;
+    const int4 *lk = C.D.clink + (size_t)C.s * I.nc;  // plane q at lk + q * pl
+    const size_t pl = (size_t)C.D.S * I.nc;
     int nq = 0;
     for (int i0 = part * 32; i0 < I.nc; i0 += 32 * wpc) {
         const int i = i0 + lane;
         bool keep = false;
         if (i < I.nc) {
-            const int4 l0 = lk[MD_LINK * (size_t)i];
+            const int4 l0 = lk[i];
             if (l0.x != r.A) {
                 const int j = l0.y, sv = l0.w, v = I.nd + i;
-                const int aout = lk[MD_LINK * (size_t)i + 1].y;
-                const int dep = TW ? lk[MD_LINK * (size_t)i + 5].w : 0;  // earliest completion at v
+                const int aout = lk[1 * pl + i].y;
+                const int dep = TW ? lk[5 * pl + i].w : 0;  // earliest completion at v
                 const bool last = sv == MD_NONE;  // v ends an open route: nothing follows seq(u)
                 const int cvu = __ldg(rowU + md_ix(C.I.err, v, C.I.nn));
                 const int cus = last ? 0 : __ldg(rowU + md_ix(C.I.err, sv, C.I.nn));
@@ -1152,7 +1153,7 @@ __device__ void eval_relocate_full(const Ctx &C, int cu, int lane, Best &b, int 
                 keep = det1 < 0 || !lb_reject(b, dA1 + cvu + cus - aout, __fadd_rd(pen1, tw1));
                 if (j == 1 && !keep) {
                     // v first on its route: seq(u) also goes between the departure depot and v
-                    const int ds = l0.z, ain = lk[MD_LINK * (size_t)i + 1].x;  // c(ds, v)
+                    const int ds = l0.z, ain = lk[1 * pl + i].x;  // c(ds, v)
                     const int eds = TW ? __ldg(&I.node[md_ix(C.I.err, ds, C.I.nn)]).z : 0;
                     const int cdu = __ldg(rowU + md_ix(C.I.err, ds, C.I.nn));
                     const int d1 = cdu + gap1 + cvu - ain;
@@ -1219,8 +1220,9 @@ __device__ void eval_swap_full(const Ctx &C, int cu, int lane, Best &b, int *wl,
     const float pen1 = pen_lo(C, A1.tw - w.oldA.tw, A1.lex - w.oldA.lex, A1.dex - w.oldA.dex, 0);
     const float pen2 = pen_lo(C, A2.tw - w.oldA.tw, A2.lex - w.oldA.lex, A2.dex - w.oldA.dex, 0);
     const int gu1 = w.u1.dur - w.u1.tw, gu2 = w.u2.dur - w.u2.tw, gu2r = w.u2r.dur - w.u2r.tw;
-    const int4 *lk = C.D.clink + (size_t)C.s * I.nc * MD_LINK;
-    const int4 lu = lk[MD_LINK * (size_t)cu + 1];
+    const int4 *lk = C.D.clink + (size_t)C.s * I.nc;  // plane q at lk + q * pl
+    const size_t pl = (size_t)C.D.S * I.nc;
+    const int4 lu = lk[1 * pl + cu];
     const int c_pu_u = lu.x, c_u_su = lu.y, c_x_sx = lu.w;  // arcs of u's route around seq(u)
     const bool su_none = w.su == MD_NONE, sx_none = !w.hasx || w.sx == MD_NONE;
     const int c_pu_su = su_none ? 0 : cost(I, w.pu, w.su), c_pu_sx = sx_none ? 0 : cost(I, w.pu, w.sx);
@@ -1235,10 +1237,10 @@ __device__ void eval_swap_full(const Ctx &C, int cu, int lane, Best &b, int *wl,
         const int i = i0 + lane;
         bool keep = false;
         if (i < I.nc) {
-            const int4 l0 = lk[MD_LINK * (size_t)i];
+            const int4 l0 = lk[i];
             if (l0.x != w.A) {
-                const int4 l1 = lk[MD_LINK * (size_t)i + 1], l2 = lk[MD_LINK * (size_t)i + 2];
-                const int4 l3 = lk[MD_LINK * (size_t)i + 3], l4 = lk[MD_LINK * (size_t)i + 4];
+                const int4 l1 = lk[1 * pl + i], l2 = lk[2 * pl + i];
+                const int4 l3 = lk[3 * pl + i], l4 = lk[4 * pl + i];
                 const int v = I.nd + i, pv = l0.z, sv = l0.w, sy = l1.z;
                 const bool hasy = sv >= I.nd;
                 const float penB1 = pen_lo32(C, l3.z, l3.w, l4.x);
@@ -1343,8 +1345,9 @@ __device__ void eval_2optstar_full(const Ctx &C, int cu, int lane, Best &b, int 
     // existing pieces
     const bool su_none = o.su == MD_NONE;
     const Seg Y2 = su_none ? Seg{0, 0, 0, 0, 0, MD_NO_LATE} : suffix_from(C, o.su);
-    const int4 *lk = C.D.clink + (size_t)C.s * I.nc * MD_LINK;
-    const int c_u_su = lk[MD_LINK * (size_t)cu + 1].y;
+    const int4 *lk = C.D.clink + (size_t)C.s * I.nc;  // plane q at lk + q * pl
+    const size_t pl = (size_t)C.D.S * I.nc;
+    const int c_u_su = lk[1 * pl + cu].y;
     const int32_t *rowU = I.dist + (size_t)o.u * I.nn;
     const int32_t *rowSU = I.dist + (size_t)(su_none ? o.u : o.su) * I.nn;
     const Seg8 *csuf = C.D.csuf + (size_t)C.s * I.nc;
@@ -1356,13 +1359,13 @@ __device__ void eval_2optstar_full(const Ctx &C, int cu, int lane, Best &b, int 
         const int i = i0 + lane;
         bool keep = false;
         if (i < I.nc) {
-            const int4 l0 = lk[MD_LINK * (size_t)i];
+            const int4 l0 = lk[i];
             if (l0.x != o.A) {
                 const int v = I.nd + i, pv = l0.z;
                 keep = pv < I.nd && o.u_last;  // v's route would empty: exact
                 if (!keep) {
-                    const int4 l1 = lk[MD_LINK * (size_t)i + 1], l2 = lk[MD_LINK * (size_t)i + 2];
-                    const int4 X2 = lk[MD_LINK * (size_t)i + 5];  // [ds_B .. pred v]: tw, load, dur
+                    const int4 l1 = lk[1 * pl + i], l2 = lk[2 * pl + i];
+                    const int4 X2 = lk[5 * pl + i];  // [ds_B .. pred v]: tw, load, dur
                     const int4 Y1 = reinterpret_cast<const int4 *>(&csuf[i])[0];  // [v .. de_B]: dist, load, dur, tw
                     const Seg oB = seg_of(ld_seg8(&C.D.rterm[md_ix(C.I.err, (size_t)C.s * C.D.R + l0.x, (size_t)C.D.S * C.D.R)]));
                     const int cuv = __ldg(rowU + md_ix(C.I.err, v, C.I.nn)), cps = su_none ? 0 : __ldg(rowSU + md_ix(C.I.err, pv, C.I.nn));

@@ -13,8 +13,10 @@
 //   csubf   Seg8  [S * nc * K]      csubf[c][t]: customers at positions p(c)..p(c)+t of c's route
 //   csubb   Seg8  [S * nc * K]      csubb[c][t]: customers at positions p(c)-t..p(c)
 //                                   (both with {first node, last node}; for intra-route moves)
-//   clink   int4  [S * nc * MD_LINK] per customer v, its links on its route (for the evaluation's
-//                                   exact lower-bound rejection on full neighbourhoods):
+//   clink   int4  [MD_LINK * S * nc] per customer v, its links on its route (for the evaluation's
+//                                   exact lower-bound rejection on full neighbourhoods), in
+//                                   MD_LINK planes [q][s][c] so a warp's reads of one plane over
+//                                   consecutive candidates are contiguous:
 //                                   {route slot, position, pred, succ},
 //                                   {c(pred, v), c(v, succ) (0: no succ), succ of succ (MD_NONE:
 //                                    none), c(succ, succ of succ) (0: none)},

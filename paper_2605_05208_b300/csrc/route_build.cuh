@@ -66,7 +66,8 @@ __device__ __forceinline__ void write_links(const DevInst &I, const DevSols &D, 
                                             int L, int ds, int de, bool open, const Seg &whole) {
     const int lane = threadIdx.x & 31;
     __syncwarp();  // the route's prefixes and suffixes are written
-    int4 *lk = D.clink + (size_t)s * I.nc * MD_LINK;
+    int4 *lk = D.clink + (size_t)s * I.nc;  // plane q at lk + q * pl
+    const size_t pl = (size_t)D.S * I.nc;
     const Seg8 *cpre = D.cpre + (size_t)s * I.nc;
     const Seg8 *csuf = D.csuf + (size_t)s * I.nc;
     const int wlex = load_ex(whole.load, I.Q), wdex = dur_ex(whole.dur, I.D);
@@ -95,15 +96,15 @@ __device__ __forceinline__ void write_links(const DevInst &I, const DevSols &D, 
             r1 = seg_cat<TW>(P, succ < I.nd ? node_seg(I.node[md_ix(I.err, succ, (size_t)I.nn)]) : seg_of(ld_seg8(&csuf[md_ix(I.err, succ - I.nd, (size_t)I.nc)])), c_ps);
         if (succ2 != MD_NONE && k + 1 < L)
             r2 = seg_cat<TW>(P, succ2 < I.nd ? node_seg(I.node[md_ix(I.err, succ2, (size_t)I.nn)]) : seg_of(ld_seg8(&csuf[md_ix(I.err, succ2 - I.nd, (size_t)I.nc)])), c_ps2);
-        int4 *e = lk + md_ix(I.err, c - I.nd, I.nc) * MD_LINK;
+        int4 *e = lk + md_ix(I.err, c - I.nd, I.nc);
         e[0] = make_int4(r, k + 1, pred, succ);
-        e[1] = make_int4(a_in, a_out, succ2, a_out2);
-        e[2] = make_int4(cs.dur, gap2, ds | (de << 16), feasible ? 1 : 0);
-        e[3] = make_int4(c_ps, c_ps2, r1.tw - whole.tw, load_ex(r1.load, I.Q) - wlex);
-        e[4] = make_int4(dur_ex(r1.dur, I.D) - wdex, r2.tw - whole.tw, load_ex(r2.load, I.Q) - wlex,
-                         dur_ex(r2.dur, I.D) - wdex);
+        e[pl] = make_int4(a_in, a_out, succ2, a_out2);
+        e[2 * pl] = make_int4(cs.dur, gap2, ds | (de << 16), feasible ? 1 : 0);
+        e[3 * pl] = make_int4(c_ps, c_ps2, r1.tw - whole.tw, load_ex(r1.load, I.Q) - wlex);
+        e[4 * pl] = make_int4(dur_ex(r1.dur, I.D) - wdex, r2.tw - whole.tw, load_ex(r2.load, I.Q) - wlex,
+                              dur_ex(r2.dur, I.D) - wdex);
         const Seg8 Pc = ld_seg8(&cpre[md_ix(I.err, c - I.nd, (size_t)I.nc)]);  // [ds .. c]
-        e[5] = make_int4(P.tw, P.load, P.dur, Pc.E + Pc.dur - Pc.tw);
+        e[5 * pl] = make_int4(P.tw, P.load, P.dur, Pc.E + Pc.dur - Pc.tw);
     }
 }
 
