@@ -427,6 +427,48 @@ md_status md_pruner_prune(md_pruner *pruner, md_instance *inst, int32_t k, void 
 md_status md_pruner_train(md_pruner *pruner, md_instance *inst, const uint8_t *labels, int32_t epochs,
                           int32_t batch, float lr, float pos_weight, float *mean_loss, void *stream);
 
+/* ---------------------------------------------------------------------------------------------
+ * One solution split over ranks by customer (multi-GPU: the evaluation of a large solution shared
+ * by several GPUs, one exchange per descent step).  The leader-follower update (Section 3.2.5)
+ * needs from an evaluation only its leader (the smallest dF < 0) and, for every route pair, the
+ * best follower: each rank evaluates the customers of its range (md_eval_range), exports that
+ * summary (md_moves_export), the ranks all-gather it, every replica merges it (the smallest leader
+ * by (dF, id); per route pair the smallest follower key; the summed scored counts) and imports it
+ * (md_moves_import), then md_select_multimove and md_apply_and_rebuild run the identical selection
+ * and apply on every replica, which therefore stay identical.
+ * ------------------------------------------------------------------------------------------- */
+
+/* A solution's best move of one evaluation. */
+typedef struct md_leader {
+    uint64_t id;      /* op << 32 | u << 18 | v << 4 | variant; 0 when valid = 0 */
+    double dF;        /* its penalised delta (FP64) */
+    uint32_t routes;  /* its route slots rA | rB << 16 */
+    int32_t valid;    /* 1: a move with dF < 0 exists */
+    int64_t scored;   /* moves scored by the evaluation for this solution */
+} md_leader;
+
+/* md_eval_neighborhood restricted to the customers u of indices c0 .. c1 - 1 (customer index =
+ * node id - n_depots): only moves keyed by those u are scored.  Every other argument as
+ * md_eval_neighborhood.  MD_ERR_ARG unless 0 <= c0 <= c1 <= n_customers. */
+md_status md_eval_range(md_solutions *sols, const int32_t *ops, int32_t c0, int32_t c1, const float *lambda,
+                        uint32_t flags, md_moves *moves, void *stream);
+
+/* The last evaluation's leader of solution sol and its follower-table entries: pairs[k] =
+ * i * r_slots + j (i <= j route slots), keys[k] = (dD ^ 0x80000000) << 32 | 32-bit move id of the
+ * pair's best follower, k < n_out; cap: the arrays' length.  Empties the solution's table.  Host
+ * buffers.  MD_ERR_CAPACITY (after writing cap entries) when n_out > cap; MD_ERR_STATE before an
+ * evaluation. */
+md_status md_moves_export(md_moves *moves, int32_t sol, md_leader *leader, uint32_t *pairs, uint64_t *keys,
+                          int64_t cap, int64_t *n_out, void *stream);
+
+/* Installs a merged summary for solution sol (the format of md_moves_export): the leader, n
+ * follower entries with distinct pairs, and leader->scored as the scored count; the solution's
+ * operator is the one of its last evaluation.  md_select_multimove may follow.  Host buffers.
+ * MD_ERR_ARG for a pair outside the table, MD_ERR_CAPACITY for more entries than the table
+ * lists. */
+md_status md_moves_import(md_moves *moves, int32_t sol, const md_leader *leader, const uint32_t *pairs,
+                          const uint64_t *keys, int64_t n, void *stream);
+
 /* Failure detection of the tensor-core scoring (md_pruner_score / md_pruner_prune): the number of
  * polls a wait for the tensor cores makes before it gives up (0: every wait gives up at once);
  * a negative value restores the default (2^20).  A wait that gives up sets the pruner's error

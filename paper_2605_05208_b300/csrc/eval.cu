@@ -37,7 +37,7 @@ __global__ void __launch_bounds__(32 * MD_EVAL_WARPS, MD_EVAL_MIN_BLOCKS) k_eval
         eval_tile_lists<TW>(C, op, blockIdx.x * wpb, gridDim.x * wpb, b, s_wl, s_tc, s_cnt);  // the whole block
     else if (op >= 0)
         for (int gw = blockIdx.x * wpb + warp; gw < I.nc * wpc; gw += gridDim.x * wpb)
-            eval_customer<TW>(C, op, gw / wpc, lane, b, s_wl[warp], gw % wpc, wpc, &s_tc[warp]);
+            if (in_range(C, gw / wpc)) eval_customer<TW>(C, op, gw / wpc, lane, b, s_wl[warp], gw % wpc, wpc, &s_tc[warp]);
     warp_commit(C, b, (size_t)blockIdx.x * wpb + warp, lane);
 }
 
@@ -77,6 +77,7 @@ __global__ void __launch_bounds__(32 * MD_EVAL_WARPS, MD_FULL_MIN_BLOCKS) k_eval
     best_init(b);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
     for (int gw = blockIdx.x * wpb + warp; gw < I.nc * wpc; gw += gridDim.x * wpb) {
+        if (!in_range(C, gw / wpc)) continue;
         if (op == MD_OP_RELOCATE) eval_relocate_full<TW>(C, gw / wpc, lane, b, s_wl[warp], gw % wpc, wpc, &s_tc[warp]);
         else if (op == MD_OP_SWAP) eval_swap_full<TW>(C, gw / wpc, lane, b, s_wl[warp], gw % wpc, wpc, &s_tc[warp]);
         else eval_2optstar_full<TW>(C, gw / wpc, lane, b, s_wl[warp], gw % wpc, wpc, &s_tc[warp]);

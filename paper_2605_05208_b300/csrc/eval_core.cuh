@@ -72,6 +72,12 @@ struct Ctx {
 
 union TileCtx;  // a warp's customer context in shared memory (below)
 
+// Whether customer index cu is in the evaluation's customer range (md_eval_range).
+__device__ __forceinline__ bool in_range(const Ctx &C, int cu) {
+    return C.M.c1 <= 0 || (cu >= C.M.c0 && cu < C.M.c1);
+}
+
+
 __device__ __forceinline__ int cost(const DevInst &I, int a, int b) {
     return __ldg(&I.dist[md_ix(I.err, (size_t)a * I.nn + b, (size_t)I.nn * I.nn)]);
 }
@@ -781,7 +787,7 @@ __device__ void eval_tile_lists(const Ctx &C, int op, int c0, int cstride, Best 
     for (int base = c0; base < I.nc; base += cstride) {
         const int cu = base + warp;
         int ni = 0, na = 0;
-        if (cu < I.nc) {
+        if (cu < I.nc && in_range(C, cu)) {
             // the candidates and their routes first: these loads overlap the customer's
             // preparation, on which they do not depend
             const int u = I.nd + cu, ncand = I.nnbr[cu];

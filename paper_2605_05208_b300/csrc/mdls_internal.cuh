@@ -141,6 +141,7 @@ __device__ __forceinline__ void block_leader(const LeadRec *rec, int n, double &
 
 struct DevMoves {
     int nblk;              // leader records per solution (evaluation blocks x MD_EVAL_WARPS)
+    int c0, c1;            // customers evaluated: indices c0 .. c1 - 1 (c1 <= 0: all)
     LeadRec *lpart;        // [S * nblk]
     unsigned long long *nscored;   // [S]
     unsigned long long *nexact;    // [S] moves evaluated exactly (NULL: not counted)

@@ -38,7 +38,7 @@ EXPORTED = (
     "md_batch_descend", "md_instance_build_neighbors",
     "md_instance_set_neighbors", "md_pruner_create", "md_pruner_destroy", "md_pruner_params",
     "md_pruner_features", "md_pruner_score", "md_pruner_prune", "md_pruner_train",
-    "md_pruner_set_wait", "md_repair_insert",
+    "md_pruner_set_wait", "md_repair_insert", "md_eval_range", "md_moves_export", "md_moves_import",
 )
 INSERT_FBI, INSERT_IBI, INSERT_FRI, INSERT_IRI = 0, 1, 2, 3  # repair insertion rules (Section 3.3)
 
@@ -78,6 +78,12 @@ class Config(C.Structure):
                 ("op_perm_device", C.c_int32), ("time_eval", C.c_int32), ("n_groups", C.c_int32),
                 ("sweep_every", C.c_int32), ("persistent", C.c_int32), ("wide_step", C.c_int32),
                 ("wait_limit", C.c_int32)]
+
+
+class Leader(C.Structure):
+    """md_leader: a solution's best move of one evaluation."""
+    _fields_ = [("id", C.c_uint64), ("dF", C.c_double), ("routes", C.c_uint32), ("valid", C.c_int32),
+                ("scored", C.c_int64)]
 
 
 class Stats(C.Structure):
@@ -136,6 +142,9 @@ def lib() -> C.CDLL:
             "md_pruner_prune": [P, P, C.c_int32, P],
             "md_pruner_train": [P, P, P, C.c_int32, C.c_int32, C.c_float, C.c_float, P, P],
             "md_pruner_set_wait": [P, C.c_int32],
+            "md_eval_range": [P, P, C.c_int32, C.c_int32, P, C.c_uint32, P, P],
+            "md_moves_export": [P, C.c_int32, C.POINTER(Leader), P, P, C.c_int64, C.POINTER(C.c_int64), P],
+            "md_moves_import": [P, C.c_int32, C.POINTER(Leader), P, P, C.c_int64, P],
             "md_batch_create": [P, C.c_int32, PP],
             "md_batch_destroy": [P],
             "md_batch_tune": [P, P],
@@ -399,6 +408,34 @@ class Moves:
         ops = np.ascontiguousarray(ops, dtype=np.int32)
         lam = None if lam is None else np.ascontiguousarray(lam, dtype=np.float32)
         _check(lib().md_eval_neighborhood(self.sols.h, _ptr(ops), _ptr(lam), flags, self.h, _stream(stream)))
+
+    def evaluate_range(self, ops, c0: int, c1: int, lam=None, flags: int = 0, stream=None):
+        """md_eval_range: only the customers of indices c0 .. c1 - 1."""
+        ops = np.ascontiguousarray(ops, dtype=np.int32)
+        lam = None if lam is None else np.ascontiguousarray(lam, dtype=np.float32)
+        _check(lib().md_eval_range(self.sols.h, _ptr(ops), int(c0), int(c1), _ptr(lam), int(flags), self.h,
+                                   _stream(stream)))
+
+    def export_summary(self, sol: int = 0, cap: int | None = None, stream=None):
+        """md_moves_export: (leader dict, follower pairs uint32[n], keys uint64[n])."""
+        cap = cap if cap is not None else self.sols.R * (self.sols.R + 1) // 2
+        L = Leader()
+        pairs = np.zeros(max(cap, 1), dtype=np.uint32)
+        keys = np.zeros(max(cap, 1), dtype=np.uint64)
+        n = C.c_int64()
+        _check(lib().md_moves_export(self.h, int(sol), C.byref(L), _ptr(pairs), _ptr(keys), int(cap), C.byref(n),
+                                     _stream(stream)))
+        lead = {"id": int(L.id), "dF": float(L.dF), "routes": int(L.routes), "valid": int(L.valid),
+                "scored": int(L.scored)}
+        return lead, pairs[:n.value].copy(), keys[:n.value].copy()
+
+    def import_summary(self, sol: int, lead: dict, pairs, keys, stream=None):
+        """md_moves_import of a merged summary."""
+        L = Leader(int(lead["id"]), float(lead["dF"]), int(lead["routes"]), int(lead["valid"]), int(lead["scored"]))
+        pairs = np.ascontiguousarray(pairs, dtype=np.uint32)
+        keys = np.ascontiguousarray(keys, dtype=np.uint64)
+        _check(lib().md_moves_import(self.h, int(sol), C.byref(L), _ptr(pairs), _ptr(keys), len(pairs),
+                                     _stream(stream)))
 
     def leaders(self, stream=None):
         S = self.sols.n_sol
