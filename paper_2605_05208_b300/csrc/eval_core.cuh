@@ -245,6 +245,53 @@ __device__ __forceinline__ void sink(const Ctx &C, uint32_t id, int dD, int dTW,
     offer(C, id, dD, dTW, dL, dU, dV, rA, rB, b, true, false, 0.0);
 }
 
+// ------------------------------------------------------------------------------------------
+// Exact lower bounds of dF (full neighbourhoods and neighbour lists; see the section on full
+// neighbourhoods below): helpers.
+// ------------------------------------------------------------------------------------------
+
+// FP32 lower bound of the FP64 penalty part w . (dTW, dL, dU, dV) of dF.
+__device__ __forceinline__ float pen_lo(const Ctx &C, int dTW, int dL, int dU, int dV) {
+    const double t0 = __dmul_rn(C.w[0], (double)dTW), t1 = __dmul_rn(C.w[1], (double)dL);
+    const double t2 = __dmul_rn(C.w[2], (double)dU), t3 = __dmul_rn(C.w[3], (double)dV);
+    const double p = __dadd_rn(__dadd_rn(__dadd_rn(t0, t1), t2), t3);
+    const double mag = fabs(t0) + fabs(t1) + fabs(t2) + fabs(t3);
+    return __double2float_rd(p - 1e-6 * mag - 1e-7);
+}
+
+// FP32 lower bound of w . (dTW, dL, dU) from the FP32 copies of the weights (their products and
+// sums stay within a few FP32 roundings of the FP64 value; the margin is far above them).
+__device__ __forceinline__ float pen_lo32(const Ctx &C, int dTW, int dL, int dU) {
+    const float t0 = C.wf[0] * (float)dTW, t1 = C.wf[1] * (float)dL, t2 = C.wf[2] * (float)dU;
+    return ((t0 + t1) + t2) - 1e-5f * (fabsf(t0) + fabsf(t1) + fabsf(t2)) - 1e-6f;
+}
+
+// Decided without its concatenations: no follower (dD >= 0), and dF >= dD + pen rules it out as
+// the lane's leader candidate.
+__device__ __forceinline__ bool lb_reject(const Best &b, int dD, float pen) {
+    const float lb = __fadd_rd((float)dD, pen);
+    return dD >= 0 && (b.valid ? lb > b.hi : lb >= 0.0f);
+}
+
+// Queues v (when keep) in the warp's survivor list wl[0..63] (nq entries, warp-uniform) and
+// returns whether 32 or more are queued.
+__device__ __forceinline__ bool queue_survivor(int *wl, int &nq, bool keep, int v, int lane) {
+    const unsigned m = __ballot_sync(0xffffffffu, keep);
+    if (keep) wl[nq + __popc(m & ((1u << lane) - 1u))] = v;
+    nq += __popc(m);
+    __syncwarp();
+    return nq >= 32;
+}
+
+__device__ __forceinline__ void dequeue_32(int *wl, int &nq, int lane) {
+    __syncwarp();
+    nq -= 32;
+    const int t = lane < nq ? wl[32 + lane] : 0;
+    __syncwarp();
+    if (lane < nq) wl[lane] = t;
+    __syncwarp();
+}
+
 // A summary with its end nodes; e marks the empty sequence.
 struct SN {
     Seg s;
@@ -561,18 +608,29 @@ struct RelocCtx {
     Seg PP, q1, q2, q2r;  // prefix through pred(u); seq(u) of 1 and 2 nodes, and reversed
     RT oldA, A1, A2;      // u's route now, and without seq(u) of 1 or 2 nodes
     int u, A, p, pu, su, x, sx, LA, dsA, dV_empty, has2, pad;
+    // bound of the lower-bound rejection: distance and FP32 penalty change of u's route when
+    // seq(u) of 1 or 2 customers leaves
+    int dA1, dA2;
+    float pen1, pen2;
 };
 
 struct SwapCtx {
     Seg PU, u1, u2, u2r;  // prefix through pred(u); seq(u) of 1 and 2 nodes, and reversed
     RT oldA;
     int u, A, p, pu, su, x, sx, dsA, hasx, pad;
+    // bound of the lower-bound rejection: FP32 penalty change of u's route without seq(u) of 1
+    // or 2 customers, and the arcs around seq(u): c(pu, u), c(u, su), c(x, sx), c(pu, su),
+    // c(pu, sx)
+    float pen1, pen2;
+    int c_pu_u, c_u_su, c_x_sx, c_pu_su, c_pu_sx, pad2;
 };
 
 struct O2Ctx {
     Seg PU;       // [ds_A..u]
     RT oldA;
     int u, A, su, dsA, deA, u_last;
+    // bound of the lower-bound rejection: [succ u .. de_A] (time warp, load, duration) and c(u, su)
+    int y2tw, y2load, y2dur, c_u_su;
 };
 
 // A warp's customer context in shared memory (tile-cooperative lists, full neighbourhoods).
@@ -583,8 +641,9 @@ union TileCtx {
 };
 
 
+// bounds: also the constants of the lower-bound rejection
 template <bool TW>
-__device__ __forceinline__ void reloc_setup(const Ctx &C, int cu, RelocCtx &r) {
+__device__ __forceinline__ void reloc_setup(const Ctx &C, int cu, RelocCtx &r, bool bounds = true) {
     const DevInst &I = C.I;
     r.u = I.nd + cu;
     const Seg8 Pu = pre8(C, r.u), Su = suf8(C, r.u);
@@ -610,6 +669,12 @@ __device__ __forceinline__ void reloc_setup(const Ctx &C, int cu, RelocCtx &r) {
     }
     r.dV_empty = ((!C.open && r.dsA != deA) ? -1 : 0) + veh_delta(C.D.dcount[md_ix(C.I.err, (size_t)C.s * I.nd + r.dsA, (size_t)C.D.S * C.I.nd)], I.NV, -1);
     r.pad = 0;
+    r.dA1 = r.A1.dist - r.oldA.dist;
+    r.dA2 = r.A2.dist - r.oldA.dist;
+    r.pen1 = r.pen2 = 0.0f;
+    if (!bounds) return;
+    r.pen1 = pen_lo(C, r.A1.tw - r.oldA.tw, r.A1.lex - r.oldA.lex, r.A1.dex - r.oldA.dex, r.LA == 1 ? r.dV_empty : 0);
+    r.pen2 = pen_lo(C, r.A2.tw - r.oldA.tw, r.A2.lex - r.oldA.lex, r.A2.dex - r.oldA.dex, r.LA == 2 ? r.dV_empty : 0);
 }
 
 // candidate v on another route than u's
@@ -681,7 +746,7 @@ __device__ __forceinline__ void reloc_intra(const Ctx &C, const RelocCtx &r, int
 }
 
 template <bool TW>
-__device__ __forceinline__ void swap_setup(const Ctx &C, int cu, SwapCtx &w) {
+__device__ __forceinline__ void swap_setup(const Ctx &C, int cu, SwapCtx &w, bool bounds = true) {
     const DevInst &I = C.I;
     w.u = I.nd + cu;
     const Seg8 Pu = pre8(C, w.u), Su = suf8(C, w.u);
@@ -701,6 +766,19 @@ __device__ __forceinline__ void swap_setup(const Ctx &C, int cu, SwapCtx &w) {
         w.u2r = join<TW>(C, nseg(C, w.x), w.x, nseg(C, w.u), w.u);
     }
     w.pad = 0;
+    w.pad2 = 0;
+    if (!bounds) return;
+    // u's route without seq(u) of one or two customers: the base of the insertion bound
+    const RT A1 = rt_of(join_opt<TW>(C, w.PU, w.pu, w.su), I);
+    const RT A2 = w.hasx ? rt_of(join_opt<TW>(C, w.PU, w.pu, w.sx), I) : A1;
+    w.pen1 = pen_lo(C, A1.tw - w.oldA.tw, A1.lex - w.oldA.lex, A1.dex - w.oldA.dex, 0);
+    w.pen2 = pen_lo(C, A2.tw - w.oldA.tw, A2.lex - w.oldA.lex, A2.dex - w.oldA.dex, 0);
+    const bool su_none = w.su == MD_NONE, sx_none = !w.hasx || w.sx == MD_NONE;
+    w.c_pu_u = cost(I, w.pu, w.u);
+    w.c_u_su = su_none ? 0 : cost(I, w.u, w.su);
+    w.c_x_sx = sx_none ? 0 : cost(I, w.x, w.sx);
+    w.c_pu_su = su_none ? 0 : cost(I, w.pu, w.su);
+    w.c_pu_sx = sx_none ? 0 : cost(I, w.pu, w.sx);
 }
 
 // candidate v on another route than u's (inter) or on u's route (intra)
@@ -767,6 +845,166 @@ __device__ __forceinline__ void swap_cand(const Ctx &C, const SwapCtx &w, int v,
     }
 }
 
+// ------------------------------------------------------------------------------------------
+// Per-candidate exact lower bounds (the rejection described with the full neighbourhoods below):
+// whether candidate v, on another route than u's, may give the leader or a follower and must be
+// evaluated exactly.  i: v's customer index; l0: its first link plane; n: the number of its
+// moves (counted as scored whether or not they are formed).
+// ------------------------------------------------------------------------------------------
+
+template <bool TW>
+__device__ __forceinline__ bool reloc_keep(const Ctx &C, const RelocCtx &r, int i, const int4 l0, const Best &b, int &n) {
+    const DevInst &I = C.I;
+    const int4 *lk = C.D.clink + (size_t)C.s * I.nc;  // plane q at lk + q * pl
+    const size_t pl = (size_t)C.D.S * I.nc;
+    const bool two = r.has2 != 0, rev = two && C.sym;
+    const int nvar = 1 + (two ? 1 : 0) + (rev ? 1 : 0);  // variants after v (as many before v when v is first)
+    const int j = l0.y, sv = l0.w, v = I.nd + i;
+    n = j == 1 ? 2 * nvar : nvar;
+    const int gap1 = r.q1.dur - r.q1.tw, gap2 = r.q2.dur - r.q2.tw, gap2r = r.q2r.dur - r.q2r.tw;
+    const int dq2 = r.q2.dist, dq2r = r.q2r.dist, dA1 = r.dA1, dA2 = r.dA2;
+    const float pen1 = r.pen1, pen2 = r.pen2;
+    // v's route gains at least tw_Q + min(warp at Q's arrival, detour) of time warp: the warp
+    // arriving late at Q's first node after v's earliest completion, when the detour covers it
+    const float w1 = C.wf[0] * (1.0f - 1e-5f);
+    const int32_t *rowU = I.dist + (size_t)r.u * I.nn;
+    const int32_t *rowX = I.dist + (size_t)(two ? r.x : r.u) * I.nn;
+    const int aout = lk[1 * pl + i].y;
+    const int dep = TW ? lk[5 * pl + i].w : 0;  // earliest completion at v
+    const bool last = sv == MD_NONE;  // v ends an open route: nothing follows seq(u)
+    const int cvu = __ldg(rowU + md_ix(C.I.err, v, C.I.nn));
+    const int cus = last ? 0 : __ldg(rowU + md_ix(C.I.err, sv, C.I.nn));
+    const int det1 = last ? (1 << 30) : cvu + gap1 + cus - aout;
+    const float tw1 = TW ? w1 * (float)(r.q1.tw + min(max(dep + cvu - r.q1.L, 0), det1)) : 0.0f;
+    bool keep = det1 < 0 || !lb_reject(b, dA1 + cvu + cus - aout, __fadd_rd(pen1, tw1));
+    if (j == 1 && !keep) {
+        // v first on its route: seq(u) also goes between the departure depot and v
+        const int ds = l0.z, ain = lk[1 * pl + i].x;  // c(ds, v)
+        const int eds = TW ? __ldg(&I.node[md_ix(C.I.err, ds, C.I.nn)]).z : 0;
+        const int cdu = __ldg(rowU + md_ix(C.I.err, ds, C.I.nn));
+        const int d1 = cdu + gap1 + cvu - ain;
+        const float t1 = TW ? w1 * (float)(r.q1.tw + min(max(eds + cdu - r.q1.L, 0), d1)) : 0.0f;
+        keep = d1 < 0 || !lb_reject(b, dA1 + cdu + cvu - ain, __fadd_rd(pen1, t1));
+        if (two && !keep) {
+            const int cxv = __ldg(rowX + md_ix(C.I.err, v, C.I.nn));
+            const int d2 = cdu + gap2 + cxv - ain;
+            const float t2 = TW ? w1 * (float)(r.q2.tw + min(max(eds + cdu - r.q2.L, 0), d2)) : 0.0f;
+            keep = d2 < 0 || !lb_reject(b, dA2 + cdu + dq2 + cxv - ain, __fadd_rd(pen2, t2));
+            if (rev && !keep) {
+                const int cdx = __ldg(rowX + md_ix(C.I.err, ds, C.I.nn));
+                const int d3 = cdx + gap2r + cvu - ain;
+                const float t3 = TW ? w1 * (float)(r.q2r.tw + min(max(eds + cdx - r.q2r.L, 0), d3)) : 0.0f;
+                keep = d3 < 0 || !lb_reject(b, dA2 + cdx + dq2r + cvu - ain, __fadd_rd(pen2, t3));
+            }
+        }
+    }
+    if (two && !keep) {
+        const int cxs = last ? 0 : __ldg(rowX + md_ix(C.I.err, sv, C.I.nn));
+        const int det2 = last ? (1 << 30) : cvu + gap2 + cxs - aout;
+        const float tw2 = TW ? w1 * (float)(r.q2.tw + min(max(dep + cvu - r.q2.L, 0), det2)) : 0.0f;
+        keep = det2 < 0 || !lb_reject(b, dA2 + cvu + dq2 + cxs - aout, __fadd_rd(pen2, tw2));
+        if (rev && !keep) {
+            const int cvx = __ldg(rowX + md_ix(C.I.err, v, C.I.nn));
+            const int det3 = last ? (1 << 30) : cvx + gap2r + cus - aout;
+            const float tw3 = TW ? w1 * (float)(r.q2r.tw + min(max(dep + cvx - r.q2r.L, 0), det3)) : 0.0f;
+            keep = det3 < 0 || !lb_reject(b, dA2 + cvx + dq2r + cus - aout, __fadd_rd(pen2, tw3));
+        }
+    }
+    return keep;
+}
+
+template <bool TW>
+__device__ __forceinline__ bool swap_keep(const Ctx &C, const SwapCtx &w, int i, const int4 l0, const Best &b, int &n) {
+    const DevInst &I = C.I;
+    const int4 *lk = C.D.clink + (size_t)C.s * I.nc;
+    const size_t pl = (size_t)C.D.S * I.nc;
+    const int4 l1 = lk[1 * pl + i], l2 = lk[2 * pl + i];
+    const int4 l3 = lk[3 * pl + i], l4 = lk[4 * pl + i];
+    const int v = I.nd + i, pv = l0.z, sv = l0.w, sy = l1.z;
+    const bool hasy = sv >= I.nd;
+    const float pen1 = w.pen1, pen2 = w.pen2;
+    const int gu1 = w.u1.dur - w.u1.tw, gu2 = w.u2.dur - w.u2.tw, gu2r = w.u2r.dur - w.u2r.tw;
+    const int c_pu_u = w.c_pu_u, c_u_su = w.c_u_su, c_x_sx = w.c_x_sx, c_pu_su = w.c_pu_su, c_pu_sx = w.c_pu_sx;
+    const bool su_none = w.su == MD_NONE, sx_none = !w.hasx || w.sx == MD_NONE;
+    const int32_t *rowPU = I.dist + (size_t)w.pu * I.nn;
+    const int32_t *rowU = I.dist + (size_t)w.u * I.nn;
+    const int32_t *rowX = I.dist + (size_t)(w.hasx ? w.x : w.u) * I.nn;
+    const int32_t *rowSU = I.dist + (size_t)(su_none ? w.u : w.su) * I.nn;
+    const int32_t *rowSX = I.dist + (size_t)(sx_none ? w.u : w.sx) * I.nn;
+    // v's route without seq(v) of one or two customers is the base of the bound on v's route
+    const float penB1 = pen_lo32(C, l3.z, l3.w, l4.x);
+    const float penB2 = hasy ? pen_lo32(C, l4.y, l4.z, l4.w) : 0.0f;
+    bool keep = false;
+    n = 0;
+    if (!C.sym) {
+        // the four variants (1,1), (2,1), (1,2), (2,2) written out, sharing their arcs: seq(v) of
+        // kv customers into u's route, seq(u) of ku into v's route
+        const int c_pu_v = __ldg(rowPU + md_ix(C.I.err, v, C.I.nn)), c_pv_u = __ldg(rowU + md_ix(C.I.err, pv, C.I.nn));
+        const bool sv_none = sv == MD_NONE, sy_none = !hasy || sy == MD_NONE;
+        const int base = c_pu_v + c_pv_u - c_pu_u - l1.x;
+        {   // (1,1)
+            const int b1 = su_none ? 0 : __ldg(rowSU + md_ix(C.I.err, v, C.I.nn)), d1 = sv_none ? 0 : __ldg(rowU + md_ix(C.I.err, sv, C.I.nn));
+            const int dD = base + b1 + d1 - c_u_su - l1.y;
+            const int detA = su_none ? 0 : c_pu_v + l2.x + b1 - c_pu_su;
+            const int detB = sv_none ? 0 : c_pv_u + gu1 + d1 - l3.x;
+            keep = detA < 0 || detB < 0 || !lb_reject(b, dD, __fadd_rd(pen1, penB1));
+            n = 1;
+        }
+        if (w.hasx) {  // (2,1)
+            const int b2 = sx_none ? 0 : __ldg(rowSX + md_ix(C.I.err, v, C.I.nn)), e1 = sv_none ? 0 : __ldg(rowX + md_ix(C.I.err, sv, C.I.nn));
+            const int dD = base + b2 + e1 - c_x_sx - l1.y;
+            const int detA = sx_none ? 0 : c_pu_v + l2.x + b2 - c_pu_sx;
+            const int detB = sv_none ? 0 : c_pv_u + gu2 + e1 - l3.x;
+            keep = keep || detA < 0 || detB < 0 || !lb_reject(b, dD, __fadd_rd(pen2, penB1));
+            n++;
+        }
+        if (hasy) {  // (1,2)
+            const int f1 = su_none ? 0 : __ldg(rowSU + md_ix(C.I.err, sv, C.I.nn)), d2 = sy_none ? 0 : __ldg(rowU + md_ix(C.I.err, sy, C.I.nn));
+            const int dD = base + f1 + d2 - c_u_su - l1.w;
+            const int detA = su_none ? 0 : c_pu_v + l2.y + f1 - c_pu_su;
+            const int detB = sy_none ? 0 : c_pv_u + gu1 + d2 - l3.y;
+            keep = keep || detA < 0 || detB < 0 || !lb_reject(b, dD, __fadd_rd(pen1, penB2));
+            n++;
+        }
+        if (w.hasx && hasy) {  // (2,2)
+            const int f2 = sx_none ? 0 : __ldg(rowSX + md_ix(C.I.err, sv, C.I.nn)), e2 = sy_none ? 0 : __ldg(rowX + md_ix(C.I.err, sy, C.I.nn));
+            const int dD = base + f2 + e2 - c_x_sx - l1.w;
+            const int detA = sx_none ? 0 : c_pu_v + l2.y + f2 - c_pu_sx;
+            const int detB = sy_none ? 0 : c_pv_u + gu2 + e2 - l3.y;
+            keep = keep || detA < 0 || detB < 0 || !lb_reject(b, dD, __fadd_rd(pen2, penB2));
+            n++;
+        }
+        return keep;
+    }
+    for (int var = 0; var < 9; var++) {
+        const int ku = SW_KU[var], kv = SW_KV[var];
+        const bool ru = SW_RU[var], rv = SW_RV[var];
+        if ((ku == 2 && !w.hasx) || (kv == 2 && !hasy)) continue;
+        n++;
+        if (keep) continue;
+        if (TW && rv) { keep = true; continue; }  // a reversed time-window sequence: no gap at hand
+        const int qvf = (kv == 2 && rv) ? sv : v, qvl = (kv == 2 && !rv) ? sv : v;
+        const bool au_none = ku == 1 ? su_none : sx_none;   // nothing after seq(u)
+        const int32_t *rowAU = ku == 1 ? rowSU : rowSX;
+        const int av = kv == 1 ? sv : sy;                   // after seq(v)
+        const bool av_none = av == MD_NONE;
+        const int quf = (ku == 2 && ru) ? w.x : w.u, qul = (ku == 2 && !ru) ? w.x : w.u;
+        const int c_pu_qvf = __ldg(rowPU + md_ix(C.I.err, qvf, C.I.nn));
+        const int c_qvl_au = au_none ? 0 : __ldg(rowAU + md_ix(C.I.err, qvl, C.I.nn));
+        const int c_pv_quf = __ldg((quf == w.u ? rowU : rowX) + md_ix(C.I.err, pv, C.I.nn));
+        const int c_qul_av = av_none ? 0 : __ldg((qul == w.u ? rowU : rowX) + md_ix(C.I.err, av, C.I.nn));
+        const int dD = c_pu_qvf + c_qvl_au + c_pv_quf + c_qul_av - c_pu_u - (ku == 1 ? c_u_su : c_x_sx) -
+                       l1.x - (kv == 1 ? l1.y : l1.w);
+        // seq(v) into u's route without seq(u), seq(u) into v's route without seq(v)
+        const int gv = kv == 1 ? l2.x : l2.y;
+        const int gu = ku == 1 ? gu1 : (ru ? gu2r : gu2);
+        const int detA = au_none ? 0 : c_pu_qvf + gv + c_qvl_au - (ku == 1 ? c_pu_su : c_pu_sx);
+        const int detB = av_none ? 0 : c_pv_quf + gu + c_qul_av - (kv == 1 ? l3.x : l3.y);
+        keep = detA < 0 || detB < 0 || !lb_reject(b, dD, __fadd_rd(ku == 1 ? pen1 : pen2, kv == 1 ? penB1 : penB2));
+    }
+    return keep;
+}
+
 // Which warp's customer holds flat index f of a kind, given the warps' counts cnt[0..W): returns
 // the warp and leaves f as the index within that warp's candidates.
 __device__ __forceinline__ int flat_owner(const int *cnt, int &f) {
@@ -779,7 +1017,7 @@ __device__ __forceinline__ int flat_owner(const int *cnt, int &f) {
 // neighbour lists hold at most 64 candidates, by the whole block.  Called by every thread of the
 // block (it synchronises the block); wl: [MD_EVAL_WARPS][64], tc: [MD_EVAL_WARPS] and
 // cnt: [2 MD_EVAL_WARPS] in shared memory.  The lanes' best moves accumulate in b.
-template <bool TW>
+template <bool TW, bool LB = true>
 __device__ void eval_tile_lists(const Ctx &C, int op, int c0, int cstride, Best &b, int (*wl)[64], TileCtx *tc,
                                 int *cnt) {
     const DevInst &I = C.I;
@@ -800,12 +1038,12 @@ __device__ void eval_tile_lists(const Ctx &C, int op, int c0, int cstride, Best 
             int A;
             if (op == MD_OP_RELOCATE) {
                 RelocCtx r;
-                reloc_setup<TW>(C, cu, r);
+                reloc_setup<TW>(C, cu, r, LB && I.list_bound && !(C.flags & MD_EVAL_DUMP));
                 A = r.A;
                 if (lane == 0) tc[warp].r = r;
             } else {
                 SwapCtx w;
-                swap_setup<TW>(C, cu, w);
+                swap_setup<TW>(C, cu, w, LB && I.list_bound && !(C.flags & MD_EVAL_DUMP));
                 A = w.A;
                 if (lane == 0) tc[warp].w = w;
             }
@@ -839,7 +1077,17 @@ __device__ void eval_tile_lists(const Ctx &C, int op, int c0, int cstride, Best 
                 int f = f0;
                 const int w = flat_owner(cnt, f);
                 const int v = wl[w][f];
-                if (op == MD_OP_RELOCATE) reloc_inter<TW>(C, tc[w].r, v, b);
+                // the exact lower bound first (not for a dump, which forms every move)
+                int n = 0;
+                bool keep = true;
+                if (LB && I.list_bound && !(C.flags & MD_EVAL_DUMP)) {
+                    const int i = v - I.nd;
+                    const int4 l0 = C.D.clink[md_ix(C.I.err, (size_t)C.s * I.nc + i, (size_t)C.D.S * C.I.nc)];
+                    keep = op == MD_OP_RELOCATE ? reloc_keep<TW>(C, tc[w].r, i, l0, b, n)
+                                                : swap_keep<TW>(C, tc[w].w, i, l0, b, n);
+                }
+                if (!keep) b.n += (unsigned long long)n;
+                else if (op == MD_OP_RELOCATE) reloc_inter<TW>(C, tc[w].r, v, b);
                 else swap_cand<TW, false>(C, tc[w].w, v, b);
             } else if (f0 >= pad_i) {
                 int f = f0 - pad_i;
@@ -859,7 +1107,7 @@ __device__ void eval_tile_lists(const Ctx &C, int op, int c0, int cstride, Best 
 
 
 template <bool TW>
-__device__ __forceinline__ void o2_setup(const Ctx &C, int cu, O2Ctx &o) {
+__device__ __forceinline__ void o2_setup(const Ctx &C, int cu, O2Ctx &o, bool bounds = true) {
     const DevInst &I = C.I;
     o.u = I.nd + cu;
     const Seg8 Pu = pre8(C, o.u), Su = suf8(C, o.u);
@@ -872,6 +1120,12 @@ __device__ __forceinline__ void o2_setup(const Ctx &C, int cu, O2Ctx &o) {
     o.oldA = rt_of(seg_of(ld_seg8(&C.D.rterm[md_ix(C.I.err, sA, (size_t)C.D.S * C.D.R)])), I);
     o.PU = seg_of(Pu);
     o.u_last = o.su < I.nd;  // depot or MD_NONE after u
+    if (!bounds) return;
+    const Seg Y2 = o.su == MD_NONE ? Seg{0, 0, 0, 0, 0, MD_NO_LATE} : suffix_from(C, o.su);
+    o.y2tw = Y2.tw;
+    o.y2load = Y2.load;
+    o.y2dur = Y2.dur;
+    o.c_u_su = o.su == MD_NONE ? 0 : cost(I, o.u, o.su);
 }
 
 // candidate v on another route than u's (returns without scoring when v is on u's route)
@@ -899,10 +1153,41 @@ __device__ __forceinline__ void o2_cand(const Ctx &C, const O2Ctx &o, int v, Bes
           false, 0.0);
 }
 
+// 2-opt* of u with v on another route (one move).  The new routes [ds_A..u] + [v..de_B] and
+// [ds_B..pred v] + [succ u..de_A] each join two existing pieces.
+template <bool TW>
+__device__ __forceinline__ bool o2_keep(const Ctx &C, const O2Ctx &o, int i, const int4 l0, const Best &b) {
+    const DevInst &I = C.I;
+    const int pv = l0.z;
+    if (pv < I.nd && o.u_last) return true;  // v's route would empty: exact
+    const int4 *lk = C.D.clink + (size_t)C.s * I.nc;
+    const size_t pl = (size_t)C.D.S * I.nc;
+    const bool su_none = o.su == MD_NONE;
+    const int v = I.nd + i;
+    const int4 l1 = lk[1 * pl + i], l2 = lk[2 * pl + i];
+    const int4 X2 = lk[5 * pl + i];  // [ds_B .. pred v]: tw, load, dur
+    const int4 Y1 = reinterpret_cast<const int4 *>(&C.D.csuf[md_ix(C.I.err, (size_t)C.s * I.nc + i, (size_t)C.D.S * C.I.nc)])[0];  // [v .. de_B]: dist, load, dur, tw
+    const Seg oB = seg_of(ld_seg8(&C.D.rterm[md_ix(C.I.err, (size_t)C.s * C.D.R + l0.x, (size_t)C.D.S * C.D.R)]));
+    const int32_t *rowU = I.dist + (size_t)o.u * I.nn;
+    const int32_t *rowSU = I.dist + (size_t)(su_none ? o.u : o.su) * I.nn;
+    const int cuv = __ldg(rowU + md_ix(C.I.err, v, C.I.nn)), cps = su_none ? 0 : __ldg(rowSU + md_ix(C.I.err, pv, C.I.nn));
+    const int dD = cuv + cps - o.c_u_su - l1.x;
+    const int dsB = l2.z & 0xffff, deB = l2.z >> 16;
+    const int dV = C.open ? 0 : (o.dsA != deB) + (dsB != o.deA) - (o.dsA != o.deA) - (dsB != deB);
+    const int dT = o.PU.tw + Y1.w + X2.x + o.y2tw - o.oldA.tw - oB.tw;
+    const int dL = load_ex(o.PU.load + Y1.y, I.Q) + load_ex(X2.y + o.y2load, I.Q) - o.oldA.lex - load_ex(oB.load, I.Q);
+    const int dU = dur_ex(o.PU.dur + Y1.z + cuv, I.D) + dur_ex(X2.z + (su_none ? 0 : o.y2dur + cps), I.D) -
+                   o.oldA.dex - dur_ex(oB.dur, I.D);
+    // w4 dV4, dV4 in -2 .. 2, as a lower bound with the FP32 weight
+    const float v4 = C.wf[3] * (float)dV;
+    const float pv4 = v4 - 1e-5f * fabsf(v4) - 1e-6f;
+    return !lb_reject(b, dD, __fadd_rd(pen_lo32(C, dT, dL, dU), pv4));
+}
+
 template <bool TW>
 __device__ void eval_2optstar_full(const Ctx &C, int cu, int lane, Best &b, int *wl, int part, int wpc, TileCtx *tc);
 
-template <bool TW>
+template <bool TW, bool LB = true>
 __device__ void eval_2optstar(const Ctx &C, int cu, int lane, Best &b, int *wl, int part, int wpc, TileCtx *tc) {
     if (!C.lists && !(C.flags & MD_EVAL_DUMP)) {
         eval_2optstar_full<TW>(C, cu, lane, b, wl, part, wpc, tc);
@@ -910,7 +1195,7 @@ __device__ void eval_2optstar(const Ctx &C, int cu, int lane, Best &b, int *wl, 
     }
     const DevInst &I = C.I;
     O2Ctx o;
-    o2_setup<TW>(C, cu, o);
+    o2_setup<TW>(C, cu, o, LB && I.list_bound && !(C.flags & MD_EVAL_DUMP));
     const int ncand = C.lists ? I.nnbr[cu] : I.nc;
     // batches of 64 candidates, or of 32 when wpc warps share the customer: warp part takes
     // every wpc-th batch
@@ -922,6 +1207,15 @@ __device__ void eval_2optstar(const Ctx &C, int cu, int lane, Best &b, int *wl, 
         for (int k = lane; k < ni_pad + na; k += 32) {
             const int v = k < ni ? wl[k] : (k >= ni_pad ? wl[63 - (k - ni_pad)] : -1);
             if (v < 0) continue;
+            if (LB && I.list_bound && !(C.flags & MD_EVAL_DUMP)) {  // the exact lower bound first
+                const int i = v - I.nd;
+                const int4 l0 = C.D.clink[md_ix(C.I.err, (size_t)C.s * I.nc + i, (size_t)C.D.S * C.I.nc)];
+                if (l0.x == o.A) continue;  // no move on u's own route
+                if (!o2_keep<TW>(C, o, i, l0, b)) {
+                    b.n += 1ull;
+                    continue;
+                }
+            }
             o2_cand<TW>(C, o, v, b);
         }
         __syncwarp();  // the list is read before the next batch overwrites it
@@ -1070,48 +1364,6 @@ __device__ void eval_depot_replace(const Ctx &C, int cu, int lane, Best &b, int 
 // in candidate order, so a warp's reads are contiguous.
 // ------------------------------------------------------------------------------------------
 
-// FP32 lower bound of the FP64 penalty part w . (dTW, dL, dU, dV) of dF.
-__device__ __forceinline__ float pen_lo(const Ctx &C, int dTW, int dL, int dU, int dV) {
-    const double t0 = __dmul_rn(C.w[0], (double)dTW), t1 = __dmul_rn(C.w[1], (double)dL);
-    const double t2 = __dmul_rn(C.w[2], (double)dU), t3 = __dmul_rn(C.w[3], (double)dV);
-    const double p = __dadd_rn(__dadd_rn(__dadd_rn(t0, t1), t2), t3);
-    const double mag = fabs(t0) + fabs(t1) + fabs(t2) + fabs(t3);
-    return __double2float_rd(p - 1e-6 * mag - 1e-7);
-}
-
-// FP32 lower bound of w . (dTW, dL, dU) from the FP32 copies of the weights (their products and
-// sums stay within a few FP32 roundings of the FP64 value; the margin is far above them).
-__device__ __forceinline__ float pen_lo32(const Ctx &C, int dTW, int dL, int dU) {
-    const float t0 = C.wf[0] * (float)dTW, t1 = C.wf[1] * (float)dL, t2 = C.wf[2] * (float)dU;
-    return ((t0 + t1) + t2) - 1e-5f * (fabsf(t0) + fabsf(t1) + fabsf(t2)) - 1e-6f;
-}
-
-// Decided without its concatenations: no follower (dD >= 0), and dF >= dD + pen rules it out as
-// the lane's leader candidate.
-__device__ __forceinline__ bool lb_reject(const Best &b, int dD, float pen) {
-    const float lb = __fadd_rd((float)dD, pen);
-    return dD >= 0 && (b.valid ? lb > b.hi : lb >= 0.0f);
-}
-
-// Queues v (when keep) in the warp's survivor list wl[0..63] (nq entries, warp-uniform) and
-// returns whether 32 or more are queued.
-__device__ __forceinline__ bool queue_survivor(int *wl, int &nq, bool keep, int v, int lane) {
-    const unsigned m = __ballot_sync(0xffffffffu, keep);
-    if (keep) wl[nq + __popc(m & ((1u << lane) - 1u))] = v;
-    nq += __popc(m);
-    __syncwarp();
-    return nq >= 32;
-}
-
-__device__ __forceinline__ void dequeue_32(int *wl, int &nq, int lane) {
-    __syncwarp();
-    nq -= 32;
-    const int t = lane < nq ? wl[32 + lane] : 0;
-    __syncwarp();
-    if (lane < nq) wl[lane] = t;
-    __syncwarp();
-}
-
 template <bool TW>
 __device__ void eval_relocate_full(const Ctx &C, int cu, int lane, Best &b, int *wl, int part, int wpc, TileCtx *tc) {
     const DevInst &I = C.I;
@@ -1125,22 +1377,7 @@ __device__ void eval_relocate_full(const Ctx &C, int cu, int lane, Best &b, int 
         __syncwarp();
     }
     const RelocCtx &r = tc->r;
-    const int dA1 = r.A1.dist - r.oldA.dist, dA2 = r.A2.dist - r.oldA.dist;
-    const float pen1 = pen_lo(C, r.A1.tw - r.oldA.tw, r.A1.lex - r.oldA.lex, r.A1.dex - r.oldA.dex,
-                              r.LA == 1 ? r.dV_empty : 0);
-    const float pen2 = pen_lo(C, r.A2.tw - r.oldA.tw, r.A2.lex - r.oldA.lex, r.A2.dex - r.oldA.dex,
-                              r.LA == 2 ? r.dV_empty : 0);
-    const int gap1 = r.q1.dur - r.q1.tw, gap2 = r.q2.dur - r.q2.tw, gap2r = r.q2r.dur - r.q2r.tw;
-    const int dq2 = r.q2.dist, dq2r = r.q2r.dist;
-    const bool two = r.has2 != 0, rev = two && C.sym;
-    // v's route gains at least tw_Q + min(warp at Q's arrival, detour) of time warp: the warp
-    // arriving late at Q's first node after v's earliest completion, when the detour covers it
-    const float w1 = C.wf[0] * (1.0f - 1e-5f);
-    const int nvar = 1 + (two ? 1 : 0) + (rev ? 1 : 0);  // variants after v (as many before v when v is first)
-    const int32_t *rowU = I.dist + (size_t)r.u * I.nn;
-    const int32_t *rowX = I.dist + (size_t)(two ? r.x : r.u) * I.nn;
-    const int4 *lk = C.D.clink + (size_t)C.s * I.nc;  // plane q at lk + q * pl
-    const size_t pl = (size_t)C.D.S * I.nc;
+    const int4 *lk = C.D.clink + (size_t)C.s * I.nc;
     int nq = 0;
     for (int i0 = part * 32; i0 < I.nc; i0 += 32 * wpc) {
         const int i = i0 + lane;
@@ -1148,49 +1385,9 @@ __device__ void eval_relocate_full(const Ctx &C, int cu, int lane, Best &b, int 
         if (i < I.nc) {
             const int4 l0 = lk[i];
             if (l0.x != r.A) {
-                const int j = l0.y, sv = l0.w, v = I.nd + i;
-                const int aout = lk[1 * pl + i].y;
-                const int dep = TW ? lk[5 * pl + i].w : 0;  // earliest completion at v
-                const bool last = sv == MD_NONE;  // v ends an open route: nothing follows seq(u)
-                const int cvu = __ldg(rowU + md_ix(C.I.err, v, C.I.nn));
-                const int cus = last ? 0 : __ldg(rowU + md_ix(C.I.err, sv, C.I.nn));
-                const int det1 = last ? (1 << 30) : cvu + gap1 + cus - aout;
-                const float tw1 = TW ? w1 * (float)(r.q1.tw + min(max(dep + cvu - r.q1.L, 0), det1)) : 0.0f;
-                keep = det1 < 0 || !lb_reject(b, dA1 + cvu + cus - aout, __fadd_rd(pen1, tw1));
-                if (j == 1 && !keep) {
-                    // v first on its route: seq(u) also goes between the departure depot and v
-                    const int ds = l0.z, ain = lk[1 * pl + i].x;  // c(ds, v)
-                    const int eds = TW ? __ldg(&I.node[md_ix(C.I.err, ds, C.I.nn)]).z : 0;
-                    const int cdu = __ldg(rowU + md_ix(C.I.err, ds, C.I.nn));
-                    const int d1 = cdu + gap1 + cvu - ain;
-                    const float t1 = TW ? w1 * (float)(r.q1.tw + min(max(eds + cdu - r.q1.L, 0), d1)) : 0.0f;
-                    keep = d1 < 0 || !lb_reject(b, dA1 + cdu + cvu - ain, __fadd_rd(pen1, t1));
-                    if (two && !keep) {
-                        const int cxv = __ldg(rowX + md_ix(C.I.err, v, C.I.nn));
-                        const int d2 = cdu + gap2 + cxv - ain;
-                        const float t2 = TW ? w1 * (float)(r.q2.tw + min(max(eds + cdu - r.q2.L, 0), d2)) : 0.0f;
-                        keep = d2 < 0 || !lb_reject(b, dA2 + cdu + dq2 + cxv - ain, __fadd_rd(pen2, t2));
-                        if (rev && !keep) {
-                            const int cdx = __ldg(rowX + md_ix(C.I.err, ds, C.I.nn));
-                            const int d3 = cdx + gap2r + cvu - ain;
-                            const float t3 = TW ? w1 * (float)(r.q2r.tw + min(max(eds + cdx - r.q2r.L, 0), d3)) : 0.0f;
-                            keep = d3 < 0 || !lb_reject(b, dA2 + cdx + dq2r + cvu - ain, __fadd_rd(pen2, t3));
-                        }
-                    }
-                }
-                if (two && !keep) {
-                    const int cxs = last ? 0 : __ldg(rowX + md_ix(C.I.err, sv, C.I.nn));
-                    const int det2 = last ? (1 << 30) : cvu + gap2 + cxs - aout;
-                    const float tw2 = TW ? w1 * (float)(r.q2.tw + min(max(dep + cvu - r.q2.L, 0), det2)) : 0.0f;
-                    keep = det2 < 0 || !lb_reject(b, dA2 + cvu + dq2 + cxs - aout, __fadd_rd(pen2, tw2));
-                    if (rev && !keep) {
-                        const int cvx = __ldg(rowX + md_ix(C.I.err, v, C.I.nn));
-                        const int det3 = last ? (1 << 30) : cvx + gap2r + cus - aout;
-                        const float tw3 = TW ? w1 * (float)(r.q2r.tw + min(max(dep + cvx - r.q2r.L, 0), det3)) : 0.0f;
-                        keep = det3 < 0 || !lb_reject(b, dA2 + cvx + dq2r + cus - aout, __fadd_rd(pen2, tw3));
-                    }
-                }
-                b.n += (unsigned long long)(j == 1 ? 2 * nvar : nvar);
+                int n;
+                keep = reloc_keep<TW>(C, r, i, l0, b, n);
+                b.n += (unsigned long long)n;
             }
         }
         if (queue_survivor(wl, nq, keep, I.nd + i, lane)) {
@@ -1219,25 +1416,7 @@ __device__ void eval_swap_full(const Ctx &C, int cu, int lane, Best &b, int *wl,
         __syncwarp();
     }
     const SwapCtx &w = tc->w;
-    // u's route without seq(u) of one or two customers: the base of the insertion bound on u's
-    // route; v's route without seq(v) (from v's link record) is the base on v's route
-    const RT A1 = rt_of(join_opt<TW>(C, w.PU, w.pu, w.su), I);
-    const RT A2 = w.hasx ? rt_of(join_opt<TW>(C, w.PU, w.pu, w.sx), I) : A1;
-    const float pen1 = pen_lo(C, A1.tw - w.oldA.tw, A1.lex - w.oldA.lex, A1.dex - w.oldA.dex, 0);
-    const float pen2 = pen_lo(C, A2.tw - w.oldA.tw, A2.lex - w.oldA.lex, A2.dex - w.oldA.dex, 0);
-    const int gu1 = w.u1.dur - w.u1.tw, gu2 = w.u2.dur - w.u2.tw, gu2r = w.u2r.dur - w.u2r.tw;
-    const int4 *lk = C.D.clink + (size_t)C.s * I.nc;  // plane q at lk + q * pl
-    const size_t pl = (size_t)C.D.S * I.nc;
-    const int4 lu = lk[1 * pl + cu];
-    const int c_pu_u = lu.x, c_u_su = lu.y, c_x_sx = lu.w;  // arcs of u's route around seq(u)
-    const bool su_none = w.su == MD_NONE, sx_none = !w.hasx || w.sx == MD_NONE;
-    const int c_pu_su = su_none ? 0 : cost(I, w.pu, w.su), c_pu_sx = sx_none ? 0 : cost(I, w.pu, w.sx);
-    const int32_t *rowPU = I.dist + (size_t)w.pu * I.nn;
-    const int32_t *rowU = I.dist + (size_t)w.u * I.nn;
-    const int32_t *rowX = I.dist + (size_t)(w.hasx ? w.x : w.u) * I.nn;
-    const int32_t *rowSU = I.dist + (size_t)(su_none ? w.u : w.su) * I.nn;
-    const int32_t *rowSX = I.dist + (size_t)(sx_none ? w.u : w.sx) * I.nn;
-    const int nvar = C.sym ? 9 : 4;
+    const int4 *lk = C.D.clink + (size_t)C.s * I.nc;
     int nq = 0;
     for (int i0 = part * 32; i0 < I.nc; i0 += 32 * wpc) {
         const int i = i0 + lane;
@@ -1245,79 +1424,8 @@ __device__ void eval_swap_full(const Ctx &C, int cu, int lane, Best &b, int *wl,
         if (i < I.nc) {
             const int4 l0 = lk[i];
             if (l0.x != w.A) {
-                const int4 l1 = lk[1 * pl + i], l2 = lk[2 * pl + i];
-                const int4 l3 = lk[3 * pl + i], l4 = lk[4 * pl + i];
-                const int v = I.nd + i, pv = l0.z, sv = l0.w, sy = l1.z;
-                const bool hasy = sv >= I.nd;
-                const float penB1 = pen_lo32(C, l3.z, l3.w, l4.x);
-                const float penB2 = hasy ? pen_lo32(C, l4.y, l4.z, l4.w) : 0.0f;
-                int n = 0;
-                if (!C.sym) {
-                    // the four variants (1,1), (2,1), (1,2), (2,2) written out, sharing their arcs:
-                    // seq(v) of kv customers into u's route, seq(u) of ku into v's route
-                    const int c_pu_v = __ldg(rowPU + md_ix(C.I.err, v, C.I.nn)), c_pv_u = __ldg(rowU + md_ix(C.I.err, pv, C.I.nn));
-                    const bool sv_none = sv == MD_NONE, sy_none = !hasy || sy == MD_NONE;
-                    const int base = c_pu_v + c_pv_u - c_pu_u - l1.x;
-                    {   // (1,1)
-                        const int b1 = su_none ? 0 : __ldg(rowSU + md_ix(C.I.err, v, C.I.nn)), d1 = sv_none ? 0 : __ldg(rowU + md_ix(C.I.err, sv, C.I.nn));
-                        const int dD = base + b1 + d1 - c_u_su - l1.y;
-                        const int detA = su_none ? 0 : c_pu_v + l2.x + b1 - c_pu_su;
-                        const int detB = sv_none ? 0 : c_pv_u + gu1 + d1 - l3.x;
-                        keep = detA < 0 || detB < 0 || !lb_reject(b, dD, __fadd_rd(pen1, penB1));
-                        n = 1;
-                    }
-                    if (w.hasx) {  // (2,1)
-                        const int b2 = sx_none ? 0 : __ldg(rowSX + md_ix(C.I.err, v, C.I.nn)), e1 = sv_none ? 0 : __ldg(rowX + md_ix(C.I.err, sv, C.I.nn));
-                        const int dD = base + b2 + e1 - c_x_sx - l1.y;
-                        const int detA = sx_none ? 0 : c_pu_v + l2.x + b2 - c_pu_sx;
-                        const int detB = sv_none ? 0 : c_pv_u + gu2 + e1 - l3.x;
-                        keep = keep || detA < 0 || detB < 0 || !lb_reject(b, dD, __fadd_rd(pen2, penB1));
-                        n++;
-                    }
-                    if (hasy) {  // (1,2)
-                        const int f1 = su_none ? 0 : __ldg(rowSU + md_ix(C.I.err, sv, C.I.nn)), d2 = sy_none ? 0 : __ldg(rowU + md_ix(C.I.err, sy, C.I.nn));
-                        const int dD = base + f1 + d2 - c_u_su - l1.w;
-                        const int detA = su_none ? 0 : c_pu_v + l2.y + f1 - c_pu_su;
-                        const int detB = sy_none ? 0 : c_pv_u + gu1 + d2 - l3.y;
-                        keep = keep || detA < 0 || detB < 0 || !lb_reject(b, dD, __fadd_rd(pen1, penB2));
-                        n++;
-                    }
-                    if (w.hasx && hasy) {  // (2,2)
-                        const int f2 = sx_none ? 0 : __ldg(rowSX + md_ix(C.I.err, sv, C.I.nn)), e2 = sy_none ? 0 : __ldg(rowX + md_ix(C.I.err, sy, C.I.nn));
-                        const int dD = base + f2 + e2 - c_x_sx - l1.w;
-                        const int detA = sx_none ? 0 : c_pu_v + l2.y + f2 - c_pu_sx;
-                        const int detB = sy_none ? 0 : c_pv_u + gu2 + e2 - l3.y;
-                        keep = keep || detA < 0 || detB < 0 || !lb_reject(b, dD, __fadd_rd(pen2, penB2));
-                        n++;
-                    }
-                } else
-                for (int var = 0; var < nvar; var++) {
-                    const int ku = SW_KU[var], kv = SW_KV[var];
-                    const bool ru = SW_RU[var], rv = SW_RV[var];
-                    if ((ku == 2 && !w.hasx) || (kv == 2 && !hasy)) continue;
-                    n++;
-                    if (keep) continue;
-                    if (TW && rv) { keep = true; continue; }  // a reversed time-window sequence: no gap at hand
-                    const int qvf = (kv == 2 && rv) ? sv : v, qvl = (kv == 2 && !rv) ? sv : v;
-                    const bool au_none = ku == 1 ? su_none : sx_none;   // nothing after seq(u)
-                    const int32_t *rowAU = ku == 1 ? rowSU : rowSX;
-                    const int av = kv == 1 ? sv : sy;                   // after seq(v)
-                    const bool av_none = av == MD_NONE;
-                    const int quf = (ku == 2 && ru) ? w.x : w.u, qul = (ku == 2 && !ru) ? w.x : w.u;
-                    const int c_pu_qvf = __ldg(rowPU + md_ix(C.I.err, qvf, C.I.nn));
-                    const int c_qvl_au = au_none ? 0 : __ldg(rowAU + md_ix(C.I.err, qvl, C.I.nn));
-                    const int c_pv_quf = __ldg((quf == w.u ? rowU : rowX) + md_ix(C.I.err, pv, C.I.nn));
-                    const int c_qul_av = av_none ? 0 : __ldg((qul == w.u ? rowU : rowX) + md_ix(C.I.err, av, C.I.nn));
-                    const int dD = c_pu_qvf + c_qvl_au + c_pv_quf + c_qul_av - c_pu_u - (ku == 1 ? c_u_su : c_x_sx) -
-                                   l1.x - (kv == 1 ? l1.y : l1.w);
-                    // seq(v) into u's route without seq(u), seq(u) into v's route without seq(v)
-                    const int gv = kv == 1 ? l2.x : l2.y;
-                    const int gu = ku == 1 ? gu1 : (ru ? gu2r : gu2);
-                    const int detA = au_none ? 0 : c_pu_qvf + gv + c_qvl_au - (ku == 1 ? c_pu_su : c_pu_sx);
-                    const int detB = av_none ? 0 : c_pv_quf + gu + c_qul_av - (kv == 1 ? l3.x : l3.y);
-                    keep = detA < 0 || detB < 0 ||
-                           !lb_reject(b, dD, __fadd_rd(ku == 1 ? pen1 : pen2, kv == 1 ? penB1 : penB2));
-                }
+                int n;
+                keep = swap_keep<TW>(C, w, i, l0, b, n);
                 b.n += (unsigned long long)n;
             }
         }
@@ -1347,19 +1455,7 @@ __device__ void eval_2optstar_full(const Ctx &C, int cu, int lane, Best &b, int 
         __syncwarp();
     }
     const O2Ctx &o = tc->o;
-    // the new routes [ds_A..u] + [v..de_B] and [ds_B..pred v] + [succ u..de_A] each join two
-    // existing pieces
-    const bool su_none = o.su == MD_NONE;
-    const Seg Y2 = su_none ? Seg{0, 0, 0, 0, 0, MD_NO_LATE} : suffix_from(C, o.su);
-    const int4 *lk = C.D.clink + (size_t)C.s * I.nc;  // plane q at lk + q * pl
-    const size_t pl = (size_t)C.D.S * I.nc;
-    const int c_u_su = lk[1 * pl + cu].y;
-    const int32_t *rowU = I.dist + (size_t)o.u * I.nn;
-    const int32_t *rowSU = I.dist + (size_t)(su_none ? o.u : o.su) * I.nn;
-    const Seg8 *csuf = C.D.csuf + (size_t)C.s * I.nc;
-    float penV[5];  // w4 dV4 for dV4 = -2 .. 2
-#pragma unroll
-    for (int k = 0; k < 5; k++) penV[k] = pen_lo(C, 0, 0, 0, k - 2);
+    const int4 *lk = C.D.clink + (size_t)C.s * I.nc;
     int nq = 0;
     for (int i0 = part * 32; i0 < I.nc; i0 += 32 * wpc) {
         const int i = i0 + lane;
@@ -1367,28 +1463,7 @@ __device__ void eval_2optstar_full(const Ctx &C, int cu, int lane, Best &b, int 
         if (i < I.nc) {
             const int4 l0 = lk[i];
             if (l0.x != o.A) {
-                const int v = I.nd + i, pv = l0.z;
-                keep = pv < I.nd && o.u_last;  // v's route would empty: exact
-                if (!keep) {
-                    const int4 l1 = lk[1 * pl + i], l2 = lk[2 * pl + i];
-                    const int4 X2 = lk[5 * pl + i];  // [ds_B .. pred v]: tw, load, dur
-                    const int4 Y1 = reinterpret_cast<const int4 *>(&csuf[i])[0];  // [v .. de_B]: dist, load, dur, tw
-                    const Seg oB = seg_of(ld_seg8(&C.D.rterm[md_ix(C.I.err, (size_t)C.s * C.D.R + l0.x, (size_t)C.D.S * C.D.R)]));
-                    const int cuv = __ldg(rowU + md_ix(C.I.err, v, C.I.nn)), cps = su_none ? 0 : __ldg(rowSU + md_ix(C.I.err, pv, C.I.nn));
-                    const int dD = cuv + cps - c_u_su - l1.x;
-                    const int dsB = l2.z & 0xffff, deB = l2.z >> 16;
-                    const int dV = C.open ? 0 : (o.dsA != deB) + (dsB != o.deA) - (o.dsA != o.deA) - (dsB != deB);
-                    const int dT = o.PU.tw + Y1.w + X2.x + Y2.tw - o.oldA.tw - oB.tw;
-                    const int dL = load_ex(o.PU.load + Y1.y, I.Q) + load_ex(X2.y + Y2.load, I.Q) - o.oldA.lex -
-                                   load_ex(oB.load, I.Q);
-                    const int dU = dur_ex(o.PU.dur + Y1.z + cuv, I.D) + dur_ex(X2.z + (su_none ? 0 : Y2.dur + cps), I.D) -
-                                   o.oldA.dex - dur_ex(oB.dur, I.D);
-                    float pv4 = penV[0];
-#pragma unroll
-                    for (int k = 1; k < 5; k++) pv4 = dV == k - 2 ? penV[k] : pv4;
-                    const float pen = __fadd_rd(pen_lo32(C, dT, dL, dU), pv4);
-                    keep = !lb_reject(b, dD, pen);
-                }
+                keep = o2_keep<TW>(C, o, i, l0, b);
                 b.n += 1ull;
             }
         }
@@ -1414,13 +1489,15 @@ __device__ __forceinline__ void best_init(Best &b) {
     b.lo = b.hi = 0.0f;
 }
 
-template <bool TW>
+// LB = false leaves the lower bounds of list evaluations out of the compiled code (the persistent
+// descent, whose instances are small).
+template <bool TW, bool LB = true>
 __device__ __forceinline__ void eval_customer(const Ctx &C, int op, int cu, int lane, Best &b, int *wl,
                                               int part, int wpc, TileCtx *tc) {
     switch (op) {
     case MD_OP_RELOCATE: eval_relocate<TW>(C, cu, lane, b, wl, part, wpc, tc); break;
     case MD_OP_SWAP: eval_swap<TW>(C, cu, lane, b, wl, part, wpc, tc); break;
-    case MD_OP_TWO_OPT_STAR: eval_2optstar<TW>(C, cu, lane, b, wl, part, wpc, tc); break;
+    case MD_OP_TWO_OPT_STAR: eval_2optstar<TW, LB>(C, cu, lane, b, wl, part, wpc, tc); break;
     case MD_OP_DEPOT_INSERT: eval_depot_insert<TW>(C, cu, lane, b, part); break;
     case MD_OP_DEPOT_REPLACE: eval_depot_replace<TW>(C, cu, lane, b, part); break;
     case MD_OP_TWO_OPT: eval_2opt<TW>(C, cu, lane, b, wl, part, wpc, tc); break;

@@ -207,6 +207,9 @@ extern "C" md_status md_instance_create(const md_instance_desc *desc, md_instanc
     DevInst &d = I->d;
     d.nd = nd; d.nc = nc; d.nn = nn; d.Q = desc->Q; d.NV = desc->N_V; d.D = desc->D;
     d.variant = desc->variant; d.theta = desc->theta;
+    // the lower-bound rejection pays on neighbour lists when a move's gathers miss L2: the
+    // matrix of 2048 nodes or more is 16 MB or more, shared with every solution's summaries
+    d.list_bound = nn >= MD_LIST_BOUND_NODES;
     double *dx = nullptr, *dy = nullptr;
     int *red = nullptr;
     unsigned long long *dsum = nullptr;

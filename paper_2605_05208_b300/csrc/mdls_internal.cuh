@@ -50,6 +50,9 @@
 #define MD_STATE 16      // ints of per-solution descent state
 #define MD_STATS 24      // counters per solution (DevSols.stats)
 #define MD_LINK 6        // int4 per customer link record (DevSols.clink)
+#ifndef MD_LIST_BOUND_NODES
+#define MD_LIST_BOUND_NODES 2048  // instances from this many nodes bound list evaluations too
+#endif
 #define MD_OP_SWEEP 0x100  // set in ops[s]: this step evaluates the full neighbourhood
 #define MD_OP_MASK 0xff
 
@@ -68,6 +71,7 @@ struct DevInst {
     int Q, NV, D;
     uint32_t variant;
     int theta;
+    int list_bound;  // 1: neighbour-list evaluations use the exact lower-bound rejection
     int64_t Theta;
     double Gamma;
     const int32_t *dist;

@@ -241,10 +241,10 @@ k_descend_persistent(DevInst I, DevSols D, DevMoves M, uint32_t flags, int wpc_f
                 Best b;
                 best_init(b);
                 if (C.lists && I.theta <= 64 && (op == MD_OP_RELOCATE || op == MD_OP_SWAP))
-                    eval_tile_lists<TW>(C, op, t * MD_EVAL_WARPS, T * MD_EVAL_WARPS, b, s_wl, s_tc, s_cnt);
+                    eval_tile_lists<TW, false>(C, op, t * MD_EVAL_WARPS, T * MD_EVAL_WARPS, b, s_wl, s_tc, s_cnt);
                 else if (op >= 0)
                     for (int gw = t * MD_EVAL_WARPS + warp; gw < I.nc * wpc; gw += T * MD_EVAL_WARPS)
-                        eval_customer<TW>(C, op, gw / wpc, lane, b, s_wl[warp], gw % wpc, wpc, &s_tc[warp]);
+                        eval_customer<TW, false>(C, op, gw / wpc, lane, b, s_wl[warp], gw % wpc, wpc, &s_tc[warp]);
                 warp_commit(C, b, (size_t)t * MD_EVAL_WARPS + warp, lane);
             }
             if (lane == 0) {
