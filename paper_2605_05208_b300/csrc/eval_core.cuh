@@ -292,6 +292,22 @@ __device__ __forceinline__ void dequeue_32(int *wl, int &nq, int lane) {
     __syncwarp();
 }
 
+// The matrix rows a customer u's bounds read: u's, its successor's, the successor after that, its
+// predecessor's (u's row stands in for a missing node).  In global memory, or staged in shared
+// memory by the full-neighbourhood kernel; read with plain (generic) loads.
+struct Rows {
+    const int32_t *u, *su, *sx, *pu;
+};
+
+__device__ __forceinline__ Rows global_rows(const DevInst &I, int u, int su, int sx, int pu) {
+    Rows r;
+    r.u = I.dist + (size_t)u * I.nn;
+    r.su = I.dist + (size_t)(su == MD_NONE ? u : su) * I.nn;
+    r.sx = I.dist + (size_t)(sx == MD_NONE ? u : sx) * I.nn;
+    r.pu = I.dist + (size_t)pu * I.nn;
+    return r;
+}
+
 // A summary with its end nodes; e marks the empty sequence.
 struct SN {
     Seg s;
@@ -853,7 +869,8 @@ __device__ __forceinline__ void swap_cand(const Ctx &C, const SwapCtx &w, int v,
 // ------------------------------------------------------------------------------------------
 
 template <bool TW>
-__device__ __forceinline__ bool reloc_keep(const Ctx &C, const RelocCtx &r, int i, const int4 l0, const Best &b, int &n) {
+__device__ __forceinline__ bool reloc_keep(const Ctx &C, const RelocCtx &r, const Rows &rw, int i, const int4 l0,
+                                           const Best &b, int &n) {
     const DevInst &I = C.I;
     const int4 *lk = C.D.clink + (size_t)C.s * I.nc;  // plane q at lk + q * pl
     const size_t pl = (size_t)C.D.S * I.nc;
@@ -867,13 +884,13 @@ __device__ __forceinline__ bool reloc_keep(const Ctx &C, const RelocCtx &r, int 
     // v's route gains at least tw_Q + min(warp at Q's arrival, detour) of time warp: the warp
     // arriving late at Q's first node after v's earliest completion, when the detour covers it
     const float w1 = C.wf[0] * (1.0f - 1e-5f);
-    const int32_t *rowU = I.dist + (size_t)r.u * I.nn;
-    const int32_t *rowX = I.dist + (size_t)(two ? r.x : r.u) * I.nn;
+    const int32_t *rowU = rw.u;
+    const int32_t *rowX = two ? rw.su : rw.u;  // x = succ u when seq(u) has two customers
     const int aout = lk[1 * pl + i].y;
     const int dep = TW ? lk[5 * pl + i].w : 0;  // earliest completion at v
     const bool last = sv == MD_NONE;  // v ends an open route: nothing follows seq(u)
-    const int cvu = __ldg(rowU + md_ix(C.I.err, v, C.I.nn));
-    const int cus = last ? 0 : __ldg(rowU + md_ix(C.I.err, sv, C.I.nn));
+    const int cvu = rowU[md_ix(C.I.err, v, C.I.nn)];
+    const int cus = last ? 0 : rowU[md_ix(C.I.err, sv, C.I.nn)];
     const int det1 = last ? (1 << 30) : cvu + gap1 + cus - aout;
     const float tw1 = TW ? w1 * (float)(r.q1.tw + min(max(dep + cvu - r.q1.L, 0), det1)) : 0.0f;
     bool keep = det1 < 0 || !lb_reject(b, dA1 + cvu + cus - aout, __fadd_rd(pen1, tw1));
@@ -881,17 +898,17 @@ __device__ __forceinline__ bool reloc_keep(const Ctx &C, const RelocCtx &r, int 
         // v first on its route: seq(u) also goes between the departure depot and v
         const int ds = l0.z, ain = lk[1 * pl + i].x;  // c(ds, v)
         const int eds = TW ? __ldg(&I.node[md_ix(C.I.err, ds, C.I.nn)]).z : 0;
-        const int cdu = __ldg(rowU + md_ix(C.I.err, ds, C.I.nn));
+        const int cdu = rowU[md_ix(C.I.err, ds, C.I.nn)];
         const int d1 = cdu + gap1 + cvu - ain;
         const float t1 = TW ? w1 * (float)(r.q1.tw + min(max(eds + cdu - r.q1.L, 0), d1)) : 0.0f;
         keep = d1 < 0 || !lb_reject(b, dA1 + cdu + cvu - ain, __fadd_rd(pen1, t1));
         if (two && !keep) {
-            const int cxv = __ldg(rowX + md_ix(C.I.err, v, C.I.nn));
+            const int cxv = rowX[md_ix(C.I.err, v, C.I.nn)];
             const int d2 = cdu + gap2 + cxv - ain;
             const float t2 = TW ? w1 * (float)(r.q2.tw + min(max(eds + cdu - r.q2.L, 0), d2)) : 0.0f;
             keep = d2 < 0 || !lb_reject(b, dA2 + cdu + dq2 + cxv - ain, __fadd_rd(pen2, t2));
             if (rev && !keep) {
-                const int cdx = __ldg(rowX + md_ix(C.I.err, ds, C.I.nn));
+                const int cdx = rowX[md_ix(C.I.err, ds, C.I.nn)];
                 const int d3 = cdx + gap2r + cvu - ain;
                 const float t3 = TW ? w1 * (float)(r.q2r.tw + min(max(eds + cdx - r.q2r.L, 0), d3)) : 0.0f;
                 keep = d3 < 0 || !lb_reject(b, dA2 + cdx + dq2r + cvu - ain, __fadd_rd(pen2, t3));
@@ -899,12 +916,12 @@ __device__ __forceinline__ bool reloc_keep(const Ctx &C, const RelocCtx &r, int 
         }
     }
     if (two && !keep) {
-        const int cxs = last ? 0 : __ldg(rowX + md_ix(C.I.err, sv, C.I.nn));
+        const int cxs = last ? 0 : rowX[md_ix(C.I.err, sv, C.I.nn)];
         const int det2 = last ? (1 << 30) : cvu + gap2 + cxs - aout;
         const float tw2 = TW ? w1 * (float)(r.q2.tw + min(max(dep + cvu - r.q2.L, 0), det2)) : 0.0f;
         keep = det2 < 0 || !lb_reject(b, dA2 + cvu + dq2 + cxs - aout, __fadd_rd(pen2, tw2));
         if (rev && !keep) {
-            const int cvx = __ldg(rowX + md_ix(C.I.err, v, C.I.nn));
+            const int cvx = rowX[md_ix(C.I.err, v, C.I.nn)];
             const int det3 = last ? (1 << 30) : cvx + gap2r + cus - aout;
             const float tw3 = TW ? w1 * (float)(r.q2r.tw + min(max(dep + cvx - r.q2r.L, 0), det3)) : 0.0f;
             keep = det3 < 0 || !lb_reject(b, dA2 + cvx + dq2r + cus - aout, __fadd_rd(pen2, tw3));
@@ -914,7 +931,8 @@ __device__ __forceinline__ bool reloc_keep(const Ctx &C, const RelocCtx &r, int 
 }
 
 template <bool TW>
-__device__ __forceinline__ bool swap_keep(const Ctx &C, const SwapCtx &w, int i, const int4 l0, const Best &b, int &n) {
+__device__ __forceinline__ bool swap_keep(const Ctx &C, const SwapCtx &w, const Rows &rw, int i, const int4 l0,
+                                          const Best &b, int &n) {
     const DevInst &I = C.I;
     const int4 *lk = C.D.clink + (size_t)C.s * I.nc;
     const size_t pl = (size_t)C.D.S * I.nc;
@@ -926,11 +944,8 @@ __device__ __forceinline__ bool swap_keep(const Ctx &C, const SwapCtx &w, int i,
     const int gu1 = w.u1.dur - w.u1.tw, gu2 = w.u2.dur - w.u2.tw, gu2r = w.u2r.dur - w.u2r.tw;
     const int c_pu_u = w.c_pu_u, c_u_su = w.c_u_su, c_x_sx = w.c_x_sx, c_pu_su = w.c_pu_su, c_pu_sx = w.c_pu_sx;
     const bool su_none = w.su == MD_NONE, sx_none = !w.hasx || w.sx == MD_NONE;
-    const int32_t *rowPU = I.dist + (size_t)w.pu * I.nn;
-    const int32_t *rowU = I.dist + (size_t)w.u * I.nn;
-    const int32_t *rowX = I.dist + (size_t)(w.hasx ? w.x : w.u) * I.nn;
-    const int32_t *rowSU = I.dist + (size_t)(su_none ? w.u : w.su) * I.nn;
-    const int32_t *rowSX = I.dist + (size_t)(sx_none ? w.u : w.sx) * I.nn;
+    const int32_t *rowPU = rw.pu, *rowU = rw.u, *rowSU = rw.su, *rowSX = rw.sx;
+    const int32_t *rowX = w.hasx ? rw.su : rw.u;  // x = succ u
     // v's route without seq(v) of one or two customers is the base of the bound on v's route
     const float penB1 = pen_lo32(C, l3.z, l3.w, l4.x);
     const float penB2 = hasy ? pen_lo32(C, l4.y, l4.z, l4.w) : 0.0f;
@@ -939,11 +954,11 @@ __device__ __forceinline__ bool swap_keep(const Ctx &C, const SwapCtx &w, int i,
     if (!C.sym) {
         // the four variants (1,1), (2,1), (1,2), (2,2) written out, sharing their arcs: seq(v) of
         // kv customers into u's route, seq(u) of ku into v's route
-        const int c_pu_v = __ldg(rowPU + md_ix(C.I.err, v, C.I.nn)), c_pv_u = __ldg(rowU + md_ix(C.I.err, pv, C.I.nn));
+        const int c_pu_v = rowPU[md_ix(C.I.err, v, C.I.nn)], c_pv_u = rowU[md_ix(C.I.err, pv, C.I.nn)];
         const bool sv_none = sv == MD_NONE, sy_none = !hasy || sy == MD_NONE;
         const int base = c_pu_v + c_pv_u - c_pu_u - l1.x;
         {   // (1,1)
-            const int b1 = su_none ? 0 : __ldg(rowSU + md_ix(C.I.err, v, C.I.nn)), d1 = sv_none ? 0 : __ldg(rowU + md_ix(C.I.err, sv, C.I.nn));
+            const int b1 = su_none ? 0 : rowSU[md_ix(C.I.err, v, C.I.nn)], d1 = sv_none ? 0 : rowU[md_ix(C.I.err, sv, C.I.nn)];
             const int dD = base + b1 + d1 - c_u_su - l1.y;
             const int detA = su_none ? 0 : c_pu_v + l2.x + b1 - c_pu_su;
             const int detB = sv_none ? 0 : c_pv_u + gu1 + d1 - l3.x;
@@ -951,7 +966,7 @@ __device__ __forceinline__ bool swap_keep(const Ctx &C, const SwapCtx &w, int i,
             n = 1;
         }
         if (w.hasx) {  // (2,1)
-            const int b2 = sx_none ? 0 : __ldg(rowSX + md_ix(C.I.err, v, C.I.nn)), e1 = sv_none ? 0 : __ldg(rowX + md_ix(C.I.err, sv, C.I.nn));
+            const int b2 = sx_none ? 0 : rowSX[md_ix(C.I.err, v, C.I.nn)], e1 = sv_none ? 0 : rowX[md_ix(C.I.err, sv, C.I.nn)];
             const int dD = base + b2 + e1 - c_x_sx - l1.y;
             const int detA = sx_none ? 0 : c_pu_v + l2.x + b2 - c_pu_sx;
             const int detB = sv_none ? 0 : c_pv_u + gu2 + e1 - l3.x;
@@ -959,7 +974,7 @@ __device__ __forceinline__ bool swap_keep(const Ctx &C, const SwapCtx &w, int i,
             n++;
         }
         if (hasy) {  // (1,2)
-            const int f1 = su_none ? 0 : __ldg(rowSU + md_ix(C.I.err, sv, C.I.nn)), d2 = sy_none ? 0 : __ldg(rowU + md_ix(C.I.err, sy, C.I.nn));
+            const int f1 = su_none ? 0 : rowSU[md_ix(C.I.err, sv, C.I.nn)], d2 = sy_none ? 0 : rowU[md_ix(C.I.err, sy, C.I.nn)];
             const int dD = base + f1 + d2 - c_u_su - l1.w;
             const int detA = su_none ? 0 : c_pu_v + l2.y + f1 - c_pu_su;
             const int detB = sy_none ? 0 : c_pv_u + gu1 + d2 - l3.y;
@@ -967,7 +982,7 @@ __device__ __forceinline__ bool swap_keep(const Ctx &C, const SwapCtx &w, int i,
             n++;
         }
         if (w.hasx && hasy) {  // (2,2)
-            const int f2 = sx_none ? 0 : __ldg(rowSX + md_ix(C.I.err, sv, C.I.nn)), e2 = sy_none ? 0 : __ldg(rowX + md_ix(C.I.err, sy, C.I.nn));
+            const int f2 = sx_none ? 0 : rowSX[md_ix(C.I.err, sv, C.I.nn)], e2 = sy_none ? 0 : rowX[md_ix(C.I.err, sy, C.I.nn)];
             const int dD = base + f2 + e2 - c_x_sx - l1.w;
             const int detA = sx_none ? 0 : c_pu_v + l2.y + f2 - c_pu_sx;
             const int detB = sy_none ? 0 : c_pv_u + gu2 + e2 - l3.y;
@@ -989,10 +1004,10 @@ __device__ __forceinline__ bool swap_keep(const Ctx &C, const SwapCtx &w, int i,
         const int av = kv == 1 ? sv : sy;                   // after seq(v)
         const bool av_none = av == MD_NONE;
         const int quf = (ku == 2 && ru) ? w.x : w.u, qul = (ku == 2 && !ru) ? w.x : w.u;
-        const int c_pu_qvf = __ldg(rowPU + md_ix(C.I.err, qvf, C.I.nn));
-        const int c_qvl_au = au_none ? 0 : __ldg(rowAU + md_ix(C.I.err, qvl, C.I.nn));
-        const int c_pv_quf = __ldg((quf == w.u ? rowU : rowX) + md_ix(C.I.err, pv, C.I.nn));
-        const int c_qul_av = av_none ? 0 : __ldg((qul == w.u ? rowU : rowX) + md_ix(C.I.err, av, C.I.nn));
+        const int c_pu_qvf = rowPU[md_ix(C.I.err, qvf, C.I.nn)];
+        const int c_qvl_au = au_none ? 0 : rowAU[md_ix(C.I.err, qvl, C.I.nn)];
+        const int c_pv_quf = (quf == w.u ? rowU : rowX)[md_ix(C.I.err, pv, C.I.nn)];
+        const int c_qul_av = av_none ? 0 : (qul == w.u ? rowU : rowX)[md_ix(C.I.err, av, C.I.nn)];
         const int dD = c_pu_qvf + c_qvl_au + c_pv_quf + c_qul_av - c_pu_u - (ku == 1 ? c_u_su : c_x_sx) -
                        l1.x - (kv == 1 ? l1.y : l1.w);
         // seq(v) into u's route without seq(u), seq(u) into v's route without seq(v)
@@ -1083,8 +1098,9 @@ __device__ void eval_tile_lists(const Ctx &C, int op, int c0, int cstride, Best 
                 if (LB && I.list_bound && !(C.flags & MD_EVAL_DUMP)) {
                     const int i = v - I.nd;
                     const int4 l0 = C.D.clink[md_ix(C.I.err, (size_t)C.s * I.nc + i, (size_t)C.D.S * C.I.nc)];
-                    keep = op == MD_OP_RELOCATE ? reloc_keep<TW>(C, tc[w].r, i, l0, b, n)
-                                                : swap_keep<TW>(C, tc[w].w, i, l0, b, n);
+                    keep = op == MD_OP_RELOCATE
+                               ? reloc_keep<TW>(C, tc[w].r, global_rows(I, tc[w].r.u, tc[w].r.su, tc[w].r.sx, tc[w].r.pu), i, l0, b, n)
+                               : swap_keep<TW>(C, tc[w].w, global_rows(I, tc[w].w.u, tc[w].w.su, tc[w].w.sx, tc[w].w.pu), i, l0, b, n);
                 }
                 if (!keep) b.n += (unsigned long long)n;
                 else if (op == MD_OP_RELOCATE) reloc_inter<TW>(C, tc[w].r, v, b);
@@ -1156,7 +1172,7 @@ __device__ __forceinline__ void o2_cand(const Ctx &C, const O2Ctx &o, int v, Bes
 // 2-opt* of u with v on another route (one move).  The new routes [ds_A..u] + [v..de_B] and
 // [ds_B..pred v] + [succ u..de_A] each join two existing pieces.
 template <bool TW>
-__device__ __forceinline__ bool o2_keep(const Ctx &C, const O2Ctx &o, int i, const int4 l0, const Best &b) {
+__device__ __forceinline__ bool o2_keep(const Ctx &C, const O2Ctx &o, const Rows &rw, int i, const int4 l0, const Best &b) {
     const DevInst &I = C.I;
     const int pv = l0.z;
     if (pv < I.nd && o.u_last) return true;  // v's route would empty: exact
@@ -1168,9 +1184,8 @@ __device__ __forceinline__ bool o2_keep(const Ctx &C, const O2Ctx &o, int i, con
     const int4 X2 = lk[5 * pl + i];  // [ds_B .. pred v]: tw, load, dur
     const int4 Y1 = reinterpret_cast<const int4 *>(&C.D.csuf[md_ix(C.I.err, (size_t)C.s * I.nc + i, (size_t)C.D.S * C.I.nc)])[0];  // [v .. de_B]: dist, load, dur, tw
     const Seg oB = seg_of(ld_seg8(&C.D.rterm[md_ix(C.I.err, (size_t)C.s * C.D.R + l0.x, (size_t)C.D.S * C.D.R)]));
-    const int32_t *rowU = I.dist + (size_t)o.u * I.nn;
-    const int32_t *rowSU = I.dist + (size_t)(su_none ? o.u : o.su) * I.nn;
-    const int cuv = __ldg(rowU + md_ix(C.I.err, v, C.I.nn)), cps = su_none ? 0 : __ldg(rowSU + md_ix(C.I.err, pv, C.I.nn));
+    const int32_t *rowU = rw.u, *rowSU = rw.su;
+    const int cuv = rowU[md_ix(C.I.err, v, C.I.nn)], cps = su_none ? 0 : rowSU[md_ix(C.I.err, pv, C.I.nn)];
     const int dD = cuv + cps - o.c_u_su - l1.x;
     const int dsB = l2.z & 0xffff, deB = l2.z >> 16;
     const int dV = C.open ? 0 : (o.dsA != deB) + (dsB != o.deA) - (o.dsA != o.deA) - (dsB != deB);
@@ -1211,7 +1226,7 @@ __device__ void eval_2optstar(const Ctx &C, int cu, int lane, Best &b, int *wl, 
                 const int i = v - I.nd;
                 const int4 l0 = C.D.clink[md_ix(C.I.err, (size_t)C.s * I.nc + i, (size_t)C.D.S * C.I.nc)];
                 if (l0.x == o.A) continue;  // no move on u's own route
-                if (!o2_keep<TW>(C, o, i, l0, b)) {
+                if (!o2_keep<TW>(C, o, global_rows(I, o.u, o.su, MD_NONE, o.u), i, l0, b)) {
                     b.n += 1ull;
                     continue;
                 }
@@ -1377,6 +1392,7 @@ __device__ void eval_relocate_full(const Ctx &C, int cu, int lane, Best &b, int 
         __syncwarp();
     }
     const RelocCtx &r = tc->r;
+    const Rows rw = global_rows(I, r.u, r.su, r.sx, r.pu);
     const int4 *lk = C.D.clink + (size_t)C.s * I.nc;
     int nq = 0;
     for (int i0 = part * 32; i0 < I.nc; i0 += 32 * wpc) {
@@ -1386,7 +1402,7 @@ __device__ void eval_relocate_full(const Ctx &C, int cu, int lane, Best &b, int 
             const int4 l0 = lk[i];
             if (l0.x != r.A) {
                 int n;
-                keep = reloc_keep<TW>(C, r, i, l0, b, n);
+                keep = reloc_keep<TW>(C, r, rw, i, l0, b, n);
                 b.n += (unsigned long long)n;
             }
         }
@@ -1416,6 +1432,7 @@ __device__ void eval_swap_full(const Ctx &C, int cu, int lane, Best &b, int *wl,
         __syncwarp();
     }
     const SwapCtx &w = tc->w;
+    const Rows rw = global_rows(I, w.u, w.su, w.sx, w.pu);
     const int4 *lk = C.D.clink + (size_t)C.s * I.nc;
     int nq = 0;
     for (int i0 = part * 32; i0 < I.nc; i0 += 32 * wpc) {
@@ -1425,7 +1442,7 @@ __device__ void eval_swap_full(const Ctx &C, int cu, int lane, Best &b, int *wl,
             const int4 l0 = lk[i];
             if (l0.x != w.A) {
                 int n;
-                keep = swap_keep<TW>(C, w, i, l0, b, n);
+                keep = swap_keep<TW>(C, w, rw, i, l0, b, n);
                 b.n += (unsigned long long)n;
             }
         }
@@ -1455,6 +1472,7 @@ __device__ void eval_2optstar_full(const Ctx &C, int cu, int lane, Best &b, int 
         __syncwarp();
     }
     const O2Ctx &o = tc->o;
+    const Rows rw = global_rows(I, o.u, o.su, MD_NONE, o.u);
     const int4 *lk = C.D.clink + (size_t)C.s * I.nc;
     int nq = 0;
     for (int i0 = part * 32; i0 < I.nc; i0 += 32 * wpc) {
@@ -1463,7 +1481,7 @@ __device__ void eval_2optstar_full(const Ctx &C, int cu, int lane, Best &b, int 
         if (i < I.nc) {
             const int4 l0 = lk[i];
             if (l0.x != o.A) {
-                keep = o2_keep<TW>(C, o, i, l0, b);
+                keep = o2_keep<TW>(C, o, rw, i, l0, b);
                 b.n += 1ull;
             }
         }

@@ -586,3 +586,35 @@ def test_wide_step_matches_single_cta_step_and_oracle(md, oracle_lib, stream, ca
                       sweep_every=kw["sweep_every"])
         assert runs[1][0][s] == canon(spec, d.solution), s
         assert list(runs[1][1][s]) == [d.moves_scored, d.steps, d.accepted_steps, d.applied_moves, d.passes], s
+
+
+@pytest.mark.parametrize("case", ["mdvrptw-3x2100", "mdovrp-3x2100", "mdvrptw-3x2100-random-routes"])
+def test_full_neighbourhood_of_2100_customers_matches_oracle(md, oracle_lib, case):
+    # a full neighbourhood of more than 2048 customers (eight warps per customer, the bounds'
+    # large-instance paths): leaders, scored counts and selections against the oracle
+    if case.startswith("mdvrptw"):
+        spec = W.gen_mdvrptw(61, n_depots=3, n_customers=2100, theta=0)
+    else:
+        spec = W.gen_mdovrp(62, n_depots=3, n_customers=2100)
+    if case.endswith("random-routes"):
+        sols = [random_solution(spec, 63, max_len=12)]
+    else:
+        sols = W.initial_solutions(spec, 64, 1)
+    o = oracle_lib.Instance(spec)
+    inst, S = setup(md, spec, sols, R=len(sols[0]) + 64, K=2 * max(len(r) for r in sols[0]) + 16)
+    lam = (1.0, 1.0, 1.0, 1.0)
+    for op in (W.OP_RELOCATE, W.OP_SWAP, W.OP_TWO_OPT_STAR):
+        M = md.Moves(S)
+        M.evaluate(np.array([op], np.int32), flags=md.EVAL_FOLLOWERS)
+        ids, f, n = M.leaders()
+        mv, scored = o.eval_op(sols[0], op, lam)
+        assert n[0] == scored, op
+        neg = mv[mv["dF"] < 0]
+        if len(neg):
+            best = neg[np.lexsort((neg["id"] & 0xFFFFFFFF, neg["dF"]))[0]]
+            assert ids[0] == best["id"] and close(f[0], best["dF"]), op
+        else:
+            assert ids[0] == 0
+        M.select(multi=True)
+        assert sorted(M.selection()[0]) == sorted(o.select(mv, len(sols[0]), multi=True)), op
+        M.close()
