@@ -931,13 +931,11 @@ __device__ __forceinline__ bool reloc_keep(const Ctx &C, const RelocCtx &r, cons
 }
 
 template <bool TW>
-__device__ __forceinline__ bool swap_keep(const Ctx &C, const SwapCtx &w, const Rows &rw, int i, const int4 l0,
+// l[0..4]: v's first five link planes
+__device__ __forceinline__ bool swap_keep(const Ctx &C, const SwapCtx &w, const Rows &rw, int i, const int4 *l,
                                           const Best &b, int &n) {
     const DevInst &I = C.I;
-    const int4 *lk = C.D.clink + (size_t)C.s * I.nc;
-    const size_t pl = (size_t)C.D.S * I.nc;
-    const int4 l1 = lk[1 * pl + i], l2 = lk[2 * pl + i];
-    const int4 l3 = lk[3 * pl + i], l4 = lk[4 * pl + i];
+    const int4 l0 = l[0], l1 = l[1], l2 = l[2], l3 = l[3], l4 = l[4];
     const int v = I.nd + i, pv = l0.z, sv = l0.w, sy = l1.z;
     const bool hasy = sv >= I.nd;
     const float pen1 = w.pen1, pen2 = w.pen2;
@@ -1097,10 +1095,16 @@ __device__ void eval_tile_lists(const Ctx &C, int op, int c0, int cstride, Best 
                 bool keep = true;
                 if (LB && I.list_bound && !(C.flags & MD_EVAL_DUMP)) {
                     const int i = v - I.nd;
-                    const int4 l0 = C.D.clink[md_ix(C.I.err, (size_t)C.s * I.nc + i, (size_t)C.D.S * C.I.nc)];
-                    keep = op == MD_OP_RELOCATE
-                               ? reloc_keep<TW>(C, tc[w].r, global_rows(I, tc[w].r.u, tc[w].r.su, tc[w].r.sx, tc[w].r.pu), i, l0, b, n)
-                               : swap_keep<TW>(C, tc[w].w, global_rows(I, tc[w].w.u, tc[w].w.su, tc[w].w.sx, tc[w].w.pu), i, l0, b, n);
+                    const int4 *lkv = C.D.clink + md_ix(C.I.err, (size_t)C.s * I.nc + i, (size_t)C.D.S * C.I.nc);
+                    const size_t pl = (size_t)C.D.S * I.nc;
+                    if (op == MD_OP_RELOCATE) {
+                        keep = reloc_keep<TW>(C, tc[w].r, global_rows(I, tc[w].r.u, tc[w].r.su, tc[w].r.sx, tc[w].r.pu), i,
+                                              lkv[0], b, n);
+                    } else {
+                        const int4 l[5] = {lkv[0], lkv[pl], lkv[2 * pl], lkv[3 * pl], lkv[4 * pl]};
+                        keep = swap_keep<TW>(C, tc[w].w, global_rows(I, tc[w].w.u, tc[w].w.su, tc[w].w.sx, tc[w].w.pu), i,
+                                             l, b, n);
+                    }
                 }
                 if (!keep) b.n += (unsigned long long)n;
                 else if (op == MD_OP_RELOCATE) reloc_inter<TW>(C, tc[w].r, v, b);
@@ -1395,11 +1399,15 @@ __device__ void eval_relocate_full(const Ctx &C, int cu, int lane, Best &b, int 
     const Rows rw = global_rows(I, r.u, r.su, r.sx, r.pu);
     const int4 *lk = C.D.clink + (size_t)C.s * I.nc;
     int nq = 0;
+    // the first link plane of the next batch is loaded one batch ahead, so the bound's matrix
+    // reads (which need the candidate's successor) do not wait for it
+    int4 l0n = part * 32 + lane < I.nc ? lk[part * 32 + lane] : make_int4(-1, 0, 0, 0);
     for (int i0 = part * 32; i0 < I.nc; i0 += 32 * wpc) {
         const int i = i0 + lane;
         bool keep = false;
+        const int4 l0 = l0n;
+        if (i + 32 * wpc < I.nc) l0n = lk[i + 32 * wpc];
         if (i < I.nc) {
-            const int4 l0 = lk[i];
             if (l0.x != r.A) {
                 int n;
                 keep = reloc_keep<TW>(C, r, rw, i, l0, b, n);
@@ -1435,14 +1443,25 @@ __device__ void eval_swap_full(const Ctx &C, int cu, int lane, Best &b, int *wl,
     const Rows rw = global_rows(I, w.u, w.su, w.sx, w.pu);
     const int4 *lk = C.D.clink + (size_t)C.s * I.nc;
     int nq = 0;
+    // the link planes of the next batch are loaded one batch ahead
+    const size_t pl = (size_t)C.D.S * I.nc;
+    int4 ln[5];
+    const int first = part * 32 + lane;
+#pragma unroll
+    for (int q = 0; q < 5; q++) ln[q] = first < I.nc ? lk[q * pl + first] : make_int4(-1, 0, 0, 0);
     for (int i0 = part * 32; i0 < I.nc; i0 += 32 * wpc) {
         const int i = i0 + lane;
         bool keep = false;
+        int4 l[5];
+#pragma unroll
+        for (int q = 0; q < 5; q++) l[q] = ln[q];
+        if (i + 32 * wpc < I.nc)
+#pragma unroll
+            for (int q = 0; q < 5; q++) ln[q] = lk[q * pl + i + 32 * wpc];
         if (i < I.nc) {
-            const int4 l0 = lk[i];
-            if (l0.x != w.A) {
+            if (l[0].x != w.A) {
                 int n;
-                keep = swap_keep<TW>(C, w, rw, i, l0, b, n);
+                keep = swap_keep<TW>(C, w, rw, i, l, b, n);
                 b.n += (unsigned long long)n;
             }
         }
@@ -1475,11 +1494,13 @@ __device__ void eval_2optstar_full(const Ctx &C, int cu, int lane, Best &b, int 
     const Rows rw = global_rows(I, o.u, o.su, MD_NONE, o.u);
     const int4 *lk = C.D.clink + (size_t)C.s * I.nc;
     int nq = 0;
+    int4 l0n = part * 32 + lane < I.nc ? lk[part * 32 + lane] : make_int4(-1, 0, 0, 0);  // one batch ahead
     for (int i0 = part * 32; i0 < I.nc; i0 += 32 * wpc) {
         const int i = i0 + lane;
         bool keep = false;
+        const int4 l0 = l0n;
+        if (i + 32 * wpc < I.nc) l0n = lk[i + 32 * wpc];
         if (i < I.nc) {
-            const int4 l0 = lk[i];
             if (l0.x != o.A) {
                 keep = o2_keep<TW>(C, o, rw, i, l0, b);
                 b.n += 1ull;
