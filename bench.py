@@ -518,7 +518,7 @@ def run_batch(args):
     }))
 
 
-LEARNED_SOL = 8         # solutions per rank and step
+LEARNED_SOL = 16        # solutions per rank and step
 LEARNED_SEEDS = 5       # instances of seeds 1..5; the timed steps cycle through them
 LEARNED_POOL = 256      # eta-ranked candidate pool per customer that the MLP scores
 LEARNED_TOPK = 64
@@ -881,7 +881,7 @@ REPAIR_RULES = ("FBI", "IBI", "FRI", "IRI")
 
 
 def repair_workload(rank: int = 0, large: bool = False):
-    """The bench instance's 32 initial solutions (large: the 20 x 10000 instance's 8) with a
+    """The bench instance's 32 initial solutions (large: the 20 x 10000 instance's 16) with a
     quarter of their routes and a tenth of the remaining customers removed, as a route exchange
     leaves them."""
     if large:
@@ -1155,7 +1155,7 @@ def main():
                                            "batch16-uneven", "plain-20x10000", "repair-mdvrptw-6x288",
                                            "mdvrp-6x288-2opt", "memetic-mdvrptw-6x288", "repair-mdvrptw-20x10000"],
                     default="learned-20x10000")
-    ap.add_argument("--solutions", type=int, default=0, help="solutions per rank of the learned workload (0: 8)")
+    ap.add_argument("--solutions", type=int, default=0, help="solutions per rank of the learned workload (0: 16)")
     ap.add_argument("--seeds", type=int, default=0, help="instances of the learned workload (0: seeds 1..5)")
     ap.add_argument("--plain-seeds", type=int, default=1,
                     help="seeds whose plain full-neighbourhood descents are timed beside the learned ones")

@@ -329,7 +329,9 @@ md_status md_solutions_stats(md_solutions *sols, int64_t *per_sol, void *stream)
 #define MD_INSERT_IRI 3
 
 /* Loads partial solutions and inserts the unrouted customers of solution s by rules[s]
- * (MD_INSERT_*; host int32 [n_sol]), one CTA per solution on the device; on return sols holds complete solutions with every summary
+ * (MD_INSERT_*; host int32 [n_sol]), one thread-block cluster per solution on the device (its
+ * CTAs split the solution's list and pick each insertion together; the cluster size follows
+ * md_solutions_set_repair_split); on return sols holds complete solutions with every summary
  * and total rebuilt (lambda reset to 1), ready for md_descend.
  *   route_nodes / route_offsets / routes_per_sol: host, the md_solutions_load layout, except
  *     that a solution may have no route (routes_per_sol[s] = 0) and leaves customers out;
@@ -347,6 +349,12 @@ md_status md_repair_insert(md_solutions *sols, const int32_t *rules, const int32
                            const int64_t *route_offsets, const int32_t *routes_per_sol,
                            const int32_t *unrouted, const int64_t *unrouted_offsets, int32_t *order,
                            void *stream);
+
+/* How md_repair_insert spreads a solution over CTAs: one CTA per per_cta listed customers of the
+ * longest list, at most 16 (0: 128, the default).  A cluster size the device cannot place is not
+ * used; among the rest the call picks the one that finishes every solution in the fewest waves
+ * per CTA.  Results do not depend on it.  MD_ERR_ARG on a null set or per_cta < 0. */
+md_status md_solutions_set_repair_split(md_solutions *sols, int32_t per_cta);
 
 /* Batches of instances of uneven size.  A batch groups solution sets of different instances
  * (each from md_solutions_create/load on the same device, each still owned by the caller) so

@@ -285,6 +285,7 @@ struct md_solutions {
     uint8_t *perm_dev;   // operator order of the last md_descend call
     size_t perm_bytes;
     md_moves *scratch;   // evaluation scratch of md_descend, created on first use
+    int repair_per_cta;  // md_repair_insert: listed customers per CTA of a cluster (0: the default)
 };
 
 struct md_moves {

@@ -2,29 +2,37 @@
 // inserted one at a time by feasible / infeasible best insertion (FBI, IBI) or feasible /
 // infeasible regret insertion (FRI, IRI), for many solutions at once.
 //
-// One CTA per solution runs the whole repair.  An insertion after position k joins three
+// One cluster of CTAs per solution runs the whole repair; the listed customers are split over
+// its CTAs in contiguous ranges.  An insertion after position k joins three
 // summaries that already exist -- the prefix [ds..c_k] (cpre of c_k, or the depot), the
 // customer, the suffix [c_{k+1}..de] (csuf of c_{k+1}, or the depot) -- so its feasibility
 // (load, time warp, duration) takes O(1) per position; its cost is the closed form
 // c(c_k, u) + c(u, c_{k+1}) - c(c_k, c_{k+1}).  The block keeps, per listed customer and route,
 // the route's cheapest insertion; an insertion changes one route, so each round rescans only
 // that route's positions for every listed customer (the first round scans all routes).  Per
-// customer the block then forms its best insertion and its best cost in another route (for the
-// regret), picks the customer by the rule; warp 0 inserts it and rebuilds that route's prefix
-// and suffix summaries (the subsequence tables, which only the descent reads, are rebuilt once
-// at the end).  Ties break as the rules state: cost, then the customer's place in the list, then
-// route slot, then position.
+// customer its CTA then forms its best insertion and its best cost in another route (for the
+// regret) and picks its candidate by the rule; the cluster's first CTA takes the best of the
+// CTAs' candidates from their shared memory, and its warp 0 inserts it and rebuilds that
+// route's prefix and suffix summaries (the subsequence tables, which only the descent reads,
+// are rebuilt once at the end).  Ties break as the rules state: cost, then the customer's place
+// in the list, then route slot, then position.  Two cluster barriers a round order the CTAs'
+// writes (global and shared) before the reads that follow them.
 #include <limits.h>
 #include <string.h>
+
+#include <cooperative_groups.h>
 
 #include <algorithm>
 #include <vector>
 
 #include "route_build.cuh"
 
+namespace cg = cooperative_groups;
+
 #ifndef MD_REPAIR_THREADS
-#define MD_REPAIR_THREADS 512  // threads of a repair CTA (one CTA per solution)
+#define MD_REPAIR_THREADS 512  // threads of a repair CTA
 #endif
+#define MD_REPAIR_PER_CTA 128  // default listed customers per CTA below which a cluster stops growing
 
 namespace {
 
@@ -83,6 +91,44 @@ __device__ __forceinline__ PickKey pick_shfl(const PickKey &k, int o) {
     return r;
 }
 
+__device__ __forceinline__ PickKey pick_key(const InsBest &b, int i) {
+    PickKey k;
+    k.valid = b.r1 >= 0;
+    k.inf = b.c2 == INT_MAX;
+    k.reg = k.inf ? 0 : (long long)b.c2 - b.c1;
+    k.c1 = b.c1;
+    k.i = i;
+    return k;
+}
+
+// A customer's best insertion and best cost in another route over route slots 0..M-1 of its row
+// (entries {cost, position}, position -1: none), by one warp: the two smallest (cost, slot) keys,
+// as ins_push folds them slot by slot.  Every lane returns the result.
+__device__ InsBest warp_best(const int2 *row, int M, int lane) {
+    InsBest b = ins_none();
+    for (int r = lane; r < M; r += 32) {
+        const int2 e = row[r];
+        if (e.y >= 0) ins_push(b, e.x, r, e.y);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const int c1 = __shfl_xor_sync(0xffffffffu, b.c1, o), r1 = __shfl_xor_sync(0xffffffffu, b.r1, o);
+        const int k1 = __shfl_xor_sync(0xffffffffu, b.k1, o);
+        const int c2 = __shfl_xor_sync(0xffffffffu, b.c2, o), r2 = __shfl_xor_sync(0xffffffffu, b.r2, o);
+        // the other lane's two keys join this lane's two (all four on different slots)
+        if (r1 >= 0) {
+            if (b.r1 < 0 || c1 < b.c1 || (c1 == b.c1 && r1 < b.r1)) {
+                // the other best leads; the second is the smaller of this best and the other second
+                if (b.r1 >= 0 && (r2 < 0 || b.c1 < c2 || (b.c1 == c2 && b.r1 < r2))) { b.c2 = b.c1; b.r2 = b.r1; }
+                else { b.c2 = c2; b.r2 = r2; }
+                b.c1 = c1; b.r1 = r1; b.k1 = k1;
+            } else if (b.r2 < 0 || c1 < b.c2 || (c1 == b.c2 && r1 < b.r2)) {
+                b.c2 = c1; b.r2 = r1;
+            }
+        }
+    }
+    return b;
+}
+
 // Cheapest insertion of u into route slot r of solution s over the positions k0, k0 + step, ...
 // (feasible ones only when feas): {cost, position}, position -1 when there is none.  Ties keep
 // the earlier position.
@@ -124,23 +170,30 @@ __device__ int2 route_best(const DevInst &I, const DevSols &D, int s, int r, int
     return make_int2(rc, rk);
 }
 
-// One CTA per solution.  U: the solution's unrouted list (device copy; an inserted customer's
-// entry becomes -1, so the list keeps its order); RB: per (list entry, route slot) the route's
-// cheapest insertion, rows of rcap slots from rb_off[s]; RS: per list entry its best insertion;
-// order: the customers in insertion order.  Routes occupy slots 0..M-1 (loaded routes first,
-// new ones appended), so an insertion changes one column of RB: round 0 fills every column, each
-// later round refreshes the column of the route that changed.
+// One cluster of CTAs per solution (solution blockIdx.x / cluster size).  U: the solution's
+// unrouted list (device copy; an inserted customer's entry becomes -1, so the list keeps its
+// order); RB: per (list entry, route slot) the route's cheapest insertion, rows of rcap slots
+// from rb_off[s]; RS: per list entry its best insertion; order: the customers in insertion
+// order.  Routes occupy slots 0..M-1 (loaded routes first, new ones appended), so an insertion
+// changes one column of RB: round 0 fills every column, each later round refreshes the column
+// of the route that changed.  CTA c of the cluster owns the list entries [i0, i1).
 template <bool TW>
 __global__ void __launch_bounds__(MD_REPAIR_THREADS, 1) k_repair(DevInst I, DevSols D, int32_t *ulist, const int64_t *uoff,
                                                 int2 *RB, const int64_t *rb_off, InsBest *res, int32_t *order,
                                                 const int32_t *rules) {
     extern __shared__ int sm_dyn[];
-    int *s_dcount = sm_dyn;              // [nd] routes departing from each depot
+    int *s_dcount = sm_dyn;              // [nd] routes departing from each depot (first CTA's kept current)
     int *s_stage = sm_dyn + I.nd;        // [K] staging of a route's tail
     int *s_arc = s_stage + D.K;          // [K + 1] arc costs of the route that changed
+    int *s_q = s_arc + D.K + 1;          // [owned entries] the entries whose routes are rescanned
     __shared__ PickKey s_red[32];
-    __shared__ int s_stop, s_M, s_dirty;
-    const int s = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    __shared__ int s_nq;
+    __shared__ PickKey s_cand;           // this CTA's candidate of the round
+    __shared__ int4 s_round;             // {route that changed, routes, stop, -}: written by the first CTA
+    __shared__ int s_M;
+    cg::cluster_group cl = cg::this_cluster();
+    const int ncl = (int)cl.num_blocks(), crank = (int)cl.block_rank();
+    const int s = blockIdx.x / ncl, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
     const int rule = rules[s];
     const bool feas = rule == MD_INSERT_FBI || rule == MD_INSERT_FRI;
     const bool regret = rule == MD_INSERT_FRI || rule == MD_INSERT_IRI;
@@ -149,29 +202,31 @@ __global__ void __launch_bounds__(MD_REPAIR_THREADS, 1) k_repair(DevInst I, DevS
     int32_t *U = ulist + u0;
     InsBest *RS = res + u0;
     const int nU = (int)(uoff[s + 1] - u0);
-    if (nU == 0) return;
+    if (nU == 0) return;  // the whole cluster
+    const int i0 = (int)((long long)nU * crank / ncl), i1 = (int)((long long)nU * (crank + 1) / ncl);
     const int rcap = (int)((rb_off[s + 1] - rb_off[s]) / nU);
     int2 *rb = RB + rb_off[s];
     for (int d = tid; d < I.nd; d += blockDim.x) s_dcount[d] = 0;
-    if (tid == 0) { s_stop = 0; s_M = 0; s_dirty = -1; }
+    if (tid == 0) { s_M = 0; s_round = make_int4(-1, 0, 0, 0); }
     __syncthreads();
     for (int r = tid; r < D.R; r += blockDim.x) {
         const int4 h = D.rhdr[(size_t)s * D.R + r];
         if (h.x > 0) { atomicAdd(&s_dcount[h.y], 1); atomicAdd(&s_M, 1); }
     }
     __syncthreads();
+    int M = s_M, dirty = -1;
     for (int done = 0; done < nU; done++) {
-        const int M = s_M;
         if (done == 0) {
-            // round 0: every (listed customer, route), one thread each
-            for (int t = tid; t < nU * M; t += blockDim.x) {
-                const int i = t / M, r = t % M;
+            // round 0: every (owned customer, route), one thread each
+            const int n = i1 - i0;
+            for (int t = tid; t < n * M; t += blockDim.x) {
+                const int i = i0 + t / M, r = t % M;
                 rb[(size_t)i * rcap + r] = route_best<TW>(I, D, s, r, U[i], feas);
             }
-        } else {
-            // the route that changed, for every listed customer: g lanes per customer split its
+        } else if (i1 > i0) {
+            // the route that changed, for every owned customer: g lanes per customer split its
             // positions (g = 1..8, as many as the customers left allow)
-            const int r = s_dirty, left = nU - done;
+            const int r = dirty, left = min(i1 - i0, nU - done);
             {
                 const int4 h = D.rhdr[(size_t)s * D.R + r];
                 const int32_t *row = D.rnodes + ((size_t)s * D.R + r) * D.K;
@@ -185,9 +240,9 @@ __global__ void __launch_bounds__(MD_REPAIR_THREADS, 1) k_repair(DevInst I, DevS
             int g = 1;
             while (g < 8 && 2 * g * left <= (int)blockDim.x) g *= 2;
             const int groups = blockDim.x / g, sub = tid & (g - 1), grp = tid / g;
-            for (int base = 0; base < nU; base += groups) {
+            for (int base = i0; base < i1; base += groups) {
                 const int i = base + grp;
-                const int u = i < nU ? U[i] : -1;
+                const int u = i < i1 ? U[i] : -1;
                 int2 e = make_int2(INT_MAX, -1);
                 if (u >= 0) e = route_best<TW>(I, D, s, r, u, feas, sub, g, s_arc);
                 for (int o = 1; o < g; o <<= 1) {  // min by (cost, position) within the group
@@ -198,35 +253,35 @@ __global__ void __launch_bounds__(MD_REPAIR_THREADS, 1) k_repair(DevInst I, DevS
             }
         }
         __syncthreads();
-        // per listed customer its best insertion and best cost in another route; the rule's pick
+        // per owned customer its best insertion and best cost in another route; the rule's pick.
+        // A customer whose best or second best route changed (every customer in round 0) has its
+        // routes rescanned by a whole warp; the others fold in the changed route.
         PickKey best;
         best.valid = 0; best.inf = 0; best.reg = 0; best.c1 = 0; best.i = INT_MAX;
-        for (int i = tid; i < nU; i += blockDim.x) {
+        if (tid == 0) s_nq = 0;
+        __syncthreads();
+        for (int i = i0 + tid; i < i1; i += blockDim.x) {
             if (U[i] < 0) continue;
-            const int2 *row = rb + (size_t)i * rcap;
-            InsBest b;
-            const int rd = done == 0 ? -1 : s_dirty;
-            if (rd < 0 || RS[i].r1 == rd || RS[i].r2 == rd) {
-                // round 0, or the changed route held this customer's best or second best: rescan
-                b = ins_none();
-                for (int r = 0; r < M; r++) {
-                    const int2 e = row[r];
-                    if (e.y >= 0) ins_push(b, e.x, r, e.y);
-                }
-            } else {
-                // any other route kept its cost: fold in the changed one
-                b = RS[i];
-                const int2 e = row[rd];
-                if (e.y >= 0) ins_push(b, e.x, rd, e.y);
+            InsBest b = RS[i];
+            if (dirty < 0 || b.r1 == dirty || b.r2 == dirty) {
+                s_q[atomicAdd(&s_nq, 1)] = i;
+                continue;
             }
+            const int2 e = rb[(size_t)i * rcap + dirty];
+            if (e.y >= 0) ins_push(b, e.x, dirty, e.y);
             RS[i] = b;
-            PickKey k;
-            k.valid = b.r1 >= 0;
-            k.inf = b.c2 == INT_MAX;
-            k.reg = k.inf ? 0 : (long long)b.c2 - b.c1;
-            k.c1 = b.c1;
-            k.i = i;
+            const PickKey k = pick_key(b, i);
             if (pick_less(k, best, regret)) best = k;
+        }
+        __syncthreads();
+        for (int q = warp; q < s_nq; q += nw) {
+            const int i = s_q[q];
+            const InsBest b = warp_best(rb + (size_t)i * rcap, M, lane);
+            if (lane == 0) {
+                RS[i] = b;
+                const PickKey k = pick_key(b, i);
+                if (pick_less(k, best, regret)) best = k;
+            }
         }
         for (int o = 16; o > 0; o >>= 1) {
             const PickKey x = pick_shfl(best, o);
@@ -240,6 +295,15 @@ __global__ void __launch_bounds__(MD_REPAIR_THREADS, 1) k_repair(DevInst I, DevS
                 const PickKey x = pick_shfl(k, o);
                 if (pick_less(x, k, regret)) k = x;
             }
+            if (lane == 0) s_cand = k;
+        }
+        cl.sync();  // every CTA's candidate and its writes of RB and RS are visible
+        if (crank == 0 && warp == 0) {
+            PickKey k = *cl.map_shared_rank(&s_cand, (unsigned)min(lane, ncl - 1));
+            for (int o = 16; o > 0; o >>= 1) {
+                const PickKey x = pick_shfl(k, o);
+                if (pick_less(x, k, regret)) k = x;
+            }
             int i = k.i;
             if (!k.valid) {  // none: the first listed customer opens a route
                 i = INT_MAX;
@@ -249,7 +313,7 @@ __global__ void __launch_bounds__(MD_REPAIR_THREADS, 1) k_repair(DevInst I, DevS
                 }
             }
             const int u = U[i];
-            int touched = -1;
+            int touched = -1, stop = 0;
             if (k.valid) {
                 const InsBest b = RS[i];
                 const int r = b.r1, pos = b.k1;
@@ -257,7 +321,8 @@ __global__ void __launch_bounds__(MD_REPAIR_THREADS, 1) k_repair(DevInst I, DevS
                 const int4 h = D.rhdr[sr];
                 const int L = h.x;
                 if (L + 1 > D.K) {
-                    if (lane == 0) { atomicCAS(D.err, 0, (int)MD_ERR_CAPACITY); s_stop = 1; }
+                    if (lane == 0) atomicCAS(D.err, 0, (int)MD_ERR_CAPACITY);
+                    stop = 1;
                 } else {
                     int32_t *row = D.rnodes + sr * D.K;
                     for (int t = pos + lane; t < L; t += 32) s_stage[t] = row[t];
@@ -284,14 +349,14 @@ __global__ void __launch_bounds__(MD_REPAIR_THREADS, 1) k_repair(DevInst I, DevS
                 const int d = (int)(bestd & 0xfffff);
                 const int slot = M;
                 if (slot >= D.R || slot >= rcap) {
-                    if (lane == 0) { atomicCAS(D.err, 0, (int)MD_ERR_CAPACITY); s_stop = 1; }
+                    if (lane == 0) atomicCAS(D.err, 0, (int)MD_ERR_CAPACITY);
+                    stop = 1;
                 } else {
                     const size_t sr = (size_t)s * D.R + slot;
                     if (lane == 0) {
                         D.rnodes[sr * D.K] = u;
                         D.rhdr[sr] = make_int4(1, d, d, u);
                         s_dcount[d]++;
-                        s_M = M + 1;
                     }
                     __syncwarp();
                     rebuild_route<TW, false>(I, D, s, slot);
@@ -300,16 +365,71 @@ __global__ void __launch_bounds__(MD_REPAIR_THREADS, 1) k_repair(DevInst I, DevS
             }
             if (lane == 0) {
                 U[i] = -1;
-                s_dirty = touched;
                 if (order) order[u0 + done] = u;
             }
+            // the round's outcome, into every CTA's shared memory
+            const int4 out = make_int4(touched, touched == M ? M + 1 : M, stop, 0);
+            if (lane < ncl) *cl.map_shared_rank(&s_round, (unsigned)lane) = out;
         }
-        __syncthreads();
-        if (s_stop) break;
+        cl.sync();  // the insertion, its rebuilt route and the round's outcome are visible
+        const int4 o = s_round;
+        if (o.z) break;
+        dirty = o.x;
+        M = o.y;
     }
 }
 
 }  // namespace
+
+namespace {
+
+// CTAs per solution, c: at most one per per_cta listed customers of the longest list and at
+// most 16.  Each size costs ceil(n / clusters of it resident at once) / c (the waves of clusters
+// over the CTAs that share a solution's work); the cheapest wins, the smaller on a tie.
+int repair_cluster(const void *fn, size_t smem, int n, const int64_t *uoff, int per_cta) {
+    long long most = 0;
+    for (int s = 0; s < n; s++) most = std::max<long long>(most, uoff[s + 1] - uoff[s]);
+    const int top = (int)std::min<long long>(16, std::max<long long>(1, (most + per_cta - 1) / per_cta));
+    const bool wide = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess;
+    cudaGetLastError();  // a refused attribute leaves no error behind
+    int dev = 0, sms = 1, per_sm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, MD_REPAIR_THREADS, smem);
+    const int res1 = std::max(1, per_sm * sms);
+    int best = 1;
+    double cost = (double)((n + res1 - 1) / res1);
+    for (int c = 2; c <= top && (c <= 8 || wide); c++) {
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = (unsigned)c;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3((unsigned)c);
+        cfg.blockDim = dim3(MD_REPAIR_THREADS);
+        cfg.dynamicSmemBytes = smem;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int active = 0;
+        if (cudaOccupancyMaxActiveClusters(&active, fn, &cfg) != cudaSuccess || active < 1) {
+            cudaGetLastError();
+            continue;
+        }
+        const double k = (double)((n + active - 1) / active) / c;
+        if (k < cost) { cost = k; best = c; }
+    }
+    cudaGetLastError();
+    return best;
+}
+
+}  // namespace
+
+extern "C" md_status md_solutions_set_repair_split(md_solutions *S, int32_t per_cta) {
+    if (!S || per_cta < 0) { md_set_error("md_solutions_set_repair_split: need a solution set and per_cta >= 0"); return MD_ERR_ARG; }
+    S->repair_per_cta = per_cta;
+    return MD_OK;
+}
 
 extern "C" md_status md_repair_insert(md_solutions *S, const int32_t *rules, const int32_t *nodes, const int64_t *off,
                                       const int32_t *per_sol, const int32_t *unrouted, const int64_t *unrouted_off,
@@ -380,14 +500,31 @@ extern "C" md_status md_repair_insert(md_solutions *S, const int32_t *rules, con
         InsBest *dres = (InsBest *)(dbuf + o_res);
         int32_t *dord = (int32_t *)(dbuf + o_ord);
         int2 *drb = (int2 *)(dbuf + o_rb);
-        const size_t smem = sizeof(int) * ((size_t)I.nd + 2 * (size_t)S->K + 1);
-        if (I.variant & MD_VARIANT_TW) {
-            MD_CUDA(md_allow_smem((const void *)k_repair<true>, smem));
-            k_repair<true><<<n, MD_REPAIR_THREADS, smem, st>>>(I, S->d, du, doff, drb, drboff, dres, dord, drules);
-        } else {
-            MD_CUDA(md_allow_smem((const void *)k_repair<false>, smem));
-            k_repair<false><<<n, MD_REPAIR_THREADS, smem, st>>>(I, S->d, du, doff, drb, drboff, dres, dord, drules);
-        }
+        // shared memory: depot counts, a route's tail and arcs, the queue of a CTA's entries
+        long long most = 0;
+        for (int s = 0; s < n; s++) most = std::max<long long>(most, unrouted_off[s + 1] - unrouted_off[s]);
+        const size_t base = sizeof(int) * ((size_t)I.nd + 2 * (size_t)S->K + 1);
+        const void *fn = (I.variant & MD_VARIANT_TW) ? (const void *)k_repair<true> : (const void *)k_repair<false>;
+        MD_CUDA(md_allow_smem(fn, base + sizeof(int) * (size_t)most));
+        const int ncl = repair_cluster(fn, base + sizeof(int) * (size_t)((most + 15) / 16), n, unrouted_off,
+                                       S->repair_per_cta > 0 ? S->repair_per_cta : MD_REPAIR_PER_CTA);
+        const size_t smem = base + sizeof(int) * (size_t)((most + ncl - 1) / ncl);
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = (unsigned)ncl;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3((unsigned)(n * ncl));
+        cfg.blockDim = dim3(MD_REPAIR_THREADS);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = st;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        if (I.variant & MD_VARIANT_TW)
+            MD_CUDA(cudaLaunchKernelEx(&cfg, k_repair<true>, I, S->d, du, doff, drb, drboff, dres, dord, (const int32_t *)drules));
+        else
+            MD_CUDA(cudaLaunchKernelEx(&cfg, k_repair<false>, I, S->d, du, doff, drb, drboff, dres, dord, (const int32_t *)drules));
         MD_CUDA(cudaGetLastError());
         r = md_launch_rebuild_all(S, st);  // the subsequence tables of the long routes
         if (r != MD_OK) return r;

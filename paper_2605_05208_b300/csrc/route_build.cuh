@@ -109,8 +109,9 @@ __device__ __forceinline__ void write_links(const DevInst &I, const DevSols &D, 
 }
 
 // Rebuilds every summary of route slot r of solution s; called by all 32 lanes of one warp.
-// SUBTABLES = false leaves the subsequence tables of routes longer than 32 customers stale (the
-// repair insertion, which reads only prefixes and suffixes, rebuilds them once at its end).
+// SUBTABLES = false leaves the subsequence tables of routes longer than 32 customers and the link
+// records stale (the repair insertion, which reads only prefixes and suffixes, rebuilds every
+// route once at its end).
 template <bool TW, bool SUBTABLES = true>
 __device__ void rebuild_route(const DevInst &I, const DevSols &D, int s, int r) {
     const int lane = threadIdx.x & 31;
@@ -182,7 +183,7 @@ __device__ void rebuild_route(const DevInst &I, const DevSols &D, int s, int r) 
         whole.load = __shfl_sync(0xffffffffu, whole.load, 0);
         whole.dur = __shfl_sync(0xffffffffu, whole.dur, 0);
         whole.tw = __shfl_sync(0xffffffffu, whole.tw, 0);
-        write_links<TW>(I, D, s, r, nodes, L, ds, de, open, whole);
+        if (SUBTABLES) write_links<TW>(I, D, s, r, nodes, L, ds, de, open, whole);
         return;
     }
 
@@ -268,5 +269,5 @@ __device__ void rebuild_route(const DevInst &I, const DevSols &D, int s, int r) 
         st_seg8(&D.rcore[md_ix(I.err, sr, (size_t)D.S * D.R)], core.s, core.first, core.last);
         D.rhdr[md_ix(I.err, sr, (size_t)D.S * D.R)] = make_int4(L, ds, de, nodes[md_ix(I.err, L - 1, (size_t)D.K)]);
     }
-    write_links<TW>(I, D, s, r, nodes, L, ds, de, open, whole.s);
+    if (SUBTABLES) write_links<TW>(I, D, s, r, nodes, L, ds, de, open, whole.s);
 }

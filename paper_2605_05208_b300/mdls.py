@@ -38,7 +38,8 @@ EXPORTED = (
     "md_batch_descend", "md_instance_build_neighbors",
     "md_instance_set_neighbors", "md_pruner_create", "md_pruner_destroy", "md_pruner_params",
     "md_pruner_features", "md_pruner_score", "md_pruner_prune", "md_pruner_train",
-    "md_pruner_set_wait", "md_repair_insert", "md_eval_range", "md_moves_export", "md_moves_import",
+    "md_pruner_set_wait", "md_repair_insert", "md_solutions_set_repair_split", "md_eval_range",
+    "md_moves_export", "md_moves_import",
 )
 INSERT_FBI, INSERT_IBI, INSERT_FRI, INSERT_IRI = 0, 1, 2, 3  # repair insertion rules (Section 3.3)
 
@@ -116,6 +117,7 @@ def lib() -> C.CDLL:
             "md_solutions_destroy": [P],
             "md_solutions_load": [P, P, P, P, P],
             "md_repair_insert": [P, P, P, P, P, P, P, P, P],
+            "md_solutions_set_repair_split": [P, C.c_int32],
             "md_solutions_copy": [P, P, P],
             "md_solutions_read": [P, P, P, P, C.c_int64, C.c_int64, P],
             "md_solution_cost": [P, P, P, P],
@@ -309,6 +311,10 @@ class Solutions:
                                       _ptr(offs) if len(nodes) else None, _ptr(per), _ptr(un), _ptr(uoff),
                                       _ptr(order), _stream(stream)))
         return [[int(x) for x in order[uoff[s]:uoff[s + 1]]] for s in range(self.n_sol)]
+
+    def set_repair_split(self, per_cta: int):
+        """Listed customers per CTA of a repair's cluster (0: the default); speed only."""
+        _check(lib().md_solutions_set_repair_split(self.h, int(per_cta)))
 
     def copy_from(self, other: "Solutions", stream=None):
         _check(lib().md_solutions_copy(self.h, other.h, _stream(stream)))

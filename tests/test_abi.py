@@ -90,3 +90,4 @@ def test_descend_rejects_bad_config_without_device(built):
     assert L.md_descend(None, None, C.byref(st), None) == mdls.MD_ERR_ARG
     assert L.md_moves_create(None, 0, C.byref(C.c_void_p())) == mdls.MD_ERR_ARG
     assert L.md_repair_insert(None, 0, None, None, None, None, None, None, None) == mdls.MD_ERR_ARG
+    assert L.md_solutions_set_repair_split(None, 0) == mdls.MD_ERR_ARG

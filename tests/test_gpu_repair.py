@@ -126,3 +126,31 @@ def test_repair_rules_differ_per_solution_in_one_launch(md, oracle_lib):
     for s in range(8):
         want, worder = o.repair(parts[s][0], parts[s][1], rules[s])
         assert got[s] == want and order[s] == worder, s
+
+
+def test_repair_split_over_a_cluster_of_16_ctas_matches_oracle(md, oracle_lib):
+    # 550 of 600 customers unrouted: with 32 customers per CTA the list is split over 16 CTAs of
+    # one cluster per solution, which pick each round's customer together; rules differ per
+    # solution; then the default split (5 CTAs) and one CTA per solution give the same
+    spec = W.gen_mdvrptw(261, n_depots=5, n_customers=600, lo=-200, hi=200, horizon=2000, Q=200, N_V=12, D=2000)
+    full = W.initial_solutions(spec, 262, 3)
+    parts = [partial_solution(sol, 263 + i, p_route=0.9, p_cust=0.5) for i, sol in enumerate(full)]
+    assert min(len(p[1]) for p in parts) > 15 * 32
+    rules = [0, 2, 1]
+    inst = md.Instance(spec)
+    S = md.Solutions(inst, 3, spec.n_customers + 1, spec.n_customers)
+    S.set_repair_split(32)
+    order = S.repair([p[0] for p in parts], [p[1] for p in parts], rules)
+    got = S.read()
+    comps, _ = S.cost()
+    o = oracle_lib.Instance(spec)
+    for s in range(3):
+        want, worder = o.repair(parts[s][0], parts[s][1], rules[s])
+        assert order[s] == worder, s
+        assert got[s] == want, s
+        T, _ = o.solution_terms(want)
+        assert comps[s][0] == T["D"] and comps[s][1] == T["TW"] and comps[s][6] == T["V4"], s
+    for split in (0, 1 << 20):
+        S.set_repair_split(split)
+        assert S.repair([p[0] for p in parts], [p[1] for p in parts], rules) == order
+        assert S.read() == got
