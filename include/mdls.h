@@ -356,6 +356,43 @@ md_status md_repair_insert(md_solutions *sols, const int32_t *rules, const int32
  * per CTA.  Results do not depend on it.  MD_ERR_ARG on a null set or per_cta < 0. */
 md_status md_solutions_set_repair_split(md_solutions *sols, int32_t per_cta);
 
+/* The route exchange of DCREX (Alg. 3, Section 3.3) for one offspring, on the host (no device
+ * work): from the main member's routes and, in the given order, the routes of other members of
+ * a population, builds the offspring's partial solution and lists its unrouted customers.
+ * Route pairs (R_i, R_j) -- R_i a route of the main member still in the offspring, R_j a route
+ * of the current other member -- score N^R + N^M + 10 N^C - E^I, where E^I counts R_j's distinct
+ * edges the offspring does not have, N^R R_i's customers R_j does not visit, N^M R_j's customers
+ * the offspring visits outside R_i, and N^C R_j's customers visited by routes introduced earlier
+ * in this call.  One of the five lowest scores (ties by i, then j) is drawn uniformly, R_j
+ * replaces R_i, and E^I + N^R + N^M is summed; the exchange goes on while the sum is below
+ * smin = degree/20 (n_customers + m) or at least smax = (degree+1)/20 (n_customers + m) (m: the
+ * main member's routes) and stops in between, or when no route of the main member is left or a
+ * member has no route.  Redundant customers then stay in the earliest-introduced route that
+ * visits them; routes left empty are dropped.  Edges are undirected pairs of consecutive nodes,
+ * depots included; open routes (open_routes != 0) have no return edge, and a closed route
+ * [d, c, d] has one edge.
+ *   nodes / offsets / routes_per_member: host, every member's routes in the md_solutions_load
+ *     layout (routes of member k follow those of member k - 1; each route starts and ends at a
+ *     depot and visits at least one customer; a member visits a customer at most once);
+ *   main_member: the main parent's index; others: host int32 [n_others], member indices in the
+ *     order they are visited;
+ *   degree: the diversity degree, 0..19;
+ *   stream: host uint64 [2], {state, counter} of a counter-based SplitMix64 stream: a draw is
+ *     the high 32 bits x of mix(state + counter' * 0x9E3779B97F4A7C15) with counter' = counter
+ *     + 1, mapped to (x * span) >> 32; the call advances counter by its draws (one per
+ *     exchanged route);
+ *   out_nodes: host int32, room for n_customers + 2 m nodes; out_offsets: host int64 [m + 1];
+ *     out_routes receives the offspring's routes (in the main member's route order, an
+ *     exchanged route in the place of the one it replaced);
+ *   unrouted: host int32 [n_customers], the customers in no route, increasing; n_unrouted their
+ *     count.
+ * MD_ERR_ARG on a null pointer, an index or degree out of range, or malformed routes. */
+md_status md_dcrex(const int32_t *nodes, const int64_t *offsets, const int32_t *routes_per_member,
+                   int32_t n_members, int32_t main_member, const int32_t *others, int32_t n_others,
+                   int32_t degree, int32_t n_depots, int32_t n_customers, int32_t open_routes,
+                   uint64_t *stream, int32_t *out_nodes, int64_t *out_offsets, int32_t *out_routes,
+                   int32_t *unrouted, int32_t *n_unrouted);
+
 /* Batches of instances of uneven size.  A batch groups solution sets of different instances
  * (each from md_solutions_create/load on the same device, each still owned by the caller) so
  * that every solution of every instance advances with ONE evaluation launch and ONE select/apply

@@ -1,4 +1,5 @@
-"""Builds libmdls.so in-tree from csrc/*.cu for sm_103a (B300) with nvcc.
+"""Builds libmdls.so in-tree from csrc/*.cu (and the host-only csrc/*.cpp) for sm_103a (B300)
+with nvcc.
 
 Usage: python -m paper_2605_05208_b300.build [--force] [--bounds]
 --bounds builds libmdls_bounds.so instead: every device-side gather checks its index and a call
@@ -25,7 +26,7 @@ def nvcc() -> str:
 
 
 def sources() -> list[str]:
-    return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
+    return sorted(glob.glob(os.path.join(CSRC, "*.cu"))) + sorted(glob.glob(os.path.join(CSRC, "*.cpp")))
 
 
 def deps() -> list[str]:
@@ -33,7 +34,7 @@ def deps() -> list[str]:
 
 
 def build(force: bool = False, verbose: bool = False, bounds: bool = False) -> str:
-    """Compiles every .cu file and links libmdls.so (rebuilds only when a source is newer);
+    """Compiles every source and links libmdls.so (rebuilds only when a source is newer);
     bounds: the bounds-checked libmdls_bounds.so."""
     out = LIB_BOUNDS if bounds else LIB
     if not force and os.path.exists(out):

@@ -39,7 +39,7 @@ EXPORTED = (
     "md_instance_set_neighbors", "md_pruner_create", "md_pruner_destroy", "md_pruner_params",
     "md_pruner_features", "md_pruner_score", "md_pruner_prune", "md_pruner_train",
     "md_pruner_set_wait", "md_repair_insert", "md_solutions_set_repair_split", "md_eval_range",
-    "md_moves_export", "md_moves_import",
+    "md_moves_export", "md_moves_import", "md_dcrex",
 )
 INSERT_FBI, INSERT_IBI, INSERT_FRI, INSERT_IRI = 0, 1, 2, 3  # repair insertion rules (Section 3.3)
 
@@ -118,6 +118,8 @@ def lib() -> C.CDLL:
             "md_solutions_load": [P, P, P, P, P],
             "md_repair_insert": [P, P, P, P, P, P, P, P, P],
             "md_solutions_set_repair_split": [P, C.c_int32],
+            "md_dcrex": [P, P, P, C.c_int32, C.c_int32, P, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
+                         C.c_int32, P, P, P, P, P, P],
             "md_solutions_copy": [P, P, P],
             "md_solutions_read": [P, P, P, P, C.c_int64, C.c_int64, P],
             "md_solution_cost": [P, P, P, P],
@@ -249,6 +251,30 @@ def flatten(sols):
             offs.append(len(nodes))
     return (np.asarray(nodes, dtype=np.int32), np.asarray(offs, dtype=np.int64),
             np.asarray(per, dtype=np.int32))
+
+
+def dcrex(nodes, offsets, per_member, main: int, others, degree: int, stream, n_depots: int,
+          n_customers: int, open_routes: bool):
+    """The route exchange of DCREX (Alg. 3) on the host (md_dcrex).  nodes / offsets /
+    per_member: every population member's routes (the flatten layout); main: the main parent;
+    others: the other parents in visiting order; stream: [state, counter] of the draws
+    (workloads.Stream's).  Returns (partial routes, unrouted customers, the advanced counter)."""
+    nodes = np.ascontiguousarray(nodes, dtype=np.int32)
+    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    per_member = np.ascontiguousarray(per_member, dtype=np.int32)
+    oth = np.ascontiguousarray(np.asarray(list(others), dtype=np.int32).reshape(-1))
+    m = int(per_member[main]) if 0 <= main < len(per_member) else 0  # the library rejects a bad index
+    st = np.asarray([int(stream[0]) & (2**64 - 1), int(stream[1])], dtype=np.uint64)
+    out = np.zeros(n_customers + 2 * m, dtype=np.int32)
+    ooff = np.zeros(m + 1, dtype=np.int64)
+    un = np.zeros(n_customers, dtype=np.int32)
+    nr, nu = C.c_int32(0), C.c_int32(0)
+    _check(lib().md_dcrex(_ptr(nodes), _ptr(offsets), _ptr(per_member), len(per_member), int(main),
+                          _ptr(oth) if len(oth) else None, len(oth), int(degree), int(n_depots), int(n_customers),
+                          1 if open_routes else 0, _ptr(st), _ptr(out), _ptr(ooff), C.byref(nr), _ptr(un),
+                          C.byref(nu)))
+    routes = [out[ooff[r]:ooff[r + 1]].tolist() for r in range(nr.value)]
+    return routes, un[:nu.value].tolist(), int(st[1])
 
 
 @dataclass

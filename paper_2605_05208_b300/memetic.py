@@ -9,7 +9,8 @@ fitness and diversity.  One generation is sequential within a run, so the B300 f
 runs): each generation's repairs are one `md_repair_insert` launch and their descents one
 `md_descend` call for all runs.  The host part -- route-pair scores, route exchange, the
 discounted UCB1 choices (Eq. 6) and the fitness-and-distance ranking (Eq. 7-9) -- is small
-per run and stays on the CPU.
+per run and stays on the CPU: the route exchange runs natively (md_dcrex in the library) by
+default; `dcrex` below is its numpy restatement, which the tests hold it to.
 
 Readings where the paper is silent:
 - DCREX scores route pairs (R_i, R_j) with R_i a route of the main parent still in the
@@ -133,9 +134,10 @@ def chi_scores(f: np.ndarray, d: np.ndarray, xi: float) -> np.ndarray:
     index."""
     n = len(f)
     dp = np.zeros(n)
-    for a in range(n):
-        others = np.sort(np.delete(d[a], a))
-        dp[a] = others[:5].mean() if len(others) else 0.0
+    if n > 1:
+        # each row without its diagonal, sorted: the five nearest other members first
+        off = np.sort(d[~np.eye(n, dtype=bool)].reshape(n, n - 1), axis=1)
+        dp = off[:, :5].mean(axis=1)
     rank_f = np.empty(n)
     rank_f[np.lexsort((np.arange(n), f))] = np.arange(1, n + 1)
     rank_d = np.empty(n)
@@ -281,6 +283,35 @@ def dcrex(main, others, degree: int, st: W.Stream, n_depots: int, n_customers: i
     return out, [c for c in range(n_depots, n_depots + n_customers) if c not in routed]
 
 
+def member_keys(sol, nn: int, open_routes: bool):
+    """A member's distinct undirected edge keys (the third of parent_arrays)."""
+    return _edge_keys(_flat_nodes(sol), open_routes, nn)[1]
+
+
+def member_flat(sol):
+    """A member's routes as (nodes int32, route lengths int64), for md_dcrex."""
+    lens = np.fromiter((len(r) for r in sol), np.int64, len(sol))
+    nodes = np.fromiter((c for r in sol for c in r), np.int32, int(lens.sum()))
+    return nodes, lens
+
+
+def _dcrex_native(flat, st, degree, nd, nc, open_routes):
+    """_dcrex_task through md_dcrex: the same draws (the main parent, the other parents' order,
+    then one per exchanged route from the same stream) and the same result."""
+    from . import mdls
+    n = len(flat)
+    m = int(st.randint(0, n - 1, 1)[0])
+    order = [i for i in np.argsort(st.u64(n)).tolist() if i != m]
+    nodes = np.concatenate([f[0] for f in flat])
+    lens = np.concatenate([f[1] for f in flat])
+    offs = np.zeros(len(lens) + 1, np.int64)
+    np.cumsum(lens, out=offs[1:])
+    per = np.fromiter((len(f[1]) for f in flat), np.int32, n)
+    part, un, st.counter = mdls.dcrex(nodes, offs, per, m, order, degree, (st.state, st.counter), nd, nc,
+                                      open_routes)
+    return part, un, m, st
+
+
 def _dcrex_task(args):
     """One run's parent choice and crossover (a process-pool task): returns the partial
     solution, its unrouted customers, the main parent's index and the advanced stream."""
@@ -331,7 +362,8 @@ class GpuBackend:
 @dataclass
 class Run:
     pop: list = field(default_factory=list)    # routes of each member
-    pre: list = field(default_factory=list)    # parent_arrays of each member
+    pre: list = field(default_factory=list)    # parent_arrays of each member (native: only the keys)
+    flat: list = field(default_factory=list)   # member_flat of each member (native route exchange)
     f: list = field(default_factory=list)      # unit-lambda F of each member
     best: float = math.inf
     best_sol: list | None = None
@@ -345,7 +377,7 @@ class MDFIHA:
     (GpuBackend by default) and the instance's Theta and Gamma."""
 
     def __init__(self, spec, n_runs: int, mu: int = 20, xi: float = 0.7, delta: int = 500, seed: int = 1,
-                 backend=None, n_ops: int = W.N_OPS, host_workers: int = 0):
+                 backend=None, n_ops: int = W.N_OPS, host_workers: int = 0, native: bool = True):
         self.spec = spec
         self.n_runs = n_runs
         self.mu = mu
@@ -354,6 +386,7 @@ class MDFIHA:
         self.seed = seed
         self.n_ops = n_ops
         self.open = bool(spec.variant & W.VAR_OPEN)
+        self.native = native  # route exchange by md_dcrex (else the numpy dcrex)
         self.backend = backend if backend is not None else GpuBackend(spec)
         self.gen = 0
         self.runs = [Run() for _ in range(n_runs)]
@@ -365,7 +398,7 @@ class MDFIHA:
         # that no worker is forked from a process that has initialised CUDA.  With populations of
         # 20 on the 6 x 288 instance, sending them to the workers costs more than it saves.
         self.pool = None
-        if host_workers > 0:
+        if host_workers > 0 and not native:
             import multiprocessing as mp
             self.pool = mp.get_context("spawn").Pool(host_workers)
 
@@ -394,9 +427,7 @@ class MDFIHA:
         for r, run in enumerate(self.runs):
             for k in range(self.mu):
                 i = r * self.mu + k
-                run.pop.append(got[i])
-                run.pre.append(parent_arrays(got[i], self.spec.n_nodes, self.open))
-                run.f.append(self._f(comps[i]))
+                self._add(run, got[i], self._f(comps[i]))
             b = int(np.argmin(run.f))
             run.best, run.best_sol = run.f[b], run.pop[b]
 
@@ -406,10 +437,14 @@ class MDFIHA:
         self.gen += 1
         degs = [run.deg.select() for run in self.runs]
         rules = [run.rule.select() for run in self.runs]
-        # the workers rebuild the parents' arrays rather than receive them
-        tasks = [(run.pop, None if self.pool is not None else run.pre, self.streams[r], degs[r],
-                  self.spec.n_depots, self.spec.n_customers, self.open) for r, run in enumerate(self.runs)]
-        res = self.pool.map(_dcrex_task, tasks) if self.pool is not None else [_dcrex_task(t) for t in tasks]
+        if self.native:
+            res = [_dcrex_native(run.flat, self.streams[r], degs[r], self.spec.n_depots, self.spec.n_customers,
+                                 self.open) for r, run in enumerate(self.runs)]
+        else:
+            # the workers rebuild the parents' arrays rather than receive them
+            tasks = [(run.pop, None if self.pool is not None else run.pre, self.streams[r], degs[r],
+                      self.spec.n_depots, self.spec.n_customers, self.open) for r, run in enumerate(self.runs)]
+            res = self.pool.map(_dcrex_task, tasks) if self.pool is not None else [_dcrex_task(t) for t in tasks]
         partials = [x[0] for x in res]
         unrouted = [x[1] for x in res]
         mains = [x[2] for x in res]
@@ -425,9 +460,7 @@ class MDFIHA:
             reward = 100.0 * (fm - f) / fm if fm != 0 else 0.0
             run.deg.update(degs[r], reward)
             run.rule.update(rules[r], reward)
-            run.pop.append(got[r])
-            run.pre.append(parent_arrays(got[r], self.spec.n_nodes, self.open))
-            run.f.append(f)
+            self._add(run, got[r], f)
             if len(run.pop) >= math.ceil(1.5 * self.mu):
                 self._reduce(run)
             if f < run.best:
@@ -436,6 +469,15 @@ class MDFIHA:
                 run.stagnation += 1
         self.offspring += self.n_runs
         self.t_total += time.perf_counter() - t0
+
+    def _add(self, run: Run, sol, f: float):
+        run.pop.append(sol)
+        if self.native:
+            run.pre.append((None, None, member_keys(sol, self.spec.n_nodes, self.open)))
+            run.flat.append(member_flat(sol))
+        else:
+            run.pre.append(parent_arrays(sol, self.spec.n_nodes, self.open))
+        run.f.append(f)
 
     def _reduce(self, run: Run):
         """Section 3.4: remove the member of lowest chi until mu remain."""
@@ -446,4 +488,6 @@ class MDFIHA:
             del run.pop[worst]
             del run.pre[worst]
             del run.f[worst]
+            if run.flat:
+                del run.flat[worst]
             d = np.delete(np.delete(d, worst, 0), worst, 1)

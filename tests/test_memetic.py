@@ -178,12 +178,71 @@ def test_memetic_crossovers_on_a_process_pool_change_nothing(oracle_lib):
     out = []
     for workers in (0, 2):
         mm = MM.MDFIHA(spec, n_runs=3, mu=4, delta=20, seed=4, backend=OracleBackend(oracle_lib, spec),
-                       host_workers=workers)
+                       host_workers=workers, native=False)
         mm.initialize()
         for _ in range(4):
             mm.generation()
         mm.close()
         out.append([(r.pop, r.f, r.deg.R.tolist(), r.rule.N.tolist()) for r in mm.runs])
+    assert out[0] == out[1]
+
+
+def _native_dcrex(main, others, degree, st, nd, nc, open_):
+    from paper_2605_05208_b300 import build, mdls
+    build.build()
+    pop = [main, *others]
+    nodes, offs, per = mdls.flatten(pop)
+    part, un, st.counter = mdls.dcrex(nodes, offs, per, 0, range(1, len(pop)), degree, (st.state, st.counter),
+                                      nd, nc, open_)
+    return part, un
+
+
+@pytest.mark.parametrize("open_", [False, True])
+def test_native_dcrex_matches_the_numpy_restatement(open_):
+    # md_dcrex against dcrex (itself pinned to pair-by-pair counts above): the same partial
+    # solution, unrouted list and number of draws, on routes of 1..9 customers (closed [d, c, d]
+    # routes included) over many degrees and streams
+    for trial, nc in enumerate((36, 60, 90)):
+        spec = tiny_spec(300 + trial, nd=3, nc=nc, Q=60, NV=8, open_=open_, sym=open_)
+        for k in range(4):
+            main = random_solution(spec, 310 + 10 * trial + k, max_len=1 + (k * 3) % 9)
+            others = [random_solution(spec, 400 + 50 * trial + 7 * k + q, max_len=1 + (q + k) % 9) for q in range(6)]
+            for degree in range(0, 20, 3):
+                a, b = W.Stream(21, trial, k, degree), W.Stream(21, trial, k, degree)
+                want = MM.dcrex(main, others, degree, a, spec.n_depots, spec.n_customers, open_)
+                got = _native_dcrex(main, others, degree, b, spec.n_depots, spec.n_customers, open_)
+                assert got == want and a.counter == b.counter, (trial, k, degree)
+
+
+def test_native_dcrex_rejects_malformed_routes():
+    from paper_2605_05208_b300 import build, mdls
+    build.build()
+    spec = tiny_spec(331, nd=2, nc=6)
+    good = [[0, 2, 3, 0], [1, 4, 5, 6, 7, 1]]
+    for bad in ([[0, 2, 2, 0], [1, 4, 5, 6, 7, 1]],   # a customer twice
+                [[0, 0], [1, 2, 3, 4, 5, 6, 7, 1]],  # a route without a customer
+                [[0, 2, 1, 3, 0], [1, 4, 5, 6, 7, 1]],  # a depot inside a route
+                [[2, 3, 0], [1, 4, 5, 6, 7, 1]],     # a route that starts at a customer
+                [[0, 2, 3, 8, 0], [1, 4, 5, 6, 7, 1]]):  # a node out of range
+        nodes, offs, per = mdls.flatten([good, bad])
+        with pytest.raises(mdls.MdError) as e:
+            mdls.dcrex(nodes, offs, per, 0, [1], 3, (1, 0), spec.n_depots, spec.n_customers, False)
+        assert e.value.status == mdls.MD_ERR_ARG
+    nodes, offs, per = mdls.flatten([good, good])
+    for main, others, degree in ((2, [1], 3), (0, [5], 3), (0, [1], 20), (0, [1], -1)):
+        with pytest.raises(mdls.MdError):
+            mdls.dcrex(nodes, offs, per, main, others, degree, (1, 0), spec.n_depots, spec.n_customers, False)
+
+
+def test_memetic_loop_with_native_route_exchange_matches_numpy(oracle_lib):
+    spec = W.mdvrp_4x50(87)
+    out = []
+    for native in (False, True):
+        mm = MM.MDFIHA(spec, n_runs=3, mu=4, delta=20, seed=6, backend=OracleBackend(oracle_lib, spec), native=native)
+        mm.initialize()
+        for _ in range(6):
+            mm.generation()
+        out.append([(r.pop, r.f, r.deg.R.tolist(), r.rule.N.tolist(), [p[2].tolist() for p in r.pre]) for r in mm.runs])
     assert out[0] == out[1]
 
 
