@@ -481,8 +481,39 @@ def run_batch(args):
             out.append(b.descend(p.data_ptr(), max_pass, use_graph=True, stream=sptr, n_ops=W.N_OPS))
         return out
 
+    tuned_solo = B.solo()
+    one_grid = [grid]
+
+    def one_launch():
+        # every instance in the one batched evaluation launch per step
+        B.set_solo(np.zeros_like(tuned_solo))
+        B.set_tuning(grid=one_grid[0])
+        try:
+            return B.descend(perm_dev.data_ptr(), max_pass, use_graph=True, stream=sptr, n_ops=W.N_OPS)
+        finally:
+            B.set_solo(tuned_solo)
+            B.set_tuning(grid=grid)
+
+    # the one-launch form's grid: the fastest of 2, 4 and 8 blocks per SM
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    best_g = None
+    for g in (2 * sms, 4 * sms, 8 * sms):
+        one_grid[0] = g
+        restore()
+        one_launch()
+        restore()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        one_launch()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1)
+        if best_g is None or t < best_g[0]:
+            best_g = (t, g)
+    one_grid[0] = best_g[1]
+
     res = {}
-    for name, fn in (("batched", batched), ("per_instance", unbatched)):
+    for name, fn in (("batched", batched), ("per_instance", unbatched), ("one_launch", one_launch)):
         for _ in range(args.warmup):
             restore()
             fn()
@@ -515,6 +546,9 @@ def run_batch(args):
                               "solo": B.solo().tolist(), "grid": grid}},
         "batched": res["batched"], "per_instance": res["per_instance"],
         "speedup_vs_per_instance": res["batched"]["moves_per_s"] / res["per_instance"]["moves_per_s"],
+        "one_launch": dict(res["one_launch"], grid=one_grid[0],
+                           note="every instance in the one persistent evaluation launch per step (no solo instance)"),
+        "one_launch_vs_per_instance": res["one_launch"]["moves_per_s"] / res["per_instance"]["moves_per_s"],
     }))
 
 
