@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(32 * MD_EVAL_WARPS, MD_FULL_MIN_BLOCKS) k_eval
 // instances of uneven size.  Tiles are taken in grid-stride order over the global work list.
 // TW_ANY: at least one item has time windows; items without them take the TW = false path.
 template <bool TW_ANY>
-__global__ void __launch_bounds__(32 * MD_EVAL_WARPS, MD_EVAL_MIN_BLOCKS) k_eval_batch(const BatchItem *__restrict__ items, int n_items, int total_tiles,
+__global__ void __launch_bounds__(32 * MD_EVAL_WARPS, MD_BATCH_MIN_BLOCKS) k_eval_batch(const BatchItem *__restrict__ items, int n_items, int total_tiles,
                                                       uint32_t flags, int *next_tile) {
     // Each warp keeps the context of its current tile in its own shared-memory slot: the
     // instance, solution and scratch descriptors are read from there when needed instead of

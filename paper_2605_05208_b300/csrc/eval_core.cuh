@@ -36,8 +36,15 @@
 #endif
 
 #ifndef MD_EVAL_MIN_BLOCKS
-// evaluation blocks resident per SM: 16 warps per SM, a register budget of 128 per thread
-#define MD_EVAL_MIN_BLOCKS (16 / MD_EVAL_WARPS)
+// evaluation blocks resident per SM: 24 warps per SM, a register budget of 85 per thread.  The
+// list paths wait on dependent gathers; more resident warps hide more of that latency than the
+// spills they cost (learned 20x10000 descents: 0.709 s against 0.774 s at 2 blocks and 1.057 s
+// at 1 block without spills)
+#define MD_EVAL_MIN_BLOCKS 3
+#endif
+#ifndef MD_BATCH_MIN_BLOCKS
+// blocks of the batched evaluation resident per SM (16 warps, 128 registers a thread)
+#define MD_BATCH_MIN_BLOCKS 2
 #endif
 
 namespace {

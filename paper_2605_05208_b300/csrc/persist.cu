@@ -31,6 +31,11 @@
 #include "eval_core.cuh"
 #include "step.cuh"
 
+#ifndef MD_PERSIST_MIN_BLOCKS
+// blocks of the persistent descent resident per SM (16 warps, 128 registers a thread)
+#define MD_PERSIST_MIN_BLOCKS 2
+#endif
+
 namespace {
 
 struct RQ {
@@ -194,7 +199,7 @@ __device__ void queue_tiles(const Queues &Q, int s, int k, int lane) {
 }
 
 template <bool TW>
-__global__ void __launch_bounds__(32 * MD_EVAL_WARPS, MD_EVAL_MIN_BLOCKS)
+__global__ void __launch_bounds__(32 * MD_EVAL_WARPS, MD_PERSIST_MIN_BLOCKS)
 k_descend_persistent(DevInst I, DevSols D, DevMoves M, uint32_t flags, int wpc_full, Queues Q) {
     // double-buffered by the parity of the block's task: the current task and the next one
     __shared__ NextTask s_nx[2];
@@ -307,7 +312,7 @@ md_status md_descend_persistent(md_solutions *s, md_moves *m, uint32_t eflags, i
         MD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_descend_persistent<false>, 32 * MD_EVAL_WARPS, smem));
     }
     if (per_sm < 1) { md_set_error("md_descend: the persistent kernel does not fit an SM"); return MD_ERR_STATE; }
-    if (per_sm > MD_EVAL_MIN_BLOCKS) per_sm = MD_EVAL_MIN_BLOCKS;
+    if (per_sm > MD_PERSIST_MIN_BLOCKS) per_sm = MD_PERSIST_MIN_BLOCKS;
     const int grid = per_sm * sms;
     // ring sizes: at most T tiles (one step) of each solution are queued or being read at once,
     // and each block holds at most one claimed index; twice that, so that a block never waits to
