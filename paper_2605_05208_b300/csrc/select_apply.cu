@@ -72,6 +72,9 @@ static size_t step_smem(const md_solutions *s, int threads) {
 #ifndef MD_STEP_THREADS
 #define MD_STEP_THREADS 256  // threads of a step CTA
 #endif
+#ifndef MD_WSELECT_THREADS
+#define MD_WSELECT_THREADS 512  // threads of the wide step's selection CTA
+#endif
 static const int STEP_THREADS = MD_STEP_THREADS;
 
 size_t md_step_smem(const md_solutions *s) { return step_smem(s, STEP_THREADS); }
@@ -138,9 +141,9 @@ md_status md_launch_step_wide(md_solutions *s, md_moves *m, cudaStream_t st, int
     if (count < 0) count = s->n_sol - s0;
     if (count <= 0) return MD_OK;
     const DevInst &I = s->inst->d;
-    const size_t sm = step_smem(s, STEP_THREADS);
+    const size_t sm = step_smem(s, MD_WSELECT_THREADS);
     MD_CUDA(md_allow_smem((const void *)k_wselect, sm));
-    k_wselect<<<count, STEP_THREADS, sm, st>>>(I, s->d, m->d, s0);
+    k_wselect<<<count, MD_WSELECT_THREADS, sm, st>>>(I, s->d, m->d, s0);
     MD_CUDA(cudaGetLastError());
     // at most one move per route slot, at most one touched route per slot
     const dim3 grid((s->R + MD_WIDE_WARPS - 1) / MD_WIDE_WARPS, count);

@@ -26,6 +26,7 @@ struct StepSmem {
     int *touched;              // [R]
     int *cnt;                  // [nd]
     int *stage;                // [nwarps * 2K]
+    int stage_ints;            // nwarps * 2K
 };
 
 __device__ __forceinline__ StepSmem carve(unsigned char *base, int R, int nd, int K, int nwarps) {
@@ -36,8 +37,7 @@ __device__ __forceinline__ StepSmem carve(unsigned char *base, int R, int nd, in
     m.touched = m.free_slots + R;
     m.cnt = m.touched + R;
     m.stage = m.cnt + ((nd + 3) & ~3);
-    (void)nwarps;
-    (void)K;
+    m.stage_ints = nwarps * 2 * K;
     return m;
 }
 
@@ -54,9 +54,18 @@ __device__ int select_moves(const DevInst &I, const DevSols &D, const DevMoves &
     double f = 0.0;
     uint32_t id = MD_NO_ID, rt = 0;
     int valid = 0;
-    for (int k = tid; k < nrec; k += nt) {
-        LeadRec r = M.lpart[(size_t)s * M.nblk + k];
-        if (r.id != MD_NO_ID && (!valid || r.f < f || (r.f == f && r.id < id))) { f = r.f; id = r.id; rt = r.routes; valid = 1; }
+    // four records in flight per thread (the minimum by (f, id) does not depend on the order)
+    for (int k0 = tid; k0 < nrec; k0 += 4 * nt) {
+        LeadRec r[4];
+        for (int q = 0; q < 4; q++) {
+            const int k = k0 + q * nt;
+            if (k < nrec) r[q] = M.lpart[(size_t)s * M.nblk + k];
+            else r[q].id = MD_NO_ID;
+        }
+        for (int q = 0; q < 4; q++)
+            if (r[q].id != MD_NO_ID && (!valid || r[q].f < f || (r[q].f == f && r[q].id < id))) {
+                f = r[q].f; id = r[q].id; rt = r[q].routes; valid = 1;
+            }
     }
     for (int o = 16; o > 0; o >>= 1) {
         const double of = __shfl_xor_sync(0xffffffffu, f, o);
@@ -84,8 +93,13 @@ __device__ int select_moves(const DevInst &I, const DevSols &D, const DevMoves &
     const int have_leader = s_n;
     // followers: the route pairs the evaluation listed (each entry is cleared for the next step)
     const size_t tab = (size_t)s * R * R;
+    // the candidates: the first scap in the staging area of shared memory (unused until the
+    // apply), the rest in global memory at the same index
     unsigned long long *ck = M.cand_key + (size_t)s * M.ncap;
     uint32_t *cr = M.cand_rt + (size_t)s * M.ncap;
+    unsigned long long *sk = reinterpret_cast<unsigned long long *>(((uintptr_t)sm.stage + 7) & ~(uintptr_t)7);
+    const int scap = (sm.stage_ints - 2) / 3;  // 12 bytes a candidate, after the 8-byte alignment
+    uint32_t *sr = reinterpret_cast<uint32_t *>(sk + scap);
     const bool use = have_leader && multi;
     const int nf = min((int)M.fcount[s], M.ncap);
     const uint32_t *fl = M.flist + (size_t)s * M.ncap;
@@ -97,7 +111,9 @@ __device__ int select_moves(const DevInst &I, const DevSols &D, const DevMoves &
         const int i = (int)(pair / (uint32_t)R), j = (int)(pair % (uint32_t)R);
         if (i == s_rA || i == s_rB || j == s_rA || j == s_rB) continue;  // blocked by the leader
         const int k = atomicAdd(&s_ncand, 1);
-        if (k < M.ncap) { ck[k] = key; cr[k] = (uint32_t)i | ((uint32_t)j << 16); }
+        const uint32_t rij = (uint32_t)i | ((uint32_t)j << 16);
+        if (k < scap) { sk[k] = key; sr[k] = rij; }
+        else if (k < M.ncap) { ck[k] = key; cr[k] = rij; }
     }
     __syncthreads();
     if (tid == 0) M.fcount[s] = 0;
@@ -116,25 +132,29 @@ __device__ int select_moves(const DevInst &I, const DevSols &D, const DevMoves &
         __syncthreads();
         int alive = 0;
         for (int k = tid; k < ncand; k += nt) {
-            const unsigned long long key = ck[k];
+            unsigned long long &kk = k < scap ? sk[k] : ck[k];
+            const unsigned long long key = kk;
             if (key == MD_EMPTY_KEY) continue;
-            const int i = cr[k] & 0xffff, j = cr[k] >> 16;
-            if (sm.claimed[md_ix(I.err, i, D.R)] || sm.claimed[md_ix(I.err, j, D.R)]) { ck[k] = MD_EMPTY_KEY; continue; }
+            const uint32_t rij = k < scap ? sr[k] : cr[k];
+            const int i = rij & 0xffff, j = rij >> 16;
+            if (sm.claimed[md_ix(I.err, i, D.R)] || sm.claimed[md_ix(I.err, j, D.R)]) { kk = MD_EMPTY_KEY; continue; }
             atomicMin(&sm.rmin[md_ix(I.err, i, D.R)], key);
             atomicMin(&sm.rmin[md_ix(I.err, j, D.R)], key);
             alive = 1;
         }
         __syncthreads();
         for (int k = tid; k < ncand; k += nt) {
-            const unsigned long long key = ck[k];
+            unsigned long long &kk = k < scap ? sk[k] : ck[k];
+            const unsigned long long key = kk;
             if (key == MD_EMPTY_KEY) continue;
-            const int i = cr[k] & 0xffff, j = cr[k] >> 16;
+            const uint32_t rij = k < scap ? sr[k] : cr[k];
+            const int i = rij & 0xffff, j = rij >> 16;
             if (sm.rmin[md_ix(I.err, i, D.R)] == key && sm.rmin[md_ix(I.err, j, D.R)] == key) {
                 const int n = atomicAdd(&s_n, 1);
                 M.sel[md_ix(I.err, (size_t)s * R + n, (size_t)D.S * D.R)] = (uint32_t)(key & 0xffffffffu);
                 sm.claimed[md_ix(I.err, i, D.R)] = 1;
                 sm.claimed[md_ix(I.err, j, D.R)] = 1;
-                ck[k] = MD_EMPTY_KEY;
+                kk = MD_EMPTY_KEY;
             }
         }
         if (!__syncthreads_or(alive)) break;
