@@ -459,7 +459,7 @@ extern "C" md_status md_descend(md_solutions *s, const md_config *cfg, md_stats 
             rr = enqueue(false);
             if (rr != MD_OK) break;
         }
-        launches += (1LL + step_launches) * steps_per_poll * G;
+        launches += ((long long)md_eval_kernels(s, eflags) + step_launches) * steps_per_poll * G;
         eval_launches += (long long)steps_per_poll * G;
         passes_done += poll;
         cudaError_t ce = cudaMemcpyAsync(state.data(), s->d.state, sizeof(int32_t) * MD_STATE * s->n_sol, cudaMemcpyDeviceToHost, st);

@@ -418,7 +418,8 @@ extern "C" md_status md_batch_descend(md_batch *b, const md_config *cfg, md_stat
             if (rr != MD_OK) break;
         }
         launches += 2LL * steps * (nb > 0 ? 1 : 0) + 1;
-        for (int i : solo_items) launches += (1LL + (md_wide_step(b->sols[i], cfg->wide_step) ? 4 : 1)) * steps;
+        for (int i : solo_items)
+            launches += ((long long)md_eval_kernels(b->sols[i], eflags) + (md_wide_step(b->sols[i], cfg->wide_step) ? 4 : 1)) * steps;
         iters++;
         passes += poll;
         cudaError_t ce = cudaMemsetAsync(b->running_d, 0, sizeof(int), st);

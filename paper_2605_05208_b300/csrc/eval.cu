@@ -32,12 +32,51 @@ __global__ void __launch_bounds__(32 * MD_EVAL_WARPS, MD_EVAL_MIN_BLOCKS) k_eval
     best_init(b);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
     const int wpc = C.lists ? 1 : wpc_full;
-    if (full_path(C, op)) return;  // k_eval_full scores this solution
-    if (C.lists && I.theta <= 64 && (op == MD_OP_RELOCATE || op == MD_OP_SWAP))
-        eval_tile_lists<TW>(C, op, blockIdx.x * wpb, gridDim.x * wpb, b, s_wl, s_tc, s_cnt);  // the whole block
-    else if (op >= 0)
+    if (full_path(C, op) || tile_path(C, op)) return;  // k_eval_full or k_eval_lists scores this solution
+    (void)s_cnt;
+    if (op >= 0)
         for (int gw = blockIdx.x * wpb + warp; gw < I.nc * wpc; gw += gridDim.x * wpb)
             if (in_range(C, gw / wpc)) eval_customer<TW>(C, op, gw / wpc, lane, b, s_wl[warp], gw % wpc, wpc, &s_tc[warp]);
+    warp_commit(C, b, (size_t)blockIdx.x * wpb + warp, lane);
+}
+
+#ifndef MD_LISTS_MIN_BLOCKS
+// blocks of the tile-list kernel resident per SM: 32 warps, 64 registers a thread (learned
+// 20x10000 descents of 80 passes: 0.694 s; 0.700 s at 3 blocks, 0.761 s at 2)
+#define MD_LISTS_MIN_BLOCKS 4
+#endif
+
+// Relocate and Swap on neighbour lists of at most 64 candidates, by whole blocks (the solutions
+// for which tile_path holds; k_eval scores the others).  Same grid and leader records as k_eval.
+// A kernel of its own, so that its registers are those of this path alone.
+template <bool TW>
+__global__ void __launch_bounds__(32 * MD_EVAL_WARPS, MD_LISTS_MIN_BLOCKS) k_eval_lists(DevInst I, DevSols D, DevMoves M,
+                                                                                       uint32_t flags, int s0) {
+    Ctx C;
+    C.I = I; C.D = D; C.M = M; C.flags = flags;
+    C.s = s0 + blockIdx.y;
+    C.open = (I.variant & MD_VARIANT_OPEN) != 0;
+    C.sym = (I.variant & MD_VARIANT_SYMMETRIC) != 0;
+    const int op_raw = D.ops[C.s];
+    const int op = op_raw < 0 ? -1 : (op_raw & MD_OP_MASK);
+    C.lists = I.theta > 0 && !(op_raw >= 0 && (op_raw & MD_OP_SWEEP));
+    if (!tile_path(C, op)) return;  // k_eval or k_eval_full scores this solution
+    __shared__ double s_w[4];
+    __shared__ float s_wf[4];
+    if (threadIdx.x < 4) {
+        s_w[threadIdx.x] = D.w[4 * C.s + threadIdx.x];
+        s_wf[threadIdx.x] = (float)s_w[threadIdx.x];
+    }
+    __syncthreads();
+    C.w = s_w;
+    C.wf = s_wf;
+    __shared__ int s_wl[MD_EVAL_WARPS][64];
+    __shared__ TileCtx s_tc[MD_EVAL_WARPS];
+    __shared__ int s_cnt[2 * MD_EVAL_WARPS];
+    Best b;
+    best_init(b);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    eval_tile_lists<TW>(C, op, blockIdx.x * wpb, gridDim.x * wpb, b, s_wl, s_tc, s_cnt);
     warp_commit(C, b, (size_t)blockIdx.x * wpb + warp, lane);
 }
 
@@ -184,12 +223,22 @@ md_status md_launch_eval(md_solutions *s, md_moves *m, uint32_t flags, cudaStrea
     if (I.variant & MD_VARIANT_TW) k_eval<true><<<grid, 32 * MD_EVAL_WARPS, 0, st>>>(I, s->d, m->d, flags, s0, wpc);
     else k_eval<false><<<grid, 32 * MD_EVAL_WARPS, 0, st>>>(I, s->d, m->d, flags, s0, wpc);
     MD_CUDA(cudaGetLastError());
+    if (I.theta > 0 && I.theta <= 64) {  // the solutions on short neighbour lists
+        if (I.variant & MD_VARIANT_TW) k_eval_lists<true><<<grid, 32 * MD_EVAL_WARPS, 0, st>>>(I, s->d, m->d, flags, s0);
+        else k_eval_lists<false><<<grid, 32 * MD_EVAL_WARPS, 0, st>>>(I, s->d, m->d, flags, s0);
+        MD_CUDA(cudaGetLastError());
+    }
     if (!(flags & MD_EVAL_DUMP)) {  // the solutions evaluated over the full neighbourhood
         if (I.variant & MD_VARIANT_TW) k_eval_full<true><<<grid, 32 * MD_EVAL_WARPS, 0, st>>>(I, s->d, m->d, flags, s0, wpc);
         else k_eval_full<false><<<grid, 32 * MD_EVAL_WARPS, 0, st>>>(I, s->d, m->d, flags, s0, wpc);
         MD_CUDA(cudaGetLastError());
     }
     return MD_OK;
+}
+
+int md_eval_kernels(const md_solutions *s, uint32_t flags) {
+    const int theta = s->inst->d.theta;
+    return 1 + (theta > 0 && theta <= 64 ? 1 : 0) + ((flags & MD_EVAL_DUMP) ? 0 : 1);
 }
 
 md_status md_launch_eval_batch(const BatchItem *items, int n_items, int total_tiles, int grid, bool tw,

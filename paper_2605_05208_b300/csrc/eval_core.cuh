@@ -1530,6 +1530,11 @@ __device__ __forceinline__ bool full_path(const Ctx &C, int op) {
            (op == MD_OP_RELOCATE || op == MD_OP_SWAP || op == MD_OP_TWO_OPT_STAR);
 }
 
+// Relocate or Swap on neighbour lists of at most 64 candidates: the block-wide tile path.
+__device__ __forceinline__ bool tile_path(const Ctx &C, int op) {
+    return C.lists && C.I.theta <= 64 && (op == MD_OP_RELOCATE || op == MD_OP_SWAP);
+}
+
 __device__ __forceinline__ void best_init(Best &b) {
     b.f = 0.0; b.id = MD_NO_ID; b.valid = 0; b.fx = 0; b.routes = 0; b.n = 0; b.nx = 0;
     b.dD = b.dT = b.dL = b.dU = b.dV = 0;

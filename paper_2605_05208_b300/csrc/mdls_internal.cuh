@@ -335,6 +335,7 @@ md_status md_load_routes(md_solutions *S, const int32_t *nodes, const int64_t *o
                          bool partial, cudaStream_t st);
 // s0 / count restrict a launch to solutions s0 .. s0 + count - 1 (count < 0: all from s0).
 md_status md_launch_eval(md_solutions *s, md_moves *m, uint32_t flags, cudaStream_t st, int s0 = 0, int count = -1);
+int md_eval_kernels(const md_solutions *s, uint32_t flags);  // kernels one md_launch_eval launches
 md_status md_launch_select(md_solutions *s, md_moves *m, int multi, cudaStream_t st);
 md_status md_launch_apply(md_solutions *s, md_moves *m, int update_lambda, cudaStream_t st);
 md_status md_launch_step(md_solutions *s, md_moves *m, cudaStream_t st, int s0 = 0, int count = -1);
