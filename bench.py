@@ -557,12 +557,13 @@ LEARNED_SEEDS = 5       # instances of seeds 1..5; the timed steps cycle through
 LEARNED_POOL = 256      # eta-ranked candidate pool per customer that the MLP scores
 LEARNED_TOPK = 64
 LEARNED_SWEEP = 20      # full plain sweep every 20 steps
-# DRAM bytes (read + write) per evaluation launch of the learned descents (one k_eval and one
-# k_eval_full launch of a stream group of 4 solutions, the unit the line's ms_per_launch times),
-# from ncu (dram__bytes_read.sum + dram__bytes_write.sum) over the 480 launch pairs of the first
-# 24 passes of one 16-solution descent of seed 1 (`python -m paper_2605_05208_b300.profile_run
-# learned 24 16`, profiles/learned-20x10000.md); stale once either kernel changes.
-TRAFFIC_20X10000 = 536.9e6
+# DRAM bytes (read + write) per evaluation launch of the learned descents (the k_eval,
+# k_eval_lists and k_eval_full launches of a stream group of 4 solutions, the unit the line's
+# ms_per_launch times), from ncu (dram__bytes_read.sum + dram__bytes_write.sum) over the 480
+# evaluations of the first 24 passes of one 16-solution descent of seed 1 (`python -m
+# paper_2605_05208_b300.profile_run learned 24 16`, profiles/learned-20x10000.md); stale once
+# one of the three kernels changes.
+TRAFFIC_20X10000 = 589.9e6
 
 
 def learned_workload(n_sol: int, seed: int = SEED, first: int = 0):
