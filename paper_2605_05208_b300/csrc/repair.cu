@@ -134,8 +134,8 @@ __device__ InsBest warp_best(const int2 *row, int M, int lane) {
 // the earlier position.
 // arc: the route's arc costs c(c_k, c_{k+1}) (k = 0..L, c_0 = ds, c_{L+1} = de) staged in shared
 // memory, or nullptr.  With step 1 the cost c(u, c_{k+1}) of position k is carried over as
-// c(c_{k+1}, u) of position k + 1 (k_dist builds the matrix from Euclidean distances, so it is symmetric whatever the
-// variant flags say), so a position reads one new entry.
+// c(c_{k+1}, u) of position k + 1, so a position reads one new entry: k_dist builds the matrix
+// from Euclidean distances, so it is symmetric whatever the variant flags say.
 template <bool TW>
 __device__ int2 route_best(const DevInst &I, const DevSols &D, int s, int r, int u, bool feas, int k0 = 0,
                            int step = 1, const int *arc = nullptr) {
